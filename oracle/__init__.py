@@ -1,0 +1,25 @@
+"""Plain FP64 CPU oracle for the hp-DG subspace-correction solver.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's
+CPU-baseline leg may import this package.  It shares no code with the CUDA
+library: it assembles the sparse DG matrix, the conforming prolongation, the
+low-order-refined matrix and the block smoother explicitly from their
+definitions, and runs PCG with them.
+
+Modules
+    basis      Gauss-Lobatto / Gauss-Legendre rules and Lagrange polynomials
+    topology   faces, sub-faces, hanging vertices and master edges of a 2D mesh
+    dg         SIPG and BR2 matrices (Section 2, Eq. fe-problem; Section 4.4)
+    space      conforming prolongation P, V_J / V_e classification (Section 3)
+    lor        low-order-refined matrices (Section 3.4)
+    amg        the deterministic smoothed-aggregation V-cycle used for LOR
+    solver     the additive preconditioner B and PCG (Section 4.1)
+    rhs        load vector of the synthetic sine right-hand side
+
+Parity status: every function is pinned by tests/test_oracle_*.py against
+closed forms, manufactured solutions, invariants or brute force, except the
+smoothed-aggregation AMG, whose aggregation choices have no counterpart in the
+paper (the paper uses BoomerAMG); its V-cycle is pinned only by properties
+(symmetry, exactness on a single level, Galerkin identity) - parity unpinned
+with respect to the paper.
+"""

@@ -1,0 +1,61 @@
+"""Low-order-refined matrices (Section 3.4).
+
+For element k of degree p the LOR element matrix is the bilinear (Q1) finite
+element stiffness matrix on the Cartesian sub-mesh whose vertices are the
+(p+1)^2 Gauss-Lobatto nodes of k.  A-tilde is block diagonal with these
+blocks (on the DG numbering); the LOR conforming matrix is P^T A-tilde P.
+Each Q1 sub-cell matrix is integrated here with a 2x2 Gauss rule from the
+bilinear shape functions (exact for the bilinear stiffness).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import basis
+from .dg import DGSpace
+
+
+def q1_cell_stiffness(a: float, b: float) -> np.ndarray:
+    """Stiffness of the 4 bilinear functions on an a x b rectangle, corner
+    order (0,0), (1,0), (0,1), (1,1)."""
+    x, w = basis.gauss(2)
+    K = np.zeros((4, 4))
+    for gx, wx in zip(x, w):
+        for gy, wy in zip(x, w):
+            # shape functions N = Nx(s) Ny(t) with Nx in {1-s, s}
+            dNx = np.array([-1.0, 1.0]) / a
+            Nx = np.array([1.0 - gx, gx])
+            dNy = np.array([-1.0, 1.0]) / b
+            Ny = np.array([1.0 - gy, gy])
+            gxv = np.array([dNx[i] * Ny[j] for j in range(2) for i in range(2)])
+            gyv = np.array([Nx[i] * dNy[j] for j in range(2) for i in range(2)])
+            K += wx * wy * a * b * (np.outer(gxv, gxv) + np.outer(gyv, gyv))
+    return K
+
+
+def lor_element(p: int, h: float = 1.0) -> np.ndarray:
+    g = basis.gll_nodes(p) * h
+    n = p + 1
+    A = np.zeros((n * n, n * n))
+    for j in range(p):
+        for i in range(p):
+            K = q1_cell_stiffness(g[i + 1] - g[i], g[j + 1] - g[j])
+            idx = [j * n + i, j * n + i + 1, (j + 1) * n + i, (j + 1) * n + i + 1]
+            A[np.ix_(idx, idx)] += K
+    return A
+
+
+def assemble_lor(space: DGSpace) -> sp.csr_matrix:
+    blocks = []
+    for k in range(space.topo.n):
+        blocks.append(lor_element(int(space.topo.p[k]), space.h(k)))
+    return sp.block_diag([sp.csr_matrix(b) for b in blocks], format="csr")
+
+
+def lor_conforming(space: DGSpace, P: sp.csr_matrix) -> sp.csr_matrix:
+    At = assemble_lor(space)
+    Ac = (P.T @ At @ P).tocsr()
+    Ac.sum_duplicates()
+    Ac.sort_indices()
+    return Ac

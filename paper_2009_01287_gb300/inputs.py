@@ -1,0 +1,162 @@
+"""Seeded synthetic inputs shared by the CUDA path, the tests and the benchmark.
+
+This module holds no arithmetic of the method: it only draws meshes (leaf boxes
+on an integer dyadic lattice, with a polynomial degree per leaf) and the
+parameters of the right-hand side.  Everything that discretises or solves lives
+elsewhere.
+
+Mesh description (dimension d = 2 or 3):
+    lo    int32 (n, d)  lower corner of each leaf in lattice units
+    size  int32 (n,)    edge length in lattice units (a power of two)
+    p     int32 (n,)    polynomial degree of the leaf
+    extent int tuple    domain [0, extent_0] x ... in lattice units
+    lattice_h float     physical length of one lattice unit
+
+Refinement process (random-refinement experiment of Section 4.3, with the
+probability / depth of the synthetic workloads): every base cell is refined
+recursively; a cell at depth < max_depth is split into 2^d children with
+probability `prob`, children visited in Morton (x-fastest) order; one PCG64
+stream per mesh seed, all coin flips first, then the degrees.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class MeshDesc:
+    dim: int
+    lo: np.ndarray          # int32 (n, dim)
+    size: np.ndarray        # int32 (n,)
+    p: np.ndarray           # int32 (n,)
+    extent: Tuple[int, ...]  # lattice units per axis
+    lattice_h: float
+
+    @property
+    def n_elems(self) -> int:
+        return int(self.size.shape[0])
+
+    def n_dofs(self) -> int:
+        return int(np.sum((self.p.astype(np.int64) + 1) ** self.dim))
+
+
+@dataclasses.dataclass
+class SineRHS:
+    """f(x) = sum_m a_m prod_d sin(pi k_{m,d} x_d) on the unit box."""
+    amps: np.ndarray    # float64 (m,)
+    waves: np.ndarray   # int32 (m, dim)
+
+
+def _morton_key(coords: Sequence[int]) -> int:
+    key = 0
+    for bit in range(16):
+        for d, c in enumerate(coords):
+            key |= ((c >> bit) & 1) << (bit * len(coords) + d)
+    return key
+
+
+def _child_offsets(dim: int) -> List[Tuple[int, ...]]:
+    # Morton order: x fastest.
+    out = []
+    for k in range(1 << dim):
+        out.append(tuple((k >> d) & 1 for d in range(dim)))
+    return out
+
+
+def random_refined_mesh(dim: int, base: int, max_depth: int, prob: float,
+                        pmin: int, pmax: int, seed: int,
+                        base_y: Optional[int] = None) -> MeshDesc:
+    """Base grid of `base`^dim unit cells, refined at random (see module doc)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cell = 1 << max_depth
+    counts = [base] * dim
+    if base_y is not None:
+        counts[1] = base_y
+    base_cells = [tuple(c) for c in np.ndindex(*reversed(counts))]
+    base_cells = [tuple(reversed(c)) for c in base_cells]
+    base_cells.sort(key=_morton_key)
+    kids = _child_offsets(dim)
+    los: List[Tuple[int, ...]] = []
+    sizes: List[int] = []
+
+    def visit(lo: Tuple[int, ...], size: int, depth: int) -> None:
+        split = False
+        if depth < max_depth:
+            split = bool(rng.random() < prob)
+        if not split:
+            los.append(lo)
+            sizes.append(size)
+            return
+        half = size // 2
+        for off in kids:
+            visit(tuple(l + o * half for l, o in zip(lo, off)), half, depth + 1)
+
+    for bc in base_cells:
+        visit(tuple(c * cell for c in bc), cell, 0)
+    n = len(sizes)
+    p = rng.integers(pmin, pmax + 1, size=n).astype(np.int32)
+    extent = tuple(c * cell for c in counts)
+    return MeshDesc(dim=dim, lo=np.asarray(los, dtype=np.int32).reshape(n, dim),
+                    size=np.asarray(sizes, dtype=np.int32), p=p,
+                    extent=extent, lattice_h=1.0 / float(base * cell))
+
+
+def uniform_mesh(dim: int, base: int, p: int) -> MeshDesc:
+    """Conforming `base`^dim grid of unit squares/cubes with uniform degree p."""
+    cells = [tuple(reversed(c)) for c in np.ndindex(*([base] * dim))]
+    n = len(cells)
+    return MeshDesc(dim=dim, lo=np.asarray(cells, dtype=np.int32).reshape(n, dim),
+                    size=np.ones(n, dtype=np.int32), p=np.full(n, p, dtype=np.int32),
+                    extent=tuple([base] * dim), lattice_h=1.0 / base)
+
+
+def sine_rhs(dim: int, seed: int, n_modes: int = 4, kmax: int = 8) -> SineRHS:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    amps = rng.standard_normal(n_modes)
+    waves = rng.integers(1, kmax + 1, size=(n_modes, dim)).astype(np.int32)
+    return SineRHS(amps=amps, waves=waves)
+
+
+def random_vector(n: int, seed: int) -> np.ndarray:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.standard_normal(n)
+
+
+# ---------------------------------------------------------------- workloads
+
+def config0() -> Tuple[MeshDesc, SineRHS]:
+    """2D, 8x8 conforming squares, p = 2 (576 DOFs)."""
+    return uniform_mesh(2, 8, 2), sine_rhs(2, 0)
+
+
+def config1(seed: int = 0) -> Tuple[MeshDesc, SineRHS]:
+    """2D hp-random: 32x32 base, prob 0.3, depth <= 3, p ~ U{1..6} (~1e5 DOFs)."""
+    return random_refined_mesh(2, 32, 3, 0.3, 1, 6, seed), sine_rhs(2, seed)
+
+
+def config2(seed: int = 0, base: int = 16) -> Tuple[MeshDesc, SineRHS]:
+    """3D hp-random: base^3 hexes, prob 0.2, depth <= 2, p ~ U{1..5}."""
+    return random_refined_mesh(3, base, 2, 0.2, 1, 5, seed), sine_rhs(3, seed)
+
+
+def config3_problem(k: int, dof_lo: int = 1000, dof_hi: int = 300000
+                    ) -> Tuple[MeshDesc, SineRHS]:
+    """Problem k of the batched workload: base N = round(exp U[ln 4, ln 64]),
+    prob 0.3, depth <= 3, p ~ U{1..8}; redrawn until the DOFs fall in range."""
+    rng = np.random.Generator(np.random.PCG64(1_000_003 + k))
+    for attempt in range(1000):
+        n = int(round(math.exp(rng.uniform(math.log(4), math.log(64)))))
+        mesh = random_refined_mesh(2, n, 3, 0.3, 1, 8, seed=k * 1000 + attempt)
+        if dof_lo <= mesh.n_dofs() <= dof_hi:
+            return mesh, sine_rhs(2, k)
+    raise RuntimeError("no mesh in the DOF range")
+
+
+def small_hp_mesh(seed: int, base: int = 3, depth: int = 2, prob: float = 0.4,
+                  pmin: int = 1, pmax: int = 4, dim: int = 2) -> MeshDesc:
+    """Small irregular hp mesh for parity tests."""
+    return random_refined_mesh(dim, base, depth, prob, pmin, pmax, seed)
