@@ -1,0 +1,156 @@
+/*
+ * dg.h - C ABI of the GB300 hp-DG subspace-correction solver.
+ *
+ * Problem (Section 2, Eq. poisson / fe-problem): -Laplace(u) = f on a box
+ * domain with u = 0 on the boundary, discretised by the symmetric interior
+ * penalty (SIPG) or BR2 (Section 4.4) DG method on a mesh of axis-aligned
+ * leaf squares (2D) of variable size (hanging nodes, arbitrary irregularity)
+ * and variable degree p in 1..8, with the Gauss-Lobatto nodal basis of
+ * Section 2.2.  Solved by conjugate gradients (Section 4.1) preconditioned by
+ * B = B_B + B_C (Section 3.1, 3.3, 3.4): variational restriction P^T, a
+ * low-order-refined (LOR) conforming solve (exact or one AMG V-cycle), the
+ * prolongation P, point Jacobi on V_J and exact block solves on the V_e.
+ *
+ * Conventions shared by every entry point
+ *   - Vectors are DEVICE pointers to double, owned by the caller, in the
+ *     element-major DG layout: element k (in the order given to
+ *     dg_mesh_create) owns (p_k+1)^2 consecutive entries; inside an element
+ *     the node (ix, iy) is entry iy*(p_k+1) + ix, nodes at the Gauss-Lobatto
+ *     points of [0,1] mapped to the element.  Unless a name ends in _host.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
+ *     is stream-ordered and returns once its work is enqueued, except where
+ *     stated.  A handle is not thread-safe; distinct handles are.
+ *   - Handles are allocated and owned by the library; free them with the
+ *     matching *_destroy.  Device memory for the handle's state is allocated
+ *     by the library (cudaMalloc) at creation time.
+ *   - Errors: a non-zero dg_status; dg_last_error() returns a message for the
+ *     calling thread.  DG_EINVAL leaves no side effects.
+ */
+#ifndef DG_H_
+#define DG_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DG_OK = 0,
+  DG_EINVAL = 1,        /* invalid argument or mesh                         */
+  DG_ENOMEM = 2,        /* host or device allocation failed                 */
+  DG_ECUDA = 3,         /* a CUDA call failed                               */
+  DG_ENOTCONV = 4,      /* PCG reached maxit; x holds the last iterate      */
+  DG_ETIMEOUT = 5,      /* a bounded device-side wait gave up               */
+  DG_EUNSUPPORTED = 6   /* valid but not supported by this build            */
+} dg_status;
+
+typedef struct dg_mesh dg_mesh;
+typedef struct dg_precond dg_precond;
+
+/* Leaf boxes on an integer lattice (Section 2: mesh T, degrees p_kappa).
+ * dim must be 2.  lo: n_elems*dim lower corners (lattice units); size:
+ * n_elems edge lengths (powers of two); p: n_elems degrees in 1..8;
+ * extent: dim domain lengths in lattice units; the physical domain is
+ * [0, extent_0*lattice_h] x [0, extent_1*lattice_h].  The boxes must tile
+ * the domain exactly.  All pointers are HOST pointers, read during the call. */
+typedef struct {
+  int dim;
+  int64_t n_elems;
+  const int32_t* lo;
+  const int32_t* size;
+  const int32_t* p;
+  const int32_t* extent;
+  double lattice_h;
+} dg_mesh_desc;
+
+enum { DG_FORM_SIPG = 0, DG_FORM_BR2 = 1 };
+/* SIPG penalty (Section 2.1): sigma = eta p_e^2 / h_e (PAPER) or
+ * eta (p_e+1)^2 / h_e (P1SQ); p_e = max, h_e = min over the two sides. */
+enum { DG_PENALTY_PAPER = 0, DG_PENALTY_P1SQ = 1 };
+enum { DG_PREC_FP64 = 0, DG_PREC_MIXED = 1 };   /* preconditioner arithmetic */
+enum { DG_LOR_EXACT = 0, DG_LOR_AMG = 1 };      /* LOR conforming solve      */
+enum { DG_SMOOTHER_FULL = 0, DG_SMOOTHER_JACOBI_ONLY = 1 }; /* B or B~ (4.1) */
+
+typedef struct {
+  int form;          /* DG_FORM_*                                           */
+  double eta;        /* penalty; <= 0 selects the default (SIPG 100, BR2:
+                        the largest number of sub-faces of one element)     */
+  int penalty_form;  /* DG_PENALTY_*                                        */
+  int precision;     /* DG_PREC_*                                           */
+  int lor;           /* DG_LOR_*                                            */
+  int smoother;      /* DG_SMOOTHER_*                                       */
+  int remark_cases;  /* 1: add the further V_J cases of the remark in
+                        Section 3.2 (coarse degree <= every fine degree)    */
+} dg_options;
+
+typedef struct {
+  int iters;         /* PCG iterations performed                            */
+  double rel_res;    /* ||r||_2 / ||b||_2 at exit                           */
+  int status;        /* DG_OK or DG_ENOTCONV                                */
+  double solve_ms;   /* device time of the iteration loop (CUDA events)     */
+} dg_solve_info;
+
+typedef struct {
+  int64_t n_dofs;        /* DG unknowns                                     */
+  int64_t n_conforming;  /* dim V_C (LOR unknowns)                          */
+  int64_t n_j;           /* nodes in V_J                                    */
+  int64_t n_e;           /* nodes in the union of the V_e                   */
+  int64_t n_blocks;      /* number of V_e                                   */
+  int64_t max_block;     /* largest dim V_e                                 */
+  int64_t lor_nnz;       /* nonzeros of the LOR conforming matrix           */
+  int64_t p_nnz;         /* nonzeros of P                                   */
+  int n_levels;          /* AMG levels (1 = exact dense solve)              */
+  int64_t level_rows[16];
+  int64_t level_nnz[16];
+} dg_precond_stats;
+
+/* Build the mesh topology (sub-faces, hanging vertices, master edges) and
+ * upload the operator data.  Section 2 (mesh, DG space) and 2.1 (sigma).
+ * opts: only form, eta and penalty_form are used here.  stream: for uploads. */
+dg_status dg_mesh_create(const dg_mesh_desc* desc, const dg_options* opts,
+                         void* stream, dg_mesh** out);
+void dg_mesh_destroy(dg_mesh* mesh);
+int64_t dg_num_dofs(const dg_mesh* mesh);
+
+/* y = A x, the matrix-free DG operator of Eq. fe-problem (SIPG) or of the
+ * BR2 form (Section 4.4), FP64.  x and y: device, n_dofs doubles, must not
+ * overlap. */
+dg_status dg_apply(const dg_mesh* mesh, const double* x, double* y, void* stream);
+
+/* Set up B = B_B + B_C (Sections 3.3, 3.4, 4.1): V_J / V_e classification,
+ * the V_e generation (connected components by jump overlap), dense block
+ * inverses, diag(A) on V_J, P, the LOR matrix P^T A~ P and its solver.
+ * Host work, then uploads; synchronous. */
+dg_status dg_precond_setup(const dg_mesh* mesh, const dg_options* opts, dg_precond** out);
+void dg_precond_destroy(dg_precond* pc);
+dg_status dg_precond_stats_get(const dg_precond* pc, dg_precond_stats* out);
+
+/* z = B r (Section 4.1).  r, z: device, n_dofs doubles, must not overlap. */
+dg_status dg_precond_apply(const dg_precond* pc, const double* r, double* z, void* stream);
+
+/* PCG (Section 4.1) from x0 = 0 until ||r||_2 <= rtol ||b||_2 or maxit.
+ * b, x: device, n_dofs doubles; x receives the solution (the last iterate on
+ * DG_ENOTCONV).  The iteration runs as one CUDA graph with a device-side
+ * while loop; the call waits for it (synchronous on `stream`). */
+dg_status dg_pcg_solve(const dg_mesh* mesh, const dg_precond* pc, const double* b,
+                       double* x, double rtol, int maxit, dg_solve_info* info,
+                       void* stream);
+
+/* The same solve with HOST b and x (copied in and out by the call). */
+dg_status dg_pcg_solve_host(const dg_mesh* mesh, const dg_precond* pc, const double* b_host,
+                            double* x_host, double rtol, int maxit, dg_solve_info* info,
+                            void* stream);
+
+/* b_i = int f phi_i for f(x) = sum_m amps[m] prod_d sin(pi waves[m*dim+d] x_d)
+ * ((p+3)-point Gauss rule per direction); b: device.  Host arithmetic. */
+dg_status dg_rhs_sine(const dg_mesh* mesh, int n_modes, const double* amps,
+                      const int32_t* waves, double* b, void* stream);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* dg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DG_H_ */

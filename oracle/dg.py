@@ -183,3 +183,41 @@ def br2_eta(topo: Topology) -> float:
         if f.kp >= 0:
             count[f.kp] += 1
     return float(count.max())
+
+
+def element_rows(space: DGSpace, k: int, x: np.ndarray, eta: float, form: str = "sipg",
+                 penalty_form: str = "paper") -> np.ndarray:
+    """(A x) restricted to the DOFs of element k, assembling only the volume
+    term of k and the sub-faces touching k (same definitions as `assemble`);
+    used to check sampled outputs of very large meshes."""
+    topo = space.topo
+    p = int(topo.p[k])
+    pts, W = space.volume_quadrature(k, p + 1)
+    _, g = space.eval(k, pts)
+    K = np.einsum("qa,qb,q->ab", g[:, :, 0], g[:, :, 0], W) + \
+        np.einsum("qa,qb,q->ab", g[:, :, 1], g[:, :, 1], W)
+    y = K @ x[space.dofs(k)]
+    for f in topo.faces_of(k):
+        sides = [f.km] + ([f.kp] if f.kp >= 0 else [])
+        q = max(int(topo.p[e]) for e in sides) + 1
+        fpts, FW, n = space.face_quadrature(f, q)
+        interior = f.kp >= 0
+        J, D, I = [], [], []
+        for si, e in enumerate(sides):
+            v, gg = space.eval(e, fpts)
+            J.append((1.0 if si == 0 else -1.0) * v)
+            D.append((0.5 if interior else 1.0) * (gg @ n))
+            I.append(space.dofs(e))
+        Jm, Dm, Im = np.concatenate(J, axis=1), np.concatenate(D, axis=1), np.concatenate(I)
+        F = -(Jm.T * FW) @ Dm - (Dm.T * FW) @ Jm
+        if form == "sipg":
+            F = F + penalty(space, f, eta, penalty_form) * ((Jm.T * FW) @ Jm)
+        else:
+            coef = 0.25 if interior else 1.0
+            for e in sides:
+                v, _ = space.eval(e, fpts)
+                b = (v.T * FW) @ Jm
+                F = F + eta * coef * (b.T @ np.linalg.inv(space.mass(e)) @ b)
+        rows = slice(0, (p + 1) ** 2) if f.km == k else slice(len(I[0]), len(I[0]) + (p + 1) ** 2)
+        y = y + F[rows] @ x[Im]
+    return y

@@ -179,6 +179,15 @@ class Topology:
                 if m.t0 < tan < m.t1:
                     m.hanging.append((m.c, tan) if m.axis == 0 else (tan, m.c))
 
+    def faces_of(self, k: int) -> List[SubFace]:
+        if not hasattr(self, "_faces_of"):
+            self._faces_of = defaultdict(list)
+            for f in self.subfaces:
+                self._faces_of[f.km].append(f)
+                if f.kp >= 0:
+                    self._faces_of[f.kp].append(f)
+        return self._faces_of[k]
+
     # ------------------------------------------------------------------
     def elements_containing(self, v: Tuple[int, int]) -> List[int]:
         x0, y0 = self.lo[:, 0], self.lo[:, 1]

@@ -1,0 +1,325 @@
+"""ctypes binding of the C ABI in include/dg.h (argument marshalling only).
+
+Functions keep the C names.  Vector arguments are CUDA tensors (torch) or raw
+device pointers (int); the library does all the work.  If the shared library
+has not been built, `lib()` raises: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from .inputs import MeshDesc
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libdgsc.so")
+INSPECT_PATH = os.path.join(HERE, "_lib", "libdgsc_inspect.so")
+
+DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_ENOTCONV, DG_ETIMEOUT, DG_EUNSUPPORTED = range(7)
+DG_FORM_SIPG, DG_FORM_BR2 = 0, 1
+DG_PENALTY_PAPER, DG_PENALTY_P1SQ = 0, 1
+DG_PREC_FP64, DG_PREC_MIXED = 0, 1
+DG_LOR_EXACT, DG_LOR_AMG = 0, 1
+DG_SMOOTHER_FULL, DG_SMOOTHER_JACOBI_ONLY = 0, 1
+
+# every entry point declared in include/dg.h
+ABI_SYMBOLS = (
+    "dg_mesh_create", "dg_mesh_destroy", "dg_num_dofs", "dg_apply", "dg_precond_setup",
+    "dg_precond_destroy", "dg_precond_stats_get", "dg_precond_apply", "dg_pcg_solve",
+    "dg_pcg_solve_host", "dg_rhs_sine", "dg_last_error",
+)
+
+
+class DgMeshDesc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n_elems", C.c_int64), ("lo", C.POINTER(C.c_int32)),
+                ("size", C.POINTER(C.c_int32)), ("p", C.POINTER(C.c_int32)),
+                ("extent", C.POINTER(C.c_int32)), ("lattice_h", C.c_double)]
+
+
+class DgOptions(C.Structure):
+    _fields_ = [("form", C.c_int), ("eta", C.c_double), ("penalty_form", C.c_int),
+                ("precision", C.c_int), ("lor", C.c_int), ("smoother", C.c_int),
+                ("remark_cases", C.c_int)]
+
+
+class DgSolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("rel_res", C.c_double), ("status", C.c_int),
+                ("solve_ms", C.c_double)]
+
+
+class DgPrecondStats(C.Structure):
+    _fields_ = [("n_dofs", C.c_int64), ("n_conforming", C.c_int64), ("n_j", C.c_int64),
+                ("n_e", C.c_int64), ("n_blocks", C.c_int64), ("max_block", C.c_int64),
+                ("lor_nnz", C.c_int64), ("p_nnz", C.c_int64), ("n_levels", C.c_int),
+                ("level_rows", C.c_int64 * 16), ("level_nnz", C.c_int64 * 16)]
+
+
+_lib = None
+_inspect = None
+
+
+def _load(path: str):
+    if not os.path.exists(path):
+        raise RuntimeError(f"{os.path.basename(path)} is not built: run __graft_entry__.build()")
+    return C.CDLL(path)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = _load(LIB_PATH)
+        vp, i64, dp, st = C.c_void_p, C.c_int64, C.c_void_p, C.c_int
+        L.dg_mesh_create.argtypes = [C.POINTER(DgMeshDesc), C.POINTER(DgOptions), vp, C.POINTER(vp)]
+        L.dg_mesh_destroy.argtypes = [vp]
+        L.dg_num_dofs.argtypes = [vp]
+        L.dg_num_dofs.restype = i64
+        L.dg_apply.argtypes = [vp, dp, dp, vp]
+        L.dg_precond_setup.argtypes = [vp, C.POINTER(DgOptions), C.POINTER(vp)]
+        L.dg_precond_destroy.argtypes = [vp]
+        L.dg_precond_stats_get.argtypes = [vp, C.POINTER(DgPrecondStats)]
+        L.dg_precond_apply.argtypes = [vp, dp, dp, vp]
+        L.dg_pcg_solve.argtypes = [vp, vp, dp, dp, C.c_double, C.c_int, C.POINTER(DgSolveInfo), vp]
+        L.dg_pcg_solve_host.argtypes = [vp, vp, dp, dp, C.c_double, C.c_int, C.POINTER(DgSolveInfo), vp]
+        L.dg_rhs_sine.argtypes = [vp, C.c_int, dp, dp, dp, vp]
+        L.dg_last_error.restype = C.c_char_p
+        for name in ABI_SYMBOLS:
+            if name not in ("dg_mesh_destroy", "dg_precond_destroy", "dg_num_dofs", "dg_last_error"):
+                getattr(L, name).restype = st
+        L.dg_mesh_destroy.restype = None
+        L.dg_precond_destroy.restype = None
+        _lib = L
+    return _lib
+
+
+class DGError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"dg status {code}: {msg}")
+        self.code = code
+
+
+def _check(code: int) -> None:
+    if code != DG_OK:
+        raise DGError(code, lib().dg_last_error().decode())
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return 0
+    if isinstance(t, int):
+        return t
+    return int(t.data_ptr())
+
+
+def _stream(s) -> int:
+    if s is None:
+        return 0
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+def make_desc(mesh: MeshDesc):
+    lo = np.ascontiguousarray(mesh.lo, dtype=np.int32)
+    size = np.ascontiguousarray(mesh.size, dtype=np.int32)
+    p = np.ascontiguousarray(mesh.p, dtype=np.int32)
+    ext = np.ascontiguousarray(mesh.extent, dtype=np.int32)
+    keep = (lo, size, p, ext)
+    d = DgMeshDesc(mesh.dim, mesh.n_elems, lo.ctypes.data_as(C.POINTER(C.c_int32)),
+                   size.ctypes.data_as(C.POINTER(C.c_int32)), p.ctypes.data_as(C.POINTER(C.c_int32)),
+                   ext.ctypes.data_as(C.POINTER(C.c_int32)), float(mesh.lattice_h))
+    return d, keep
+
+
+def make_options(form=DG_FORM_SIPG, eta=0.0, penalty_form=DG_PENALTY_PAPER, precision=DG_PREC_FP64,
+                 lor=DG_LOR_AMG, smoother=DG_SMOOTHER_FULL, remark_cases=0) -> DgOptions:
+    return DgOptions(form, eta, penalty_form, precision, lor, smoother, remark_cases)
+
+
+# ------------------------------------------------------------ C-named calls
+def dg_mesh_create(mesh: MeshDesc, opts: Optional[DgOptions] = None, stream=None) -> int:
+    d, keep = make_desc(mesh)
+    h = C.c_void_p()
+    _check(lib().dg_mesh_create(C.byref(d), C.byref(opts) if opts else None, _stream(stream), C.byref(h)))
+    return h.value
+
+
+def dg_mesh_destroy(h: int) -> None:
+    lib().dg_mesh_destroy(h)
+
+
+def dg_num_dofs(h: int) -> int:
+    return int(lib().dg_num_dofs(h))
+
+
+def dg_apply(h: int, x, y, stream=None) -> None:
+    _check(lib().dg_apply(h, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def dg_precond_setup(mesh_h: int, opts: Optional[DgOptions] = None) -> int:
+    h = C.c_void_p()
+    _check(lib().dg_precond_setup(mesh_h, C.byref(opts) if opts else None, C.byref(h)))
+    return h.value
+
+
+def dg_precond_destroy(h: int) -> None:
+    lib().dg_precond_destroy(h)
+
+
+def dg_precond_stats_get(h: int) -> DgPrecondStats:
+    s = DgPrecondStats()
+    _check(lib().dg_precond_stats_get(h, C.byref(s)))
+    return s
+
+
+def dg_precond_apply(h: int, r, z, stream=None) -> None:
+    _check(lib().dg_precond_apply(h, _ptr(r), _ptr(z), _stream(stream)))
+
+
+def dg_pcg_solve(mesh_h: int, pc_h: int, b, x, rtol: float, maxit: int, stream=None,
+                 raise_on_notconv: bool = True) -> DgSolveInfo:
+    info = DgSolveInfo()
+    code = lib().dg_pcg_solve(mesh_h, pc_h, _ptr(b), _ptr(x), rtol, maxit, C.byref(info), _stream(stream))
+    if code != DG_ENOTCONV or raise_on_notconv:
+        _check(code)
+    return info
+
+
+def dg_pcg_solve_host(mesh_h: int, pc_h: int, b: np.ndarray, x: np.ndarray, rtol: float, maxit: int,
+                      stream=None) -> DgSolveInfo:
+    assert b.dtype == np.float64 and x.dtype == np.float64 and b.flags.c_contiguous and x.flags.c_contiguous
+    info = DgSolveInfo()
+    _check(lib().dg_pcg_solve_host(mesh_h, pc_h, b.ctypes.data, x.ctypes.data, rtol, maxit,
+                                   C.byref(info), _stream(stream)))
+    return info
+
+
+def dg_rhs_sine(mesh_h: int, amps, waves, b, stream=None) -> None:
+    a = np.ascontiguousarray(amps, dtype=np.float64)
+    w = np.ascontiguousarray(waves, dtype=np.int32)
+    _check(lib().dg_rhs_sine(mesh_h, len(a), a.ctypes.data, w.ctypes.data, _ptr(b), _stream(stream)))
+
+
+# ------------------------------------------------------------ handles with lifetime
+class Mesh:
+    def __init__(self, mesh: MeshDesc, opts: Optional[DgOptions] = None, stream=None):
+        self.desc = mesh
+        self.opts = opts or make_options()
+        self.h = dg_mesh_create(mesh, self.opts, stream)
+        self.n_dofs = dg_num_dofs(self.h)
+
+    def close(self):
+        if self.h:
+            dg_mesh_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Precond:
+    def __init__(self, mesh: Mesh, opts: Optional[DgOptions] = None):
+        self.mesh = mesh
+        self.h = dg_precond_setup(mesh.h, opts or mesh.opts)
+        self.stats = dg_precond_stats_get(self.h)
+
+    def close(self):
+        if self.h:
+            dg_precond_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------ host inspection
+def inspect_lib():
+    global _inspect
+    if _inspect is None:
+        L = _load(INSPECT_PATH)
+        vp = C.c_void_p
+        L.dginspect_create.argtypes = [C.POINTER(DgMeshDesc), C.POINTER(DgOptions), C.c_int]
+        L.dginspect_create.restype = vp
+        L.dginspect_destroy.argtypes = [vp]
+        L.dginspect_last_error.restype = C.c_char_p
+        for n in ("dginspect_sizes", "dginspect_kind", "dginspect_dinv"):
+            getattr(L, n).argtypes = [vp, vp]
+        for n in ("dginspect_P", "dginspect_lor"):
+            getattr(L, n).argtypes = [vp, vp, vp, vp]
+        L.dginspect_blocks.argtypes = [vp, vp, vp, vp]
+        L.dginspect_level_rows.argtypes = [vp, C.c_int]
+        L.dginspect_level_rows.restype = C.c_int64
+        L.dginspect_level_nnz.argtypes = [vp, C.c_int]
+        L.dginspect_level_nnz.restype = C.c_int64
+        L.dginspect_level_A.argtypes = [vp, C.c_int, vp, vp, vp]
+        L.dginspect_apply.argtypes = [vp, vp, vp]
+        _inspect = L
+    return _inspect
+
+
+class HostSetup:
+    """The library's host-side setup, run without a GPU (inspection only)."""
+
+    def __init__(self, mesh: MeshDesc, opts: Optional[DgOptions] = None, amg: bool = True):
+        import scipy.sparse as sp
+        self._sp = sp
+        L = inspect_lib()
+        d, keep = make_desc(mesh)
+        o = opts or make_options()
+        self.h = L.dginspect_create(C.byref(d), C.byref(o), 1 if amg else 0)
+        if not self.h:
+            raise DGError(DG_EINVAL, L.dginspect_last_error().decode())
+        s = np.zeros(9, dtype=np.int64)
+        L.dginspect_sizes(self.h, s.ctypes.data)
+        self.n, self.nC, nnzP, nnzA, nb, nbd, self.n_levels, eta, nsq = (int(v) for v in s)
+        self.eta = eta / 1e6
+        self.P = self._csr(L.dginspect_P, self.n, self.nC, nnzP)
+        self.Ac = self._csr(L.dginspect_lor, self.nC, self.nC, nnzA)
+        self.kind = np.zeros(self.n, dtype=np.int8)
+        L.dginspect_kind(self.h, self.kind.ctypes.data)
+        self.dinv = np.zeros(self.n)
+        L.dginspect_dinv(self.h, self.dinv.ctypes.data)
+        off = np.zeros(nb + 1, dtype=np.int64)
+        nodes = np.zeros(max(nbd, 1), dtype=np.int64)
+        inv = np.zeros(max(nsq, 1))
+        L.dginspect_blocks(self.h, off.ctypes.data, nodes.ctypes.data, inv.ctypes.data)
+        self.blocks = [nodes[off[i]:off[i + 1]].copy() for i in range(nb)]
+        self.block_inv = []
+        q = 0
+        for b in self.blocks:
+            d2 = len(b) * len(b)
+            self.block_inv.append(inv[q:q + d2].reshape(len(b), len(b)).copy())
+            q += d2
+        self.levels = []
+        for l in range(self.n_levels):
+            r = int(L.dginspect_level_rows(self.h, l))
+            nz = int(L.dginspect_level_nnz(self.h, l))
+            self.levels.append(self._csr(lambda h, a, b, c, l=l: L.dginspect_level_A(h, l, a, b, c), r, r, nz))
+
+    def _csr(self, fn, rows, cols, nnz):
+        ptr = np.zeros(rows + 1, dtype=np.int64)
+        idx = np.zeros(max(nnz, 1), dtype=np.int32)
+        val = np.zeros(max(nnz, 1))
+        fn(self.h, ptr.ctypes.data, idx.ctypes.data, val.ctypes.data)
+        return self._sp.csr_matrix((val[:nnz], idx[:nnz], ptr), shape=(rows, cols))
+
+    def apply(self, x: np.ndarray) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.zeros(self.n)
+        inspect_lib().dginspect_apply(self.h, x.ctypes.data, y.ctypes.data)
+        return y
+
+    def __del__(self):
+        try:
+            inspect_lib().dginspect_destroy(self.h)
+        except Exception:
+            pass
+

@@ -1,0 +1,454 @@
+// C ABI entry points (include/dg.h): validation, host setup, uploads, the
+// graph-captured PCG loop.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "kernels.cuh"
+#include "precond_setup.h"
+
+namespace dg {
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+template <typename F>
+static dg_status guarded(F&& f) {
+  try {
+    f();
+    g_last_error.clear();
+    return DG_OK;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host allocation failed");
+    return DG_ENOMEM;
+  } catch (const std::exception& e) {
+    set_last_error(e.what());
+    return DG_EINVAL;
+  }
+}
+
+static void build_mesh(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opts, cudaStream_t s) {
+  build_mesh_host(M, desc, opts);
+  const HostMesh& m = M->host;
+  apply_kernel_setup();
+  // upload
+  DevArena& a = M->arena;
+  M->d_p = a.upload(m.p, s);
+  M->d_off = a.upload(m.off, s);
+  M->d_h = a.upload(M->h_h, s);
+  M->d_sf_ptr = a.upload(m.sf_ptr, s);
+  M->d_sf = a.upload(M->h_sf, s);
+  M->d_tables = a.upload(M->h_tables, s);
+  M->d_order = a.upload(M->h_order, s);
+  M->d_tiles = a.upload(M->h_tiles, s);
+  DG_CUDA(cudaStreamSynchronize(s));
+}
+
+
+// ----------------------------------------------------------------- precond upload
+template <typename T>
+static void upload_csr(DevArena& a, const Csr& C, DevCsr& D, cudaStream_t s) {
+  DG_REQUIRE(C.nnz() < (1LL << 31), "matrix too large for 32-bit indices");
+  std::vector<int32_t> ptr(C.ptr.begin(), C.ptr.end());
+  std::vector<T> val(C.val.begin(), C.val.end());
+  D.rows = C.rows;
+  D.nnz = C.nnz();
+  D.ptr = a.upload(ptr, s);
+  D.idx = a.upload(C.idx, s);
+  D.val = a.upload(val, s);
+}
+
+template <typename T>
+static void upload_precond(dg_precond* pc, HostPrecond& H, cudaStream_t s) {
+  DevArena& a = pc->arena;
+  upload_csr<T>(a, H.P, pc->P, s);
+  Csr PT = csr_transpose(H.P);
+  upload_csr<T>(a, PT, pc->PT, s);
+  pc->dinv = a.upload(std::vector<T>(H.dinv.begin(), H.dinv.end()), s);
+  const int64_t n = pc->n_dofs;
+  std::vector<int32_t> eb(n, -1), el(n, 0), dofs_off, dims, dofs;
+  std::vector<int64_t> inv_off;
+  std::vector<T> inv;
+  for (size_t b = 0; b < H.blocks.size(); ++b) {
+    const auto& blk = H.blocks[b];
+    dofs_off.push_back((int32_t)dofs.size());
+    dims.push_back((int32_t)blk.size());
+    inv_off.push_back((int64_t)inv.size());
+    for (size_t i = 0; i < blk.size(); ++i) {
+      eb[blk[i]] = (int32_t)b;
+      el[blk[i]] = (int32_t)i;
+      dofs.push_back((int32_t)blk[i]);
+    }
+    inv.insert(inv.end(), H.block_inv[b].begin(), H.block_inv[b].end());
+  }
+  pc->e_block = a.upload(eb, s);
+  pc->e_local = a.upload(el, s);
+  pc->blk_inv_off = a.upload(inv_off, s);
+  pc->blk_dofs_off = a.upload(dofs_off, s);
+  pc->blk_dim = a.upload(dims, s);
+  pc->blk_dofs = a.upload(dofs, s);
+  pc->blk_inv = a.upload(inv, s);
+  pc->rc = a.alloc<T>(pc->n_c);
+  pc->ec = a.alloc<T>(pc->n_c);
+  if (pc->n_c > 0 && pc->lor == DG_LOR_EXACT) {
+    DG_REQUIRE(pc->n_c <= 8192, "exact LOR solve limited to 8192 conforming unknowns");
+    std::vector<double> dense((size_t)pc->n_c * pc->n_c, 0.0);
+    for (int64_t i = 0; i < H.Ac.rows; ++i)
+      for (int64_t t = H.Ac.ptr[i]; t < H.Ac.ptr[i + 1]; ++t) dense[i * pc->n_c + H.Ac.idx[t]] = H.Ac.val[t];
+    dense_inverse_spd((int)pc->n_c, dense);
+    pc->lor_inv = a.upload(std::vector<T>(dense.begin(), dense.end()), s);
+    pc->stats.n_levels = 1;
+    pc->stats.level_rows[0] = pc->n_c;
+    pc->stats.level_nnz[0] = H.Ac.nnz();
+  } else if (pc->n_c > 0) {
+    AmgHierarchy Hm = amg_setup(H.Ac);
+    pc->levels.resize(Hm.levels.size());
+    for (size_t l = 0; l < Hm.levels.size(); ++l) {
+      const AmgLevel& L = Hm.levels[l];
+      DevLevel& D = pc->levels[l];
+      D.n = L.A.rows;
+      upload_csr<T>(a, L.A, D.A, s);
+      if (l + 1 < Hm.levels.size()) {
+        upload_csr<T>(a, L.P, D.P, s);
+        upload_csr<T>(a, L.R, D.R, s);
+      }
+      std::vector<T> di(L.dl1.size());
+      for (size_t i = 0; i < di.size(); ++i) di[i] = (T)(1.0 / L.dl1[i]);
+      D.dinv = a.upload(di, s);
+      D.b = a.alloc<T>(D.n);
+      D.x = a.alloc<T>(D.n);
+      D.xo = a.alloc<T>(D.n);
+      D.r = a.alloc<T>(D.n);
+      if (l < 16) {
+        pc->stats.level_rows[l] = D.n;
+        pc->stats.level_nnz[l] = L.A.nnz();
+      }
+    }
+    pc->n_coarse = Hm.levels.back().A.rows;
+    pc->coarse_inv = a.upload(std::vector<T>(Hm.coarse_inv.begin(), Hm.coarse_inv.end()), s);
+    pc->stats.n_levels = (int)Hm.levels.size();
+  }
+  DG_CUDA(cudaStreamSynchronize(s));
+}
+
+// ----------------------------------------------------------------- PCG workspace
+struct PcgWork {
+  int64_t n = 0;
+  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  double *part_pq = nullptr, *part_rr = nullptr, *part_rz = nullptr, *part_bb = nullptr;
+  double* sc = nullptr;
+  double* hsc = nullptr;  // pinned host copy of the scalars
+  DevArena arena;
+  // captured iteration graph and the arguments it was captured with
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;
+  double* g_x = nullptr;
+  int g_maxit = -1;
+  double g_rtol2 = -1.0;
+  bool graph_failed = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  void drop_graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+  }
+  ~PcgWork() {
+    drop_graph();
+    if (cap) cudaStreamDestroy(cap);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    arena.release();
+    if (hsc) cudaFreeHost(hsc);
+  }
+};
+
+static void free_pcg_work(void* p) { delete (PcgWork*)p; }
+
+static PcgWork& pcg_work(const dg_precond* pc) {
+  dg_precond* m = const_cast<dg_precond*>(pc);
+  if (m->pcg_cache) return *(PcgWork*)m->pcg_cache;
+  PcgWork* w = new PcgWork();
+  m->pcg_cache = w;
+  m->pcg_cache_free = free_pcg_work;
+  const dg_mesh* M = pc->mesh;
+  w->n = M->n_dofs;
+  w->r = w->arena.alloc<double>(w->n);
+  w->z = w->arena.alloc<double>(w->n);
+  w->p = w->arena.alloc<double>(w->n);
+  w->q = w->arena.alloc<double>(w->n);
+  w->part_pq = w->arena.alloc<double>(std::max(M->n_tiles, 1));
+  w->part_rr = w->arena.alloc<double>(kVecBlocks);
+  w->part_rz = w->arena.alloc<double>(kVecBlocks);
+  w->part_bb = w->arena.alloc<double>(kVecBlocks);
+  w->sc = w->arena.alloc<double>(SC_COUNT);
+  DG_CUDA(cudaMallocHost(&w->hsc, SC_COUNT * sizeof(double)));
+  DG_CUDA(cudaEventCreate(&w->e0));
+  DG_CUDA(cudaEventCreate(&w->e1));
+  DG_CUDA(cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking));
+  return *w;
+}
+
+static void pcg_body(const dg_mesh* M, const dg_precond* pc, PcgWork& w, double* x, int maxit,
+                     double rtol2, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
+  const int nrz = precond_final_blocks(*pc);
+  launch_apply(*M, w.p, w.q, w.part_pq, s);
+  launch_pcg_update_xr(x, w.r, w.p, w.q, w.n, w.part_pq, M->n_tiles, w.sc, w.part_rr, s);
+  launch_precond(*pc, w.r, w.z, w.part_rz, s);
+  launch_pcg_update_p(w.p, w.z, w.n, w.part_rz, nrz, w.sc, s);
+  launch_pcg_check(w.part_rr, kVecBlocks, w.part_rz, nrz, w.sc, maxit, rtol2,
+                   (unsigned long long)h, use_cond, s);
+}
+
+// one graph: while (cond) { PCG iteration }, the condition set on the device
+static bool pcg_capture(const dg_mesh* M, const dg_precond* pc, PcgWork& w, double* x, int maxit,
+                        double rtol2) {
+  if (w.exec && w.g_x == x && w.g_maxit == maxit && w.g_rtol2 == rtol2) return true;
+  w.drop_graph();
+  if (w.graph_failed) return false;
+  cudaGraphConditionalHandle handle = 0;
+  bool ok = false;
+  if (cudaGraphCreate(&w.graph, 0) == cudaSuccess &&
+      cudaGraphConditionalHandleCreate(&handle, w.graph, 1, cudaGraphCondAssignDefault) == cudaSuccess) {
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, w.graph, nullptr, nullptr, 0, &cp) == cudaSuccess) {
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      if (cudaStreamBeginCaptureToGraph(w.cap, body, nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+        bool launched = true;
+        try {
+          pcg_body(M, pc, w, x, maxit, rtol2, handle, 1, w.cap);
+        } catch (const Error&) {
+          launched = false;
+        }
+        cudaGraph_t out = nullptr;
+        if (cudaStreamEndCapture(w.cap, &out) == cudaSuccess && launched &&
+            cudaGraphInstantiate(&w.exec, w.graph, 0) == cudaSuccess)
+          ok = true;
+      }
+    }
+  }
+  cudaGetLastError();
+  if (!ok) {
+    w.drop_graph();
+    w.graph_failed = true;
+    return false;
+  }
+  w.g_x = x;
+  w.g_maxit = maxit;
+  w.g_rtol2 = rtol2;
+  return true;
+}
+
+static void pcg_run(const dg_mesh* M, const dg_precond* pc, const double* b, double* x, double rtol,
+                    int maxit, dg_solve_info* info, cudaStream_t s) {
+  DG_REQUIRE(M && pc && b && x, "null argument");
+  DG_REQUIRE(pc->mesh == M, "preconditioner belongs to another mesh");
+  DG_REQUIRE(rtol > 0.0 && maxit >= 1, "rtol must be > 0 and maxit >= 1");
+  PcgWork& w = pcg_work(pc);
+  const int nrz = precond_final_blocks(*pc);
+  const double rtol2 = rtol * rtol;
+  const bool use_graph = pcg_capture(M, pc, w, x, maxit, rtol2);
+  DG_CUDA(cudaEventRecord(w.e0, s));
+  launch_pcg_init(b, x, w.r, w.n, w.part_bb, s);
+  launch_precond(*pc, w.r, w.z, w.part_rz, s);
+  launch_pcg_first(w.part_rz, nrz, w.part_bb, w.sc, s);
+  launch_copy(w.z, w.p, w.n, s);
+  DG_CUDA(cudaMemcpyAsync(w.hsc, w.sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+  DG_CUDA(cudaStreamSynchronize(s));
+  if (w.hsc[SC_BB] > 0.0) {
+    if (use_graph) {
+      DG_CUDA(cudaGraphLaunch(w.exec, s));
+    } else {
+      // host-driven loop, status read back every 8 iterations
+      for (int it = 0; it < maxit;) {
+        for (int j = 0; j < 8 && it < maxit; ++j, ++it) pcg_body(M, pc, w, x, maxit, rtol2, 0, 0, s);
+        DG_CUDA(cudaMemcpyAsync(w.hsc, w.sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+        DG_CUDA(cudaStreamSynchronize(s));
+        if (w.hsc[SC_STATUS] != 0.0) break;
+      }
+    }
+  }
+  DG_CUDA(cudaEventRecord(w.e1, s));
+  DG_CUDA(cudaMemcpyAsync(w.hsc, w.sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+  DG_CUDA(cudaStreamSynchronize(s));
+  float ms = 0.0f;
+  DG_CUDA(cudaEventElapsedTime(&ms, w.e0, w.e1));
+  const int iters = (int)w.hsc[SC_IT];
+  const double bb = w.hsc[SC_BB];
+  const double rel = bb > 0.0 ? std::sqrt(w.hsc[SC_RR] / bb) : 0.0;
+  const bool conv = bb == 0.0 || w.hsc[SC_STATUS] == 1.0;
+  if (info) {
+    info->iters = bb > 0.0 ? iters : 0;
+    info->rel_res = rel;
+    info->status = conv ? DG_OK : DG_ENOTCONV;
+    info->solve_ms = ms;
+  }
+  if (!conv) throw Error(DG_ENOTCONV, "PCG reached maxit");
+}
+
+}  // namespace dg
+
+using namespace dg;
+
+extern "C" {
+
+const char* dg_last_error(void) { return g_last_error.c_str(); }
+
+dg_status dg_mesh_create(const dg_mesh_desc* desc, const dg_options* opts, void* stream, dg_mesh** out) {
+  if (!out) { set_last_error("null output handle"); return DG_EINVAL; }
+  *out = nullptr;
+  dg_mesh* M = nullptr;
+  dg_status st = guarded([&] {
+    M = new dg_mesh();
+    build_mesh(M, desc, opts, (cudaStream_t)stream);
+  });
+  if (st != DG_OK) { delete M; return st; }
+  *out = M;
+  return DG_OK;
+}
+
+void dg_mesh_destroy(dg_mesh* mesh) { delete mesh; }
+
+int64_t dg_num_dofs(const dg_mesh* mesh) { return mesh ? mesh->n_dofs : -1; }
+
+dg_status dg_apply(const dg_mesh* mesh, const double* x, double* y, void* stream) {
+  return guarded([&] {
+    DG_REQUIRE(mesh && x && y, "null argument");
+    DG_REQUIRE(x != y, "x and y must not alias");
+    launch_apply(*mesh, x, y, nullptr, (cudaStream_t)stream);
+  });
+}
+
+dg_status dg_precond_setup(const dg_mesh* mesh, const dg_options* opts, dg_precond** out) {
+  if (!out) { set_last_error("null output handle"); return DG_EINVAL; }
+  *out = nullptr;
+  dg_precond* pc = nullptr;
+  dg_status st = guarded([&] {
+    DG_REQUIRE(mesh != nullptr, "null mesh");
+    dg_options o = mesh->opts;
+    if (opts) {
+      o.precision = opts->precision;
+      o.lor = opts->lor;
+      o.smoother = opts->smoother;
+      o.remark_cases = opts->remark_cases;
+    }
+    DG_REQUIRE(o.precision == DG_PREC_FP64 || o.precision == DG_PREC_MIXED, "unknown precision");
+    DG_REQUIRE(o.lor == DG_LOR_EXACT || o.lor == DG_LOR_AMG, "unknown LOR solver");
+    DG_REQUIRE(o.smoother == DG_SMOOTHER_FULL || o.smoother == DG_SMOOTHER_JACOBI_ONLY, "unknown smoother");
+    HostPrecond H = build_host_precond(*mesh, o);
+    pc = new dg_precond();
+    pc->mesh = mesh;
+    pc->precision = o.precision;
+    pc->lor = o.lor;
+    pc->n_dofs = mesh->n_dofs;
+    pc->n_c = H.nC;
+    auto& S = pc->stats;
+    S.n_dofs = mesh->n_dofs;
+    S.n_conforming = H.nC;
+    for (auto k : H.kind) { S.n_j += (k == 1); S.n_e += (k == 2); }
+    S.n_blocks = (int64_t)H.blocks.size();
+    for (auto& b : H.blocks) S.max_block = std::max<int64_t>(S.max_block, (int64_t)b.size());
+    S.lor_nnz = H.Ac.nnz();
+    S.p_nnz = H.P.nnz();
+    cudaStream_t s = nullptr;
+    if (o.precision == DG_PREC_MIXED) upload_precond<float>(pc, H, s);
+    else upload_precond<double>(pc, H, s);
+  });
+  if (st != DG_OK) { delete pc; return st; }
+  *out = pc;
+  return DG_OK;
+}
+
+void dg_precond_destroy(dg_precond* pc) { delete pc; }
+
+dg_status dg_precond_stats_get(const dg_precond* pc, dg_precond_stats* out) {
+  return guarded([&] {
+    DG_REQUIRE(pc && out, "null argument");
+    *out = pc->stats;
+  });
+}
+
+dg_status dg_precond_apply(const dg_precond* pc, const double* r, double* z, void* stream) {
+  return guarded([&] {
+    DG_REQUIRE(pc && r && z, "null argument");
+    DG_REQUIRE(r != z, "r and z must not alias");
+    launch_precond(*pc, r, z, nullptr, (cudaStream_t)stream);
+  });
+}
+
+dg_status dg_pcg_solve(const dg_mesh* mesh, const dg_precond* pc, const double* b, double* x,
+                       double rtol, int maxit, dg_solve_info* info, void* stream) {
+  return guarded([&] { pcg_run(mesh, pc, b, x, rtol, maxit, info, (cudaStream_t)stream); });
+}
+
+dg_status dg_pcg_solve_host(const dg_mesh* mesh, const dg_precond* pc, const double* b_host,
+                            double* x_host, double rtol, int maxit, dg_solve_info* info,
+                            void* stream) {
+  return guarded([&] {
+    DG_REQUIRE(mesh && pc && b_host && x_host, "null argument");
+    const cudaStream_t s = (cudaStream_t)stream;
+    DevArena a;
+    struct Free { DevArena& a; ~Free() { a.release(); } } fr{a};
+    double* b = a.alloc<double>(mesh->n_dofs);
+    double* x = a.alloc<double>(mesh->n_dofs);
+    DG_CUDA(cudaMemcpyAsync(b, b_host, mesh->n_dofs * sizeof(double), cudaMemcpyHostToDevice, s));
+    dg_status st = DG_OK;
+    try {
+      pcg_run(mesh, pc, b, x, rtol, maxit, info, s);
+    } catch (const Error& e) {
+      if (e.code != DG_ENOTCONV) throw;
+      st = DG_ENOTCONV;
+    }
+    DG_CUDA(cudaMemcpyAsync(x_host, x, mesh->n_dofs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    DG_CUDA(cudaStreamSynchronize(s));
+    if (st != DG_OK) throw Error(st, "PCG reached maxit");
+  });
+}
+
+dg_status dg_rhs_sine(const dg_mesh* mesh, int n_modes, const double* amps, const int32_t* waves,
+                      double* b, void* stream) {
+  return guarded([&] {
+    DG_REQUIRE(mesh && b && n_modes >= 0 && (n_modes == 0 || (amps && waves)), "bad argument");
+    const HostMesh& m = mesh->host;
+    std::vector<double> hb(mesh->n_dofs, 0.0);
+    for (int64_t k = 0; k < m.n; ++k) {
+      const int P = m.p[k], NP = P + 1;
+      const Basis1D& B = basis1d(P);
+      std::vector<double> gx, gw;
+      gauss_rule(P + 3, gx, gw);
+      const double h = mesh->h_h[k];
+      const double x0 = m.lo[2 * k] * m.lh, y0 = m.lo[2 * k + 1] * m.lh;
+      const int q = (int)gx.size();
+      std::vector<double> L((size_t)q * NP);
+      for (int g = 0; g < q; ++g) lagrange_eval(B.nodes, gx[g], &L[(size_t)g * NP]);
+      for (int gy = 0; gy < q; ++gy)
+        for (int gxi = 0; gxi < q; ++gxi) {
+          const double X = x0 + h * gx[gxi], Y = y0 + h * gx[gy];
+          double f = 0.0;
+          for (int md = 0; md < n_modes; ++md)
+            f += amps[md] * std::sin(M_PI * waves[2 * md] * X) * std::sin(M_PI * waves[2 * md + 1] * Y);
+          const double w = gw[gxi] * gw[gy] * h * h * f;
+          for (int iy = 0; iy < NP; ++iy)
+            for (int ix = 0; ix < NP; ++ix)
+              hb[m.off[k] + iy * NP + ix] += w * L[(size_t)gy * NP + iy] * L[(size_t)gxi * NP + ix];
+        }
+    }
+    DG_CUDA(cudaMemcpyAsync(b, hb.data(), hb.size() * sizeof(double), cudaMemcpyHostToDevice,
+                            (cudaStream_t)stream));
+    DG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  });
+}
+
+}  // extern "C"

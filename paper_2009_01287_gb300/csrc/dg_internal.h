@@ -1,0 +1,135 @@
+// Internal data structures of the hp-DG library (host + device).
+#pragma once
+
+#include <cstdint>
+#include <map>
+#include <stdexcept>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/dg.h"
+
+namespace dg {
+
+constexpr int kMaxP = 8;
+constexpr int kMaxN = kMaxP + 1;
+constexpr int kThreads = 256;   // threads per CTA of the operator kernel
+// elements of degree p per operator CTA (one thread per node, at most 16)
+constexpr int apply_epb(int p) {
+  return (kThreads / ((p + 1) * (p + 1))) > 16 ? 16 : (kThreads / ((p + 1) * (p + 1)));
+}
+
+// ------------------------------------------------------------------ errors
+struct Error : std::runtime_error {
+  dg_status code;
+  Error(dg_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+void set_last_error(const std::string& msg);
+#define DG_REQUIRE(cond, msg) \
+  do { if (!(cond)) throw ::dg::Error(DG_EINVAL, msg); } while (0)
+#define DG_CUDA(call)                                                            \
+  do {                                                                           \
+    cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess)                                                       \
+      throw ::dg::Error(e_ == cudaErrorMemoryAllocation ? DG_ENOMEM : DG_ECUDA,  \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));     \
+  } while (0)
+
+// ------------------------------------------------------------------ basis (host)
+// Gauss-Lobatto nodes on [0,1] (Section 2.2), Gauss-Legendre rules, Lagrange
+// values by the barycentric formula.
+std::vector<double> gll_nodes(int p);
+void gauss_rule(int q, std::vector<double>& x, std::vector<double>& w);
+// values l_j(t), j = 0..n-1, of the Lagrange basis on `nodes` at t
+void lagrange_eval(const std::vector<double>& nodes, double t, double* out);
+void lagrange_deriv_eval(const std::vector<double>& nodes, double t, double* out);
+
+// 1D reference matrices of degree p on [0,1] (exact Gauss integration)
+struct Basis1D {
+  int p;
+  std::vector<double> nodes;   // p+1
+  std::vector<double> M, K;    // (p+1)^2 row-major, exact mass / stiffness
+  std::vector<double> Minv;    // inverse of M
+  std::vector<double> d0, d1;  // l_k'(0), l_k'(1)
+};
+const Basis1D& basis1d(int p);
+
+// ------------------------------------------------------------------ device records
+// One sub-face seen from one of its sides (the "own" element).
+struct SubFaceRec {
+  int32_t nb;        // neighbour element, -1 on the boundary
+  int32_t nb_side;   // neighbour side holding the sub-face
+  int32_t pn;        // neighbour degree
+  int32_t tab_oo;    // offset of the own-own face mass (ref, (p+1)^2)
+  int32_t tab_on;    // offset of own-neighbour face mass ((p+1) x (pn+1))
+  int32_t tab_nn;    // offset of neighbour-neighbour face mass ((pn+1)^2)
+  double sigma;      // SIPG penalty
+  double len;        // physical length of the sub-face
+};
+
+// Offsets of the degree-p 1D matrices inside the device table buffer.
+struct BasisOff {
+  int M, K, Minv, d0, d1;
+};
+
+// Per-CTA work item of the operator kernel: a run of elements of one degree.
+struct ApplyTile {
+  int32_t p;
+  int32_t first;     // index into the degree-sorted element order
+  int32_t count;
+  int32_t pad;
+};
+
+// ------------------------------------------------------------------ mesh (host topology)
+struct HostMesh {
+  int dim = 2;
+  int64_t n = 0;
+  std::vector<int32_t> lo;      // n*2
+  std::vector<int32_t> size;    // n
+  std::vector<int32_t> p;       // n
+  int32_t extent[2] = {0, 0};
+  double lh = 1.0;
+  std::vector<int64_t> off;     // n+1 DOF offsets
+  std::vector<int32_t> cellmap; // extent0*extent1 -> element
+
+  // sub-faces seen from each element side: sf_ptr[4k+s] .. sf_ptr[4k+s+1]
+  std::vector<int32_t> sf_ptr;
+  struct SF { int32_t nb, nb_side, t0, t1; };
+  std::vector<SF> sf;
+
+  // master edges
+  struct Master {
+    int axis, c, t0, t1;
+    bool boundary;
+    int p;                          // min degree of owners and slaves
+    std::vector<int32_t> owners, slaves;
+    std::vector<std::pair<int,int>> hanging;  // interior hanging vertices
+  };
+  std::vector<Master> masters;
+  std::vector<int32_t> side_master;  // 4n
+
+  int32_t elem_at(int x, int y) const { return cellmap[(int64_t)y * extent[0] + x]; }
+  void side_segment(int k, int s, int& axis, int& c, int& t0, int& t1) const;
+  bool corner_of(int k, int x, int y) const;
+  // element + side containing (x,y) in the relative interior of the side, or -1
+  int containing_side(int x, int y, int* side) const;
+  bool on_boundary(int x, int y) const {
+    return x == 0 || y == 0 || x == extent[0] || y == extent[1];
+  }
+  bool is_hp_vertex(int x, int y) const;
+};
+
+void build_topology(HostMesh& m);   // fills sf, masters, side_master
+
+// Face-mass tables (Section 2: exact face integrals on sub-faces).
+struct FaceTables {
+  std::vector<double> data;
+  std::map<std::tuple<int,int,int,int,int,int>, int> index;
+  int get(int p, int L, int off, int pn, int Ln, int offn);
+};
+
+}  // namespace dg
+

@@ -1,0 +1,131 @@
+// Host evaluation of one element's rows of the DG operator (same sub-face
+// formulation as the device kernel).  Used at setup to read the diagonal of A
+// on V_J and the dense blocks A_e = R_e A R_e^T of the V_e (Section 4.1, items
+// 2: "assembly of the diagonal ... and of the diagonal blocks").
+#include <cmath>
+#include <vector>
+
+#include "dg_internal.h"
+#include "host_state.h"
+
+namespace dg {
+
+void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double* y) {
+  const HostMesh& m = M.host;
+  const int P = m.p[k], NP = P + 1, NN = NP * NP;
+  const Basis1D& B = basis1d(P);
+  const double hk = M.h_h[k];
+  const double* xk = x + m.off[k];
+  auto sn = [](int s, int i, int q, int np) { return (s < 2) ? (i * np + q) : (q * np + i); };
+  // volume: (K (x) M + M (x) K) x  with local index iy*NP + ix
+  for (int iy = 0; iy < NP; ++iy)
+    for (int ix = 0; ix < NP; ++ix) {
+      double v = 0.0;
+      for (int qy = 0; qy < NP; ++qy)
+        for (int qx = 0; qx < NP; ++qx) {
+          const double xv = xk[qy * NP + qx];
+          v += (B.K[ix * NP + qx] * B.M[iy * NP + qy] + B.M[ix * NP + qx] * B.K[iy * NP + qy]) * xv;
+        }
+      y[iy * NP + ix] = v;
+    }
+  std::vector<double> dn(4 * NP), r(4 * NP, 0.0), c2(4 * NP, 0.0);
+  for (int s = 0; s < 4; ++s)
+    for (int i = 0; i < NP; ++i) {
+      const std::vector<double>& dv = (s & 1) ? B.d1 : B.d0;
+      double acc = 0.0;
+      for (int q = 0; q < NP; ++q) acc += dv[q] * xk[sn(s, i, q, NP)];
+      dn[s * NP + i] = ((s & 1) ? 1.0 : -1.0) / hk * acc;
+    }
+  const double* T = M.h_tables.data();
+  for (int s = 0; s < 4; ++s) {
+    const int kedge = (s & 1) ? P : 0;
+    for (int j = m.sf_ptr[4 * k + s]; j < m.sf_ptr[4 * k + s + 1]; ++j) {
+      const SubFaceRec& f = M.h_sf[j];
+      std::vector<double> un(kMaxN, 0.0), dnn(kMaxN, 0.0);
+      int np = 0;
+      if (f.nb >= 0) {
+        np = f.pn + 1;
+        const Basis1D& Bn = basis1d(f.pn);
+        const double* xn = x + m.off[f.nb];
+        const int ke = (f.nb_side & 1) ? f.pn : 0;
+        const std::vector<double>& dv = (f.nb_side & 1) ? Bn.d1 : Bn.d0;
+        const double sg = ((f.nb_side & 1) ? -1.0 : 1.0) / M.h_h[f.nb];
+        for (int q = 0; q < np; ++q) {
+          un[q] = xn[sn(f.nb_side, q, ke, np)];
+          double acc = 0.0;
+          for (int t = 0; t < np; ++t) acc += dv[t] * xn[sn(f.nb_side, q, t, np)];
+          dnn[q] = sg * acc;
+        }
+      }
+      std::vector<double> jo(NP), cd(NP), jn(kMaxN, 0.0);
+      for (int i = 0; i < NP; ++i) {
+        double a = 0.0, c = 0.0, b = 0.0, d = 0.0;
+        for (int q = 0; q < NP; ++q) {
+          a += T[f.tab_oo + i * NP + q] * xk[sn(s, q, kedge, NP)];
+          c += T[f.tab_oo + i * NP + q] * dn[s * NP + q];
+        }
+        for (int q = 0; q < np; ++q) {
+          b += T[f.tab_on + i * np + q] * un[q];
+          d += T[f.tab_on + i * np + q] * dnn[q];
+        }
+        a *= f.len; b *= f.len; c *= f.len; d *= f.len;
+        if (f.nb < 0) {
+          c2[s * NP + i] -= a;
+          jo[i] = a;
+          cd[i] = -c;
+          if (M.opts.form == DG_FORM_SIPG) r[s * NP + i] += -c + f.sigma * a;
+        } else {
+          c2[s * NP + i] -= 0.5 * (a - b);
+          jo[i] = a - b;
+          cd[i] = -0.5 * (c + d);
+          if (M.opts.form == DG_FORM_SIPG) r[s * NP + i] += -0.5 * (c + d) + f.sigma * (a - b);
+        }
+      }
+      if (M.opts.form == DG_FORM_BR2) {
+        for (int q = 0; q < np; ++q) {
+          double v = 0.0;
+          for (int i = 0; i < NP; ++i) v += T[f.tab_on + i * np + q] * xk[sn(s, i, kedge, NP)];
+          for (int t = 0; t < np; ++t) v -= T[f.tab_nn + q * np + t] * un[t];
+          jn[q] = v * f.len;
+        }
+        std::vector<double> go(NP), gn(kMaxN, 0.0);
+        for (int i = 0; i < NP; ++i) {
+          double g = 0.0;
+          for (int q = 0; q < NP; ++q) g += B.Minv[i * NP + q] * jo[q];
+          go[i] = g * B.Minv[0] / (hk * hk);
+        }
+        if (np) {
+          const Basis1D& Bn = basis1d(f.pn);
+          const double hn = M.h_h[f.nb];
+          for (int q = 0; q < np; ++q) {
+            double g = 0.0;
+            for (int t = 0; t < np; ++t) g += Bn.Minv[q * np + t] * jn[t];
+            gn[q] = g * Bn.Minv[0] / (hn * hn);
+          }
+        }
+        const double coef = (f.nb < 0) ? 1.0 : 0.25;
+        for (int i = 0; i < NP; ++i) {
+          double st = 0.0;
+          for (int q = 0; q < NP; ++q) st += T[f.tab_oo + i * NP + q] * go[q];
+          for (int q = 0; q < np; ++q) st += T[f.tab_on + i * np + q] * gn[q];
+          r[s * NP + i] += cd[i] + M.eta * coef * f.len * st;
+        }
+      }
+    }
+  }
+  for (int node = 0; node < NN; ++node) {
+    const int ix = node % NP, iy = node / NP;
+    double v = y[node];
+    v += -B.d0[ix] / hk * c2[0 * NP + iy];
+    v += B.d1[ix] / hk * c2[1 * NP + iy];
+    v += -B.d0[iy] / hk * c2[2 * NP + ix];
+    v += B.d1[iy] / hk * c2[3 * NP + ix];
+    if (ix == 0) v += r[0 * NP + iy];
+    if (ix == P) v += r[1 * NP + iy];
+    if (iy == 0) v += r[2 * NP + ix];
+    if (iy == P) v += r[3 * NP + ix];
+    y[node] = v;
+  }
+}
+
+}  // namespace dg

@@ -1,0 +1,117 @@
+// Definitions of the opaque handles and the device-side views used by the
+// kernels.
+#pragma once
+
+#include <vector>
+
+#include "dg_internal.h"
+#include "sparse.h"
+
+namespace dg {
+
+// device allocation tracked by its owner
+struct DevArena {
+  std::vector<void*> ptrs;
+  template <typename T>
+  T* alloc(size_t n) {
+    void* p = nullptr;
+    if (n == 0) n = 1;
+    DG_CUDA(cudaMalloc(&p, n * sizeof(T)));
+    ptrs.push_back(p);
+    return (T*)p;
+  }
+  template <typename T>
+  T* upload(const std::vector<T>& v, cudaStream_t s) {
+    T* d = alloc<T>(v.size());
+    if (!v.empty()) DG_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return d;
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+// CSR on the device: int32 indices, values of the preconditioner precision
+struct DevCsr {
+  int64_t rows = 0, nnz = 0;
+  int32_t* ptr = nullptr;
+  int32_t* idx = nullptr;
+  void* val = nullptr;
+};
+
+struct DevLevel {
+  int64_t n = 0;
+  DevCsr A, P, R;      // P: from the next level to this one, R = P^T
+  void* dinv = nullptr;  // 1 / l1 diagonal
+  void* b = nullptr;     // right-hand side of this level
+  void* x = nullptr;     // after pre-smoothing and coarse correction
+  void* xo = nullptr;    // after post-smoothing (the level's output)
+  void* r = nullptr;     // residual after pre-smoothing
+};
+
+}  // namespace dg
+
+struct dg_mesh {
+  dg::HostMesh host;
+  dg_options opts{};
+  double eta = 0.0;
+  int64_t n_dofs = 0;
+  // host copies of what the device holds
+  std::vector<double> h_h;
+  std::vector<dg::SubFaceRec> h_sf;
+  std::vector<double> h_tables;
+  dg::BasisOff boff[dg::kMaxP + 1];
+  std::vector<dg::ApplyTile> h_tiles;
+  std::vector<int32_t> h_order;      // degree-sorted element order
+  // device
+  dg::DevArena arena;
+  int32_t* d_p = nullptr;
+  int64_t* d_off = nullptr;
+  double* d_h = nullptr;
+  int32_t* d_sf_ptr = nullptr;
+  dg::SubFaceRec* d_sf = nullptr;
+  double* d_tables = nullptr;
+  int32_t* d_order = nullptr;
+  dg::ApplyTile* d_tiles = nullptr;
+  int n_tiles = 0;
+  ~dg_mesh() { arena.release(); }
+};
+
+struct dg_precond {
+  const dg_mesh* mesh = nullptr;
+  int precision = DG_PREC_FP64;
+  int lor = DG_LOR_AMG;
+  int64_t n_dofs = 0, n_c = 0;
+  dg_precond_stats stats{};
+  dg::DevArena arena;
+  dg::DevCsr P, PT;          // P: n_dofs x n_c (rows = DG nodes), PT = P^T
+  void* dinv = nullptr;      // n_dofs, 1/A_jj on V_J and 0 elsewhere
+  int32_t* e_block = nullptr;   // n_dofs, V_e index or -1
+  int32_t* e_local = nullptr;   // n_dofs, position inside its V_e
+  int64_t* blk_inv_off = nullptr;
+  int32_t* blk_dofs_off = nullptr;
+  int32_t* blk_dim = nullptr;
+  int32_t* blk_dofs = nullptr;
+  void* blk_inv = nullptr;   // row-major dense inverses
+  void* lor_inv = nullptr;   // exact LOR solve: dense inverse n_c x n_c
+  std::vector<dg::DevLevel> levels;  // AMG (level 0 = LOR matrix)
+  void* coarse_inv = nullptr;
+  int64_t n_coarse = 0;
+  void* rc = nullptr;        // n_c restriction of r
+  void* ec = nullptr;        // n_c LOR correction
+  // PCG workspace and captured iteration graph, built on the first solve
+  void* pcg_cache = nullptr;
+  void (*pcg_cache_free)(void*) = nullptr;
+  ~dg_precond() {
+    if (pcg_cache_free) pcg_cache_free(pcg_cache);
+    arena.release();
+  }
+};
+
+namespace dg {
+// validate the description and build everything the device needs, on the host
+void build_mesh_host(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opts);
+// rows of element k of y = A x (x: full host vector), same formulation as the kernel
+void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double* y);
+}  // namespace dg

@@ -1,0 +1,122 @@
+// Host-only inspection library (libdgsc_inspect.so): runs the library's own
+// host setup - topology, conforming prolongation, V_J / V_e split, LOR matrix,
+// AMG hierarchy - and the host mirror of the operator, without a GPU, so that
+// they can be compared with an independent implementation on a CPU machine.
+// Not part of the solver ABI (include/dg.h); every call is synchronous.
+#include <cstring>
+#include <memory>
+
+#include "dg_internal.h"
+#include "host_state.h"
+#include "precond_setup.h"
+
+using namespace dg;
+
+namespace {
+struct Inspect {
+  dg_mesh mesh;
+  HostPrecond pc;
+  AmgHierarchy amg;
+  std::string err;
+};
+thread_local std::string g_err;
+}  // namespace
+
+namespace dg {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}
+
+extern "C" {
+
+const char* dginspect_last_error(void) { return g_err.c_str(); }
+
+void* dginspect_create(const dg_mesh_desc* desc, const dg_options* opts, int with_amg) {
+  try {
+    std::unique_ptr<Inspect> I(new Inspect());
+    build_mesh_host(&I->mesh, desc, opts);
+    dg_options o = I->mesh.opts;
+    if (opts) {
+      o.smoother = opts->smoother;
+      o.remark_cases = opts->remark_cases;
+    }
+    I->pc = build_host_precond(I->mesh, o);
+    if (with_amg && I->pc.nC > 0) I->amg = amg_setup(I->pc.Ac);
+    return I.release();
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return nullptr;
+  }
+}
+
+void dginspect_destroy(void* h) { delete (Inspect*)h; }
+
+// sizes: [n_dofs, n_c, nnz(P), nnz(Ac), n_blocks, total block dofs, n_levels,
+//         eta*1e6, sum of squared block dims]
+void dginspect_sizes(void* h, int64_t* out) {
+  Inspect* I = (Inspect*)h;
+  out[0] = I->mesh.n_dofs;
+  out[1] = I->pc.nC;
+  out[2] = I->pc.P.nnz();
+  out[3] = I->pc.Ac.nnz();
+  out[4] = (int64_t)I->pc.blocks.size();
+  int64_t t = 0;
+  for (auto& b : I->pc.blocks) t += (int64_t)b.size();
+  out[5] = t;
+  out[6] = (int64_t)I->amg.levels.size();
+  out[7] = (int64_t)(I->mesh.eta * 1e6);
+  int64_t q = 0;
+  for (auto& b : I->pc.blocks) q += (int64_t)b.size() * (int64_t)b.size();
+  out[8] = q;
+}
+
+static void copy_csr(const Csr& C, int64_t* ptr, int32_t* idx, double* val) {
+  std::memcpy(ptr, C.ptr.data(), C.ptr.size() * sizeof(int64_t));
+  std::memcpy(idx, C.idx.data(), C.idx.size() * sizeof(int32_t));
+  std::memcpy(val, C.val.data(), C.val.size() * sizeof(double));
+}
+
+void dginspect_P(void* h, int64_t* ptr, int32_t* idx, double* val) { copy_csr(((Inspect*)h)->pc.P, ptr, idx, val); }
+void dginspect_lor(void* h, int64_t* ptr, int32_t* idx, double* val) { copy_csr(((Inspect*)h)->pc.Ac, ptr, idx, val); }
+
+void dginspect_kind(void* h, int8_t* kind) {
+  Inspect* I = (Inspect*)h;
+  std::memcpy(kind, I->pc.kind.data(), I->pc.kind.size());
+}
+
+void dginspect_dinv(void* h, double* dinv) {
+  Inspect* I = (Inspect*)h;
+  std::memcpy(dinv, I->pc.dinv.data(), I->pc.dinv.size() * sizeof(double));
+}
+
+// blocks: offsets (n_blocks+1) and node lists; inverse entries concatenated
+void dginspect_blocks(void* h, int64_t* offsets, int64_t* nodes, double* inv) {
+  Inspect* I = (Inspect*)h;
+  int64_t o = 0, q = 0;
+  offsets[0] = 0;
+  for (size_t b = 0; b < I->pc.blocks.size(); ++b) {
+    for (int64_t r : I->pc.blocks[b]) nodes[o++] = r;
+    offsets[b + 1] = o;
+    for (double v : I->pc.block_inv[b]) inv[q++] = v;
+  }
+}
+
+int64_t dginspect_level_rows(void* h, int l) {
+  Inspect* I = (Inspect*)h;
+  return I->amg.levels[l].A.rows;
+}
+int64_t dginspect_level_nnz(void* h, int l) {
+  Inspect* I = (Inspect*)h;
+  return I->amg.levels[l].A.nnz();
+}
+void dginspect_level_A(void* h, int l, int64_t* ptr, int32_t* idx, double* val) {
+  copy_csr(((Inspect*)h)->amg.levels[l].A, ptr, idx, val);
+}
+
+// y = A x with the host mirror of the operator kernel
+void dginspect_apply(void* h, const double* x, double* y) {
+  Inspect* I = (Inspect*)h;
+  const HostMesh& m = I->mesh.host;
+  for (int64_t k = 0; k < m.n; ++k) host_element_residual(I->mesh, k, x, y + m.off[k]);
+}
+
+}  // extern "C"

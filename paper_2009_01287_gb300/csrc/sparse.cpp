@@ -1,0 +1,250 @@
+// Host CSR utilities and the smoothed-aggregation AMG setup used as the LOR
+// conforming solver (Section 3.4 uses one AMG V-cycle on P^T A~ P).
+//
+// AMG algorithm (fixed so that it is deterministic):
+//   strength   j != i strong for i  iff  a_ij^2 > theta^2 a_ii a_jj
+//   pass 1     i unaggregated with >= 1 strong neighbour, all of them
+//              unaggregated: new aggregate {i} + strong neighbours
+//   pass 2     i unaggregated: joins the pass-1 aggregate of its
+//              lowest-numbered strong neighbour that has one
+//   pass 3     i still unaggregated: new aggregate {i} + its unaggregated
+//              strong neighbours
+//   smoothing  P = (I - omega D^-1 A) T, omega = 4/(3 rho),
+//              rho = max_i sum_j |a_ij| / a_ii
+//   coarse     A_c = P^T A P; stop at <= kAmgCoarseMax rows, when a level
+//              does not shrink below 0.9 n, or at kAmgMaxLevels levels; the
+//              last level is inverted densely.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "dg_internal.h"
+#include "sparse.h"
+
+namespace dg {
+
+Csr csr_from_triplets(int64_t rows, int64_t cols, std::vector<int64_t>& r,
+                      std::vector<int32_t>& c, std::vector<double>& v) {
+  Csr A;
+  A.rows = rows;
+  A.cols = cols;
+  std::vector<int64_t> order(r.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    return r[a] != r[b] ? r[a] < r[b] : c[a] < c[b];
+  });
+  A.ptr.assign(rows + 1, 0);
+  for (size_t t = 0; t < order.size();) {
+    size_t u = t;
+    double s = 0.0;
+    while (u < order.size() && r[order[u]] == r[order[t]] && c[order[u]] == c[order[t]]) {
+      s += v[order[u]];
+      ++u;
+    }
+    A.idx.push_back(c[order[t]]);
+    A.val.push_back(s);
+    A.ptr[r[order[t]] + 1]++;
+    t = u;
+  }
+  for (int64_t i = 0; i < rows; ++i) A.ptr[i + 1] += A.ptr[i];
+  return A;
+}
+
+Csr csr_transpose(const Csr& A) {
+  Csr T;
+  T.rows = A.cols;
+  T.cols = A.rows;
+  T.ptr.assign(T.rows + 1, 0);
+  for (int32_t c : A.idx) T.ptr[c + 1]++;
+  for (int64_t i = 0; i < T.rows; ++i) T.ptr[i + 1] += T.ptr[i];
+  T.idx.resize(A.idx.size());
+  T.val.resize(A.val.size());
+  std::vector<int64_t> pos(T.ptr.begin(), T.ptr.end() - 1);
+  for (int64_t i = 0; i < A.rows; ++i)
+    for (int64_t t = A.ptr[i]; t < A.ptr[i + 1]; ++t) {
+      int64_t d = pos[A.idx[t]]++;
+      T.idx[d] = (int32_t)i;
+      T.val[d] = A.val[t];
+    }
+  return T;
+}
+
+Csr csr_multiply(const Csr& A, const Csr& B) {
+  Csr C;
+  C.rows = A.rows;
+  C.cols = B.cols;
+  C.ptr.assign(A.rows + 1, 0);
+  std::vector<int64_t> mark(B.cols, -1);
+  std::vector<double> acc(B.cols, 0.0);
+  std::vector<int32_t> cols;
+  for (int64_t i = 0; i < A.rows; ++i) {
+    cols.clear();
+    for (int64_t t = A.ptr[i]; t < A.ptr[i + 1]; ++t) {
+      const int32_t a = A.idx[t];
+      const double av = A.val[t];
+      for (int64_t u = B.ptr[a]; u < B.ptr[a + 1]; ++u) {
+        const int32_t b = B.idx[u];
+        if (mark[b] != i) {
+          mark[b] = i;
+          acc[b] = 0.0;
+          cols.push_back(b);
+        }
+        acc[b] += av * B.val[u];
+      }
+    }
+    std::sort(cols.begin(), cols.end());
+    for (int32_t b : cols) {
+      C.idx.push_back(b);
+      C.val.push_back(acc[b]);
+    }
+    C.ptr[i + 1] = (int64_t)C.idx.size();
+  }
+  return C;
+}
+
+void dense_inverse_spd(int n, std::vector<double>& a) {
+  // Cholesky A = L L^T, then A^-1 = L^-T L^-1 (column by column)
+  std::vector<double> L(a);
+  for (int j = 0; j < n; ++j) {
+    double d = L[(int64_t)j * n + j];
+    for (int k = 0; k < j; ++k) d -= L[(int64_t)j * n + k] * L[(int64_t)j * n + k];
+    if (!(d > 0.0)) throw Error(DG_EINVAL, "matrix not positive definite");
+    d = std::sqrt(d);
+    L[(int64_t)j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double s = L[(int64_t)i * n + j];
+      for (int k = 0; k < j; ++k) s -= L[(int64_t)i * n + k] * L[(int64_t)j * n + k];
+      L[(int64_t)i * n + j] = s / d;
+    }
+  }
+  std::vector<double> col(n);
+  for (int c = 0; c < n; ++c) {
+    // solve L y = e_c
+    for (int i = 0; i < n; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) s -= L[(int64_t)i * n + k] * col[k];
+      col[i] = s / L[(int64_t)i * n + i];
+    }
+    // solve L^T z = y
+    for (int i = n - 1; i >= 0; --i) {
+      double s = col[i];
+      for (int k = i + 1; k < n; ++k) s -= L[(int64_t)k * n + i] * col[k];
+      col[i] = s / L[(int64_t)i * n + i];
+    }
+    for (int i = 0; i < n; ++i) a[(int64_t)i * n + c] = col[i];
+  }
+}
+
+namespace {
+
+std::vector<int32_t> aggregate(const Csr& A) {
+  const int64_t n = A.rows;
+  std::vector<double> diag(n, 0.0);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t t = A.ptr[i]; t < A.ptr[i + 1]; ++t)
+      if (A.idx[t] == i) diag[i] = A.val[t];
+  // strong neighbour lists (columns ascending)
+  std::vector<int64_t> sptr(n + 1, 0);
+  std::vector<int32_t> sidx;
+  const double th2 = kAmgTheta * kAmgTheta;
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t t = A.ptr[i]; t < A.ptr[i + 1]; ++t) {
+      const int32_t j = A.idx[t];
+      if (j == i) continue;
+      const double v = A.val[t];
+      if (v * v > th2 * diag[i] * diag[j]) sidx.push_back(j);
+    }
+    sptr[i + 1] = (int64_t)sidx.size();
+  }
+  std::vector<int32_t> agg(n, -1);
+  int32_t na = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (agg[i] >= 0 || sptr[i + 1] == sptr[i]) continue;
+    bool free_all = true;
+    for (int64_t t = sptr[i]; t < sptr[i + 1]; ++t)
+      if (agg[sidx[t]] >= 0) { free_all = false; break; }
+    if (!free_all) continue;
+    agg[i] = na;
+    for (int64_t t = sptr[i]; t < sptr[i + 1]; ++t) agg[sidx[t]] = na;
+    ++na;
+  }
+  std::vector<int32_t> after1(agg);
+  for (int64_t i = 0; i < n; ++i) {
+    if (agg[i] >= 0) continue;
+    for (int64_t t = sptr[i]; t < sptr[i + 1]; ++t)
+      if (after1[sidx[t]] >= 0) { agg[i] = after1[sidx[t]]; break; }
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    if (agg[i] >= 0) continue;
+    agg[i] = na;
+    for (int64_t t = sptr[i]; t < sptr[i + 1]; ++t)
+      if (agg[sidx[t]] < 0) agg[sidx[t]] = na;
+    ++na;
+  }
+  return agg;
+}
+
+std::vector<double> l1_diag(const Csr& A) {
+  std::vector<double> d(A.rows, 0.0);
+  for (int64_t i = 0; i < A.rows; ++i)
+    for (int64_t t = A.ptr[i]; t < A.ptr[i + 1]; ++t) d[i] += std::fabs(A.val[t]);
+  return d;
+}
+
+}  // namespace
+
+AmgHierarchy amg_setup(const Csr& A0) {
+  AmgHierarchy H;
+  H.levels.push_back({A0, l1_diag(A0), {}, {}});
+  while (true) {
+    AmgLevel& L = H.levels.back();
+    const int64_t n = L.A.rows;
+    if (n <= kAmgCoarseMax || (int)H.levels.size() >= kAmgMaxLevels) break;
+    std::vector<int32_t> agg = aggregate(L.A);
+    int64_t nc = 0;
+    for (int32_t a : agg) nc = std::max<int64_t>(nc, a + 1);
+    if ((double)nc >= 0.9 * (double)n) break;
+    std::vector<double> diag(n, 0.0);
+    double rho = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int64_t t = L.A.ptr[i]; t < L.A.ptr[i + 1]; ++t) {
+        if (L.A.idx[t] == i) diag[i] = L.A.val[t];
+        s += std::fabs(L.A.val[t]);
+      }
+      rho = std::max(rho, s / diag[i]);
+    }
+    const double omega = 4.0 / (3.0 * rho);
+    // P = (I - omega D^-1 A) T: row i, column agg[j] gets delta_ij - omega a_ij / a_ii
+    std::vector<int64_t> r;
+    std::vector<int32_t> c;
+    std::vector<double> v;
+    for (int64_t i = 0; i < n; ++i) {
+      r.push_back(i);
+      c.push_back(agg[i]);
+      v.push_back(1.0);
+      for (int64_t t = L.A.ptr[i]; t < L.A.ptr[i + 1]; ++t) {
+        r.push_back(i);
+        c.push_back(agg[L.A.idx[t]]);
+        v.push_back(-omega * L.A.val[t] / diag[i]);
+      }
+    }
+    Csr P = csr_from_triplets(n, nc, r, c, v);
+    Csr R = csr_transpose(P);
+    Csr Ac = csr_multiply(R, csr_multiply(L.A, P));
+    L.P = std::move(P);
+    L.R = std::move(R);
+    AmgLevel next{std::move(Ac), {}, {}, {}};
+    next.dl1 = l1_diag(next.A);
+    H.levels.push_back(std::move(next));
+  }
+  const Csr& C = H.levels.back().A;
+  const int nc = (int)C.rows;
+  H.coarse_inv.assign((int64_t)nc * nc, 0.0);
+  for (int64_t i = 0; i < nc; ++i)
+    for (int64_t t = C.ptr[i]; t < C.ptr[i + 1]; ++t) H.coarse_inv[i * nc + C.idx[t]] = C.val[t];
+  dense_inverse_spd(nc, H.coarse_inv);
+  return H;
+}
+
+}  // namespace dg

@@ -1,0 +1,42 @@
+// Small host CSR toolkit for the preconditioner setup (LOR triple product and
+// the smoothed-aggregation hierarchy).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+namespace dg {
+
+struct Csr {
+  int64_t rows = 0, cols = 0;
+  std::vector<int64_t> ptr;   // rows+1
+  std::vector<int32_t> idx;
+  std::vector<double> val;
+  int64_t nnz() const { return (int64_t)idx.size(); }
+};
+
+// Triplets -> CSR with duplicates summed and columns sorted.
+Csr csr_from_triplets(int64_t rows, int64_t cols, std::vector<int64_t>& r,
+                      std::vector<int32_t>& c, std::vector<double>& v);
+Csr csr_transpose(const Csr& A);
+Csr csr_multiply(const Csr& A, const Csr& B);   // sorted columns, exact zeros kept
+
+// Deterministic smoothed-aggregation AMG hierarchy (setup only).
+struct AmgLevel {
+  Csr A;
+  std::vector<double> dl1;   // l1-Jacobi diagonal sum_j |a_ij|
+  Csr P, R;                  // prolongator to this level from the next, R = P^T
+};
+struct AmgHierarchy {
+  std::vector<AmgLevel> levels;
+  std::vector<double> coarse_inv;  // dense inverse of the last level (row-major)
+};
+
+constexpr double kAmgTheta = 0.08;
+constexpr int kAmgCoarseMax = 256;
+constexpr int kAmgMaxLevels = 12;
+
+AmgHierarchy amg_setup(const Csr& A);
+void dense_inverse_spd(int n, std::vector<double>& a);  // in place, Cholesky based
+
+}  // namespace dg

@@ -1,0 +1,45 @@
+"""The C-ABI library loads and exports every entry point of include/dg.h
+(no compute calls: these run without a GPU)."""
+import ctypes
+import os
+import re
+import subprocess
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "dg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dg_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_matches_binding(built_lib):
+    assert declared_symbols() == sorted(built_lib.ABI_SYMBOLS)
+
+
+def test_library_exports_every_symbol(built_lib):
+    L = ctypes.CDLL(built_lib.LIB_PATH)
+    for name in declared_symbols():
+        assert hasattr(L, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", built_lib.LIB_PATH],
+                         capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (dg_\w+)", out))
+    assert set(declared_symbols()) <= exported
+
+
+def test_last_error_callable_without_gpu(built_lib):
+    assert built_lib.lib().dg_last_error() == b""
+
+
+def test_invalid_mesh_rejected_without_side_effects(built_lib):
+    """DG_EINVAL for overlapping boxes, before any device work."""
+    import numpy as np
+    from paper_2009_01287_gb300.inputs import MeshDesc
+    bad = MeshDesc(2, np.array([[0, 0], [0, 0]], dtype=np.int32), np.array([1, 1], dtype=np.int32),
+                   np.array([1, 1], dtype=np.int32), (2, 1), 0.5)
+    try:
+        built_lib.dg_mesh_create(bad)
+        raise AssertionError("accepted an invalid mesh")
+    except built_lib.DGError as e:
+        assert e.code == built_lib.DG_EINVAL

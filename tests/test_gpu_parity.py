@@ -1,0 +1,229 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: operator and FP64 preconditioner applies to 1e-12 relative
+(max-norm of the difference over the max-norm of the oracle result); PCG
+iteration counts within +-1 of the oracle at the same tolerance; the mixed
+FP32-preconditioner path within +10% iterations of the FP64 path.
+"""
+import numpy as np
+import pytest
+
+from oracle import dg, rhs, solver
+from paper_2009_01287_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+MESHES = {
+    "cfg0": (lambda: inputs.config0()[0], 10.0, "p1sq"),
+    "hp-a": (lambda: inputs.small_hp_mesh(1, base=4, depth=3, prob=0.4, pmax=5), None, "paper"),
+    "hp-b": (lambda: inputs.small_hp_mesh(2, base=3, depth=3, prob=0.5, pmin=1, pmax=8), None, "paper"),
+    "hp-high": (lambda: inputs.small_hp_mesh(5, base=2, depth=2, prob=0.5, pmin=7, pmax=8), None, "paper"),
+    "single": (lambda: inputs.uniform_mesh(2, 1, 8), None, "paper"),
+    "ragged": (lambda: inputs.random_refined_mesh(2, 5, 3, 0.35, 1, 4, seed=9, base_y=3), None, "paper"),
+}
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _opts(B, form, eta, pform, **kw):
+    return B.make_options(form=B.DG_FORM_BR2 if form == "br2" else B.DG_FORM_SIPG, eta=eta or 0.0,
+                          penalty_form=B.DG_PENALTY_P1SQ if pform == "p1sq" else B.DG_PENALTY_PAPER, **kw)
+
+
+@pytest.fixture(scope="module")
+def torch_mod(cuda_device):
+    import torch
+    return torch
+
+
+def dev(torch, a):
+    return torch.tensor(np.asarray(a), dtype=torch.float64, device="cuda")
+
+
+@pytest.mark.parametrize("form", ["sipg", "br2"])
+@pytest.mark.parametrize("name", list(MESHES))
+def test_apply_parity(built_lib, torch_mod, name, form):
+    mk, eta, pform = MESHES[name]
+    mesh = mk()
+    prob = solver.build_problem(mesh, form=form, eta=eta, penalty_form=pform)
+    B = built_lib
+    M = B.Mesh(mesh, _opts(B, form, eta, pform))
+    x = inputs.random_vector(M.n_dofs, 3)
+    xd = dev(torch_mod, x)
+    yd = torch_mod.empty_like(xd)
+    B.dg_apply(M.h, xd, yd)
+    torch_mod.cuda.synchronize()
+    y = yd.cpu().numpy()
+    assert rel(y, prob.A @ x) <= 1e-12
+    # deterministic: a second apply is bit-identical
+    yd2 = torch_mod.empty_like(xd)
+    B.dg_apply(M.h, xd, yd2)
+    torch_mod.cuda.synchronize()
+    assert torch_mod.equal(yd, yd2)
+
+
+@pytest.mark.parametrize("lor", ["exact", "amg"])
+@pytest.mark.parametrize("name", ["cfg0", "hp-a", "hp-b", "ragged"])
+def test_precond_parity_fp64(built_lib, torch_mod, name, lor):
+    mk, eta, pform = MESHES[name]
+    mesh = mk()
+    prob = solver.build_problem(mesh, eta=eta, penalty_form=pform)
+    opc = solver.Preconditioner(prob, lor=lor)
+    B = built_lib
+    o = _opts(B, "sipg", eta, pform, lor=B.DG_LOR_EXACT if lor == "exact" else B.DG_LOR_AMG)
+    M = B.Mesh(mesh, o)
+    pc = B.Precond(M, o)
+    r = inputs.random_vector(M.n_dofs, 4)
+    rd = dev(torch_mod, r)
+    zd = torch_mod.empty_like(rd)
+    B.dg_precond_apply(pc.h, rd, zd)
+    torch_mod.cuda.synchronize()
+    assert rel(zd.cpu().numpy(), opc.apply(r)) <= 1e-12
+
+
+def test_precond_jacobi_only_fp64(built_lib, torch_mod):
+    mk, eta, pform = MESHES["hp-a"]
+    mesh = mk()
+    prob = solver.build_problem(mesh)
+    opc = solver.Preconditioner(prob, lor="amg", smoother="jacobi_only")
+    B = built_lib
+    o = _opts(B, "sipg", None, "paper", smoother=B.DG_SMOOTHER_JACOBI_ONLY)
+    M = B.Mesh(mesh, o)
+    pc = B.Precond(M, o)
+    r = inputs.random_vector(M.n_dofs, 6)
+    rd = dev(torch_mod, r)
+    zd = torch_mod.empty_like(rd)
+    B.dg_precond_apply(pc.h, rd, zd)
+    torch_mod.cuda.synchronize()
+    assert rel(zd.cpu().numpy(), opc.apply(r)) <= 1e-12
+
+
+def test_precond_mixed_close(built_lib, torch_mod):
+    """FP32 preconditioner: within FP32 round-off of the FP64 oracle."""
+    mk, eta, pform = MESHES["hp-a"]
+    mesh = mk()
+    prob = solver.build_problem(mesh)
+    opc = solver.Preconditioner(prob, lor="amg")
+    B = built_lib
+    o = _opts(B, "sipg", None, "paper", precision=B.DG_PREC_MIXED)
+    M = B.Mesh(mesh, o)
+    pc = B.Precond(M, o)
+    r = inputs.random_vector(M.n_dofs, 7)
+    rd = dev(torch_mod, r)
+    zd = torch_mod.empty_like(rd)
+    B.dg_precond_apply(pc.h, rd, zd)
+    torch_mod.cuda.synchronize()
+    assert rel(zd.cpu().numpy(), opc.apply(r)) <= 1e-4
+
+
+@pytest.mark.parametrize("name,lor,form,tol", [("cfg0", "exact", "sipg", 1e-10), ("hp-a", "amg", "sipg", 1e-8),
+                                               ("hp-b", "amg", "br2", 1e-8), ("ragged", "amg", "sipg", 1e-8)])
+def test_pcg_iterations_match_oracle(built_lib, torch_mod, name, lor, form, tol):
+    mk, eta, pform = MESHES[name]
+    mesh = mk()
+    prob = solver.build_problem(mesh, form=form, eta=eta, penalty_form=pform)
+    opc = solver.Preconditioner(prob, lor=lor)
+    rh = inputs.sine_rhs(2, 0)
+    b = rhs.load_vector(prob.space, rh.amps, rh.waves)
+    ref = solver.pcg(prob.A, b, opc.apply, tol, 2000)
+    B = built_lib
+    o = _opts(B, form, eta, pform, lor=B.DG_LOR_EXACT if lor == "exact" else B.DG_LOR_AMG)
+    M = B.Mesh(mesh, o)
+    pc = B.Precond(M, o)
+    bd = dev(torch_mod, b)
+    xd = torch_mod.empty_like(bd)
+    info = B.dg_pcg_solve(M.h, pc.h, bd, xd, tol, 2000)
+    assert info.status == 0 and info.rel_res <= tol
+    assert abs(info.iters - ref.iters) <= 1
+    x = xd.cpu().numpy()
+    assert rel(x, ref.x) <= 1e2 * tol
+
+
+@pytest.mark.parametrize("name", ["hp-a", "ragged"])
+def test_pcg_mixed_within_ten_percent(built_lib, torch_mod, name):
+    mk, eta, pform = MESHES[name]
+    mesh = mk()
+    B = built_lib
+    M = B.Mesh(mesh, _opts(B, "sipg", eta, pform))
+    pc64 = B.Precond(M, _opts(B, "sipg", eta, pform))
+    pc32 = B.Precond(M, _opts(B, "sipg", eta, pform, precision=B.DG_PREC_MIXED))
+    bd = torch_mod.empty(M.n_dofs, dtype=torch_mod.float64, device="cuda")
+    rh = inputs.sine_rhs(2, 1)
+    B.dg_rhs_sine(M.h, rh.amps, rh.waves, bd)
+    x64 = torch_mod.empty_like(bd)
+    x32 = torch_mod.empty_like(bd)
+    i64 = B.dg_pcg_solve(M.h, pc64.h, bd, x64, 1e-8, 2000)
+    i32 = B.dg_pcg_solve(M.h, pc32.h, bd, x32, 1e-8, 2000)
+    assert i32.rel_res <= 1e-8
+    assert i32.iters <= int(1.1 * i64.iters) + 1
+    # the true residual of the mixed solution, with the FP64 operator
+    r = torch_mod.empty_like(bd)
+    B.dg_apply(M.h, x32, r)
+    torch_mod.cuda.synchronize()
+    assert float(torch_mod.linalg.norm(r - bd) / torch_mod.linalg.norm(bd)) <= 1.5e-8
+
+
+def test_rhs_matches_oracle(built_lib, torch_mod):
+    mesh = MESHES["hp-b"][0]()
+    prob = solver.build_problem(mesh)
+    rh = inputs.sine_rhs(2, 3)
+    B = built_lib
+    M = B.Mesh(mesh)
+    bd = torch_mod.empty(M.n_dofs, dtype=torch_mod.float64, device="cuda")
+    B.dg_rhs_sine(M.h, rh.amps, rh.waves, bd)
+    assert rel(bd.cpu().numpy(), rhs.load_vector(prob.space, rh.amps, rh.waves)) <= 1e-12
+
+
+def test_pcg_host_entry_identical(built_lib, torch_mod):
+    mesh = MESHES["hp-a"][0]()
+    B = built_lib
+    M = B.Mesh(mesh)
+    pc = B.Precond(M)
+    b = inputs.random_vector(M.n_dofs, 8)
+    xd = torch_mod.empty(M.n_dofs, dtype=torch_mod.float64, device="cuda")
+    i1 = B.dg_pcg_solve(M.h, pc.h, dev(torch_mod, b), xd, 1e-8, 1000)
+    xh = np.zeros(M.n_dofs)
+    i2 = B.dg_pcg_solve_host(M.h, pc.h, b, xh, 1e-8, 1000)
+    assert i1.iters == i2.iters
+    assert np.array_equal(xd.cpu().numpy(), xh)
+
+
+def test_zero_rhs_and_maxit(built_lib, torch_mod):
+    mesh = MESHES["hp-a"][0]()
+    B = built_lib
+    M = B.Mesh(mesh)
+    pc = B.Precond(M)
+    b = torch_mod.zeros(M.n_dofs, dtype=torch_mod.float64, device="cuda")
+    x = torch_mod.full_like(b, 7.0)
+    info = B.dg_pcg_solve(M.h, pc.h, b, x, 1e-8, 100)
+    assert info.iters == 0 and float(x.abs().max()) == 0.0
+    b = dev(torch_mod, inputs.random_vector(M.n_dofs, 9))
+    info = B.dg_pcg_solve(M.h, pc.h, b, x, 1e-14, 3, raise_on_notconv=False)
+    assert info.status == B.DG_ENOTCONV and info.iters == 3
+
+
+def test_full_size_config1_sampled(built_lib, torch_mod):
+    """Full 2D hp-random workload (32x32 base, depth 3): the apply in the
+    launch configuration the benchmark times, checked on sampled elements
+    whose rows the oracle computes one by one."""
+    mesh, _ = inputs.config1(0)
+    B = built_lib
+    M = B.Mesh(mesh)
+    x = inputs.random_vector(M.n_dofs, 10)
+    xd = dev(torch_mod, x)
+    yd = torch_mod.empty_like(xd)
+    B.dg_apply(M.h, xd, yd)
+    torch_mod.cuda.synchronize()
+    y = yd.cpu().numpy()
+    from oracle.dg import DGSpace
+    from oracle.topology import Topology
+    topo = Topology(mesh.lo, mesh.size, mesh.p, mesh.extent)
+    space = DGSpace(topo, mesh.lattice_h)
+    rng = np.random.default_rng(0)
+    ks = rng.choice(topo.n, size=40, replace=False)
+    for k in ks:
+        ref = dg.element_rows(space, int(k), x, 100.0)
+        got = y[space.offset[k]:space.offset[k + 1]]
+        assert rel(got, ref) <= 1e-12, int(k)

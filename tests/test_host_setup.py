@@ -1,0 +1,54 @@
+"""The library's host setup (run through the inspection library, no GPU)
+against the oracle: topology-derived operator rows, conforming prolongation,
+V_J / V_e split, LOR matrix, block inverses and AMG hierarchy."""
+import numpy as np
+import pytest
+
+from oracle import solver
+from paper_2009_01287_gb300 import inputs
+
+CASES = [
+    ("cfg0", lambda: inputs.config0()[0], "sipg", 10.0, "p1sq"),
+    ("hp1", lambda: inputs.small_hp_mesh(1, base=4, depth=3, prob=0.4, pmax=5), "sipg", None, "paper"),
+    ("hp2-br2", lambda: inputs.small_hp_mesh(2, base=4, depth=3, prob=0.4, pmax=6), "br2", None, "paper"),
+    ("hp3-p8", lambda: inputs.small_hp_mesh(3, base=3, depth=2, prob=0.5, pmin=6, pmax=8), "sipg", None, "paper"),
+    ("single", lambda: inputs.uniform_mesh(2, 1, 3), "sipg", None, "paper"),
+]
+
+
+def _pair(built_lib, mk, form, eta, pform):
+    mesh = mk()
+    prob = solver.build_problem(mesh, form=form, eta=eta, penalty_form=pform)
+    B = built_lib
+    opts = B.make_options(form=B.DG_FORM_BR2 if form == "br2" else B.DG_FORM_SIPG, eta=eta or 0.0,
+                          penalty_form=B.DG_PENALTY_P1SQ if pform == "p1sq" else B.DG_PENALTY_PAPER)
+    return prob, B.HostSetup(mesh, opts)
+
+
+@pytest.mark.parametrize("name,mk,form,eta,pform", CASES, ids=[c[0] for c in CASES])
+def test_host_setup_matches_oracle(built_lib, name, mk, form, eta, pform):
+    prob, hs = _pair(built_lib, mk, form, eta, pform)
+    x = inputs.random_vector(prob.space.n, 11)
+    ya, yb = prob.A @ x, hs.apply(x)
+    assert np.abs(ya - yb).max() <= 1e-12 * np.abs(ya).max()
+    assert hs.nC == prob.cs.n
+    assert abs(prob.cs.P - hs.P).max() < 1e-13
+    assert np.array_equal(prob.cs.kind, hs.kind)
+    assert len(hs.blocks) == len(prob.cs.blocks)
+    for a, b in zip(prob.cs.blocks, hs.blocks):
+        assert np.array_equal(a, b)
+    pc = solver.Preconditioner(prob, lor="amg")
+    assert abs(pc.Ac - hs.Ac).max() <= 1e-13 * abs(pc.Ac).max()
+    d = np.where(pc.jmask, pc.dinv, 0.0)
+    assert np.abs(d - hs.dinv).max() <= 1e-12 * np.abs(d).max()
+    for a, b in zip(pc.block_inv, hs.block_inv):
+        assert np.abs(a - b).max() <= 1e-10 * np.abs(a).max()
+    assert [L.n for L in pc.levels] == [l.shape[0] for l in hs.levels]
+    for L, l in zip(pc.levels, hs.levels):
+        assert abs(L.A - l).max() <= 1e-11 * abs(L.A).max()
+
+
+def test_default_br2_penalty_matches(built_lib):
+    prob, hs = _pair(built_lib, CASES[2][1], "br2", None, "paper")
+    from oracle.dg import br2_eta
+    assert hs.eta == br2_eta(prob.topo)
