@@ -1,0 +1,327 @@
+"""Benchmark: PCG solves of the 2D hp-random workload through the C ABI.
+
+Workload: 2D Poisson on [0,1]^2, 32x32 base squares refined at random
+(probability 0.3 per cell, depth <= 3, arbitrarily irregular), degrees
+p ~ U{1..6}, SIPG with eta = 100, sine right-hand side (4 seeded modes),
+relative tolerance 1e-8; preconditioner B = B_B + B_C with one AMG V-cycle
+on the LOR matrix.  A step is one complete PCG solve (every PCG iteration
+runs the operator apply, the preconditioner and the vector updates).
+`value` is DOF-iterations per second of the mixed-precision solve (FP32
+preconditioner, FP64 operator / residual / dots); the FP64 solve is timed
+beside it.  L2 is flushed (a 512 MiB write) before every timed step.
+
+--impl reference times the FP64 CPU oracle on the same workload (a bounded
+sample of PCG iterations per step).  Multi-GPU: independent replicas
+(the problem does not shard), one per rank.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "2D hp-random 32x32 base, prob 0.3, depth<=3, p~U{1..6}, SIPG eta=100, tol 1e-8, seed 0"
+METRIC = "DOF-iters/s (PCG on the 2D hp-random workload, mixed FP32 preconditioner / FP64 outer)"
+ORACLE_SAMPLE_ITERS = 20
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 9:
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return json.load(open(path)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def fp64_peak_tflops(sm_mhz: float) -> float:
+    """FP64 FMA peak: 152 SMs x 2 FP64 FMA per SM per clock (GB300 nominal
+    1.25 TFLOP/s at ~2.07 GHz), at the SM clock sampled under load."""
+    return 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2009_01287_gb300 import binding as B
+    from paper_2009_01287_gb300 import inputs
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    mesh, rh = inputs.config1(args.seed)
+    opts64 = B.make_options(precision=B.DG_PREC_FP64, lor=B.DG_LOR_AMG)
+    opts32 = B.make_options(precision=B.DG_PREC_MIXED, lor=B.DG_LOR_AMG)
+    M = B.Mesh(mesh, opts64, stream)
+    t0 = time.perf_counter()
+    pc32 = B.Precond(M, opts32)
+    setup_s = time.perf_counter() - t0
+    pc64 = B.Precond(M, opts64)
+    n = M.n_dofs
+    b = torch.empty(n, dtype=torch.float64, device=dev)
+    B.dg_rhs_sine(M.h, rh.amps, rh.waves, b, stream)
+    x = torch.empty_like(b)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    tol, maxit = args.tol, 5000
+
+    def solve(pc):
+        return B.dg_pcg_solve(M.h, pc.h, b, x, tol, maxit, stream)
+
+    for _ in range(args.warmup):
+        solve(pc32)
+        solve(pc64)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms32, it32, ms64, it64 = [], [], [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        info = solve(pc32)
+        ms32.append(info.solve_ms)
+        it32.append(info.iters)
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        info = solve(pc64)
+        ms64.append(info.solve_ms)
+        it64.append(info.iters)
+    torch.cuda.synchronize()
+    # dominant kernel: the operator apply, timed alone on the launching stream
+    xin = torch.randn(n, dtype=torch.float64, device=dev)
+    yout = torch.empty_like(xin)
+    for _ in range(5):
+        B.dg_apply(M.h, xin, yout, stream)
+    napply = 50
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * napply)]
+    for i in range(napply):
+        flush.fill_(2.0)
+        ev[2 * i].record(stream)
+        B.dg_apply(M.h, xin, yout, stream)
+        ev[2 * i + 1].record(stream)
+    torch.cuda.synchronize()
+    apply_ms = statistics.mean(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(napply))
+    # end to end: host buffers in and out through the C ABI (pinned)
+    bh = b.cpu().numpy().copy()
+    xh = np.zeros(n)
+    t_e2e, it_e2e = [], []
+    for _ in range(args.steps):
+        flush.fill_(3.0)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        info = B.dg_pcg_solve_host(M.h, pc32.h, bh, xh, tol, maxit, stream)
+        t_e2e.append(time.perf_counter() - t1)
+        it_e2e.append(info.iters)
+    clk = clocks.stop()
+    t32 = sum(ms32) / 1e3
+    t64 = sum(ms64) / 1e3
+    dof_iters32 = n * sum(it32)
+    if dist:
+        tt = torch.tensor([t32, t64, sum(t_e2e)], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t32, t64, te = (float(v) for v in tt)
+    else:
+        te = sum(t_e2e)
+    value = ws * dof_iters32 / t32
+    stats = M.stats
+    s32 = pc32.stats
+    peaks, peak_kind = _peaks()
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp64_peak = fp64_peak_tflops(sm_mhz)
+    achieved_tf = stats.apply_flops / (apply_ms / 1e3) / 1e12
+    levels = s32.n_levels
+    kernels_per_iter = 1 + 1 + (1 + 4 * (levels - 1) + 1 + 1) + 1 + 1
+    launches = sum(4 + 2 * levels + it * kernels_per_iter for it in it32)  # init + first precond
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "DOF-iters/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * t32 / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64 (outer PCG, operator) + f32 (preconditioner)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_dofs": n, "n_elems": int(stats.n_elems),
+                   "n_conforming": int(s32.n_conforming), "amg_levels": levels,
+                   "n_blocks": int(s32.n_blocks), "max_block": int(s32.max_block),
+                   "parallelism": f"replicas x{ws}", "l2": "flushed (512 MiB write) before every step"},
+        "iters_mixed": statistics.median(it32),
+        "iters_fp64": statistics.median(it64),
+        "time_to_tol_ms_mixed": statistics.median(ms32),
+        "time_to_tol_ms_fp64": statistics.median(ms64),
+        "dof_iters_per_s_fp64": ws * n * sum(it64) / t64,
+        "setup_s": setup_s,
+        "e2e": {"value": ws * n * sum(it_e2e) / te, "unit": "DOF-iters/s",
+                "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
+        "roofline": {"kernel": "apply_kernel (SIPG operator, FP64)", "bound": "alu",
+                     "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": achieved_tf / fp64_peak, "traffic": None,
+                     "flops_per_launch": stats.apply_flops, "launch_ms": apply_ms,
+                     "hbm_gbs": stats.apply_bytes / (apply_ms / 1e3) / 1e9,
+                     "hbm_frac": stats.apply_bytes / (apply_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                     "peak_source": f"FP64 FMA units x sampled SM clock; HBM {peak_kind}"},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        out["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def _oracle_setup(seed: int):
+    from oracle import rhs, solver
+    from paper_2009_01287_gb300 import inputs
+    mesh, rh = inputs.config1(seed)
+    prob = solver.build_problem(mesh)
+    pc = solver.Preconditioner(prob, lor="amg")
+    b = rhs.load_vector(prob.space, rh.amps, rh.waves)
+    return prob, pc, b
+
+
+def _oracle_step(prob, pc, b, iters: int) -> float:
+    from oracle import solver
+    t = time.perf_counter()
+    solver.pcg(prob.A, b, pc.apply, 1e-30, iters)
+    return time.perf_counter() - t
+
+
+def cpu_baseline(args):
+    prob, pc, b = _oracle_setup(args.seed)
+    dt = _oracle_step(prob, pc, b, ORACLE_SAMPLE_ITERS)
+    return {"value": prob.space.n * ORACLE_SAMPLE_ITERS / dt, "unit": "DOF-iters/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{ORACLE_SAMPLE_ITERS} FP64 PCG iterations of the same workload "
+                      f"(setup untimed), scipy sparse + numpy, one thread"}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    prob, pc, b = _oracle_setup(args.seed)
+    for _ in range(args.warmup):
+        _oracle_step(prob, pc, b, ORACLE_SAMPLE_ITERS)
+    times = [_oracle_step(prob, pc, b, ORACLE_SAMPLE_ITERS) for _ in range(args.steps)]
+    n = prob.space.n
+    value = n * ORACLE_SAMPLE_ITERS * args.steps / sum(times)
+    out = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "DOF-iters/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_dofs": n},
+        "cpu_baseline": {"value": value, "unit": "DOF-iters/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{ORACLE_SAMPLE_ITERS} FP64 PCG iterations per step"},
+        "e2e": {"value": value, "unit": "DOF-iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -105,6 +105,16 @@ typedef struct {
   int64_t level_nnz[16];
 } dg_precond_stats;
 
+typedef struct {
+  int64_t n_elems;
+  int64_t n_dofs;
+  int64_t n_subfaces;     /* sub-faces counted once per side (interior ones twice) */
+  int64_t max_level_gap;  /* largest log2 size ratio across a sub-face            */
+  double apply_flops;     /* FP64 flops of one dg_apply as formulated (FMA = 2)  */
+  double apply_bytes;     /* algorithmic bytes of one dg_apply: x read, y write,
+                             per-element and per-sub-face records read once     */
+} dg_mesh_stats;
+
 /* Build the mesh topology (sub-faces, hanging vertices, master edges) and
  * upload the operator data.  Section 2 (mesh, DG space) and 2.1 (sigma).
  * opts: only form, eta and penalty_form are used here.  stream: for uploads. */
@@ -112,6 +122,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, const dg_options* opts,
                          void* stream, dg_mesh** out);
 void dg_mesh_destroy(dg_mesh* mesh);
 int64_t dg_num_dofs(const dg_mesh* mesh);
+dg_status dg_mesh_stats_get(const dg_mesh* mesh, dg_mesh_stats* out);
 
 /* y = A x, the matrix-free DG operator of Eq. fe-problem (SIPG) or of the
  * BR2 form (Section 4.4), FP64.  x and y: device, n_dofs doubles, must not

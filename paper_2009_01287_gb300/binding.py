@@ -27,7 +27,7 @@ DG_SMOOTHER_FULL, DG_SMOOTHER_JACOBI_ONLY = 0, 1
 
 # every entry point declared in include/dg.h
 ABI_SYMBOLS = (
-    "dg_mesh_create", "dg_mesh_destroy", "dg_num_dofs", "dg_apply", "dg_precond_setup",
+    "dg_mesh_create", "dg_mesh_destroy", "dg_num_dofs", "dg_mesh_stats_get", "dg_apply", "dg_precond_setup",
     "dg_precond_destroy", "dg_precond_stats_get", "dg_precond_apply", "dg_pcg_solve",
     "dg_pcg_solve_host", "dg_rhs_sine", "dg_last_error",
 )
@@ -48,6 +48,11 @@ class DgOptions(C.Structure):
 class DgSolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("rel_res", C.c_double), ("status", C.c_int),
                 ("solve_ms", C.c_double)]
+
+
+class DgMeshStats(C.Structure):
+    _fields_ = [("n_elems", C.c_int64), ("n_dofs", C.c_int64), ("n_subfaces", C.c_int64),
+                ("max_level_gap", C.c_int64), ("apply_flops", C.c_double), ("apply_bytes", C.c_double)]
 
 
 class DgPrecondStats(C.Structure):
@@ -76,6 +81,7 @@ def lib():
         L.dg_mesh_destroy.argtypes = [vp]
         L.dg_num_dofs.argtypes = [vp]
         L.dg_num_dofs.restype = i64
+        L.dg_mesh_stats_get.argtypes = [vp, C.POINTER(DgMeshStats)]
         L.dg_apply.argtypes = [vp, dp, dp, vp]
         L.dg_precond_setup.argtypes = [vp, C.POINTER(DgOptions), C.POINTER(vp)]
         L.dg_precond_destroy.argtypes = [vp]
@@ -154,6 +160,12 @@ def dg_num_dofs(h: int) -> int:
     return int(lib().dg_num_dofs(h))
 
 
+def dg_mesh_stats_get(h: int) -> DgMeshStats:
+    s = DgMeshStats()
+    _check(lib().dg_mesh_stats_get(h, C.byref(s)))
+    return s
+
+
 def dg_apply(h: int, x, y, stream=None) -> None:
     _check(lib().dg_apply(h, _ptr(x), _ptr(y), _stream(stream)))
 
@@ -209,6 +221,7 @@ class Mesh:
         self.opts = opts or make_options()
         self.h = dg_mesh_create(mesh, self.opts, stream)
         self.n_dofs = dg_num_dofs(self.h)
+        self.stats = dg_mesh_stats_get(self.h)
 
     def close(self):
         if self.h:

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -143,6 +144,8 @@ struct PcgWork {
   double *part_pq = nullptr, *part_rr = nullptr, *part_rz = nullptr, *part_bb = nullptr;
   double* sc = nullptr;
   double* hsc = nullptr;  // pinned host copy of the scalars
+  double* hb = nullptr;   // device copies for the host-buffer entry point
+  double* hx = nullptr;
   DevArena arena;
   // captured iteration graph and the arguments it was captured with
   cudaGraph_t graph = nullptr;
@@ -188,6 +191,8 @@ static PcgWork& pcg_work(const dg_precond* pc) {
   w->part_rz = w->arena.alloc<double>(kVecBlocks);
   w->part_bb = w->arena.alloc<double>(kVecBlocks);
   w->sc = w->arena.alloc<double>(SC_COUNT);
+  w->hb = w->arena.alloc<double>(w->n);
+  w->hx = w->arena.alloc<double>(w->n);
   DG_CUDA(cudaMallocHost(&w->hsc, SC_COUNT * sizeof(double)));
   DG_CUDA(cudaEventCreate(&w->e0));
   DG_CUDA(cudaEventCreate(&w->e1));
@@ -212,6 +217,8 @@ static bool pcg_capture(const dg_mesh* M, const dg_precond* pc, PcgWork& w, doub
   if (w.exec && w.g_x == x && w.g_maxit == maxit && w.g_rtol2 == rtol2) return true;
   w.drop_graph();
   if (w.graph_failed) return false;
+  const char* env = std::getenv("DG_PCG_GRAPH");
+  if (env && env[0] == '0') return false;  // host-driven loop requested
   cudaGraphConditionalHandle handle = 0;
   bool ok = false;
   if (cudaGraphCreate(&w.graph, 0) == cudaSuccess &&
@@ -323,6 +330,13 @@ void dg_mesh_destroy(dg_mesh* mesh) { delete mesh; }
 
 int64_t dg_num_dofs(const dg_mesh* mesh) { return mesh ? mesh->n_dofs : -1; }
 
+dg_status dg_mesh_stats_get(const dg_mesh* mesh, dg_mesh_stats* out) {
+  return guarded([&] {
+    DG_REQUIRE(mesh && out, "null argument");
+    *out = mesh->stats;
+  });
+}
+
 dg_status dg_apply(const dg_mesh* mesh, const double* x, double* y, void* stream) {
   return guarded([&] {
     DG_REQUIRE(mesh && x && y, "null argument");
@@ -398,11 +412,11 @@ dg_status dg_pcg_solve_host(const dg_mesh* mesh, const dg_precond* pc, const dou
                             void* stream) {
   return guarded([&] {
     DG_REQUIRE(mesh && pc && b_host && x_host, "null argument");
+    DG_REQUIRE(pc->mesh == mesh, "preconditioner belongs to another mesh");
     const cudaStream_t s = (cudaStream_t)stream;
-    DevArena a;
-    struct Free { DevArena& a; ~Free() { a.release(); } } fr{a};
-    double* b = a.alloc<double>(mesh->n_dofs);
-    double* x = a.alloc<double>(mesh->n_dofs);
+    PcgWork& w = pcg_work(pc);
+    double* b = w.hb;
+    double* x = w.hx;
     DG_CUDA(cudaMemcpyAsync(b, b_host, mesh->n_dofs * sizeof(double), cudaMemcpyHostToDevice, s));
     dg_status st = DG_OK;
     try {

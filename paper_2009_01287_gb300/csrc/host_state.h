@@ -57,6 +57,7 @@ struct dg_mesh {
   dg_options opts{};
   double eta = 0.0;
   int64_t n_dofs = 0;
+  dg_mesh_stats stats{};
   // host copies of what the device holds
   std::vector<double> h_h;
   std::vector<dg::SubFaceRec> h_sf;

@@ -302,6 +302,33 @@ void build_mesh_host(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opt
   }
   M->n_tiles = (int)M->h_tiles.size();
   M->h_order = order;
+  // operation and byte counts of one operator apply, as the kernel does it
+  dg_mesh_stats& S = M->stats;
+  S = dg_mesh_stats{};
+  S.n_elems = m.n;
+  S.n_dofs = M->n_dofs;
+  S.n_subfaces = (int64_t)m.sf.size();
+  double fl = 0.0;
+  for (int64_t k = 0; k < m.n; ++k) {
+    const double n1 = m.p[k] + 1.0;
+    fl += 2.0 * (4.0 * n1 * n1 * n1 + 4.0 * n1 * n1 + 4.0 * n1 * n1);  // volume, own dn, gather
+    for (int j = m.sf_ptr[4 * k]; j < m.sf_ptr[4 * k + 4]; ++j) {
+      const auto& f = m.sf[j];
+      if (f.nb < 0) {
+        fl += 2.0 * (2.0 * n1 * n1);
+        if (o.form == DG_FORM_BR2) fl += 2.0 * (2.0 * n1 * n1);
+        continue;
+      }
+      const double nn = m.p[f.nb] + 1.0;
+      fl += 2.0 * (2.0 * n1 * n1 + 2.0 * n1 * nn + nn * nn);
+      if (o.form == DG_FORM_BR2) fl += 2.0 * (2.0 * n1 * nn + 2.0 * nn * nn + n1 * n1 + n1 * n1);
+      const int lg = std::abs(ilog2(m.size[k]) - ilog2(m.size[f.nb]));
+      S.max_level_gap = std::max<int64_t>(S.max_level_gap, lg);
+    }
+  }
+  S.apply_flops = fl;
+  S.apply_bytes = 16.0 * (double)M->n_dofs + (double)m.n * (4 + 8 + 8 + 4 + 16) +
+                  (double)m.sf.size() * sizeof(SubFaceRec);
 }
 
 }  // namespace dg
