@@ -340,6 +340,7 @@ pcg_update_xr_kernel(double* __restrict__ x, double* __restrict__ r, const doubl
                      const double* __restrict__ q, int64_t n, const double* part_pq, int n_pq,
                      double* sc, double* part_rr) {
   __shared__ double red[kVecThreads];
+  if (sc[SC_STATUS] != 0.0) return;  // converged or stopped: iterations queued after it are no-ops
   const double pq = sum_partials<kVecThreads>(part_pq, n_pq, red);
   const double alpha = sc[SC_RZ] / pq;
   if (blockIdx.x == 0 && threadIdx.x == 0) sc[SC_ALPHA] = alpha;
@@ -366,6 +367,7 @@ __global__ void __launch_bounds__(kVecThreads)
 pcg_update_p_kernel(double* __restrict__ p, const double* __restrict__ z, int64_t n,
                     const double* part_rz, int n_rz, const double* sc) {
   __shared__ double red[kVecThreads];
+  if (sc[SC_STATUS] != 0.0) return;
   const double rz_new = sum_partials<kVecThreads>(part_rz, n_rz, red);
   const double beta = rz_new / sc[SC_RZ];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -383,6 +385,10 @@ __global__ void pcg_check_kernel(const double* part_rr, int n_rr, const double* 
                                  double* sc, int maxit, double rtol2,
                                  cudaGraphConditionalHandle h, int use_cond) {
   __shared__ double red[kVecThreads];
+  if (sc[SC_STATUS] != 0.0) {
+    if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+    return;
+  }
   const double rr = sum_partials<kVecThreads>(part_rr, n_rr, red);
   const double rz = sum_partials<kVecThreads>(part_rz, n_rz, red);
   if (threadIdx.x == 0) {

@@ -227,3 +227,21 @@ def test_full_size_config1_sampled(built_lib, torch_mod):
         ref = dg.element_rows(space, int(k), x, 100.0)
         got = y[space.offset[k]:space.offset[k + 1]]
         assert rel(got, ref) <= 1e-12, int(k)
+
+
+def test_pcg_host_loop_matches_graph(built_lib, torch_mod, monkeypatch):
+    """The host-driven PCG loop (graphs disabled) stops at the same iteration
+    and returns the same iterate as the graph-launched loop."""
+    mesh = MESHES["hp-a"][0]()
+    B = built_lib
+    M = B.Mesh(mesh)
+    b = dev(torch_mod, inputs.random_vector(M.n_dofs, 12))
+    pc_g = B.Precond(M)
+    xg = torch_mod.empty_like(b)
+    ig = B.dg_pcg_solve(M.h, pc_g.h, b, xg, 1e-10, 2000)
+    monkeypatch.setenv("DG_PCG_GRAPH", "0")
+    pc_h = B.Precond(M)
+    xh = torch_mod.empty_like(b)
+    ih = B.dg_pcg_solve(M.h, pc_h.h, b, xh, 1e-10, 2000)
+    assert ih.iters == ig.iters
+    assert torch_mod.equal(xg, xh)
