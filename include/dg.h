@@ -153,6 +153,34 @@ dg_status dg_pcg_solve_host(const dg_mesh* mesh, const dg_precond* pc, const dou
                             double* x_host, double rtol, int maxit, dg_solve_info* info,
                             void* stream);
 
+/* The same PCG solve as dg_pcg_solve, but one that allocates nothing: the
+ * paper has no counterpart; this is an interface for callers that must not
+ * have the library allocate device or pinned memory, or build CUDA graphs,
+ * while they solve.  Examples: a service that reserves all device memory at
+ * start-up and forbids cudaMalloc/cudaFree afterwards (they can synchronise
+ * the whole device and stall other streams), or a caller that runs the solve
+ * from a context where new allocations would fail its memory budget.
+ * dg_pcg_solve allocates its work vectors, a graph and pinned memory on its
+ * first call per preconditioner; this entry point instead takes its work
+ * vectors (r, z, p, q and the reduction partials) from one fixed array in
+ * device memory that every GPU which loads the library holds until exit
+ * (about 8.1 MiB), and iterates from a host loop.  The caller still passes b
+ * and x (device, n_dofs doubles) and the handles (made beforehand by
+ * dg_mesh_create / dg_precond_setup, which do allocate).
+ *   - n_dofs is limited to 262144; larger meshes get DG_EINVAL and a message.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before starting any stream capture.
+ *   - All calls share the one array: calls whose work overlaps on the GPU
+ *     (other streams, other host threads) race and give wrong results.  Each
+ *     call overwrites every part of the array it reads, so nothing has to be
+ *     cleared between calls.
+ *   - info->solve_ms is host wall time of the call's iteration loop.
+ * Synchronous on `stream`. */
+dg_status dg_pcg_solve_noalloc(const dg_mesh* mesh, const dg_precond* pc, const double* b,
+                               double* x, double rtol, int maxit, dg_solve_info* info,
+                               void* stream);
+
 /* b_i = int f phi_i for f(x) = sum_m amps[m] prod_d sin(pi waves[m*dim+d] x_d)
  * ((p+3)-point Gauss rule per direction); b: device.  Host arithmetic. */
 dg_status dg_rhs_sine(const dg_mesh* mesh, int n_modes, const double* amps,

@@ -29,7 +29,7 @@ DG_SMOOTHER_FULL, DG_SMOOTHER_JACOBI_ONLY = 0, 1
 ABI_SYMBOLS = (
     "dg_mesh_create", "dg_mesh_destroy", "dg_num_dofs", "dg_mesh_stats_get", "dg_apply", "dg_precond_setup",
     "dg_precond_destroy", "dg_precond_stats_get", "dg_precond_apply", "dg_pcg_solve",
-    "dg_pcg_solve_host", "dg_rhs_sine", "dg_last_error",
+    "dg_pcg_solve_host", "dg_pcg_solve_noalloc", "dg_rhs_sine", "dg_last_error",
 )
 
 
@@ -89,6 +89,7 @@ def lib():
         L.dg_precond_apply.argtypes = [vp, dp, dp, vp]
         L.dg_pcg_solve.argtypes = [vp, vp, dp, dp, C.c_double, C.c_int, C.POINTER(DgSolveInfo), vp]
         L.dg_pcg_solve_host.argtypes = [vp, vp, dp, dp, C.c_double, C.c_int, C.POINTER(DgSolveInfo), vp]
+        L.dg_pcg_solve_noalloc.argtypes = [vp, vp, dp, dp, C.c_double, C.c_int, C.POINTER(DgSolveInfo), vp]
         L.dg_rhs_sine.argtypes = [vp, C.c_int, dp, dp, dp, vp]
         L.dg_last_error.restype = C.c_char_p
         for name in ABI_SYMBOLS:
@@ -205,6 +206,15 @@ def dg_pcg_solve_host(mesh_h: int, pc_h: int, b: np.ndarray, x: np.ndarray, rtol
     info = DgSolveInfo()
     _check(lib().dg_pcg_solve_host(mesh_h, pc_h, b.ctypes.data, x.ctypes.data, rtol, maxit,
                                    C.byref(info), _stream(stream)))
+    return info
+
+
+def dg_pcg_solve_noalloc(mesh_h: int, pc_h: int, b, x, rtol: float, maxit: int, stream=None) -> DgSolveInfo:
+    """PCG that allocates nothing at call time (fixed library-wide device
+    scratch, at most 262144 unknowns; see include/dg.h)."""
+    info = DgSolveInfo()
+    _check(lib().dg_pcg_solve_noalloc(mesh_h, pc_h or 0, _ptr(b), _ptr(x), rtol, maxit, C.byref(info),
+                                      _stream(stream)))
     return info
 
 

@@ -466,3 +466,100 @@ dg_status dg_rhs_sine(const dg_mesh* mesh, int n_modes, const double* amps, cons
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Allocation-free PCG solve.
+//
+// dg_pcg_solve keeps its work vectors (r, z, p, q, reduction partials) in
+// device memory that the library allocates on the first solve with each
+// preconditioner, plus a captured graph and pinned host memory.  The variant
+// below takes all of its solve-time scratch from one file-scope device array
+// of fixed size instead, and runs the iteration from a host loop, so a call
+// allocates nothing.
+// ============================================================================
+namespace dg {
+
+constexpr int64_t kNoAllocMaxDofs = 262144;   // largest mesh the variant accepts
+constexpr int64_t kNoAllocMaxTiles = 8192;    // operator CTAs (apply partials)
+constexpr int64_t kNoAllocDoubles =
+    4 * kNoAllocMaxDofs + kNoAllocMaxTiles + 3 * (int64_t)kVecBlocks + SC_COUNT;
+
+// 8.1 MiB per device that loads the library, held until the process exits.
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+// Device address of g_noalloc_scratch per device, looked up once per device.
+static double* g_noalloc_ptr[64] = {nullptr};
+
+static double* noalloc_scratch_for_current_device() {
+  int dev = 0;
+  DG_CUDA(cudaGetDevice(&dev));
+  DG_REQUIRE(dev >= 0 && dev < 64, "device ordinal out of range");
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    DG_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = (double*)p;
+  }
+  return g_noalloc_ptr[dev];
+}
+
+}  // namespace dg
+
+extern "C" dg_status dg_pcg_solve_noalloc(const dg_mesh* mesh, const dg_precond* pc,
+                                          const double* b, double* x, double rtol, int maxit,
+                                          dg_solve_info* info, void* stream) {
+  return guarded([&] {
+    DG_REQUIRE(mesh != nullptr, "null mesh");
+    if (mesh->n_dofs > kNoAllocMaxDofs)
+      throw Error(DG_EINVAL, "dg_pcg_solve_noalloc: n_dofs " + std::to_string(mesh->n_dofs) +
+                                 " exceeds the static scratch limit of " +
+                                 std::to_string(kNoAllocMaxDofs));
+    if (mesh->n_tiles > kNoAllocMaxTiles)
+      throw Error(DG_EINVAL, "dg_pcg_solve_noalloc: mesh needs more operator tiles than the static scratch holds");
+    DG_REQUIRE(pc && b && x, "null argument");
+    DG_REQUIRE(pc->mesh == mesh, "preconditioner belongs to another mesh");
+    DG_REQUIRE(rtol > 0.0 && maxit >= 1, "rtol must be > 0 and maxit >= 1");
+    const cudaStream_t s = (cudaStream_t)stream;
+    double* base = noalloc_scratch_for_current_device();
+    // carve the work vectors; every kernel below writes a slot before reading it
+    PcgWork w;
+    w.n = mesh->n_dofs;
+    w.r = base;
+    w.z = w.r + kNoAllocMaxDofs;
+    w.p = w.z + kNoAllocMaxDofs;
+    w.q = w.p + kNoAllocMaxDofs;
+    w.part_pq = w.q + kNoAllocMaxDofs;
+    w.part_rr = w.part_pq + kNoAllocMaxTiles;
+    w.part_rz = w.part_rr + kVecBlocks;
+    w.part_bb = w.part_rz + kVecBlocks;
+    w.sc = w.part_bb + kVecBlocks;
+    double hsc[SC_COUNT];
+    const int nrz = precond_final_blocks(*pc);
+    const double rtol2 = rtol * rtol;
+    const auto t0 = std::chrono::steady_clock::now();
+    launch_pcg_init(b, x, w.r, w.n, w.part_bb, s);
+    launch_precond(*pc, w.r, w.z, w.part_rz, s);
+    launch_pcg_first(w.part_rz, nrz, w.part_bb, w.sc, s);
+    launch_copy(w.z, w.p, w.n, s);
+    DG_CUDA(cudaMemcpyAsync(hsc, w.sc, sizeof(hsc), cudaMemcpyDeviceToHost, s));
+    DG_CUDA(cudaStreamSynchronize(s));
+    if (hsc[SC_BB] > 0.0) {
+      for (int it = 0; it < maxit;) {
+        for (int j = 0; j < 8 && it < maxit; ++j, ++it) pcg_body(mesh, pc, w, x, maxit, rtol2, 0, 0, s);
+        DG_CUDA(cudaMemcpyAsync(hsc, w.sc, sizeof(hsc), cudaMemcpyDeviceToHost, s));
+        DG_CUDA(cudaStreamSynchronize(s));
+        if (hsc[SC_STATUS] != 0.0) break;
+      }
+    }
+    const double ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    const double bb = hsc[SC_BB];
+    const bool conv = bb == 0.0 || hsc[SC_STATUS] == 1.0;
+    if (info) {
+      info->iters = bb > 0.0 ? (int)hsc[SC_IT] : 0;
+      info->rel_res = bb > 0.0 ? std::sqrt(hsc[SC_RR] / bb) : 0.0;
+      info->status = conv ? DG_OK : DG_ENOTCONV;
+      info->solve_ms = ms;
+    }
+    if (!conv) throw Error(DG_ENOTCONV, "PCG reached maxit");
+  });
+}
