@@ -42,6 +42,17 @@ static void build_mesh(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* o
   M->d_p = a.upload(m.p, s);
   M->d_off = a.upload(m.off, s);
   M->d_h = a.upload(M->h_h, s);
+  {
+    std::vector<double> ih(m.n);
+    std::vector<int64_t> toff(m.n + 1, 0);
+    for (int64_t k = 0; k < m.n; ++k) {
+      ih[k] = 1.0 / M->h_h[k];
+      toff[k + 1] = toff[k] + 8 * (int64_t)(m.p[k] + 1);
+    }
+    M->d_ih = a.upload(ih, s);
+    M->d_toff = a.upload(toff, s);
+    M->d_tr = a.alloc<double>(toff[m.n]);
+  }
   M->d_sf_ptr = a.upload(m.sf_ptr, s);
   M->d_sf = a.upload(M->h_sf, s);
   M->d_tables = a.upload(M->h_tables, s);
@@ -59,6 +70,7 @@ static void upload_csr(DevArena& a, const Csr& C, DevCsr& D, cudaStream_t s) {
   std::vector<T> val(C.val.begin(), C.val.end());
   D.rows = C.rows;
   D.nnz = C.nnz();
+  D.group = csr_group_for(C.rows ? (double)C.nnz() / (double)C.rows : 1.0);
   D.ptr = a.upload(ptr, s);
   D.idx = a.upload(C.idx, s);
   D.val = a.upload(val, s);

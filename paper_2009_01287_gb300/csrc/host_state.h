@@ -38,7 +38,15 @@ struct DevCsr {
   int32_t* ptr = nullptr;
   int32_t* idx = nullptr;
   void* val = nullptr;
+  int group = 1;   // lanes per row in the row kernels (power of two <= 32)
 };
+
+// lanes per row for a CSR with the given average row length
+inline int csr_group_for(double avg) {
+  int g = 1;
+  while (g < 32 && g * 2 <= avg) g *= 2;
+  return g;
+}
 
 struct DevLevel {
   int64_t n = 0;
@@ -70,6 +78,9 @@ struct dg_mesh {
   int32_t* d_p = nullptr;
   int64_t* d_off = nullptr;
   double* d_h = nullptr;
+  double* d_ih = nullptr;       // 1 / h
+  int64_t* d_toff = nullptr;    // side-trace offsets (8 (p+1) doubles per element)
+  double* d_tr = nullptr;       // side traces written by each apply
   int32_t* d_sf_ptr = nullptr;
   dg::SubFaceRec* d_sf = nullptr;
   double* d_tables = nullptr;

@@ -7,6 +7,21 @@
 namespace dg {
 
 // ============================================================== operator
+__global__ void __launch_bounds__(kThreads) trace_kernel(const ApplyArgs A) {
+  const ApplyTile T = A.tiles[blockIdx.x];
+  switch (T.p) {
+    case 1: trace_tile<1>(A, T); break;
+    case 2: trace_tile<2>(A, T); break;
+    case 3: trace_tile<3>(A, T); break;
+    case 4: trace_tile<4>(A, T); break;
+    case 5: trace_tile<5>(A, T); break;
+    case 6: trace_tile<6>(A, T); break;
+    case 7: trace_tile<7>(A, T); break;
+    case 8: trace_tile<8>(A, T); break;
+    default: break;
+  }
+}
+
 template <bool BR2>
 __global__ void __launch_bounds__(kThreads) apply_kernel(const ApplyArgs A) {
   extern __shared__ double smem[];
@@ -40,9 +55,10 @@ ApplyArgs make_apply_args(const dg_mesh& M, const double* x, double* y, double* 
   ApplyArgs A;
   A.x = x;
   A.y = y;
-  A.p = M.d_p;
   A.off = M.d_off;
-  A.h = M.d_h;
+  A.ih = M.d_ih;
+  A.toff = M.d_toff;
+  A.tr = M.d_tr;
   A.sf_ptr = M.d_sf_ptr;
   A.sf = M.d_sf;
   A.tab = M.d_tables;
@@ -65,6 +81,7 @@ void launch_apply(const dg_mesh& M, const double* x, double* y, double* dot_part
   if (M.n_tiles == 0) return;
   const ApplyArgs A = make_apply_args(M, x, y, dot_partial);
   const int smem = apply_smem_bytes();
+  trace_kernel<<<M.n_tiles, kThreads, 0, s>>>(A);
   if (M.opts.form == DG_FORM_BR2) apply_kernel<true><<<M.n_tiles, kThreads, smem, s>>>(A);
   else apply_kernel<false><<<M.n_tiles, kThreads, smem, s>>>(A);
   DG_CUDA(cudaGetLastError());
@@ -98,29 +115,91 @@ __device__ __forceinline__ double sum_partials(const double* part, int n, double
 template <typename T>
 __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
 
-// rc = P^T r  (rows of P^T)
-template <typename T>
-__global__ void restrict_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-                                const T* __restrict__ val, const double* __restrict__ r,
-                                T* __restrict__ out, int64_t rows) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows;
-       i += (int64_t)gridDim.x * blockDim.x) {
+// ---- group-per-row CSR kernels: G lanes of a warp share one row, strided
+// over its entries, then a fixed shuffle tree (deterministic for a fixed G).
+// The row loop advances by whole warps so that every lane of a warp reaches
+// the shuffles together.
+template <typename T, int G, class Op>
+__global__ void __launch_bounds__(kVecThreads)
+csr_rows_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                const T* __restrict__ val, int64_t rows, Op op) {
+  const int lane = threadIdx.x % G;
+  const int64_t groups_per_grid = ((int64_t)gridDim.x * blockDim.x) / G;
+  const int64_t g0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+  const int64_t rounds = (rows + groups_per_grid - 1) / groups_per_grid;
+  for (int64_t rd = 0; rd < rounds; ++rd) {
+    const int64_t row = g0 + rd * groups_per_grid;
     T s = 0;
-    for (int t = ptr[i]; t < ptr[i + 1]; ++t) s += ld(val + t) * (T)__ldg(r + ld(idx + t));
-    out[i] = s;
+    if (row < rows) {
+      const int e = ptr[row + 1];
+      for (int t = ptr[row] + lane; t < e; t += G) s += __ldg(val + t) * op.x(__ldg(idx + t));
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, G);
+    if (row < rows && lane == 0) op.store(row, s);
   }
 }
 
-// y = A x for a CSR of precision T
 template <typename T>
-__global__ void spmv_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-                            const T* __restrict__ val, const T* __restrict__ x, T* __restrict__ y,
-                            int64_t rows) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    T s = 0;
-    for (int t = ptr[i]; t < ptr[i + 1]; ++t) s += ld(val + t) * ld(x + ld(idx + t));
-    y[i] = s;
+struct OpSpmv {  // y = A v
+  const T* v;
+  T* y;
+  __device__ T x(int j) const { return __ldg(v + j); }
+  __device__ void store(int64_t i, T s) const { y[i] = s; }
+};
+template <typename T>
+struct OpRestrict {  // out = P^T r, r in FP64
+  const double* r;
+  T* out;
+  __device__ T x(int j) const { return (T)__ldg(r + j); }
+  __device__ void store(int64_t i, T s) const { out[i] = s; }
+};
+template <typename T>
+struct OpPre {  // x = b d ; r = b - A (b d)
+  const T* b;
+  const T* dinv;
+  T* xo;
+  T* r;
+  __device__ T x(int j) const { return __ldg(b + j) * __ldg(dinv + j); }
+  __device__ void store(int64_t i, T s) const {
+    const T bi = b[i];
+    xo[i] = bi * dinv[i];
+    r[i] = bi - s;
+  }
+};
+template <typename T>
+struct OpProlong {  // x += P xc
+  const T* xc;
+  T* xo;
+  __device__ T x(int j) const { return __ldg(xc + j); }
+  __device__ void store(int64_t i, T s) const { xo[i] += s; }
+};
+template <typename T>
+struct OpPost {  // xo = x + d (b - A x)
+  const T* xin;
+  const T* b;
+  const T* dinv;
+  T* xo;
+  __device__ T x(int j) const { return __ldg(xin + j); }
+  __device__ void store(int64_t i, T s) const { xo[i] = xin[i] + dinv[i] * (b[i] - s); }
+};
+
+template <typename T, class Op>
+static void launch_rows(const DevCsr& A, const Op& op, cudaStream_t s) {
+  if (A.rows == 0) return;
+  int64_t threads = A.rows * (int64_t)A.group;
+  int64_t blocks = (threads + kVecThreads - 1) / kVecThreads;
+  if (blocks > 8 * 152) blocks = 8 * 152;
+  const int32_t* p = A.ptr;
+  const int32_t* ix = A.idx;
+  const T* v = (const T*)A.val;
+  switch (A.group) {
+    case 1: csr_rows_kernel<T, 1, Op><<<(int)blocks, kVecThreads, 0, s>>>(p, ix, v, A.rows, op); break;
+    case 2: csr_rows_kernel<T, 2, Op><<<(int)blocks, kVecThreads, 0, s>>>(p, ix, v, A.rows, op); break;
+    case 4: csr_rows_kernel<T, 4, Op><<<(int)blocks, kVecThreads, 0, s>>>(p, ix, v, A.rows, op); break;
+    case 8: csr_rows_kernel<T, 8, Op><<<(int)blocks, kVecThreads, 0, s>>>(p, ix, v, A.rows, op); break;
+    case 16: csr_rows_kernel<T, 16, Op><<<(int)blocks, kVecThreads, 0, s>>>(p, ix, v, A.rows, op); break;
+    default: csr_rows_kernel<T, 32, Op><<<(int)blocks, kVecThreads, 0, s>>>(p, ix, v, A.rows, op); break;
   }
 }
 
@@ -129,63 +208,19 @@ template <typename T>
 __global__ void dense_mv_kernel(const T* __restrict__ Ainv, const T* __restrict__ x,
                                 T* __restrict__ y, int64_t n) {
   const int lane = threadIdx.x & 31;
-  for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; row < n;
-       row += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; row < n; row += warps) {
     T s = 0;
-    for (int64_t j = lane; j < n; j += 32) s += ld(Ainv + row * n + j) * ld(x + j);
+    for (int64_t j = lane; j < n; j += 32) s += __ldg(Ainv + row * n + j) * __ldg(x + j);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) y[row] = s;
   }
 }
 
-// pre-smoothing from zero and residual: x = b d, r = b - A (b d)
-template <typename T>
-__global__ void amg_pre_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-                               const T* __restrict__ val, const T* __restrict__ dinv,
-                               const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
-                               int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    T s = 0;
-    for (int t = ptr[i]; t < ptr[i + 1]; ++t) {
-      const int j = ld(idx + t);
-      s += ld(val + t) * (ld(b + j) * ld(dinv + j));
-    }
-    const T bi = ld(b + i);
-    x[i] = bi * ld(dinv + i);
-    r[i] = bi - s;
-  }
-}
-
-// coarse-grid correction: x += P xc
-template <typename T>
-__global__ void amg_prolong_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-                                   const T* __restrict__ val, const T* __restrict__ xc,
-                                   T* __restrict__ x, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    T s = 0;
-    for (int t = ptr[i]; t < ptr[i + 1]; ++t) s += ld(val + t) * ld(xc + ld(idx + t));
-    x[i] += s;
-  }
-}
-
-// post-smoothing: xo = x + d (b - A x)
-template <typename T>
-__global__ void amg_post_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-                                const T* __restrict__ val, const T* __restrict__ dinv,
-                                const T* __restrict__ b, const T* __restrict__ x,
-                                T* __restrict__ xo, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    T s = 0;
-    for (int t = ptr[i]; t < ptr[i + 1]; ++t) s += ld(val + t) * ld(x + ld(idx + t));
-    xo[i] = ld(x + i) + ld(dinv + i) * (ld(b + i) - s);
-  }
-}
-
-// z = P e_C + D_J^-1 r + sum_e R_e^T A_e^-1 R_e r, and a partial of r . z
+// z = P e_C + D_J^-1 r + sum_e R_e^T A_e^-1 R_e r, and a partial of r . z.
+// kFinalG lanes per DG row: they share the P entries and the block row.
+constexpr int kFinalG = 8;
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
 precond_final_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
@@ -197,25 +232,33 @@ precond_final_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict_
                      const double* __restrict__ r, double* __restrict__ z, int64_t n,
                      double* __restrict__ dot_partial) {
   __shared__ double red[kVecThreads];
+  constexpr int G = kFinalG;
+  const int lane = threadIdx.x % G;
+  const int64_t groups_per_grid = ((int64_t)gridDim.x * blockDim.x) / G;
+  const int64_t g0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+  const int64_t rounds = (n + groups_per_grid - 1) / groups_per_grid;
   double dot = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t rd = 0; rd < rounds; ++rd) {
+    const int64_t i = g0 + rd * groups_per_grid;
     T s = 0;
-    for (int t = ptr[i]; t < ptr[i + 1]; ++t) s += ld(val + t) * ld(ec + ld(idx + t));
-    const double ri = __ldg(r + i);
-    s += ld(dinv + i) * (T)ri;
-    const int b = __ldg(e_block + i);
-    if (b >= 0) {
-      const int d = __ldg(dim + b);
-      const T* row = inv + __ldg(inv_off + b) + (int64_t)__ldg(e_local + i) * d;
-      const int32_t* ds = dofs + __ldg(dofs_off + b);
-      T acc = 0;
-      for (int m = 0; m < d; ++m) acc += ld(row + m) * (T)__ldg(r + __ldg(ds + m));
-      s += acc;
+    if (i < n) {
+      for (int t = ptr[i] + lane; t < ptr[i + 1]; t += G) s += __ldg(val + t) * __ldg(ec + __ldg(idx + t));
+      const int b = __ldg(e_block + i);
+      if (b >= 0) {
+        const int d = __ldg(dim + b);
+        const T* row = inv + __ldg(inv_off + b) + (int64_t)__ldg(e_local + i) * d;
+        const int32_t* ds = dofs + __ldg(dofs_off + b);
+        for (int m = lane; m < d; m += G) s += __ldg(row + m) * (T)__ldg(r + __ldg(ds + m));
+      }
     }
-    const double zi = (double)s;
-    z[i] = zi;
-    dot += zi * ri;
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, G);
+    if (i < n && lane == 0) {
+      const double ri = __ldg(r + i);
+      const double zi = (double)(s + __ldg(dinv + i) * (T)ri);
+      z[i] = zi;
+      dot += zi * ri;
+    }
   }
   const double tot = block_sum<kVecThreads>(dot, red);
   if (dot_partial && threadIdx.x == 0) dot_partial[blockIdx.x] = tot;
@@ -228,7 +271,11 @@ static int grid_for(int64_t n, int threads = kVecThreads) {
   return (int)b;
 }
 
-int precond_final_blocks(const dg_precond& pc) { return grid_for(pc.n_dofs); }
+int precond_final_blocks(const dg_precond& pc) {
+  int64_t b = (pc.n_dofs * kFinalG + kVecThreads - 1) / kVecThreads;
+  if (b > kVecBlocks) b = kVecBlocks;
+  return (int)(b < 1 ? 1 : b);
+}
 
 template <typename T>
 static void vcycle(const dg_precond& pc, size_t l, cudaStream_t s) {
@@ -239,15 +286,11 @@ static void vcycle(const dg_precond& pc, size_t l, cudaStream_t s) {
     return;
   }
   const DevLevel& C = pc.levels[l + 1];
-  amg_pre_kernel<T><<<grid_for(L.n), kVecThreads, 0, s>>>(L.A.ptr, L.A.idx, (const T*)L.A.val,
-      (const T*)L.dinv, (const T*)L.b, (T*)L.x, (T*)L.r, L.n);
-  spmv_kernel<T><<<grid_for(C.n), kVecThreads, 0, s>>>(L.R.ptr, L.R.idx, (const T*)L.R.val,
-      (const T*)L.r, (T*)C.b, C.n);
+  launch_rows<T>(L.A, OpPre<T>{(const T*)L.b, (const T*)L.dinv, (T*)L.x, (T*)L.r}, s);
+  launch_rows<T>(L.R, OpSpmv<T>{(const T*)L.r, (T*)C.b}, s);
   vcycle<T>(pc, l + 1, s);
-  amg_prolong_kernel<T><<<grid_for(L.n), kVecThreads, 0, s>>>(L.P.ptr, L.P.idx, (const T*)L.P.val,
-      (const T*)C.xo, (T*)L.x, L.n);
-  amg_post_kernel<T><<<grid_for(L.n), kVecThreads, 0, s>>>(L.A.ptr, L.A.idx, (const T*)L.A.val,
-      (const T*)L.dinv, (const T*)L.b, (const T*)L.x, (T*)L.xo, L.n);
+  launch_rows<T>(L.P, OpProlong<T>{(const T*)C.xo, (T*)L.x}, s);
+  launch_rows<T>(L.A, OpPost<T>{(const T*)L.x, (const T*)L.b, (const T*)L.dinv, (T*)L.xo}, s);
 }
 
 template <typename T>
@@ -256,14 +299,12 @@ static void precond_impl(const dg_precond& pc, const double* r, double* z, doubl
   const void* ec = nullptr;
   if (pc.n_c > 0) {
     if (pc.lor == DG_LOR_EXACT) {
-      restrict_kernel<T><<<grid_for(pc.n_c), kVecThreads, 0, s>>>(pc.PT.ptr, pc.PT.idx,
-          (const T*)pc.PT.val, r, (T*)pc.rc, pc.n_c);
+      launch_rows<T>(pc.PT, OpRestrict<T>{r, (T*)pc.rc}, s);
       dense_mv_kernel<T><<<grid_for(pc.n_c * 32), kVecThreads, 0, s>>>(
           (const T*)pc.lor_inv, (const T*)pc.rc, (T*)pc.ec, pc.n_c);
       ec = pc.ec;
     } else {
-      restrict_kernel<T><<<grid_for(pc.n_c), kVecThreads, 0, s>>>(pc.PT.ptr, pc.PT.idx,
-          (const T*)pc.PT.val, r, (T*)pc.levels[0].b, pc.n_c);
+      launch_rows<T>(pc.PT, OpRestrict<T>{r, (T*)pc.levels[0].b}, s);
       vcycle<T>(pc, 0, s);
       ec = pc.levels[0].xo;
     }

@@ -320,7 +320,7 @@ void build_mesh_host(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opt
         continue;
       }
       const double nn = m.p[f.nb] + 1.0;
-      fl += 2.0 * (2.0 * n1 * n1 + 2.0 * n1 * nn + nn * nn);
+      fl += 2.0 * (2.0 * n1 * n1 + 2.0 * n1 * nn);
       if (o.form == DG_FORM_BR2) fl += 2.0 * (2.0 * n1 * nn + 2.0 * nn * nn + n1 * n1 + n1 * n1);
       const int lg = std::abs(ilog2(m.size[k]) - ilog2(m.size[f.nb]));
       S.max_level_gap = std::max<int64_t>(S.max_level_gap, lg);
