@@ -32,6 +32,55 @@
 
 namespace dg {
 
+// A grid-wide deterministic dot product: each CTA writes its partial, the last
+// CTA to finish (atomic ticket) sums the partials in CTA order into *out and
+// resets the ticket.  All-null = no reduction.
+struct Reduce {
+  double* partial = nullptr;
+  double* out = nullptr;
+  unsigned* ticket = nullptr;
+};
+
+// ============================================================== reductions
+// Deterministic block sum: fixed strided assignment + fixed tree.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const int t = threadIdx.x;
+  red[t] = v;
+  __syncthreads();
+#pragma unroll
+  for (int w = NT / 2; w > 0; w >>= 1) {
+    if (t < w) red[t] += red[t + w];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// Last-CTA finalisation of a grid-wide sum (see Reduce): deterministic, the
+// partials are summed in CTA order whichever CTA finishes last.
+template <int NT>
+__device__ __forceinline__ void reduce_finalize(double tot, const Reduce& R, double* red) {
+  __shared__ unsigned s_last;
+  if (threadIdx.x == 0) {
+    R.partial[blockIdx.x] = tot;
+    __threadfence();
+    s_last = (atomicAdd(R.ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    double v = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += NT) v += __ldcg(R.partial + i);
+    v = block_sum<NT>(v, red);
+    if (threadIdx.x == 0) {
+      *R.out = v;
+      *R.ticket = 0u;
+    }
+  }
+}
+
 struct ApplyArgs {
   const double* x;
   double* y;
@@ -45,7 +94,9 @@ struct ApplyArgs {
   const int32_t* order;       // degree-sorted element order
   const ApplyTile* tiles;
   double eta;                 // BR2 penalty
-  double* dot_partial;        // optional per-CTA partial of x . y
+  double* dot_partial;        // optional reduction of x . y (see Reduce)
+  double* dot_out;
+  unsigned* dot_ticket;
   BasisOff boff[kMaxP + 1];
 };
 
@@ -328,15 +379,10 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& 
     part = fma(y, sx[t], part);
   }
   if (A.dot_partial) {
-    // deterministic tile partial of x . y: fixed tree over the CTA
+    // deterministic x . y over all tiles
     __shared__ double red[kThreads];
-    red[tid] = part;
-    __syncthreads();
-    for (int w = kThreads / 2; w > 0; w >>= 1) {
-      if (tid < w) red[tid] += red[tid + w];
-      __syncthreads();
-    }
-    if (tid == 0) A.dot_partial[blockIdx.x] = red[0];
+    const double tot = block_sum<kThreads>(part, red);
+    reduce_finalize<kThreads>(tot, Reduce{A.dot_partial, A.dot_out, A.dot_ticket}, red);
   }
 }
 

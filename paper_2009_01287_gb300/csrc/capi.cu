@@ -106,6 +106,15 @@ static void upload_precond(dg_precond* pc, HostPrecond& H, cudaStream_t s) {
   pc->blk_dim = a.upload(dims, s);
   pc->blk_dofs = a.upload(dofs, s);
   pc->blk_inv = a.upload(inv, s);
+  pc->zE = a.alloc<T>(dofs.size());
+  pc->n_blocks = (int64_t)H.blocks.size();
+  pc->max_block = 0;
+  for (auto& b : H.blocks) pc->max_block = std::max<int64_t>(pc->max_block, (int64_t)b.size());
+  DG_REQUIRE(pc->max_block * (int64_t)sizeof(T) <= 48 * 1024,
+             "a V_e block is too large for the block-solve kernel's shared memory");
+  DG_CUDA(cudaStreamCreateWithFlags(&pc->side, cudaStreamNonBlocking));
+  DG_CUDA(cudaEventCreateWithFlags(&pc->ev_fork, cudaEventDisableTiming));
+  DG_CUDA(cudaEventCreateWithFlags(&pc->ev_join, cudaEventDisableTiming));
   pc->rc = a.alloc<T>(pc->n_c);
   pc->ec = a.alloc<T>(pc->n_c);
   if (pc->n_c > 0 && pc->lor == DG_LOR_EXACT) {
@@ -155,6 +164,7 @@ struct PcgWork {
   double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
   double *part_pq = nullptr, *part_rr = nullptr, *part_rz = nullptr, *part_bb = nullptr;
   double* sc = nullptr;
+  unsigned* tick = nullptr;  // reduction tickets (TK_*)
   double* hsc = nullptr;  // pinned host copy of the scalars
   double* hb = nullptr;   // device copies for the host-buffer entry point
   double* hx = nullptr;
@@ -203,6 +213,8 @@ static PcgWork& pcg_work(const dg_precond* pc) {
   w->part_rz = w->arena.alloc<double>(kVecBlocks);
   w->part_bb = w->arena.alloc<double>(kVecBlocks);
   w->sc = w->arena.alloc<double>(SC_COUNT);
+  w->tick = w->arena.alloc<unsigned>(TK_COUNT);
+  DG_CUDA(cudaMemset(w->tick, 0, TK_COUNT * sizeof(unsigned)));
   w->hb = w->arena.alloc<double>(w->n);
   w->hx = w->arena.alloc<double>(w->n);
   DG_CUDA(cudaMallocHost(&w->hsc, SC_COUNT * sizeof(double)));
@@ -214,13 +226,22 @@ static PcgWork& pcg_work(const dg_precond* pc) {
 
 static void pcg_body(const dg_mesh* M, const dg_precond* pc, PcgWork& w, double* x, int maxit,
                      double rtol2, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
-  const int nrz = precond_final_blocks(*pc);
-  launch_apply(*M, w.p, w.q, w.part_pq, s);
-  launch_pcg_update_xr(x, w.r, w.p, w.q, w.n, w.part_pq, M->n_tiles, w.sc, w.part_rr, s);
-  launch_precond(*pc, w.r, w.z, w.part_rz, s);
-  launch_pcg_update_p(w.p, w.z, w.n, w.part_rz, nrz, w.sc, s);
-  launch_pcg_check(w.part_rr, kVecBlocks, w.part_rz, nrz, w.sc, maxit, rtol2,
-                   (unsigned long long)h, use_cond, s);
+  launch_apply(*M, w.p, w.q, Reduce{w.part_pq, w.sc + SC_PQ, w.tick + TK_PQ}, s);
+  launch_pcg_update_xr(x, w.r, w.p, w.q, w.n, w.sc, Reduce{w.part_rr, w.sc + SC_RRNEW, w.tick + TK_RR}, s);
+  launch_precond(*pc, w.r, w.z, Reduce{w.part_rz, w.sc + SC_RZNEW, w.tick + TK_RZ}, s);
+  launch_pcg_update_p(w.p, w.z, w.n, w.sc, w.tick + TK_P, maxit, rtol2, (unsigned long long)h,
+                      use_cond, s);
+}
+
+// PCG start: x = 0, r = b, z = B r, p = z, scalars; returns b . b (synchronises)
+static double pcg_start(const dg_precond* pc, PcgWork& w, const double* b, double* x, double* hsc,
+                        cudaStream_t s) {
+  launch_pcg_init(b, x, w.r, w.n, Reduce{w.part_bb, w.sc + SC_BB, w.tick + TK_BB}, s);
+  launch_precond(*pc, w.r, w.z, Reduce{w.part_rz, w.sc + SC_RZNEW, w.tick + TK_RZ}, s);
+  launch_pcg_first(w.z, w.p, w.n, w.sc, s);
+  DG_CUDA(cudaMemcpyAsync(hsc, w.sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+  DG_CUDA(cudaStreamSynchronize(s));
+  return hsc[SC_BB];
 }
 
 // one graph: while (cond) { PCG iteration }, the condition set on the device
@@ -276,16 +297,10 @@ static void pcg_run(const dg_mesh* M, const dg_precond* pc, const double* b, dou
   DG_REQUIRE(pc->mesh == M, "preconditioner belongs to another mesh");
   DG_REQUIRE(rtol > 0.0 && maxit >= 1, "rtol must be > 0 and maxit >= 1");
   PcgWork& w = pcg_work(pc);
-  const int nrz = precond_final_blocks(*pc);
   const double rtol2 = rtol * rtol;
   const bool use_graph = pcg_capture(M, pc, w, x, maxit, rtol2);
   DG_CUDA(cudaEventRecord(w.e0, s));
-  launch_pcg_init(b, x, w.r, w.n, w.part_bb, s);
-  launch_precond(*pc, w.r, w.z, w.part_rz, s);
-  launch_pcg_first(w.part_rz, nrz, w.part_bb, w.sc, s);
-  launch_copy(w.z, w.p, w.n, s);
-  DG_CUDA(cudaMemcpyAsync(w.hsc, w.sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
-  DG_CUDA(cudaStreamSynchronize(s));
+  pcg_start(pc, w, b, x, w.hsc, s);
   if (w.hsc[SC_BB] > 0.0) {
     if (use_graph) {
       DG_CUDA(cudaGraphLaunch(w.exec, s));
@@ -353,7 +368,7 @@ dg_status dg_apply(const dg_mesh* mesh, const double* x, double* y, void* stream
   return guarded([&] {
     DG_REQUIRE(mesh && x && y, "null argument");
     DG_REQUIRE(x != y, "x and y must not alias");
-    launch_apply(*mesh, x, y, nullptr, (cudaStream_t)stream);
+    launch_apply(*mesh, x, y, Reduce{}, (cudaStream_t)stream);
   });
 }
 
@@ -410,7 +425,7 @@ dg_status dg_precond_apply(const dg_precond* pc, const double* r, double* z, voi
   return guarded([&] {
     DG_REQUIRE(pc && r && z, "null argument");
     DG_REQUIRE(r != z, "r and z must not alias");
-    launch_precond(*pc, r, z, nullptr, (cudaStream_t)stream);
+    launch_precond(*pc, r, z, Reduce{}, (cudaStream_t)stream);
   });
 }
 
@@ -494,7 +509,7 @@ namespace dg {
 constexpr int64_t kNoAllocMaxDofs = 262144;   // largest mesh the variant accepts
 constexpr int64_t kNoAllocMaxTiles = 8192;    // operator CTAs (apply partials)
 constexpr int64_t kNoAllocDoubles =
-    4 * kNoAllocMaxDofs + kNoAllocMaxTiles + 3 * (int64_t)kVecBlocks + SC_COUNT;
+    4 * kNoAllocMaxDofs + kNoAllocMaxTiles + 3 * (int64_t)kVecBlocks + SC_COUNT + TK_COUNT;
 
 // 8.1 MiB per device that loads the library, held until the process exits.
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
@@ -544,17 +559,13 @@ extern "C" dg_status dg_pcg_solve_noalloc(const dg_mesh* mesh, const dg_precond*
     w.part_rz = w.part_rr + kVecBlocks;
     w.part_bb = w.part_rz + kVecBlocks;
     w.sc = w.part_bb + kVecBlocks;
+    w.tick = reinterpret_cast<unsigned*>(w.sc + SC_COUNT);
     double hsc[SC_COUNT];
-    const int nrz = precond_final_blocks(*pc);
     const double rtol2 = rtol * rtol;
     const auto t0 = std::chrono::steady_clock::now();
-    launch_pcg_init(b, x, w.r, w.n, w.part_bb, s);
-    launch_precond(*pc, w.r, w.z, w.part_rz, s);
-    launch_pcg_first(w.part_rz, nrz, w.part_bb, w.sc, s);
-    launch_copy(w.z, w.p, w.n, s);
-    DG_CUDA(cudaMemcpyAsync(hsc, w.sc, sizeof(hsc), cudaMemcpyDeviceToHost, s));
-    DG_CUDA(cudaStreamSynchronize(s));
-    if (hsc[SC_BB] > 0.0) {
+    // the reduction tickets must start at zero
+    DG_CUDA(cudaMemsetAsync(w.tick, 0, TK_COUNT * sizeof(unsigned), s));
+    if (pcg_start(pc, w, b, x, hsc, s) > 0.0) {
       for (int it = 0; it < maxit;) {
         for (int j = 0; j < 8 && it < maxit; ++j, ++it) pcg_body(mesh, pc, w, x, maxit, rtol2, 0, 0, s);
         DG_CUDA(cudaMemcpyAsync(hsc, w.sc, sizeof(hsc), cudaMemcpyDeviceToHost, s));

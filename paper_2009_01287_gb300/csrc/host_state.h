@@ -112,11 +112,18 @@ struct dg_precond {
   int64_t n_coarse = 0;
   void* rc = nullptr;        // n_c restriction of r
   void* ec = nullptr;        // n_c LOR correction
+  void* zE = nullptr;        // block-solve results, one per V_e node (block order)
+  int64_t n_blocks = 0, max_block = 0;
+  cudaStream_t side = nullptr;   // the block solves run here, beside the V-cycle
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // PCG workspace and captured iteration graph, built on the first solve
   void* pcg_cache = nullptr;
   void (*pcg_cache_free)(void*) = nullptr;
   ~dg_precond() {
     if (pcg_cache_free) pcg_cache_free(pcg_cache);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (side) cudaStreamDestroy(side);
     arena.release();
   }
 };

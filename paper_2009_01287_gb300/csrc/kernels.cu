@@ -51,7 +51,7 @@ static int apply_smem_bytes() {
   return m * (int)sizeof(double);
 }
 
-ApplyArgs make_apply_args(const dg_mesh& M, const double* x, double* y, double* dot_partial) {
+ApplyArgs make_apply_args(const dg_mesh& M, const double* x, double* y, Reduce red) {
   ApplyArgs A;
   A.x = x;
   A.y = y;
@@ -65,7 +65,9 @@ ApplyArgs make_apply_args(const dg_mesh& M, const double* x, double* y, double* 
   A.order = M.d_order;
   A.tiles = M.d_tiles;
   A.eta = M.eta;
-  A.dot_partial = dot_partial;
+  A.dot_partial = red.partial;
+  A.dot_out = red.out;
+  A.dot_ticket = red.ticket;
   for (int p = 0; p <= kMaxP; ++p) A.boff[p] = M.boff[p];
   return A;
 }
@@ -77,31 +79,14 @@ void apply_kernel_setup() {
   DG_CUDA(cudaFuncSetAttribute(apply_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
 }
 
-void launch_apply(const dg_mesh& M, const double* x, double* y, double* dot_partial, cudaStream_t s) {
+void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cudaStream_t s) {
   if (M.n_tiles == 0) return;
-  const ApplyArgs A = make_apply_args(M, x, y, dot_partial);
+  const ApplyArgs A = make_apply_args(M, x, y, red);
   const int smem = apply_smem_bytes();
   trace_kernel<<<M.n_tiles, kThreads, 0, s>>>(A);
   if (M.opts.form == DG_FORM_BR2) apply_kernel<true><<<M.n_tiles, kThreads, smem, s>>>(A);
   else apply_kernel<false><<<M.n_tiles, kThreads, smem, s>>>(A);
   DG_CUDA(cudaGetLastError());
-}
-
-// ============================================================== reductions
-// Deterministic block sum: fixed strided assignment + fixed tree.
-template <int NT>
-__device__ __forceinline__ double block_sum(double v, double* red) {
-  const int t = threadIdx.x;
-  red[t] = v;
-  __syncthreads();
-#pragma unroll
-  for (int w = NT / 2; w > 0; w >>= 1) {
-    if (t < w) red[t] += red[t + w];
-    __syncthreads();
-  }
-  const double r = red[0];
-  __syncthreads();
-  return r;
 }
 
 template <int NT>
@@ -112,8 +97,6 @@ __device__ __forceinline__ double sum_partials(const double* part, int n, double
 }
 
 // ============================================================== preconditioner
-template <typename T>
-__device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
 
 // ---- group-per-row CSR kernels: G lanes of a warp share one row, strided
 // over its entries, then a fixed shuffle tree (deterministic for a fixed G).
@@ -218,21 +201,47 @@ __global__ void dense_mv_kernel(const T* __restrict__ Ainv, const T* __restrict_
   }
 }
 
-// z = P e_C + D_J^-1 r + sum_e R_e^T A_e^-1 R_e r, and a partial of r . z.
-// kFinalG lanes per DG row: they share the P entries and the block row.
-constexpr int kFinalG = 8;
+// V_e block solves, one CTA per block (Section 3.3, T_E = sum_e P_e): the
+// block's residual entries are gathered into shared memory once, then each
+// warp forms rows of A_e^-1 r_e with lanes striding along the (row-major)
+// inverse, so the loads of a row are coalesced.
 template <typename T>
+__global__ void __launch_bounds__(128)
+block_solve_kernel(const int64_t* __restrict__ inv_off, const int32_t* __restrict__ dofs_off,
+                   const int32_t* __restrict__ dim, const int32_t* __restrict__ dofs,
+                   const T* __restrict__ inv, const double* __restrict__ r, T* __restrict__ zE,
+                   int nblocks) {
+  extern __shared__ unsigned char smem_raw[];
+  T* sr = reinterpret_cast<T*>(smem_raw);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
+    const int d = __ldg(dim + b);
+    const int32_t* ds = dofs + __ldg(dofs_off + b);
+    for (int m = threadIdx.x; m < d; m += blockDim.x) sr[m] = (T)__ldg(r + __ldg(ds + m));
+    __syncthreads();
+    const T* A = inv + __ldg(inv_off + b);
+    for (int l = warp; l < d; l += nw) {
+      T acc = 0;
+      for (int m = lane; m < d; m += 32) acc += __ldg(A + (int64_t)l * d + m) * sr[m];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) zE[__ldg(dofs_off + b) + l] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// z = P e_C + D_J^-1 r + (block result on V_e nodes), and the r . z reduction.
+// G lanes per DG row share its P entries.
+template <typename T, int G>
 __global__ void __launch_bounds__(kVecThreads)
 precond_final_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
                      const T* __restrict__ val, const T* __restrict__ ec,
                      const T* __restrict__ dinv, const int32_t* __restrict__ e_block,
-                     const int32_t* __restrict__ e_local, const int64_t* __restrict__ inv_off,
-                     const int32_t* __restrict__ dofs_off, const int32_t* __restrict__ dim,
-                     const int32_t* __restrict__ dofs, const T* __restrict__ inv,
-                     const double* __restrict__ r, double* __restrict__ z, int64_t n,
-                     double* __restrict__ dot_partial) {
-  __shared__ double red[kVecThreads];
-  constexpr int G = kFinalG;
+                     const int32_t* __restrict__ e_local, const int32_t* __restrict__ dofs_off,
+                     const T* __restrict__ zE, const double* __restrict__ r,
+                     double* __restrict__ z, int64_t n, Reduce red) {
+  __shared__ double sred[kVecThreads];
   const int lane = threadIdx.x % G;
   const int64_t groups_per_grid = ((int64_t)gridDim.x * blockDim.x) / G;
   const int64_t g0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
@@ -241,27 +250,24 @@ precond_final_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict_
   for (int64_t rd = 0; rd < rounds; ++rd) {
     const int64_t i = g0 + rd * groups_per_grid;
     T s = 0;
-    if (i < n) {
+    if (i < n)
       for (int t = ptr[i] + lane; t < ptr[i + 1]; t += G) s += __ldg(val + t) * __ldg(ec + __ldg(idx + t));
-      const int b = __ldg(e_block + i);
-      if (b >= 0) {
-        const int d = __ldg(dim + b);
-        const T* row = inv + __ldg(inv_off + b) + (int64_t)__ldg(e_local + i) * d;
-        const int32_t* ds = dofs + __ldg(dofs_off + b);
-        for (int m = lane; m < d; m += G) s += __ldg(row + m) * (T)__ldg(r + __ldg(ds + m));
-      }
-    }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, G);
     if (i < n && lane == 0) {
       const double ri = __ldg(r + i);
-      const double zi = (double)(s + __ldg(dinv + i) * (T)ri);
+      s += __ldg(dinv + i) * (T)ri;
+      const int b = __ldg(e_block + i);
+      if (b >= 0) s += __ldg(zE + __ldg(dofs_off + b) + __ldg(e_local + i));
+      const double zi = (double)s;
       z[i] = zi;
       dot += zi * ri;
     }
   }
-  const double tot = block_sum<kVecThreads>(dot, red);
-  if (dot_partial && threadIdx.x == 0) dot_partial[blockIdx.x] = tot;
+  if (red.partial) {
+    const double tot = block_sum<kVecThreads>(dot, sred);
+    reduce_finalize<kVecThreads>(tot, red, sred);
+  }
 }
 
 static int grid_for(int64_t n, int threads = kVecThreads) {
@@ -272,7 +278,7 @@ static int grid_for(int64_t n, int threads = kVecThreads) {
 }
 
 int precond_final_blocks(const dg_precond& pc) {
-  int64_t b = (pc.n_dofs * kFinalG + kVecThreads - 1) / kVecThreads;
+  int64_t b = (pc.n_dofs * pc.P.group + kVecThreads - 1) / kVecThreads;
   if (b > kVecBlocks) b = kVecBlocks;
   return (int)(b < 1 ? 1 : b);
 }
@@ -294,8 +300,19 @@ static void vcycle(const dg_precond& pc, size_t l, cudaStream_t s) {
 }
 
 template <typename T>
-static void precond_impl(const dg_precond& pc, const double* r, double* z, double* dot_partial,
+static void precond_impl(const dg_precond& pc, const double* r, double* z, Reduce red,
                          cudaStream_t s) {
+  // fork: the block solves depend only on r
+  if (pc.n_blocks > 0) {
+    DG_CUDA(cudaEventRecord(pc.ev_fork, s));
+    DG_CUDA(cudaStreamWaitEvent(pc.side, pc.ev_fork, 0));
+    int g = (int)(pc.n_blocks < 8 * 152 ? pc.n_blocks : 8 * 152);
+    block_solve_kernel<T><<<g, 128, (size_t)pc.max_block * sizeof(T), pc.side>>>(
+        pc.blk_inv_off, pc.blk_dofs_off, pc.blk_dim, pc.blk_dofs, (const T*)pc.blk_inv, r,
+        (T*)pc.zE, (int)pc.n_blocks);
+    DG_CUDA(cudaGetLastError());
+    DG_CUDA(cudaEventRecord(pc.ev_join, pc.side));
+  }
   const void* ec = nullptr;
   if (pc.n_c > 0) {
     if (pc.lor == DG_LOR_EXACT) {
@@ -309,23 +326,28 @@ static void precond_impl(const dg_precond& pc, const double* r, double* z, doubl
       ec = pc.levels[0].xo;
     }
   }
-  precond_final_kernel<T><<<precond_final_blocks(pc), kVecThreads, 0, s>>>(
-      pc.P.ptr, pc.P.idx, (const T*)pc.P.val, (const T*)ec, (const T*)pc.dinv, pc.e_block,
-      pc.e_local, pc.blk_inv_off, pc.blk_dofs_off, pc.blk_dim, pc.blk_dofs,
-      (const T*)pc.blk_inv, r, z, pc.n_dofs, dot_partial);
+  if (pc.n_blocks > 0) DG_CUDA(cudaStreamWaitEvent(s, pc.ev_join, 0));
+  const int nb = precond_final_blocks(pc);
+#define DG_FINAL(G)                                                                          \
+  precond_final_kernel<T, G><<<nb, kVecThreads, 0, s>>>(                                     \
+      pc.P.ptr, pc.P.idx, (const T*)pc.P.val, (const T*)ec, (const T*)pc.dinv, pc.e_block,   \
+      pc.e_local, pc.blk_dofs_off, (const T*)pc.zE, r, z, pc.n_dofs, red)
+  if (pc.P.group <= 1) DG_FINAL(1);
+  else if (pc.P.group == 2) DG_FINAL(2);
+  else DG_FINAL(4);
+#undef DG_FINAL
   DG_CUDA(cudaGetLastError());
 }
 
-void launch_precond(const dg_precond& pc, const double* r, double* z, double* dot_partial,
-                    cudaStream_t s) {
-  if (pc.precision == DG_PREC_MIXED) precond_impl<float>(pc, r, z, dot_partial, s);
-  else precond_impl<double>(pc, r, z, dot_partial, s);
+void launch_precond(const dg_precond& pc, const double* r, double* z, Reduce red, cudaStream_t s) {
+  if (pc.precision == DG_PREC_MIXED) precond_impl<float>(pc, r, z, red, s);
+  else precond_impl<double>(pc, r, z, red, s);
 }
 
 // ============================================================== PCG
-
-__global__ void pcg_init_kernel(const double* __restrict__ b, double* __restrict__ x,
-                                double* __restrict__ r, int64_t n, double* part_bb) {
+__global__ void __launch_bounds__(kVecThreads)
+pcg_init_kernel(const double* __restrict__ b, double* __restrict__ x, double* __restrict__ r,
+                int64_t n, Reduce bb) {
   __shared__ double red[kVecThreads];
   double s = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -335,55 +357,39 @@ __global__ void pcg_init_kernel(const double* __restrict__ b, double* __restrict
     r[i] = bi;
     s += bi * bi;
   }
-  const double t = block_sum<kVecThreads>(s, red);
-  if (threadIdx.x == 0) part_bb[blockIdx.x] = t;
+  reduce_finalize<kVecThreads>(block_sum<kVecThreads>(s, red), bb, red);
 }
 
-void launch_pcg_init(const double* b, double* x, double* r, int64_t n, double* partial_bb,
-                     cudaStream_t s) {
-  pcg_init_kernel<<<kVecBlocks, kVecThreads, 0, s>>>(b, x, r, n, partial_bb);
+void launch_pcg_init(const double* b, double* x, double* r, int64_t n, Reduce bb, cudaStream_t s) {
+  pcg_init_kernel<<<grid_for(n), kVecThreads, 0, s>>>(b, x, r, n, bb);
   DG_CUDA(cudaGetLastError());
 }
 
-__global__ void copy_kernel(const double* __restrict__ a, double* __restrict__ b, int64_t n) {
+// p = z and the initial scalars (rz from the preconditioner's reduction)
+__global__ void pcg_first_kernel(const double* __restrict__ z, double* __restrict__ p, int64_t n,
+                                 double* sc) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = a[i];
-}
-
-void launch_copy(const double* src, double* dst, int64_t n, cudaStream_t s) {
-  copy_kernel<<<grid_for(n), kVecThreads, 0, s>>>(src, dst, n);
-  DG_CUDA(cudaGetLastError());
-}
-
-__global__ void pcg_first_kernel(const double* part_rz, int n_rz, const double* part_bb,
-                                 double* sc) {
-  __shared__ double red[kVecThreads];
-  const double rz = sum_partials<kVecThreads>(part_rz, n_rz, red);
-  const double bb = sum_partials<kVecThreads>(part_bb, kVecBlocks, red);
-  if (threadIdx.x == 0) {
-    sc[SC_RZ] = rz;
-    sc[SC_BB] = bb;
-    sc[SC_RR] = bb;
+    p[i] = z[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc[SC_RZ] = sc[SC_RZNEW];
+    sc[SC_RR] = sc[SC_BB];
     sc[SC_IT] = 0.0;
     sc[SC_STATUS] = 0.0;
   }
 }
 
-void launch_pcg_first(const double* part_rz, int n_rz, const double* part_bb, double* sc,
-                      cudaStream_t s) {
-  pcg_first_kernel<<<1, kVecThreads, 0, s>>>(part_rz, n_rz, part_bb, sc);
+void launch_pcg_first(const double* z, double* p, int64_t n, double* sc, cudaStream_t s) {
+  pcg_first_kernel<<<grid_for(n), kVecThreads, 0, s>>>(z, p, n, sc);
   DG_CUDA(cudaGetLastError());
 }
 
 __global__ void __launch_bounds__(kVecThreads)
 pcg_update_xr_kernel(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
-                     const double* __restrict__ q, int64_t n, const double* part_pq, int n_pq,
-                     double* sc, double* part_rr) {
+                     const double* __restrict__ q, int64_t n, double* sc, Reduce rr) {
   __shared__ double red[kVecThreads];
   if (sc[SC_STATUS] != 0.0) return;  // converged or stopped: iterations queued after it are no-ops
-  const double pq = sum_partials<kVecThreads>(part_pq, n_pq, red);
-  const double alpha = sc[SC_RZ] / pq;
+  const double alpha = sc[SC_RZ] / sc[SC_PQ];
   if (blockIdx.x == 0 && threadIdx.x == 0) sc[SC_ALPHA] = alpha;
   double s = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -393,62 +399,54 @@ pcg_update_xr_kernel(double* __restrict__ x, double* __restrict__ r, const doubl
     r[i] = ri;
     s += ri * ri;
   }
-  const double t = block_sum<kVecThreads>(s, red);
-  if (threadIdx.x == 0) part_rr[blockIdx.x] = t;
+  reduce_finalize<kVecThreads>(block_sum<kVecThreads>(s, red), rr, red);
 }
 
 void launch_pcg_update_xr(double* x, double* r, const double* p, const double* q, int64_t n,
-                          const double* part_pq, int n_pq, double* sc, double* part_rr,
-                          cudaStream_t s) {
-  pcg_update_xr_kernel<<<kVecBlocks, kVecThreads, 0, s>>>(x, r, p, q, n, part_pq, n_pq, sc, part_rr);
+                          double* sc, Reduce rr, cudaStream_t s) {
+  pcg_update_xr_kernel<<<grid_for(n), kVecThreads, 0, s>>>(x, r, p, q, n, sc, rr);
   DG_CUDA(cudaGetLastError());
 }
 
 __global__ void __launch_bounds__(kVecThreads)
-pcg_update_p_kernel(double* __restrict__ p, const double* __restrict__ z, int64_t n,
-                    const double* part_rz, int n_rz, const double* sc) {
-  __shared__ double red[kVecThreads];
-  if (sc[SC_STATUS] != 0.0) return;
-  const double rz_new = sum_partials<kVecThreads>(part_rz, n_rz, red);
-  const double beta = rz_new / sc[SC_RZ];
+pcg_update_p_kernel(double* __restrict__ p, const double* __restrict__ z, int64_t n, double* sc,
+                    unsigned* ticket, int maxit, double rtol2, cudaGraphConditionalHandle h,
+                    int use_cond) {
+  __shared__ unsigned s_last;
+  if (sc[SC_STATUS] != 0.0) {
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+    return;
+  }
+  const double beta = sc[SC_RZNEW] / sc[SC_RZ];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     p[i] = fma(beta, p[i], z[i]);
-}
-
-void launch_pcg_update_p(double* p, const double* z, int64_t n, const double* part_rz, int n_rz,
-                         double* sc, cudaStream_t s) {
-  pcg_update_p_kernel<<<kVecBlocks, kVecThreads, 0, s>>>(p, z, n, part_rz, n_rz, sc);
-  DG_CUDA(cudaGetLastError());
-}
-
-__global__ void pcg_check_kernel(const double* part_rr, int n_rr, const double* part_rz, int n_rz,
-                                 double* sc, int maxit, double rtol2,
-                                 cudaGraphConditionalHandle h, int use_cond) {
-  __shared__ double red[kVecThreads];
-  if (sc[SC_STATUS] != 0.0) {
-    if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
-    return;
-  }
-  const double rr = sum_partials<kVecThreads>(part_rr, n_rr, red);
-  const double rz = sum_partials<kVecThreads>(part_rz, n_rz, red);
+  __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    // every CTA has read rz: advance the scalars, test convergence
     const double it = sc[SC_IT] + 1.0;
+    const double rr = sc[SC_RRNEW];
     sc[SC_IT] = it;
     sc[SC_RR] = rr;
-    sc[SC_RZ] = rz;
+    sc[SC_RZ] = sc[SC_RZNEW];
     int cont = 1;
     if (rr <= rtol2 * sc[SC_BB]) { sc[SC_STATUS] = 1.0; cont = 0; }
     else if (it >= (double)maxit) { sc[SC_STATUS] = 2.0; cont = 0; }
+    *ticket = 0u;
     if (use_cond) cudaGraphSetConditional(h, cont ? 1u : 0u);
   }
 }
 
-void launch_pcg_check(const double* part_rr, int n_rr, const double* part_rz, int n_rz,
-                      double* sc, int maxit, double rtol2, unsigned long long cond_handle,
-                      int use_cond, cudaStream_t s) {
-  pcg_check_kernel<<<1, kVecThreads, 0, s>>>(part_rr, n_rr, part_rz, n_rz, sc, maxit, rtol2,
-                                             (cudaGraphConditionalHandle)cond_handle, use_cond);
+void launch_pcg_update_p(double* p, const double* z, int64_t n, double* sc, unsigned* ticket,
+                         int maxit, double rtol2, unsigned long long cond_handle, int use_cond,
+                         cudaStream_t s) {
+  pcg_update_p_kernel<<<grid_for(n), kVecThreads, 0, s>>>(
+      p, z, n, sc, ticket, maxit, rtol2, (cudaGraphConditionalHandle)cond_handle, use_cond);
   DG_CUDA(cudaGetLastError());
 }
 
