@@ -286,7 +286,7 @@ static int grid_for(int64_t n, int threads = kVecThreads) {
 // stages are separated by the hardware cluster barrier.  Vectors written in
 // the kernel are read through L2 (ld.global.cg) so no CTA sees a stale L1 line.
 constexpr int kMaxAmgLevels = 16;
-constexpr int kClusterThreads = 512;
+constexpr int kClusterThreads = 1024;
 
 template <typename T>
 struct LevelView {
