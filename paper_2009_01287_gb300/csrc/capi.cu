@@ -153,13 +153,6 @@ static void upload_precond(dg_precond* pc, HostPrecond& H, cudaStream_t s) {
     }
     pc->n_coarse = Hm.levels.back().A.rows;
     DG_REQUIRE(Hm.levels.size() <= 16, "too many AMG levels");
-    // coarse levels (<= kClusterMaxRows rows, below level 0) in one cluster kernel
-    const char* env = std::getenv("DG_AMG_CLUSTER");
-    pc->cluster_size = (env && env[0] == '0') ? 0 : coarse_cluster_size(pc->precision);
-    pc->cluster_first = -1;
-    if (pc->cluster_size > 0)
-      for (size_t l = 1; l < Hm.levels.size(); ++l)
-        if (Hm.levels[l].A.rows <= kClusterMaxRows) { pc->cluster_first = (int)l; break; }
     pc->coarse_inv = a.upload(std::vector<T>(Hm.coarse_inv.begin(), Hm.coarse_inv.end()), s);
     pc->stats.n_levels = (int)Hm.levels.size();
   }

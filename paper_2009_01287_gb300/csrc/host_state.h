@@ -108,8 +108,6 @@ struct dg_precond {
   void* blk_inv = nullptr;   // row-major dense inverses
   void* lor_inv = nullptr;   // exact LOR solve: dense inverse n_c x n_c
   std::vector<dg::DevLevel> levels;  // AMG (level 0 = LOR matrix)
-  int cluster_first = -1;            // first level run by the cluster kernel (-1: none)
-  int cluster_size = 0;              // CTAs per cluster for that kernel
   void* coarse_inv = nullptr;
   int64_t n_coarse = 0;
   void* rc = nullptr;        // n_c restriction of r

@@ -2,8 +2,6 @@
 // P^T, LOR solve, P, point Jacobi, block solves) and the PCG vector work.
 #include <cstdio>
 
-#include <cooperative_groups.h>
-
 #include "kernels.cuh"
 
 namespace dg {
@@ -279,174 +277,6 @@ static int grid_for(int64_t n, int threads = kVecThreads) {
   return (int)b;
 }
 
-// ---- coarse AMG levels in one cluster kernel.  The levels from `first` to
-// the coarsest run inside one thread-block cluster: every stage of the
-// V-cycle (pre-smoothing + residual, restriction, dense coarse solve,
-// prolongation, post-smoothing) is spread over the cluster's threads and the
-// stages are separated by the hardware cluster barrier.  Vectors written in
-// the kernel are read through L2 (ld.global.cg) so no CTA sees a stale L1 line.
-constexpr int kMaxAmgLevels = 16;
-constexpr int kClusterThreads = 1024;
-
-template <typename T>
-struct LevelView {
-  const int32_t *Ap, *Ai, *Pp, *Pi, *Rp, *Ri;
-  const T *Av, *Pv, *Rv, *dinv;
-  T *b, *x, *xo, *r;
-  int n, nc;   // rows of this level and of the next one
-};
-
-template <typename T>
-struct CoarseArgs {
-  LevelView<T> lv[kMaxAmgLevels];
-  int first, last;         // last = index of the coarsest (dense) level
-  const T* cinv;
-};
-
-template <typename T>
-__device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
-
-// rows [0, n) of a CSR, one warp per row, over all warps of the cluster
-template <typename T, class F>
-__device__ __forceinline__ void cluster_rows(const int32_t* ptr, const int32_t* idx, const T* val,
-                                             int n, int gwarp, int nwarps, int lane, F&& body) {
-  for (int row = gwarp; row < n; row += nwarps) {
-    T s = 0;
-    const int e = __ldg(ptr + row + 1);
-    for (int t = __ldg(ptr + row) + lane; t < e; t += 32) s += __ldg(val + t) * body.x(__ldg(idx + t));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) body.store(row, s);
-  }
-}
-
-template <typename T>
-struct CPre {
-  const LevelView<T>& L;
-  __device__ T x(int j) const { return ldcg(L.b + j) * __ldg(L.dinv + j); }
-  __device__ void store(int i, T s) const {
-    const T bi = ldcg(L.b + i);
-    __stcg(L.x + i, bi * __ldg(L.dinv + i));
-    __stcg(L.r + i, bi - s);
-  }
-};
-template <typename T>
-struct CRestrict {
-  const LevelView<T>& L;
-  T* bc;
-  __device__ T x(int j) const { return ldcg(L.r + j); }
-  __device__ void store(int i, T s) const { __stcg(bc + i, s); }
-};
-template <typename T>
-struct CProlong {
-  const LevelView<T>& L;
-  const T* xc;
-  __device__ T x(int j) const { return ldcg(xc + j); }
-  __device__ void store(int i, T s) const { __stcg(L.x + i, ldcg(L.x + i) + s); }
-};
-template <typename T>
-struct CPost {
-  const LevelView<T>& L;
-  __device__ T x(int j) const { return ldcg(L.x + j); }
-  __device__ void store(int i, T s) const {
-    __stcg(L.xo + i, ldcg(L.x + i) + __ldg(L.dinv + i) * (ldcg(L.b + i) - s));
-  }
-};
-
-template <typename T>
-__global__ void __launch_bounds__(kClusterThreads) coarse_cycle_kernel(const CoarseArgs<T> a) {
-  namespace cg = cooperative_groups;
-  cg::cluster_group cl = cg::this_cluster();
-  const int lane = threadIdx.x & 31;
-  const int nwarps = (int)cl.num_blocks() * (kClusterThreads / 32);
-  const int gwarp = (int)cl.block_rank() * (kClusterThreads / 32) + (threadIdx.x >> 5);
-  for (int l = a.first; l < a.last; ++l) {
-    const LevelView<T>& L = a.lv[l];
-    cluster_rows(L.Ap, L.Ai, L.Av, L.n, gwarp, nwarps, lane, CPre<T>{L});
-    cl.sync();
-    cluster_rows(L.Rp, L.Ri, L.Rv, L.nc, gwarp, nwarps, lane, CRestrict<T>{L, a.lv[l + 1].b});
-    cl.sync();
-  }
-  {
-    const LevelView<T>& C = a.lv[a.last];
-    for (int row = gwarp; row < C.n; row += nwarps) {
-      T s = 0;
-      for (int j = lane; j < C.n; j += 32) s += __ldg(a.cinv + (int64_t)row * C.n + j) * ldcg(C.b + j);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) __stcg(C.xo + row, s);
-    }
-    cl.sync();
-  }
-  for (int l = a.last - 1; l >= a.first; --l) {
-    const LevelView<T>& L = a.lv[l];
-    cluster_rows(L.Pp, L.Pi, L.Pv, L.n, gwarp, nwarps, lane, CProlong<T>{L, a.lv[l + 1].xo});
-    cl.sync();
-    cluster_rows(L.Ap, L.Ai, L.Av, L.n, gwarp, nwarps, lane, CPost<T>{L});
-    cl.sync();
-  }
-}
-
-template <typename T>
-static void launch_coarse_cycle(const dg_precond& pc, int first, cudaStream_t s) {
-  CoarseArgs<T> a{};
-  const int L = (int)pc.levels.size();
-  a.first = first;
-  a.last = L - 1;
-  a.cinv = (const T*)pc.coarse_inv;
-  for (int l = first; l < L; ++l) {
-    const DevLevel& D = pc.levels[l];
-    LevelView<T>& v = a.lv[l];
-    v.Ap = D.A.ptr; v.Ai = D.A.idx; v.Av = (const T*)D.A.val;
-    v.Pp = D.P.ptr; v.Pi = D.P.idx; v.Pv = (const T*)D.P.val;
-    v.Rp = D.R.ptr; v.Ri = D.R.idx; v.Rv = (const T*)D.R.val;
-    v.dinv = (const T*)D.dinv;
-    v.b = (T*)D.b; v.x = (T*)D.x; v.xo = (T*)D.xo; v.r = (T*)D.r;
-    v.n = (int)D.n;
-    v.nc = (l + 1 < L) ? (int)pc.levels[l + 1].n : 0;
-  }
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3(pc.cluster_size, 1, 1);
-  cfg.blockDim = dim3(kClusterThreads, 1, 1);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = pc.cluster_size;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  DG_CUDA(cudaLaunchKernelEx(&cfg, coarse_cycle_kernel<T>, a));
-}
-
-// cluster size for the coarse-level kernel on the current device (16 if the
-// device can co-schedule it, else the portable 8, else 0 = not available)
-int coarse_cluster_size(int precision) {
-  for (int cs : {16, 8}) {
-    const void* fn = precision == DG_PREC_MIXED ? (const void*)coarse_cycle_kernel<float>
-                                                : (const void*)coarse_cycle_kernel<double>;
-    if (cs > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
-      cudaGetLastError();
-      continue;
-    }
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(cs, 1, 1);
-    cfg.blockDim = dim3(kClusterThreads, 1, 1);
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess && n > 0) return cs;
-    cudaGetLastError();
-  }
-  return 0;
-}
-
 int precond_final_blocks(const dg_precond& pc) {
   int64_t b = (pc.n_dofs * pc.P.group + kVecThreads - 1) / kVecThreads;
   if (b > kVecBlocks) b = kVecBlocks;
@@ -455,10 +285,6 @@ int precond_final_blocks(const dg_precond& pc) {
 
 template <typename T>
 static void vcycle(const dg_precond& pc, size_t l, cudaStream_t s) {
-  if (pc.cluster_first >= 0 && (int)l == pc.cluster_first) {
-    launch_coarse_cycle<T>(pc, (int)l, s);
-    return;
-  }
   const DevLevel& L = pc.levels[l];
   if (l + 1 == pc.levels.size()) {
     dense_mv_kernel<T><<<grid_for(L.n * 32), kVecThreads, 0, s>>>(

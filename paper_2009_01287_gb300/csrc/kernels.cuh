@@ -17,8 +17,6 @@ void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cuda
 // z = B r (FP64 or mixed); optional reduction of r . z
 void launch_precond(const dg_precond& pc, const double* r, double* z, Reduce red, cudaStream_t s);
 int precond_final_blocks(const dg_precond& pc);
-int coarse_cluster_size(int precision);
-constexpr int kClusterMaxRows = 2048;  // levels at most this size go to the cluster kernel
 
 // PCG scalar slots (doubles) and reduction tickets
 enum {
