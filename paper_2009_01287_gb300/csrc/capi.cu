@@ -9,6 +9,7 @@
 
 #include "kernels.cuh"
 #include "precond_setup.h"
+#include "union.h"
 
 namespace dg {
 
@@ -78,84 +79,28 @@ static void upload_csr(DevArena& a, const Csr& C, DevCsr& D, cudaStream_t s) {
 
 template <typename T>
 static void upload_precond(dg_precond* pc, HostPrecond& H, cudaStream_t s) {
-  DevArena& a = pc->arena;
-  upload_csr<T>(a, H.P, pc->P, s);
-  Csr PT = csr_transpose(H.P);
-  upload_csr<T>(a, PT, pc->PT, s);
-  pc->dinv = a.upload(std::vector<T>(H.dinv.begin(), H.dinv.end()), s);
-  const int64_t n = pc->n_dofs;
-  std::vector<int32_t> eb(n, -1), el(n, 0), dofs_off, dims, dofs;
-  std::vector<int64_t> inv_off;
-  std::vector<T> inv;
-  for (size_t b = 0; b < H.blocks.size(); ++b) {
-    const auto& blk = H.blocks[b];
-    dofs_off.push_back((int32_t)dofs.size());
-    dims.push_back((int32_t)blk.size());
-    inv_off.push_back((int64_t)inv.size());
-    for (size_t i = 0; i < blk.size(); ++i) {
-      eb[blk[i]] = (int32_t)b;
-      el[blk[i]] = (int32_t)i;
-      dofs.push_back((int32_t)blk[i]);
-    }
-    inv.insert(inv.end(), H.block_inv[b].begin(), H.block_inv[b].end());
-  }
-  pc->e_block = a.upload(eb, s);
-  pc->e_local = a.upload(el, s);
-  pc->blk_inv_off = a.upload(inv_off, s);
-  pc->blk_dofs_off = a.upload(dofs_off, s);
-  pc->blk_dim = a.upload(dims, s);
-  pc->blk_dofs = a.upload(dofs, s);
-  pc->blk_inv = a.upload(inv, s);
-  pc->zE = a.alloc<T>(dofs.size());
-  pc->n_blocks = (int64_t)H.blocks.size();
-  pc->max_block = 0;
-  for (auto& b : H.blocks) pc->max_block = std::max<int64_t>(pc->max_block, (int64_t)b.size());
-  DG_REQUIRE(pc->max_block * (int64_t)sizeof(T) <= 48 * 1024,
-             "a V_e block is too large for the block-solve kernel's shared memory");
-  DG_CUDA(cudaStreamCreateWithFlags(&pc->side, cudaStreamNonBlocking));
-  DG_CUDA(cudaEventCreateWithFlags(&pc->ev_fork, cudaEventDisableTiming));
-  DG_CUDA(cudaEventCreateWithFlags(&pc->ev_join, cudaEventDisableTiming));
-  pc->rc = a.alloc<T>(pc->n_c);
-  pc->ec = a.alloc<T>(pc->n_c);
-  if (pc->n_c > 0 && pc->lor == DG_LOR_EXACT) {
-    DG_REQUIRE(pc->n_c <= 8192, "exact LOR solve limited to 8192 conforming unknowns");
-    std::vector<double> dense((size_t)pc->n_c * pc->n_c, 0.0);
-    for (int64_t i = 0; i < H.Ac.rows; ++i)
-      for (int64_t t = H.Ac.ptr[i]; t < H.Ac.ptr[i + 1]; ++t) dense[i * pc->n_c + H.Ac.idx[t]] = H.Ac.val[t];
-    dense_inverse_spd((int)pc->n_c, dense);
-    pc->lor_inv = a.upload(std::vector<T>(dense.begin(), dense.end()), s);
-    pc->stats.n_levels = 1;
-    pc->stats.level_rows[0] = pc->n_c;
-    pc->stats.level_nnz[0] = H.Ac.nnz();
-  } else if (pc->n_c > 0) {
+  if (pc->lor == DG_LOR_AMG) {
     AmgHierarchy Hm = amg_setup(H.Ac);
-    pc->levels.resize(Hm.levels.size());
-    for (size_t l = 0; l < Hm.levels.size(); ++l) {
-      const AmgLevel& L = Hm.levels[l];
-      DevLevel& D = pc->levels[l];
-      D.n = L.A.rows;
-      upload_csr<T>(a, L.A, D.A, s);
-      if (l + 1 < Hm.levels.size()) {
-        upload_csr<T>(a, L.P, D.P, s);
-        upload_csr<T>(a, L.R, D.R, s);
-      }
-      std::vector<T> di(L.dl1.size());
-      for (size_t i = 0; i < di.size(); ++i) di[i] = (T)(1.0 / L.dl1[i]);
-      D.dinv = a.upload(di, s);
-      D.b = a.alloc<T>(D.n);
-      D.x = a.alloc<T>(D.n);
-      D.xo = a.alloc<T>(D.n);
-      D.r = a.alloc<T>(D.n);
-      if (l < 16) {
-        pc->stats.level_rows[l] = D.n;
-        pc->stats.level_nnz[l] = L.A.nnz();
-      }
-    }
-    pc->n_coarse = Hm.levels.back().A.rows;
-    DG_REQUIRE(Hm.levels.size() <= 16, "too many AMG levels");
-    pc->coarse_inv = a.upload(std::vector<T>(Hm.coarse_inv.begin(), Hm.coarse_inv.end()), s);
-    pc->stats.n_levels = (int)Hm.levels.size();
+    upload_union_precond<T>(pc, {InstSrc{&H, &Hm, 0}}, s);
+    return;
   }
+  // exact LOR solve: P, blocks and Jacobi as in the union form, dense inverse of A~_C
+  AmgHierarchy none;
+  none.levels.push_back({Csr{}, {}, {}, {}});
+  none.levels[0].A.rows = H.nC;
+  HostPrecond Hp = H;
+  upload_union_precond<T>(pc, {InstSrc{&Hp, &none, 0}}, s);
+  pc->levels.clear();
+  DevArena& a = pc->arena;
+  DG_REQUIRE(pc->n_c <= 8192, "exact LOR solve limited to 8192 conforming unknowns");
+  std::vector<double> dense((size_t)pc->n_c * pc->n_c, 0.0);
+  for (int64_t i = 0; i < H.Ac.rows; ++i)
+    for (int64_t t = H.Ac.ptr[i]; t < H.Ac.ptr[i + 1]; ++t) dense[i * pc->n_c + H.Ac.idx[t]] = H.Ac.val[t];
+  if (pc->n_c > 0) dense_inverse_spd((int)pc->n_c, dense);
+  pc->lor_inv = a.upload(std::vector<T>(dense.begin(), dense.end()), s);
+  pc->stats.n_levels = 1;
+  pc->stats.level_rows[0] = pc->n_c;
+  pc->stats.level_nnz[0] = H.Ac.nnz();
   DG_CUDA(cudaStreamSynchronize(s));
 }
 

@@ -50,7 +50,15 @@ inline int csr_group_for(double avg) {
 
 struct DevLevel {
   int64_t n = 0;
-  DevCsr A, P, R;      // P: from the next level to this one, R = P^T
+  int64_t n_cont = 0;  // rows [0, n_cont) continue to the next level (smoothed,
+                       // restricted); rows [n_cont, n) are coarsest levels of
+                       // their problem and are solved densely (blocks below)
+  DevCsr A, P, R;      // on the continuing rows; P: from the next level, R = P^T
+  int n_end = 0;                   // dense coarse blocks
+  int max_end = 0;                 // largest of them
+  int32_t* end_row = nullptr;      // n_end+1 row offsets (level numbering)
+  int64_t* end_inv_off = nullptr;  // offsets of the row-major inverses
+  void* end_inv = nullptr;
   void* dinv = nullptr;  // 1 / l1 diagonal
   void* b = nullptr;     // right-hand side of this level
   void* x = nullptr;     // after pre-smoothing and coarse correction
@@ -108,8 +116,6 @@ struct dg_precond {
   void* blk_inv = nullptr;   // row-major dense inverses
   void* lor_inv = nullptr;   // exact LOR solve: dense inverse n_c x n_c
   std::vector<dg::DevLevel> levels;  // AMG (level 0 = LOR matrix)
-  void* coarse_inv = nullptr;
-  int64_t n_coarse = 0;
   void* rc = nullptr;        // n_c restriction of r
   void* ec = nullptr;        // n_c LOR correction
   void* zE = nullptr;        // block-solve results, one per V_e node (block order)

@@ -283,20 +283,44 @@ int precond_final_blocks(const dg_precond& pc) {
   return (int)(b < 1 ? 1 : b);
 }
 
+// dense solves of the coarsest blocks of a level: block j covers level rows
+// [row[j], row[j+1]); blockIdx.y picks 8 rows of it (one per warp)
+template <typename T>
+__global__ void __launch_bounds__(256)
+dense_blocks_kernel(const int32_t* __restrict__ row, const int64_t* __restrict__ inv_off,
+                    const T* __restrict__ inv, const T* __restrict__ b, T* __restrict__ xo,
+                    int nblocks) {
+  const int lane = threadIdx.x & 31;
+  const int l = blockIdx.y * 8 + (threadIdx.x >> 5);
+  for (int j = blockIdx.x; j < nblocks; j += gridDim.x) {
+    const int r0 = __ldg(row + j);
+    const int d = __ldg(row + j + 1) - r0;
+    if (l >= d) continue;
+    const T* A = inv + __ldg(inv_off + j) + (int64_t)l * d;
+    T s = 0;
+    for (int m = lane; m < d; m += 32) s += __ldg(A + m) * __ldg(b + r0 + m);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) xo[r0 + l] = s;
+  }
+}
+
 template <typename T>
 static void vcycle(const dg_precond& pc, size_t l, cudaStream_t s) {
   const DevLevel& L = pc.levels[l];
-  if (l + 1 == pc.levels.size()) {
-    dense_mv_kernel<T><<<grid_for(L.n * 32), kVecThreads, 0, s>>>(
-        (const T*)pc.coarse_inv, (const T*)L.b, (T*)L.xo, L.n);
-    return;
+  if (L.n_cont > 0) {
+    const DevLevel& C = pc.levels[l + 1];
+    launch_rows<T>(L.A, OpPre<T>{(const T*)L.b, (const T*)L.dinv, (T*)L.x, (T*)L.r}, s);
+    launch_rows<T>(L.R, OpSpmv<T>{(const T*)L.r, (T*)C.b}, s);
+    vcycle<T>(pc, l + 1, s);
+    launch_rows<T>(L.P, OpProlong<T>{(const T*)C.xo, (T*)L.x}, s);
+    launch_rows<T>(L.A, OpPost<T>{(const T*)L.x, (const T*)L.b, (const T*)L.dinv, (T*)L.xo}, s);
   }
-  const DevLevel& C = pc.levels[l + 1];
-  launch_rows<T>(L.A, OpPre<T>{(const T*)L.b, (const T*)L.dinv, (T*)L.x, (T*)L.r}, s);
-  launch_rows<T>(L.R, OpSpmv<T>{(const T*)L.r, (T*)C.b}, s);
-  vcycle<T>(pc, l + 1, s);
-  launch_rows<T>(L.P, OpProlong<T>{(const T*)C.xo, (T*)L.x}, s);
-  launch_rows<T>(L.A, OpPost<T>{(const T*)L.x, (const T*)L.b, (const T*)L.dinv, (T*)L.xo}, s);
+  if (L.n_end > 0 && L.max_end > 0) {
+    const int gx = L.n_end < 8 * 152 ? L.n_end : 8 * 152;
+    dense_blocks_kernel<T><<<dim3(gx, (L.max_end + 7) / 8), 256, 0, s>>>(
+        L.end_row, L.end_inv_off, (const T*)L.end_inv, (const T*)L.b, (T*)L.xo, L.n_end);
+  }
 }
 
 template <typename T>

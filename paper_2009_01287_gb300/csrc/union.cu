@@ -1,0 +1,181 @@
+// Device images of one or many problems ("instances") side by side.
+//
+// A single solve is the one-instance case.  With several instances (the
+// batched solver) every operator is block diagonal: the meshes are concatenated
+// (element and DOF numbers shifted, sub-face neighbours and table offsets
+// remapped), and the preconditioner's pieces are concatenated per instance.
+// The AMG hierarchies of the instances are built independently (each exactly
+// as it would be alone) and stacked level by level: at level l the instances
+// that continue to level l+1 come first (their rows are smoothed and
+// restricted), the instances whose coarsest level is l follow and are solved
+// with their own dense inverse.  Each instance therefore sees exactly the
+// preconditioner it would have alone.
+#include <algorithm>
+#include <cstring>
+
+#include "kernels.cuh"
+#include "precond_setup.h"
+#include "union.h"
+
+namespace dg {
+
+namespace {
+
+void append_rows(Csr& out, const Csr& in, int64_t col_shift) {
+  if (out.ptr.empty()) out.ptr.push_back(0);
+  for (int64_t i = 0; i < in.rows; ++i) {
+    for (int64_t t = in.ptr[i]; t < in.ptr[i + 1]; ++t) {
+      out.idx.push_back((int32_t)(in.idx[t] + col_shift));
+      out.val.push_back(in.val[t]);
+    }
+    out.ptr.push_back((int64_t)out.idx.size());
+  }
+  out.rows += in.rows;
+}
+
+template <typename T>
+void upload_csr_t(DevArena& a, const Csr& C, DevCsr& D, cudaStream_t s) {
+  DG_REQUIRE(C.nnz() < (1LL << 31), "matrix too large for 32-bit indices");
+  std::vector<int32_t> ptr(C.ptr.begin(), C.ptr.end());
+  if (ptr.empty()) ptr.push_back(0);
+  std::vector<T> val(C.val.begin(), C.val.end());
+  D.rows = C.rows;
+  D.nnz = C.nnz();
+  D.group = csr_group_for(C.rows ? (double)C.nnz() / (double)C.rows : 1.0);
+  D.ptr = a.upload(ptr, s);
+  D.idx = a.upload(C.idx, s);
+  D.val = a.upload(val, s);
+}
+
+}  // namespace
+
+template <typename T>
+void upload_union_precond(dg_precond* pc, const std::vector<InstSrc>& inst, cudaStream_t s) {
+  DevArena& a = pc->arena;
+  const size_t ni = inst.size();
+  // ---- AMG level layout
+  size_t nlev = 0;
+  for (const auto& I : inst) nlev = std::max(nlev, I.A->levels.size());
+  DG_REQUIRE(nlev <= 16, "too many AMG levels");
+  // row offset of every instance at every level (-1: absent)
+  std::vector<std::vector<int64_t>> row_off(nlev, std::vector<int64_t>(ni, -1));
+  std::vector<std::vector<size_t>> order(nlev);   // level row order of instances
+  std::vector<int64_t> nrows(nlev, 0), ncont(nlev, 0);
+  for (size_t l = 0; l < nlev; ++l) {
+    for (int pass = 0; pass < 2; ++pass)
+      for (size_t i = 0; i < ni; ++i) {
+        const size_t L = inst[i].A->levels.size();
+        const bool cont = L > l + 1, end = L == l + 1;
+        if ((pass == 0 && cont) || (pass == 1 && end)) {
+          row_off[l][i] = nrows[l];
+          order[l].push_back(i);
+          nrows[l] += inst[i].A->levels[l].A.rows;
+          if (cont) ncont[l] = nrows[l];
+        }
+      }
+  }
+  // ---- DG-level pieces: P (columns = level-0 rows), D_J^-1, V_e blocks
+  Csr P;
+  std::vector<double> dinv;
+  std::vector<int32_t> eb, el, dofs_off, dims, dofs;
+  std::vector<int64_t> inv_off;
+  std::vector<T> inv;
+  int64_t nb = 0;
+  for (size_t i = 0; i < ni; ++i) {
+    const HostPrecond& H = *inst[i].H;
+    append_rows(P, H.P, nlev ? row_off[0][i] : 0);
+    dinv.insert(dinv.end(), H.dinv.begin(), H.dinv.end());
+    const size_t base = eb.size();
+    eb.resize(base + H.dinv.size(), -1);
+    el.resize(base + H.dinv.size(), 0);
+    for (size_t b = 0; b < H.blocks.size(); ++b) {
+      const auto& blk = H.blocks[b];
+      dofs_off.push_back((int32_t)dofs.size());
+      dims.push_back((int32_t)blk.size());
+      inv_off.push_back((int64_t)inv.size());
+      for (size_t j = 0; j < blk.size(); ++j) {
+        eb[base + blk[j]] = (int32_t)(nb + b);
+        el[base + blk[j]] = (int32_t)j;
+        dofs.push_back((int32_t)(inst[i].dof_off + blk[j]));
+      }
+      inv.insert(inv.end(), H.block_inv[b].begin(), H.block_inv[b].end());
+      pc->max_block = std::max<int64_t>(pc->max_block, (int64_t)blk.size());
+    }
+    nb += (int64_t)H.blocks.size();
+  }
+  P.cols = nlev ? nrows[0] : 0;
+  DG_REQUIRE((int64_t)dinv.size() == pc->n_dofs, "instance sizes do not add up");
+  upload_csr_t<T>(a, P, pc->P, s);
+  upload_csr_t<T>(a, csr_transpose(P), pc->PT, s);
+  pc->dinv = a.upload(std::vector<T>(dinv.begin(), dinv.end()), s);
+  pc->e_block = a.upload(eb, s);
+  pc->e_local = a.upload(el, s);
+  pc->blk_inv_off = a.upload(inv_off, s);
+  pc->blk_dofs_off = a.upload(dofs_off, s);
+  pc->blk_dim = a.upload(dims, s);
+  pc->blk_dofs = a.upload(dofs, s);
+  pc->blk_inv = a.upload(inv, s);
+  pc->zE = a.alloc<T>(dofs.size());
+  pc->n_blocks = nb;
+  DG_REQUIRE(pc->max_block * (int64_t)sizeof(T) <= 48 * 1024,
+             "a V_e block is too large for the block-solve kernel's shared memory");
+  pc->n_c = nlev ? nrows[0] : 0;
+  // ---- AMG levels
+  pc->levels.resize(nlev);
+  for (size_t l = 0; l < nlev; ++l) {
+    DevLevel& D = pc->levels[l];
+    D.n = nrows[l];
+    D.n_cont = ncont[l];
+    Csr A, R, Pl;
+    std::vector<T> di(nrows[l], (T)0);
+    std::vector<int32_t> end_row{(int32_t)ncont[l]};
+    std::vector<int64_t> end_off;
+    std::vector<T> end_inv;
+    int64_t nnz_all = 0;
+    for (size_t i : order[l]) {
+      const AmgLevel& L = inst[i].A->levels[l];
+      nnz_all += L.A.nnz();
+      if (row_off[l][i] < ncont[l]) {
+        append_rows(A, L.A, row_off[l][i]);
+        append_rows(Pl, L.P, row_off[l + 1][i]);
+        for (int64_t r = 0; r < L.A.rows; ++r) di[row_off[l][i] + r] = (T)(1.0 / L.dl1[r]);
+      } else {
+        end_off.push_back((int64_t)end_inv.size());
+        end_inv.insert(end_inv.end(), inst[i].A->coarse_inv.begin(), inst[i].A->coarse_inv.end());
+        end_row.push_back((int32_t)(row_off[l][i] + L.A.rows));
+        D.max_end = std::max<int>(D.max_end, (int)L.A.rows);
+      }
+    }
+    if (l + 1 < nlev)
+      for (size_t i : order[l + 1]) append_rows(R, inst[i].A->levels[l].R, row_off[l][i]);
+    A.cols = ncont[l];
+    Pl.cols = (l + 1 < nlev) ? nrows[l + 1] : 0;
+    R.cols = ncont[l];
+    upload_csr_t<T>(a, A, D.A, s);
+    upload_csr_t<T>(a, Pl, D.P, s);
+    upload_csr_t<T>(a, R, D.R, s);
+    D.dinv = a.upload(di, s);
+    D.n_end = (int)end_off.size();
+    D.end_row = a.upload(end_row, s);
+    D.end_inv_off = a.upload(end_off, s);
+    D.end_inv = a.upload(end_inv, s);
+    D.b = a.alloc<T>(D.n);
+    D.x = a.alloc<T>(D.n);
+    D.xo = a.alloc<T>(D.n);
+    D.r = a.alloc<T>(D.n);
+    pc->stats.level_rows[l] = D.n;
+    pc->stats.level_nnz[l] = nnz_all;
+  }
+  pc->stats.n_levels = (int)nlev;
+  DG_CUDA(cudaStreamCreateWithFlags(&pc->side, cudaStreamNonBlocking));
+  DG_CUDA(cudaEventCreateWithFlags(&pc->ev_fork, cudaEventDisableTiming));
+  DG_CUDA(cudaEventCreateWithFlags(&pc->ev_join, cudaEventDisableTiming));
+  pc->rc = a.alloc<T>(pc->n_c);
+  pc->ec = a.alloc<T>(pc->n_c);
+  DG_CUDA(cudaStreamSynchronize(s));
+}
+
+template void upload_union_precond<float>(dg_precond*, const std::vector<InstSrc>&, cudaStream_t);
+template void upload_union_precond<double>(dg_precond*, const std::vector<InstSrc>&, cudaStream_t);
+
+}  // namespace dg
