@@ -186,6 +186,32 @@ dg_status dg_pcg_solve_noalloc(const dg_mesh* mesh, const dg_precond* pc, const 
 dg_status dg_rhs_sine(const dg_mesh* mesh, int n_modes, const double* amps,
                       const int32_t* waves, double* b, void* stream);
 
+/* ---- Batched solver: many problems x several right-hand sides, one launch.
+ * Each (problem k, right-hand side r) pair is an instance, numbered
+ * k*n_rhs + r; the batch's vectors hold all instances one after another
+ * (offsets from dg_batch_offsets).  The problems are independent: the batch
+ * is one block-diagonal system whose PCG keeps alpha, beta and the stopping
+ * test per instance (Section 4.1's PCG for every instance), so every
+ * instance follows the iteration it would follow alone.  opts: form, eta,
+ * penalty_form, precision, smoother and remark_cases apply to every problem;
+ * the LOR solve is one AMG V-cycle; BR2 needs an explicit eta.  The host
+ * setup of the problems runs on all host threads. */
+typedef struct dg_batch dg_batch;
+dg_status dg_batch_create(const dg_mesh_desc* descs, int n_problems, int n_rhs,
+                          const dg_options* opts, void* stream, dg_batch** out);
+void dg_batch_destroy(dg_batch* batch);
+int64_t dg_batch_num_dofs(const dg_batch* batch);
+/* offsets: n_problems*n_rhs + 1 entries (host). */
+dg_status dg_batch_offsets(const dg_batch* batch, int64_t* offsets);
+/* Solve all instances from x0 = 0 to ||r_i|| <= rtol ||b_i|| (or maxit each).
+ * b, x: device, dg_batch_num_dofs doubles.  results: host array of
+ * n_problems*n_rhs entries (iters, rel_res, status per instance);
+ * solve_ms: device time of the whole batch.  One CUDA graph with a device
+ * while loop that runs until every instance has stopped; synchronous.
+ * Returns DG_ENOTCONV if any instance reached maxit. */
+dg_status dg_batch_solve(dg_batch* batch, const double* b, double* x, double rtol, int maxit,
+                         dg_solve_info* results, double* solve_ms, void* stream);
+
 /* Message of the last failure on this thread ("" if none). */
 const char* dg_last_error(void);
 

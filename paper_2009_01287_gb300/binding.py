@@ -30,6 +30,7 @@ ABI_SYMBOLS = (
     "dg_mesh_create", "dg_mesh_destroy", "dg_num_dofs", "dg_mesh_stats_get", "dg_apply", "dg_precond_setup",
     "dg_precond_destroy", "dg_precond_stats_get", "dg_precond_apply", "dg_pcg_solve",
     "dg_pcg_solve_host", "dg_pcg_solve_noalloc", "dg_rhs_sine", "dg_last_error",
+    "dg_batch_create", "dg_batch_destroy", "dg_batch_num_dofs", "dg_batch_offsets", "dg_batch_solve",
 )
 
 
@@ -92,8 +93,18 @@ def lib():
         L.dg_pcg_solve_noalloc.argtypes = [vp, vp, dp, dp, C.c_double, C.c_int, C.POINTER(DgSolveInfo), vp]
         L.dg_rhs_sine.argtypes = [vp, C.c_int, dp, dp, dp, vp]
         L.dg_last_error.restype = C.c_char_p
+        L.dg_batch_create.argtypes = [C.POINTER(DgMeshDesc), C.c_int, C.c_int, C.POINTER(DgOptions), vp,
+                                      C.POINTER(vp)]
+        L.dg_batch_destroy.argtypes = [vp]
+        L.dg_batch_destroy.restype = None
+        L.dg_batch_num_dofs.argtypes = [vp]
+        L.dg_batch_num_dofs.restype = i64
+        L.dg_batch_offsets.argtypes = [vp, vp]
+        L.dg_batch_solve.argtypes = [vp, dp, dp, C.c_double, C.c_int, C.POINTER(DgSolveInfo),
+                                     C.POINTER(C.c_double), vp]
         for name in ABI_SYMBOLS:
-            if name not in ("dg_mesh_destroy", "dg_precond_destroy", "dg_num_dofs", "dg_last_error"):
+            if name not in ("dg_mesh_destroy", "dg_precond_destroy", "dg_num_dofs", "dg_last_error",
+                            "dg_batch_destroy", "dg_batch_num_dofs"):
                 getattr(L, name).restype = st
         L.dg_mesh_destroy.restype = None
         L.dg_precond_destroy.restype = None
@@ -254,6 +265,48 @@ class Precond:
     def close(self):
         if self.h:
             dg_precond_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many problems x n_rhs right-hand sides solved by one graph launch."""
+
+    def __init__(self, meshes, n_rhs: int = 1, opts: Optional[DgOptions] = None, stream=None):
+        descs = (DgMeshDesc * len(meshes))()
+        self._keep = []
+        for i, m in enumerate(meshes):
+            d, keep = make_desc(m)
+            descs[i] = d
+            self._keep.append(keep)
+        self.n_problems = len(meshes)
+        self.n_rhs = n_rhs
+        self.n_inst = len(meshes) * n_rhs
+        o = opts or make_options(precision=DG_PREC_MIXED)
+        h = C.c_void_p()
+        _check(lib().dg_batch_create(descs, len(meshes), n_rhs, C.byref(o), _stream(stream), C.byref(h)))
+        self.h = h.value
+        self.n_dofs = int(lib().dg_batch_num_dofs(self.h))
+        off = np.zeros(self.n_inst + 1, dtype=np.int64)
+        _check(lib().dg_batch_offsets(self.h, off.ctypes.data))
+        self.offsets = off
+
+    def solve(self, b, x, rtol: float, maxit: int, stream=None, raise_on_notconv: bool = True):
+        res = (DgSolveInfo * self.n_inst)()
+        ms = C.c_double()
+        code = lib().dg_batch_solve(self.h, _ptr(b), _ptr(x), rtol, maxit, res, C.byref(ms), _stream(stream))
+        if code != DG_ENOTCONV or raise_on_notconv:
+            _check(code)
+        return list(res), ms.value
+
+    def close(self):
+        if self.h:
+            lib().dg_batch_destroy(self.h)
             self.h = 0
 
     def __del__(self):

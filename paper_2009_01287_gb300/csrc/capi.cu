@@ -36,6 +36,10 @@ static dg_status guarded(F&& f) {
 
 static void build_mesh(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opts, cudaStream_t s) {
   build_mesh_host(M, desc, opts);
+  upload_mesh(M, s);
+}
+
+void upload_mesh(dg_mesh* M, cudaStream_t s) {
   const HostMesh& m = M->host;
   apply_kernel_setup();
   // upload

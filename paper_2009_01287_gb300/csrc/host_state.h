@@ -137,6 +137,10 @@ struct dg_precond {
 namespace dg {
 // validate the description and build everything the device needs, on the host
 void build_mesh_host(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opts);
+// degree-sorted element order and operator tiles from M->host.p
+void build_tiles(dg_mesh* M);
+// upload the host-built operator data (M->host.p/off/sf_ptr, h_* arrays)
+void upload_mesh(dg_mesh* M, cudaStream_t s);
 // rows of element k of y = A x (x: full host vector), same formulation as the kernel
 void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double* y);
 }  // namespace dg

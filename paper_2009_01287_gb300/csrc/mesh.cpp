@@ -203,6 +203,25 @@ static int ilog2(int v) {
   return l;
 }
 
+void build_tiles(dg_mesh* M) {
+  // tiles of the operator kernel: degree-descending element order, runs of
+  // at most apply_epb(p) elements of one degree
+  const HostMesh& m = M->host;
+  std::vector<int32_t> order(m.n);
+  for (int64_t k = 0; k < m.n; ++k) order[k] = (int32_t)k;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return m.p[a] > m.p[b]; });
+  M->h_tiles.clear();
+  for (int64_t i = 0; i < m.n;) {
+    const int P = m.p[order[i]];
+    int64_t j = i;
+    while (j < m.n && m.p[order[j]] == P && j - i < apply_epb(P)) ++j;
+    M->h_tiles.push_back({P, (int32_t)i, (int32_t)(j - i), 0});
+    i = j;
+  }
+  M->n_tiles = (int)M->h_tiles.size();
+  M->h_order = order;
+}
+
 void build_mesh_host(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opts) {
   HostMesh& m = M->host;
   validate_and_copy(desc, m);
@@ -288,20 +307,7 @@ void build_mesh_host(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opt
     r.tab_on += base;
     r.tab_nn += base;
   }
-  // tiles: degree-descending element order
-  std::vector<int32_t> order(m.n);
-  for (int64_t k = 0; k < m.n; ++k) order[k] = (int32_t)k;
-  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return m.p[a] > m.p[b]; });
-  M->h_tiles.clear();
-  for (int64_t i = 0; i < m.n;) {
-    const int P = m.p[order[i]];
-    int64_t j = i;
-    while (j < m.n && m.p[order[j]] == P && j - i < apply_epb(P)) ++j;
-    M->h_tiles.push_back({P, (int32_t)i, (int32_t)(j - i), 0});
-    i = j;
-  }
-  M->n_tiles = (int)M->h_tiles.size();
-  M->h_order = order;
+  build_tiles(M);
   // operation and byte counts of one operator apply, as the kernel does it
   dg_mesh_stats& S = M->stats;
   S = dg_mesh_stats{};
