@@ -203,6 +203,10 @@ void dg_batch_destroy(dg_batch* batch);
 int64_t dg_batch_num_dofs(const dg_batch* batch);
 /* offsets: n_problems*n_rhs + 1 entries (host). */
 dg_status dg_batch_offsets(const dg_batch* batch, int64_t* offsets);
+/* Sine right-hand sides for every instance (as dg_rhs_sine): amps holds
+ * n_modes values per instance, waves 2*n_modes per instance; b: device. */
+dg_status dg_batch_rhs_sine(const dg_batch* batch, int n_modes, const double* amps,
+                            const int32_t* waves, double* b, void* stream);
 /* Solve all instances from x0 = 0 to ||r_i|| <= rtol ||b_i|| (or maxit each).
  * b, x: device, dg_batch_num_dofs doubles.  results: host array of
  * n_problems*n_rhs entries (iters, rel_res, status per instance);

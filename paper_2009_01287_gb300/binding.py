@@ -30,7 +30,8 @@ ABI_SYMBOLS = (
     "dg_mesh_create", "dg_mesh_destroy", "dg_num_dofs", "dg_mesh_stats_get", "dg_apply", "dg_precond_setup",
     "dg_precond_destroy", "dg_precond_stats_get", "dg_precond_apply", "dg_pcg_solve",
     "dg_pcg_solve_host", "dg_pcg_solve_noalloc", "dg_rhs_sine", "dg_last_error",
-    "dg_batch_create", "dg_batch_destroy", "dg_batch_num_dofs", "dg_batch_offsets", "dg_batch_solve",
+    "dg_batch_create", "dg_batch_destroy", "dg_batch_num_dofs", "dg_batch_offsets", "dg_batch_rhs_sine",
+    "dg_batch_solve",
 )
 
 
@@ -100,6 +101,7 @@ def lib():
         L.dg_batch_num_dofs.argtypes = [vp]
         L.dg_batch_num_dofs.restype = i64
         L.dg_batch_offsets.argtypes = [vp, vp]
+        L.dg_batch_rhs_sine.argtypes = [vp, C.c_int, dp, dp, dp, vp]
         L.dg_batch_solve.argtypes = [vp, dp, dp, C.c_double, C.c_int, C.POINTER(DgSolveInfo),
                                      C.POINTER(C.c_double), vp]
         for name in ABI_SYMBOLS:
@@ -295,6 +297,14 @@ class Batch:
         off = np.zeros(self.n_inst + 1, dtype=np.int64)
         _check(lib().dg_batch_offsets(self.h, off.ctypes.data))
         self.offsets = off
+
+    def rhs_sine(self, rhs_list, b, stream=None):
+        """rhs_list: one SineRHS per instance (same number of modes)."""
+        amps = np.ascontiguousarray(np.concatenate([r.amps for r in rhs_list]), dtype=np.float64)
+        waves = np.ascontiguousarray(np.concatenate([np.asarray(r.waves).ravel() for r in rhs_list]),
+                                     dtype=np.int32)
+        _check(lib().dg_batch_rhs_sine(self.h, len(rhs_list[0].amps), amps.ctypes.data, waves.ctypes.data,
+                                       _ptr(b), _stream(stream)))
 
     def solve(self, b, x, rtol: float, maxit: int, stream=None, raise_on_notconv: bool = True):
         res = (DgSolveInfo * self.n_inst)()

@@ -464,6 +464,30 @@ dg_status dg_batch_offsets(const dg_batch* b, int64_t* offsets) {
   return DG_OK;
 }
 
+dg_status dg_batch_rhs_sine(const dg_batch* B, int n_modes, const double* amps,
+                            const int32_t* waves, double* b, void* stream) {
+  try {
+    DG_REQUIRE(B && b && n_modes >= 0 && (n_modes == 0 || (amps && waves)), "bad argument");
+    std::vector<double> hb(B->U.n_dofs, 0.0);
+    std::vector<std::thread> pool;
+    const int nth = std::max(1, std::min<int>(B->n_inst, (int)std::thread::hardware_concurrency()));
+    for (int t = 0; t < nth; ++t)
+      pool.emplace_back([&, t] {
+        for (int i = t; i < B->n_inst; i += nth)
+          host_rhs_sine(*B->meshes[i / B->n_rhs], n_modes, amps + (size_t)i * n_modes,
+                        waves + (size_t)i * n_modes * 2, hb.data() + B->inst_off[i]);
+      });
+    for (auto& th : pool) th.join();
+    DG_CUDA(cudaMemcpyAsync(b, hb.data(), hb.size() * sizeof(double), cudaMemcpyHostToDevice,
+                            (cudaStream_t)stream));
+    DG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  }
+  return DG_OK;
+}
+
 dg_status dg_batch_solve(dg_batch* B, const double* b, double* x, double rtol, int maxit,
                          dg_solve_info* results, double* solve_ms, void* stream) {
   try {

@@ -67,6 +67,34 @@ void upload_mesh(dg_mesh* M, cudaStream_t s) {
 }
 
 
+// b_i = int f phi_i with a (p+3)-point Gauss rule per direction (host)
+void host_rhs_sine(const dg_mesh& mesh, int n_modes, const double* amps, const int32_t* waves,
+                   double* hb) {
+  const HostMesh& m = mesh.host;
+  for (int64_t k = 0; k < m.n; ++k) {
+    const int P = m.p[k], NP = P + 1;
+    const Basis1D& B = basis1d(P);
+    std::vector<double> gx, gw;
+    gauss_rule(P + 3, gx, gw);
+    const double h = mesh.h_h[k];
+    const double x0 = m.lo[2 * k] * m.lh, y0 = m.lo[2 * k + 1] * m.lh;
+    const int q = (int)gx.size();
+    std::vector<double> L((size_t)q * NP);
+    for (int g = 0; g < q; ++g) lagrange_eval(B.nodes, gx[g], &L[(size_t)g * NP]);
+    for (int gy = 0; gy < q; ++gy)
+      for (int gxi = 0; gxi < q; ++gxi) {
+        const double X = x0 + h * gx[gxi], Y = y0 + h * gx[gy];
+        double f = 0.0;
+        for (int md = 0; md < n_modes; ++md)
+          f += amps[md] * std::sin(M_PI * waves[2 * md] * X) * std::sin(M_PI * waves[2 * md + 1] * Y);
+        const double w = gw[gxi] * gw[gy] * h * h * f;
+        for (int iy = 0; iy < NP; ++iy)
+          for (int ix = 0; ix < NP; ++ix)
+            hb[m.off[k] + iy * NP + ix] += w * L[(size_t)gy * NP + iy] * L[(size_t)gxi * NP + ix];
+      }
+  }
+}
+
 // ----------------------------------------------------------------- precond upload
 template <typename T>
 static void upload_csr(DevArena& a, const Csr& C, DevCsr& D, cudaStream_t s) {
@@ -412,30 +440,8 @@ dg_status dg_rhs_sine(const dg_mesh* mesh, int n_modes, const double* amps, cons
                       double* b, void* stream) {
   return guarded([&] {
     DG_REQUIRE(mesh && b && n_modes >= 0 && (n_modes == 0 || (amps && waves)), "bad argument");
-    const HostMesh& m = mesh->host;
     std::vector<double> hb(mesh->n_dofs, 0.0);
-    for (int64_t k = 0; k < m.n; ++k) {
-      const int P = m.p[k], NP = P + 1;
-      const Basis1D& B = basis1d(P);
-      std::vector<double> gx, gw;
-      gauss_rule(P + 3, gx, gw);
-      const double h = mesh->h_h[k];
-      const double x0 = m.lo[2 * k] * m.lh, y0 = m.lo[2 * k + 1] * m.lh;
-      const int q = (int)gx.size();
-      std::vector<double> L((size_t)q * NP);
-      for (int g = 0; g < q; ++g) lagrange_eval(B.nodes, gx[g], &L[(size_t)g * NP]);
-      for (int gy = 0; gy < q; ++gy)
-        for (int gxi = 0; gxi < q; ++gxi) {
-          const double X = x0 + h * gx[gxi], Y = y0 + h * gx[gy];
-          double f = 0.0;
-          for (int md = 0; md < n_modes; ++md)
-            f += amps[md] * std::sin(M_PI * waves[2 * md] * X) * std::sin(M_PI * waves[2 * md + 1] * Y);
-          const double w = gw[gxi] * gw[gy] * h * h * f;
-          for (int iy = 0; iy < NP; ++iy)
-            for (int ix = 0; ix < NP; ++ix)
-              hb[m.off[k] + iy * NP + ix] += w * L[(size_t)gy * NP + iy] * L[(size_t)gxi * NP + ix];
-        }
-    }
+    host_rhs_sine(*mesh, n_modes, amps, waves, hb.data());
     DG_CUDA(cudaMemcpyAsync(b, hb.data(), hb.size() * sizeof(double), cudaMemcpyHostToDevice,
                             (cudaStream_t)stream));
     DG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));

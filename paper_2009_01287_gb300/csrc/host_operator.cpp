@@ -17,21 +17,30 @@ void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double*
   const double hk = M.h_h[k];
   const double* xk = x + m.off[k];
   auto sn = [](int s, int i, int q, int np) { return (s < 2) ? (i * np + q) : (q * np + i); };
-  // volume: (K (x) M + M (x) K) x  with local index iy*NP + ix
-  for (int iy = 0; iy < NP; ++iy)
-    for (int ix = 0; ix < NP; ++ix) {
-      double v = 0.0;
-      for (int qy = 0; qy < NP; ++qy)
+  // volume: (K (x) M + M (x) K) x  with local index iy*NP + ix, two passes
+  {
+    double t1[kMaxN * kMaxN], t2[kMaxN * kMaxN];
+    for (int qy = 0; qy < NP; ++qy)
+      for (int ix = 0; ix < NP; ++ix) {
+        double a = 0.0, b = 0.0;
         for (int qx = 0; qx < NP; ++qx) {
-          const double xv = xk[qy * NP + qx];
-          v += (B.K[ix * NP + qx] * B.M[iy * NP + qy] + B.M[ix * NP + qx] * B.K[iy * NP + qy]) * xv;
+          a += B.K[ix * NP + qx] * xk[qy * NP + qx];
+          b += B.M[ix * NP + qx] * xk[qy * NP + qx];
         }
-      y[iy * NP + ix] = v;
-    }
-  std::vector<double> dn(4 * NP), r(4 * NP, 0.0), c2(4 * NP, 0.0);
+        t1[qy * NP + ix] = a;
+        t2[qy * NP + ix] = b;
+      }
+    for (int iy = 0; iy < NP; ++iy)
+      for (int ix = 0; ix < NP; ++ix) {
+        double v = 0.0;
+        for (int qy = 0; qy < NP; ++qy) v += B.M[iy * NP + qy] * t1[qy * NP + ix] + B.K[iy * NP + qy] * t2[qy * NP + ix];
+        y[iy * NP + ix] = v;
+      }
+  }
+  double dn[4 * kMaxN], r[4 * kMaxN] = {0.0}, c2[4 * kMaxN] = {0.0};
   for (int s = 0; s < 4; ++s)
     for (int i = 0; i < NP; ++i) {
-      const std::vector<double>& dv = (s & 1) ? B.d1 : B.d0;
+      const double* dv = (s & 1) ? B.d1.data() : B.d0.data();
       double acc = 0.0;
       for (int q = 0; q < NP; ++q) acc += dv[q] * xk[sn(s, i, q, NP)];
       dn[s * NP + i] = ((s & 1) ? 1.0 : -1.0) / hk * acc;
@@ -41,14 +50,14 @@ void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double*
     const int kedge = (s & 1) ? P : 0;
     for (int j = m.sf_ptr[4 * k + s]; j < m.sf_ptr[4 * k + s + 1]; ++j) {
       const SubFaceRec& f = M.h_sf[j];
-      std::vector<double> un(kMaxN, 0.0), dnn(kMaxN, 0.0);
+      double un[kMaxN] = {0.0}, dnn[kMaxN] = {0.0};
       int np = 0;
       if (f.nb >= 0) {
         np = f.pn + 1;
         const Basis1D& Bn = basis1d(f.pn);
         const double* xn = x + m.off[f.nb];
         const int ke = (f.nb_side & 1) ? f.pn : 0;
-        const std::vector<double>& dv = (f.nb_side & 1) ? Bn.d1 : Bn.d0;
+        const double* dv = (f.nb_side & 1) ? Bn.d1.data() : Bn.d0.data();
         const double sg = ((f.nb_side & 1) ? -1.0 : 1.0) / M.h_h[f.nb];
         for (int q = 0; q < np; ++q) {
           un[q] = xn[sn(f.nb_side, q, ke, np)];
@@ -57,7 +66,7 @@ void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double*
           dnn[q] = sg * acc;
         }
       }
-      std::vector<double> jo(NP), cd(NP), jn(kMaxN, 0.0);
+      double jo[kMaxN], cd[kMaxN], jn[kMaxN] = {0.0};
       for (int i = 0; i < NP; ++i) {
         double a = 0.0, c = 0.0, b = 0.0, d = 0.0;
         for (int q = 0; q < NP; ++q) {
@@ -88,7 +97,7 @@ void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double*
           for (int t = 0; t < np; ++t) v -= T[f.tab_nn + q * np + t] * un[t];
           jn[q] = v * f.len;
         }
-        std::vector<double> go(NP), gn(kMaxN, 0.0);
+        double go[kMaxN], gn[kMaxN] = {0.0};
         for (int i = 0; i < NP; ++i) {
           double g = 0.0;
           for (int q = 0; q < NP; ++q) g += B.Minv[i * NP + q] * jo[q];
@@ -125,6 +134,62 @@ void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double*
     if (iy == 0) v += r[2 * NP + ix];
     if (iy == P) v += r[3 * NP + ix];
     y[node] = v;
+  }
+}
+
+// Diagonal of element k's rows, in closed form: the volume diagonal plus, for
+// every side holding the node, the sub-face terms of the node's own basis
+// function (its trace is l_i on that side, its outward normal derivative is
+// dv l_i, dv = l_edge'(edge) / h with the outward sign).
+void host_element_diag(const dg_mesh& M, int64_t k, double* d) {
+  const HostMesh& m = M.host;
+  const int P = m.p[k], NP = P + 1;
+  const Basis1D& B = basis1d(P);
+  const double hk = M.h_h[k];
+  const double* T = M.h_tables.data();
+  const bool br2 = M.opts.form == DG_FORM_BR2;
+  for (int iy = 0; iy < NP; ++iy)
+    for (int ix = 0; ix < NP; ++ix)
+      d[iy * NP + ix] = B.K[ix * NP + ix] * B.M[iy * NP + iy] + B.M[ix * NP + ix] * B.K[iy * NP + iy];
+  double go[kMaxN], gn[kMaxN], jo[kMaxN], jn[kMaxN];
+  for (int s = 0; s < 4; ++s) {
+    const double dv = ((s & 1) ? B.d1[P] : -B.d0[0]) / hk;
+    for (int i = 0; i < NP; ++i) {
+      const int node = (s < 2) ? (i * NP + ((s & 1) ? P : 0)) : (((s & 1) ? P : 0) * NP + i);
+      double add = 0.0;
+      for (int j = m.sf_ptr[4 * k + s]; j < m.sf_ptr[4 * k + s + 1]; ++j) {
+        const SubFaceRec& f = M.h_sf[j];
+        const double moo = T[f.tab_oo + i * NP + i];
+        const bool interior = f.nb >= 0;
+        if (!br2) {
+          add += f.len * moo * (f.sigma - (interior ? 1.0 : 2.0) * dv);
+          continue;
+        }
+        add -= (interior ? 1.0 : 2.0) * f.len * moo * dv;
+        for (int q = 0; q < NP; ++q) jo[q] = f.len * T[f.tab_oo + q * NP + i];
+        for (int a = 0; a < NP; ++a) {
+          double g = 0.0;
+          for (int q = 0; q < NP; ++q) g += B.Minv[a * NP + q] * jo[q];
+          go[a] = g * B.Minv[0] / (hk * hk);
+        }
+        double st = 0.0;
+        for (int a = 0; a < NP; ++a) st += T[f.tab_oo + i * NP + a] * go[a];
+        if (interior) {
+          const int np = f.pn + 1;
+          const Basis1D& Bn = basis1d(f.pn);
+          const double hn = M.h_h[f.nb];
+          for (int q = 0; q < np; ++q) jn[q] = f.len * T[f.tab_on + i * np + q];
+          for (int a = 0; a < np; ++a) {
+            double g = 0.0;
+            for (int q = 0; q < np; ++q) g += Bn.Minv[a * np + q] * jn[q];
+            gn[a] = g * Bn.Minv[0] / (hn * hn);
+          }
+          for (int a = 0; a < np; ++a) st += T[f.tab_on + i * np + a] * gn[a];
+        }
+        add += M.eta * (interior ? 0.25 : 1.0) * f.len * st;
+      }
+      d[node] += add;
+    }
   }
 }
 

@@ -143,4 +143,9 @@ void build_tiles(dg_mesh* M);
 void upload_mesh(dg_mesh* M, cudaStream_t s);
 // rows of element k of y = A x (x: full host vector), same formulation as the kernel
 void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double* y);
+// load vector of the sine right-hand side into hb (n_dofs doubles, zeroed)
+void host_rhs_sine(const dg_mesh& mesh, int n_modes, const double* amps, const int32_t* waves,
+                   double* hb);
+// diagonal of element k's rows of A (closed form of the same terms)
+void host_element_diag(const dg_mesh& M, int64_t k, double* d);
 }  // namespace dg

@@ -18,6 +18,9 @@
 #include <functional>
 #include <numeric>
 #include <unordered_map>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 
 #include "dg_internal.h"
 #include "host_state.h"
@@ -240,11 +243,22 @@ int64_t find_root(std::vector<int64_t>& parent, int64_t a) {
 HostPrecond build_host_precond(const dg_mesh& M, const dg_options& o) {
   const HostMesh& m = M.host;
   HostPrecond H;
+  const bool timing = std::getenv("DG_SETUP_TIMING") != nullptr;
+  auto t0 = std::chrono::steady_clock::now();
+  auto lap = [&](const char* what) {
+    if (!timing) return;
+    auto t1 = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "[setup] %-12s %8.3f s\n", what, std::chrono::duration<double>(t1 - t0).count());
+    t0 = t1;
+  };
   Builder B(M, o.remark_cases != 0);
   B.number();
+  lap("number");
   H.nC = B.nC;
   H.P = B.build_P();
+  lap("P");
   H.kind = B.classify();
+  lap("classify");
   if (o.smoother == DG_SMOOTHER_JACOBI_ONLY)
     for (auto& k : H.kind)
       if (k == 2) k = 1;
@@ -286,21 +300,21 @@ HostPrecond build_host_precond(const dg_mesh& M, const dg_options& o) {
     }
     H.blocks[it->second].push_back(r);
   }
+  lap("components");
   // ---- entries of A: diagonal on V_J and the V_e blocks, read off element rows
   H.dinv.assign(n, 0.0);
   std::vector<double> x(n, 0.0), y((kMaxN) * (kMaxN));
   for (int64_t k = 0; k < m.n; ++k) {
     const int P = m.p[k], NN = (P + 1) * (P + 1);
+    host_element_diag(M, k, y.data());
     for (int i = 0; i < NN; ++i) {
       const int64_t r = m.off[k] + i;
       if (H.kind[r] != 1) continue;
-      x[r] = 1.0;
-      host_element_residual(M, k, x.data(), y.data());
-      x[r] = 0.0;
       if (!(y[i] > 0.0)) throw Error(DG_EINVAL, "non-positive diagonal");
       H.dinv[r] = 1.0 / y[i];
     }
   }
+  lap("diagonal");
   auto elem_of = [&](int64_t r) {
     return (int64_t)(std::upper_bound(m.off.begin(), m.off.end(), r) - m.off.begin() - 1);
   };
@@ -314,7 +328,15 @@ HostPrecond build_host_precond(const dg_mesh& M, const dg_options& o) {
     uel.erase(std::unique(uel.begin(), uel.end()), uel.end());
     for (int b = 0; b < d; ++b) {
       x[blk[b]] = 1.0;
-      for (int64_t k : uel) {
+      const int64_t kb = el[b];
+      // rows that can see column b: its own element and the elements sharing a sub-face
+      std::vector<int64_t> near{kb};
+      for (int j = m.sf_ptr[4 * kb]; j < m.sf_ptr[4 * kb + 4]; ++j)
+        if (m.sf[j].nb >= 0) near.push_back(m.sf[j].nb);
+      std::sort(near.begin(), near.end());
+      near.erase(std::unique(near.begin(), near.end()), near.end());
+      for (int64_t k : near) {
+        if (!std::binary_search(uel.begin(), uel.end(), k)) continue;
         host_element_residual(M, k, x.data(), y.data());
         for (int a = 0; a < d; ++a)
           if (el[a] == k) Ab[(int64_t)a * d + b] = y[blk[a] - m.off[k]];
@@ -330,36 +352,45 @@ HostPrecond build_host_precond(const dg_mesh& M, const dg_options& o) {
     dense_inverse_spd(d, Ab);
     H.block_inv.push_back(std::move(Ab));
   }
-  // ---- LOR: Q1 stiffness on the Gauss-Lobatto sub-grid of each element,
-  // A~_C = P^T A~ P
+  lap("blocks");
+  // ---- LOR: Q1 stiffness on the Gauss-Lobatto sub-grid of each element
+  // (block diagonal A~ on the DG numbering), A~_C = P^T A~ P
   {
-    std::vector<int64_t> r;
-    std::vector<int32_t> c;
-    std::vector<double> v;
+    Csr At;
+    At.rows = At.cols = n;
+    At.ptr.assign(n + 1, 0);
     const double m1[2][2] = {{2.0 / 6.0, 1.0 / 6.0}, {1.0 / 6.0, 2.0 / 6.0}};
     const double k1[2][2] = {{1.0, -1.0}, {-1.0, 1.0}};
     for (int64_t k = 0; k < m.n; ++k) {
       const int P = m.p[k], NP = P + 1;
       const auto& g = basis1d(P).nodes;
-      for (int j = 0; j < P; ++j)
-        for (int i = 0; i < P; ++i) {
-          const double a = g[i + 1] - g[i], b = g[j + 1] - g[j];
-          int64_t loc[4] = {m.off[k] + j * NP + i, m.off[k] + j * NP + i + 1,
-                            m.off[k] + (j + 1) * NP + i, m.off[k] + (j + 1) * NP + i + 1};
-          for (int p = 0; p < 4; ++p)
-            for (int q = 0; q < 4; ++q) {
-              const int px = p & 1, py = p >> 1, qx = q & 1, qy = q >> 1;
-              const double kv = (b / a) * m1[py][qy] * k1[px][qx] + (a / b) * k1[py][qy] * m1[px][qx];
-              for (int64_t s = H.P.ptr[loc[p]]; s < H.P.ptr[loc[p] + 1]; ++s)
-                for (int64_t t = H.P.ptr[loc[q]]; t < H.P.ptr[loc[q] + 1]; ++t) {
-                  r.push_back(H.P.idx[s]);
-                  c.push_back(H.P.idx[t]);
-                  v.push_back(H.P.val[s] * kv * H.P.val[t]);
-                }
+      // local stencil: node (i, j) couples to (i+di, j+dj), |di|,|dj| <= 1
+      for (int j = 0; j < NP; ++j)
+        for (int i = 0; i < NP; ++i) {
+          double row[3][3] = {{0}};
+          for (int cj = j - 1; cj <= j; ++cj)
+            for (int ci = i - 1; ci <= i; ++ci) {
+              if (ci < 0 || cj < 0 || ci >= P || cj >= P) continue;
+              const double a = g[ci + 1] - g[ci], b = g[cj + 1] - g[cj];
+              const int px = i - ci, py = j - cj;   // this node's corner in the cell
+              for (int qy = 0; qy < 2; ++qy)
+                for (int qx = 0; qx < 2; ++qx)
+                  row[cj + qy - j + 1][ci + qx - i + 1] +=
+                      (b / a) * m1[py][qy] * k1[px][qx] + (a / b) * k1[py][qy] * m1[px][qx];
             }
+          for (int dj = 0; dj < 3; ++dj)
+            for (int di = 0; di < 3; ++di) {
+              const int ii = i + di - 1, jj = j + dj - 1;
+              if (ii < 0 || jj < 0 || ii > P || jj > P) continue;
+              At.idx.push_back((int32_t)(m.off[k] + jj * NP + ii));
+              At.val.push_back(row[dj][di]);
+            }
+          At.ptr[m.off[k] + j * NP + i + 1] = (int64_t)At.idx.size();
         }
     }
-    H.Ac = csr_from_triplets(H.nC, H.nC, r, c, v);
+    lap("lor-local");
+    H.Ac = csr_multiply(csr_transpose(H.P), csr_multiply(At, H.P));
+    lap("lor-spgemm");
   }
   return H;
 }
