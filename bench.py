@@ -175,8 +175,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     apply_ms = statistics.mean(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(napply))
     # end to end: host buffers in and out through the C ABI (pinned)
-    bh = b.cpu().numpy().copy()
-    xh = np.zeros(n)
+    bh = b.cpu().pin_memory()
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
     t_e2e, it_e2e = [], []
     for _ in range(args.steps):
         flush.fill_(3.0)
@@ -249,6 +249,141 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+SERVE_WORKLOAD = ("serving: {n} requests, Poisson arrivals {rate}/s, {m} distinct 2D hp-random meshes "
+                  "(DOFs log-uniform in [5k, 200k], prob 0.3, depth<=3, p~U{{1..6}}), seeded sine RHS per request, "
+                  "tol 1e-8, {slots} slots")
+
+
+def serve_meshes(m: int, seed: int = 0):
+    """m distinct meshes with DOF targets log-uniform in [5k, 200k]."""
+    import numpy as np
+    from paper_2009_01287_gb300 import inputs
+    rng = np.random.Generator(np.random.PCG64(777 + seed))
+    out = []
+    for j in range(m):
+        target = math.exp(rng.uniform(math.log(5e3), math.log(2e5)))
+        base = max(2, int(round(math.sqrt(target / 99.0))))
+        out.append(inputs.random_refined_mesh(2, base, 3, 0.3, 1, 6, seed=9000 + j))
+    return out
+
+
+def run_serving(args):
+    import torch
+
+    from paper_2009_01287_gb300 import binding as B
+    from paper_2009_01287_gb300 import serve
+
+    torch.cuda.set_device(0)
+    meshes = serve_meshes(args.serve_meshes)
+    reqs = serve.poisson_stream(args.serve_requests, args.serve_rate, meshes, seed=0)
+    # warm-up: resident state for every mesh (setup is reported, not timed as latency)
+    srv = serve.Server(slots=args.serve_slots, precision=B.DG_PREC_MIXED)
+    warm = [serve.Request(rid=10 ** 6 + j, arrival=0.0, mesh=m, rhs=reqs[0].rhs) for j, m in enumerate(meshes)]
+    t = time.perf_counter()
+    srv.run(warm, realtime=False)
+    setup_s = time.perf_counter() - t
+    clocks = ClockSampler(0)
+    clocks.start()
+    t = time.perf_counter()
+    res = srv.run(reqs, realtime=True)
+    wall = time.perf_counter() - t
+    clk = clocks.stop()
+    rep = serve.report(res, wall)
+    srv.close()
+    # sequential plain-FP64 loop over the same requests (one slot, FP64 preconditioner)
+    seq = serve.Server(slots=1, precision=B.DG_PREC_FP64)
+    seq.run(warm, realtime=False)
+    t = time.perf_counter()
+    res_seq = seq.run(reqs, realtime=True)
+    wall_seq = time.perf_counter() - t
+    rep_seq = serve.report(res_seq, wall_seq)
+    seq.close()
+    out = {
+        "metric": "p50/p99 solve latency and DOF-iters/s (continuous-batching server)",
+        "value": rep["dof_iters_per_s"],
+        "unit": "DOF-iters/s",
+        "n_gpus": 1,
+        "steps": 1,
+        "warmup": 1,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64 (outer PCG, operator) + f32 (preconditioner)",
+        "data": "synthetic",
+        "config": {"workload": SERVE_WORKLOAD.format(n=len(reqs), rate=args.serve_rate, m=len(meshes),
+                                                     slots=args.serve_slots)},
+        "p50_latency_s": rep["p50_latency_s"],
+        "p99_latency_s": rep["p99_latency_s"],
+        "ok": rep["ok"],
+        "wall_s": wall,
+        "max_inflight": srv.max_inflight,
+        "sequential_fp64": rep_seq,
+        "setup_s_all_meshes": setup_s,
+        "clocks": clk,
+    }
+    print(json.dumps(out))
+
+
+BATCH_WORKLOAD = ("batched: {n} 2D hp-random problems (base N log-uniform in [4,64], prob 0.3, depth<=3, "
+                  "p~U{{1..8}}, 1k-300k DOFs each) x {r} seeded sine RHS, SIPG eta=100, tol 1e-8, one graph launch")
+
+
+def run_batched(args):
+    """Batched workload: many uneven problems x several right-hand sides in
+    one graph launch (every instance keeps its own PCG scalars)."""
+    import torch
+
+    from paper_2009_01287_gb300 import binding as B
+    from paper_2009_01287_gb300 import inputs
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    meshes = [inputs.config3_problem(k)[0] for k in range(args.batch_problems)]
+    n_rhs = args.batch_rhs
+    prec = B.DG_PREC_FP64 if args.batch_fp64 else B.DG_PREC_MIXED
+    t0 = time.perf_counter()
+    bat = B.Batch(meshes, n_rhs=n_rhs, opts=B.make_options(precision=prec), stream=stream)
+    setup_s = time.perf_counter() - t0
+    b = torch.empty(bat.n_dofs, dtype=torch.float64, device=dev)
+    bat.rhs_sine([inputs.sine_rhs(2, 1000 + i) for i in range(bat.n_inst)], b, stream)
+    x = torch.empty_like(b)
+    for _ in range(args.warmup):
+        bat.solve(b, x, args.tol, 5000, stream)
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms, dofit, iters = [], 0, []
+    sizes = [int(bat.offsets[i + 1] - bat.offsets[i]) for i in range(bat.n_inst)]
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        res, t = bat.solve(b, x, args.tol, 5000, stream)
+        ms.append(t)
+        dofit += sum(n * r.iters for n, r in zip(sizes, res))
+        iters.append([r.iters for r in res])
+    clk = clocks.stop()
+    flat = [i for row in iters for i in row]
+    out = {
+        "metric": "DOF-iters/s (batched PCG, all instances in one graph launch)",
+        "value": dofit / (sum(ms) / 1e3),
+        "unit": "DOF-iters/s",
+        "n_gpus": 1,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": statistics.mean(ms),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64 (outer PCG, operator) + " + ("f64" if args.batch_fp64 else "f32") + " (preconditioner)",
+        "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD.format(n=len(meshes), r=n_rhs), "instances": bat.n_inst,
+                   "total_dofs": bat.n_dofs, "l2": "vectors exceed L2 (no flush)"},
+        "iters_min_median_max": [min(flat), statistics.median(flat), max(flat)],
+        "setup_s": setup_s,
+        "clocks": clk,
+    }
+    print(json.dumps(out))
+
+
 def _oracle_setup(seed: int):
     from oracle import rhs, solver
     from paper_2009_01287_gb300 import inputs
@@ -316,7 +451,21 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="hp2d", choices=["hp2d", "batched", "serving"])
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-meshes", type=int, default=16)
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--batch-problems", type=int, default=256)
+    ap.add_argument("--batch-rhs", type=int, default=4)
+    ap.add_argument("--batch-fp64", action="store_true")
     args = ap.parse_args()
+    if args.workload == "batched" and args.impl == "ours":
+        run_batched(args)
+        return
+    if args.workload == "serving" and args.impl == "ours":
+        run_serving(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -213,11 +213,17 @@ def dg_pcg_solve(mesh_h: int, pc_h: int, b, x, rtol: float, maxit: int, stream=N
     return info
 
 
-def dg_pcg_solve_host(mesh_h: int, pc_h: int, b: np.ndarray, x: np.ndarray, rtol: float, maxit: int,
-                      stream=None) -> DgSolveInfo:
-    assert b.dtype == np.float64 and x.dtype == np.float64 and b.flags.c_contiguous and x.flags.c_contiguous
+def _host_ptr(a) -> int:
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+        return a.ctypes.data
+    return _ptr(a)   # a CPU torch tensor (e.g. pinned) or a raw address
+
+
+def dg_pcg_solve_host(mesh_h: int, pc_h: int, b, x, rtol: float, maxit: int, stream=None) -> DgSolveInfo:
+    """b, x: host float64 buffers (numpy arrays, CPU tensors or addresses)."""
     info = DgSolveInfo()
-    _check(lib().dg_pcg_solve_host(mesh_h, pc_h, b.ctypes.data, x.ctypes.data, rtol, maxit,
+    _check(lib().dg_pcg_solve_host(mesh_h, pc_h, _host_ptr(b), _host_ptr(x), rtol, maxit,
                                    C.byref(info), _stream(stream)))
     return info
 
