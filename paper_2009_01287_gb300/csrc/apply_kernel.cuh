@@ -97,6 +97,8 @@ struct ApplyArgs {
   double* dot_partial;        // optional reduction of x . y (see Reduce)
   double* dot_out;
   unsigned* dot_ticket;
+  const double* skip;         // batch: tiles whose instance has skip[inst * skip_stride] != 0 are idle
+  int skip_stride;
   BasisOff boff[kMaxP + 1];
 };
 
@@ -121,6 +123,7 @@ template <int P>
 __device__ __forceinline__ void trace_tile(const ApplyArgs& A, const ApplyTile& T) {
   constexpr int NP = P + 1;
   const BasisOff bo = A.boff[P];
+  if (A.skip && A.skip[(int64_t)T.inst * A.skip_stride] != 0.0) return;
   const int ntask = T.count * 4 * NP;
   for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
     const int e = t / (4 * NP);
@@ -158,6 +161,7 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& 
   double* sgn = sjn + EPB * 4 * kMaxN;
 
   const int tid = threadIdx.x;
+  if (A.skip && A.skip[(int64_t)T.inst * A.skip_stride] != 0.0) return;   // CTA-uniform
   const int count = T.count;
   const int nnode = count * NN;           // volume / gather tasks
   const int nside = count * 4 * NP;       // face tasks

@@ -268,7 +268,27 @@ static void build_union_mesh(dg_batch* B, cudaStream_t s) {
   U.n_dofs = um.off.back();
   U.stats.n_dofs = U.n_dofs;
   DG_REQUIRE(U.n_dofs < (1LL << 31) && um.n < (1LL << 31), "batch too large for 32-bit indices");
-  build_tiles(&U);
+  // tiles never span two instances, so a converged instance's tiles can be skipped
+  std::vector<int32_t> order;
+  U.h_tiles.clear();
+  int64_t e0 = 0;
+  for (int i = 0; i < B->n_inst; ++i) {
+    const int64_t ne = B->meshes[i / B->n_rhs]->host.n;
+    std::vector<int32_t> loc(ne);
+    for (int64_t e = 0; e < ne; ++e) loc[e] = (int32_t)(e0 + e);
+    std::stable_sort(loc.begin(), loc.end(), [&](int32_t a, int32_t b) { return um.p[a] > um.p[b]; });
+    for (int64_t j = 0; j < ne;) {
+      const int P = um.p[loc[j]];
+      int64_t l = j;
+      while (l < ne && um.p[loc[l]] == P && l - j < apply_epb(P)) ++l;
+      U.h_tiles.push_back({P, (int32_t)(order.size() + j), (int32_t)(l - j), i});
+      j = l;
+    }
+    order.insert(order.end(), loc.begin(), loc.end());
+    e0 += ne;
+  }
+  U.h_order = order;
+  U.n_tiles = (int)U.h_tiles.size();
   upload_mesh(&U, s);
 }
 
@@ -440,6 +460,8 @@ dg_status dg_batch_create(const dg_mesh_desc* descs, int n_problems, int n_rhs,
     if (o.precision == DG_PREC_MIXED) upload_union_precond<float>(&B->UP, inst, s);
     else upload_union_precond<double>(&B->UP, inst, s);
     batch_alloc(B.get());
+    B->U.skip_status = B->sc + BS_STATUS;
+    B->U.skip_stride = BS_N;
   } catch (const Error& e) {
     set_last_error(e.what());
     return e.code;

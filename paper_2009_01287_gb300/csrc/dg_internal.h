@@ -80,7 +80,7 @@ struct ApplyTile {
   int32_t p;
   int32_t first;     // index into the degree-sorted element order
   int32_t count;
-  int32_t pad;
+  int32_t inst;      // batch instance of the tile's elements (0 for a single mesh)
 };
 
 // ------------------------------------------------------------------ mesh (host topology)

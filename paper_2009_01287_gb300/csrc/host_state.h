@@ -95,6 +95,9 @@ struct dg_mesh {
   int32_t* d_order = nullptr;
   dg::ApplyTile* d_tiles = nullptr;
   int n_tiles = 0;
+  // batch only: per-instance stop flags; tiles of stopped instances are skipped
+  const double* skip_status = nullptr;
+  int skip_stride = 0;
   ~dg_mesh() { arena.release(); }
 };
 

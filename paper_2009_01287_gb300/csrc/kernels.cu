@@ -68,6 +68,8 @@ ApplyArgs make_apply_args(const dg_mesh& M, const double* x, double* y, Reduce r
   A.dot_partial = red.partial;
   A.dot_out = red.out;
   A.dot_ticket = red.ticket;
+  A.skip = M.skip_status;
+  A.skip_stride = M.skip_stride;
   for (int p = 0; p <= kMaxP; ++p) A.boff[p] = M.boff[p];
   return A;
 }
