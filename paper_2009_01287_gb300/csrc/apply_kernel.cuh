@@ -107,9 +107,9 @@ struct ApplyShape {
   static constexpr int NP = P + 1;
   static constexpr int NN = NP * NP;
   static constexpr int EPB = apply_epb(P);
-  // shared doubles: M, K (2 NN) + x, T1, T2 (3 EPB NN) + r, c2, rn, c2n (16 EPB NP)
+  // shared doubles: M, K (2 NN) + x, T1, T2 (3 EPB NN) + r, c2 (8 EPB NP)
   // + BR2: jo, go, cd (12 EPB NP), jn, gn (8 EPB kMaxN)
-  static constexpr int SMEM = 2 * NN + 3 * EPB * NN + 16 * EPB * NP + 12 * EPB * NP + 8 * EPB * kMaxN;
+  static constexpr int SMEM = 2 * NN + 3 * EPB * NN + 8 * EPB * NP + 12 * EPB * NP + 8 * EPB * kMaxN;
 };
 
 __device__ __forceinline__ int side_node(int s, int i, int k, int np) {
@@ -144,8 +144,7 @@ __device__ __forceinline__ void trace_tile(const ApplyArgs& A, const ApplyTile& 
 }
 
 template <int P, bool BR2>
-__device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& T, double* sm,
-                                           double* red) {
+__device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& T, double* sm) {
   using S = ApplyShape<P>;
   constexpr int NP = S::NP, NN = S::NN, EPB = S::EPB;
   double* sM = sm;
@@ -155,9 +154,7 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& 
   double* sT2 = sT1 + EPB * NN;
   double* sr = sT2 + EPB * NN;           // [EPB][4][NP]
   double* sc2 = sr + EPB * 4 * NP;       // [EPB][4][NP]
-  double* srn = sc2 + EPB * 4 * NP;      // neighbour halves of r, c2
-  double* sc2n = srn + EPB * 4 * NP;
-  double* sjo = sc2n + EPB * 4 * NP;     // BR2 [EPB][4][NP]
+  double* sjo = sc2 + EPB * 4 * NP;      // BR2 [EPB][4][NP]
   double* sgo = sjo + EPB * 4 * NP;
   double* scd = sgo + EPB * 4 * NP;
   double* sjn = scd + EPB * 4 * NP;      // [EPB][4][kMaxN]
@@ -179,38 +176,29 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& 
     sx[t] = A.x[A.off[A.order[T.first + e]] + (t - e * NN)];
   }
   __syncthreads();
-  // ---- volume pass 1 (contract along x) and, for SIPG, the face terms.
-  // One task list spread evenly over the CTA: nnode volume tasks, then nside
-  // own-side face tasks, then nside neighbour-side face tasks.  The face
-  // residual is linear in the own projections (a, c) and in the neighbour's
-  // (b, d), so the two halves are computed by different threads into separate
-  // accumulators and summed in the gather.
-  const int ntask = nnode + (BR2 ? 0 : 2 * nside);
-  for (int t = tid; t < ntask; t += blockDim.x) {
-    if (t < nnode) {
-      const int e = t / NN, node = t - e * NN;
-      const int ix = node % NP, iy = node / NP;
-      const double* xr = sx + e * NN + iy * NP;
-      double t1 = 0.0, t2 = 0.0;
+  // ---- volume pass 1: contract along x
+  for (int t = tid; t < nnode; t += blockDim.x) {
+    const int e = t / NN, node = t - e * NN;
+    const int ix = node % NP, iy = node / NP;
+    const double* xr = sx + e * NN + iy * NP;
+    double t1 = 0.0, t2 = 0.0;
 #pragma unroll
-      for (int j = 0; j < NP; ++j) {
-        t1 = fma(sK[ix * NP + j], xr[j], t1);
-        t2 = fma(sM[ix * NP + j], xr[j], t2);
-      }
-      sT1[t] = t1;
-      sT2[t] = t2;
-      continue;
+    for (int j = 0; j < NP; ++j) {
+      t1 = fma(sK[ix * NP + j], xr[j], t1);
+      t2 = fma(sM[ix * NP + j], xr[j], t2);
     }
-    const int u = t - nnode;
-    const bool nbside = u >= nside;
-    const int ft = nbside ? u - nside : u;
-    const int e = ft / (4 * NP);
-    const int s = (ft / NP) & 3;
-    const int i = ft % NP;
-    const int k = A.order[T.first + e];
-    double r = 0.0, c2 = 0.0;
-    if (!nbside) {
+    sT1[t] = t1;
+    sT2[t] = t2;
+  }
+  // ---- faces (SIPG): one thread per side node walks the side's sub-faces
+  if (!BR2) {
+    for (int t = tid; t < nside; t += blockDim.x) {
+      const int e = t / (4 * NP);
+      const int s = (t / NP) & 3;
+      const int i = t % NP;
+      const int k = A.order[T.first + e];
       const double2* trk = reinterpret_cast<const double2*>(A.tr + A.toff[k]) + s * NP;
+      double r = 0.0, c2 = 0.0;
       for (int j = A.sf_ptr[4 * k + s]; j < A.sf_ptr[4 * k + s + 1]; ++j) {
         const SubFaceRec f = A.sf[j];
         const double* Moo = A.tab + f.tab_oo + i * NP;
@@ -222,41 +210,32 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& 
           a = fma(w, v.x, a);
           c = fma(w, v.y, c);
         }
-        // interior: sigma a - c/2 and -a/2; boundary: sigma a - c and -a
-        const double half = f.nb < 0 ? 1.0 : 0.5;
-        r = fma(f.len, fma(f.sigma, a, -half * c), r);
-        c2 = fma(-half * f.len, a, c2);
-      }
-      sr[ft] = r;
-      sc2[ft] = c2;
-    } else {
-      for (int j = A.sf_ptr[4 * k + s]; j < A.sf_ptr[4 * k + s + 1]; ++j) {
-        const SubFaceRec f = A.sf[j];
-        if (f.nb < 0) continue;
-        const int np = f.pn + 1;
-        const double* Mon = A.tab + f.tab_on + i * np;
-        const double2* trn = reinterpret_cast<const double2*>(A.tr + A.toff[f.nb]) + f.nb_side * np;
-        double b = 0.0, d = 0.0;
-        for (int m = 0; m < np; ++m) {
-          const double w = __ldg(Mon + m);
-          const double2 v = trn[m];
-          b = fma(w, v.x, b);
-          d = fma(w, v.y, d);   // neighbour's outward dn: this side's dn+ is -v.y
+        if (f.nb < 0) {
+          r += f.len * (f.sigma * a - c);
+          c2 -= f.len * a;
+        } else {
+          const int np = f.pn + 1;
+          const double* Mon = A.tab + f.tab_on + i * np;
+          const double2* trn = reinterpret_cast<const double2*>(A.tr + A.toff[f.nb]) + f.nb_side * np;
+          double b = 0.0, d = 0.0;
+          for (int m = 0; m < np; ++m) {
+            const double w = __ldg(Mon + m);
+            const double2 v = trn[m];
+            b = fma(w, v.x, b);
+            d = fma(w, v.y, d);   // neighbour's outward dn: this side's dn+ is -v.y
+          }
+          const double jmp = a - b;
+          r += f.len * (f.sigma * jmp - 0.5 * (c - d));
+          c2 -= 0.5 * f.len * jmp;
         }
-        // -sigma b + d/2 and +b/2
-        r = fma(f.len, fma(-f.sigma, b, 0.5 * d), r);
-        c2 = fma(0.5 * f.len, b, c2);
       }
-      srn[ft] = r;
-      sc2n[ft] = c2;
+      sr[t] = r;
+      sc2[t] = c2;
     }
-  }
-  if (BR2) {
+  } else {
     for (int t = tid; t < nside; t += blockDim.x) {
       sr[t] = 0.0;
       sc2[t] = 0.0;
-      srn[t] = 0.0;
-      sc2n[t] = 0.0;
     }
   }
   __syncthreads();
@@ -390,23 +369,22 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& 
     const double* d1 = A.tab + bo.d1;
     const double ih = A.ih[k];
     const double* c2 = sc2 + e * 4 * NP;
-    const double* c2n = sc2n + e * 4 * NP;
     const double* r = sr + e * 4 * NP;
-    const double* rn = srn + e * 4 * NP;
-    double g = -__ldg(d0 + ix) * (c2[0 * NP + iy] + c2n[0 * NP + iy]);
-    g = fma(__ldg(d1 + ix), c2[1 * NP + iy] + c2n[1 * NP + iy], g);
-    g = fma(-__ldg(d0 + iy), c2[2 * NP + ix] + c2n[2 * NP + ix], g);
-    g = fma(__ldg(d1 + iy), c2[3 * NP + ix] + c2n[3 * NP + ix], g);
+    double g = -__ldg(d0 + ix) * c2[0 * NP + iy];
+    g = fma(__ldg(d1 + ix), c2[1 * NP + iy], g);
+    g = fma(-__ldg(d0 + iy), c2[2 * NP + ix], g);
+    g = fma(__ldg(d1 + iy), c2[3 * NP + ix], g);
     y = fma(g, ih, y);
-    if (ix == 0) y += r[0 * NP + iy] + rn[0 * NP + iy];
-    if (ix == P) y += r[1 * NP + iy] + rn[1 * NP + iy];
-    if (iy == 0) y += r[2 * NP + ix] + rn[2 * NP + ix];
-    if (iy == P) y += r[3 * NP + ix] + rn[3 * NP + ix];
+    if (ix == 0) y += r[0 * NP + iy];
+    if (ix == P) y += r[1 * NP + iy];
+    if (iy == 0) y += r[2 * NP + ix];
+    if (iy == P) y += r[3 * NP + ix];
     A.y[A.off[k] + node] = y;
     part = fma(y, sx[t], part);
   }
   if (A.dot_partial) {
     // deterministic x . y over all tiles
+    __shared__ double red[kThreads];
     const double tot = block_sum<kThreads>(part, red);
     reduce_finalize<kThreads>(tot, Reduce{A.dot_partial, A.dot_out, A.dot_ticket}, red);
   }
