@@ -186,16 +186,10 @@ def run_ours(args):
         t_e2e.append(time.perf_counter() - t1)
         it_e2e.append(info.iters)
     clk = clocks.stop()
-    t32 = sum(ms32) / 1e3
-    t64 = sum(ms64) / 1e3
-    dof_iters32 = n * sum(it32)
-    if dist:
-        tt = torch.tensor([t32, t64, sum(t_e2e)], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t32, t64, te = (float(v) for v in tt)
-    else:
-        te = sum(t_e2e)
-    value = ws * dof_iters32 / t32
+    from paper_2009_01287_gb300 import replicas
+    (t32, t64, te), dof_iters32 = replicas.aggregate(
+        [sum(ms32) / 1e3, sum(ms64) / 1e3, sum(t_e2e)], n * sum(it32), device=dev)
+    value = dof_iters32 / t32
     stats = M.stats
     s32 = pc32.stats
     peaks, peak_kind = _peaks()
@@ -226,7 +220,7 @@ def run_ours(args):
         "iters_fp64": statistics.median(it64),
         "time_to_tol_ms_mixed": statistics.median(ms32),
         "time_to_tol_ms_fp64": statistics.median(ms64),
-        "dof_iters_per_s_fp64": ws * n * sum(it64) / t64,
+        "dof_iters_per_s_fp64": ws * n * sum(it64) / t64,   # replicas: identical per rank
         "setup_s": setup_s,
         "e2e": {"value": ws * n * sum(it_e2e) / te, "unit": "DOF-iters/s",
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},

@@ -144,7 +144,8 @@ __device__ __forceinline__ void trace_tile(const ApplyArgs& A, const ApplyTile& 
 }
 
 template <int P, bool BR2>
-__device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& T, double* sm) {
+__device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& T, double* sm,
+                                           double* red) {
   using S = ApplyShape<P>;
   constexpr int NP = S::NP, NN = S::NN, EPB = S::EPB;
   double* sM = sm;
@@ -384,7 +385,6 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& 
   }
   if (A.dot_partial) {
     // deterministic x . y over all tiles
-    __shared__ double red[kThreads];
     const double tot = block_sum<kThreads>(part, red);
     reduce_finalize<kThreads>(tot, Reduce{A.dot_partial, A.dot_out, A.dot_ticket}, red);
   }

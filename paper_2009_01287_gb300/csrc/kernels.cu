@@ -25,16 +25,17 @@ __global__ void __launch_bounds__(kThreads) trace_kernel(const ApplyArgs A) {
 template <bool BR2>
 __global__ void __launch_bounds__(kThreads) apply_kernel(const ApplyArgs A) {
   extern __shared__ double smem[];
+  __shared__ double red[kThreads];
   const ApplyTile T = A.tiles[blockIdx.x];
   switch (T.p) {
-    case 1: apply_tile<1, BR2>(A, T, smem); break;
-    case 2: apply_tile<2, BR2>(A, T, smem); break;
-    case 3: apply_tile<3, BR2>(A, T, smem); break;
-    case 4: apply_tile<4, BR2>(A, T, smem); break;
-    case 5: apply_tile<5, BR2>(A, T, smem); break;
-    case 6: apply_tile<6, BR2>(A, T, smem); break;
-    case 7: apply_tile<7, BR2>(A, T, smem); break;
-    case 8: apply_tile<8, BR2>(A, T, smem); break;
+    case 1: apply_tile<1, BR2>(A, T, smem, red); break;
+    case 2: apply_tile<2, BR2>(A, T, smem, red); break;
+    case 3: apply_tile<3, BR2>(A, T, smem, red); break;
+    case 4: apply_tile<4, BR2>(A, T, smem, red); break;
+    case 5: apply_tile<5, BR2>(A, T, smem, red); break;
+    case 6: apply_tile<6, BR2>(A, T, smem, red); break;
+    case 7: apply_tile<7, BR2>(A, T, smem, red); break;
+    case 8: apply_tile<8, BR2>(A, T, smem, red); break;
     default: break;
   }
 }
