@@ -99,6 +99,8 @@ struct ApplyArgs {
   unsigned* dot_ticket;
   const double* skip;         // batch: tiles whose instance has skip[inst * skip_stride] != 0 are idle
   int skip_stride;
+  int n_tiles;
+  unsigned* sched;            // [0] next tile, [1] exit ticket (both zero between launches)
   BasisOff boff[kMaxP + 1];
 };
 
@@ -144,8 +146,8 @@ __device__ __forceinline__ void trace_tile(const ApplyArgs& A, const ApplyTile& 
 }
 
 template <int P, bool BR2>
-__device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& T, double* sm,
-                                           double* red) {
+__device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& T, int tile,
+                                           double* sm, double* red) {
   using S = ApplyShape<P>;
   constexpr int NP = S::NP, NN = S::NN, EPB = S::EPB;
   double* sM = sm;
@@ -162,7 +164,10 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& 
   double* sgn = sjn + EPB * 4 * kMaxN;
 
   const int tid = threadIdx.x;
-  if (A.skip && A.skip[(int64_t)T.inst * A.skip_stride] != 0.0) return;   // CTA-uniform
+  if (A.skip && A.skip[(int64_t)T.inst * A.skip_stride] != 0.0) {   // CTA-uniform
+    if (A.dot_partial && tid == 0) A.dot_partial[tile] = 0.0;
+    return;
+  }
   const int count = T.count;
   const int nnode = count * NN;           // volume / gather tasks
   const int nside = count * 4 * NP;       // face tasks
@@ -384,9 +389,9 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& 
     part = fma(y, sx[t], part);
   }
   if (A.dot_partial) {
-    // deterministic x . y over all tiles
+    // tile partial of x . y (summed in tile order when the launch ends)
     const double tot = block_sum<kThreads>(part, red);
-    reduce_finalize<kThreads>(tot, Reduce{A.dot_partial, A.dot_out, A.dot_ticket}, red);
+    if (tid == 0) A.dot_partial[tile] = tot;
   }
 }
 

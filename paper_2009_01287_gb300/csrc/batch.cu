@@ -449,7 +449,6 @@ dg_status dg_batch_create(const dg_mesh_desc* descs, int n_problems, int n_rhs,
     for (int i = 0; i < B->n_inst; ++i)
       B->inst_off.push_back(B->inst_off.back() + B->meshes[i / n_rhs]->n_dofs);
     build_union_mesh(B.get(), s);
-    apply_kernel_setup();
     // union preconditioner
     B->UP.mesh = &B->U;
     B->UP.precision = o.precision;

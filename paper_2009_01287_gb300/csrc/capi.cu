@@ -41,7 +41,7 @@ static void build_mesh(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* o
 
 void upload_mesh(dg_mesh* M, cudaStream_t s) {
   const HostMesh& m = M->host;
-  apply_kernel_setup();
+  M->apply_grid = apply_kernel_setup(M->opts.form);
   // upload
   DevArena& a = M->arena;
   M->d_p = a.upload(m.p, s);
@@ -63,6 +63,8 @@ void upload_mesh(dg_mesh* M, cudaStream_t s) {
   M->d_tables = a.upload(M->h_tables, s);
   M->d_order = a.upload(M->h_order, s);
   M->d_tiles = a.upload(M->h_tiles, s);
+  M->d_sched = a.alloc<unsigned>(2);
+  DG_CUDA(cudaMemsetAsync(M->d_sched, 0, 2 * sizeof(unsigned), s));
   DG_CUDA(cudaStreamSynchronize(s));
 }
 

@@ -95,6 +95,8 @@ struct dg_mesh {
   int32_t* d_order = nullptr;
   dg::ApplyTile* d_tiles = nullptr;
   int n_tiles = 0;
+  unsigned* d_sched = nullptr;  // operator tile counter + exit ticket
+  int apply_grid = 1;           // resident CTAs of the persistent operator kernel
   // batch only: per-instance stop flags; tiles of stopped instances are skipped
   const double* skip_status = nullptr;
   int skip_stride = 0;

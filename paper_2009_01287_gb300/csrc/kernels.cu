@@ -22,21 +22,54 @@ __global__ void __launch_bounds__(kThreads) trace_kernel(const ApplyArgs A) {
   }
 }
 
+// Persistent operator kernel: a grid sized to the resident capacity takes
+// tiles from an atomic counter, heaviest first (tiles are degree-sorted), so
+// the uneven tiles balance across SMs.  The last CTA to leave resets the
+// counter and, when a dot product is requested, sums the tile partials in
+// tile order (deterministic whichever CTA ran which tile).
 template <bool BR2>
 __global__ void __launch_bounds__(kThreads) apply_kernel(const ApplyArgs A) {
   extern __shared__ double smem[];
   __shared__ double red[kThreads];
-  const ApplyTile T = A.tiles[blockIdx.x];
-  switch (T.p) {
-    case 1: apply_tile<1, BR2>(A, T, smem, red); break;
-    case 2: apply_tile<2, BR2>(A, T, smem, red); break;
-    case 3: apply_tile<3, BR2>(A, T, smem, red); break;
-    case 4: apply_tile<4, BR2>(A, T, smem, red); break;
-    case 5: apply_tile<5, BR2>(A, T, smem, red); break;
-    case 6: apply_tile<6, BR2>(A, T, smem, red); break;
-    case 7: apply_tile<7, BR2>(A, T, smem, red); break;
-    case 8: apply_tile<8, BR2>(A, T, smem, red); break;
-    default: break;
+  __shared__ int s_tile;
+  __shared__ unsigned s_last;
+  while (true) {
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(A.sched, 1u);
+    __syncthreads();
+    const int t = s_tile;
+    __syncthreads();
+    if (t >= A.n_tiles) break;
+    const ApplyTile T = A.tiles[t];
+    switch (T.p) {
+      case 1: apply_tile<1, BR2>(A, T, t, smem, red); break;
+      case 2: apply_tile<2, BR2>(A, T, t, smem, red); break;
+      case 3: apply_tile<3, BR2>(A, T, t, smem, red); break;
+      case 4: apply_tile<4, BR2>(A, T, t, smem, red); break;
+      case 5: apply_tile<5, BR2>(A, T, t, smem, red); break;
+      case 6: apply_tile<6, BR2>(A, T, t, smem, red); break;
+      case 7: apply_tile<7, BR2>(A, T, t, smem, red); break;
+      case 8: apply_tile<8, BR2>(A, T, t, smem, red); break;
+      default: break;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = (atomicAdd(A.sched + 1, 1u) == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    if (A.dot_partial) {
+      double v = 0.0;
+      for (int i = threadIdx.x; i < A.n_tiles; i += kThreads) v += __ldcg(A.dot_partial + i);
+      v = block_sum<kThreads>(v, red);
+      if (threadIdx.x == 0) *A.dot_out = v;
+    }
+    if (threadIdx.x == 0) {
+      A.sched[0] = 0u;
+      A.sched[1] = 0u;
+    }
   }
 }
 
@@ -71,15 +104,26 @@ ApplyArgs make_apply_args(const dg_mesh& M, const double* x, double* y, Reduce r
   A.dot_ticket = red.ticket;
   A.skip = M.skip_status;
   A.skip_stride = M.skip_stride;
+  A.n_tiles = M.n_tiles;
+  A.sched = M.d_sched;
   for (int p = 0; p <= kMaxP; ++p) A.boff[p] = M.boff[p];
   return A;
 }
 
-void apply_kernel_setup() {
-  // the shared-memory opt-in is per device: set it on the current one
+int apply_kernel_setup(int form) {
+  // the shared-memory opt-in is per device: set it on the current one, and
+  // return the resident capacity (CTAs) of the persistent operator kernel
   const int smem = apply_smem_bytes();
   DG_CUDA(cudaFuncSetAttribute(apply_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   DG_CUDA(cudaFuncSetAttribute(apply_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int dev = 0, sms = 0, per = 0;
+  DG_CUDA(cudaGetDevice(&dev));
+  DG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (form == DG_FORM_BR2)
+    DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, apply_kernel<true>, kThreads, smem));
+  else
+    DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, apply_kernel<false>, kThreads, smem));
+  return sms * (per > 0 ? per : 1);
 }
 
 void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cudaStream_t s) {
@@ -87,8 +131,9 @@ void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cuda
   const ApplyArgs A = make_apply_args(M, x, y, red);
   const int smem = apply_smem_bytes();
   trace_kernel<<<M.n_tiles, kThreads, 0, s>>>(A);
-  if (M.opts.form == DG_FORM_BR2) apply_kernel<true><<<M.n_tiles, kThreads, smem, s>>>(A);
-  else apply_kernel<false><<<M.n_tiles, kThreads, smem, s>>>(A);
+  const int grid = M.n_tiles < M.apply_grid ? M.n_tiles : M.apply_grid;
+  if (M.opts.form == DG_FORM_BR2) apply_kernel<true><<<grid, kThreads, smem, s>>>(A);
+  else apply_kernel<false><<<grid, kThreads, smem, s>>>(A);
   DG_CUDA(cudaGetLastError());
 }
 

@@ -9,7 +9,7 @@ namespace dg {
 constexpr int kVecThreads = 256;
 constexpr int kVecBlocks = 608;   // 4 x 152 SMs: fixed so reductions are deterministic
 
-void apply_kernel_setup();
+int apply_kernel_setup(int form);
 
 ApplyArgs make_apply_args(const dg_mesh& M, const double* x, double* y, Reduce red);
 void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cudaStream_t s);
