@@ -28,9 +28,38 @@
 // bit-reproducible.
 #pragma once
 
+#include <utility>
+
 #include "dg_internal.h"
 
 namespace dg {
+
+// Programmatic dependent launch: every kernel lets the next kernel in its
+// stream start launching at once, then waits until its own predecessor has
+// completed (with its memory visible) before touching any data.  Launch
+// latency of the next kernel thus overlaps this kernel's execution.  Without
+// the launch attribute both instructions are no-ops.
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// kernel launch with programmatic stream serialisation allowed
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                     Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  DG_CUDA(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...));
+}
 
 // A grid-wide deterministic dot product: each CTA writes its partial, the last
 // CTA to finish (atomic ticket) sums the partials in CTA order into *out and

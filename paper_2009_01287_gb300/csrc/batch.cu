@@ -47,6 +47,7 @@ __device__ __forceinline__ double inst_sum(const SegView& v, const double* part,
 __global__ void __launch_bounds__(kSegThreads)
 seg_dot_kernel(SegView v, const double* __restrict__ a, const double* __restrict__ b,
                double* __restrict__ part) {
+  pdl_entry();
   __shared__ double red[kSegThreads];
   for (int c = blockIdx.x; c < v.nchunks; c += gridDim.x) {
     double s = 0.0;
@@ -59,6 +60,7 @@ seg_dot_kernel(SegView v, const double* __restrict__ a, const double* __restrict
 __global__ void __launch_bounds__(kSegThreads)
 seg_init_kernel(SegView v, const double* __restrict__ b, double* __restrict__ x,
                 double* __restrict__ r, double* __restrict__ part) {
+  pdl_entry();
   __shared__ double red[kSegThreads];
   for (int c = blockIdx.x; c < v.nchunks; c += gridDim.x) {
     double s = 0.0;
@@ -77,6 +79,7 @@ seg_init_kernel(SegView v, const double* __restrict__ b, double* __restrict__ x,
 __global__ void __launch_bounds__(kSegThreads)
 seg_start_kernel(SegView v, const double* part_rz, const double* part_bb, double* sc,
                  unsigned* n_done) {
+  pdl_entry();
   __shared__ double red[kSegThreads];
   for (int i = blockIdx.x; i < v.ninst; i += gridDim.x) {
     const double rz = inst_sum(v, part_rz, i, red);
@@ -95,6 +98,7 @@ seg_start_kernel(SegView v, const double* part_rz, const double* part_bb, double
 
 __global__ void __launch_bounds__(kSegThreads)
 seg_copy_kernel(SegView v, const double* __restrict__ z, double* __restrict__ p) {
+  pdl_entry();
   for (int c = blockIdx.x; c < v.nchunks; c += gridDim.x)
     for (int64_t i = v.c_beg[c] + threadIdx.x; i < v.c_end[c]; i += kSegThreads) p[i] = z[i];
 }
@@ -103,6 +107,7 @@ __global__ void __launch_bounds__(kSegThreads)
 seg_update_xr_kernel(SegView v, double* __restrict__ x, double* __restrict__ r,
                      const double* __restrict__ p, const double* __restrict__ q, const double* sc,
                      const double* part_pq, double* part_rr) {
+  pdl_entry();
   __shared__ double red[kSegThreads];
   for (int c = blockIdx.x; c < v.nchunks; c += gridDim.x) {
     const int inst = v.c_inst[c];
@@ -131,6 +136,7 @@ seg_update_p_kernel(SegView v, double* __restrict__ p, const double* __restrict_
                     const double* part_rz, const double* part_rr, unsigned* inst_ticket,
                     unsigned* grid_ticket, unsigned* n_done, int maxit, double rtol2,
                     cudaGraphConditionalHandle h, int use_cond) {
+  pdl_entry();
   __shared__ double red[kSegThreads];
   __shared__ unsigned s_last;
   for (int c = blockIdx.x; c < v.nchunks; c += gridDim.x) {
@@ -338,12 +344,12 @@ static void batch_alloc(dg_batch* B) {
 static void batch_body(dg_batch* B, double* x, int maxit, double rtol2,
                        cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
   launch_apply(B->U, B->p, B->q, Reduce{}, s);
-  seg_dot_kernel<<<B->grid, kSegThreads, 0, s>>>(B->seg, B->p, B->q, B->part_pq);
-  seg_update_xr_kernel<<<B->grid, kSegThreads, 0, s>>>(B->seg, x, B->r, B->p, B->q, B->sc,
+  launch_k(seg_dot_kernel, B->grid, kSegThreads, 0, s, B->seg, B->p, B->q, B->part_pq);
+  launch_k(seg_update_xr_kernel, B->grid, kSegThreads, 0, s, B->seg, x, B->r, B->p, B->q, B->sc,
                                                         B->part_pq, B->part_rr);
   launch_precond(B->UP, B->r, B->z, Reduce{}, s);
-  seg_dot_kernel<<<B->grid, kSegThreads, 0, s>>>(B->seg, B->r, B->z, B->part_rz);
-  seg_update_p_kernel<<<B->grid, kSegThreads, 0, s>>>(B->seg, B->p, B->z, B->sc, B->part_rz,
+  launch_k(seg_dot_kernel, B->grid, kSegThreads, 0, s, B->seg, B->r, B->z, B->part_rz);
+  launch_k(seg_update_p_kernel, B->grid, kSegThreads, 0, s, B->seg, B->p, B->z, B->sc, B->part_rz,
                                                        B->part_rr, B->inst_ticket, B->grid_ticket,
                                                        B->n_done, maxit, rtol2, h, use_cond);
   DG_CUDA(cudaGetLastError());
@@ -519,12 +525,12 @@ dg_status dg_batch_solve(dg_batch* B, const double* b, double* x, double rtol, i
     const bool use_graph = batch_capture(B, x, maxit, rtol2);
     DG_CUDA(cudaEventRecord(B->e0, s));
     DG_CUDA(cudaMemsetAsync(B->n_done, 0, sizeof(unsigned), s));
-    seg_init_kernel<<<B->grid, kSegThreads, 0, s>>>(B->seg, b, x, B->r, B->part_bb);
+    launch_k(seg_init_kernel, B->grid, kSegThreads, 0, s, B->seg, b, x, B->r, B->part_bb);
     launch_precond(B->UP, B->r, B->z, Reduce{}, s);
-    seg_dot_kernel<<<B->grid, kSegThreads, 0, s>>>(B->seg, B->r, B->z, B->part_rz);
-    seg_start_kernel<<<std::max(1, std::min(B->n_inst, 8 * 152)), kSegThreads, 0, s>>>(
+    launch_k(seg_dot_kernel, B->grid, kSegThreads, 0, s, B->seg, B->r, B->z, B->part_rz);
+    launch_k(seg_start_kernel, std::max(1, std::min(B->n_inst, 8 * 152)), kSegThreads, 0, s, 
         B->seg, B->part_rz, B->part_bb, B->sc, B->n_done);
-    seg_copy_kernel<<<B->grid, kSegThreads, 0, s>>>(B->seg, B->z, B->p);
+    launch_k(seg_copy_kernel, B->grid, kSegThreads, 0, s, B->seg, B->z, B->p);
     DG_CUDA(cudaGetLastError());
     if (use_graph) {
       DG_CUDA(cudaGraphLaunch(B->exec, s));

@@ -8,6 +8,7 @@ namespace dg {
 
 // ============================================================== operator
 __global__ void __launch_bounds__(kThreads) trace_kernel(const ApplyArgs A) {
+  pdl_entry();
   const ApplyTile T = A.tiles[blockIdx.x];
   switch (T.p) {
     case 1: trace_tile<1>(A, T); break;
@@ -29,6 +30,7 @@ __global__ void __launch_bounds__(kThreads) trace_kernel(const ApplyArgs A) {
 // tile order (deterministic whichever CTA ran which tile).
 template <bool BR2>
 __global__ void __launch_bounds__(kThreads) apply_kernel(const ApplyArgs A) {
+  pdl_entry();
   extern __shared__ double smem[];
   __shared__ double red[kThreads];
   __shared__ int s_tile;
@@ -130,10 +132,10 @@ void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cuda
   if (M.n_tiles == 0) return;
   const ApplyArgs A = make_apply_args(M, x, y, red);
   const int smem = apply_smem_bytes();
-  trace_kernel<<<M.n_tiles, kThreads, 0, s>>>(A);
+  launch_k(trace_kernel, M.n_tiles, kThreads, 0, s, A);
   const int grid = M.n_tiles < M.apply_grid ? M.n_tiles : M.apply_grid;
-  if (M.opts.form == DG_FORM_BR2) apply_kernel<true><<<grid, kThreads, smem, s>>>(A);
-  else apply_kernel<false><<<grid, kThreads, smem, s>>>(A);
+  if (M.opts.form == DG_FORM_BR2) launch_k(apply_kernel<true>, grid, kThreads, smem, s, A);
+  else launch_k(apply_kernel<false>, grid, kThreads, smem, s, A);
   DG_CUDA(cudaGetLastError());
 }
 
@@ -154,6 +156,7 @@ template <typename T, int G, class Op>
 __global__ void __launch_bounds__(kVecThreads)
 csr_rows_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
                 const T* __restrict__ val, int64_t rows, Op op) {
+  pdl_entry();
   const int lane = threadIdx.x % G;
   const int64_t groups_per_grid = ((int64_t)gridDim.x * blockDim.x) / G;
   const int64_t g0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
@@ -225,12 +228,12 @@ static void launch_rows(const DevCsr& A, const Op& op, cudaStream_t s) {
   const int32_t* ix = A.idx;
   const T* v = (const T*)A.val;
   switch (A.group) {
-    case 1: csr_rows_kernel<T, 1, Op><<<(int)blocks, kVecThreads, 0, s>>>(p, ix, v, A.rows, op); break;
-    case 2: csr_rows_kernel<T, 2, Op><<<(int)blocks, kVecThreads, 0, s>>>(p, ix, v, A.rows, op); break;
-    case 4: csr_rows_kernel<T, 4, Op><<<(int)blocks, kVecThreads, 0, s>>>(p, ix, v, A.rows, op); break;
-    case 8: csr_rows_kernel<T, 8, Op><<<(int)blocks, kVecThreads, 0, s>>>(p, ix, v, A.rows, op); break;
-    case 16: csr_rows_kernel<T, 16, Op><<<(int)blocks, kVecThreads, 0, s>>>(p, ix, v, A.rows, op); break;
-    default: csr_rows_kernel<T, 32, Op><<<(int)blocks, kVecThreads, 0, s>>>(p, ix, v, A.rows, op); break;
+    case 1: launch_k(csr_rows_kernel<T, 1, Op>, (int)blocks, kVecThreads, 0, s, p, ix, v, A.rows, op); break;
+    case 2: launch_k(csr_rows_kernel<T, 2, Op>, (int)blocks, kVecThreads, 0, s, p, ix, v, A.rows, op); break;
+    case 4: launch_k(csr_rows_kernel<T, 4, Op>, (int)blocks, kVecThreads, 0, s, p, ix, v, A.rows, op); break;
+    case 8: launch_k(csr_rows_kernel<T, 8, Op>, (int)blocks, kVecThreads, 0, s, p, ix, v, A.rows, op); break;
+    case 16: launch_k(csr_rows_kernel<T, 16, Op>, (int)blocks, kVecThreads, 0, s, p, ix, v, A.rows, op); break;
+    default: launch_k(csr_rows_kernel<T, 32, Op>, (int)blocks, kVecThreads, 0, s, p, ix, v, A.rows, op); break;
   }
 }
 
@@ -238,6 +241,7 @@ static void launch_rows(const DevCsr& A, const Op& op, cudaStream_t s) {
 template <typename T>
 __global__ void dense_mv_kernel(const T* __restrict__ Ainv, const T* __restrict__ x,
                                 T* __restrict__ y, int64_t n) {
+  pdl_entry();
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; row < n; row += warps) {
@@ -259,6 +263,7 @@ block_solve_kernel(const int64_t* __restrict__ inv_off, const int32_t* __restric
                    const int32_t* __restrict__ dim, const int32_t* __restrict__ dofs,
                    const T* __restrict__ inv, const double* __restrict__ r, T* __restrict__ zE,
                    int nblocks) {
+  pdl_entry();
   extern __shared__ unsigned char smem_raw[];
   T* sr = reinterpret_cast<T*>(smem_raw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -289,6 +294,7 @@ precond_final_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict_
                      const int32_t* __restrict__ e_local, const int32_t* __restrict__ dofs_off,
                      const T* __restrict__ zE, const double* __restrict__ r,
                      double* __restrict__ z, int64_t n, Reduce red) {
+  pdl_entry();
   __shared__ double sred[kVecThreads];
   const int lane = threadIdx.x % G;
   const int64_t groups_per_grid = ((int64_t)gridDim.x * blockDim.x) / G;
@@ -338,6 +344,7 @@ __global__ void __launch_bounds__(256)
 dense_blocks_kernel(const int32_t* __restrict__ row, const int64_t* __restrict__ inv_off,
                     const T* __restrict__ inv, const T* __restrict__ b, T* __restrict__ xo,
                     int nblocks) {
+  pdl_entry();
   const int lane = threadIdx.x & 31;
   const int l = blockIdx.y * 8 + (threadIdx.x >> 5);
   for (int j = blockIdx.x; j < nblocks; j += gridDim.x) {
@@ -366,7 +373,7 @@ static void vcycle(const dg_precond& pc, size_t l, cudaStream_t s) {
   }
   if (L.n_end > 0 && L.max_end > 0) {
     const int gx = L.n_end < 8 * 152 ? L.n_end : 8 * 152;
-    dense_blocks_kernel<T><<<dim3(gx, (L.max_end + 7) / 8), 256, 0, s>>>(
+    launch_k(dense_blocks_kernel<T>, dim3(gx, (L.max_end + 7) / 8), 256, 0, s, 
         L.end_row, L.end_inv_off, (const T*)L.end_inv, (const T*)L.b, (T*)L.xo, L.n_end);
   }
 }
@@ -379,7 +386,7 @@ static void precond_impl(const dg_precond& pc, const double* r, double* z, Reduc
     DG_CUDA(cudaEventRecord(pc.ev_fork, s));
     DG_CUDA(cudaStreamWaitEvent(pc.side, pc.ev_fork, 0));
     int g = (int)(pc.n_blocks < 8 * 152 ? pc.n_blocks : 8 * 152);
-    block_solve_kernel<T><<<g, 128, (size_t)pc.max_block * sizeof(T), pc.side>>>(
+    launch_k(block_solve_kernel<T>, g, 128, (size_t)pc.max_block * sizeof(T), pc.side, 
         pc.blk_inv_off, pc.blk_dofs_off, pc.blk_dim, pc.blk_dofs, (const T*)pc.blk_inv, r,
         (T*)pc.zE, (int)pc.n_blocks);
     DG_CUDA(cudaGetLastError());
@@ -389,7 +396,7 @@ static void precond_impl(const dg_precond& pc, const double* r, double* z, Reduc
   if (pc.n_c > 0) {
     if (pc.lor == DG_LOR_EXACT) {
       launch_rows<T>(pc.PT, OpRestrict<T>{r, (T*)pc.rc}, s);
-      dense_mv_kernel<T><<<grid_for(pc.n_c * 32), kVecThreads, 0, s>>>(
+      launch_k(dense_mv_kernel<T>, grid_for(pc.n_c * 32), kVecThreads, 0, s, 
           (const T*)pc.lor_inv, (const T*)pc.rc, (T*)pc.ec, pc.n_c);
       ec = pc.ec;
     } else {
@@ -401,7 +408,7 @@ static void precond_impl(const dg_precond& pc, const double* r, double* z, Reduc
   if (pc.n_blocks > 0) DG_CUDA(cudaStreamWaitEvent(s, pc.ev_join, 0));
   const int nb = precond_final_blocks(pc);
 #define DG_FINAL(G)                                                                          \
-  precond_final_kernel<T, G><<<nb, kVecThreads, 0, s>>>(                                     \
+  launch_k(precond_final_kernel<T, G>, nb, kVecThreads, 0, s,                                      \
       pc.P.ptr, pc.P.idx, (const T*)pc.P.val, (const T*)ec, (const T*)pc.dinv, pc.e_block,   \
       pc.e_local, pc.blk_dofs_off, (const T*)pc.zE, r, z, pc.n_dofs, red)
   if (pc.P.group <= 1) DG_FINAL(1);
@@ -420,6 +427,7 @@ void launch_precond(const dg_precond& pc, const double* r, double* z, Reduce red
 __global__ void __launch_bounds__(kVecThreads)
 pcg_init_kernel(const double* __restrict__ b, double* __restrict__ x, double* __restrict__ r,
                 int64_t n, Reduce bb) {
+  pdl_entry();
   __shared__ double red[kVecThreads];
   double s = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -433,13 +441,14 @@ pcg_init_kernel(const double* __restrict__ b, double* __restrict__ x, double* __
 }
 
 void launch_pcg_init(const double* b, double* x, double* r, int64_t n, Reduce bb, cudaStream_t s) {
-  pcg_init_kernel<<<grid_for(n), kVecThreads, 0, s>>>(b, x, r, n, bb);
+  launch_k(pcg_init_kernel, grid_for(n), kVecThreads, 0, s, b, x, r, n, bb);
   DG_CUDA(cudaGetLastError());
 }
 
 // p = z and the initial scalars (rz from the preconditioner's reduction)
 __global__ void pcg_first_kernel(const double* __restrict__ z, double* __restrict__ p, int64_t n,
                                  double* sc) {
+  pdl_entry();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     p[i] = z[i];
@@ -452,13 +461,14 @@ __global__ void pcg_first_kernel(const double* __restrict__ z, double* __restric
 }
 
 void launch_pcg_first(const double* z, double* p, int64_t n, double* sc, cudaStream_t s) {
-  pcg_first_kernel<<<grid_for(n), kVecThreads, 0, s>>>(z, p, n, sc);
+  launch_k(pcg_first_kernel, grid_for(n), kVecThreads, 0, s, z, p, n, sc);
   DG_CUDA(cudaGetLastError());
 }
 
 __global__ void __launch_bounds__(kVecThreads)
 pcg_update_xr_kernel(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
                      const double* __restrict__ q, int64_t n, double* sc, Reduce rr) {
+  pdl_entry();
   __shared__ double red[kVecThreads];
   if (sc[SC_STATUS] != 0.0) return;  // converged or stopped: iterations queued after it are no-ops
   const double alpha = sc[SC_RZ] / sc[SC_PQ];
@@ -476,7 +486,7 @@ pcg_update_xr_kernel(double* __restrict__ x, double* __restrict__ r, const doubl
 
 void launch_pcg_update_xr(double* x, double* r, const double* p, const double* q, int64_t n,
                           double* sc, Reduce rr, cudaStream_t s) {
-  pcg_update_xr_kernel<<<grid_for(n), kVecThreads, 0, s>>>(x, r, p, q, n, sc, rr);
+  launch_k(pcg_update_xr_kernel, grid_for(n), kVecThreads, 0, s, x, r, p, q, n, sc, rr);
   DG_CUDA(cudaGetLastError());
 }
 
@@ -484,6 +494,7 @@ __global__ void __launch_bounds__(kVecThreads)
 pcg_update_p_kernel(double* __restrict__ p, const double* __restrict__ z, int64_t n, double* sc,
                     unsigned* ticket, int maxit, double rtol2, cudaGraphConditionalHandle h,
                     int use_cond) {
+  pdl_entry();
   __shared__ unsigned s_last;
   if (sc[SC_STATUS] != 0.0) {
     if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
@@ -517,7 +528,7 @@ pcg_update_p_kernel(double* __restrict__ p, const double* __restrict__ z, int64_
 void launch_pcg_update_p(double* p, const double* z, int64_t n, double* sc, unsigned* ticket,
                          int maxit, double rtol2, unsigned long long cond_handle, int use_cond,
                          cudaStream_t s) {
-  pcg_update_p_kernel<<<grid_for(n), kVecThreads, 0, s>>>(
+  launch_k(pcg_update_p_kernel, grid_for(n), kVecThreads, 0, s, 
       p, z, n, sc, ticket, maxit, rtol2, (cudaGraphConditionalHandle)cond_handle, use_cond);
   DG_CUDA(cudaGetLastError());
 }
