@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -247,20 +248,29 @@ static bool pcg_capture(const dg_mesh* M, const dg_precond* pc, PcgWork& w, doub
       if (cudaStreamBeginCaptureToGraph(w.cap, body, nullptr, nullptr, 0,
                                         cudaStreamCaptureModeRelaxed) == cudaSuccess) {
         bool launched = true;
+        std::string why;
         try {
           pcg_body(M, pc, w, x, maxit, rtol2, handle, 1, w.cap);
-        } catch (const Error&) {
+        } catch (const Error& e) {
           launched = false;
+          why = e.what();
         }
         cudaGraph_t out = nullptr;
-        if (cudaStreamEndCapture(w.cap, &out) == cudaSuccess && launched &&
-            cudaGraphInstantiate(&w.exec, w.graph, 0) == cudaSuccess)
-          ok = true;
+        const cudaError_t ec = cudaStreamEndCapture(w.cap, &out);
+        cudaError_t ei = cudaErrorUnknown;
+        if (ec == cudaSuccess && launched) ei = cudaGraphInstantiate(&w.exec, w.graph, 0);
+        ok = ec == cudaSuccess && launched && ei == cudaSuccess;
+        if (!ok && std::getenv("DG_VERBOSE"))
+          std::fprintf(stderr, "dg: capture: launch [%s] end-capture %s instantiate %s\n", why.c_str(),
+                       cudaGetErrorString(ec), cudaGetErrorString(ei));
       }
     }
   }
-  cudaGetLastError();
+  const cudaError_t cap_err = cudaGetLastError();
   if (!ok) {
+    if (std::getenv("DG_VERBOSE"))
+      std::fprintf(stderr, "dg: PCG graph capture failed (%s), using the host-driven loop\n",
+                   cudaGetErrorString(cap_err));
     w.drop_graph();
     w.graph_failed = true;
     return false;
