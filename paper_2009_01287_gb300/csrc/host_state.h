@@ -53,17 +53,14 @@ struct DevLevel {
   int64_t n_cont = 0;  // rows [0, n_cont) continue to the next level (smoothed,
                        // restricted); rows [n_cont, n) are coarsest levels of
                        // their problem and are solved densely (blocks below)
-  DevCsr A, P, R;      // on the continuing rows; P: from the next level, R = P^T
+  DevCsr Rpre, Sb, Sp;  // composite V-cycle operators on the continuing rows (see AmgLevel)
   int n_end = 0;                   // dense coarse blocks
   int max_end = 0;                 // largest of them
   int32_t* end_row = nullptr;      // n_end+1 row offsets (level numbering)
   int64_t* end_inv_off = nullptr;  // offsets of the row-major inverses
   void* end_inv = nullptr;
-  void* dinv = nullptr;  // 1 / l1 diagonal
   void* b = nullptr;     // right-hand side of this level
-  void* x = nullptr;     // after pre-smoothing and coarse correction
-  void* xo = nullptr;    // after post-smoothing (the level's output)
-  void* r = nullptr;     // residual after pre-smoothing
+  void* xo = nullptr;    // the level's output (after post-smoothing)
 };
 
 }  // namespace dg

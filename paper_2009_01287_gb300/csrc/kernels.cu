@@ -188,36 +188,6 @@ struct OpRestrict {  // out = P^T r, r in FP64
   __device__ T x(int j) const { return (T)__ldg(r + j); }
   __device__ void store(int64_t i, T s) const { out[i] = s; }
 };
-template <typename T>
-struct OpPre {  // x = b d ; r = b - A (b d)
-  const T* b;
-  const T* dinv;
-  T* xo;
-  T* r;
-  __device__ T x(int j) const { return __ldg(b + j) * __ldg(dinv + j); }
-  __device__ void store(int64_t i, T s) const {
-    const T bi = b[i];
-    xo[i] = bi * dinv[i];
-    r[i] = bi - s;
-  }
-};
-template <typename T>
-struct OpProlong {  // x += P xc
-  const T* xc;
-  T* xo;
-  __device__ T x(int j) const { return __ldg(xc + j); }
-  __device__ void store(int64_t i, T s) const { xo[i] += s; }
-};
-template <typename T>
-struct OpPost {  // xo = x + d (b - A x)
-  const T* xin;
-  const T* b;
-  const T* dinv;
-  T* xo;
-  __device__ T x(int j) const { return __ldg(xin + j); }
-  __device__ void store(int64_t i, T s) const { xo[i] = xin[i] + dinv[i] * (b[i] - s); }
-};
-
 template <typename T, class Op>
 static void launch_rows(const DevCsr& A, const Op& op, cudaStream_t s) {
   if (A.rows == 0) return;
@@ -337,6 +307,50 @@ int precond_final_blocks(const dg_precond& pc) {
   return (int)(b < 1 ? 1 : b);
 }
 
+// fused up-sweep of one AMG level: xo = Sb b + Sp xc (G lanes per row share
+// both rows; fixed shuffle tree)
+template <typename T, int G>
+__global__ void __launch_bounds__(kVecThreads)
+amg_up_kernel(const int32_t* __restrict__ bp, const int32_t* __restrict__ bi, const T* __restrict__ bv,
+              const int32_t* __restrict__ pp, const int32_t* __restrict__ pi, const T* __restrict__ pv,
+              const T* __restrict__ b, const T* __restrict__ xc, T* __restrict__ xo, int64_t rows) {
+  pdl_entry();
+  const int lane = threadIdx.x % G;
+  const int64_t groups_per_grid = ((int64_t)gridDim.x * blockDim.x) / G;
+  const int64_t g0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+  const int64_t rounds = (rows + groups_per_grid - 1) / groups_per_grid;
+  for (int64_t rd = 0; rd < rounds; ++rd) {
+    const int64_t row = g0 + rd * groups_per_grid;
+    T s = 0;
+    if (row < rows) {
+      for (int t = bp[row] + lane; t < bp[row + 1]; t += G) s += __ldg(bv + t) * __ldg(b + __ldg(bi + t));
+      for (int t = pp[row] + lane; t < pp[row + 1]; t += G) s += __ldg(pv + t) * __ldg(xc + __ldg(pi + t));
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, G);
+    if (row < rows && lane == 0) xo[row] = s;
+  }
+}
+
+template <typename T>
+static void launch_up(const DevLevel& L, const T* b, const T* xc, T* xo, cudaStream_t s) {
+  if (L.n_cont == 0) return;
+  int64_t blocks = (L.n_cont * (int64_t)L.Sb.group + kVecThreads - 1) / kVecThreads;
+  if (blocks > 8 * 152) blocks = 8 * 152;
+#define DG_UP(G)                                                                                  \
+  launch_k(amg_up_kernel<T, G>, (int)blocks, kVecThreads, 0, s, L.Sb.ptr, L.Sb.idx,              \
+           (const T*)L.Sb.val, L.Sp.ptr, L.Sp.idx, (const T*)L.Sp.val, b, xc, xo, L.n_cont)
+  switch (L.Sb.group) {
+    case 1: DG_UP(1); break;
+    case 2: DG_UP(2); break;
+    case 4: DG_UP(4); break;
+    case 8: DG_UP(8); break;
+    case 16: DG_UP(16); break;
+    default: DG_UP(32); break;
+  }
+#undef DG_UP
+}
+
 // dense solves of the coarsest blocks of a level: block j covers level rows
 // [row[j], row[j+1]); blockIdx.y picks 8 rows of it (one per warp)
 template <typename T>
@@ -365,11 +379,9 @@ static void vcycle(const dg_precond& pc, size_t l, cudaStream_t s) {
   const DevLevel& L = pc.levels[l];
   if (L.n_cont > 0) {
     const DevLevel& C = pc.levels[l + 1];
-    launch_rows<T>(L.A, OpPre<T>{(const T*)L.b, (const T*)L.dinv, (T*)L.x, (T*)L.r}, s);
-    launch_rows<T>(L.R, OpSpmv<T>{(const T*)L.r, (T*)C.b}, s);
+    launch_rows<T>(L.Rpre, OpSpmv<T>{(const T*)L.b, (T*)C.b}, s);   // restrict b - A D^-1 b
     vcycle<T>(pc, l + 1, s);
-    launch_rows<T>(L.P, OpProlong<T>{(const T*)C.xo, (T*)L.x}, s);
-    launch_rows<T>(L.A, OpPost<T>{(const T*)L.x, (const T*)L.b, (const T*)L.dinv, (T*)L.xo}, s);
+    launch_up<T>(L, (const T*)L.b, (const T*)C.xo, (T*)L.xo, s);    // correction + smoothing
   }
   if (L.n_end > 0 && L.max_end > 0) {
     const int gx = L.n_end < 8 * 152 ? L.n_end : 8 * 152;

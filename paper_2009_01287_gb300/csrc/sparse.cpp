@@ -238,6 +238,24 @@ AmgHierarchy amg_setup(const Csr& A0) {
     next.dl1 = l1_diag(next.A);
     H.levels.push_back(std::move(next));
   }
+  // composite operators of every level that continues
+  for (size_t l = 0; l + 1 < H.levels.size(); ++l) {
+    AmgLevel& L = H.levels[l];
+    const Csr& A = L.A;
+    const std::vector<double>& d = L.dl1;
+    Csr M1 = A, M2 = A, Sb = A;   // I - A D^-1, I - D^-1 A, 2 D^-1 - D^-1 A D^-1
+    for (int64_t i = 0; i < A.rows; ++i)
+      for (int64_t t = A.ptr[i]; t < A.ptr[i + 1]; ++t) {
+        const int32_t j = A.idx[t];
+        const double a = A.val[t];
+        M1.val[t] = (i == j ? 1.0 : 0.0) - a / d[j];
+        M2.val[t] = (i == j ? 1.0 : 0.0) - a / d[i];
+        Sb.val[t] = (i == j ? 2.0 / d[i] : 0.0) - a / (d[i] * d[j]);
+      }
+    L.Rpre = csr_multiply(L.R, M1);
+    L.Sp = csr_multiply(M2, L.P);
+    L.Sb = std::move(Sb);
+  }
   const Csr& C = H.levels.back().A;
   const int nc = (int)C.rows;
   H.coarse_inv.assign((int64_t)nc * nc, 0.0);

@@ -26,6 +26,12 @@ struct AmgLevel {
   Csr A;
   std::vector<double> dl1;   // l1-Jacobi diagonal sum_j |a_ij|
   Csr P, R;                  // prolongator to this level from the next, R = P^T
+  // The V-cycle of this level rewritten with composite operators (D = diag(dl1)):
+  //   b_next = Rpre b,           Rpre = R (I - A D^-1)
+  //   x_out  = Sb b + Sp x_next, Sb = 2 D^-1 - D^-1 A D^-1, Sp = (I - D^-1 A) P
+  // which is pre-smoothing x = D^-1 b, restriction of b - A x, coarse
+  // correction x += P x_next and post-smoothing x += D^-1 (b - A x) exactly.
+  Csr Rpre, Sb, Sp;
 };
 struct AmgHierarchy {
   std::vector<AmgLevel> levels;

@@ -126,8 +126,7 @@ void upload_union_precond(dg_precond* pc, const std::vector<InstSrc>& inst, cuda
     DevLevel& D = pc->levels[l];
     D.n = nrows[l];
     D.n_cont = ncont[l];
-    Csr A, R, Pl;
-    std::vector<T> di(nrows[l], (T)0);
+    Csr Sb, Sp, Rp;
     std::vector<int32_t> end_row{(int32_t)ncont[l]};
     std::vector<int64_t> end_off;
     std::vector<T> end_inv;
@@ -136,9 +135,8 @@ void upload_union_precond(dg_precond* pc, const std::vector<InstSrc>& inst, cuda
       const AmgLevel& L = inst[i].A->levels[l];
       nnz_all += L.A.nnz();
       if (row_off[l][i] < ncont[l]) {
-        append_rows(A, L.A, row_off[l][i]);
-        append_rows(Pl, L.P, row_off[l + 1][i]);
-        for (int64_t r = 0; r < L.A.rows; ++r) di[row_off[l][i] + r] = (T)(1.0 / L.dl1[r]);
+        append_rows(Sb, L.Sb, row_off[l][i]);
+        append_rows(Sp, L.Sp, row_off[l + 1][i]);
       } else {
         end_off.push_back((int64_t)end_inv.size());
         end_inv.insert(end_inv.end(), inst[i].A->coarse_inv.begin(), inst[i].A->coarse_inv.end());
@@ -147,22 +145,21 @@ void upload_union_precond(dg_precond* pc, const std::vector<InstSrc>& inst, cuda
       }
     }
     if (l + 1 < nlev)
-      for (size_t i : order[l + 1]) append_rows(R, inst[i].A->levels[l].R, row_off[l][i]);
-    A.cols = ncont[l];
-    Pl.cols = (l + 1 < nlev) ? nrows[l + 1] : 0;
-    R.cols = ncont[l];
-    upload_csr_t<T>(a, A, D.A, s);
-    upload_csr_t<T>(a, Pl, D.P, s);
-    upload_csr_t<T>(a, R, D.R, s);
-    D.dinv = a.upload(di, s);
+      for (size_t i : order[l + 1]) append_rows(Rp, inst[i].A->levels[l].Rpre, row_off[l][i]);
+    Sb.cols = ncont[l];
+    Sp.cols = (l + 1 < nlev) ? nrows[l + 1] : 0;
+    Rp.cols = ncont[l];
+    upload_csr_t<T>(a, Sb, D.Sb, s);
+    upload_csr_t<T>(a, Sp, D.Sp, s);
+    upload_csr_t<T>(a, Rp, D.Rpre, s);
+    // lanes per row of the fused up-sweep: both operators' rows together
+    D.Sb.group = csr_group_for(ncont[l] ? (double)(Sb.nnz() + Sp.nnz()) / (double)ncont[l] : 1.0);
     D.n_end = (int)end_off.size();
     D.end_row = a.upload(end_row, s);
     D.end_inv_off = a.upload(end_off, s);
     D.end_inv = a.upload(end_inv, s);
     D.b = a.alloc<T>(D.n);
-    D.x = a.alloc<T>(D.n);
     D.xo = a.alloc<T>(D.n);
-    D.r = a.alloc<T>(D.n);
     pc->stats.level_rows[l] = D.n;
     pc->stats.level_nnz[l] = nnz_all;
   }
