@@ -254,7 +254,7 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& 
         } else {
           const int np = f.pn + 1;
           const double* Mon = A.tab + f.tab_on + i * np;
-          const double2* trn = reinterpret_cast<const double2*>(A.tr + f.tr_nb);
+          const double2* trn = reinterpret_cast<const double2*>(A.tr + A.toff[f.nb]) + f.nb_side * np;
           double b = 0.0, d = 0.0;
           for (int m = 0; m < np; ++m) {
             const double w = __ldg(Mon + m);

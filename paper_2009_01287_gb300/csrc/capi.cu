@@ -58,8 +58,6 @@ void upload_mesh(dg_mesh* M, cudaStream_t s) {
     M->d_ih = a.upload(ih, s);
     M->d_toff = a.upload(toff, s);
     M->d_tr = a.alloc<double>(toff[m.n]);
-    for (auto& r : M->h_sf)
-      r.tr_nb = r.nb >= 0 ? toff[r.nb] + 2 * (int64_t)r.nb_side * (r.pn + 1) : 0;
   }
   M->d_sf_ptr = a.upload(m.sf_ptr, s);
   M->d_sf = a.upload(M->h_sf, s);

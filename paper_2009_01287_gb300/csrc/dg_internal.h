@@ -68,7 +68,6 @@ struct SubFaceRec {
   int32_t tab_nn;    // offset of neighbour-neighbour face mass ((pn+1)^2)
   double sigma;      // SIPG penalty
   double len;        // physical length of the sub-face
-  int64_t tr_nb;     // offset of the neighbour side's traces in the trace buffer
 };
 
 // Offsets of the degree-p 1D matrices inside the device table buffer.
