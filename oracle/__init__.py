@@ -9,7 +9,8 @@ definitions, and runs PCG with them.
 Modules
     basis      Gauss-Lobatto / Gauss-Legendre rules and Lagrange polynomials
     topology   faces, sub-faces, hanging vertices and master edges of a 2D mesh
-    dg         SIPG and BR2 matrices (Section 2, Eq. fe-problem; Section 4.4)
+    topology3  sub-faces of a 3D mesh of cubes
+    dg         SIPG and BR2 matrices, 2D and 3D (Section 2, Eq. fe-problem; Section 4.4)
     space      conforming prolongation P, V_J / V_e classification (Section 3)
     lor        low-order-refined matrices (Section 3.4)
     amg        the deterministic smoothed-aggregation V-cycle used for LOR

@@ -1,12 +1,14 @@
-"""Explicit assembly of the 2D DG stiffness matrix (Section 2, Eq. fe-problem;
-BR2 form of Section 4.4).
+"""Explicit assembly of the DG stiffness matrix (Section 2, Eq. fe-problem;
+BR2 form of Section 4.4), on squares (2D) or cubes (3D).
 
-Global numbering: element-major, element k owns (p_k+1)^2 consecutive DOFs;
-inside an element the nodal DOF (ix, iy) has local index iy*(p+1) + ix, with
-the Gauss-Lobatto nodes of Section 2.2 in each direction.
+Global numbering: element-major, element k owns (p_k+1)^d consecutive DOFs;
+inside an element the nodal DOF (ix, iy[, iz]) has local index
+ix + (p+1) iy [+ (p+1)^2 iz], with the Gauss-Lobatto nodes of Section 2.2 in
+each direction.
 
-Quadrature (exact on axis-aligned squares): Gauss-Legendre with p+1 points per
-direction for the volume, max(p-, p+)+1 points on every sub-face.
+Quadrature (exact on axis-aligned boxes): Gauss-Legendre with p+1 points per
+direction for the volume, max(p-, p+)+1 points per tangential direction on
+every sub-face.
 
 Sign convention: the paper writes Laplace(u) = f; this oracle solves
 -Laplace(u) = f so that the matrix is SPD (the two differ by f -> -f).
@@ -36,9 +38,10 @@ from .topology import Topology
 class DGSpace:
     def __init__(self, topo: Topology, lattice_h: float):
         self.topo = topo
+        self.dim = int(getattr(topo, "dim", 2))
         self.lh = float(lattice_h)
         p = topo.p
-        self.ndof_elem = (p + 1) ** 2
+        self.ndof_elem = (p + 1) ** self.dim
         self.offset = np.zeros(topo.n + 1, dtype=np.int64)
         self.offset[1:] = np.cumsum(self.ndof_elem)
         self.n = int(self.offset[-1])
@@ -50,9 +53,14 @@ class DGSpace:
         return self.topo.lo[k].astype(np.float64) * self.lh
 
     def node_coords(self, k: int) -> np.ndarray:
-        """Physical coordinates of the (p+1)^2 nodes, local order."""
+        """Physical coordinates of the (p+1)^d nodes, local order."""
         p = int(self.topo.p[k])
         g = basis.gll_nodes(p)
+        if self.dim == 3:
+            Z, Y, X = np.meshgrid(g, g, g, indexing="ij")   # iz outer, ix inner
+            o = self.origin(k)
+            h = self.h(k)
+            return np.stack([o[0] + h * X.ravel(), o[1] + h * Y.ravel(), o[2] + h * Z.ravel()], axis=1)
         X, Y = np.meshgrid(g, g)          # Y varies along rows -> iy outer
         o = self.origin(k)
         h = self.h(k)
@@ -64,6 +72,17 @@ class DGSpace:
         g = basis.gll_nodes(p)
         h = self.h(k)
         o = self.origin(k)
+        if self.dim == 3:
+            l = [basis.lagrange(g, (pts[:, d] - o[d]) / h) for d in range(3)]
+            dl = [basis.lagrange_deriv(g, (pts[:, d] - o[d]) / h) for d in range(3)]
+            m = len(pts)
+
+            def prod(fx, fy, fz):   # local index iz*(p+1)^2 + iy*(p+1) + ix
+                return (fz[:, :, None, None] * fy[:, None, :, None] * fx[:, None, None, :]).reshape(m, -1)
+            val = prod(l[0], l[1], l[2])
+            grad = np.stack([prod(dl[0], l[1], l[2]) / h, prod(l[0], dl[1], l[2]) / h,
+                             prod(l[0], l[1], dl[2]) / h], axis=2)
+            return val, grad
         xi = (pts[:, 0] - o[0]) / h
         et = (pts[:, 1] - o[1]) / h
         lx, ly = basis.lagrange(g, xi), basis.lagrange(g, et)
@@ -76,6 +95,13 @@ class DGSpace:
 
     def volume_quadrature(self, k: int, q: int) -> Tuple[np.ndarray, np.ndarray]:
         x, w = basis.gauss(q)
+        if self.dim == 3:
+            Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+            W = np.einsum("a,b,c->abc", w, w, w).ravel()
+            o = self.origin(k)
+            h = self.h(k)
+            pts = np.stack([o[0] + h * X.ravel(), o[1] + h * Y.ravel(), o[2] + h * Z.ravel()], axis=1)
+            return pts, W * h ** 3
         X, Y = np.meshgrid(x, x)
         W = np.outer(w, w).ravel()
         o = self.origin(k)
@@ -84,8 +110,18 @@ class DGSpace:
         return pts, W * h * h
 
     def face_quadrature(self, f, q: int) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
-        """Points, weights (with the length) and unit normal of a sub-face."""
+        """Points, weights (with the length / area) and unit normal of a sub-face."""
         x, w = basis.gauss(q)
+        if self.dim == 3:
+            (a, b), (l0, l1), (h0, h1) = f.ta, f.lo, f.hi
+            U, T = np.meshgrid(x, x, indexing="ij")        # second tangential axis outer
+            pts = np.zeros((q * q, 3))
+            pts[:, f.axis] = f.c * self.lh
+            pts[:, a] = (l0 + (h0 - l0) * T.ravel()) * self.lh
+            pts[:, b] = (l1 + (h1 - l1) * U.ravel()) * self.lh
+            n = np.zeros(3)
+            n[f.axis] = f.normal_sign
+            return pts, np.outer(w, w).ravel() * (h0 - l0) * (h1 - l1) * self.lh ** 2, n
         t = (f.t0 + (f.t1 - f.t0) * x) * self.lh
         c = np.full(q, f.c * self.lh)
         pts = np.stack([c, t], axis=1) if f.axis == 0 else np.stack([t, c], axis=1)
@@ -134,8 +170,7 @@ def assemble(space: DGSpace, eta: float, form: str = "sipg",
         p = int(topo.p[k])
         pts, W = space.volume_quadrature(k, p + 1)
         _, g = space.eval(k, pts)
-        K = np.einsum("qa,qb,q->ab", g[:, :, 0], g[:, :, 0], W) + \
-            np.einsum("qa,qb,q->ab", g[:, :, 1], g[:, :, 1], W)
+        K = sum(np.einsum("qa,qb,q->ab", g[:, :, d], g[:, :, d], W) for d in range(space.dim))
         add(space.dofs(k), space.dofs(k), K)
 
     if not broken_only:
@@ -194,8 +229,7 @@ def element_rows(space: DGSpace, k: int, x: np.ndarray, eta: float, form: str = 
     p = int(topo.p[k])
     pts, W = space.volume_quadrature(k, p + 1)
     _, g = space.eval(k, pts)
-    K = np.einsum("qa,qb,q->ab", g[:, :, 0], g[:, :, 0], W) + \
-        np.einsum("qa,qb,q->ab", g[:, :, 1], g[:, :, 1], W)
+    K = sum(np.einsum("qa,qb,q->ab", g[:, :, d], g[:, :, d], W) for d in range(space.dim))
     y = K @ x[space.dofs(k)]
     for f in topo.faces_of(k):
         sides = [f.km] + ([f.kp] if f.kp >= 0 else [])
@@ -218,6 +252,7 @@ def element_rows(space: DGSpace, k: int, x: np.ndarray, eta: float, form: str = 
                 v, _ = space.eval(e, fpts)
                 b = (v.T * FW) @ Jm
                 F = F + eta * coef * (b.T @ np.linalg.inv(space.mass(e)) @ b)
-        rows = slice(0, (p + 1) ** 2) if f.km == k else slice(len(I[0]), len(I[0]) + (p + 1) ** 2)
+        nk = (p + 1) ** space.dim
+        rows = slice(0, nk) if f.km == k else slice(len(I[0]), len(I[0]) + nk)
         y = y + F[rows] @ x[Im]
     return y

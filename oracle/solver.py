@@ -32,13 +32,23 @@ class Problem:
     cs: ConformingSpace
 
 
-def build_problem(mesh, form: str = "sipg", eta: Optional[float] = None,
-                  penalty_form: str = "paper", remark_cases: bool = False) -> Problem:
-    topo = Topology(mesh.lo, mesh.size, mesh.p, mesh.extent)
+def build_operator(mesh, form: str = "sipg", eta: Optional[float] = None,
+                   penalty_form: str = "paper"):
+    """(topology, DG space, sparse A) of a 2D or 3D mesh description."""
+    if mesh.dim == 3:
+        from .topology3 import Topology3
+        topo = Topology3(mesh.lo, mesh.size, mesh.p, mesh.extent)
+    else:
+        topo = Topology(mesh.lo, mesh.size, mesh.p, mesh.extent)
     space = DGSpace(topo, mesh.lattice_h)
     if eta is None:
         eta = br2_eta(topo) if form == "br2" else 100.0
-    A = assemble(space, eta, form=form, penalty_form=penalty_form)
+    return topo, space, assemble(space, eta, form=form, penalty_form=penalty_form)
+
+
+def build_problem(mesh, form: str = "sipg", eta: Optional[float] = None,
+                  penalty_form: str = "paper", remark_cases: bool = False) -> Problem:
+    topo, space, A = build_operator(mesh, form, eta, penalty_form)
     cs = ConformingSpace(space, remark_cases=remark_cases)
     return Problem(topo, space, A, cs)
 
