@@ -170,7 +170,7 @@ def assemble(space: DGSpace, eta: float, form: str = "sipg",
         p = int(topo.p[k])
         pts, W = space.volume_quadrature(k, p + 1)
         _, g = space.eval(k, pts)
-        K = sum(np.einsum("qa,qb,q->ab", g[:, :, d], g[:, :, d], W) for d in range(space.dim))
+        K = sum((g[:, :, d].T * W) @ g[:, :, d] for d in range(space.dim))
         add(space.dofs(k), space.dofs(k), K)
 
     if not broken_only:
@@ -229,7 +229,7 @@ def element_rows(space: DGSpace, k: int, x: np.ndarray, eta: float, form: str = 
     p = int(topo.p[k])
     pts, W = space.volume_quadrature(k, p + 1)
     _, g = space.eval(k, pts)
-    K = sum(np.einsum("qa,qb,q->ab", g[:, :, d], g[:, :, d], W) for d in range(space.dim))
+    K = sum((g[:, :, d].T * W) @ g[:, :, d] for d in range(space.dim))
     y = K @ x[space.dofs(k)]
     for f in topo.faces_of(k):
         sides = [f.km] + ([f.kp] if f.kp >= 0 else [])

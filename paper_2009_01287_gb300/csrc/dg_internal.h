@@ -70,6 +70,30 @@ struct SubFaceRec {
   double len;        // physical length of the sub-face
 };
 
+// One sub-face of a cube mesh seen from one of its sides.  The sub-face is a
+// square; its face integrals factor into two 1D tables, one per tangential
+// axis of the side (the lower-numbered axis first).
+struct SubFaceRec3 {
+  int32_t nb;        // neighbour element, -1 on the boundary
+  int32_t nb_side;   // neighbour side holding the sub-face
+  int32_t pn;        // neighbour degree
+  int32_t pad;
+  int32_t tab_oo[2]; // own-own 1D face mass per tangential axis ((p+1)^2)
+  int32_t tab_on[2]; // own-neighbour ((p+1) x (pn+1))
+  int32_t tab_nn[2]; // neighbour-neighbour ((pn+1)^2)
+  double sigma;      // SIPG penalty
+  double area;       // physical area of the sub-face
+};
+
+// Shared-memory budget (doubles) of one 3D operator tile; the host sizes the
+// tiles so that every one fits.
+constexpr int kApply3Budget = 13 * 1024;
+// doubles of shared memory one element of degree p needs in a 3D tile whose
+// elements see neighbour degrees below nq (nq = max(p, pn) + 1)
+constexpr int apply3_elem_doubles(int p, int nq, bool br2) {
+  return 5 * (p + 1) * (p + 1) * (p + 1) + 12 * (p + 1) * (p + 1) + 6 * (br2 ? 8 : 4) * nq * nq;
+}
+
 // Offsets of the degree-p 1D matrices inside the device table buffer.
 struct BasisOff {
   int M, K, Minv, d0, d1;
@@ -81,19 +105,30 @@ struct ApplyTile {
   int32_t first;     // index into the degree-sorted element order
   int32_t count;
   int32_t inst;      // batch instance of the tile's elements (0 for a single mesh)
+  int32_t nq;        // 3D: max(p, neighbour degrees) + 1 over the tile
+  int32_t maxsub;    // 3D: most sub-faces on one side of a tile element
 };
 
 // ------------------------------------------------------------------ mesh (host topology)
 struct HostMesh {
   int dim = 2;
   int64_t n = 0;
-  std::vector<int32_t> lo;      // n*2
+  std::vector<int32_t> lo;      // n*dim
   std::vector<int32_t> size;    // n
   std::vector<int32_t> p;       // n
-  int32_t extent[2] = {0, 0};
+  int32_t extent[3] = {0, 0, 1};
   double lh = 1.0;
   std::vector<int64_t> off;     // n+1 DOF offsets
-  std::vector<int32_t> cellmap; // extent0*extent1 -> element
+  std::vector<int32_t> cellmap; // lattice cell (x fastest) -> element
+
+  // 3D: sub-faces seen from every element side, sf_ptr[6k+s] .. sf_ptr[6k+s+1];
+  // a sub-face is the square [a0, a0+len] x [b0, b0+len] in the side's
+  // (first, second) tangential lattice coordinates
+  struct SF3 { int32_t nb, nb_side, a0, b0, len; };
+  std::vector<SF3> sf3;
+  int32_t elem_at3(int x, int y, int z) const {
+    return cellmap[((int64_t)z * extent[1] + y) * extent[0] + x];
+  }
 
   // sub-faces seen from each element side: sf_ptr[4k+s] .. sf_ptr[4k+s+1]
   std::vector<int32_t> sf_ptr;
@@ -123,6 +158,15 @@ struct HostMesh {
 };
 
 void build_topology(HostMesh& m);   // fills sf, masters, side_master
+void build_topology3(HostMesh& m);  // fills sf_ptr (6 per element), sf3
+
+// side s of a cube: normal axis s / 2, upper face if s is odd; tangential axes
+// in increasing order
+inline void side_axes3(int s, int& ax, int& t0, int& t1) {
+  ax = s >> 1;
+  t0 = (ax == 0) ? 1 : 0;
+  t1 = (ax == 2) ? 1 : 2;
+}
 
 // Face-mass tables (Section 2: exact face integrals on sub-faces).
 struct FaceTables {

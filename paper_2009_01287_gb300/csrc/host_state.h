@@ -74,6 +74,8 @@ struct dg_mesh {
   // host copies of what the device holds
   std::vector<double> h_h;
   std::vector<dg::SubFaceRec> h_sf;
+  std::vector<dg::SubFaceRec3> h_sf3;   // cube meshes
+  int64_t apply3_smem = 0;              // dynamic shared memory of the 3D operator kernel
   std::vector<double> h_tables;
   dg::BasisOff boff[dg::kMaxP + 1];
   std::vector<dg::ApplyTile> h_tiles;
@@ -88,6 +90,7 @@ struct dg_mesh {
   double* d_tr = nullptr;       // side traces written by each apply
   int32_t* d_sf_ptr = nullptr;
   dg::SubFaceRec* d_sf = nullptr;
+  dg::SubFaceRec3* d_sf3 = nullptr;
   double* d_tables = nullptr;
   int32_t* d_order = nullptr;
   dg::ApplyTile* d_tiles = nullptr;
@@ -143,8 +146,11 @@ void build_mesh_host(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opt
 void build_tiles(dg_mesh* M);
 // upload the host-built operator data (M->host.p/off/sf_ptr, h_* arrays)
 void upload_mesh(dg_mesh* M, cudaStream_t s);
+// cube meshes: topology, records, tables, tiles, stats (opts already validated)
+void build_mesh_host3(dg_mesh* M, const dg_mesh_desc* desc, const dg_options& opts);
 // rows of element k of y = A x (x: full host vector), same formulation as the kernel
 void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double* y);
+void host_element_residual3(const dg_mesh& M, int64_t k, const double* x, double* y);
 // load vector of the sine right-hand side into hb (n_dofs doubles, zeroed)
 void host_rhs_sine(const dg_mesh& mesh, int n_modes, const double* amps, const int32_t* waves,
                    double* hb);

@@ -39,8 +39,10 @@ void* dginspect_create(const dg_mesh_desc* desc, const dg_options* opts, int wit
       o.smoother = opts->smoother;
       o.remark_cases = opts->remark_cases;
     }
-    I->pc = build_host_precond(I->mesh, o);
-    if (with_amg && I->pc.nC > 0) I->amg = amg_setup(I->pc.Ac);
+    if (I->mesh.host.dim == 2) {
+      I->pc = build_host_precond(I->mesh, o);
+      if (with_amg && I->pc.nC > 0) I->amg = amg_setup(I->pc.Ac);
+    }
     return I.release();
   } catch (const std::exception& e) {
     g_err = e.what();
@@ -116,7 +118,10 @@ void dginspect_level_A(void* h, int l, int64_t* ptr, int32_t* idx, double* val) 
 void dginspect_apply(void* h, const double* x, double* y) {
   Inspect* I = (Inspect*)h;
   const HostMesh& m = I->mesh.host;
-  for (int64_t k = 0; k < m.n; ++k) host_element_residual(I->mesh, k, x, y + m.off[k]);
+  for (int64_t k = 0; k < m.n; ++k) {
+    if (m.dim == 3) host_element_residual3(I->mesh, k, x, y + m.off[k]);
+    else host_element_residual(I->mesh, k, x, y + m.off[k]);
+  }
 }
 
 }  // extern "C"

@@ -159,7 +159,7 @@ static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 static void validate_and_copy(const dg_mesh_desc* d, HostMesh& m) {
   DG_REQUIRE(d != nullptr, "null mesh description");
-  DG_REQUIRE(d->dim == 2, "only dim = 2 is supported");
+  DG_REQUIRE(d->dim == 2, "dim must be 2 or 3");
   DG_REQUIRE(d->n_elems > 0 && d->n_elems < (1LL << 30), "n_elems out of range");
   DG_REQUIRE(d->lo && d->size && d->p && d->extent, "null array in mesh description");
   DG_REQUIRE(d->lattice_h > 0.0 && std::isfinite(d->lattice_h), "lattice_h must be positive");
@@ -224,7 +224,6 @@ void build_tiles(dg_mesh* M) {
 
 void build_mesh_host(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opts) {
   HostMesh& m = M->host;
-  validate_and_copy(desc, m);
   dg_options o{};
   o.form = DG_FORM_SIPG;
   o.penalty_form = DG_PENALTY_PAPER;
@@ -232,6 +231,12 @@ void build_mesh_host(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opt
   DG_REQUIRE(o.form == DG_FORM_SIPG || o.form == DG_FORM_BR2, "unknown form");
   DG_REQUIRE(o.penalty_form == DG_PENALTY_PAPER || o.penalty_form == DG_PENALTY_P1SQ, "unknown penalty form");
   M->opts = o;
+  DG_REQUIRE(desc != nullptr, "null mesh description");
+  if (desc->dim == 3) {
+    build_mesh_host3(M, desc, o);
+    return;
+  }
+  validate_and_copy(desc, m);
   build_topology(m);
   M->n_dofs = m.off[m.n];
   DG_REQUIRE(M->n_dofs < (1LL << 31), "too many unknowns for 32-bit indices");
