@@ -1,0 +1,361 @@
+// Matrix-free SIPG / BR2 operator y = A x on cube meshes (the method of
+// Section 2 on hexahedra; BR2 stabilisation of Section 4.4), FP64.
+//
+// The same two kernels as on squares:
+//  trace3  for every element side, the value u and outward normal derivative
+//          dn at its (p+1)^2 side nodes (one contraction along the normal);
+//  apply3  one CTA per tile of elements of one degree P:
+//    volume  y = h (K x M x M + M x K x M + M x M x K) x, sum factorised in
+//            three passes through shared memory (7 (p+1)^4 FMAs per element):
+//              along z: A = M x, B = K x;  along y: C = M A, D = K A + M B;
+//              along x: y = h (K C + M D);
+//    faces   in rounds: round j takes the j-th sub-face of every side of the
+//            tile.  A sub-face is a square whose face-mass matrices are Kronecker
+//            products of 1D tables (first tangential axis a, second b), so every
+//            face product is two 1D contractions with a barrier between them:
+//              a = M_oo u-, c = M_oo dn-, b = M_on u+, d = M_on dn+
+//            and, for SIPG, side residual += area (sigma (a - b) - (c - d) / 2)
+//            and normal-derivative coefficient c2 -= area (a - b) / 2
+//            (boundary: area (sigma a - c) and -area a).  For BR2 the sigma term
+//            becomes eta/4 area [M_oo G_o jo + M_on G_n jn] with the jump
+//            projections jo = area (a - b), jn = area (M_no u- - M_nn u+) and
+//            G = h^-3 Minv_00 (Minv x Minv), the side block of the element mass
+//            inverse (boundary: eta area M_oo G_o jo);
+//    gather  volume pass along x, side residuals and the normal-derivative
+//            terms c2 (x) dn(v) of all six sides.
+// Each sub-face is evaluated from both of its sides (no atomics): applies are
+// bit-reproducible.
+#pragma once
+
+#include "apply_kernel.cuh"
+
+namespace dg {
+
+// volume index of side node (i, j) at normal index q on side s
+template <int NP>
+__device__ __forceinline__ int side_node3(int s, int i, int j, int q) {
+  const int ax = s >> 1;
+  return ax == 0 ? q + NP * (i + NP * j) : (ax == 1 ? i + NP * (q + NP * j) : i + NP * (j + NP * q));
+}
+
+template <int P>
+__device__ __forceinline__ void trace3_tile(const ApplyArgs& A, const ApplyTile& T) {
+  constexpr int NP = P + 1, N2 = NP * NP;
+  const BasisOff bo = A.boff[P];
+  const int ntask = T.count * 6 * N2;
+  for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
+    const int e = t / (6 * N2);
+    const int rem = t - e * 6 * N2;
+    const int s = rem / N2;
+    const int ij = rem - s * N2;
+    const int i = ij % NP, j = ij / NP;
+    const int k = A.order[T.first + e];
+    const double* xk = A.x + A.off[k];
+    const double* dv = A.tab + ((s & 1) ? bo.d1 : bo.d0);
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) acc = fma(__ldg(dv + q), __ldg(xk + side_node3<NP>(s, i, j, q)), acc);
+    const double sg = (s & 1) ? A.ih[k] : -A.ih[k];
+    double2 v;
+    v.x = __ldg(xk + side_node3<NP>(s, i, j, (s & 1) ? P : 0));
+    v.y = sg * acc;
+    reinterpret_cast<double2*>(A.tr + A.toff[k])[s * N2 + ij] = v;
+  }
+}
+
+template <int P, bool BR2>
+__device__ __forceinline__ void apply3_tile(const ApplyArgs& A, const ApplyTile& T, int tile,
+                                            double* sm, double* red) {
+  constexpr int NP = P + 1, N2 = NP * NP, N3 = N2 * NP;
+  constexpr int S = BR2 ? 8 : 4;          // scratch arrays per side and round
+  const int cnt = T.count, NQ = T.nq, Q2 = NQ * NQ;
+  double* sM = sm;
+  double* sK = sM + N2;
+  double* sx = sK + N2;
+  double* sA = sx + cnt * N3;
+  double* sB = sA + cnt * N3;
+  double* sC = sB + cnt * N3;
+  double* sD = sC + cnt * N3;
+  double* sr = sD + cnt * N3;             // [cnt][6][N2] side residuals
+  double* sc2 = sr + cnt * 6 * N2;        // [cnt][6][N2] normal-derivative coefficients
+  double* sw = sc2 + cnt * 6 * N2;        // [cnt][6][S][Q2] round scratch
+
+  const int tid = threadIdx.x;
+  if (A.skip && A.skip[(int64_t)T.inst * A.skip_stride] != 0.0) {   // CTA-uniform
+    if (A.dot_partial && tid == 0) A.dot_partial[tile] = 0.0;
+    return;
+  }
+  const BasisOff bo = A.boff[P];
+  const int nvol = cnt * N3;
+  for (int i = tid; i < N2; i += blockDim.x) {
+    sM[i] = __ldg(A.tab + bo.M + i);
+    sK[i] = __ldg(A.tab + bo.K + i);
+  }
+  for (int t = tid; t < nvol; t += blockDim.x) {
+    const int e = t / N3;
+    sx[t] = A.x[A.off[A.order[T.first + e]] + (t - e * N3)];
+  }
+  for (int t = tid; t < cnt * 6 * N2; t += blockDim.x) {
+    sr[t] = 0.0;
+    sc2[t] = 0.0;
+  }
+  __syncthreads();
+  // ---- volume pass along z
+  for (int t = tid; t < nvol; t += blockDim.x) {
+    const int e = t / N3, node = t - e * N3;
+    const int ixy = node % N2, iz = node / N2;
+    const double* xc = sx + e * N3 + ixy;
+    double a = 0.0, b = 0.0;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const double v = xc[q * N2];
+      a = fma(sM[iz * NP + q], v, a);
+      b = fma(sK[iz * NP + q], v, b);
+    }
+    sA[t] = a;
+    sB[t] = b;
+  }
+  __syncthreads();
+  // ---- volume pass along y
+  for (int t = tid; t < nvol; t += blockDim.x) {
+    const int e = t / N3, node = t - e * N3;
+    const int ix = node % NP, iy = (node / NP) % NP, iz = node / N2;
+    const double* ac = sA + e * N3 + iz * N2 + ix;
+    const double* bc = sB + e * N3 + iz * N2 + ix;
+    double c = 0.0, d = 0.0;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const double m = sM[iy * NP + q], kk = sK[iy * NP + q];
+      c = fma(m, ac[q * NP], c);
+      d = fma(kk, ac[q * NP], d);
+      d = fma(m, bc[q * NP], d);
+    }
+    sC[t] = c;
+    sD[t] = d;
+  }
+  // ---- faces, one sub-face per side per round
+  const int nface = cnt * 6 * Q2;
+  const double* tab = A.tab;
+  for (int j = 0; j < T.maxsub; ++j) {
+    // P1: contractions along the first tangential axis
+    for (int t = tid; t < nface; t += blockDim.x) {
+      const int es = t / Q2, q = t - es * Q2;
+      const int e = es / 6, s = es - e * 6;
+      const int i = q % NQ, n = q / NQ;
+      const int k = A.order[T.first + e];
+      const int b0 = A.sf_ptr[6 * k + s];
+      if (j >= A.sf_ptr[6 * k + s + 1] - b0) continue;
+      const SubFaceRec3& f = A.sf3[b0 + j];
+      const int np = f.pn + 1;
+      const bool in = f.nb >= 0;
+      double* W = sw + es * S * Q2;
+      const double2* trk = reinterpret_cast<const double2*>(A.tr + A.toff[k]) + s * N2;
+      if (i < NP && n < NP) {
+        const double* Ma = tab + f.tab_oo[0] + i * NP;
+        double wa = 0.0, wc = 0.0;
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+          const double2 v = trk[n * NP + m];
+          const double w = __ldg(Ma + m);
+          wa = fma(w, v.x, wa);
+          wc = fma(w, v.y, wc);
+        }
+        W[0 * Q2 + i * NQ + n] = wa;
+        W[1 * Q2 + i * NQ + n] = wc;
+      }
+      if (!in) continue;
+      const double2* trn = reinterpret_cast<const double2*>(A.tr + A.toff[f.nb]) + f.nb_side * np * np;
+      if (i < NP && n < np) {
+        const double* Ma = tab + f.tab_on[0] + i * np;
+        double wb = 0.0, wd = 0.0;
+        for (int m = 0; m < np; ++m) {
+          const double2 v = trn[n * np + m];
+          const double w = __ldg(Ma + m);
+          wb = fma(w, v.x, wb);
+          wd = fma(w, v.y, wd);
+        }
+        W[2 * Q2 + i * NQ + n] = wb;
+        W[3 * Q2 + i * NQ + n] = wd;
+      }
+      if (BR2 && i < np) {
+        if (n < NP) {
+          double w1 = 0.0;
+#pragma unroll
+          for (int m = 0; m < NP; ++m) w1 = fma(__ldg(tab + f.tab_on[0] + m * np + i), trk[n * NP + m].x, w1);
+          W[4 * Q2 + i * NQ + n] = w1;
+        }
+        if (n < np) {
+          double w2 = 0.0;
+          for (int m = 0; m < np; ++m) w2 = fma(__ldg(tab + f.tab_nn[0] + i * np + m), trn[n * np + m].x, w2);
+          W[5 * Q2 + i * NQ + n] = w2;
+        }
+      }
+    }
+    __syncthreads();
+    // P2: contractions along the second tangential axis; SIPG terms, jumps
+    for (int t = tid; t < nface; t += blockDim.x) {
+      const int es = t / Q2, q = t - es * Q2;
+      const int e = es / 6, s = es - e * 6;
+      const int i = q % NQ, jj = q / NQ;
+      const int k = A.order[T.first + e];
+      const int b0 = A.sf_ptr[6 * k + s];
+      if (j >= A.sf_ptr[6 * k + s + 1] - b0) continue;
+      const SubFaceRec3& f = A.sf3[b0 + j];
+      const int np = f.pn + 1;
+      const bool in = f.nb >= 0;
+      double* W = sw + es * S * Q2;
+      const double ar = f.area;
+      if (i < NP && jj < NP) {
+        const double* Mb = tab + f.tab_oo[1] + jj * NP;
+        double a = 0.0, c = 0.0, b = 0.0, d = 0.0;
+#pragma unroll
+        for (int n = 0; n < NP; ++n) {
+          const double w = __ldg(Mb + n);
+          a = fma(w, W[0 * Q2 + i * NQ + n], a);
+          c = fma(w, W[1 * Q2 + i * NQ + n], c);
+        }
+        if (in) {
+          const double* Mbn = tab + f.tab_on[1] + jj * np;
+          for (int n = 0; n < np; ++n) {
+            const double w = __ldg(Mbn + n);
+            b = fma(w, W[2 * Q2 + i * NQ + n], b);
+            d = fma(w, W[3 * Q2 + i * NQ + n], d);
+          }
+        }
+        const int o = es * N2 + jj * NP + i;
+        const double jmp = a - b;
+        double rr, cc;
+        if (in) {
+          rr = -0.5 * ar * (c - d);
+          cc = -0.5 * ar * jmp;
+        } else {
+          rr = -ar * c;
+          cc = -ar * a;
+        }
+        if (!BR2) rr = fma(f.sigma * ar, jmp, rr);
+        sr[o] += rr;
+        sc2[o] += cc;
+        if (BR2) W[6 * Q2 + i * NQ + jj] = ar * jmp;
+      }
+      if (BR2 && in && i < np && jj < np) {
+        double v = 0.0;
+#pragma unroll
+        for (int n = 0; n < NP; ++n) v = fma(__ldg(tab + f.tab_on[1] + n * np + jj), W[4 * Q2 + i * NQ + n], v);
+        for (int n = 0; n < np; ++n) v = fma(-__ldg(tab + f.tab_nn[1] + jj * np + n), W[5 * Q2 + i * NQ + n], v);
+        W[7 * Q2 + i * NQ + jj] = ar * v;
+      }
+    }
+    __syncthreads();
+    if (!BR2) continue;
+    // P3..P6 (BR2): G = side block of the mass inverse on both elements, then
+    // the face mass back onto this element's side nodes
+    for (int ph = 3; ph <= 6; ++ph) {
+      for (int t = tid; t < nface; t += blockDim.x) {
+        const int es = t / Q2, q = t - es * Q2;
+        const int e = es / 6, s = es - e * 6;
+        const int i = q % NQ, n = q / NQ;
+        const int k = A.order[T.first + e];
+        const int b0 = A.sf_ptr[6 * k + s];
+        if (j >= A.sf_ptr[6 * k + s + 1] - b0) continue;
+        const SubFaceRec3& f = A.sf3[b0 + j];
+        const int np = f.pn + 1;
+        const bool in = f.nb >= 0;
+        double* W = sw + es * S * Q2;
+        const double* Mi = tab + bo.Minv;
+        const double* Min = tab + A.boff[f.pn].Minv;
+        if (ph == 3) {          // t1 = Minv_a jo, t2 = Minvn_a jn
+          if (i < NP && n < NP) {
+            double v = 0.0;
+#pragma unroll
+            for (int m = 0; m < NP; ++m) v = fma(__ldg(Mi + i * NP + m), W[6 * Q2 + m * NQ + n], v);
+            W[0 * Q2 + i * NQ + n] = v;
+          }
+          if (in && i < np && n < np) {
+            double v = 0.0;
+            for (int m = 0; m < np; ++m) v = fma(__ldg(Min + i * np + m), W[7 * Q2 + m * NQ + n], v);
+            W[1 * Q2 + i * NQ + n] = v;
+          }
+        } else if (ph == 4) {   // go = sc t1 Minv_b^T, gn likewise
+          if (i < NP && n < NP) {
+            double v = 0.0;
+#pragma unroll
+            for (int m = 0; m < NP; ++m) v = fma(__ldg(Mi + n * NP + m), W[0 * Q2 + i * NQ + m], v);
+            const double ih = A.ih[k];
+            W[2 * Q2 + i * NQ + n] = v * __ldg(Mi) * ih * ih * ih;
+          }
+          if (in && i < np && n < np) {
+            double v = 0.0;
+            for (int m = 0; m < np; ++m) v = fma(__ldg(Min + n * np + m), W[1 * Q2 + i * NQ + m], v);
+            const double ihn = A.ih[f.nb];
+            W[3 * Q2 + i * NQ + n] = v * __ldg(Min) * ihn * ihn * ihn;
+          }
+        } else if (ph == 5) {   // v1 = Moo_a go, v2 = Mon_a gn
+          if (i < NP && n < NP) {
+            double v = 0.0;
+#pragma unroll
+            for (int m = 0; m < NP; ++m) v = fma(__ldg(tab + f.tab_oo[0] + i * NP + m), W[2 * Q2 + m * NQ + n], v);
+            W[4 * Q2 + i * NQ + n] = v;
+          }
+          if (in && i < NP && n < np) {
+            double v = 0.0;
+            for (int m = 0; m < np; ++m) v = fma(__ldg(tab + f.tab_on[0] + i * np + m), W[3 * Q2 + m * NQ + n], v);
+            W[5 * Q2 + i * NQ + n] = v;
+          }
+        } else {                // residual += eta coef area (v1 Moo_b^T + v2 Mon_b^T)
+          if (i < NP && n < NP) {
+            const int jj = n;
+            double st = 0.0;
+#pragma unroll
+            for (int m = 0; m < NP; ++m) st = fma(__ldg(tab + f.tab_oo[1] + jj * NP + m), W[4 * Q2 + i * NQ + m], st);
+            if (in)
+              for (int m = 0; m < np; ++m) st = fma(__ldg(tab + f.tab_on[1] + jj * np + m), W[5 * Q2 + i * NQ + m], st);
+            sr[es * N2 + jj * NP + i] += A.eta * (in ? 0.25 : 1.0) * f.area * st;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  // ---- gather: pass along x, side residuals, normal-derivative terms
+  double part = 0.0;
+  const double* d0 = A.tab + bo.d0;
+  const double* d1 = A.tab + bo.d1;
+  for (int t = tid; t < nvol; t += blockDim.x) {
+    const int e = t / N3, node = t - e * N3;
+    const int ix = node % NP, iy = (node / NP) % NP, iz = node / N2;
+    const int k = A.order[T.first + e];
+    const double* cr = sC + e * N3 + iz * N2 + iy * NP;
+    const double* dr = sD + e * N3 + iz * N2 + iy * NP;
+    double v = 0.0;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      v = fma(sK[ix * NP + q], cr[q], v);
+      v = fma(sM[ix * NP + q], dr[q], v);
+    }
+    double y = A.hk[k] * v;
+    const double* c2 = sc2 + e * 6 * N2;
+    const double* r = sr + e * 6 * N2;
+    double g = -__ldg(d0 + ix) * c2[0 * N2 + iz * NP + iy];
+    g = fma(__ldg(d1 + ix), c2[1 * N2 + iz * NP + iy], g);
+    g = fma(-__ldg(d0 + iy), c2[2 * N2 + iz * NP + ix], g);
+    g = fma(__ldg(d1 + iy), c2[3 * N2 + iz * NP + ix], g);
+    g = fma(-__ldg(d0 + iz), c2[4 * N2 + iy * NP + ix], g);
+    g = fma(__ldg(d1 + iz), c2[5 * N2 + iy * NP + ix], g);
+    y = fma(g, A.ih[k], y);
+    if (ix == 0) y += r[0 * N2 + iz * NP + iy];
+    if (ix == P) y += r[1 * N2 + iz * NP + iy];
+    if (iy == 0) y += r[2 * N2 + iz * NP + ix];
+    if (iy == P) y += r[3 * N2 + iz * NP + ix];
+    if (iz == 0) y += r[4 * N2 + iy * NP + ix];
+    if (iz == P) y += r[5 * N2 + iy * NP + ix];
+    A.y[A.off[k] + node] = y;
+    part = fma(y, sx[t], part);
+  }
+  if (A.dot_partial) {
+    const double tot = block_sum<kThreads>(part, red);
+    if (tid == 0) A.dot_partial[tile] = tot;
+  }
+}
+
+}  // namespace dg

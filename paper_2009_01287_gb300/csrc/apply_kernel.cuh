@@ -122,6 +122,8 @@ struct ApplyArgs {
   double* tr;                 // side traces: [side][node][u, dn]
   const int32_t* sf_ptr;
   const SubFaceRec* sf;
+  const SubFaceRec3* sf3;     // cube meshes
+  const double* hk;           // h per element (cube meshes)
   const double* tab;          // basis + face tables
   const int32_t* order;       // degree-sorted element order
   const ApplyTile* tiles;

@@ -412,6 +412,8 @@ dg_status dg_batch_create(const dg_mesh_desc* descs, int n_problems, int n_rhs,
   std::unique_ptr<dg_batch> B(new dg_batch());
   try {
     DG_REQUIRE(descs && n_problems >= 1 && n_rhs >= 1, "bad batch size");
+    for (int k = 0; k < n_problems; ++k)
+      if (descs[k].dim != 2) throw Error(DG_EUNSUPPORTED, "the batched solver takes square meshes only");
     dg_options o{};
     o.form = DG_FORM_SIPG;
     o.precision = DG_PREC_MIXED;

@@ -42,7 +42,7 @@ static void build_mesh(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* o
 
 void upload_mesh(dg_mesh* M, cudaStream_t s) {
   const HostMesh& m = M->host;
-  M->apply_grid = apply_kernel_setup(M->opts.form);
+  M->apply_grid = apply_kernel_setup(*M);
   // upload
   DevArena& a = M->arena;
   M->d_p = a.upload(m.p, s);
@@ -53,7 +53,8 @@ void upload_mesh(dg_mesh* M, cudaStream_t s) {
     std::vector<int64_t> toff(m.n + 1, 0);
     for (int64_t k = 0; k < m.n; ++k) {
       ih[k] = 1.0 / M->h_h[k];
-      toff[k + 1] = toff[k] + 8 * (int64_t)(m.p[k] + 1);
+      const int64_t np = m.p[k] + 1;
+      toff[k + 1] = toff[k] + (m.dim == 3 ? 12 * np * np : 8 * np);
     }
     M->d_ih = a.upload(ih, s);
     M->d_toff = a.upload(toff, s);
@@ -61,6 +62,7 @@ void upload_mesh(dg_mesh* M, cudaStream_t s) {
   }
   M->d_sf_ptr = a.upload(m.sf_ptr, s);
   M->d_sf = a.upload(M->h_sf, s);
+  M->d_sf3 = a.upload(M->h_sf3, s);
   M->d_tables = a.upload(M->h_tables, s);
   M->d_order = a.upload(M->h_order, s);
   M->d_tiles = a.upload(M->h_tiles, s);
@@ -74,27 +76,39 @@ void upload_mesh(dg_mesh* M, cudaStream_t s) {
 void host_rhs_sine(const dg_mesh& mesh, int n_modes, const double* amps, const int32_t* waves,
                    double* hb) {
   const HostMesh& m = mesh.host;
+  const int dim = m.dim;
   for (int64_t k = 0; k < m.n; ++k) {
     const int P = m.p[k], NP = P + 1;
     const Basis1D& B = basis1d(P);
     std::vector<double> gx, gw;
     gauss_rule(P + 3, gx, gw);
     const double h = mesh.h_h[k];
-    const double x0 = m.lo[2 * k] * m.lh, y0 = m.lo[2 * k + 1] * m.lh;
+    double x0[3] = {0.0, 0.0, 0.0};
+    for (int d = 0; d < dim; ++d) x0[d] = m.lo[dim * k + d] * m.lh;
     const int q = (int)gx.size();
     std::vector<double> L((size_t)q * NP);
     for (int g = 0; g < q; ++g) lagrange_eval(B.nodes, gx[g], &L[(size_t)g * NP]);
-    for (int gy = 0; gy < q; ++gy)
-      for (int gxi = 0; gxi < q; ++gxi) {
-        const double X = x0 + h * gx[gxi], Y = y0 + h * gx[gy];
-        double f = 0.0;
-        for (int md = 0; md < n_modes; ++md)
-          f += amps[md] * std::sin(M_PI * waves[2 * md] * X) * std::sin(M_PI * waves[2 * md + 1] * Y);
-        const double w = gw[gxi] * gw[gy] * h * h * f;
-        for (int iy = 0; iy < NP; ++iy)
-          for (int ix = 0; ix < NP; ++ix)
-            hb[m.off[k] + iy * NP + ix] += w * L[(size_t)gy * NP + iy] * L[(size_t)gxi * NP + ix];
-      }
+    const int qz = dim == 3 ? q : 1, nz = dim == 3 ? NP : 1;
+    for (int gz = 0; gz < qz; ++gz)
+      for (int gy = 0; gy < q; ++gy)
+        for (int gxi = 0; gxi < q; ++gxi) {
+          const double X[3] = {x0[0] + h * gx[gxi], x0[1] + h * gx[gy], x0[2] + h * gx[gz]};
+          double f = 0.0;
+          for (int md = 0; md < n_modes; ++md) {
+            double t = amps[md];
+            for (int d = 0; d < dim; ++d) t *= std::sin(M_PI * waves[dim * md + d] * X[d]);
+            f += t;
+          }
+          double w = gw[gxi] * gw[gy] * h * h * f;
+          if (dim == 3) w *= gw[gz] * h;
+          for (int iz = 0; iz < nz; ++iz) {
+            const double lz = dim == 3 ? L[(size_t)gz * NP + iz] : 1.0;
+            for (int iy = 0; iy < NP; ++iy)
+              for (int ix = 0; ix < NP; ++ix)
+                hb[m.off[k] + (iz * NP + iy) * NP + ix] +=
+                    w * lz * L[(size_t)gy * NP + iy] * L[(size_t)gxi * NP + ix];
+          }
+        }
   }
 }
 
@@ -378,6 +392,8 @@ dg_status dg_precond_setup(const dg_mesh* mesh, const dg_options* opts, dg_preco
     DG_REQUIRE(o.precision == DG_PREC_FP64 || o.precision == DG_PREC_MIXED, "unknown precision");
     DG_REQUIRE(o.lor == DG_LOR_EXACT || o.lor == DG_LOR_AMG, "unknown LOR solver");
     DG_REQUIRE(o.smoother == DG_SMOOTHER_FULL || o.smoother == DG_SMOOTHER_JACOBI_ONLY, "unknown smoother");
+    if (mesh->host.dim != 2)
+      throw Error(DG_EUNSUPPORTED, "the preconditioner is built for square meshes only");
     HostPrecond H = build_host_precond(*mesh, o);
     pc = new dg_precond();
     pc->mesh = mesh;

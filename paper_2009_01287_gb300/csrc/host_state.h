@@ -118,7 +118,7 @@ struct dg_precond {
   int32_t* blk_dofs_off = nullptr;
   int32_t* blk_dim = nullptr;
   int32_t* blk_dofs = nullptr;
-  void* blk_inv = nullptr;   // row-major dense inverses
+  void* blk_inv = nullptr;   // dense inverses, column-major
   void* lor_inv = nullptr;   // exact LOR solve: dense inverse n_c x n_c
   std::vector<dg::DevLevel> levels;  // AMG (level 0 = LOR matrix)
   void* rc = nullptr;        // n_c restriction of r

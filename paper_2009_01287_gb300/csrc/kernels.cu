@@ -23,6 +23,30 @@ __global__ void __launch_bounds__(kThreads) trace_kernel(const ApplyArgs A) {
   }
 }
 
+// End of a persistent operator launch: the last CTA to leave resets the tile
+// counter and sums the tile partials of x . y in tile order.
+__device__ __forceinline__ void apply_exit(const ApplyArgs& A, double* red) {
+  __shared__ unsigned s_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = (atomicAdd(A.sched + 1, 1u) == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    if (A.dot_partial) {
+      double v = 0.0;
+      for (int i = threadIdx.x; i < A.n_tiles; i += kThreads) v += __ldcg(A.dot_partial + i);
+      v = block_sum<kThreads>(v, red);
+      if (threadIdx.x == 0) *A.dot_out = v;
+    }
+    if (threadIdx.x == 0) {
+      A.sched[0] = 0u;
+      A.sched[1] = 0u;
+    }
+  }
+}
+
 // Persistent operator kernel: a grid sized to the resident capacity takes
 // tiles from an atomic counter, heaviest first (tiles are degree-sorted), so
 // the uneven tiles balance across SMs.  The last CTA to leave resets the
@@ -34,7 +58,6 @@ __global__ void __launch_bounds__(kThreads) apply_kernel(const ApplyArgs A) {
   extern __shared__ double smem[];
   __shared__ double red[kThreads];
   __shared__ int s_tile;
-  __shared__ unsigned s_last;
   while (true) {
     if (threadIdx.x == 0) s_tile = (int)atomicAdd(A.sched, 1u);
     __syncthreads();
@@ -55,24 +78,53 @@ __global__ void __launch_bounds__(kThreads) apply_kernel(const ApplyArgs A) {
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = (atomicAdd(A.sched + 1, 1u) == gridDim.x - 1) ? 1u : 0u;
+  apply_exit(A, red);
+}
+
+__global__ void __launch_bounds__(kThreads) trace3_kernel(const ApplyArgs A) {
+  pdl_entry();
+  const ApplyTile T = A.tiles[blockIdx.x];
+  switch (T.p) {
+    case 1: trace3_tile<1>(A, T); break;
+    case 2: trace3_tile<2>(A, T); break;
+    case 3: trace3_tile<3>(A, T); break;
+    case 4: trace3_tile<4>(A, T); break;
+    case 5: trace3_tile<5>(A, T); break;
+    case 6: trace3_tile<6>(A, T); break;
+    case 7: trace3_tile<7>(A, T); break;
+    case 8: trace3_tile<8>(A, T); break;
+    default: break;
   }
-  __syncthreads();
-  if (s_last) {
-    __threadfence();
-    if (A.dot_partial) {
-      double v = 0.0;
-      for (int i = threadIdx.x; i < A.n_tiles; i += kThreads) v += __ldcg(A.dot_partial + i);
-      v = block_sum<kThreads>(v, red);
-      if (threadIdx.x == 0) *A.dot_out = v;
+}
+
+// Persistent operator kernel of cube meshes (same scheduling as on squares).
+template <bool BR2>
+__global__ void __launch_bounds__(kThreads) apply3_kernel(const ApplyArgs A) {
+  pdl_entry();
+  extern __shared__ double smem[];
+  __shared__ double red[kThreads];
+  __shared__ int s_tile;
+  while (true) {
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(A.sched, 1u);
+    __syncthreads();
+    const int t = s_tile;
+    __syncthreads();
+    if (t >= A.n_tiles) break;
+    const ApplyTile T = A.tiles[t];
+    switch (T.p) {
+      case 1: apply3_tile<1, BR2>(A, T, t, smem, red); break;
+      case 2: apply3_tile<2, BR2>(A, T, t, smem, red); break;
+      case 3: apply3_tile<3, BR2>(A, T, t, smem, red); break;
+      case 4: apply3_tile<4, BR2>(A, T, t, smem, red); break;
+      case 5: apply3_tile<5, BR2>(A, T, t, smem, red); break;
+      case 6: apply3_tile<6, BR2>(A, T, t, smem, red); break;
+      case 7: apply3_tile<7, BR2>(A, T, t, smem, red); break;
+      case 8: apply3_tile<8, BR2>(A, T, t, smem, red); break;
+      default: break;
     }
-    if (threadIdx.x == 0) {
-      A.sched[0] = 0u;
-      A.sched[1] = 0u;
-    }
+    __syncthreads();
   }
+  apply_exit(A, red);
 }
 
 static int apply_smem_bytes() {
@@ -97,6 +149,8 @@ ApplyArgs make_apply_args(const dg_mesh& M, const double* x, double* y, Reduce r
   A.tr = M.d_tr;
   A.sf_ptr = M.d_sf_ptr;
   A.sf = M.d_sf;
+  A.sf3 = M.d_sf3;
+  A.hk = M.d_h;
   A.tab = M.d_tables;
   A.order = M.d_order;
   A.tiles = M.d_tiles;
@@ -112,16 +166,25 @@ ApplyArgs make_apply_args(const dg_mesh& M, const double* x, double* y, Reduce r
   return A;
 }
 
-int apply_kernel_setup(int form) {
+int apply_kernel_setup(const dg_mesh& M) {
   // the shared-memory opt-in is per device: set it on the current one, and
   // return the resident capacity (CTAs) of the persistent operator kernel
-  const int smem = apply_smem_bytes();
-  DG_CUDA(cudaFuncSetAttribute(apply_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  DG_CUDA(cudaFuncSetAttribute(apply_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int dev = 0, sms = 0, per = 0;
   DG_CUDA(cudaGetDevice(&dev));
   DG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  if (form == DG_FORM_BR2)
+  const bool br2 = M.opts.form == DG_FORM_BR2;
+  if (M.host.dim == 3) {
+    const int smem = (int)M.apply3_smem;
+    DG_CUDA(cudaFuncSetAttribute(apply3_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    DG_CUDA(cudaFuncSetAttribute(apply3_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    if (br2) DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, apply3_kernel<true>, kThreads, smem));
+    else DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, apply3_kernel<false>, kThreads, smem));
+    return sms * (per > 0 ? per : 1);
+  }
+  const int smem = apply_smem_bytes();
+  DG_CUDA(cudaFuncSetAttribute(apply_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  DG_CUDA(cudaFuncSetAttribute(apply_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  if (br2)
     DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, apply_kernel<true>, kThreads, smem));
   else
     DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, apply_kernel<false>, kThreads, smem));
@@ -131,9 +194,17 @@ int apply_kernel_setup(int form) {
 void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cudaStream_t s) {
   if (M.n_tiles == 0) return;
   const ApplyArgs A = make_apply_args(M, x, y, red);
+  const int grid = M.n_tiles < M.apply_grid ? M.n_tiles : M.apply_grid;
+  if (M.host.dim == 3) {
+    launch_k(trace3_kernel, M.n_tiles, kThreads, 0, s, A);
+    const int smem3 = (int)M.apply3_smem;
+    if (M.opts.form == DG_FORM_BR2) launch_k(apply3_kernel<true>, grid, kThreads, smem3, s, A);
+    else launch_k(apply3_kernel<false>, grid, kThreads, smem3, s, A);
+    DG_CUDA(cudaGetLastError());
+    return;
+  }
   const int smem = apply_smem_bytes();
   launch_k(trace_kernel, M.n_tiles, kThreads, 0, s, A);
-  const int grid = M.n_tiles < M.apply_grid ? M.n_tiles : M.apply_grid;
   if (M.opts.form == DG_FORM_BR2) launch_k(apply_kernel<true>, grid, kThreads, smem, s, A);
   else launch_k(apply_kernel<false>, grid, kThreads, smem, s, A);
   DG_CUDA(cudaGetLastError());
@@ -224,9 +295,11 @@ __global__ void dense_mv_kernel(const T* __restrict__ Ainv, const T* __restrict_
 }
 
 // V_e block solves, one CTA per block (Section 3.3, T_E = sum_e P_e): the
-// block's residual entries are gathered into shared memory once, then each
-// warp forms rows of A_e^-1 r_e with lanes striding along the (row-major)
-// inverse, so the loads of a row are coalesced.
+// block's residual entries are gathered into shared memory once, then thread l
+// forms row l of A_e^-1 r_e.  The inverse is stored column-major, so at every
+// step the threads of a warp read consecutive entries of one column, and each
+// thread's loads are independent of its running sum (unrolled, in flight
+// together).
 template <typename T>
 __global__ void __launch_bounds__(128)
 block_solve_kernel(const int64_t* __restrict__ inv_off, const int32_t* __restrict__ dofs_off,
@@ -236,19 +309,18 @@ block_solve_kernel(const int64_t* __restrict__ inv_off, const int32_t* __restric
   pdl_entry();
   extern __shared__ unsigned char smem_raw[];
   T* sr = reinterpret_cast<T*>(smem_raw);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
     const int d = __ldg(dim + b);
     const int32_t* ds = dofs + __ldg(dofs_off + b);
     for (int m = threadIdx.x; m < d; m += blockDim.x) sr[m] = (T)__ldg(r + __ldg(ds + m));
     __syncthreads();
-    const T* A = inv + __ldg(inv_off + b);
-    for (int l = warp; l < d; l += nw) {
+    // thread l: row l of A_e^-1 (stored column-major: step m reads a contiguous column)
+    const T* At = inv + __ldg(inv_off + b);
+    for (int l = threadIdx.x; l < d; l += blockDim.x) {
       T acc = 0;
-      for (int m = lane; m < d; m += 32) acc += __ldg(A + (int64_t)l * d + m) * sr[m];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) zE[__ldg(dofs_off + b) + l] = acc;
+#pragma unroll 8
+      for (int m = 0; m < d; ++m) acc = fma(__ldg(At + (int64_t)m * d + l), sr[m], acc);
+      zE[__ldg(dofs_off + b) + l] = acc;
     }
     __syncthreads();
   }
@@ -397,7 +469,7 @@ static void precond_impl(const dg_precond& pc, const double* r, double* z, Reduc
   if (pc.n_blocks > 0) {
     DG_CUDA(cudaEventRecord(pc.ev_fork, s));
     DG_CUDA(cudaStreamWaitEvent(pc.side, pc.ev_fork, 0));
-    int g = (int)(pc.n_blocks < 8 * 152 ? pc.n_blocks : 8 * 152);
+    int g = (int)(pc.n_blocks < 16 * 152 ? pc.n_blocks : 16 * 152);
     launch_k(block_solve_kernel<T>, g, 128, (size_t)pc.max_block * sizeof(T), pc.side, 
         pc.blk_inv_off, pc.blk_dofs_off, pc.blk_dim, pc.blk_dofs, (const T*)pc.blk_inv, r,
         (T*)pc.zE, (int)pc.n_blocks);

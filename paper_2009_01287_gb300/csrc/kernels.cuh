@@ -2,6 +2,7 @@
 #pragma once
 
 #include "apply_kernel.cuh"
+#include "apply3_kernel.cuh"
 #include "host_state.h"
 
 namespace dg {
@@ -9,7 +10,9 @@ namespace dg {
 constexpr int kVecThreads = 256;
 constexpr int kVecBlocks = 608;   // 4 x 152 SMs: fixed so reductions are deterministic
 
-int apply_kernel_setup(int form);
+// resident CTAs of the persistent operator kernel of this mesh (sets the
+// kernel's shared-memory opt-in on the current device)
+int apply_kernel_setup(const dg_mesh& M);
 
 ApplyArgs make_apply_args(const dg_mesh& M, const double* x, double* y, Reduce red);
 void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cudaStream_t s);

@@ -98,7 +98,12 @@ void upload_union_precond(dg_precond* pc, const std::vector<InstSrc>& inst, cuda
         el[base + blk[j]] = (int32_t)j;
         dofs.push_back((int32_t)(inst[i].dof_off + blk[j]));
       }
-      inv.insert(inv.end(), H.block_inv[b].begin(), H.block_inv[b].end());
+      // stored transposed (column-major) so that the block-solve threads,
+      // one per output row, read consecutive addresses at every step
+      const size_t d = blk.size(), o = inv.size();
+      inv.resize(o + d * d);
+      for (size_t r = 0; r < d; ++r)
+        for (size_t c = 0; c < d; ++c) inv[o + c * d + r] = (T)H.block_inv[b][r * d + c];
       pc->max_block = std::max<int64_t>(pc->max_block, (int64_t)blk.size());
     }
     nb += (int64_t)H.blocks.size();
