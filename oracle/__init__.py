@@ -12,7 +12,8 @@ Modules
     topology3  sub-faces of a 3D mesh of cubes
     dg         SIPG and BR2 matrices, 2D and 3D (Section 2, Eq. fe-problem; Section 4.4)
     space      conforming prolongation P, V_J / V_e classification (Section 3)
-    lor        low-order-refined matrices (Section 3.4)
+    space3     the same built from master entities, any dimension (cube meshes)
+    lor        low-order-refined matrices (Section 3.4), squares and cubes
     amg        the deterministic smoothed-aggregation V-cycle used for LOR
     solver     the additive preconditioner B and PCG (Section 4.1)
     rhs        load vector of the synthetic sine right-hand side

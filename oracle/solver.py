@@ -49,7 +49,11 @@ def build_operator(mesh, form: str = "sipg", eta: Optional[float] = None,
 def build_problem(mesh, form: str = "sipg", eta: Optional[float] = None,
                   penalty_form: str = "paper", remark_cases: bool = False) -> Problem:
     topo, space, A = build_operator(mesh, form, eta, penalty_form)
-    cs = ConformingSpace(space, remark_cases=remark_cases)
+    if mesh.dim == 3:
+        from .space3 import ConformingSpaceN
+        cs = ConformingSpaceN(space)
+    else:
+        cs = ConformingSpace(space, remark_cases=remark_cases)
     return Problem(topo, space, A, cs)
 
 
