@@ -7,7 +7,8 @@ up), step by step:
 
 setup(A):
   1. if n <= COARSE_MAX: coarsest level, dense inverse.
-  2. strength: j != i is strong for i when a_ij^2 > THETA^2 a_ii a_jj.
+  2. strength: j != i is strong for i when a_ij^2 > theta^2 a_ii a_jj
+     (theta = THETA on squares, THETA3 on cubes).
   3. aggregation in natural order:
      pass 1: i unaggregated, has a strong neighbour, and all its strong
              neighbours unaggregated -> new aggregate {i} + strong neighbours;
@@ -33,7 +34,8 @@ from typing import List
 import numpy as np
 import scipy.sparse as sp
 
-THETA = 0.08
+THETA = 0.08          # squares: the Q1 9-point stencil's links are strong
+THETA3 = 0.02         # cubes: the trilinear 27-point stencil's links are ~1/32 of the diagonal
 COARSE_MAX = 256
 MAX_LEVELS = 12
 
@@ -48,21 +50,21 @@ class Level:
         self.Ainv = None
 
 
-def strength_lists(A: sp.csr_matrix) -> List[np.ndarray]:
+def strength_lists(A: sp.csr_matrix, theta: float = THETA) -> List[np.ndarray]:
     d = A.diagonal()
     out = []
     for i in range(A.shape[0]):
         cols = A.indices[A.indptr[i]:A.indptr[i + 1]]
         vals = A.data[A.indptr[i]:A.indptr[i + 1]]
         keep = [(c, v) for c, v in zip(cols, vals)
-                if c != i and v * v > THETA * THETA * d[i] * d[c]]
+                if c != i and v * v > theta * theta * d[i] * d[c]]
         out.append(np.asarray(sorted(c for c, _ in keep), dtype=np.int64))
     return out
 
 
-def aggregate(A: sp.csr_matrix) -> np.ndarray:
+def aggregate(A: sp.csr_matrix, theta: float = THETA) -> np.ndarray:
     n = A.shape[0]
-    S = strength_lists(A)
+    S = strength_lists(A, theta)
     agg = np.full(n, -1, dtype=np.int64)
     na = 0
     for i in range(n):
@@ -87,13 +89,13 @@ def aggregate(A: sp.csr_matrix) -> np.ndarray:
     return agg
 
 
-def setup(A: sp.csr_matrix) -> List[Level]:
+def setup(A: sp.csr_matrix, theta: float = THETA) -> List[Level]:
     levels = [Level(A)]
     while True:
         L = levels[-1]
         if L.n <= COARSE_MAX or len(levels) >= MAX_LEVELS:
             break
-        agg = aggregate(L.A)
+        agg = aggregate(L.A, theta)
         nc = int(agg.max()) + 1
         if nc >= 0.9 * L.n:
             break

@@ -68,7 +68,7 @@ class Preconditioner:
         if lor == "exact":
             self.Ac_inv = np.linalg.inv(self.Ac.toarray())
         else:
-            self.levels = amg_mod.setup(self.Ac)
+            self.levels = amg_mod.setup(self.Ac, amg_mod.THETA3 if prob.space.dim == 3 else amg_mod.THETA)
         diag = A.diagonal()
         kind = cs.kind.copy()
         if smoother == "jacobi_only":

@@ -129,7 +129,7 @@ static void upload_csr(DevArena& a, const Csr& C, DevCsr& D, cudaStream_t s) {
 template <typename T>
 static void upload_precond(dg_precond* pc, HostPrecond& H, cudaStream_t s) {
   if (pc->lor == DG_LOR_AMG) {
-    AmgHierarchy Hm = amg_setup(H.Ac);
+    AmgHierarchy Hm = amg_setup(H.Ac, pc->mesh->host.dim == 3 ? kAmgTheta3 : kAmgTheta);
     upload_union_precond<T>(pc, {InstSrc{&H, &Hm, 0}}, s);
     return;
   }
@@ -392,9 +392,7 @@ dg_status dg_precond_setup(const dg_mesh* mesh, const dg_options* opts, dg_preco
     DG_REQUIRE(o.precision == DG_PREC_FP64 || o.precision == DG_PREC_MIXED, "unknown precision");
     DG_REQUIRE(o.lor == DG_LOR_EXACT || o.lor == DG_LOR_AMG, "unknown LOR solver");
     DG_REQUIRE(o.smoother == DG_SMOOTHER_FULL || o.smoother == DG_SMOOTHER_JACOBI_ONLY, "unknown smoother");
-    if (mesh->host.dim != 2)
-      throw Error(DG_EUNSUPPORTED, "the preconditioner is built for square meshes only");
-    HostPrecond H = build_host_precond(*mesh, o);
+    HostPrecond H = (mesh->host.dim == 3) ? build_host_precond3(*mesh, o) : build_host_precond(*mesh, o);
     pc = new dg_precond();
     pc->mesh = mesh;
     pc->precision = o.precision;

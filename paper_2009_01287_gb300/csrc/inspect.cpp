@@ -39,10 +39,9 @@ void* dginspect_create(const dg_mesh_desc* desc, const dg_options* opts, int wit
       o.smoother = opts->smoother;
       o.remark_cases = opts->remark_cases;
     }
-    if (I->mesh.host.dim == 2) {
-      I->pc = build_host_precond(I->mesh, o);
-      if (with_amg && I->pc.nC > 0) I->amg = amg_setup(I->pc.Ac);
-    }
+    I->pc = (I->mesh.host.dim == 3) ? build_host_precond3(I->mesh, o) : build_host_precond(I->mesh, o);
+    if (with_amg && I->pc.nC > 0)
+      I->amg = amg_setup(I->pc.Ac, I->mesh.host.dim == 3 ? kAmgTheta3 : kAmgTheta);
     return I.release();
   } catch (const std::exception& e) {
     g_err = e.what();

@@ -284,21 +284,41 @@ void host_element_residual3(const dg_mesh& M, int64_t k, const double* x, double
   const double* xk = x + m.off[k];
   const double* T = M.h_tables.data();
   const bool br2 = M.opts.form == DG_FORM_BR2;
-  // volume: h (K x M x M + M x K x M + M x M x K) x, index ix + NP (iy + NP iz)
-  for (int iz = 0; iz < NP; ++iz)
-    for (int iy = 0; iy < NP; ++iy)
+  // volume: h (K x M x M + M x K x M + M x M x K) x, index ix + NP (iy + NP iz),
+  // sum factorised: along z A = M x, Bz = K x; along y C = M A, D = K A + M Bz;
+  // along x y = h (K C + M D)
+  {
+    double A[kMaxN * kMaxN * kMaxN], Bz[kMaxN * kMaxN * kMaxN];
+    double C[kMaxN * kMaxN * kMaxN], D[kMaxN * kMaxN * kMaxN];
+    for (int iz = 0; iz < NP; ++iz)
+      for (int r = 0; r < N2; ++r) {
+        double a = 0.0, b = 0.0;
+        for (int q = 0; q < NP; ++q) {
+          a += B.M[iz * NP + q] * xk[q * N2 + r];
+          b += B.K[iz * NP + q] * xk[q * N2 + r];
+        }
+        A[iz * N2 + r] = a;
+        Bz[iz * N2 + r] = b;
+      }
+    for (int iz = 0; iz < NP; ++iz)
+      for (int iy = 0; iy < NP; ++iy)
+        for (int ix = 0; ix < NP; ++ix) {
+          double c = 0.0, d = 0.0;
+          for (int q = 0; q < NP; ++q) {
+            const double av = A[iz * N2 + q * NP + ix];
+            c += B.M[iy * NP + q] * av;
+            d += B.K[iy * NP + q] * av + B.M[iy * NP + q] * Bz[iz * N2 + q * NP + ix];
+          }
+          C[iz * N2 + iy * NP + ix] = c;
+          D[iz * N2 + iy * NP + ix] = d;
+        }
+    for (int r = 0; r < N3; r += NP)
       for (int ix = 0; ix < NP; ++ix) {
         double v = 0.0;
-        for (int qz = 0; qz < NP; ++qz)
-          for (int qy = 0; qy < NP; ++qy)
-            for (int qx = 0; qx < NP; ++qx) {
-              const double w = B.K[ix * NP + qx] * B.M[iy * NP + qy] * B.M[iz * NP + qz] +
-                               B.M[ix * NP + qx] * B.K[iy * NP + qy] * B.M[iz * NP + qz] +
-                               B.M[ix * NP + qx] * B.M[iy * NP + qy] * B.K[iz * NP + qz];
-              v += w * xk[qx + NP * (qy + NP * qz)];
-            }
-        y[ix + NP * (iy + NP * iz)] = hk * v;
+        for (int q = 0; q < NP; ++q) v += B.K[ix * NP + q] * C[r + q] + B.M[ix * NP + q] * D[r + q];
+        y[r + ix] = hk * v;
       }
+  }
   // traces (value, outward normal derivative) of an element side
   auto trace = [&](int64_t e, int s, std::vector<double>& u, std::vector<double>& dn) {
     const int pe = m.p[e], ne = pe + 1;
@@ -317,19 +337,21 @@ void host_element_residual3(const dg_mesh& M, int64_t k, const double* x, double
       }
   };
   // 2D contraction out[i + ro*j] = sum_{m,n} Ta[i][m] Tb[j][n] in[m + ci*n]
-  // (table rows of length ca / cb; `tr` reads the tables transposed)
+  // (table rows of length ci; `tr` reads the tables transposed), in two passes
   auto contract = [&](int ta, int tb, int ro, int ci, bool tr, const std::vector<double>& in,
                       std::vector<double>& out) {
+    double w[kMaxN * kMaxN];
+    for (int nn = 0; nn < ci; ++nn)
+      for (int i = 0; i < ro; ++i) {
+        double v = 0.0;
+        for (int mm = 0; mm < ci; ++mm) v += (tr ? T[ta + mm * ro + i] : T[ta + i * ci + mm]) * in[mm + ci * nn];
+        w[i + ro * nn] = v;
+      }
     out.assign(ro * ro, 0.0);
     for (int j = 0; j < ro; ++j)
       for (int i = 0; i < ro; ++i) {
         double v = 0.0;
-        for (int nn = 0; nn < ci; ++nn)
-          for (int mm = 0; mm < ci; ++mm) {
-            const double a = tr ? T[ta + mm * ro + i] : T[ta + i * ci + mm];
-            const double b = tr ? T[tb + nn * ro + j] : T[tb + j * ci + nn];
-            v += a * b * in[mm + ci * nn];
-          }
+        for (int nn = 0; nn < ci; ++nn) v += (tr ? T[tb + nn * ro + j] : T[tb + j * ci + nn]) * w[i + ro * nn];
         out[i + ro * j] = v;
       }
   };

@@ -21,5 +21,7 @@ struct HostPrecond {
 };
 
 HostPrecond build_host_precond(const dg_mesh& M, const dg_options& o);
+// the same on cube meshes (master-entity construction)
+HostPrecond build_host_precond3(const dg_mesh& M, const dg_options& o);
 
 }  // namespace dg

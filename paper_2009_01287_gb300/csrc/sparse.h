@@ -38,11 +38,13 @@ struct AmgHierarchy {
   std::vector<double> coarse_inv;  // dense inverse of the last level (row-major)
 };
 
-constexpr double kAmgTheta = 0.08;
+constexpr double kAmgTheta = 0.08;    // squares: the Q1 9-point stencil's links are strong
+constexpr double kAmgTheta3 = 0.02;   // cubes: trilinear 27-point links are ~1/32 of the diagonal
 constexpr int kAmgCoarseMax = 256;
 constexpr int kAmgMaxLevels = 12;
+constexpr int kAmgDenseMax = 8192;    // largest coarsest level inverted densely
 
-AmgHierarchy amg_setup(const Csr& A);
+AmgHierarchy amg_setup(const Csr& A, double theta = kAmgTheta);
 void dense_inverse_spd(int n, std::vector<double>& a);  // in place, Cholesky based
 
 }  // namespace dg

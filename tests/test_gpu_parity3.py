@@ -1,7 +1,9 @@
-"""GPU parity on cube meshes: the 3D operator (through the C ABI) against the
-FP64 oracle, to 1e-12 relative (max-norm of the difference over the max-norm
-of the oracle result), on hanging hp meshes, at degrees up to 8, and on the
-full 3D hp-random workload (sampled elements); the load vector likewise."""
+"""GPU parity on cube meshes (through the C ABI) against the FP64 oracle: the
+3D operator and the FP64 preconditioner to 1e-12 relative (max-norm of the
+difference over the max-norm of the oracle result) on hanging hp meshes, at
+degrees up to 8, and on the full 3D hp-random workload (sampled elements); the
+load vector likewise; PCG iterations within +-1 of the oracle, the mixed
+FP32-preconditioner path within +10% of FP64; a full-size 3D solve."""
 import numpy as np
 import pytest
 
@@ -65,12 +67,68 @@ def test_rhs3_parity(built_lib, torch_mod):
     assert rel(bd.cpu().numpy(), rhs.load_vector(space, r.amps, r.waves)) <= 1e-12
 
 
-def test_precond3_unsupported(built_lib, torch_mod):
+PC3 = ["hp0", "hp1", "ragged"]
+
+
+def _opts3(B, form, **kw):
+    return B.make_options(form=B.DG_FORM_BR2 if form == "br2" else B.DG_FORM_SIPG, **kw)
+
+
+@pytest.mark.parametrize("lor", ["exact", "amg"])
+@pytest.mark.parametrize("name", PC3)
+def test_precond3_parity_fp64(built_lib, torch_mod, name, lor):
+    mesh = MESHES3[name]()
+    prob = solver.build_problem(mesh)
+    opc = solver.Preconditioner(prob, lor=lor)
     B = built_lib
-    M = B.Mesh(MESHES3["hp0"]())
-    with pytest.raises(B.DGError) as e:
-        B.Precond(M)
-    assert e.value.code == B.DG_EUNSUPPORTED
+    o = _opts3(B, "sipg", lor=B.DG_LOR_EXACT if lor == "exact" else B.DG_LOR_AMG)
+    M = B.Mesh(mesh, o)
+    pc = B.Precond(M, o)
+    r = inputs.random_vector(M.n_dofs, 4)
+    rd = dev(torch_mod, r)
+    zd = torch_mod.empty_like(rd)
+    B.dg_precond_apply(pc.h, rd, zd)
+    torch_mod.cuda.synchronize()
+    assert rel(zd.cpu().numpy(), opc.apply(r)) <= 1e-12
+
+
+@pytest.mark.parametrize("form", ["sipg", "br2"])
+@pytest.mark.parametrize("name", PC3)
+def test_pcg3_iterations_match_oracle(built_lib, torch_mod, name, form):
+    mesh = MESHES3[name]()
+    prob = solver.build_problem(mesh, form=form)
+    opc = solver.Preconditioner(prob, lor="amg")
+    rh = inputs.sine_rhs(3, 0)
+    b = rhs.load_vector(prob.space, rh.amps, rh.waves)
+    tol = 1e-8
+    ref = solver.pcg(prob.A, b, opc.apply, tol, 3000)
+    B = built_lib
+    o = _opts3(B, form)
+    M = B.Mesh(mesh, o)
+    pc = B.Precond(M, o)
+    bd = dev(torch_mod, b)
+    xd = torch_mod.empty_like(bd)
+    info = B.dg_pcg_solve(M.h, pc.h, bd, xd, tol, 3000)
+    assert info.status == 0 and info.rel_res <= tol
+    assert abs(info.iters - ref.iters) <= 1
+    assert rel(xd.cpu().numpy(), ref.x) <= 1e2 * tol
+
+
+@pytest.mark.parametrize("name", ["hp1", "ragged"])
+def test_pcg3_mixed_within_ten_percent(built_lib, torch_mod, name):
+    mesh = MESHES3[name]()
+    B = built_lib
+    M = B.Mesh(mesh, _opts3(B, "br2"))
+    pc64 = B.Precond(M, _opts3(B, "br2"))
+    pc32 = B.Precond(M, _opts3(B, "br2", precision=B.DG_PREC_MIXED))
+    bd = torch_mod.empty(M.n_dofs, dtype=torch_mod.float64, device="cuda")
+    rh = inputs.sine_rhs(3, 1)
+    B.dg_rhs_sine(M.h, rh.amps, rh.waves, bd)
+    x64, x32 = torch_mod.empty_like(bd), torch_mod.empty_like(bd)
+    i64 = B.dg_pcg_solve(M.h, pc64.h, bd, x64, 1e-8, 3000)
+    i32 = B.dg_pcg_solve(M.h, pc32.h, bd, x32, 1e-8, 3000)
+    assert i64.status == 0 and i32.status == 0
+    assert i32.iters <= 1.1 * i64.iters + 1
 
 
 def test_full_size_config2_sampled(built_lib, torch_mod):
@@ -96,3 +154,23 @@ def test_full_size_config2_sampled(built_lib, torch_mod):
         ref = dg.element_rows(space, int(k), x, eta, form="br2")
         got = y[space.offset[k]:space.offset[k + 1]]
         assert rel(got, ref) <= 1e-12, int(k)
+
+
+def test_full_size_config2_solve(built_lib, torch_mod):
+    """Full 3D hp-random workload, BR2, mixed-precision preconditioner with the
+    AMG LOR solve: PCG reaches 1e-8 and the true residual agrees."""
+    mesh, rh = inputs.config2(0)
+    B = built_lib
+    o = B.make_options(form=B.DG_FORM_BR2, precision=B.DG_PREC_MIXED)
+    M = B.Mesh(mesh, o)
+    pc = B.Precond(M, o)
+    bd = torch_mod.empty(M.n_dofs, dtype=torch_mod.float64, device="cuda")
+    B.dg_rhs_sine(M.h, rh.amps, rh.waves, bd)
+    xd = torch_mod.empty_like(bd)
+    info = B.dg_pcg_solve(M.h, pc.h, bd, xd, 1e-8, 5000)
+    assert info.status == 0 and info.rel_res <= 1e-8
+    yd = torch_mod.empty_like(bd)
+    B.dg_apply(M.h, xd, yd)
+    torch_mod.cuda.synchronize()
+    res = float(torch_mod.linalg.norm(bd - yd) / torch_mod.linalg.norm(bd))
+    assert res <= 2e-8

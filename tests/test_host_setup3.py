@@ -28,3 +28,36 @@ def test_host_apply3_matches_oracle(built_lib, name, mk, form):
     x = inputs.random_vector(space.n, 5)
     ya, yb = A @ x, hs.apply(x)
     assert np.abs(ya - yb).max() <= 1e-12 * np.abs(ya).max()
+
+
+PC_CASES = [
+    ("hp0-sipg", lambda: inputs.small_hp_mesh(0, base=2, depth=2, prob=0.3, pmin=1, pmax=3, dim=3), "sipg"),
+    ("hp1-br2", lambda: inputs.small_hp_mesh(1, base=2, depth=2, prob=0.3, pmin=1, pmax=4, dim=3), "br2"),
+    ("hp3-sipg", lambda: inputs.small_hp_mesh(3, base=2, depth=2, prob=0.4, pmin=1, pmax=2, dim=3), "sipg"),
+    ("uniform", lambda: inputs.uniform_mesh(3, 2, 3), "sipg"),
+]
+
+
+@pytest.mark.parametrize("name,mk,form", PC_CASES, ids=[c[0] for c in PC_CASES])
+def test_host_precond3_matches_oracle(built_lib, name, mk, form):
+    """Conforming numbering and P, node classes, V_e blocks, the V_J diagonal
+    (closed form), block inverses, LOR matrix and AMG levels on cube meshes."""
+    B = built_lib
+    mesh = mk()
+    prob = solver.build_problem(mesh, form=form)
+    hs = B.HostSetup(mesh, B.make_options(form=B.DG_FORM_BR2 if form == "br2" else B.DG_FORM_SIPG))
+    cs = prob.cs
+    assert hs.nC == cs.n
+    assert abs(cs.P - hs.P).max() < 1e-13
+    assert np.array_equal(cs.kind, hs.kind)
+    assert len(hs.blocks) == len(cs.blocks)
+    assert all(np.array_equal(a, b) for a, b in zip(cs.blocks, hs.blocks))
+    pc = solver.Preconditioner(prob, lor="amg")
+    assert abs(pc.Ac - hs.Ac).max() <= 1e-13 * abs(pc.Ac).max()
+    d = np.where(pc.jmask, pc.dinv, 0.0)
+    assert np.abs(d - hs.dinv).max() <= 1e-12 * np.abs(d).max()
+    for a, b in zip(pc.block_inv, hs.block_inv):
+        assert np.abs(a - b).max() <= 1e-10 * np.abs(a).max()
+    assert [L.n for L in pc.levels] == [l.shape[0] for l in hs.levels]
+    for L, l in zip(pc.levels, hs.levels):
+        assert abs(L.A - l).max() <= 1e-11 * abs(L.A).max()
