@@ -32,6 +32,9 @@ if ROOT not in sys.path:
 
 WORKLOAD = "2D hp-random 32x32 base, prob 0.3, depth<=3, p~U{1..6}, SIPG eta=100, tol 1e-8, seed 0"
 METRIC = "DOF-iters/s (PCG on the 2D hp-random workload, mixed FP32 preconditioner / FP64 outer)"
+WORKLOAD3 = ("3D hp-random 16^3 base, prob 0.2, depth<=2, p~U{1..5}, BR2 (eta = most sub-faces of one "
+             "element), tol 1e-8, seed 0")
+METRIC3 = "DOF-iters/s (PCG on the 3D hp-random workload, mixed FP32 preconditioner / FP64 outer)"
 ORACLE_SAMPLE_ITERS = 20
 
 # DRAM bytes (read + write) of one apply_kernel launch on this workload, from
@@ -43,13 +46,21 @@ APPLY_TRAFFIC = {"sources": ["paper_2009_01287_gb300/csrc/apply_kernel.cuh",
                  "sha256_16": "d56ec2b850b82c8f", "bytes": 3259904 + 0}
 
 
-def apply_traffic():
+APPLY3_TRAFFIC = {"sources": ["paper_2009_01287_gb300/csrc/apply3_kernel.cuh",
+                              "paper_2009_01287_gb300/csrc/kernels.cu"],
+                  "sha256_16": None, "bytes": None}
+
+
+def apply_traffic(three: bool = False):
     import hashlib
+    rec = APPLY3_TRAFFIC if three else APPLY_TRAFFIC
+    if rec["bytes"] is None:
+        return None
     h = hashlib.sha256()
-    for f in APPLY_TRAFFIC["sources"]:
+    for f in rec["sources"]:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
-    return APPLY_TRAFFIC["bytes"] if h.hexdigest()[:16] == APPLY_TRAFFIC["sha256_16"] else None
+    return rec["bytes"] if h.hexdigest()[:16] == rec["sha256_16"] else None
 
 
 def _dist():
@@ -135,9 +146,11 @@ def run_ours(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    mesh, rh = inputs.config1(args.seed)
-    opts64 = B.make_options(precision=B.DG_PREC_FP64, lor=B.DG_LOR_AMG)
-    opts32 = B.make_options(precision=B.DG_PREC_MIXED, lor=B.DG_LOR_AMG)
+    three = args.workload == "hp3d"
+    mesh, rh = inputs.config2(args.seed) if three else inputs.config1(args.seed)
+    form = B.DG_FORM_BR2 if three else B.DG_FORM_SIPG
+    opts64 = B.make_options(form=form, precision=B.DG_PREC_FP64, lor=B.DG_LOR_AMG)
+    opts32 = B.make_options(form=form, precision=B.DG_PREC_MIXED, lor=B.DG_LOR_AMG)
     M = B.Mesh(mesh, opts64, stream)
     t0 = time.perf_counter()
     pc32 = B.Precond(M, opts32)
@@ -217,7 +230,7 @@ def run_ours(args):
     kernels_per_iter = 1 + 1 + (1 + 4 * (levels - 1) + 1 + 1) + 1 + 1
     launches = sum(4 + 2 * levels + it * kernels_per_iter for it in it32)  # init + first precond
     out = {
-        "metric": METRIC,
+        "metric": METRIC3 if three else METRIC,
         "value": value,
         "unit": "DOF-iters/s",
         "n_gpus": ws,
@@ -229,7 +242,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f64 (outer PCG, operator) + f32 (preconditioner)",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_dofs": n, "n_elems": int(stats.n_elems),
+        "config": {"workload": WORKLOAD3 if three else WORKLOAD, "n_dofs": n, "n_elems": int(stats.n_elems),
                    "n_conforming": int(s32.n_conforming), "amg_levels": levels,
                    "n_blocks": int(s32.n_blocks), "max_block": int(s32.max_block),
                    "parallelism": f"replicas x{ws}", "l2": "flushed (512 MiB write) before every step"},
@@ -241,9 +254,10 @@ def run_ours(args):
         "setup_s": setup_s,
         "e2e": {"value": ws * n * sum(it_e2e) / te, "unit": "DOF-iters/s",
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
-        "roofline": {"kernel": "apply_kernel (SIPG operator, FP64)", "bound": "alu",
+        "roofline": {"kernel": ("apply3_kernel (BR2 operator on cubes, FP64)" if three
+                                else "apply_kernel (SIPG operator, FP64)"), "bound": "alu",
                      "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": achieved_tf / fp64_peak, "traffic": apply_traffic(),
+                     "frac": achieved_tf / fp64_peak, "traffic": apply_traffic(three),
                      "algorithmic_bytes": stats.apply_bytes,
                      "flops_per_launch": stats.apply_flops, "launch_ms": apply_ms,
                      "hbm_gbs": stats.apply_bytes / (apply_ms / 1e3) / 1e9,
@@ -253,7 +267,7 @@ def run_ours(args):
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        out["cpu_baseline"] = cpu_baseline(args)
+        out["cpu_baseline"] = cpu_baseline3(args) if three else cpu_baseline(args)
     if rank == 0:
         print(json.dumps(out))
     if dist:
@@ -413,6 +427,23 @@ def _oracle_step(prob, pc, b, iters: int) -> float:
     return time.perf_counter() - t
 
 
+def cpu_baseline3(args):
+    """The oracle on a bounded sample of the 3D workload: the same refinement
+    and degree recipe on a 4^3 base (25k DOFs; the full 16^3 mesh is beyond the
+    oracle's setup), FP64 PCG iterations, one thread."""
+    from oracle import rhs, solver
+    from paper_2009_01287_gb300 import inputs
+    mesh, rh = inputs.config2(args.seed, base=4)
+    prob = solver.build_problem(mesh, form="br2")
+    pc = solver.Preconditioner(prob, lor="amg")
+    b = rhs.load_vector(prob.space, rh.amps, rh.waves)
+    dt = _oracle_step(prob, pc, b, ORACLE_SAMPLE_ITERS)
+    return {"value": prob.space.n * ORACLE_SAMPLE_ITERS / dt, "unit": "DOF-iters/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{ORACLE_SAMPLE_ITERS} FP64 PCG iterations on the same recipe with a 4^3 base "
+                      f"({prob.space.n} DOFs; setup untimed), scipy sparse + numpy, one thread"}
+
+
 def cpu_baseline(args):
     prob, pc, b = _oracle_setup(args.seed)
     dt = _oracle_step(prob, pc, b, ORACLE_SAMPLE_ITERS)
@@ -463,7 +494,7 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="hp2d", choices=["hp2d", "batched", "serving"])
+    ap.add_argument("--workload", default="hp2d", choices=["hp2d", "hp3d", "batched", "serving"])
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-meshes", type=int, default=16)
