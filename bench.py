@@ -46,9 +46,10 @@ APPLY_TRAFFIC = {"sources": ["paper_2009_01287_gb300/csrc/apply_kernel.cuh",
                  "sha256_16": "d56ec2b850b82c8f", "bytes": 3259904 + 0}
 
 
+# likewise for the 3D operator (profiles/apply3_kernel_hp3d_16cube.md)
 APPLY3_TRAFFIC = {"sources": ["paper_2009_01287_gb300/csrc/apply3_kernel.cuh",
                               "paper_2009_01287_gb300/csrc/kernels.cu"],
-                  "sha256_16": None, "bytes": None}
+                  "sha256_16": "02c1a23d67bf7188", "bytes": 57317376 + 1885952}
 
 
 def apply_traffic(three: bool = False):
