@@ -20,7 +20,12 @@
 //            becomes eta/4 area [M_oo G_o jo + M_on G_n jn] with the jump
 //            projections jo = area (a - b), jn = area (M_no u- - M_nn u+) and
 //            G = h^-3 Minv_00 (Minv x Minv), the side block of the element mass
-//            inverse (boundary: eta area M_oo G_o jo);
+//            inverse (boundary: eta area M_oo G_o jo).  Multiplied out per axis
+//            it is cz [(Z x Z) u- - (V x V) u+] + cx [(X x X) u- - (Y x Y) u+]
+//            with the 1D products Z = M_oo Minv M_oo, V = M_oo Minv M_on,
+//            X = M_on Minv_n M_no, Y = M_on Minv_n M_nn and the scalars
+//            cz, cx = eta/4 area^2 Minv_00 / h^3 of the two elements, so BR2
+//            takes the same two passes per round as SIPG;
 //    gather  volume pass along x, side residuals and the normal-derivative
 //            terms c2 (x) dn(v) of all six sides.
 // Each sub-face is evaluated from both of its sides (no atomics): applies are
@@ -152,169 +157,111 @@ __device__ __forceinline__ void apply3_tile(const ApplyArgs& A, const ApplyTile&
       const double2* trk = reinterpret_cast<const double2*>(A.tr + A.toff[k]) + s * N2;
       if (i < NP && n < NP) {
         const double* Ma = tab + f.tab_oo[0] + i * NP;
-        double wa = 0.0, wc = 0.0;
+        const double* Za = tab + f.tab_z[0] + i * NP;
+        const double* Xa = tab + f.tab_x[0] + i * NP;
+        double wa = 0.0, wc = 0.0, wz = 0.0, wx = 0.0;
 #pragma unroll
         for (int m = 0; m < NP; ++m) {
           const double2 v = trk[n * NP + m];
           const double w = __ldg(Ma + m);
           wa = fma(w, v.x, wa);
           wc = fma(w, v.y, wc);
+          if (BR2) {
+            wz = fma(__ldg(Za + m), v.x, wz);
+            if (in) wx = fma(__ldg(Xa + m), v.x, wx);
+          }
         }
         W[0 * Q2 + i * NQ + n] = wa;
         W[1 * Q2 + i * NQ + n] = wc;
+        if (BR2) {
+          W[4 * Q2 + i * NQ + n] = wz;
+          W[5 * Q2 + i * NQ + n] = wx;
+        }
       }
       if (!in) continue;
       const double2* trn = reinterpret_cast<const double2*>(A.tr + A.toff[f.nb]) + f.nb_side * np * np;
       if (i < NP && n < np) {
         const double* Ma = tab + f.tab_on[0] + i * np;
-        double wb = 0.0, wd = 0.0;
+        const double* Va = tab + f.tab_v[0] + i * np;
+        const double* Ya = tab + f.tab_y[0] + i * np;
+        double wb = 0.0, wd = 0.0, wv = 0.0, wy = 0.0;
         for (int m = 0; m < np; ++m) {
           const double2 v = trn[n * np + m];
           const double w = __ldg(Ma + m);
           wb = fma(w, v.x, wb);
           wd = fma(w, v.y, wd);
+          if (BR2) {
+            wv = fma(__ldg(Va + m), v.x, wv);
+            wy = fma(__ldg(Ya + m), v.x, wy);
+          }
         }
         W[2 * Q2 + i * NQ + n] = wb;
         W[3 * Q2 + i * NQ + n] = wd;
-      }
-      if (BR2 && i < np) {
-        if (n < NP) {
-          double w1 = 0.0;
-#pragma unroll
-          for (int m = 0; m < NP; ++m) w1 = fma(__ldg(tab + f.tab_on[0] + m * np + i), trk[n * NP + m].x, w1);
-          W[4 * Q2 + i * NQ + n] = w1;
-        }
-        if (n < np) {
-          double w2 = 0.0;
-          for (int m = 0; m < np; ++m) w2 = fma(__ldg(tab + f.tab_nn[0] + i * np + m), trn[n * np + m].x, w2);
-          W[5 * Q2 + i * NQ + n] = w2;
+        if (BR2) {
+          W[6 * Q2 + i * NQ + n] = wv;
+          W[7 * Q2 + i * NQ + n] = wy;
         }
       }
     }
     __syncthreads();
-    // P2: contractions along the second tangential axis; SIPG terms, jumps
+    // P2: contractions along the second tangential axis and the side terms
     for (int t = tid; t < nface; t += blockDim.x) {
       const int es = t / Q2, q = t - es * Q2;
       const int e = es / 6, s = es - e * 6;
       const int i = q % NQ, jj = q / NQ;
+      if (i >= NP || jj >= NP) continue;
       const int k = A.order[T.first + e];
       const int b0 = A.sf_ptr[6 * k + s];
       if (j >= A.sf_ptr[6 * k + s + 1] - b0) continue;
       const SubFaceRec3& f = A.sf3[b0 + j];
       const int np = f.pn + 1;
       const bool in = f.nb >= 0;
-      double* W = sw + es * S * Q2;
+      const double* W = sw + es * S * Q2;
       const double ar = f.area;
-      if (i < NP && jj < NP) {
-        const double* Mb = tab + f.tab_oo[1] + jj * NP;
-        double a = 0.0, c = 0.0, b = 0.0, d = 0.0;
+      const double* Mb = tab + f.tab_oo[1] + jj * NP;
+      const double* Zb = tab + f.tab_z[1] + jj * NP;
+      const double* Xb = tab + f.tab_x[1] + jj * NP;
+      double a = 0.0, c = 0.0, b = 0.0, d = 0.0, zz = 0.0, xx = 0.0, vv = 0.0, yy = 0.0;
 #pragma unroll
-        for (int n = 0; n < NP; ++n) {
-          const double w = __ldg(Mb + n);
-          a = fma(w, W[0 * Q2 + i * NQ + n], a);
-          c = fma(w, W[1 * Q2 + i * NQ + n], c);
+      for (int n = 0; n < NP; ++n) {
+        const double w = __ldg(Mb + n);
+        a = fma(w, W[0 * Q2 + i * NQ + n], a);
+        c = fma(w, W[1 * Q2 + i * NQ + n], c);
+        if (BR2) {
+          zz = fma(__ldg(Zb + n), W[4 * Q2 + i * NQ + n], zz);
+          if (in) xx = fma(__ldg(Xb + n), W[5 * Q2 + i * NQ + n], xx);
         }
-        if (in) {
-          const double* Mbn = tab + f.tab_on[1] + jj * np;
-          for (int n = 0; n < np; ++n) {
-            const double w = __ldg(Mbn + n);
-            b = fma(w, W[2 * Q2 + i * NQ + n], b);
-            d = fma(w, W[3 * Q2 + i * NQ + n], d);
+      }
+      if (in) {
+        const double* Mbn = tab + f.tab_on[1] + jj * np;
+        const double* Vb = tab + f.tab_v[1] + jj * np;
+        const double* Yb = tab + f.tab_y[1] + jj * np;
+        for (int n = 0; n < np; ++n) {
+          const double w = __ldg(Mbn + n);
+          b = fma(w, W[2 * Q2 + i * NQ + n], b);
+          d = fma(w, W[3 * Q2 + i * NQ + n], d);
+          if (BR2) {
+            vv = fma(__ldg(Vb + n), W[6 * Q2 + i * NQ + n], vv);
+            yy = fma(__ldg(Yb + n), W[7 * Q2 + i * NQ + n], yy);
           }
         }
-        const int o = es * N2 + jj * NP + i;
-        const double jmp = a - b;
-        double rr, cc;
-        if (in) {
-          rr = -0.5 * ar * (c - d);
-          cc = -0.5 * ar * jmp;
-        } else {
-          rr = -ar * c;
-          cc = -ar * a;
-        }
-        if (!BR2) rr = fma(f.sigma * ar, jmp, rr);
-        sr[o] += rr;
-        sc2[o] += cc;
-        if (BR2) W[6 * Q2 + i * NQ + jj] = ar * jmp;
       }
-      if (BR2 && in && i < np && jj < np) {
-        double v = 0.0;
-#pragma unroll
-        for (int n = 0; n < NP; ++n) v = fma(__ldg(tab + f.tab_on[1] + n * np + jj), W[4 * Q2 + i * NQ + n], v);
-        for (int n = 0; n < np; ++n) v = fma(-__ldg(tab + f.tab_nn[1] + jj * np + n), W[5 * Q2 + i * NQ + n], v);
-        W[7 * Q2 + i * NQ + jj] = ar * v;
+      const int o = es * N2 + jj * NP + i;
+      const double jmp = a - b;
+      double rr, cc;
+      if (in) {
+        rr = -0.5 * ar * (c - d);
+        cc = -0.5 * ar * jmp;
+      } else {
+        rr = -ar * c;
+        cc = -ar * a;
       }
+      if (BR2) rr += f.cz * (zz - vv) + f.cx * (xx - yy);
+      else rr = fma(f.sigma * ar, jmp, rr);
+      sr[o] += rr;
+      sc2[o] += cc;
     }
     __syncthreads();
-    if (!BR2) continue;
-    // P3..P6 (BR2): G = side block of the mass inverse on both elements, then
-    // the face mass back onto this element's side nodes
-    for (int ph = 3; ph <= 6; ++ph) {
-      for (int t = tid; t < nface; t += blockDim.x) {
-        const int es = t / Q2, q = t - es * Q2;
-        const int e = es / 6, s = es - e * 6;
-        const int i = q % NQ, n = q / NQ;
-        const int k = A.order[T.first + e];
-        const int b0 = A.sf_ptr[6 * k + s];
-        if (j >= A.sf_ptr[6 * k + s + 1] - b0) continue;
-        const SubFaceRec3& f = A.sf3[b0 + j];
-        const int np = f.pn + 1;
-        const bool in = f.nb >= 0;
-        double* W = sw + es * S * Q2;
-        const double* Mi = tab + bo.Minv;
-        const double* Min = tab + A.boff[f.pn].Minv;
-        if (ph == 3) {          // t1 = Minv_a jo, t2 = Minvn_a jn
-          if (i < NP && n < NP) {
-            double v = 0.0;
-#pragma unroll
-            for (int m = 0; m < NP; ++m) v = fma(__ldg(Mi + i * NP + m), W[6 * Q2 + m * NQ + n], v);
-            W[0 * Q2 + i * NQ + n] = v;
-          }
-          if (in && i < np && n < np) {
-            double v = 0.0;
-            for (int m = 0; m < np; ++m) v = fma(__ldg(Min + i * np + m), W[7 * Q2 + m * NQ + n], v);
-            W[1 * Q2 + i * NQ + n] = v;
-          }
-        } else if (ph == 4) {   // go = sc t1 Minv_b^T, gn likewise
-          if (i < NP && n < NP) {
-            double v = 0.0;
-#pragma unroll
-            for (int m = 0; m < NP; ++m) v = fma(__ldg(Mi + n * NP + m), W[0 * Q2 + i * NQ + m], v);
-            const double ih = A.ih[k];
-            W[2 * Q2 + i * NQ + n] = v * __ldg(Mi) * ih * ih * ih;
-          }
-          if (in && i < np && n < np) {
-            double v = 0.0;
-            for (int m = 0; m < np; ++m) v = fma(__ldg(Min + n * np + m), W[1 * Q2 + i * NQ + m], v);
-            const double ihn = A.ih[f.nb];
-            W[3 * Q2 + i * NQ + n] = v * __ldg(Min) * ihn * ihn * ihn;
-          }
-        } else if (ph == 5) {   // v1 = Moo_a go, v2 = Mon_a gn
-          if (i < NP && n < NP) {
-            double v = 0.0;
-#pragma unroll
-            for (int m = 0; m < NP; ++m) v = fma(__ldg(tab + f.tab_oo[0] + i * NP + m), W[2 * Q2 + m * NQ + n], v);
-            W[4 * Q2 + i * NQ + n] = v;
-          }
-          if (in && i < NP && n < np) {
-            double v = 0.0;
-            for (int m = 0; m < np; ++m) v = fma(__ldg(tab + f.tab_on[0] + i * np + m), W[3 * Q2 + m * NQ + n], v);
-            W[5 * Q2 + i * NQ + n] = v;
-          }
-        } else {                // residual += eta coef area (v1 Moo_b^T + v2 Mon_b^T)
-          if (i < NP && n < NP) {
-            const int jj = n;
-            double st = 0.0;
-#pragma unroll
-            for (int m = 0; m < NP; ++m) st = fma(__ldg(tab + f.tab_oo[1] + jj * NP + m), W[4 * Q2 + i * NQ + m], st);
-            if (in)
-              for (int m = 0; m < np; ++m) st = fma(__ldg(tab + f.tab_on[1] + jj * np + m), W[5 * Q2 + i * NQ + m], st);
-            sr[es * N2 + jj * NP + i] += A.eta * (in ? 0.25 : 1.0) * f.area * st;
-          }
-        }
-      }
-      __syncthreads();
-    }
   }
   __syncthreads();
   // ---- gather: pass along x, side residuals, normal-derivative terms

@@ -9,10 +9,12 @@
 //  apply_kernel  one CTA per tile of EPB elements of one degree P:
 //    volume  y = (K (x) M + M (x) K) x, sum factorised through shared memory
 //            (Section 4.1: O(p^{d+1}) work per element);
-//    faces   one thread per (element, side, side node) - packed so that the
-//            active lanes fill whole warps - walks the sub-faces of its side.
+//    faces   one thread per (sub-face item, side node) of the tile - the
+//            tile's sub-faces are a flat list, so a side with many hanging
+//            sub-faces does not hold the whole CTA at the next barrier - then
+//            one thread per side node sums its sub-faces in order.
 //            With the exact face mass matrices of the sub-face, M_oo (own-own)
-//            and M_on (own-neighbour), it forms
+//            and M_on (own-neighbour), an item forms
 //              a = M_oo u-, c = M_oo dn-, b = M_on u+, d = M_on dn+
 //            (dn+ along this element's outward normal), and accumulates the
 //            residual of this element's test functions:
@@ -127,6 +129,9 @@ struct ApplyArgs {
   const double* tab;          // basis + face tables
   const int32_t* order;       // degree-sorted element order
   const ApplyTile* tiles;
+  const int2* items;          // square meshes, SIPG: (record, e_local * 4 + s) per sub-face item
+  const int32_t* item_ptr;    // items of tile t: [item_ptr[t], item_ptr[t + 1])
+  const int2* side_items;     // per (order position, side): first item, count
   double eta;                 // BR2 penalty
   double* dot_partial;        // optional reduction of x . y (see Reduce)
   double* dot_out;
@@ -146,6 +151,8 @@ struct ApplyShape {
   // shared doubles: M, K (2 NN) + x, T1, T2 (3 EPB NN) + r, c2 (8 EPB NP)
   // + BR2: jo, go, cd (12 EPB NP), jn, gn (8 EPB kMaxN)
   static constexpr int SMEM = 2 * NN + 3 * EPB * NN + 8 * EPB * NP + 12 * EPB * NP + 8 * EPB * kMaxN;
+  // start (doubles) of the SIPG sub-face item partials: double2, so 16-byte aligned
+  static constexpr int PART = (SMEM + 1) & ~1;
 };
 
 __device__ __forceinline__ int side_node(int s, int i, int k, int np) {
@@ -230,44 +237,61 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& 
     sT1[t] = t1;
     sT2[t] = t2;
   }
-  // ---- faces (SIPG): one thread per side node walks the side's sub-faces
+  // ---- faces (SIPG): one thread per (sub-face item, side node) forms that
+  // sub-face's contribution to the node, then one thread per side node sums
+  // its sub-faces' contributions in sub-face order (deterministic)
   if (!BR2) {
+    const int ib = A.item_ptr[tile];
+    const int nit = A.item_ptr[tile + 1] - ib;
+    double2* part = reinterpret_cast<double2*>(sm + S::PART);   // [nit][NP]
+    for (int t = tid; t < nit * NP; t += blockDim.x) {
+      const int it = t / NP, i = t - it * NP;
+      const int2 item = A.items[ib + it];
+      const SubFaceRec f = A.sf[item.x];
+      const int e = item.y >> 2, s = item.y & 3;
+      const int k = A.order[T.first + e];
+      const double2* trk = reinterpret_cast<const double2*>(A.tr + A.toff[k]) + s * NP;
+      const double* Moo = A.tab + f.tab_oo + i * NP;
+      double a = 0.0, c = 0.0;
+#pragma unroll
+      for (int m = 0; m < NP; ++m) {
+        const double w = __ldg(Moo + m);
+        const double2 v = trk[m];
+        a = fma(w, v.x, a);
+        c = fma(w, v.y, c);
+      }
+      double r, c2;
+      if (f.nb < 0) {
+        r = f.len * (f.sigma * a - c);
+        c2 = -f.len * a;
+      } else {
+        const int np = f.pn + 1;
+        const double* Mon = A.tab + f.tab_on + i * np;
+        const double2* trn = reinterpret_cast<const double2*>(A.tr + A.toff[f.nb]) + f.nb_side * np;
+        double b = 0.0, d = 0.0;
+        for (int m = 0; m < np; ++m) {
+          const double w = __ldg(Mon + m);
+          const double2 v = trn[m];
+          b = fma(w, v.x, b);
+          d = fma(w, v.y, d);   // neighbour's outward dn: this side's dn+ is -v.y
+        }
+        const double jmp = a - b;
+        r = f.len * (f.sigma * jmp - 0.5 * (c - d));
+        c2 = -0.5 * f.len * jmp;
+      }
+      part[t] = make_double2(r, c2);
+    }
+    __syncthreads();
     for (int t = tid; t < nside; t += blockDim.x) {
       const int e = t / (4 * NP);
       const int s = (t / NP) & 3;
       const int i = t % NP;
-      const int k = A.order[T.first + e];
-      const double2* trk = reinterpret_cast<const double2*>(A.tr + A.toff[k]) + s * NP;
+      const int2 si = A.side_items[(int64_t)(T.first + e) * 4 + s];
       double r = 0.0, c2 = 0.0;
-      for (int j = A.sf_ptr[4 * k + s]; j < A.sf_ptr[4 * k + s + 1]; ++j) {
-        const SubFaceRec f = A.sf[j];
-        const double* Moo = A.tab + f.tab_oo + i * NP;
-        double a = 0.0, c = 0.0;
-#pragma unroll
-        for (int m = 0; m < NP; ++m) {
-          const double w = __ldg(Moo + m);
-          const double2 v = trk[m];
-          a = fma(w, v.x, a);
-          c = fma(w, v.y, c);
-        }
-        if (f.nb < 0) {
-          r += f.len * (f.sigma * a - c);
-          c2 -= f.len * a;
-        } else {
-          const int np = f.pn + 1;
-          const double* Mon = A.tab + f.tab_on + i * np;
-          const double2* trn = reinterpret_cast<const double2*>(A.tr + A.toff[f.nb]) + f.nb_side * np;
-          double b = 0.0, d = 0.0;
-          for (int m = 0; m < np; ++m) {
-            const double w = __ldg(Mon + m);
-            const double2 v = trn[m];
-            b = fma(w, v.x, b);
-            d = fma(w, v.y, d);   // neighbour's outward dn: this side's dn+ is -v.y
-          }
-          const double jmp = a - b;
-          r += f.len * (f.sigma * jmp - 0.5 * (c - d));
-          c2 -= 0.5 * f.len * jmp;
-        }
+      for (int j = 0; j < si.y; ++j) {
+        const double2 v = part[(si.x - ib + j) * NP + i];
+        r += v.x;
+        c2 += v.y;
       }
       sr[t] = r;
       sc2[t] = c2;

@@ -295,6 +295,7 @@ static void build_union_mesh(dg_batch* B, cudaStream_t s) {
   }
   U.h_order = order;
   U.n_tiles = (int)U.h_tiles.size();
+  build_face_items(&U);
   upload_mesh(&U, s);
 }
 

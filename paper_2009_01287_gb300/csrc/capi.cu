@@ -42,6 +42,7 @@ static void build_mesh(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* o
 
 void upload_mesh(dg_mesh* M, cudaStream_t s) {
   const HostMesh& m = M->host;
+  M->apply_smem = apply_smem_for(*M);
   M->apply_grid = apply_kernel_setup(*M);
   // upload
   DevArena& a = M->arena;
@@ -66,6 +67,9 @@ void upload_mesh(dg_mesh* M, cudaStream_t s) {
   M->d_tables = a.upload(M->h_tables, s);
   M->d_order = a.upload(M->h_order, s);
   M->d_tiles = a.upload(M->h_tiles, s);
+  M->d_items = a.upload(M->h_items, s);
+  M->d_item_ptr = a.upload(M->h_item_ptr, s);
+  M->d_side_items = a.upload(M->h_side_items, s);
   M->d_sched = a.alloc<unsigned>(2);
   DG_CUDA(cudaMemsetAsync(M->d_sched, 0, 2 * sizeof(unsigned), s));
   DG_CUDA(cudaStreamSynchronize(s));

@@ -81,8 +81,12 @@ struct SubFaceRec3 {
   int32_t tab_oo[2]; // own-own 1D face mass per tangential axis ((p+1)^2)
   int32_t tab_on[2]; // own-neighbour ((p+1) x (pn+1))
   int32_t tab_nn[2]; // neighbour-neighbour ((pn+1)^2)
+  // BR2 lifting products per tangential axis (Minv: 1D mass inverse):
+  //   Z = M_oo Minv M_oo, V = M_oo Minv M_on, X = M_on Minv_n M_no, Y = M_on Minv_n M_nn
+  int32_t tab_z[2], tab_v[2], tab_x[2], tab_y[2];
   double sigma;      // SIPG penalty
   double area;       // physical area of the sub-face
+  double cz, cx;     // BR2: eta coef area^2 Minv_00 / h^3 of the own / neighbour element
 };
 
 // Shared-memory budget (doubles) of one 3D operator tile; the host sizes the

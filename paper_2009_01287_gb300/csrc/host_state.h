@@ -80,6 +80,13 @@ struct dg_mesh {
   dg::BasisOff boff[dg::kMaxP + 1];
   std::vector<dg::ApplyTile> h_tiles;
   std::vector<int32_t> h_order;      // degree-sorted element order
+  // square meshes, SIPG: the sub-face work of every tile as a flat list of
+  // (record, tile-local side) items, and per element side (in tile order) the
+  // first item and the item count
+  std::vector<int32_t> h_items;       // 2 per item: record index, e_local * 4 + s
+  std::vector<int32_t> h_item_ptr;    // n_tiles + 1
+  std::vector<int32_t> h_side_items;  // 2 per (order position, side): first item, count
+  int64_t apply_smem = 0;             // dynamic shared memory of the 2D operator kernel
   // device
   dg::DevArena arena;
   int32_t* d_p = nullptr;
@@ -94,6 +101,9 @@ struct dg_mesh {
   double* d_tables = nullptr;
   int32_t* d_order = nullptr;
   dg::ApplyTile* d_tiles = nullptr;
+  int32_t* d_items = nullptr;
+  int32_t* d_item_ptr = nullptr;
+  int32_t* d_side_items = nullptr;
   int n_tiles = 0;
   unsigned* d_sched = nullptr;  // operator tile counter + exit ticket
   int apply_grid = 1;           // resident CTAs of the persistent operator kernel
@@ -144,6 +154,8 @@ namespace dg {
 void build_mesh_host(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opts);
 // degree-sorted element order and operator tiles from M->host.p
 void build_tiles(dg_mesh* M);
+// flat sub-face item lists of the tiles (square meshes; after the tiles)
+void build_face_items(dg_mesh* M);
 // upload the host-built operator data (M->host.p/off/sf_ptr, h_* arrays)
 void upload_mesh(dg_mesh* M, cudaStream_t s);
 // cube meshes: topology, records, tables, tiles, stats (opts already validated)

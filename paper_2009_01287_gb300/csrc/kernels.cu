@@ -55,7 +55,7 @@ __device__ __forceinline__ void apply_exit(const ApplyArgs& A, double* red) {
 template <bool BR2>
 __global__ void __launch_bounds__(kThreads) apply_kernel(const ApplyArgs A) {
   pdl_entry();
-  extern __shared__ double smem[];
+  extern __shared__ __align__(16) double smem[];
   __shared__ double red[kThreads];
   __shared__ int s_tile;
   while (true) {
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kThreads) trace3_kernel(const ApplyArgs A) {
 template <bool BR2>
 __global__ void __launch_bounds__(kThreads) apply3_kernel(const ApplyArgs A) {
   pdl_entry();
-  extern __shared__ double smem[];
+  extern __shared__ __align__(16) double smem[];
   __shared__ double red[kThreads];
   __shared__ int s_tile;
   while (true) {
@@ -127,16 +127,30 @@ __global__ void __launch_bounds__(kThreads) apply3_kernel(const ApplyArgs A) {
   apply_exit(A, red);
 }
 
-static int apply_smem_bytes() {
-  int m = ApplyShape<1>::SMEM;
-  m = m > ApplyShape<2>::SMEM ? m : ApplyShape<2>::SMEM;
-  m = m > ApplyShape<3>::SMEM ? m : ApplyShape<3>::SMEM;
-  m = m > ApplyShape<4>::SMEM ? m : ApplyShape<4>::SMEM;
-  m = m > ApplyShape<5>::SMEM ? m : ApplyShape<5>::SMEM;
-  m = m > ApplyShape<6>::SMEM ? m : ApplyShape<6>::SMEM;
-  m = m > ApplyShape<7>::SMEM ? m : ApplyShape<7>::SMEM;
-  m = m > ApplyShape<8>::SMEM ? m : ApplyShape<8>::SMEM;
-  return m * (int)sizeof(double);
+// static shared-memory layout of a degree-p tile up to the item partials (doubles)
+static int apply_shape_smem(int p) {
+  switch (p) {
+    case 1: return ApplyShape<1>::PART;
+    case 2: return ApplyShape<2>::PART;
+    case 3: return ApplyShape<3>::PART;
+    case 4: return ApplyShape<4>::PART;
+    case 5: return ApplyShape<5>::PART;
+    case 6: return ApplyShape<6>::PART;
+    case 7: return ApplyShape<7>::PART;
+    default: return ApplyShape<8>::PART;
+  }
+}
+
+int64_t apply_smem_for(const dg_mesh& M) {
+  if (M.host.dim == 3) return M.apply3_smem;
+  // the layout of the tile's degree plus its sub-face item partials
+  int64_t mx = 0;
+  for (int t = 0; t < M.n_tiles; ++t) {
+    const ApplyTile& T = M.h_tiles[t];
+    const int64_t nit = M.h_item_ptr.empty() ? 0 : M.h_item_ptr[t + 1] - M.h_item_ptr[t];
+    mx = std::max<int64_t>(mx, apply_shape_smem(T.p) + 2 * nit * (T.p + 1));
+  }
+  return 8 * mx;
 }
 
 ApplyArgs make_apply_args(const dg_mesh& M, const double* x, double* y, Reduce red) {
@@ -154,6 +168,9 @@ ApplyArgs make_apply_args(const dg_mesh& M, const double* x, double* y, Reduce r
   A.tab = M.d_tables;
   A.order = M.d_order;
   A.tiles = M.d_tiles;
+  A.items = reinterpret_cast<const int2*>(M.d_items);
+  A.item_ptr = M.d_item_ptr;
+  A.side_items = reinterpret_cast<const int2*>(M.d_side_items);
   A.eta = M.eta;
   A.dot_partial = red.partial;
   A.dot_out = red.out;
@@ -167,23 +184,29 @@ ApplyArgs make_apply_args(const dg_mesh& M, const double* x, double* y, Reduce r
 }
 
 int apply_kernel_setup(const dg_mesh& M) {
-  // the shared-memory opt-in is per device: set it on the current one, and
-  // return the resident capacity (CTAs) of the persistent operator kernel
-  int dev = 0, sms = 0, per = 0;
+  // The shared-memory opt-in is an attribute of the kernel function on the
+  // current device, shared by every mesh: raise it to the device limit (a
+  // mesh's own size could lower it under an earlier mesh's needs), and size the
+  // resident grid of this mesh's persistent launch from its own tile layout.
+  int dev = 0, sms = 0, per = 0, optin = 0;
   DG_CUDA(cudaGetDevice(&dev));
   DG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  DG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  optin -= 4 * 1024;   // room for the kernels' static shared memory
   const bool br2 = M.opts.form == DG_FORM_BR2;
   if (M.host.dim == 3) {
     const int smem = (int)M.apply3_smem;
-    DG_CUDA(cudaFuncSetAttribute(apply3_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    DG_CUDA(cudaFuncSetAttribute(apply3_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    DG_REQUIRE(smem <= optin, "operator tile needs too much shared memory");
+    DG_CUDA(cudaFuncSetAttribute(apply3_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    DG_CUDA(cudaFuncSetAttribute(apply3_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     if (br2) DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, apply3_kernel<true>, kThreads, smem));
     else DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, apply3_kernel<false>, kThreads, smem));
     return sms * (per > 0 ? per : 1);
   }
-  const int smem = apply_smem_bytes();
-  DG_CUDA(cudaFuncSetAttribute(apply_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  DG_CUDA(cudaFuncSetAttribute(apply_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const int smem = (int)M.apply_smem;
+  DG_REQUIRE(smem <= optin, "operator tile needs too much shared memory");
+  DG_CUDA(cudaFuncSetAttribute(apply_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  DG_CUDA(cudaFuncSetAttribute(apply_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   if (br2)
     DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, apply_kernel<true>, kThreads, smem));
   else
@@ -203,7 +226,7 @@ void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cuda
     DG_CUDA(cudaGetLastError());
     return;
   }
-  const int smem = apply_smem_bytes();
+  const int smem = (int)M.apply_smem;
   launch_k(trace_kernel, M.n_tiles, kThreads, 0, s, A);
   if (M.opts.form == DG_FORM_BR2) launch_k(apply_kernel<true>, grid, kThreads, smem, s, A);
   else launch_k(apply_kernel<false>, grid, kThreads, smem, s, A);

@@ -13,6 +13,8 @@ constexpr int kVecBlocks = 608;   // 4 x 152 SMs: fixed so reductions are determ
 // resident CTAs of the persistent operator kernel of this mesh (sets the
 // kernel's shared-memory opt-in on the current device)
 int apply_kernel_setup(const dg_mesh& M);
+// dynamic shared memory of the operator kernel of this mesh (bytes)
+int64_t apply_smem_for(const dg_mesh& M);
 
 ApplyArgs make_apply_args(const dg_mesh& M, const double* x, double* y, Reduce red);
 void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cudaStream_t s);

@@ -220,6 +220,30 @@ void build_tiles(dg_mesh* M) {
   }
   M->n_tiles = (int)M->h_tiles.size();
   M->h_order = order;
+  build_face_items(M);
+}
+
+void build_face_items(dg_mesh* M) {
+  const HostMesh& m = M->host;
+  M->h_items.clear();
+  M->h_item_ptr.assign(1, 0);
+  M->h_side_items.assign(8 * M->h_order.size(), 0);
+  for (const ApplyTile& T : M->h_tiles) {
+    for (int e = 0; e < T.count; ++e) {
+      const int64_t pos = T.first + e;
+      const int32_t k = M->h_order[pos];
+      for (int s = 0; s < 4; ++s) {
+        const int b = m.sf_ptr[4 * (int64_t)k + s], c = m.sf_ptr[4 * (int64_t)k + s + 1] - b;
+        M->h_side_items[8 * pos + 2 * s] = (int32_t)(M->h_items.size() / 2);
+        M->h_side_items[8 * pos + 2 * s + 1] = c;
+        for (int j = 0; j < c; ++j) {
+          M->h_items.push_back(b + j);
+          M->h_items.push_back(4 * e + s);
+        }
+      }
+    }
+    M->h_item_ptr.push_back((int32_t)(M->h_items.size() / 2));
+  }
 }
 
 void build_mesh_host(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opts) {

@@ -9,6 +9,8 @@
 // tangential axis (increasing axis numbers).
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <tuple>
 
 #include "dg_internal.h"
 #include "host_state.h"
@@ -235,13 +237,83 @@ void build_mesh_host3(dg_mesh* M, const dg_mesh_desc* desc, const dg_options& o)
         M->h_sf3[j] = r;
       }
     }
+  // BR2 lifting products of the face tables (the lifting of a sub-face jump,
+  // its element mass inverse and the face mass back onto the side nodes, per
+  // tangential axis), appended after the face tables
+  std::vector<double> prod;
+  std::map<std::tuple<int, int, int, int>, int> pindex;
+  const int pbase = (int)ft.data.size();
+  auto product = [&](int kind, int p, int pn, int oo, int on, int nn) {
+    const auto key = std::make_tuple(kind, kind == 0 ? oo : on, kind == 3 ? nn : (kind == 1 ? oo : -1), p * 16 + pn);
+    auto it = pindex.find(key);
+    if (it != pindex.end()) return it->second;
+    const int a = p + 1, b = pn + 1;
+    const double* Moo = ft.data.data() + oo;
+    const double* Mon = ft.data.data() + on;
+    const double* Mnn = ft.data.data() + nn;
+    const std::vector<double>& Mi = basis1d(p).Minv;
+    const std::vector<double>& Min = basis1d(pn).Minv;
+    const int cols = (kind == 0 || kind == 2) ? a : b;
+    const int o = (int)prod.size();
+    prod.resize(o + (size_t)a * cols, 0.0);
+    for (int i = 0; i < a; ++i)
+      for (int j = 0; j < cols; ++j) {
+        double v = 0.0;
+        if (kind == 0) {          // Z = M_oo Minv M_oo
+          for (int u = 0; u < a; ++u)
+            for (int w = 0; w < a; ++w) v += Moo[i * a + u] * Mi[u * a + w] * Moo[w * a + j];
+        } else if (kind == 1) {   // V = M_oo Minv M_on
+          for (int u = 0; u < a; ++u)
+            for (int w = 0; w < a; ++w) v += Moo[i * a + u] * Mi[u * a + w] * Mon[w * b + j];
+        } else if (kind == 2) {   // X = M_on Minv_n M_no
+          for (int u = 0; u < b; ++u)
+            for (int w = 0; w < b; ++w) v += Mon[i * b + u] * Min[u * b + w] * Mon[j * b + w];
+        } else {                  // Y = M_on Minv_n M_nn
+          for (int u = 0; u < b; ++u)
+            for (int w = 0; w < b; ++w) v += Mon[i * b + u] * Min[u * b + w] * Mnn[w * b + j];
+        }
+        prod[o + (size_t)i * cols + j] = v;
+      }
+    pindex.emplace(key, pbase + o);
+    return pbase + o;
+  };
+  for (int64_t k = 0; k < m.n; ++k)
+    for (int s = 0; s < 6; ++s)
+      for (int j = m.sf_ptr[6 * k + s]; j < m.sf_ptr[6 * k + s + 1]; ++j) {
+        SubFaceRec3& r = M->h_sf3[j];
+        const int P = m.p[k];
+        const bool in = r.nb >= 0;
+        const double coef = in ? 0.25 : 1.0;
+        const double hk = M->h_h[k];
+        r.cz = M->eta * coef * r.area * r.area * basis1d(P).Minv[0] / (hk * hk * hk);
+        for (int d = 0; d < 2; ++d) {
+          r.tab_z[d] = product(0, P, P, r.tab_oo[d], r.tab_oo[d], r.tab_oo[d]);
+          if (in) {
+            r.tab_v[d] = product(1, P, r.pn, r.tab_oo[d], r.tab_on[d], r.tab_nn[d]);
+            r.tab_x[d] = product(2, P, r.pn, r.tab_oo[d], r.tab_on[d], r.tab_nn[d]);
+            r.tab_y[d] = product(3, P, r.pn, r.tab_oo[d], r.tab_on[d], r.tab_nn[d]);
+          } else {
+            r.tab_v[d] = r.tab_x[d] = r.tab_y[d] = r.tab_z[d];
+          }
+        }
+        if (in) {
+          const double hn = M->h_h[r.nb];
+          r.cx = M->eta * coef * r.area * r.area * basis1d(r.pn).Minv[0] / (hn * hn * hn);
+        }
+      }
   const int base = (int)M->h_tables.size();
   M->h_tables.insert(M->h_tables.end(), ft.data.begin(), ft.data.end());
+  M->h_tables.insert(M->h_tables.end(), prod.begin(), prod.end());
+  DG_REQUIRE(M->h_tables.size() < (1ULL << 31), "face tables too large");
   for (auto& r : M->h_sf3)
     for (int d = 0; d < 2; ++d) {
       r.tab_oo[d] += base;
       r.tab_on[d] += base;
       r.tab_nn[d] += base;
+      r.tab_z[d] += base;
+      r.tab_v[d] += base;
+      r.tab_x[d] += base;
+      r.tab_y[d] += base;
     }
   build_tiles3(M);
   // operation and byte counts of one operator apply, as the kernels do it
@@ -258,13 +330,12 @@ void build_mesh_host3(dg_mesh* M, const dg_mesh_desc* desc, const dg_options& o)
     for (int j = m.sf_ptr[6 * k]; j < m.sf_ptr[6 * k + 6]; ++j) {
       const auto& f = m.sf3[j];
       if (f.nb < 0) {
-        fma += 4.0 * a3 + (br2 ? 4.0 * a3 : 0.0);
+        fma += 4.0 * a3 + (br2 ? 2.0 * a3 : 0.0);   // M_oo on u, dn; BR2: Z on u
         continue;
       }
-      const double b = m.p[f.nb] + 1.0, b2 = b * b, b3 = b2 * b;
-      fma += 2.0 * a3 + 2.0 * a * b2 + 2.0 * a3 + 2.0 * a2 * b;
-      if (br2)
-        fma += b * a2 + b3 + b2 * (a + b) + a3 + b3 + a3 + b3 + a3 + a * b2 + a2 * (a + b);
+      const double b = m.p[f.nb] + 1.0, b2 = b * b;
+      fma += 4.0 * a3 + 2.0 * a * b2 + 2.0 * a2 * b;   // M_oo on u-, dn-; M_on on u+, dn+
+      if (br2) fma += 4.0 * a3 + 2.0 * a * b2 + 2.0 * a2 * b;   // Z, X on u-; V, Y on u+
       const int lg = std::abs(ilog2(m.size[k]) - ilog2(m.size[f.nb]));
       S.max_level_gap = std::max<int64_t>(S.max_level_gap, lg);
     }
