@@ -228,8 +228,12 @@ def run_ours(args):
     fp64_peak = fp64_peak_tflops(sm_mhz)
     achieved_tf = stats.apply_flops / (apply_ms / 1e3) / 1e12
     levels = s32.n_levels
-    kernels_per_iter = 1 + 1 + (1 + 4 * (levels - 1) + 1 + 1) + 1 + 1
-    launches = sum(4 + 2 * levels + it * kernels_per_iter for it in it32)  # init + first precond
+    # preconditioner: restriction, two kernels per AMG level, dense coarsest
+    # level, block solves, final combination
+    precond_kernels = 1 + 2 * (levels - 1) + 1 + 1 + 1
+    # iteration: operator apply, x / r update, preconditioner, p update with traces
+    kernels_per_iter = 1 + 1 + precond_kernels + 1
+    launches = sum(2 + precond_kernels + it * kernels_per_iter for it in it32)  # + init, first p
     out = {
         "metric": METRIC3 if three else METRIC,
         "value": value,

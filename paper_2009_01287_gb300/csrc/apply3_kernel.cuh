@@ -43,7 +43,7 @@ __device__ __forceinline__ int side_node3(int s, int i, int j, int q) {
   return ax == 0 ? q + NP * (i + NP * j) : (ax == 1 ? i + NP * (q + NP * j) : i + NP * (j + NP * q));
 }
 
-template <int P>
+template <int P, bool RO = true>
 __device__ __forceinline__ void trace3_tile(const ApplyArgs& A, const ApplyTile& T) {
   constexpr int NP = P + 1, N2 = NP * NP;
   const BasisOff bo = A.boff[P];
@@ -59,10 +59,10 @@ __device__ __forceinline__ void trace3_tile(const ApplyArgs& A, const ApplyTile&
     const double* dv = A.tab + ((s & 1) ? bo.d1 : bo.d0);
     double acc = 0.0;
 #pragma unroll
-    for (int q = 0; q < NP; ++q) acc = fma(__ldg(dv + q), __ldg(xk + side_node3<NP>(s, i, j, q)), acc);
+    for (int q = 0; q < NP; ++q) acc = fma(__ldg(dv + q), ld_x<RO>(xk + side_node3<NP>(s, i, j, q)), acc);
     const double sg = (s & 1) ? A.ih[k] : -A.ih[k];
     double2 v;
-    v.x = __ldg(xk + side_node3<NP>(s, i, j, (s & 1) ? P : 0));
+    v.x = ld_x<RO>(xk + side_node3<NP>(s, i, j, (s & 1) ? P : 0));
     v.y = sg * acc;
     reinterpret_cast<double2*>(A.tr + A.toff[k])[s * N2 + ij] = v;
   }

@@ -161,8 +161,16 @@ __device__ __forceinline__ int side_node(int s, int i, int k, int np) {
   return (s < 2) ? (i * np + k) : (k * np + i);
 }
 
+// load through the read-only path, or a plain load when the data may have been
+// written earlier in the same kernel
+template <bool RO>
+__device__ __forceinline__ double ld_x(const double* p) {
+  if (RO) return __ldg(p);
+  return *p;
+}
+
 // Side traces of one tile: task = (element, side, node), packed.
-template <int P>
+template <int P, bool RO = true>
 __device__ __forceinline__ void trace_tile(const ApplyArgs& A, const ApplyTile& T) {
   constexpr int NP = P + 1;
   const BasisOff bo = A.boff[P];
@@ -177,10 +185,10 @@ __device__ __forceinline__ void trace_tile(const ApplyArgs& A, const ApplyTile& 
     const double* dv = A.tab + ((s & 1) ? bo.d1 : bo.d0);
     double acc = 0.0;
 #pragma unroll
-    for (int q = 0; q < NP; ++q) acc = fma(__ldg(dv + q), __ldg(xk + side_node(s, i, q, NP)), acc);
+    for (int q = 0; q < NP; ++q) acc = fma(__ldg(dv + q), ld_x<RO>(xk + side_node(s, i, q, NP)), acc);
     const double sg = (s & 1) ? A.ih[k] : -A.ih[k];
     double2 v;
-    v.x = __ldg(xk + side_node(s, i, (s & 1) ? P : 0, NP));
+    v.x = ld_x<RO>(xk + side_node(s, i, (s & 1) ? P : 0, NP));
     v.y = sg * acc;
     reinterpret_cast<double2*>(A.tr + A.toff[k])[s * NP + i] = v;
   }

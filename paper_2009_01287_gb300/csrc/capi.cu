@@ -225,11 +225,11 @@ static PcgWork& pcg_work(const dg_precond* pc) {
 
 static void pcg_body(const dg_mesh* M, const dg_precond* pc, PcgWork& w, double* x, int maxit,
                      double rtol2, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
-  launch_apply(*M, w.p, w.q, Reduce{w.part_pq, w.sc + SC_PQ, w.tick + TK_PQ}, s);
+  // the side traces of p were written with p (launch_pcg_p_trace)
+  launch_apply(*M, w.p, w.q, Reduce{w.part_pq, w.sc + SC_PQ, w.tick + TK_PQ}, s, false);
   launch_pcg_update_xr(x, w.r, w.p, w.q, w.n, w.sc, Reduce{w.part_rr, w.sc + SC_RRNEW, w.tick + TK_RR}, s);
   launch_precond(*pc, w.r, w.z, Reduce{w.part_rz, w.sc + SC_RZNEW, w.tick + TK_RZ}, s);
-  launch_pcg_update_p(w.p, w.z, w.n, w.sc, w.tick + TK_P, maxit, rtol2, (unsigned long long)h,
-                      use_cond, s);
+  launch_pcg_p_trace(*M, w.p, w.z, w.sc, w.tick + TK_P, maxit, rtol2, (unsigned long long)h, use_cond, 0, s);
 }
 
 // PCG start: x = 0, r = b, z = B r, p = z, scalars; returns b . b (synchronises)
@@ -237,7 +237,7 @@ static double pcg_start(const dg_precond* pc, PcgWork& w, const double* b, doubl
                         cudaStream_t s) {
   launch_pcg_init(b, x, w.r, w.n, Reduce{w.part_bb, w.sc + SC_BB, w.tick + TK_BB}, s);
   launch_precond(*pc, w.r, w.z, Reduce{w.part_rz, w.sc + SC_RZNEW, w.tick + TK_RZ}, s);
-  launch_pcg_first(w.z, w.p, w.n, w.sc, s);
+  launch_pcg_p_trace(*pc->mesh, w.p, w.z, w.sc, w.tick + TK_P, 0, 0.0, 0ull, 0, 1, s);
   DG_CUDA(cudaMemcpyAsync(hsc, w.sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
   DG_CUDA(cudaStreamSynchronize(s));
   return hsc[SC_BB];

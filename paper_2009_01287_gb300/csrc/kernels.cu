@@ -214,12 +214,13 @@ int apply_kernel_setup(const dg_mesh& M) {
   return sms * (per > 0 ? per : 1);
 }
 
-void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cudaStream_t s) {
+void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cudaStream_t s,
+                  bool with_trace) {
   if (M.n_tiles == 0) return;
   const ApplyArgs A = make_apply_args(M, x, y, red);
   const int grid = M.n_tiles < M.apply_grid ? M.n_tiles : M.apply_grid;
   if (M.host.dim == 3) {
-    launch_k(trace3_kernel, M.n_tiles, kThreads, 0, s, A);
+    if (with_trace) launch_k(trace3_kernel, M.n_tiles, kThreads, 0, s, A);
     const int smem3 = (int)M.apply3_smem;
     if (M.opts.form == DG_FORM_BR2) launch_k(apply3_kernel<true>, grid, kThreads, smem3, s, A);
     else launch_k(apply3_kernel<false>, grid, kThreads, smem3, s, A);
@@ -227,7 +228,7 @@ void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cuda
     return;
   }
   const int smem = (int)M.apply_smem;
-  launch_k(trace_kernel, M.n_tiles, kThreads, 0, s, A);
+  if (with_trace) launch_k(trace_kernel, M.n_tiles, kThreads, 0, s, A);
   if (M.opts.form == DG_FORM_BR2) launch_k(apply_kernel<true>, grid, kThreads, smem, s, A);
   else launch_k(apply_kernel<false>, grid, kThreads, smem, s, A);
   DG_CUDA(cudaGetLastError());
@@ -552,26 +553,6 @@ void launch_pcg_init(const double* b, double* x, double* r, int64_t n, Reduce bb
   DG_CUDA(cudaGetLastError());
 }
 
-// p = z and the initial scalars (rz from the preconditioner's reduction)
-__global__ void pcg_first_kernel(const double* __restrict__ z, double* __restrict__ p, int64_t n,
-                                 double* sc) {
-  pdl_entry();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = z[i];
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    sc[SC_RZ] = sc[SC_RZNEW];
-    sc[SC_RR] = sc[SC_BB];
-    sc[SC_IT] = 0.0;
-    sc[SC_STATUS] = 0.0;
-  }
-}
-
-void launch_pcg_first(const double* z, double* p, int64_t n, double* sc, cudaStream_t s) {
-  launch_k(pcg_first_kernel, grid_for(n), kVecThreads, 0, s, z, p, n, sc);
-  DG_CUDA(cudaGetLastError());
-}
-
 __global__ void __launch_bounds__(kVecThreads)
 pcg_update_xr_kernel(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
                      const double* __restrict__ q, int64_t n, double* sc, Reduce rr) {
@@ -597,20 +578,49 @@ void launch_pcg_update_xr(double* x, double* r, const double* p, const double* q
   DG_CUDA(cudaGetLastError());
 }
 
-__global__ void __launch_bounds__(kVecThreads)
-pcg_update_p_kernel(double* __restrict__ p, const double* __restrict__ z, int64_t n, double* sc,
-                    unsigned* ticket, int maxit, double rtol2, cudaGraphConditionalHandle h,
-                    int use_cond) {
+// p = z + beta p (first: p = z) tile by tile, and the side traces of the new p
+// for the next operator apply, so the apply needs no trace launch of its own.
+// The last CTA to finish advances the iteration count and the scalars, tests
+// convergence and sets the graph's while condition (first: the initial
+// scalars, from the preconditioner's r . z and b . b).
+template <bool CUBE>
+__global__ void __launch_bounds__(kThreads)
+pcg_p_trace_kernel(const ApplyArgs A, double* __restrict__ p, const double* __restrict__ z, double* sc,
+                   unsigned* ticket, int maxit, double rtol2, cudaGraphConditionalHandle h, int use_cond,
+                   int first) {
   pdl_entry();
   __shared__ unsigned s_last;
-  if (sc[SC_STATUS] != 0.0) {
+  if (!first && sc[SC_STATUS] != 0.0) {
     if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
     return;
   }
-  const double beta = sc[SC_RZNEW] / sc[SC_RZ];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = fma(beta, p[i], z[i]);
+  const double beta = first ? 0.0 : sc[SC_RZNEW] / sc[SC_RZ];
+  const ApplyTile T = A.tiles[blockIdx.x];
+  const int np = T.p + 1;
+  const int nn = CUBE ? np * np * np : np * np;
+  for (int t = threadIdx.x; t < T.count * nn; t += blockDim.x) {
+    const int e = t / nn;
+    const int64_t i = A.off[A.order[T.first + e]] + (t - e * nn);
+    p[i] = first ? z[i] : fma(beta, p[i], z[i]);
+  }
+  __syncthreads();
+  switch (T.p) {
+#define DG_TRACE_CASE(PP) \
+    case PP: if (CUBE) trace3_tile<PP, false>(A, T); else trace_tile<PP, false>(A, T); break;
+    DG_TRACE_CASE(1) DG_TRACE_CASE(2) DG_TRACE_CASE(3) DG_TRACE_CASE(4)
+    DG_TRACE_CASE(5) DG_TRACE_CASE(6) DG_TRACE_CASE(7) DG_TRACE_CASE(8)
+#undef DG_TRACE_CASE
+    default: break;
+  }
+  if (first) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      sc[SC_RZ] = sc[SC_RZNEW];
+      sc[SC_RR] = sc[SC_BB];
+      sc[SC_IT] = 0.0;
+      sc[SC_STATUS] = 0.0;
+    }
+    return;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -618,7 +628,6 @@ pcg_update_p_kernel(double* __restrict__ p, const double* __restrict__ z, int64_
   }
   __syncthreads();
   if (s_last && threadIdx.x == 0) {
-    // every CTA has read rz: advance the scalars, test convergence
     const double it = sc[SC_IT] + 1.0;
     const double rr = sc[SC_RRNEW];
     sc[SC_IT] = it;
@@ -632,11 +641,17 @@ pcg_update_p_kernel(double* __restrict__ p, const double* __restrict__ z, int64_
   }
 }
 
-void launch_pcg_update_p(double* p, const double* z, int64_t n, double* sc, unsigned* ticket,
-                         int maxit, double rtol2, unsigned long long cond_handle, int use_cond,
-                         cudaStream_t s) {
-  launch_k(pcg_update_p_kernel, grid_for(n), kVecThreads, 0, s, 
-      p, z, n, sc, ticket, maxit, rtol2, (cudaGraphConditionalHandle)cond_handle, use_cond);
+void launch_pcg_p_trace(const dg_mesh& M, double* p, const double* z, double* sc, unsigned* ticket,
+                        int maxit, double rtol2, unsigned long long cond_handle, int use_cond, int first,
+                        cudaStream_t s) {
+  if (M.n_tiles == 0) return;
+  const ApplyArgs A = make_apply_args(M, p, nullptr, Reduce{});
+  if (M.host.dim == 3)
+    launch_k(pcg_p_trace_kernel<true>, M.n_tiles, kThreads, 0, s, A, p, z, sc, ticket, maxit, rtol2,
+             (cudaGraphConditionalHandle)cond_handle, use_cond, first);
+  else
+    launch_k(pcg_p_trace_kernel<false>, M.n_tiles, kThreads, 0, s, A, p, z, sc, ticket, maxit, rtol2,
+             (cudaGraphConditionalHandle)cond_handle, use_cond, first);
   DG_CUDA(cudaGetLastError());
 }
 

@@ -17,7 +17,10 @@ int apply_kernel_setup(const dg_mesh& M);
 int64_t apply_smem_for(const dg_mesh& M);
 
 ApplyArgs make_apply_args(const dg_mesh& M, const double* x, double* y, Reduce red);
-void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cudaStream_t s);
+// y = A x; with_trace = false when the side traces of x are already in place
+// (written by launch_pcg_p_trace)
+void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cudaStream_t s,
+                  bool with_trace = true);
 
 // z = B r (FP64 or mixed); optional reduction of r . z
 void launch_precond(const dg_precond& pc, const double* r, double* z, Reduce red, cudaStream_t s);
@@ -31,13 +34,13 @@ enum {
 enum { TK_PQ = 0, TK_RR = 1, TK_RZ = 2, TK_P = 3, TK_BB = 4, TK_COUNT = 8 };
 
 void launch_pcg_init(const double* b, double* x, double* r, int64_t n, Reduce bb, cudaStream_t s);
-void launch_pcg_first(const double* z, double* p, int64_t n, double* sc, cudaStream_t s);
 void launch_pcg_update_xr(double* x, double* r, const double* p, const double* q, int64_t n,
                           double* sc, Reduce rr, cudaStream_t s);
-// p = z + beta p; the last CTA also advances the iteration, tests convergence
-// and sets the graph's while condition
-void launch_pcg_update_p(double* p, const double* z, int64_t n, double* sc, unsigned* ticket,
-                         int maxit, double rtol2, unsigned long long cond_handle, int use_cond,
-                         cudaStream_t s);
+// p = z + beta p (first: p = z and the initial scalars) tile by tile, writing
+// the side traces of the new p for the next operator apply; the last CTA
+// advances the iteration, tests convergence and sets the graph's while condition
+void launch_pcg_p_trace(const dg_mesh& M, double* p, const double* z, double* sc, unsigned* ticket,
+                        int maxit, double rtol2, unsigned long long cond_handle, int use_cond, int first,
+                        cudaStream_t s);
 
 }  // namespace dg
