@@ -43,13 +43,13 @@ ORACLE_SAMPLE_ITERS = 20
 # as soon as their hash differs.
 APPLY_TRAFFIC = {"sources": ["paper_2009_01287_gb300/csrc/apply_kernel.cuh",
                              "paper_2009_01287_gb300/csrc/kernels.cu"],
-                 "sha256_16": "d56ec2b850b82c8f", "bytes": 3259904 + 0}
+                 "sha256_16": "f32483348a3f4ff7", "bytes": 3513600 + 0}
 
 
 # likewise for the 3D operator (profiles/apply3_kernel_hp3d_16cube.md)
 APPLY3_TRAFFIC = {"sources": ["paper_2009_01287_gb300/csrc/apply3_kernel.cuh",
                               "paper_2009_01287_gb300/csrc/kernels.cu"],
-                  "sha256_16": "02c1a23d67bf7188", "bytes": 57317376 + 1885952}
+                  "sha256_16": "9734b94dee010b9b", "bytes": 64756480 + 4792576}
 
 
 def apply_traffic(three: bool = False):
@@ -205,6 +205,14 @@ def run_ours(args):
         ev[2 * i + 1].record(stream)
     torch.cuda.synchronize()
     apply_ms = statistics.mean(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(napply))
+    # the mixed preconditioner alone, timed the same way (phase breakdown)
+    for i in range(napply):
+        flush.fill_(4.0)
+        ev[2 * i].record(stream)
+        B.dg_precond_apply(pc32.h, xin, yout, stream)
+        ev[2 * i + 1].record(stream)
+    torch.cuda.synchronize()
+    precond_ms = statistics.mean(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(napply))
     # end to end: host buffers in and out through the C ABI (pinned)
     bh = b.cpu().pin_memory()
     xh = torch.zeros(n, dtype=torch.float64).pin_memory()
@@ -257,6 +265,8 @@ def run_ours(args):
         "time_to_tol_ms_fp64": statistics.median(ms64),
         "dof_iters_per_s_fp64": ws * n * sum(it64) / t64,   # replicas: identical per rank
         "setup_s": setup_s,
+        "phase_ms": {"iteration_mixed": statistics.median(ms32) / statistics.median(it32),
+                     "operator_apply": apply_ms, "preconditioner_mixed": precond_ms},
         "e2e": {"value": ws * n * sum(it_e2e) / te, "unit": "DOF-iters/s",
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
         "roofline": {"kernel": ("apply3_kernel (BR2 operator on cubes, FP64)" if three
