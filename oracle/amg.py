@@ -6,7 +6,8 @@ oracle instead fixes one plain algorithm (the same one the CUDA library sets
 up), step by step:
 
 setup(A):
-  1. if n <= COARSE_MAX: coarsest level, dense inverse.
+  1. if n <= coarse_max (COARSE_MAX unless a test asks for fewer): coarsest
+     level, dense inverse.
   2. strength: j != i is strong for i when a_ij^2 > theta^2 a_ii a_jj
      (theta = THETA on squares, THETA3 on cubes).
   3. aggregation in natural order:
@@ -36,7 +37,7 @@ import scipy.sparse as sp
 
 THETA = 0.08          # squares: the Q1 9-point stencil's links are strong
 THETA3 = 0.02         # cubes: the trilinear 27-point stencil's links are ~1/32 of the diagonal
-COARSE_MAX = 256
+COARSE_MAX = 1024
 MAX_LEVELS = 12
 
 
@@ -89,11 +90,11 @@ def aggregate(A: sp.csr_matrix, theta: float = THETA) -> np.ndarray:
     return agg
 
 
-def setup(A: sp.csr_matrix, theta: float = THETA) -> List[Level]:
+def setup(A: sp.csr_matrix, theta: float = THETA, coarse_max: int = COARSE_MAX) -> List[Level]:
     levels = [Level(A)]
     while True:
         L = levels[-1]
-        if L.n <= COARSE_MAX or len(levels) >= MAX_LEVELS:
+        if L.n <= coarse_max or len(levels) >= MAX_LEVELS:
             break
         agg = aggregate(L.A, theta)
         nc = int(agg.max()) + 1

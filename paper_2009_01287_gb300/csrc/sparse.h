@@ -40,7 +40,7 @@ struct AmgHierarchy {
 
 constexpr double kAmgTheta = 0.08;    // squares: the Q1 9-point stencil's links are strong
 constexpr double kAmgTheta3 = 0.02;   // cubes: trilinear 27-point links are ~1/32 of the diagonal
-constexpr int kAmgCoarseMax = 256;
+constexpr int kAmgCoarseMax = 1024;
 constexpr int kAmgMaxLevels = 12;
 constexpr int kAmgDenseMax = 8192;    // largest coarsest level inverted densely
 

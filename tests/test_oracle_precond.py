@@ -67,8 +67,8 @@ def _poisson5(n):
 
 
 def test_amg_vcycle_properties():
-    A = _poisson5(40)                      # 1600 unknowns -> several levels
-    levels = amg.setup(A)
+    A = _poisson5(40)                      # 1600 unknowns -> several levels below 64 rows
+    levels = amg.setup(A, coarse_max=64)
     assert len(levels) >= 3
     n = A.shape[0]
     rng = np.random.default_rng(0)
