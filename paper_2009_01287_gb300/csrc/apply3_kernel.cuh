@@ -9,10 +9,13 @@
 //            three passes through shared memory (7 (p+1)^4 FMAs per element):
 //              along z: A = M x, B = K x;  along y: C = M A, D = K A + M B;
 //              along x: y = h (K C + M D);
-//    faces   in rounds: round j takes the j-th sub-face of every side of the
-//            tile.  A sub-face is a square whose face-mass matrices are Kronecker
-//            products of 1D tables (first tangential axis a, second b), so every
-//            face product is two 1D contractions with a barrier between them:
+//    faces   the tile's sub-faces are a flat list of (record, side) items,
+//            taken in chunks that fit shared memory.  A sub-face is a square
+//            whose face-mass matrices are Kronecker products of 1D tables (first
+//            tangential axis a, second b), so every face product is two 1D
+//            contractions, one pass over all items of the chunk each, with a
+//            barrier between them; a third pass adds each item's partials to
+//            its side nodes in sub-face order (deterministic):
 //              a = M_oo u-, c = M_oo dn-, b = M_on u+, d = M_on dn+
 //            and, for SIPG, side residual += area (sigma (a - b) - (c - d) / 2)
 //            and normal-derivative coefficient c2 -= area (a - b) / 2
@@ -25,7 +28,7 @@
 //            with the 1D products Z = M_oo Minv M_oo, V = M_oo Minv M_on,
 //            X = M_on Minv_n M_no, Y = M_on Minv_n M_nn and the scalars
 //            cz, cx = eta/4 area^2 Minv_00 / h^3 of the two elements, so BR2
-//            takes the same two passes per round as SIPG;
+//            takes the same two passes as SIPG;
 //    gather  volume pass along x, side residuals and the normal-derivative
 //            terms c2 (x) dn(v) of all six sides.
 // Each sub-face is evaluated from both of its sides (no atomics): applies are
@@ -72,8 +75,8 @@ template <int P, bool BR2>
 __device__ __forceinline__ void apply3_tile(const ApplyArgs& A, const ApplyTile& T, int tile,
                                             double* sm, double* red) {
   constexpr int NP = P + 1, N2 = NP * NP, N3 = N2 * NP;
-  constexpr int S = BR2 ? 8 : 4;          // scratch arrays per side and round
-  const int cnt = T.count, NQ = T.nq, Q2 = NQ * NQ;
+  constexpr int S = BR2 ? 8 : 4;          // first-pass products per sub-face item
+  const int cnt = T.count, NQ = T.nq, WQ = NP * NQ;
   double* sM = sm;
   double* sK = sM + N2;
   double* sx = sK + N2;
@@ -83,7 +86,8 @@ __device__ __forceinline__ void apply3_tile(const ApplyArgs& A, const ApplyTile&
   double* sD = sC + cnt * N3;
   double* sr = sD + cnt * N3;             // [cnt][6][N2] side residuals
   double* sc2 = sr + cnt * 6 * N2;        // [cnt][6][N2] normal-derivative coefficients
-  double* sw = sc2 + cnt * 6 * N2;        // [cnt][6][S][Q2] round scratch
+  double* sw = sc2 + cnt * 6 * N2;        // [chunk][S][NP x NQ] first-pass scratch
+  double* sp = sw + T.chunk * S * WQ;     // [chunk][2][N2] item partials (residual, c2)
 
   const int tid = threadIdx.x;
   if (A.skip && A.skip[(int64_t)T.inst * A.skip_stride] != 0.0) {   // CTA-uniform
@@ -138,24 +142,27 @@ __device__ __forceinline__ void apply3_tile(const ApplyArgs& A, const ApplyTile&
     sC[t] = c;
     sD[t] = d;
   }
-  // ---- faces, one sub-face per side per round
-  const int nface = cnt * 6 * Q2;
+  // ---- faces: the tile's sub-face items in chunks; per chunk two passes
+  // (one per tangential axis) over all items at once, then every side node
+  // adds its items' partials in sub-face order
   const double* tab = A.tab;
-  for (int j = 0; j < T.maxsub; ++j) {
+  const int ib = A.item_ptr[tile];
+  const int nit = A.item_ptr[tile + 1] - ib;
+  for (int c0 = 0; c0 < nit; c0 += T.chunk) {
+    const int nc = min(T.chunk, nit - c0);
     // P1: contractions along the first tangential axis
-    for (int t = tid; t < nface; t += blockDim.x) {
-      const int es = t / Q2, q = t - es * Q2;
-      const int e = es / 6, s = es - e * 6;
-      const int i = q % NQ, n = q / NQ;
+    for (int t = tid; t < nc * WQ; t += blockDim.x) {
+      const int it = t / WQ, q = t - it * WQ;
+      const int i = q % NP, n = q / NP;
+      const int2 item = A.items[ib + c0 + it];
+      const SubFaceRec3& f = A.sf3[item.x];
+      const int e = item.y / 6, s = item.y - e * 6;
       const int k = A.order[T.first + e];
-      const int b0 = A.sf_ptr[6 * k + s];
-      if (j >= A.sf_ptr[6 * k + s + 1] - b0) continue;
-      const SubFaceRec3& f = A.sf3[b0 + j];
       const int np = f.pn + 1;
       const bool in = f.nb >= 0;
-      double* W = sw + es * S * Q2;
-      const double2* trk = reinterpret_cast<const double2*>(A.tr + A.toff[k]) + s * N2;
-      if (i < NP && n < NP) {
+      double* W = sw + it * S * WQ;
+      if (n < NP) {
+        const double2* trk = reinterpret_cast<const double2*>(A.tr + A.toff[k]) + s * N2;
         const double* Ma = tab + f.tab_oo[0] + i * NP;
         const double* Za = tab + f.tab_z[0] + i * NP;
         const double* Xa = tab + f.tab_x[0] + i * NP;
@@ -171,16 +178,15 @@ __device__ __forceinline__ void apply3_tile(const ApplyArgs& A, const ApplyTile&
             if (in) wx = fma(__ldg(Xa + m), v.x, wx);
           }
         }
-        W[0 * Q2 + i * NQ + n] = wa;
-        W[1 * Q2 + i * NQ + n] = wc;
+        W[0 * WQ + i * NQ + n] = wa;
+        W[1 * WQ + i * NQ + n] = wc;
         if (BR2) {
-          W[4 * Q2 + i * NQ + n] = wz;
-          W[5 * Q2 + i * NQ + n] = wx;
+          W[4 * WQ + i * NQ + n] = wz;
+          W[5 * WQ + i * NQ + n] = wx;
         }
       }
-      if (!in) continue;
-      const double2* trn = reinterpret_cast<const double2*>(A.tr + A.toff[f.nb]) + f.nb_side * np * np;
-      if (i < NP && n < np) {
+      if (in && n < np) {
+        const double2* trn = reinterpret_cast<const double2*>(A.tr + A.toff[f.nb]) + f.nb_side * np * np;
         const double* Ma = tab + f.tab_on[0] + i * np;
         const double* Va = tab + f.tab_v[0] + i * np;
         const double* Ya = tab + f.tab_y[0] + i * np;
@@ -195,28 +201,24 @@ __device__ __forceinline__ void apply3_tile(const ApplyArgs& A, const ApplyTile&
             wy = fma(__ldg(Ya + m), v.x, wy);
           }
         }
-        W[2 * Q2 + i * NQ + n] = wb;
-        W[3 * Q2 + i * NQ + n] = wd;
+        W[2 * WQ + i * NQ + n] = wb;
+        W[3 * WQ + i * NQ + n] = wd;
         if (BR2) {
-          W[6 * Q2 + i * NQ + n] = wv;
-          W[7 * Q2 + i * NQ + n] = wy;
+          W[6 * WQ + i * NQ + n] = wv;
+          W[7 * WQ + i * NQ + n] = wy;
         }
       }
     }
     __syncthreads();
-    // P2: contractions along the second tangential axis and the side terms
-    for (int t = tid; t < nface; t += blockDim.x) {
-      const int es = t / Q2, q = t - es * Q2;
-      const int e = es / 6, s = es - e * 6;
-      const int i = q % NQ, jj = q / NQ;
-      if (i >= NP || jj >= NP) continue;
-      const int k = A.order[T.first + e];
-      const int b0 = A.sf_ptr[6 * k + s];
-      if (j >= A.sf_ptr[6 * k + s + 1] - b0) continue;
-      const SubFaceRec3& f = A.sf3[b0 + j];
+    // P2: contractions along the second tangential axis: the item's partials
+    for (int t = tid; t < nc * N2; t += blockDim.x) {
+      const int it = t / N2, q = t - it * N2;
+      const int i = q % NP, jj = q / NP;
+      const int2 item = A.items[ib + c0 + it];
+      const SubFaceRec3& f = A.sf3[item.x];
       const int np = f.pn + 1;
       const bool in = f.nb >= 0;
-      const double* W = sw + es * S * Q2;
+      const double* W = sw + it * S * WQ;
       const double ar = f.area;
       const double* Mb = tab + f.tab_oo[1] + jj * NP;
       const double* Zb = tab + f.tab_z[1] + jj * NP;
@@ -225,11 +227,11 @@ __device__ __forceinline__ void apply3_tile(const ApplyArgs& A, const ApplyTile&
 #pragma unroll
       for (int n = 0; n < NP; ++n) {
         const double w = __ldg(Mb + n);
-        a = fma(w, W[0 * Q2 + i * NQ + n], a);
-        c = fma(w, W[1 * Q2 + i * NQ + n], c);
+        a = fma(w, W[0 * WQ + i * NQ + n], a);
+        c = fma(w, W[1 * WQ + i * NQ + n], c);
         if (BR2) {
-          zz = fma(__ldg(Zb + n), W[4 * Q2 + i * NQ + n], zz);
-          if (in) xx = fma(__ldg(Xb + n), W[5 * Q2 + i * NQ + n], xx);
+          zz = fma(__ldg(Zb + n), W[4 * WQ + i * NQ + n], zz);
+          if (in) xx = fma(__ldg(Xb + n), W[5 * WQ + i * NQ + n], xx);
         }
       }
       if (in) {
@@ -238,15 +240,14 @@ __device__ __forceinline__ void apply3_tile(const ApplyArgs& A, const ApplyTile&
         const double* Yb = tab + f.tab_y[1] + jj * np;
         for (int n = 0; n < np; ++n) {
           const double w = __ldg(Mbn + n);
-          b = fma(w, W[2 * Q2 + i * NQ + n], b);
-          d = fma(w, W[3 * Q2 + i * NQ + n], d);
+          b = fma(w, W[2 * WQ + i * NQ + n], b);
+          d = fma(w, W[3 * WQ + i * NQ + n], d);
           if (BR2) {
-            vv = fma(__ldg(Vb + n), W[6 * Q2 + i * NQ + n], vv);
-            yy = fma(__ldg(Yb + n), W[7 * Q2 + i * NQ + n], yy);
+            vv = fma(__ldg(Vb + n), W[6 * WQ + i * NQ + n], vv);
+            yy = fma(__ldg(Yb + n), W[7 * WQ + i * NQ + n], yy);
           }
         }
       }
-      const int o = es * N2 + jj * NP + i;
       const double jmp = a - b;
       double rr, cc;
       if (in) {
@@ -258,8 +259,25 @@ __device__ __forceinline__ void apply3_tile(const ApplyArgs& A, const ApplyTile&
       }
       if (BR2) rr += f.cz * (zz - vv) + f.cx * (xx - yy);
       else rr = fma(f.sigma * ar, jmp, rr);
-      sr[o] += rr;
-      sc2[o] += cc;
+      sp[it * 2 * N2 + q] = rr;
+      sp[it * 2 * N2 + N2 + q] = cc;
+    }
+    __syncthreads();
+    // P3: every side node adds the partials of its items in this chunk, in order
+    for (int t = tid; t < cnt * 6 * N2; t += blockDim.x) {
+      const int es = t / N2, q = t - es * N2;
+      const int e = es / 6, s = es - e * 6;
+      const int2 si = A.side_items[(int64_t)(T.first + e) * 6 + s];
+      const int lo = max(si.x - ib, c0), hi = min(si.x - ib + si.y, c0 + nc);
+      double rr = 0.0, cc = 0.0;
+      for (int g = lo; g < hi; ++g) {
+        rr += sp[(g - c0) * 2 * N2 + q];
+        cc += sp[(g - c0) * 2 * N2 + N2 + q];
+      }
+      if (hi > lo) {
+        sr[t] += rr;
+        sc2[t] += cc;
+      }
     }
     __syncthreads();
   }

@@ -90,12 +90,18 @@ struct SubFaceRec3 {
 };
 
 // Shared-memory budget (doubles) of one 3D operator tile; the host sizes the
-// tiles so that every one fits.
+// tiles and their sub-face item chunks so that every one fits.
 constexpr int kApply3Budget = 13 * 1024;
-// doubles of shared memory one element of degree p needs in a 3D tile whose
-// elements see neighbour degrees below nq (nq = max(p, pn) + 1)
-constexpr int apply3_elem_doubles(int p, int nq, bool br2) {
-  return 5 * (p + 1) * (p + 1) * (p + 1) + 12 * (p + 1) * (p + 1) + 6 * (br2 ? 8 : 4) * nq * nq;
+constexpr int kApply3MinChunk = 12;   // sub-face items a tile keeps room for
+// doubles of shared memory one element of degree p needs in a 3D tile (volume
+// passes and the per-side residual and normal-derivative coefficients)
+constexpr int apply3_elem_doubles(int p) {
+  return 5 * (p + 1) * (p + 1) * (p + 1) + 12 * (p + 1) * (p + 1);
+}
+// doubles one sub-face item needs: first-pass scratch ((p+1) x nq per product,
+// nq = max(p, pn) + 1) and its two partial side arrays
+constexpr int apply3_item_doubles(int p, int nq, bool br2) {
+  return (br2 ? 8 : 4) * (p + 1) * nq + 2 * (p + 1) * (p + 1);
 }
 
 // Offsets of the degree-p 1D matrices inside the device table buffer.
@@ -110,7 +116,7 @@ struct ApplyTile {
   int32_t count;
   int32_t inst;      // batch instance of the tile's elements (0 for a single mesh)
   int32_t nq;        // 3D: max(p, neighbour degrees) + 1 over the tile
-  int32_t maxsub;    // 3D: most sub-faces on one side of a tile element
+  int32_t chunk;     // 3D: sub-face items processed at a time
 };
 
 // ------------------------------------------------------------------ mesh (host topology)

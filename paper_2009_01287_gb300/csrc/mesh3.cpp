@@ -111,54 +111,74 @@ void build_topology3(HostMesh& m) {
   }
 }
 
-// degree-sorted element order and tiles of the 3D operator kernel: elements
-// sorted by (p, nq, most sub-faces on one side), descending; runs of equal
-// (p, nq), as many elements as fill 256 threads within the shared-memory budget
+// degree-sorted element order and tiles of the 3D operator kernel.  Elements
+// are sorted by (p, nq), descending, nq = max(p, neighbour degrees) + 1; a tile
+// is a run of equal (p, nq) with as many elements as fill 256 threads while the
+// volume and side arrays leave room for a chunk of at least kApply3MinChunk
+// sub-face items.  The tile's sub-faces are a flat list of (record, side)
+// items, processed in chunks that fit the shared-memory budget; per element
+// side the first item and the count.
 static void build_tiles3(dg_mesh* M) {
   const HostMesh& m = M->host;
   const bool br2 = M->opts.form == DG_FORM_BR2;
-  std::vector<int32_t> nq(m.n), ms(m.n);
+  std::vector<int32_t> nq(m.n), nitem(m.n);
   for (int64_t k = 0; k < m.n; ++k) {
-    int q = m.p[k] + 1, mx = 0;
-    for (int s = 0; s < 6; ++s) {
-      const int b = m.sf_ptr[6 * k + s], e = m.sf_ptr[6 * k + s + 1];
-      mx = std::max(mx, e - b);
-      for (int j = b; j < e; ++j)
-        if (m.sf3[j].nb >= 0) q = std::max(q, m.p[m.sf3[j].nb] + 1);
-    }
+    int q = m.p[k] + 1;
+    const int b = m.sf_ptr[6 * k], e = m.sf_ptr[6 * k + 6];
+    for (int j = b; j < e; ++j)
+      if (m.sf3[j].nb >= 0) q = std::max(q, m.p[m.sf3[j].nb] + 1);
     nq[k] = q;
-    ms[k] = mx;
+    nitem[k] = e - b;
   }
   std::vector<int32_t> order(m.n);
   for (int64_t k = 0; k < m.n; ++k) order[k] = (int32_t)k;
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
     if (m.p[a] != m.p[b]) return m.p[a] > m.p[b];
-    if (nq[a] != nq[b]) return nq[a] > nq[b];
-    return ms[a] > ms[b];
+    return nq[a] > nq[b];
   });
   M->h_tiles.clear();
+  M->h_items.clear();
+  M->h_item_ptr.assign(1, 0);
+  M->h_side_items.assign(12 * (size_t)m.n, 0);
   M->apply3_smem = 0;
   for (int64_t i = 0; i < m.n;) {
     const int P = m.p[order[i]], Q = nq[order[i]], NP = P + 1;
-    const int per = apply3_elem_doubles(P, Q, br2);
+    const int fixed_per = apply3_elem_doubles(P);
+    const int item_per = apply3_item_doubles(P, Q, br2);
     const int by_threads = std::max(1, kThreads / (NP * NP * NP));
-    const int by_smem = (kApply3Budget - 2 * NP * NP) / per;
-    DG_REQUIRE(by_smem >= 1, "3D operator tile does not fit in shared memory");
-    const int epb = std::min(by_threads, by_smem);
-    int64_t j = i;
-    int mx = 0;
-    while (j < m.n && m.p[order[j]] == P && nq[order[j]] == Q && j - i < epb) {
-      mx = std::max(mx, ms[order[j]]);
+    int64_t j = i, items = 0;
+    while (j < m.n && m.p[order[j]] == P && nq[order[j]] == Q && j - i < by_threads) {
+      const int64_t cnt = j - i + 1, it = items + nitem[order[j]];
+      const int64_t need = 2 * NP * NP + cnt * fixed_per + std::min<int64_t>(it, kApply3MinChunk) * item_per;
+      if (need > kApply3Budget && j > i) break;
+      items = it;
       ++j;
     }
+    const int64_t fixed = 2 * NP * NP + (j - i) * fixed_per;
+    const int64_t room = (kApply3Budget - fixed) / item_per;
+    DG_REQUIRE(room >= 1, "3D operator tile does not fit in shared memory");
     ApplyTile T{};
     T.p = P;
     T.first = (int32_t)i;
     T.count = (int32_t)(j - i);
     T.nq = Q;
-    T.maxsub = mx;
+    T.chunk = (int32_t)std::min<int64_t>(items, room);
+    for (int64_t e = 0; e < T.count; ++e) {
+      const int64_t pos = i + e;
+      const int32_t k = order[pos];
+      for (int s = 0; s < 6; ++s) {
+        const int b = m.sf_ptr[6 * (int64_t)k + s], c = m.sf_ptr[6 * (int64_t)k + s + 1] - b;
+        M->h_side_items[12 * pos + 2 * s] = (int32_t)(M->h_items.size() / 2);
+        M->h_side_items[12 * pos + 2 * s + 1] = c;
+        for (int q = 0; q < c; ++q) {
+          M->h_items.push_back(b + q);
+          M->h_items.push_back((int32_t)(6 * e + s));
+        }
+      }
+    }
+    M->h_item_ptr.push_back((int32_t)(M->h_items.size() / 2));
     M->h_tiles.push_back(T);
-    M->apply3_smem = std::max<int64_t>(M->apply3_smem, 8LL * (2 * NP * NP + T.count * per));
+    M->apply3_smem = std::max<int64_t>(M->apply3_smem, 8LL * (fixed + T.chunk * item_per));
     i = j;
   }
   M->n_tiles = (int)M->h_tiles.size();
