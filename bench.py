@@ -42,14 +42,13 @@ ORACLE_SAMPLE_ITERS = 20
 # only for the kernel sources it was taken on: the line reports null traffic
 # as soon as their hash differs.
 APPLY_TRAFFIC = {"sources": ["paper_2009_01287_gb300/csrc/apply_kernel.cuh",
-                             "paper_2009_01287_gb300/csrc/kernels.cu"],
-                 "sha256_16": "f32483348a3f4ff7", "bytes": 3513600 + 0}
-
-
+                             "paper_2009_01287_gb300/csrc/apply_launch.cu"],
+                 "sha256_16": None, "bytes": None}
 # likewise for the 3D operator (profiles/apply3_kernel_hp3d_16cube.md)
-APPLY3_TRAFFIC = {"sources": ["paper_2009_01287_gb300/csrc/apply3_kernel.cuh",
-                              "paper_2009_01287_gb300/csrc/kernels.cu"],
-                  "sha256_16": "9734b94dee010b9b", "bytes": 64756480 + 4792576}
+APPLY3_TRAFFIC = {"sources": ["paper_2009_01287_gb300/csrc/apply_kernel.cuh",
+                              "paper_2009_01287_gb300/csrc/apply3_kernel.cuh",
+                              "paper_2009_01287_gb300/csrc/apply_launch.cu"],
+                  "sha256_16": None, "bytes": None}
 
 
 def apply_traffic(three: bool = False):
@@ -236,9 +235,9 @@ def run_ours(args):
     fp64_peak = fp64_peak_tflops(sm_mhz)
     achieved_tf = stats.apply_flops / (apply_ms / 1e3) / 1e12
     levels = s32.n_levels
-    # preconditioner: restriction, two kernels per AMG level, dense coarsest
-    # level, block solves, final combination
-    precond_kernels = 1 + 2 * (levels - 1) + 1 + 1 + 1
+    # preconditioner launches as the library reports them (restriction, two or
+    # four kernels per AMG level, dense coarsest level, block solves, final)
+    precond_kernels = int(s32.kernels_per_apply)
     # iteration: operator apply, x / r update, preconditioner, p update with traces
     kernels_per_iter = 1 + 1 + precond_kernels + 1
     launches = sum(2 + precond_kernels + it * kernels_per_iter for it in it32)  # + init, first p
@@ -258,6 +257,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD3 if three else WORKLOAD, "n_dofs": n, "n_elems": int(stats.n_elems),
                    "n_conforming": int(s32.n_conforming), "amg_levels": levels,
                    "n_blocks": int(s32.n_blocks), "max_block": int(s32.max_block),
+                   "amg_plain_levels": [int(s32.level_plain[i]) for i in range(levels)],
                    "parallelism": f"replicas x{ws}", "l2": "flushed (512 MiB write) before every step"},
         "iters_mixed": statistics.median(it32),
         "iters_fp64": statistics.median(it64),

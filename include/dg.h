@@ -103,6 +103,9 @@ typedef struct {
   int n_levels;          /* AMG levels (1 = exact dense solve)              */
   int64_t level_rows[16];
   int64_t level_nnz[16];
+  int level_plain[16];   /* 1: level applied in the plain form (A, R, P),
+                            0: composite operators (see dg_precond_setup)   */
+  int kernels_per_apply; /* device kernel launches of one dg_precond_apply  */
 } dg_precond_stats;
 
 typedef struct {
@@ -130,9 +133,12 @@ dg_status dg_mesh_stats_get(const dg_mesh* mesh, dg_mesh_stats* out);
 dg_status dg_apply(const dg_mesh* mesh, const double* x, double* y, void* stream);
 
 /* Set up B = B_B + B_C (Sections 3.3, 3.4, 4.1): V_J / V_e classification,
- * the V_e generation (connected components by jump overlap), dense block
- * inverses, diag(A) on V_J, P, the LOR matrix P^T A~ P and its solver.
- * Host work, then uploads; synchronous. */
+ * the V_e generation (connected components by jump overlap; on cube meshes the
+ * E nodes of each master entity), dense block inverses, diag(A) on V_J, P,
+ * the LOR matrix P^T A~ P and its solver.  An AMG level is applied either
+ * through composite operators (two kernels) or, when its matrix is large, in
+ * the plain form (four kernels, about half the bytes); both are the same
+ * V-cycle.  Host work, then uploads; synchronous. */
 dg_status dg_precond_setup(const dg_mesh* mesh, const dg_options* opts, dg_precond** out);
 void dg_precond_destroy(dg_precond* pc);
 dg_status dg_precond_stats_get(const dg_precond* pc, dg_precond_stats* out);

@@ -61,7 +61,8 @@ class DgPrecondStats(C.Structure):
     _fields_ = [("n_dofs", C.c_int64), ("n_conforming", C.c_int64), ("n_j", C.c_int64),
                 ("n_e", C.c_int64), ("n_blocks", C.c_int64), ("max_block", C.c_int64),
                 ("lor_nnz", C.c_int64), ("p_nnz", C.c_int64), ("n_levels", C.c_int),
-                ("level_rows", C.c_int64 * 16), ("level_nnz", C.c_int64 * 16)]
+                ("level_rows", C.c_int64 * 16), ("level_nnz", C.c_int64 * 16),
+                ("level_plain", C.c_int * 16), ("kernels_per_apply", C.c_int)]
 
 
 _lib = None

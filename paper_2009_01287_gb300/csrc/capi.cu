@@ -426,6 +426,7 @@ dg_status dg_precond_stats_get(const dg_precond* pc, dg_precond_stats* out) {
   return guarded([&] {
     DG_REQUIRE(pc && out, "null argument");
     *out = pc->stats;
+    out->kernels_per_apply = precond_kernel_count(*pc);
   });
 }
 

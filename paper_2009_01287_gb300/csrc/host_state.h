@@ -54,6 +54,14 @@ struct DevLevel {
                        // restricted); rows [n_cont, n) are coarsest levels of
                        // their problem and are solved densely (blocks below)
   DevCsr Rpre, Sb, Sp;  // composite V-cycle operators on the continuing rows (see AmgLevel)
+  // large levels take the plain form instead (fewer matrix bytes, two more
+  // launches): A on the continuing rows, R = P^T, P, the l1 diagonal inverse
+  // and two work vectors
+  bool plain = false;
+  DevCsr A, R, P;
+  void* dinv = nullptr;
+  void* t1 = nullptr;
+  void* t2 = nullptr;
   int n_end = 0;                   // dense coarse blocks
   int max_end = 0;                 // largest of them
   int32_t* end_row = nullptr;      // n_end+1 row offsets (level numbering)

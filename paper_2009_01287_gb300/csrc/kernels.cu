@@ -1,245 +1,11 @@
-// Device kernels: operator apply launch, preconditioner pieces (Section 4.1:
-// P^T, LOR solve, P, point Jacobi, block solves) and the PCG vector work.
+// Device kernels: preconditioner pieces (Section 4.1: P^T, LOR solve, P, point
+// Jacobi, block solves) and the PCG vector work.  The operator's launch code
+// is in apply_launch.cu.
 #include <cstdio>
 
 #include "kernels.cuh"
 
 namespace dg {
-
-// ============================================================== operator
-__global__ void __launch_bounds__(kThreads) trace_kernel(const ApplyArgs A) {
-  pdl_entry();
-  const ApplyTile T = A.tiles[blockIdx.x];
-  switch (T.p) {
-    case 1: trace_tile<1>(A, T); break;
-    case 2: trace_tile<2>(A, T); break;
-    case 3: trace_tile<3>(A, T); break;
-    case 4: trace_tile<4>(A, T); break;
-    case 5: trace_tile<5>(A, T); break;
-    case 6: trace_tile<6>(A, T); break;
-    case 7: trace_tile<7>(A, T); break;
-    case 8: trace_tile<8>(A, T); break;
-    default: break;
-  }
-}
-
-// End of a persistent operator launch: the last CTA to leave resets the tile
-// counter and sums the tile partials of x . y in tile order.
-__device__ __forceinline__ void apply_exit(const ApplyArgs& A, double* red) {
-  __shared__ unsigned s_last;
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = (atomicAdd(A.sched + 1, 1u) == gridDim.x - 1) ? 1u : 0u;
-  }
-  __syncthreads();
-  if (s_last) {
-    __threadfence();
-    if (A.dot_partial) {
-      double v = 0.0;
-      for (int i = threadIdx.x; i < A.n_tiles; i += kThreads) v += __ldcg(A.dot_partial + i);
-      v = block_sum<kThreads>(v, red);
-      if (threadIdx.x == 0) *A.dot_out = v;
-    }
-    if (threadIdx.x == 0) {
-      A.sched[0] = 0u;
-      A.sched[1] = 0u;
-    }
-  }
-}
-
-// Persistent operator kernel: a grid sized to the resident capacity takes
-// tiles from an atomic counter, heaviest first (tiles are degree-sorted), so
-// the uneven tiles balance across SMs.  The last CTA to leave resets the
-// counter and, when a dot product is requested, sums the tile partials in
-// tile order (deterministic whichever CTA ran which tile).
-template <bool BR2>
-__global__ void __launch_bounds__(kThreads) apply_kernel(const ApplyArgs A) {
-  pdl_entry();
-  extern __shared__ __align__(16) double smem[];
-  __shared__ double red[kThreads];
-  __shared__ int s_tile;
-  while (true) {
-    if (threadIdx.x == 0) s_tile = (int)atomicAdd(A.sched, 1u);
-    __syncthreads();
-    const int t = s_tile;
-    __syncthreads();
-    if (t >= A.n_tiles) break;
-    const ApplyTile T = A.tiles[t];
-    switch (T.p) {
-      case 1: apply_tile<1, BR2>(A, T, t, smem, red); break;
-      case 2: apply_tile<2, BR2>(A, T, t, smem, red); break;
-      case 3: apply_tile<3, BR2>(A, T, t, smem, red); break;
-      case 4: apply_tile<4, BR2>(A, T, t, smem, red); break;
-      case 5: apply_tile<5, BR2>(A, T, t, smem, red); break;
-      case 6: apply_tile<6, BR2>(A, T, t, smem, red); break;
-      case 7: apply_tile<7, BR2>(A, T, t, smem, red); break;
-      case 8: apply_tile<8, BR2>(A, T, t, smem, red); break;
-      default: break;
-    }
-    __syncthreads();
-  }
-  apply_exit(A, red);
-}
-
-__global__ void __launch_bounds__(kThreads) trace3_kernel(const ApplyArgs A) {
-  pdl_entry();
-  const ApplyTile T = A.tiles[blockIdx.x];
-  switch (T.p) {
-    case 1: trace3_tile<1>(A, T); break;
-    case 2: trace3_tile<2>(A, T); break;
-    case 3: trace3_tile<3>(A, T); break;
-    case 4: trace3_tile<4>(A, T); break;
-    case 5: trace3_tile<5>(A, T); break;
-    case 6: trace3_tile<6>(A, T); break;
-    case 7: trace3_tile<7>(A, T); break;
-    case 8: trace3_tile<8>(A, T); break;
-    default: break;
-  }
-}
-
-// Persistent operator kernel of cube meshes (same scheduling as on squares).
-template <bool BR2>
-__global__ void __launch_bounds__(kThreads) apply3_kernel(const ApplyArgs A) {
-  pdl_entry();
-  extern __shared__ __align__(16) double smem[];
-  __shared__ double red[kThreads];
-  __shared__ int s_tile;
-  while (true) {
-    if (threadIdx.x == 0) s_tile = (int)atomicAdd(A.sched, 1u);
-    __syncthreads();
-    const int t = s_tile;
-    __syncthreads();
-    if (t >= A.n_tiles) break;
-    const ApplyTile T = A.tiles[t];
-    switch (T.p) {
-      case 1: apply3_tile<1, BR2>(A, T, t, smem, red); break;
-      case 2: apply3_tile<2, BR2>(A, T, t, smem, red); break;
-      case 3: apply3_tile<3, BR2>(A, T, t, smem, red); break;
-      case 4: apply3_tile<4, BR2>(A, T, t, smem, red); break;
-      case 5: apply3_tile<5, BR2>(A, T, t, smem, red); break;
-      case 6: apply3_tile<6, BR2>(A, T, t, smem, red); break;
-      case 7: apply3_tile<7, BR2>(A, T, t, smem, red); break;
-      case 8: apply3_tile<8, BR2>(A, T, t, smem, red); break;
-      default: break;
-    }
-    __syncthreads();
-  }
-  apply_exit(A, red);
-}
-
-// static shared-memory layout of a degree-p tile up to the item partials (doubles)
-static int apply_shape_smem(int p) {
-  switch (p) {
-    case 1: return ApplyShape<1>::PART;
-    case 2: return ApplyShape<2>::PART;
-    case 3: return ApplyShape<3>::PART;
-    case 4: return ApplyShape<4>::PART;
-    case 5: return ApplyShape<5>::PART;
-    case 6: return ApplyShape<6>::PART;
-    case 7: return ApplyShape<7>::PART;
-    default: return ApplyShape<8>::PART;
-  }
-}
-
-int64_t apply_smem_for(const dg_mesh& M) {
-  if (M.host.dim == 3) return M.apply3_smem;
-  // the layout of the tile's degree plus its sub-face item partials
-  int64_t mx = 0;
-  for (int t = 0; t < M.n_tiles; ++t) {
-    const ApplyTile& T = M.h_tiles[t];
-    const int64_t nit = M.h_item_ptr.empty() ? 0 : M.h_item_ptr[t + 1] - M.h_item_ptr[t];
-    mx = std::max<int64_t>(mx, apply_shape_smem(T.p) + 2 * nit * (T.p + 1));
-  }
-  return 8 * mx;
-}
-
-ApplyArgs make_apply_args(const dg_mesh& M, const double* x, double* y, Reduce red) {
-  ApplyArgs A;
-  A.x = x;
-  A.y = y;
-  A.off = M.d_off;
-  A.ih = M.d_ih;
-  A.toff = M.d_toff;
-  A.tr = M.d_tr;
-  A.sf_ptr = M.d_sf_ptr;
-  A.sf = M.d_sf;
-  A.sf3 = M.d_sf3;
-  A.hk = M.d_h;
-  A.tab = M.d_tables;
-  A.order = M.d_order;
-  A.tiles = M.d_tiles;
-  A.items = reinterpret_cast<const int2*>(M.d_items);
-  A.item_ptr = M.d_item_ptr;
-  A.side_items = reinterpret_cast<const int2*>(M.d_side_items);
-  A.eta = M.eta;
-  A.dot_partial = red.partial;
-  A.dot_out = red.out;
-  A.dot_ticket = red.ticket;
-  A.skip = M.skip_status;
-  A.skip_stride = M.skip_stride;
-  A.n_tiles = M.n_tiles;
-  A.sched = M.d_sched;
-  for (int p = 0; p <= kMaxP; ++p) A.boff[p] = M.boff[p];
-  return A;
-}
-
-int apply_kernel_setup(const dg_mesh& M) {
-  // The shared-memory opt-in is an attribute of the kernel function on the
-  // current device, shared by every mesh: raise it to the device limit (a
-  // mesh's own size could lower it under an earlier mesh's needs), and size the
-  // resident grid of this mesh's persistent launch from its own tile layout.
-  int dev = 0, sms = 0, per = 0, optin = 0;
-  DG_CUDA(cudaGetDevice(&dev));
-  DG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  DG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  optin -= 4 * 1024;   // room for the kernels' static shared memory
-  const bool br2 = M.opts.form == DG_FORM_BR2;
-  if (M.host.dim == 3) {
-    const int smem = (int)M.apply3_smem;
-    DG_REQUIRE(smem <= optin, "operator tile needs too much shared memory");
-    DG_CUDA(cudaFuncSetAttribute(apply3_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    DG_CUDA(cudaFuncSetAttribute(apply3_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    if (br2) DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, apply3_kernel<true>, kThreads, smem));
-    else DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, apply3_kernel<false>, kThreads, smem));
-    return sms * (per > 0 ? per : 1);
-  }
-  const int smem = (int)M.apply_smem;
-  DG_REQUIRE(smem <= optin, "operator tile needs too much shared memory");
-  DG_CUDA(cudaFuncSetAttribute(apply_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-  DG_CUDA(cudaFuncSetAttribute(apply_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-  if (br2)
-    DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, apply_kernel<true>, kThreads, smem));
-  else
-    DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, apply_kernel<false>, kThreads, smem));
-  return sms * (per > 0 ? per : 1);
-}
-
-void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cudaStream_t s,
-                  bool with_trace) {
-  if (M.n_tiles == 0) return;
-  const ApplyArgs A = make_apply_args(M, x, y, red);
-  const int grid = M.n_tiles < M.apply_grid ? M.n_tiles : M.apply_grid;
-  if (M.host.dim == 3) {
-    if (with_trace) launch_k(trace3_kernel, M.n_tiles, kThreads, 0, s, A);
-    const int smem3 = (int)M.apply3_smem;
-    if (M.opts.form == DG_FORM_BR2) launch_k(apply3_kernel<true>, grid, kThreads, smem3, s, A);
-    else launch_k(apply3_kernel<false>, grid, kThreads, smem3, s, A);
-    DG_CUDA(cudaGetLastError());
-    return;
-  }
-  const int smem = (int)M.apply_smem;
-  if (with_trace) launch_k(trace_kernel, M.n_tiles, kThreads, 0, s, A);
-  if (M.opts.form == DG_FORM_BR2) launch_k(apply_kernel<true>, grid, kThreads, smem, s, A);
-  else launch_k(apply_kernel<false>, grid, kThreads, smem, s, A);
-  DG_CUDA(cudaGetLastError());
-}
-
-template <int NT>
-__device__ __forceinline__ double sum_partials(const double* part, int n, double* red) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += NT) s += part[i];
-  return block_sum<NT>(s, red);
-}
 
 // ============================================================== preconditioner
 
@@ -283,6 +49,34 @@ struct OpRestrict {  // out = P^T r, r in FP64
   __device__ T x(int j) const { return (T)__ldg(r + j); }
   __device__ void store(int64_t i, T s) const { out[i] = s; }
 };
+// plain V-cycle level (D = diag(l1 row sums)):
+template <typename T>
+struct OpResid {  // out = b - A D^-1 b (pre-smoothing from zero, then the residual)
+  const T* b;
+  const T* dinv;
+  T* out;
+  __device__ T x(int j) const { return __ldg(b + j) * __ldg(dinv + j); }
+  __device__ void store(int64_t i, T s) const { out[i] = b[i] - s; }
+};
+template <typename T>
+struct OpCorr {  // out = D^-1 b + P xc (pre-smoothed iterate plus coarse correction)
+  const T* b;
+  const T* dinv;
+  const T* xc;
+  T* out;
+  __device__ T x(int j) const { return __ldg(xc + j); }
+  __device__ void store(int64_t i, T s) const { out[i] = fma(b[i], dinv[i], s); }
+};
+template <typename T>
+struct OpPost {  // out = xp + D^-1 (b - A xp) (post-smoothing)
+  const T* xp;
+  const T* b;
+  const T* dinv;
+  T* out;
+  __device__ T x(int j) const { return __ldg(xp + j); }
+  __device__ void store(int64_t i, T s) const { out[i] = fma(dinv[i], b[i] - s, xp[i]); }
+};
+
 template <typename T, class Op>
 static void launch_rows(const DevCsr& A, const Op& op, cudaStream_t s) {
   if (A.rows == 0) return;
@@ -473,7 +267,16 @@ dense_blocks_kernel(const int32_t* __restrict__ row, const int64_t* __restrict__
 template <typename T>
 static void vcycle(const dg_precond& pc, size_t l, cudaStream_t s) {
   const DevLevel& L = pc.levels[l];
-  if (L.n_cont > 0) {
+  if (L.n_cont > 0 && L.plain) {
+    const DevLevel& C = pc.levels[l + 1];
+    const T* b = (const T*)L.b;
+    const T* dinv = (const T*)L.dinv;
+    launch_rows<T>(L.A, OpResid<T>{b, dinv, (T*)L.t1}, s);                  // b - A D^-1 b
+    launch_rows<T>(L.R, OpSpmv<T>{(const T*)L.t1, (T*)C.b}, s);             // restrict
+    vcycle<T>(pc, l + 1, s);
+    launch_rows<T>(L.P, OpCorr<T>{b, dinv, (const T*)C.xo, (T*)L.t2}, s);   // D^-1 b + P xc
+    launch_rows<T>(L.A, OpPost<T>{(const T*)L.t2, b, dinv, (T*)L.xo}, s);   // post-smoothing
+  } else if (L.n_cont > 0) {
     const DevLevel& C = pc.levels[l + 1];
     launch_rows<T>(L.Rpre, OpSpmv<T>{(const T*)L.b, (T*)C.b}, s);   // restrict b - A D^-1 b
     vcycle<T>(pc, l + 1, s);
@@ -524,6 +327,19 @@ static void precond_impl(const dg_precond& pc, const double* r, double* z, Reduc
   else DG_FINAL(4);
 #undef DG_FINAL
   DG_CUDA(cudaGetLastError());
+}
+
+int precond_kernel_count(const dg_precond& pc) {
+  int k = (pc.n_blocks > 0 ? 1 : 0) + 1;   // block solves, final combination
+  if (pc.n_c > 0) {
+    k += 1;                                // restriction
+    if (pc.lor == DG_LOR_EXACT) return k + 1;
+    for (const DevLevel& L : pc.levels) {
+      if (L.n_cont > 0) k += L.plain ? 4 : 2;
+      if (L.n_end > 0 && L.max_end > 0) k += 1;
+    }
+  }
+  return k;
 }
 
 void launch_precond(const dg_precond& pc, const double* r, double* z, Reduce red, cudaStream_t s) {

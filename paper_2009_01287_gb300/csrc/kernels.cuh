@@ -25,6 +25,8 @@ void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cuda
 // z = B r (FP64 or mixed); optional reduction of r . z
 void launch_precond(const dg_precond& pc, const double* r, double* z, Reduce red, cudaStream_t s);
 int precond_final_blocks(const dg_precond& pc);
+// device kernel launches of one preconditioner apply
+int precond_kernel_count(const dg_precond& pc);
 
 // PCG scalar slots (doubles) and reduction tickets
 enum {

@@ -43,6 +43,11 @@ constexpr double kAmgTheta3 = 0.02;   // cubes: trilinear 27-point links are ~1/
 constexpr int kAmgCoarseMax = 1024;
 constexpr int kAmgMaxLevels = 12;
 constexpr int kAmgDenseMax = 8192;    // largest coarsest level inverted densely
+// A level whose continuing rows hold more nonzeros than this is applied in the
+// plain form (A, R, P: about half the matrix bytes of the composite operators,
+// which pays when the level is bandwidth-bound); smaller levels, bound by
+// launch latency, keep the two-kernel composite form.
+constexpr int64_t kAmgPlainNnz = 4000000;
 
 AmgHierarchy amg_setup(const Csr& A, double theta = kAmgTheta);
 void dense_inverse_spd(int n, std::vector<double>& a);  // in place, Cholesky based

@@ -135,13 +135,24 @@ void upload_union_precond(dg_precond* pc, const std::vector<InstSrc>& inst, cuda
     std::vector<int32_t> end_row{(int32_t)ncont[l]};
     std::vector<int64_t> end_off;
     std::vector<T> end_inv;
-    int64_t nnz_all = 0;
+    int64_t nnz_all = 0, nnz_cont = 0;
+    for (size_t i : order[l])
+      if (row_off[l][i] < ncont[l]) nnz_cont += inst[i].A->levels[l].A.nnz();
+    D.plain = nnz_cont > kAmgPlainNnz;
+    Csr Ac, Pc, Rc;
+    std::vector<T> dinv_c;
     for (size_t i : order[l]) {
       const AmgLevel& L = inst[i].A->levels[l];
       nnz_all += L.A.nnz();
       if (row_off[l][i] < ncont[l]) {
-        append_rows(Sb, L.Sb, row_off[l][i]);
-        append_rows(Sp, L.Sp, row_off[l + 1][i]);
+        if (D.plain) {
+          append_rows(Ac, L.A, row_off[l][i]);
+          append_rows(Pc, L.P, row_off[l + 1][i]);
+          for (double d : L.dl1) dinv_c.push_back((T)(1.0 / d));
+        } else {
+          append_rows(Sb, L.Sb, row_off[l][i]);
+          append_rows(Sp, L.Sp, row_off[l + 1][i]);
+        }
       } else {
         end_off.push_back((int64_t)end_inv.size());
         end_inv.insert(end_inv.end(), inst[i].A->coarse_inv.begin(), inst[i].A->coarse_inv.end());
@@ -150,15 +161,30 @@ void upload_union_precond(dg_precond* pc, const std::vector<InstSrc>& inst, cuda
       }
     }
     if (l + 1 < nlev)
-      for (size_t i : order[l + 1]) append_rows(Rp, inst[i].A->levels[l].Rpre, row_off[l][i]);
-    Sb.cols = ncont[l];
-    Sp.cols = (l + 1 < nlev) ? nrows[l + 1] : 0;
-    Rp.cols = ncont[l];
-    upload_csr_t<T>(a, Sb, D.Sb, s);
-    upload_csr_t<T>(a, Sp, D.Sp, s);
-    upload_csr_t<T>(a, Rp, D.Rpre, s);
-    // lanes per row of the fused up-sweep: both operators' rows together
-    D.Sb.group = csr_group_for(ncont[l] ? (double)(Sb.nnz() + Sp.nnz()) / (double)ncont[l] : 1.0);
+      for (size_t i : order[l + 1]) {
+        if (D.plain) append_rows(Rc, inst[i].A->levels[l].R, row_off[l][i]);
+        else append_rows(Rp, inst[i].A->levels[l].Rpre, row_off[l][i]);
+      }
+    if (D.plain) {
+      Ac.cols = ncont[l];
+      Pc.cols = (l + 1 < nlev) ? nrows[l + 1] : 0;
+      Rc.cols = ncont[l];
+      upload_csr_t<T>(a, Ac, D.A, s);
+      upload_csr_t<T>(a, Pc, D.P, s);
+      upload_csr_t<T>(a, Rc, D.R, s);
+      D.dinv = a.upload(dinv_c, s);
+      D.t1 = a.alloc<T>(ncont[l]);
+      D.t2 = a.alloc<T>(ncont[l]);
+    } else {
+      Sb.cols = ncont[l];
+      Sp.cols = (l + 1 < nlev) ? nrows[l + 1] : 0;
+      Rp.cols = ncont[l];
+      upload_csr_t<T>(a, Sb, D.Sb, s);
+      upload_csr_t<T>(a, Sp, D.Sp, s);
+      upload_csr_t<T>(a, Rp, D.Rpre, s);
+      // lanes per row of the fused up-sweep: both operators' rows together
+      D.Sb.group = csr_group_for(ncont[l] ? (double)(Sb.nnz() + Sp.nnz()) / (double)ncont[l] : 1.0);
+    }
     D.n_end = (int)end_off.size();
     D.end_row = a.upload(end_row, s);
     D.end_inv_off = a.upload(end_off, s);
@@ -167,6 +193,7 @@ void upload_union_precond(dg_precond* pc, const std::vector<InstSrc>& inst, cuda
     D.xo = a.alloc<T>(D.n);
     pc->stats.level_rows[l] = D.n;
     pc->stats.level_nnz[l] = nnz_all;
+    pc->stats.level_plain[l] = D.plain ? 1 : 0;
   }
   pc->stats.n_levels = (int)nlev;
   DG_CUDA(cudaStreamCreateWithFlags(&pc->side, cudaStreamNonBlocking));
