@@ -43,12 +43,12 @@ ORACLE_SAMPLE_ITERS = 20
 # as soon as their hash differs.
 APPLY_TRAFFIC = {"sources": ["paper_2009_01287_gb300/csrc/apply_kernel.cuh",
                              "paper_2009_01287_gb300/csrc/apply_launch.cu"],
-                 "sha256_16": None, "bytes": None}
+                 "sha256_16": "d2b5098a6ef33efd", "bytes": 3513600 + 0}
 # likewise for the 3D operator (profiles/apply3_kernel_hp3d_16cube.md)
 APPLY3_TRAFFIC = {"sources": ["paper_2009_01287_gb300/csrc/apply_kernel.cuh",
                               "paper_2009_01287_gb300/csrc/apply3_kernel.cuh",
                               "paper_2009_01287_gb300/csrc/apply_launch.cu"],
-                  "sha256_16": None, "bytes": None}
+                  "sha256_16": "35ebf08c80f82ee2", "bytes": 66486016 + 5127168}
 
 
 def apply_traffic(three: bool = False):
