@@ -28,7 +28,10 @@
 //            with the 1D products Z = M_oo Minv M_oo, V = M_oo Minv M_on,
 //            X = M_on Minv_n M_no, Y = M_on Minv_n M_nn and the scalars
 //            cz, cx = eta/4 area^2 Minv_00 / h^3 of the two elements, so BR2
-//            takes the same two passes as SIPG;
+//            takes the same two passes as SIPG.  On a sub-face that is the
+//            whole own face Z = M_oo and V = M_on (M_oo is then the 1D mass
+//            matrix), on the whole neighbour face Y = M_on: those products are
+//            taken from a and b, their loops skipped as a whole;
 //    gather  volume pass along x, side residuals and the normal-derivative
 //            terms c2 (x) dn(v) of all six sides.
 // Each sub-face is evaluated from both of its sides (no atomics): applies are
@@ -161,50 +164,65 @@ __device__ __forceinline__ void apply3_tile(const ApplyArgs& A, const ApplyTile&
       const int np = f.pn + 1;
       const bool in = f.nb >= 0;
       double* W = sw + it * S * WQ;
+      // on a whole own face Z = M_oo, V = M_on; on a whole neighbour face Y = M_on:
+      // those products are not formed (their loops skipped as a whole)
+      const bool zv = BR2 && !(f.full & 1), yy_ = BR2 && !(f.full & 2);
       if (n < NP) {
         const double2* trk = reinterpret_cast<const double2*>(A.tr + A.toff[k]) + s * N2;
         const double* Ma = tab + f.tab_oo[0] + i * NP;
-        const double* Za = tab + f.tab_z[0] + i * NP;
-        const double* Xa = tab + f.tab_x[0] + i * NP;
-        double wa = 0.0, wc = 0.0, wz = 0.0, wx = 0.0;
+        double wa = 0.0, wc = 0.0, wx = 0.0;
+        if (BR2 && in) {
+          const double* Xa = tab + f.tab_x[0] + i * NP;
 #pragma unroll
-        for (int m = 0; m < NP; ++m) {
-          const double2 v = trk[n * NP + m];
-          const double w = __ldg(Ma + m);
-          wa = fma(w, v.x, wa);
-          wc = fma(w, v.y, wc);
-          if (BR2) {
-            wz = fma(__ldg(Za + m), v.x, wz);
-            if (in) wx = fma(__ldg(Xa + m), v.x, wx);
+          for (int m = 0; m < NP; ++m) {
+            const double2 v = trk[n * NP + m];
+            const double w = __ldg(Ma + m);
+            wa = fma(w, v.x, wa);
+            wc = fma(w, v.y, wc);
+            wx = fma(__ldg(Xa + m), v.x, wx);
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < NP; ++m) {
+            const double2 v = trk[n * NP + m];
+            const double w = __ldg(Ma + m);
+            wa = fma(w, v.x, wa);
+            wc = fma(w, v.y, wc);
           }
         }
         W[0 * WQ + i * NQ + n] = wa;
         W[1 * WQ + i * NQ + n] = wc;
-        if (BR2) {
+        if (BR2) W[5 * WQ + i * NQ + n] = wx;
+        if (zv) {
+          const double* Za = tab + f.tab_z[0] + i * NP;
+          double wz = 0.0;
+#pragma unroll
+          for (int m = 0; m < NP; ++m) wz = fma(__ldg(Za + m), trk[n * NP + m].x, wz);
           W[4 * WQ + i * NQ + n] = wz;
-          W[5 * WQ + i * NQ + n] = wx;
         }
       }
       if (in && n < np) {
         const double2* trn = reinterpret_cast<const double2*>(A.tr + A.toff[f.nb]) + f.nb_side * np * np;
         const double* Ma = tab + f.tab_on[0] + i * np;
-        const double* Va = tab + f.tab_v[0] + i * np;
-        const double* Ya = tab + f.tab_y[0] + i * np;
-        double wb = 0.0, wd = 0.0, wv = 0.0, wy = 0.0;
+        double wb = 0.0, wd = 0.0;
         for (int m = 0; m < np; ++m) {
           const double2 v = trn[n * np + m];
           const double w = __ldg(Ma + m);
           wb = fma(w, v.x, wb);
           wd = fma(w, v.y, wd);
-          if (BR2) {
-            wv = fma(__ldg(Va + m), v.x, wv);
-            wy = fma(__ldg(Ya + m), v.x, wy);
-          }
         }
         W[2 * WQ + i * NQ + n] = wb;
         W[3 * WQ + i * NQ + n] = wd;
-        if (BR2) {
+        if (zv) {
+          const double* Va = tab + f.tab_v[0] + i * np;
+          double wv = 0.0;
+          for (int m = 0; m < np; ++m) wv = fma(__ldg(Va + m), trn[n * np + m].x, wv);
           W[6 * WQ + i * NQ + n] = wv;
+        }
+        if (yy_) {
+          const double* Ya = tab + f.tab_y[0] + i * np;
+          double wy = 0.0;
+          for (int m = 0; m < np; ++m) wy = fma(__ldg(Ya + m), trn[n * np + m].x, wy);
           W[7 * WQ + i * NQ + n] = wy;
         }
       }
@@ -221,33 +239,51 @@ __device__ __forceinline__ void apply3_tile(const ApplyArgs& A, const ApplyTile&
       const double* W = sw + it * S * WQ;
       const double ar = f.area;
       const double* Mb = tab + f.tab_oo[1] + jj * NP;
-      const double* Zb = tab + f.tab_z[1] + jj * NP;
-      const double* Xb = tab + f.tab_x[1] + jj * NP;
+      const bool zv = BR2 && !(f.full & 1), yy_ = BR2 && !(f.full & 2);
       double a = 0.0, c = 0.0, b = 0.0, d = 0.0, zz = 0.0, xx = 0.0, vv = 0.0, yy = 0.0;
+      if (BR2 && in) {
+        const double* Xb = tab + f.tab_x[1] + jj * NP;
 #pragma unroll
-      for (int n = 0; n < NP; ++n) {
-        const double w = __ldg(Mb + n);
-        a = fma(w, W[0 * WQ + i * NQ + n], a);
-        c = fma(w, W[1 * WQ + i * NQ + n], c);
-        if (BR2) {
-          zz = fma(__ldg(Zb + n), W[4 * WQ + i * NQ + n], zz);
-          if (in) xx = fma(__ldg(Xb + n), W[5 * WQ + i * NQ + n], xx);
+        for (int n = 0; n < NP; ++n) {
+          const double w = __ldg(Mb + n);
+          a = fma(w, W[0 * WQ + i * NQ + n], a);
+          c = fma(w, W[1 * WQ + i * NQ + n], c);
+          xx = fma(__ldg(Xb + n), W[5 * WQ + i * NQ + n], xx);
         }
+      } else {
+#pragma unroll
+        for (int n = 0; n < NP; ++n) {
+          const double w = __ldg(Mb + n);
+          a = fma(w, W[0 * WQ + i * NQ + n], a);
+          c = fma(w, W[1 * WQ + i * NQ + n], c);
+        }
+      }
+      if (zv) {
+        const double* Zb = tab + f.tab_z[1] + jj * NP;
+#pragma unroll
+        for (int n = 0; n < NP; ++n) zz = fma(__ldg(Zb + n), W[4 * WQ + i * NQ + n], zz);
       }
       if (in) {
         const double* Mbn = tab + f.tab_on[1] + jj * np;
-        const double* Vb = tab + f.tab_v[1] + jj * np;
-        const double* Yb = tab + f.tab_y[1] + jj * np;
         for (int n = 0; n < np; ++n) {
           const double w = __ldg(Mbn + n);
           b = fma(w, W[2 * WQ + i * NQ + n], b);
           d = fma(w, W[3 * WQ + i * NQ + n], d);
-          if (BR2) {
-            vv = fma(__ldg(Vb + n), W[6 * WQ + i * NQ + n], vv);
-            yy = fma(__ldg(Yb + n), W[7 * WQ + i * NQ + n], yy);
-          }
+        }
+        if (zv) {
+          const double* Vb = tab + f.tab_v[1] + jj * np;
+          for (int n = 0; n < np; ++n) vv = fma(__ldg(Vb + n), W[6 * WQ + i * NQ + n], vv);
+        }
+        if (yy_) {
+          const double* Yb = tab + f.tab_y[1] + jj * np;
+          for (int n = 0; n < np; ++n) yy = fma(__ldg(Yb + n), W[7 * WQ + i * NQ + n], yy);
         }
       }
+      if (BR2 && !zv) {   // whole own face: Z = M_oo, V = M_on
+        zz = a;
+        vv = b;
+      }
+      if (BR2 && !yy_) yy = b;   // whole neighbour face: Y = M_on
       const double jmp = a - b;
       double rr, cc;
       if (in) {

@@ -77,12 +77,14 @@ struct SubFaceRec3 {
   int32_t nb;        // neighbour element, -1 on the boundary
   int32_t nb_side;   // neighbour side holding the sub-face
   int32_t pn;        // neighbour degree
-  int32_t pad;
+  int32_t full;      // bit 0: the sub-face is the own element's whole face, bit 1: the neighbour's
   int32_t tab_oo[2]; // own-own 1D face mass per tangential axis ((p+1)^2)
   int32_t tab_on[2]; // own-neighbour ((p+1) x (pn+1))
   int32_t tab_nn[2]; // neighbour-neighbour ((pn+1)^2)
   // BR2 lifting products per tangential axis (Minv: 1D mass inverse):
   //   Z = M_oo Minv M_oo, V = M_oo Minv M_on, X = M_on Minv_n M_no, Y = M_on Minv_n M_nn
+  // (on a whole own face M_oo is the 1D mass matrix, so Z = M_oo and V = M_on;
+  // on a whole neighbour face likewise Y = M_on)
   int32_t tab_z[2], tab_v[2], tab_x[2], tab_y[2];
   double sigma;      // SIPG penalty
   double area;       // physical area of the sub-face

@@ -231,6 +231,7 @@ void build_mesh_host3(dg_mesh* M, const dg_mesh_desc* desc, const dg_options& o)
         const int oa = (f.a0 - A0) / f.len, ob = (f.b0 - B0) / f.len;
         r.nb = f.nb;
         r.nb_side = f.nb_side;
+        r.full = (Lo == 0) ? 1 : 0;
         r.area = (double)f.len * f.len * m.lh * m.lh;
         r.tab_oo[0] = ft.get(P, Lo, oa, P, Lo, oa);
         r.tab_oo[1] = ft.get(P, Lo, ob, P, Lo, ob);
@@ -242,6 +243,7 @@ void build_mesh_host3(dg_mesh* M, const dg_mesh_desc* desc, const dg_options& o)
           const int Ln = ilog2(nh / f.len);
           const int na = (f.a0 - nA) / f.len, nbo = (f.b0 - nB) / f.len;
           r.pn = pn;
+          if (Ln == 0) r.full |= 2;
           r.tab_on[0] = ft.get(P, Lo, oa, pn, Ln, na);
           r.tab_on[1] = ft.get(P, Lo, ob, pn, Ln, nbo);
           r.tab_nn[0] = ft.get(pn, Ln, na, pn, Ln, na);
@@ -349,13 +351,19 @@ void build_mesh_host3(dg_mesh* M, const dg_mesh_desc* desc, const dg_options& o)
     fma += 7.0 * a3 * a + 6.0 * a3 + 6.0 * a3;   // volume, traces' dn, gather
     for (int j = m.sf_ptr[6 * k]; j < m.sf_ptr[6 * k + 6]; ++j) {
       const auto& f = m.sf3[j];
+      const bool own_full = f.len == m.size[k];
       if (f.nb < 0) {
-        fma += 4.0 * a3 + (br2 ? 2.0 * a3 : 0.0);   // M_oo on u, dn; BR2: Z on u
+        fma += 4.0 * a3 + ((br2 && !own_full) ? 2.0 * a3 : 0.0);   // M_oo on u, dn; BR2: Z on u
         continue;
       }
       const double b = m.p[f.nb] + 1.0, b2 = b * b;
+      const bool nb_full = f.len == m.size[f.nb];
       fma += 4.0 * a3 + 2.0 * a * b2 + 2.0 * a2 * b;   // M_oo on u-, dn-; M_on on u+, dn+
-      if (br2) fma += 4.0 * a3 + 2.0 * a * b2 + 2.0 * a2 * b;   // Z, X on u-; V, Y on u+
+      if (br2) {
+        fma += 2.0 * a3;                                          // X on u-
+        if (!own_full) fma += 2.0 * a3 + a * b2 + a2 * b;         // Z on u-, V on u+
+        if (!nb_full) fma += a * b2 + a2 * b;                     // Y on u+
+      }
       const int lg = std::abs(ilog2(m.size[k]) - ilog2(m.size[f.nb]));
       S.max_level_gap = std::max<int64_t>(S.max_level_gap, lg);
     }
