@@ -48,7 +48,7 @@ APPLY_TRAFFIC = {"sources": ["paper_2009_01287_gb300/csrc/apply_kernel.cuh",
 APPLY3_TRAFFIC = {"sources": ["paper_2009_01287_gb300/csrc/apply_kernel.cuh",
                               "paper_2009_01287_gb300/csrc/apply3_kernel.cuh",
                               "paper_2009_01287_gb300/csrc/apply_launch.cu"],
-                  "sha256_16": "35ebf08c80f82ee2", "bytes": 66486016 + 5127168}
+                  "sha256_16": "b8ae8d3d92b398a1", "bytes": 66526976 + 4917760}
 
 
 def apply_traffic(three: bool = False):

@@ -1,6 +1,8 @@
 """The C-ABI library loads and exports every entry point of include/dg.h
 (no compute calls: these run without a GPU)."""
 import ctypes
+
+import pytest
 import os
 import re
 import subprocess
@@ -43,3 +45,35 @@ def test_invalid_mesh_rejected_without_side_effects(built_lib):
         raise AssertionError("accepted an invalid mesh")
     except built_lib.DGError as e:
         assert e.code == built_lib.DG_EINVAL
+
+
+def _desc(dim, lo, size, p, extent, lh=0.25):
+    import numpy as np
+    from paper_2009_01287_gb300.inputs import MeshDesc
+    return MeshDesc(dim, np.asarray(lo, dtype=np.int32).reshape(-1, dim), np.asarray(size, dtype=np.int32),
+                    np.asarray(p, dtype=np.int32), tuple(extent), lh)
+
+
+BAD = {
+    "3d-overlap": lambda: _desc(3, [(0, 0, 0), (0, 0, 0)], [1, 1], [1, 1], (2, 1, 1)),
+    "3d-gap": lambda: _desc(3, [(0, 0, 0)], [1], [2], (2, 1, 1)),
+    "3d-misaligned": lambda: _desc(3, [(1, 0, 0), (0, 0, 0), (0, 2, 0)], [2, 1, 1], [1, 1, 1], (3, 3, 1)),
+    "3d-size-not-pow2": lambda: _desc(3, [(0, 0, 0)], [3], [1], (3, 3, 3)),
+    "3d-degree-0": lambda: _desc(3, [(0, 0, 0)], [1], [0], (1, 1, 1)),
+    "3d-degree-9": lambda: _desc(3, [(0, 0, 0)], [1], [9], (1, 1, 1)),
+    "3d-outside": lambda: _desc(3, [(0, 0, 0), (1, 0, 0)], [1, 1], [1, 1], (1, 1, 1)),
+    "2d-gap": lambda: _desc(2, [(0, 0)], [1], [2], (2, 1)),
+}
+
+
+@pytest.mark.parametrize("name", list(BAD))
+def test_invalid_meshes_rejected(built_lib, name):
+    """Invalid 2D and 3D descriptions give DG_EINVAL with a message, before
+    any device work (overlap, gap, misaligned or non-dyadic boxes, degrees
+    outside 1..8, boxes outside the domain)."""
+    try:
+        built_lib.dg_mesh_create(BAD[name]())
+        raise AssertionError("accepted an invalid mesh")
+    except built_lib.DGError as e:
+        assert e.code == built_lib.DG_EINVAL
+        assert str(e)
