@@ -174,3 +174,28 @@ def test_full_size_config2_solve(built_lib, torch_mod):
     torch_mod.cuda.synchronize()
     res = float(torch_mod.linalg.norm(bd - yd) / torch_mod.linalg.norm(bd))
     assert res <= 2e-8
+
+
+def test_pcg3_single_element_and_degenerate(built_lib, torch_mod):
+    """One cube (no interior faces, V_E empty): PCG matches the oracle; a zero
+    right-hand side returns x = 0 after no iteration; maxit = 1 reports
+    DG_ENOTCONV with the iterate of that step."""
+    mesh = inputs.uniform_mesh(3, 1, 4)
+    prob = solver.build_problem(mesh, form="br2")
+    rh = inputs.sine_rhs(3, 3)
+    b = rhs.load_vector(prob.space, rh.amps, rh.waves)
+    ref = solver.pcg(prob.A, b, solver.Preconditioner(prob, lor="amg").apply, 1e-8, 500)
+    B = built_lib
+    o = _opts3(B, "br2")
+    M = B.Mesh(mesh, o)
+    pc = B.Precond(M, o)
+    bd = dev(torch_mod, b)
+    xd = torch_mod.empty_like(bd)
+    info = B.dg_pcg_solve(M.h, pc.h, bd, xd, 1e-8, 500)
+    assert info.status == 0 and abs(info.iters - ref.iters) <= 1
+    zd = torch_mod.zeros_like(bd)
+    info0 = B.dg_pcg_solve(M.h, pc.h, zd, xd, 1e-8, 500)
+    assert info0.status == 0 and info0.iters == 0
+    assert float(torch_mod.abs(xd).max()) == 0.0
+    info1 = B.dg_pcg_solve(M.h, pc.h, bd, xd, 1e-14, 1, raise_on_notconv=False)
+    assert info1.status == B.DG_ENOTCONV and info1.iters == 1
