@@ -130,8 +130,7 @@ struct dg_precond {
   dg::DevArena arena;
   dg::DevCsr P, PT;          // P: n_dofs x n_c (rows = DG nodes), PT = P^T
   void* dinv = nullptr;      // n_dofs, 1/A_jj on V_J and 0 elsewhere
-  int32_t* e_block = nullptr;   // n_dofs, V_e index or -1
-  int32_t* e_local = nullptr;   // n_dofs, position inside its V_e
+  int32_t* e_pos = nullptr;     // n_dofs, slot of the node's result in zE, or -1 outside the V_e
   int64_t* blk_inv_off = nullptr;
   int32_t* blk_dofs_off = nullptr;
   int32_t* blk_dim = nullptr;

@@ -135,10 +135,15 @@ block_solve_kernel(const int64_t* __restrict__ inv_off, const int32_t* __restric
     // thread l: row l of A_e^-1 (stored column-major: step m reads a contiguous column)
     const T* At = inv + __ldg(inv_off + b);
     for (int l = threadIdx.x; l < d; l += blockDim.x) {
-      T acc = 0;
+      T acc0 = 0, acc1 = 0;   // even / odd columns: two independent FMA chains
+      int m = 0;
 #pragma unroll 8
-      for (int m = 0; m < d; ++m) acc = fma(__ldg(At + (int64_t)m * d + l), sr[m], acc);
-      zE[__ldg(dofs_off + b) + l] = acc;
+      for (; m + 1 < d; m += 2) {
+        acc0 = fma(__ldg(At + (int64_t)m * d + l), sr[m], acc0);
+        acc1 = fma(__ldg(At + (int64_t)(m + 1) * d + l), sr[m + 1], acc1);
+      }
+      if (m < d) acc0 = fma(__ldg(At + (int64_t)m * d + l), sr[m], acc0);
+      zE[__ldg(dofs_off + b) + l] = acc0 + acc1;
     }
     __syncthreads();
   }
@@ -150,8 +155,7 @@ template <typename T, int G>
 __global__ void __launch_bounds__(kVecThreads)
 precond_final_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
                      const T* __restrict__ val, const T* __restrict__ ec,
-                     const T* __restrict__ dinv, const int32_t* __restrict__ e_block,
-                     const int32_t* __restrict__ e_local, const int32_t* __restrict__ dofs_off,
+                     const T* __restrict__ dinv, const int32_t* __restrict__ e_pos,
                      const T* __restrict__ zE, const double* __restrict__ r,
                      double* __restrict__ z, int64_t n, Reduce red) {
   pdl_entry();
@@ -171,8 +175,8 @@ precond_final_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict_
     if (i < n && lane == 0) {
       const double ri = __ldg(r + i);
       s += __ldg(dinv + i) * (T)ri;
-      const int b = __ldg(e_block + i);
-      if (b >= 0) s += __ldg(zE + __ldg(dofs_off + b) + __ldg(e_local + i));
+      const int ep = __ldg(e_pos + i);
+      if (ep >= 0) s += __ldg(zE + ep);
       const double zi = (double)s;
       z[i] = zi;
       dot += zi * ri;
@@ -320,8 +324,8 @@ static void precond_impl(const dg_precond& pc, const double* r, double* z, Reduc
   const int nb = precond_final_blocks(pc);
 #define DG_FINAL(G)                                                                          \
   launch_k(precond_final_kernel<T, G>, nb, kVecThreads, 0, s,                                      \
-      pc.P.ptr, pc.P.idx, (const T*)pc.P.val, (const T*)ec, (const T*)pc.dinv, pc.e_block,   \
-      pc.e_local, pc.blk_dofs_off, (const T*)pc.zE, r, z, pc.n_dofs, red)
+      pc.P.ptr, pc.P.idx, (const T*)pc.P.val, (const T*)ec, (const T*)pc.dinv, pc.e_pos,     \
+      (const T*)pc.zE, r, z, pc.n_dofs, red)
   if (pc.P.group <= 1) DG_FINAL(1);
   else if (pc.P.group == 2) DG_FINAL(2);
   else DG_FINAL(4);

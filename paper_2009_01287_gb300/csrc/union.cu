@@ -77,7 +77,7 @@ void upload_union_precond(dg_precond* pc, const std::vector<InstSrc>& inst, cuda
   // ---- DG-level pieces: P (columns = level-0 rows), D_J^-1, V_e blocks
   Csr P;
   std::vector<double> dinv;
-  std::vector<int32_t> eb, el, dofs_off, dims, dofs;
+  std::vector<int32_t> eb, dofs_off, dims, dofs;
   std::vector<int64_t> inv_off;
   std::vector<T> inv;
   int64_t nb = 0;
@@ -87,15 +87,18 @@ void upload_union_precond(dg_precond* pc, const std::vector<InstSrc>& inst, cuda
     dinv.insert(dinv.end(), H.dinv.begin(), H.dinv.end());
     const size_t base = eb.size();
     eb.resize(base + H.dinv.size(), -1);
-    el.resize(base + H.dinv.size(), 0);
-    for (size_t b = 0; b < H.blocks.size(); ++b) {
+    // largest blocks first: the block-solve CTAs take blocks in this order
+    std::vector<size_t> border(H.blocks.size());
+    for (size_t b = 0; b < border.size(); ++b) border[b] = b;
+    std::stable_sort(border.begin(), border.end(),
+                     [&](size_t x, size_t y) { return H.blocks[x].size() > H.blocks[y].size(); });
+    for (size_t b : border) {
       const auto& blk = H.blocks[b];
       dofs_off.push_back((int32_t)dofs.size());
       dims.push_back((int32_t)blk.size());
       inv_off.push_back((int64_t)inv.size());
       for (size_t j = 0; j < blk.size(); ++j) {
-        eb[base + blk[j]] = (int32_t)(nb + b);
-        el[base + blk[j]] = (int32_t)j;
+        eb[base + blk[j]] = (int32_t)dofs.size();   // the node's slot in the block results
         dofs.push_back((int32_t)(inst[i].dof_off + blk[j]));
       }
       // stored transposed (column-major) so that the block-solve threads,
@@ -113,8 +116,7 @@ void upload_union_precond(dg_precond* pc, const std::vector<InstSrc>& inst, cuda
   upload_csr_t<T>(a, P, pc->P, s);
   upload_csr_t<T>(a, csr_transpose(P), pc->PT, s);
   pc->dinv = a.upload(std::vector<T>(dinv.begin(), dinv.end()), s);
-  pc->e_block = a.upload(eb, s);
-  pc->e_local = a.upload(el, s);
+  pc->e_pos = a.upload(eb, s);
   pc->blk_inv_off = a.upload(inv_off, s);
   pc->blk_dofs_off = a.upload(dofs_off, s);
   pc->blk_dim = a.upload(dims, s);
