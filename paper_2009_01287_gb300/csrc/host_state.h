@@ -131,17 +131,19 @@ struct dg_precond {
   dg::DevCsr P, PT;          // P: n_dofs x n_c (rows = DG nodes), PT = P^T
   void* dinv = nullptr;      // n_dofs, 1/A_jj on V_J and 0 elsewhere
   int32_t* e_pos = nullptr;     // n_dofs, slot of the node's result in zE, or -1 outside the V_e
-  int64_t* blk_inv_off = nullptr;
-  int32_t* blk_dofs_off = nullptr;
-  int32_t* blk_dim = nullptr;
-  int32_t* blk_dofs = nullptr;
+  // block-solve work units, one per 32-row panel of a V_e block, largest blocks
+  // first: {slot of the block's first node in zE, d, first row, 0} and the offset
+  // of the panel's first row in blk_inv
+  int32_t* blk_unit = nullptr;   // 4 per unit
+  int64_t* blk_ubase = nullptr;
+  int32_t* blk_dofs = nullptr;   // DG node of every slot, block by block
   void* blk_inv = nullptr;   // dense inverses, column-major
   void* lor_inv = nullptr;   // exact LOR solve: dense inverse n_c x n_c
   std::vector<dg::DevLevel> levels;  // AMG (level 0 = LOR matrix)
   void* rc = nullptr;        // n_c restriction of r
   void* ec = nullptr;        // n_c LOR correction
   void* zE = nullptr;        // block-solve results, one per V_e node (block order)
-  int64_t n_blocks = 0, max_block = 0;
+  int64_t n_blocks = 0, max_block = 0, n_units = 0;
   cudaStream_t side = nullptr;   // the block solves run here, beside the V-cycle
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // PCG workspace and captured iteration graph, built on the first solve

@@ -112,40 +112,49 @@ __global__ void dense_mv_kernel(const T* __restrict__ Ainv, const T* __restrict_
   }
 }
 
-// V_e block solves, one CTA per block (Section 3.3, T_E = sum_e P_e): the
-// block's residual entries are gathered into shared memory once, then thread l
-// forms row l of A_e^-1 r_e.  The inverse is stored column-major, so at every
-// step the threads of a warp read consecutive entries of one column, and each
-// thread's loads are independent of its running sum (unrolled, in flight
-// together).
+// V_e block solves (Section 3.3, T_E = sum_e P_e): z_e = A_e^-1 r_e.  A work
+// unit is a panel of 32 consecutive rows of one block and is taken by one warp:
+// lane l forms row row0 + l over all d columns.  The inverse is stored
+// column-major, so every step reads 32 consecutive entries of one column; the
+// block's residual entries are gathered 32 at a time, one per lane, and reach
+// the other lanes by shuffles.  No shared memory and no block barrier; a warp
+// issues a whole chunk of column loads before its first FMA.  Units are sorted
+// by block size (largest first) and dealt round-robin over the grid's warps.
 template <typename T>
-__global__ void __launch_bounds__(128)
-block_solve_kernel(const int64_t* __restrict__ inv_off, const int32_t* __restrict__ dofs_off,
-                   const int32_t* __restrict__ dim, const int32_t* __restrict__ dofs,
-                   const T* __restrict__ inv, const double* __restrict__ r, T* __restrict__ zE,
-                   int nblocks) {
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3)
+block_solve_kernel(const int4* __restrict__ unit, const int64_t* __restrict__ ubase,
+                   const int32_t* __restrict__ dofs, const T* __restrict__ inv,
+                   const double* __restrict__ r, T* __restrict__ zE, int nunits) {
   pdl_entry();
-  extern __shared__ unsigned char smem_raw[];
-  T* sr = reinterpret_cast<T*>(smem_raw);
-  for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
-    const int d = __ldg(dim + b);
-    const int32_t* ds = dofs + __ldg(dofs_off + b);
-    for (int m = threadIdx.x; m < d; m += blockDim.x) sr[m] = (T)__ldg(r + __ldg(ds + m));
-    __syncthreads();
-    // thread l: row l of A_e^-1 (stored column-major: step m reads a contiguous column)
-    const T* At = inv + __ldg(inv_off + b);
-    for (int l = threadIdx.x; l < d; l += blockDim.x) {
-      T acc0 = 0, acc1 = 0;   // even / odd columns: two independent FMA chains
-      int m = 0;
-#pragma unroll 8
-      for (; m + 1 < d; m += 2) {
-        acc0 = fma(__ldg(At + (int64_t)m * d + l), sr[m], acc0);
-        acc1 = fma(__ldg(At + (int64_t)(m + 1) * d + l), sr[m + 1], acc1);
+  constexpr int H = 16;   // column loads per lane in one batch
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nunits; u += nw) {
+    const int4 h = __ldg(unit + u);   // {slot of the block's first node, d, row0, -}
+    const int d = h.y, row = h.z + lane;
+    const bool act = row < d;
+    const T* At = inv + __ldg(ubase + u) + lane;   // column 0 of this lane's row
+    const int32_t* ds = dofs + h.x;
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    for (int c0 = 0; c0 < d; c0 += 32) {
+      const T rv = c0 + lane < d ? (T)__ldg(r + __ldg(ds + c0 + lane)) : (T)0;
+#pragma unroll
+      for (int hh = 0; hh < 32; hh += H) {
+        const int cnt = d - c0 - hh;   // columns left from this half on
+        const T* Ac = At + (int64_t)(c0 + hh) * d;
+        T v[H];
+#pragma unroll
+        for (int j = 0; j < H; ++j) v[j] = (act && j < cnt) ? __ldg(Ac + (int64_t)j * d) : (T)0;
+#pragma unroll
+        for (int j = 0; j < H; j += 4) {
+          a0 = fma(v[j], __shfl_sync(0xffffffffu, rv, hh + j), a0);
+          a1 = fma(v[j + 1], __shfl_sync(0xffffffffu, rv, hh + j + 1), a1);
+          a2 = fma(v[j + 2], __shfl_sync(0xffffffffu, rv, hh + j + 2), a2);
+          a3 = fma(v[j + 3], __shfl_sync(0xffffffffu, rv, hh + j + 3), a3);
+        }
       }
-      if (m < d) acc0 = fma(__ldg(At + (int64_t)m * d + l), sr[m], acc0);
-      zE[__ldg(dofs_off + b) + l] = acc0 + acc1;
     }
-    __syncthreads();
+    if (act) zE[h.x + row] = (a0 + a1) + (a2 + a3);
   }
 }
 
@@ -300,10 +309,11 @@ static void precond_impl(const dg_precond& pc, const double* r, double* z, Reduc
   if (pc.n_blocks > 0) {
     DG_CUDA(cudaEventRecord(pc.ev_fork, s));
     DG_CUDA(cudaStreamWaitEvent(pc.side, pc.ev_fork, 0));
-    int g = (int)(pc.n_blocks < 16 * 152 ? pc.n_blocks : 16 * 152);
-    launch_k(block_solve_kernel<T>, g, 128, (size_t)pc.max_block * sizeof(T), pc.side, 
-        pc.blk_inv_off, pc.blk_dofs_off, pc.blk_dim, pc.blk_dofs, (const T*)pc.blk_inv, r,
-        (T*)pc.zE, (int)pc.n_blocks);
+    // 8 warps per CTA; as many CTAs as the launch bounds keep resident on 152 SMs
+    const int64_t gc = (pc.n_units + 7) / 8, gmax = (sizeof(T) == 8 ? 2 : 3) * 152;
+    const int g = (int)(gc < gmax ? gc : gmax);
+    launch_k(block_solve_kernel<T>, g, 256, 0, pc.side, (const int4*)pc.blk_unit, pc.blk_ubase,
+        pc.blk_dofs, (const T*)pc.blk_inv, r, (T*)pc.zE, (int)pc.n_units);
     DG_CUDA(cudaGetLastError());
     DG_CUDA(cudaEventRecord(pc.ev_join, pc.side));
   }

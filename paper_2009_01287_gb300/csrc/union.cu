@@ -117,15 +117,28 @@ void upload_union_precond(dg_precond* pc, const std::vector<InstSrc>& inst, cuda
   upload_csr_t<T>(a, csr_transpose(P), pc->PT, s);
   pc->dinv = a.upload(std::vector<T>(dinv.begin(), dinv.end()), s);
   pc->e_pos = a.upload(eb, s);
-  pc->blk_inv_off = a.upload(inv_off, s);
-  pc->blk_dofs_off = a.upload(dofs_off, s);
-  pc->blk_dim = a.upload(dims, s);
+  // block-solve units: 32-row panels, largest blocks first over all instances
+  DG_REQUIRE(pc->max_block <= 32 * 256, "a V_e block has more than 8192 nodes");
+  std::vector<int64_t> uorder;
+  for (int64_t b = 0; b < nb; ++b)
+    for (int32_t r0 = 0; r0 < dims[b]; r0 += 32) uorder.push_back(b << 8 | (r0 >> 5));
+  std::stable_sort(uorder.begin(), uorder.end(),
+                   [&](int64_t x, int64_t y) { return dims[x >> 8] > dims[y >> 8]; });
+  std::vector<int32_t> unit;
+  std::vector<int64_t> ubase;
+  for (int64_t k : uorder) {
+    const int64_t b = k >> 8;
+    const int32_t r0 = (int32_t)(k & 255) * 32;
+    unit.insert(unit.end(), {dofs_off[b], dims[b], r0, 0});
+    ubase.push_back(inv_off[b] + r0);
+  }
+  pc->blk_unit = a.upload(unit, s);
+  pc->blk_ubase = a.upload(ubase, s);
   pc->blk_dofs = a.upload(dofs, s);
   pc->blk_inv = a.upload(inv, s);
   pc->zE = a.alloc<T>(dofs.size());
   pc->n_blocks = nb;
-  DG_REQUIRE(pc->max_block * (int64_t)sizeof(T) <= 48 * 1024,
-             "a V_e block is too large for the block-solve kernel's shared memory");
+  pc->n_units = (int64_t)ubase.size();
   pc->n_c = nlev ? nrows[0] : 0;
   // ---- AMG levels
   pc->levels.resize(nlev);
