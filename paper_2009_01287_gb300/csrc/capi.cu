@@ -118,19 +118,6 @@ void host_rhs_sine(const dg_mesh& mesh, int n_modes, const double* amps, const i
 
 // ----------------------------------------------------------------- precond upload
 template <typename T>
-static void upload_csr(DevArena& a, const Csr& C, DevCsr& D, cudaStream_t s) {
-  DG_REQUIRE(C.nnz() < (1LL << 31), "matrix too large for 32-bit indices");
-  std::vector<int32_t> ptr(C.ptr.begin(), C.ptr.end());
-  std::vector<T> val(C.val.begin(), C.val.end());
-  D.rows = C.rows;
-  D.nnz = C.nnz();
-  D.group = csr_group_for(C.rows ? (double)C.nnz() / (double)C.rows : 1.0);
-  D.ptr = a.upload(ptr, s);
-  D.idx = a.upload(C.idx, s);
-  D.val = a.upload(val, s);
-}
-
-template <typename T>
 static void upload_precond(dg_precond* pc, HostPrecond& H, cudaStream_t s) {
   if (pc->lor == DG_LOR_AMG) {
     AmgHierarchy Hm = amg_setup(H.Ac, pc->mesh->host.dim == 3 ? kAmgTheta3 : kAmgTheta);

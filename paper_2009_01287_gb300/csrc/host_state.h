@@ -38,7 +38,14 @@ struct DevCsr {
   int32_t* ptr = nullptr;
   int32_t* idx = nullptr;
   void* val = nullptr;
-  int group = 1;   // lanes per row in the row kernels (power of two <= 32)
+  int group = 1;       // lanes per row in the group tier (power of two <= 32)
+  int group_all = 1;   // lanes per row from the mean of all rows (fused AMG up-sweep)
+  // rows read by a whole CTA (more than kCsrCtaRow entries) and by a whole
+  // warp (more than long_min entries); the group tier skips both
+  int32_t* cta_rows = nullptr;
+  int32_t* warp_rows = nullptr;
+  int n_cta = 0, n_warp = 0;
+  int long_min = 0x7fffffff;
 };
 
 // lanes per row for a CSR with the given average row length
@@ -47,6 +54,17 @@ inline int csr_group_for(double avg) {
   while (g < 32 && g * 2 <= avg) g *= 2;
   return g;
 }
+
+// rows with more entries than this are read by a whole CTA in the row kernels
+constexpr int kCsrCtaRow = 1024;
+
+// the CTA and warp tiers of a CSR row kernel launch (see DevCsr)
+struct CsrTiers {
+  const int32_t* cta_rows;
+  const int32_t* warp_rows;
+  int n_cta, n_warp;
+  int long_min;
+};
 
 struct DevLevel {
   int64_t n = 0;

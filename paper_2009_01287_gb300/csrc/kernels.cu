@@ -9,29 +9,63 @@ namespace dg {
 
 // ============================================================== preconditioner
 
-// ---- group-per-row CSR kernels: G lanes of a warp share one row, strided
-// over its entries, then a fixed shuffle tree (deterministic for a fixed G).
-// The row loop advances by whole warps so that every lane of a warp reaches
-// the shuffles together.
+// ---- CSR row kernels in three tiers (the rows of P^T and of the AMG levels
+// are very uneven): rows longer than kCsrCtaRow entries take one CTA each
+// (entries strided over the CTA, fixed block tree), rows longer than
+// long_min take one warp each (fixed shuffle tree), and the rest are read by
+// G lanes per row (fixed shuffle tree over G).  The grid holds the CTA-tier
+// CTAs first, then the warp tier (8 rows per CTA), then the group tier, whose
+// row loop advances by whole warps so that every lane reaches the shuffles.
+// Every sum has a fixed order, so the results are deterministic.
 template <typename T, int G, class Op>
 __global__ void __launch_bounds__(kVecThreads)
 csr_rows_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-                const T* __restrict__ val, int64_t rows, Op op) {
+                const T* __restrict__ val, int64_t rows, CsrTiers tiers, Op op) {
   pdl_entry();
+  int bid = blockIdx.x;
+  if (bid < tiers.n_cta) {
+    __shared__ double sred[kVecThreads];
+    const int row = __ldg(tiers.cta_rows + bid);
+    const int e = ptr[row + 1];
+    T s = 0;
+    for (int t = ptr[row] + threadIdx.x; t < e; t += kVecThreads) s += __ldg(val + t) * op.x(__ldg(idx + t));
+    const double tot = block_sum<kVecThreads>((double)s, sred);
+    if (threadIdx.x == 0) op.store(row, (T)tot);
+    return;
+  }
+  bid -= tiers.n_cta;
+  const int warp_ctas = (tiers.n_warp + 7) >> 3;
+  if (bid < warp_ctas) {
+    const int w = bid * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (w >= tiers.n_warp) return;   // whole warps leave together
+    const int row = __ldg(tiers.warp_rows + w);
+    const int e = ptr[row + 1];
+    T s = 0;
+    for (int t = ptr[row] + lane; t < e; t += 32) s += __ldg(val + t) * op.x(__ldg(idx + t));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) op.store(row, s);
+    return;
+  }
+  bid -= warp_ctas;
+  const int nb = gridDim.x - tiers.n_cta - warp_ctas;
   const int lane = threadIdx.x % G;
-  const int64_t groups_per_grid = ((int64_t)gridDim.x * blockDim.x) / G;
-  const int64_t g0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+  const int64_t groups_per_grid = ((int64_t)nb * blockDim.x) / G;
+  const int64_t g0 = (bid * (int64_t)blockDim.x + threadIdx.x) / G;
   const int64_t rounds = (rows + groups_per_grid - 1) / groups_per_grid;
   for (int64_t rd = 0; rd < rounds; ++rd) {
     const int64_t row = g0 + rd * groups_per_grid;
     T s = 0;
+    bool mine = false;
     if (row < rows) {
-      const int e = ptr[row + 1];
-      for (int t = ptr[row] + lane; t < e; t += G) s += __ldg(val + t) * op.x(__ldg(idx + t));
+      const int b = ptr[row], e = ptr[row + 1];
+      mine = e - b <= tiers.long_min;
+      if (mine)
+        for (int t = b + lane; t < e; t += G) s += __ldg(val + t) * op.x(__ldg(idx + t));
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, G);
-    if (row < rows && lane == 0) op.store(row, s);
+    if (mine && lane == 0) op.store(row, s);
   }
 }
 
@@ -86,14 +120,18 @@ static void launch_rows(const DevCsr& A, const Op& op, cudaStream_t s) {
   const int32_t* p = A.ptr;
   const int32_t* ix = A.idx;
   const T* v = (const T*)A.val;
+  const CsrTiers tr{A.cta_rows, A.warp_rows, A.n_cta, A.n_warp, A.long_min};
+  const int g = (int)blocks + A.n_cta + (A.n_warp + 7) / 8;
+#define DG_ROWS(G) launch_k(csr_rows_kernel<T, G, Op>, g, kVecThreads, 0, s, p, ix, v, A.rows, tr, op)
   switch (A.group) {
-    case 1: launch_k(csr_rows_kernel<T, 1, Op>, (int)blocks, kVecThreads, 0, s, p, ix, v, A.rows, op); break;
-    case 2: launch_k(csr_rows_kernel<T, 2, Op>, (int)blocks, kVecThreads, 0, s, p, ix, v, A.rows, op); break;
-    case 4: launch_k(csr_rows_kernel<T, 4, Op>, (int)blocks, kVecThreads, 0, s, p, ix, v, A.rows, op); break;
-    case 8: launch_k(csr_rows_kernel<T, 8, Op>, (int)blocks, kVecThreads, 0, s, p, ix, v, A.rows, op); break;
-    case 16: launch_k(csr_rows_kernel<T, 16, Op>, (int)blocks, kVecThreads, 0, s, p, ix, v, A.rows, op); break;
-    default: launch_k(csr_rows_kernel<T, 32, Op>, (int)blocks, kVecThreads, 0, s, p, ix, v, A.rows, op); break;
+    case 1: DG_ROWS(1); break;
+    case 2: DG_ROWS(2); break;
+    case 4: DG_ROWS(4); break;
+    case 8: DG_ROWS(8); break;
+    case 16: DG_ROWS(16); break;
+    default: DG_ROWS(32); break;
   }
+#undef DG_ROWS
 }
 
 // dense y = Ainv x, one warp per row
@@ -205,7 +243,7 @@ static int grid_for(int64_t n, int threads = kVecThreads) {
 }
 
 int precond_final_blocks(const dg_precond& pc) {
-  int64_t b = (pc.n_dofs * pc.P.group + kVecThreads - 1) / kVecThreads;
+  int64_t b = (pc.n_dofs * pc.P.group_all + kVecThreads - 1) / kVecThreads;
   if (b > kVecBlocks) b = kVecBlocks;
   return (int)(b < 1 ? 1 : b);
 }
@@ -238,12 +276,12 @@ amg_up_kernel(const int32_t* __restrict__ bp, const int32_t* __restrict__ bi, co
 template <typename T>
 static void launch_up(const DevLevel& L, const T* b, const T* xc, T* xo, cudaStream_t s) {
   if (L.n_cont == 0) return;
-  int64_t blocks = (L.n_cont * (int64_t)L.Sb.group + kVecThreads - 1) / kVecThreads;
+  int64_t blocks = (L.n_cont * (int64_t)L.Sb.group_all + kVecThreads - 1) / kVecThreads;
   if (blocks > 8 * 152) blocks = 8 * 152;
 #define DG_UP(G)                                                                                  \
   launch_k(amg_up_kernel<T, G>, (int)blocks, kVecThreads, 0, s, L.Sb.ptr, L.Sb.idx,              \
            (const T*)L.Sb.val, L.Sp.ptr, L.Sp.idx, (const T*)L.Sp.val, b, xc, xo, L.n_cont)
-  switch (L.Sb.group) {
+  switch (L.Sb.group_all) {
     case 1: DG_UP(1); break;
     case 2: DG_UP(2); break;
     case 4: DG_UP(4); break;
@@ -336,8 +374,8 @@ static void precond_impl(const dg_precond& pc, const double* r, double* z, Reduc
   launch_k(precond_final_kernel<T, G>, nb, kVecThreads, 0, s,                                      \
       pc.P.ptr, pc.P.idx, (const T*)pc.P.val, (const T*)ec, (const T*)pc.dinv, pc.e_pos,     \
       (const T*)pc.zE, r, z, pc.n_dofs, red)
-  if (pc.P.group <= 1) DG_FINAL(1);
-  else if (pc.P.group == 2) DG_FINAL(2);
+  if (pc.P.group_all <= 1) DG_FINAL(1);
+  else if (pc.P.group_all == 2) DG_FINAL(2);
   else DG_FINAL(4);
 #undef DG_FINAL
   DG_CUDA(cudaGetLastError());

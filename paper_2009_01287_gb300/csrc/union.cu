@@ -41,7 +41,33 @@ void upload_csr_t(DevArena& a, const Csr& C, DevCsr& D, cudaStream_t s) {
   std::vector<T> val(C.val.begin(), C.val.end());
   D.rows = C.rows;
   D.nnz = C.nnz();
-  D.group = csr_group_for(C.rows ? (double)C.nnz() / (double)C.rows : 1.0);
+  D.group_all = csr_group_for(C.rows ? (double)C.nnz() / (double)C.rows : 1.0);
+  // row tiers: the group width follows the rows of at most 64 entries; rows
+  // longer than 8 group rounds go to a warp each, rows longer than
+  // kCsrCtaRow to a CTA each (longest first in both lists)
+  double ssum = 0.0;
+  int64_t scnt = 0;
+  for (int64_t i = 0; i < C.rows; ++i) {
+    const int64_t len = C.ptr[i + 1] - C.ptr[i];
+    if (len <= 64) ssum += (double)len, ++scnt;
+  }
+  D.group = csr_group_for(scnt ? ssum / (double)scnt : 64.0);
+  D.long_min = D.group >= 32 ? kCsrCtaRow : std::max(8 * D.group, 16);
+  std::vector<int32_t> cta, warp;
+  for (int64_t i = 0; i < C.rows; ++i) {
+    const int64_t len = C.ptr[i + 1] - C.ptr[i];
+    if (len > kCsrCtaRow) cta.push_back((int32_t)i);
+    else if (len > D.long_min) warp.push_back((int32_t)i);
+  }
+  auto longer = [&](int32_t x, int32_t y) {
+    return C.ptr[x + 1] - C.ptr[x] > C.ptr[y + 1] - C.ptr[y];
+  };
+  std::stable_sort(cta.begin(), cta.end(), longer);
+  std::stable_sort(warp.begin(), warp.end(), longer);
+  D.n_cta = (int)cta.size();
+  D.n_warp = (int)warp.size();
+  if (!cta.empty()) D.cta_rows = a.upload(cta, s);
+  if (!warp.empty()) D.warp_rows = a.upload(warp, s);
   D.ptr = a.upload(ptr, s);
   D.idx = a.upload(C.idx, s);
   D.val = a.upload(val, s);
@@ -198,7 +224,7 @@ void upload_union_precond(dg_precond* pc, const std::vector<InstSrc>& inst, cuda
       upload_csr_t<T>(a, Sp, D.Sp, s);
       upload_csr_t<T>(a, Rp, D.Rpre, s);
       // lanes per row of the fused up-sweep: both operators' rows together
-      D.Sb.group = csr_group_for(ncont[l] ? (double)(Sb.nnz() + Sp.nnz()) / (double)ncont[l] : 1.0);
+      D.Sb.group_all = csr_group_for(ncont[l] ? (double)(Sb.nnz() + Sp.nnz()) / (double)ncont[l] : 1.0);
     }
     D.n_end = (int)end_off.size();
     D.end_row = a.upload(end_row, s);
