@@ -109,6 +109,7 @@ seg_update_xr_kernel(SegView v, double* __restrict__ x, double* __restrict__ r,
                      const double* part_pq, double* part_rr) {
   pdl_entry();
   __shared__ double red[kSegThreads];
+  __shared__ double s_q;
   for (int c = blockIdx.x; c < v.nchunks; c += gridDim.x) {
     const int inst = v.c_inst[c];
     const double* s = sc + BS_N * inst;
@@ -116,7 +117,10 @@ seg_update_xr_kernel(SegView v, double* __restrict__ x, double* __restrict__ r,
       if (threadIdx.x == 0) part_rr[c] = 0.0;
       continue;
     }
-    const double alpha = s[BS_RZ] / inst_sum(v, part_pq, inst, red);
+    const double pq = inst_sum(v, part_pq, inst, red);
+    if (threadIdx.x == 0) s_q = s[BS_RZ] / pq;   // one FP64 division per chunk
+    __syncthreads();
+    const double alpha = s_q;
     double acc = 0.0;
     for (int64_t i = v.c_beg[c] + threadIdx.x; i < v.c_end[c]; i += kSegThreads) {
       x[i] = fma(alpha, p[i], x[i]);
@@ -139,12 +143,15 @@ seg_update_p_kernel(SegView v, double* __restrict__ p, const double* __restrict_
   pdl_entry();
   __shared__ double red[kSegThreads];
   __shared__ unsigned s_last;
+  __shared__ double s_q;
   for (int c = blockIdx.x; c < v.nchunks; c += gridDim.x) {
     const int inst = v.c_inst[c];
     double* s = sc + BS_N * inst;
     if (s[BS_STATUS] != 0.0) continue;
     const double rz_new = inst_sum(v, part_rz, inst, red);
-    const double beta = rz_new / s[BS_RZ];
+    if (threadIdx.x == 0) s_q = rz_new / s[BS_RZ];   // one FP64 division per chunk
+    __syncthreads();
+    const double beta = s_q;
     for (int64_t i = v.c_beg[c] + threadIdx.x; i < v.c_end[c]; i += kSegThreads)
       p[i] = fma(beta, p[i], z[i]);
     const double rr = inst_sum(v, part_rr, inst, red);   // every CTA reads rz before its ticket

@@ -197,9 +197,11 @@ block_solve_kernel(const int4* __restrict__ unit, const int64_t* __restrict__ ub
 }
 
 // z = P e_C + D_J^-1 r + (block result on V_e nodes), and the r . z reduction.
-// G lanes per DG row share its P entries.
+// G lanes per DG row share its P entries; the row's own terms (r, D_J^-1, the
+// block result) are loaded before the P entries so that both chains of loads
+// are in flight together.
 template <typename T, int G>
-__global__ void __launch_bounds__(kVecThreads)
+__global__ void __launch_bounds__(kVecThreads, 8)
 precond_final_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
                      const T* __restrict__ val, const T* __restrict__ ec,
                      const T* __restrict__ dinv, const int32_t* __restrict__ e_pos,
@@ -214,16 +216,24 @@ precond_final_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict_
   double dot = 0.0;
   for (int64_t rd = 0; rd < rounds; ++rd) {
     const int64_t i = g0 + rd * groups_per_grid;
-    T s = 0;
-    if (i < n)
+    T s = 0, tj = 0, te = 0;
+    double ri = 0.0;
+    bool has_e = false;
+    if (i < n) {
+      if (lane == 0) {
+        ri = __ldg(r + i);
+        tj = __ldg(dinv + i) * (T)ri;
+        const int ep = __ldg(e_pos + i);
+        has_e = ep >= 0;
+        if (has_e) te = __ldg(zE + ep);
+      }
       for (int t = ptr[i] + lane; t < ptr[i + 1]; t += G) s += __ldg(val + t) * __ldg(ec + __ldg(idx + t));
+    }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, G);
     if (i < n && lane == 0) {
-      const double ri = __ldg(r + i);
-      s += __ldg(dinv + i) * (T)ri;
-      const int ep = __ldg(e_pos + i);
-      if (ep >= 0) s += __ldg(zE + ep);
+      s += tj;
+      if (has_e) s += te;
       const double zi = (double)s;
       z[i] = zi;
       dot += zi * ri;
@@ -426,9 +436,16 @@ pcg_update_xr_kernel(double* __restrict__ x, double* __restrict__ r, const doubl
                      const double* __restrict__ q, int64_t n, double* sc, Reduce rr) {
   pdl_entry();
   __shared__ double red[kVecThreads];
+  __shared__ double s_alpha;
   if (sc[SC_STATUS] != 0.0) return;  // converged or stopped: iterations queued after it are no-ops
-  const double alpha = sc[SC_RZ] / sc[SC_PQ];
-  if (blockIdx.x == 0 && threadIdx.x == 0) sc[SC_ALPHA] = alpha;
+  // an FP64 division is a sequence of FP64 instructions: one thread per CTA
+  // forms it, the others read it from shared memory
+  if (threadIdx.x == 0) {
+    s_alpha = sc[SC_RZ] / sc[SC_PQ];
+    if (blockIdx.x == 0) sc[SC_ALPHA] = s_alpha;
+  }
+  __syncthreads();
+  const double alpha = s_alpha;
   double s = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -458,11 +475,15 @@ pcg_p_trace_kernel(const ApplyArgs A, double* __restrict__ p, const double* __re
                    int first) {
   pdl_entry();
   __shared__ unsigned s_last;
+  __shared__ double s_beta;
   if (!first && sc[SC_STATUS] != 0.0) {
     if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
     return;
   }
-  const double beta = first ? 0.0 : sc[SC_RZNEW] / sc[SC_RZ];
+  // one FP64 division per CTA, shared through shared memory
+  if (threadIdx.x == 0) s_beta = first ? 0.0 : sc[SC_RZNEW] / sc[SC_RZ];
+  __syncthreads();
+  const double beta = s_beta;
   const ApplyTile T = A.tiles[blockIdx.x];
   const int np = T.p + 1;
   const int nn = CUBE ? np * np * np : np * np;

@@ -8,7 +8,7 @@
 namespace dg {
 
 constexpr int kVecThreads = 256;
-constexpr int kVecBlocks = 608;   // 4 x 152 SMs: fixed so reductions are deterministic
+constexpr int kVecBlocks = 1216;   // 8 x 152 SMs: fixed so reductions are deterministic
 
 // resident CTAs of the persistent operator kernel of this mesh (sets the
 // kernel's shared-memory opt-in on the current device)
