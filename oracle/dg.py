@@ -36,10 +36,14 @@ from .topology import Topology
 
 
 class DGSpace:
-    def __init__(self, topo: Topology, lattice_h: float):
+    def __init__(self, topo: Topology, lattice_h: float, coef=None):
         self.topo = topo
         self.dim = int(getattr(topo, "dim", 2))
         self.lh = float(lattice_h)
+        # piecewise-constant diffusion coefficient a, one value per element
+        # (the random-refinement problem of Section 4.3); None means a = 1
+        self.coef = (np.ones(topo.n) if coef is None
+                     else np.asarray(coef, dtype=np.float64).reshape(topo.n).copy())
         p = topo.p
         self.ndof_elem = (p + 1) ** self.dim
         self.offset = np.zeros(topo.n + 1, dtype=np.int64)
@@ -140,23 +144,30 @@ class DGSpace:
 
 
 def penalty(space: DGSpace, f, eta: float, form: str) -> float:
+    """SIPG penalty of a sub-face (Section 2): eta p_e^2 / h_e with p_e the
+    larger degree and h_e the smaller size of the two sides, times the larger
+    coefficient of the two sides."""
     t = space.topo
     if f.kp >= 0:
         pe = max(int(t.p[f.km]), int(t.p[f.kp]))
         he = min(space.h(f.km), space.h(f.kp))
+        ae = max(space.coef[f.km], space.coef[f.kp])
     else:
-        pe, he = int(t.p[f.km]), space.h(f.km)
+        pe, he, ae = int(t.p[f.km]), space.h(f.km), space.coef[f.km]
     if form == "paper":
-        return eta * pe * pe / he
+        return ae * eta * pe * pe / he
     if form == "p1sq":
-        return eta * (pe + 1) ** 2 / he
+        return ae * eta * (pe + 1) ** 2 / he
     raise ValueError(form)
 
 
 def assemble(space: DGSpace, eta: float, form: str = "sipg",
              penalty_form: str = "paper", broken_only: bool = False) -> sp.csr_matrix:
-    """Sparse DG matrix.  form: "sipg" or "br2".  broken_only: the broken
-    Laplacian A-hat of Section 3.4 (volume terms only)."""
+    """Sparse DG matrix of -div(a grad u) = f.  form: "sipg" or "br2".
+    broken_only: the broken Laplacian A-hat of Section 3.4 (volume terms only).
+    With a coefficient a: a_k on the volume term of element k, the face
+    averages of a grad u, the SIPG penalty times the larger a of the two sides,
+    and each side's BR2 lifting energy times that side's a."""
     topo = space.topo
     rows, cols, vals = [], [], []
 
@@ -171,7 +182,7 @@ def assemble(space: DGSpace, eta: float, form: str = "sipg",
         pts, W = space.volume_quadrature(k, p + 1)
         _, g = space.eval(k, pts)
         K = sum((g[:, :, d].T * W) @ g[:, :, d] for d in range(space.dim))
-        add(space.dofs(k), space.dofs(k), K)
+        add(space.dofs(k), space.dofs(k), space.coef[k] * K)
 
     if not broken_only:
         for f in topo.subfaces:
@@ -185,7 +196,7 @@ def assemble(space: DGSpace, eta: float, form: str = "sipg",
                 sgn = 1.0 if si == 0 else -1.0
                 jump_parts.append(sgn * v)                 # [[phi]] . n
                 dn = g @ n                                  # grad phi . n
-                avg_parts.append((0.5 if interior else 1.0) * dn)
+                avg_parts.append((0.5 if interior else 1.0) * space.coef[k] * dn)   # {a grad phi} . n
                 idx.append(space.dofs(k))
             J = np.concatenate(jump_parts, axis=1)        # (q, nloc)
             D = np.concatenate(avg_parts, axis=1)
@@ -200,7 +211,7 @@ def assemble(space: DGSpace, eta: float, form: str = "sipg",
                     v, _ = space.eval(k, pts)
                     b = (v.T * W) @ J                       # b[i, a] = int_e phi_i^k j_a
                     Minv = np.linalg.inv(space.mass(k))
-                    F = F + eta * coef * (b.T @ Minv @ b)
+                    F = F + eta * coef * space.coef[k] * (b.T @ Minv @ b)
             else:
                 raise ValueError(form)
             add(I, I, F)
@@ -230,7 +241,7 @@ def element_rows(space: DGSpace, k: int, x: np.ndarray, eta: float, form: str = 
     pts, W = space.volume_quadrature(k, p + 1)
     _, g = space.eval(k, pts)
     K = sum((g[:, :, d].T * W) @ g[:, :, d] for d in range(space.dim))
-    y = K @ x[space.dofs(k)]
+    y = space.coef[k] * (K @ x[space.dofs(k)])
     for f in topo.faces_of(k):
         sides = [f.km] + ([f.kp] if f.kp >= 0 else [])
         q = max(int(topo.p[e]) for e in sides) + 1
@@ -240,7 +251,7 @@ def element_rows(space: DGSpace, k: int, x: np.ndarray, eta: float, form: str = 
         for si, e in enumerate(sides):
             v, gg = space.eval(e, fpts)
             J.append((1.0 if si == 0 else -1.0) * v)
-            D.append((0.5 if interior else 1.0) * (gg @ n))
+            D.append((0.5 if interior else 1.0) * space.coef[e] * (gg @ n))
             I.append(space.dofs(e))
         Jm, Dm, Im = np.concatenate(J, axis=1), np.concatenate(D, axis=1), np.concatenate(I)
         F = -(Jm.T * FW) @ Dm - (Dm.T * FW) @ Jm
@@ -251,7 +262,7 @@ def element_rows(space: DGSpace, k: int, x: np.ndarray, eta: float, form: str = 
             for e in sides:
                 v, _ = space.eval(e, fpts)
                 b = (v.T * FW) @ Jm
-                F = F + eta * coef * (b.T @ np.linalg.inv(space.mass(e)) @ b)
+                F = F + eta * coef * space.coef[e] * (b.T @ np.linalg.inv(space.mass(e)) @ b)
         nk = (p + 1) ** space.dim
         rows = slice(0, nk) if f.km == k else slice(len(I[0]), len(I[0]) + nk)
         y = y + F[rows] @ x[Im]

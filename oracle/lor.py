@@ -74,9 +74,11 @@ def lor_element(p: int, h: float = 1.0, dim: int = 2) -> np.ndarray:
 
 
 def assemble_lor(space: DGSpace) -> sp.csr_matrix:
+    """Block-diagonal A-tilde; element k's block is scaled by its coefficient
+    a_k, so that A-tilde discretises the same -div(a grad u) as A."""
     blocks = []
     for k in range(space.topo.n):
-        blocks.append(lor_element(int(space.topo.p[k]), space.h(k), space.dim))
+        blocks.append(space.coef[k] * lor_element(int(space.topo.p[k]), space.h(k), space.dim))
     return sp.block_diag([sp.csr_matrix(b) for b in blocks], format="csr")
 
 

@@ -35,6 +35,9 @@ class MeshDesc:
     p: np.ndarray           # int32 (n,)
     extent: Tuple[int, ...]  # lattice units per axis
     lattice_h: float
+    # float64 (n,) piecewise-constant diffusion coefficient a per leaf, or
+    # None for a = 1
+    coeff: Optional[np.ndarray] = None
 
     @property
     def n_elems(self) -> int:
@@ -105,6 +108,24 @@ def random_refined_mesh(dim: int, base: int, max_depth: int, prob: float,
                     extent=extent, lattice_h=1.0 / float(base * cell))
 
 
+def base_parity_coeff(mesh: MeshDesc, base: int, values=(1.0, 20.0)) -> np.ndarray:
+    """Coefficient of the random-refinement problem (Section 4.3): a takes the
+    two values by the parity of the lexicographic number (x fastest) of the
+    base cell that holds each leaf."""
+    cell = mesh.extent[0] // base
+    bc = mesh.lo // cell
+    num = np.zeros(mesh.n_elems, dtype=np.int64)
+    stride = 1
+    for d in range(mesh.dim):
+        num += bc[:, d].astype(np.int64) * stride
+        stride *= mesh.extent[d] // cell
+    return np.where(num % 2 == 0, values[0], values[1]).astype(np.float64)
+
+
+def with_coeff(mesh: MeshDesc, coeff: np.ndarray) -> MeshDesc:
+    return dataclasses.replace(mesh, coeff=np.asarray(coeff, dtype=np.float64))
+
+
 def uniform_mesh(dim: int, base: int, p: int) -> MeshDesc:
     """Conforming `base`^dim grid of unit squares/cubes with uniform degree p."""
     cells = [tuple(reversed(c)) for c in np.ndindex(*([base] * dim))]
@@ -136,6 +157,13 @@ def config0() -> Tuple[MeshDesc, SineRHS]:
 def config1(seed: int = 0) -> Tuple[MeshDesc, SineRHS]:
     """2D hp-random: 32x32 base, prob 0.3, depth <= 3, p ~ U{1..6} (~1e5 DOFs)."""
     return random_refined_mesh(2, 32, 3, 0.3, 1, 6, seed), sine_rhs(2, seed)
+
+
+def config1_coeff(seed: int = 0) -> Tuple[MeshDesc, SineRHS]:
+    """The 2D hp-random workload with the coefficient a in {1, 20} of the
+    random-refinement problem (by base-cell parity)."""
+    mesh, rhs = config1(seed)
+    return with_coeff(mesh, base_parity_coeff(mesh, 32)), rhs
 
 
 def config2(seed: int = 0, base: int = 16) -> Tuple[MeshDesc, SineRHS]:
