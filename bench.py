@@ -10,6 +10,10 @@ runs the operator apply, the preconditioner and the vector updates).
 preconditioner, FP64 operator / residual / dots); the FP64 solve is timed
 beside it.  L2 is flushed (a 512 MiB write) before every timed step.
 
+--workload hp2d-coef runs the same mesh with the piecewise-constant coefficient
+a in {1, 20} of the random-refinement problem (Section 4.3); hp3d the cube
+workload; batched and serving the B1 and V1 forms.
+
 --impl reference times the FP64 CPU oracle on the same workload (a bounded
 sample of PCG iterations per step).  Multi-GPU: independent replicas
 (the problem does not shard), one per rank.
@@ -35,19 +39,27 @@ METRIC = "DOF-iters/s (PCG on the 2D hp-random workload, mixed FP32 precondition
 WORKLOAD3 = ("3D hp-random 16^3 base, prob 0.2, depth<=2, p~U{1..5}, BR2 (eta = most sub-faces of one "
              "element), tol 1e-8, seed 0")
 METRIC3 = "DOF-iters/s (PCG on the 3D hp-random workload, mixed FP32 preconditioner / FP64 outer)"
+WORKLOADC = ("2D hp-random 32x32 base, prob 0.3, depth<=3, p~U{1..6}, coefficient a in {1, 20} by base-cell "
+             "parity, SIPG eta=100 (times the larger a of the two sides), tol 1e-8, seed 0")
+METRICC = ("DOF-iters/s (PCG on the 2D hp-random workload with a piecewise-constant coefficient, mixed FP32 "
+           "preconditioner / FP64 outer)")
 ORACLE_SAMPLE_ITERS = 20
 
 # DRAM bytes (read + write) of one apply_kernel launch on this workload, from
 # the ncu capture summarised in profiles/apply_kernel_hp2d_32x32.md.  Valid
-# only for the kernel sources it was taken on: the line reports null traffic
-# as soon as their hash differs.
+# only for the kernel and tile-building sources it was taken on: the line
+# reports null traffic as soon as their hash differs.
 APPLY_TRAFFIC = {"sources": ["paper_2009_01287_gb300/csrc/apply_kernel.cuh",
-                             "paper_2009_01287_gb300/csrc/apply_launch.cu"],
+                             "paper_2009_01287_gb300/csrc/apply_launch.cu",
+                             "paper_2009_01287_gb300/csrc/dg_internal.h",
+                             "paper_2009_01287_gb300/csrc/mesh.cpp"],
                  "sha256_16": "d2b5098a6ef33efd", "bytes": 3513600 + 0}
 # likewise for the 3D operator (profiles/apply3_kernel_hp3d_16cube.md)
 APPLY3_TRAFFIC = {"sources": ["paper_2009_01287_gb300/csrc/apply_kernel.cuh",
                               "paper_2009_01287_gb300/csrc/apply3_kernel.cuh",
-                              "paper_2009_01287_gb300/csrc/apply_launch.cu"],
+                              "paper_2009_01287_gb300/csrc/apply_launch.cu",
+                              "paper_2009_01287_gb300/csrc/dg_internal.h",
+                              "paper_2009_01287_gb300/csrc/mesh3.cpp"],
                   "sha256_16": "b8ae8d3d92b398a1", "bytes": 66526976 + 4917760}
 
 
@@ -147,7 +159,11 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     three = args.workload == "hp3d"
-    mesh, rh = inputs.config2(args.seed) if three else inputs.config1(args.seed)
+    coef = args.workload == "hp2d-coef"
+    if three:
+        mesh, rh = inputs.config2(args.seed)
+    else:
+        mesh, rh = inputs.config1_coeff(args.seed) if coef else inputs.config1(args.seed)
     form = B.DG_FORM_BR2 if three else B.DG_FORM_SIPG
     opts64 = B.make_options(form=form, precision=B.DG_PREC_FP64, lor=B.DG_LOR_AMG)
     opts32 = B.make_options(form=form, precision=B.DG_PREC_MIXED, lor=B.DG_LOR_AMG)
@@ -242,7 +258,7 @@ def run_ours(args):
     kernels_per_iter = 1 + 1 + precond_kernels + 1
     launches = sum(2 + precond_kernels + it * kernels_per_iter for it in it32)  # + init, first p
     out = {
-        "metric": METRIC3 if three else METRIC,
+        "metric": METRIC3 if three else (METRICC if coef else METRIC),
         "value": value,
         "unit": "DOF-iters/s",
         "n_gpus": ws,
@@ -254,7 +270,8 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f64 (outer PCG, operator) + f32 (preconditioner)",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD3 if three else WORKLOAD, "n_dofs": n, "n_elems": int(stats.n_elems),
+        "config": {"workload": WORKLOAD3 if three else (WORKLOADC if coef else WORKLOAD), "n_dofs": n,
+                   "n_elems": int(stats.n_elems),
                    "n_conforming": int(s32.n_conforming), "amg_levels": levels,
                    "n_blocks": int(s32.n_blocks), "max_block": int(s32.max_block),
                    "amg_plain_levels": [int(s32.level_plain[i]) for i in range(levels)],
@@ -272,7 +289,7 @@ def run_ours(args):
         "roofline": {"kernel": ("apply3_kernel (BR2 operator on cubes, FP64)" if three
                                 else "apply_kernel (SIPG operator, FP64)"), "bound": "alu",
                      "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": achieved_tf / fp64_peak, "traffic": apply_traffic(three),
+                     "frac": achieved_tf / fp64_peak, "traffic": None if coef else apply_traffic(three),
                      "algorithmic_bytes": stats.apply_bytes,
                      "flops_per_launch": stats.apply_flops, "launch_ms": apply_ms,
                      "hbm_gbs": stats.apply_bytes / (apply_ms / 1e3) / 1e9,
@@ -282,7 +299,7 @@ def run_ours(args):
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        out["cpu_baseline"] = cpu_baseline3(args) if three else cpu_baseline(args)
+        out["cpu_baseline"] = cpu_baseline3(args) if three else cpu_baseline(args, coef)
     if rank == 0:
         print(json.dumps(out))
     if dist:
@@ -425,10 +442,10 @@ def run_batched(args):
     print(json.dumps(out))
 
 
-def _oracle_setup(seed: int):
+def _oracle_setup(seed: int, coef: bool = False):
     from oracle import rhs, solver
     from paper_2009_01287_gb300 import inputs
-    mesh, rh = inputs.config1(seed)
+    mesh, rh = inputs.config1_coeff(seed) if coef else inputs.config1(seed)
     prob = solver.build_problem(mesh)
     pc = solver.Preconditioner(prob, lor="amg")
     b = rhs.load_vector(prob.space, rh.amps, rh.waves)
@@ -459,8 +476,8 @@ def cpu_baseline3(args):
                       f"({prob.space.n} DOFs; setup untimed), scipy sparse + numpy, one thread"}
 
 
-def cpu_baseline(args):
-    prob, pc, b = _oracle_setup(args.seed)
+def cpu_baseline(args, coef: bool = False):
+    prob, pc, b = _oracle_setup(args.seed, coef)
     dt = _oracle_step(prob, pc, b, ORACLE_SAMPLE_ITERS)
     return {"value": prob.space.n * ORACLE_SAMPLE_ITERS / dt, "unit": "DOF-iters/s", "cores": 1,
             "kind": "oracle",
@@ -509,7 +526,7 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="hp2d", choices=["hp2d", "hp3d", "batched", "serving"])
+    ap.add_argument("--workload", default="hp2d", choices=["hp2d", "hp2d-coef", "hp3d", "batched", "serving"])
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-meshes", type=int, default=16)

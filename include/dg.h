@@ -49,11 +49,17 @@ typedef struct dg_mesh dg_mesh;
 typedef struct dg_precond dg_precond;
 
 /* Leaf boxes on an integer lattice (Section 2: mesh T, degrees p_kappa).
- * dim must be 2.  lo: n_elems*dim lower corners (lattice units); size:
- * n_elems edge lengths (powers of two); p: n_elems degrees in 1..8;
- * extent: dim domain lengths in lattice units; the physical domain is
- * [0, extent_0*lattice_h] x [0, extent_1*lattice_h].  The boxes must tile
- * the domain exactly.  All pointers are HOST pointers, read during the call. */
+ * dim is 2 (squares) or 3 (cubes).  lo: n_elems*dim lower corners (lattice
+ * units); size: n_elems edge lengths (powers of two); p: n_elems degrees in
+ * 1..8; extent: dim domain lengths in lattice units; the physical domain is
+ * [0, extent_0*lattice_h] x ... .  The boxes must tile the domain exactly.
+ * coeff: NULL (a = 1) or n_elems values a_kappa > 0 of the piecewise-constant
+ * coefficient of -div(a grad u) = f (Section 4.3, random refinement): a_kappa
+ * weights element kappa's volume term, its share of the face averages
+ * {a grad u} and its BR2 lifting energy; the SIPG penalty of a sub-face takes
+ * the larger a of its two sides; the LOR blocks are weighted by a_kappa.
+ * A value that is not positive and finite is DG_EINVAL.  All pointers are
+ * HOST pointers, read during the call. */
 typedef struct {
   int dim;
   int64_t n_elems;
@@ -62,6 +68,7 @@ typedef struct {
   const int32_t* p;
   const int32_t* extent;
   double lattice_h;
+  const double* coeff;
 } dg_mesh_desc;
 
 enum { DG_FORM_SIPG = 0, DG_FORM_BR2 = 1 };

@@ -38,7 +38,8 @@ ABI_SYMBOLS = (
 class DgMeshDesc(C.Structure):
     _fields_ = [("dim", C.c_int), ("n_elems", C.c_int64), ("lo", C.POINTER(C.c_int32)),
                 ("size", C.POINTER(C.c_int32)), ("p", C.POINTER(C.c_int32)),
-                ("extent", C.POINTER(C.c_int32)), ("lattice_h", C.c_double)]
+                ("extent", C.POINTER(C.c_int32)), ("lattice_h", C.c_double),
+                ("coeff", C.POINTER(C.c_double))]
 
 
 class DgOptions(C.Structure):
@@ -147,10 +148,14 @@ def make_desc(mesh: MeshDesc):
     size = np.ascontiguousarray(mesh.size, dtype=np.int32)
     p = np.ascontiguousarray(mesh.p, dtype=np.int32)
     ext = np.ascontiguousarray(mesh.extent, dtype=np.int32)
-    keep = (lo, size, p, ext)
+    coeff = getattr(mesh, "coeff", None)
+    if coeff is not None:
+        coeff = np.ascontiguousarray(coeff, dtype=np.float64)
+    keep = (lo, size, p, ext, coeff)
     d = DgMeshDesc(mesh.dim, mesh.n_elems, lo.ctypes.data_as(C.POINTER(C.c_int32)),
                    size.ctypes.data_as(C.POINTER(C.c_int32)), p.ctypes.data_as(C.POINTER(C.c_int32)),
-                   ext.ctypes.data_as(C.POINTER(C.c_int32)), float(mesh.lattice_h))
+                   ext.ctypes.data_as(C.POINTER(C.c_int32)), float(mesh.lattice_h),
+                   None if coeff is None else coeff.ctypes.data_as(C.POINTER(C.c_double)))
     return d, keep
 
 

@@ -66,7 +66,7 @@ __device__ __forceinline__ void trace3_tile(const ApplyArgs& A, const ApplyTile&
     double acc = 0.0;
 #pragma unroll
     for (int q = 0; q < NP; ++q) acc = fma(__ldg(dv + q), ld_x<RO>(xk + side_node3<NP>(s, i, j, q)), acc);
-    const double sg = (s & 1) ? A.ih[k] : -A.ih[k];
+    const double sg = (s & 1) ? A.aih[k] : -A.aih[k];   // a grad u . n
     double2 v;
     v.x = ld_x<RO>(xk + side_node3<NP>(s, i, j, (s & 1) ? P : 0));
     v.y = sg * acc;
@@ -334,7 +334,7 @@ __device__ __forceinline__ void apply3_tile(const ApplyArgs& A, const ApplyTile&
       v = fma(sK[ix * NP + q], cr[q], v);
       v = fma(sM[ix * NP + q], dr[q], v);
     }
-    double y = A.hk[k] * v;
+    double y = A.ahk[k] * v;
     const double* c2 = sc2 + e * 6 * N2;
     const double* r = sr + e * 6 * N2;
     double g = -__ldg(d0 + ix) * c2[0 * N2 + iz * NP + iy];
@@ -343,7 +343,7 @@ __device__ __forceinline__ void apply3_tile(const ApplyArgs& A, const ApplyTile&
     g = fma(__ldg(d1 + iy), c2[3 * N2 + iz * NP + ix], g);
     g = fma(-__ldg(d0 + iz), c2[4 * N2 + iy * NP + ix], g);
     g = fma(__ldg(d1 + iz), c2[5 * N2 + iy * NP + ix], g);
-    y = fma(g, A.ih[k], y);
+    y = fma(g, A.aih[k], y);
     if (ix == 0) y += r[0 * N2 + iz * NP + iy];
     if (ix == P) y += r[1 * N2 + iz * NP + iy];
     if (iy == 0) y += r[2 * N2 + iz * NP + ix];

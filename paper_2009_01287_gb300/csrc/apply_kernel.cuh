@@ -120,12 +120,14 @@ struct ApplyArgs {
   double* y;
   const int64_t* off;
   const double* ih;           // 1 / h per element
+  const double* aih;          // a / h per element (a: the diffusion coefficient)
+  const double* ahk;          // a h per element (cube meshes)
+  const double* ak;           // a per element
   const int64_t* toff;        // offset of the element's side traces in tr
   double* tr;                 // side traces: [side][node][u, dn]
   const int32_t* sf_ptr;
   const SubFaceRec* sf;
   const SubFaceRec3* sf3;     // cube meshes
-  const double* hk;           // h per element (cube meshes)
   const double* tab;          // basis + face tables
   const int32_t* order;       // degree-sorted element order
   const ApplyTile* tiles;
@@ -186,7 +188,7 @@ __device__ __forceinline__ void trace_tile(const ApplyArgs& A, const ApplyTile& 
     double acc = 0.0;
 #pragma unroll
     for (int q = 0; q < NP; ++q) acc = fma(__ldg(dv + q), ld_x<RO>(xk + side_node(s, i, q, NP)), acc);
-    const double sg = (s & 1) ? A.ih[k] : -A.ih[k];
+    const double sg = (s & 1) ? A.aih[k] : -A.aih[k];   // a grad u . n
     double2 v;
     v.x = ld_x<RO>(xk + side_node(s, i, (s & 1) ? P : 0, NP));
     v.y = sg * acc;
@@ -386,7 +388,7 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& 
 #pragma unroll
         for (int m = 0; m < NP; ++m) g = fma(__ldg(Mi + i * NP + m), sjo[t - i + m], g);
         const double ih = A.ih[k];
-        sgo[t] = g * __ldg(Mi) * ih * ih;
+        sgo[t] = A.ak[k] * (g * __ldg(Mi) * ih * ih);   // each side's lifting carries its a
       }
       for (int t = tid; t < nnb; t += blockDim.x) {
         const int e = t / (4 * kMaxN), s = (t / kMaxN) & 3, m = t % kMaxN;
@@ -400,7 +402,7 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& 
         double g = 0.0;
         for (int q = 0; q < np; ++q) g = fma(__ldg(Mi + m * np + q), sjn[(e * 4 + s) * kMaxN + q], g);
         const double ihn = A.ih[f.nb];
-        sgn[(e * 4 + s) * kMaxN + m] = g * __ldg(Mi) * ihn * ihn;
+        sgn[(e * 4 + s) * kMaxN + m] = A.ak[f.nb] * (g * __ldg(Mi) * ihn * ihn);
       }
       __syncthreads();
       // stage C: stabilisation residual
@@ -439,14 +441,15 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& 
     }
     const double* d0 = A.tab + bo.d0;
     const double* d1 = A.tab + bo.d1;
-    const double ih = A.ih[k];
+    const double aih = A.aih[k];
+    y *= A.ak[k];
     const double* c2 = sc2 + e * 4 * NP;
     const double* r = sr + e * 4 * NP;
     double g = -__ldg(d0 + ix) * c2[0 * NP + iy];
     g = fma(__ldg(d1 + ix), c2[1 * NP + iy], g);
     g = fma(-__ldg(d0 + iy), c2[2 * NP + ix], g);
     g = fma(__ldg(d1 + iy), c2[3 * NP + ix], g);
-    y = fma(g, ih, y);
+    y = fma(g, aih, y);
     if (ix == 0) y += r[0 * NP + iy];
     if (ix == P) y += r[1 * NP + iy];
     if (iy == 0) y += r[2 * NP + ix];

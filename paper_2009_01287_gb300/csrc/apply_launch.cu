@@ -159,12 +159,14 @@ ApplyArgs make_apply_args(const dg_mesh& M, const double* x, double* y, Reduce r
   A.y = y;
   A.off = M.d_off;
   A.ih = M.d_ih;
+  A.aih = M.d_aih;
+  A.ahk = M.d_ahk;
+  A.ak = M.d_ak;
   A.toff = M.d_toff;
   A.tr = M.d_tr;
   A.sf_ptr = M.d_sf_ptr;
   A.sf = M.d_sf;
   A.sf3 = M.d_sf3;
-  A.hk = M.d_h;
   A.tab = M.d_tables;
   A.order = M.d_order;
   A.tiles = M.d_tiles;

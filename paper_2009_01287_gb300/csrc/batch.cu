@@ -260,6 +260,7 @@ static void build_union_mesh(dg_batch* B, cudaStream_t s) {
     const int64_t e0 = um.n, d0 = um.off.back();
     const int32_t s0 = (int32_t)U.h_sf.size();
     um.p.insert(um.p.end(), m.p.begin(), m.p.end());
+    um.coef.insert(um.coef.end(), m.coef.begin(), m.coef.end());
     for (int64_t e = 0; e < m.n; ++e) um.off.push_back(d0 + m.off[e + 1]);
     for (int64_t j = 1; j <= 4 * m.n; ++j) um.sf_ptr.push_back(s0 + m.sf_ptr[j]);
     U.h_h.insert(U.h_h.end(), M.h_h.begin(), M.h_h.end());

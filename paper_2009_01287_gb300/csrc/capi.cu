@@ -48,16 +48,20 @@ void upload_mesh(dg_mesh* M, cudaStream_t s) {
   DevArena& a = M->arena;
   M->d_p = a.upload(m.p, s);
   M->d_off = a.upload(m.off, s);
-  M->d_h = a.upload(M->h_h, s);
   {
-    std::vector<double> ih(m.n);
+    std::vector<double> ih(m.n), aih(m.n), ahk(m.n);
     std::vector<int64_t> toff(m.n + 1, 0);
     for (int64_t k = 0; k < m.n; ++k) {
       ih[k] = 1.0 / M->h_h[k];
+      aih[k] = m.coef[k] / M->h_h[k];
+      ahk[k] = m.coef[k] * M->h_h[k];
       const int64_t np = m.p[k] + 1;
       toff[k + 1] = toff[k] + (m.dim == 3 ? 12 * np * np : 8 * np);
     }
     M->d_ih = a.upload(ih, s);
+    M->d_aih = a.upload(aih, s);
+    M->d_ahk = a.upload(ahk, s);
+    M->d_ak = a.upload(m.coef, s);
     M->d_toff = a.upload(toff, s);
     M->d_tr = a.alloc<double>(toff[m.n]);
   }

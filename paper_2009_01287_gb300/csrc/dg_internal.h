@@ -1,6 +1,7 @@
 // Internal data structures of the hp-DG library (host + device).
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <map>
 #include <stdexcept>
@@ -93,7 +94,7 @@ struct SubFaceRec3 {
 
 // Shared-memory budget (doubles) of one 3D operator tile; the host sizes the
 // tiles and their sub-face item chunks so that every one fits.
-constexpr int kApply3Budget = 13 * 1024;
+constexpr int kApply3Budget = 9 * 1024;
 constexpr int kApply3MinChunk = 12;   // sub-face items a tile keeps room for
 // doubles of shared memory one element of degree p needs in a 3D tile (volume
 // passes and the per-side residual and normal-derivative coefficients)
@@ -122,6 +123,17 @@ struct ApplyTile {
 };
 
 // ------------------------------------------------------------------ mesh (host topology)
+// a_kappa of every element from a mesh description (all 1 when coeff is NULL)
+inline void copy_coeff(const dg_mesh_desc* d, std::vector<double>& coef) {
+  coef.assign(d->n_elems, 1.0);
+  if (!d->coeff) return;
+  for (int64_t k = 0; k < d->n_elems; ++k) {
+    const double a = d->coeff[k];
+    if (!(a > 0.0) || !std::isfinite(a)) throw Error(DG_EINVAL, "coefficient must be positive and finite");
+    coef[k] = a;
+  }
+}
+
 struct HostMesh {
   int dim = 2;
   int64_t n = 0;
@@ -130,6 +142,7 @@ struct HostMesh {
   std::vector<int32_t> p;       // n
   int32_t extent[3] = {0, 0, 1};
   double lh = 1.0;
+  std::vector<double> coef;     // n coefficients a (1 when none given)
   std::vector<int64_t> off;     // n+1 DOF offsets
   std::vector<int32_t> cellmap; // lattice cell (x fastest) -> element
 

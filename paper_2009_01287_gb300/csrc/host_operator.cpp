@@ -14,7 +14,7 @@ void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double*
   const HostMesh& m = M.host;
   const int P = m.p[k], NP = P + 1, NN = NP * NP;
   const Basis1D& B = basis1d(P);
-  const double hk = M.h_h[k];
+  const double hk = M.h_h[k], ak = m.coef[k];
   const double* xk = x + m.off[k];
   auto sn = [](int s, int i, int q, int np) { return (s < 2) ? (i * np + q) : (q * np + i); };
   // volume: (K (x) M + M (x) K) x  with local index iy*NP + ix, two passes
@@ -34,7 +34,7 @@ void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double*
       for (int ix = 0; ix < NP; ++ix) {
         double v = 0.0;
         for (int qy = 0; qy < NP; ++qy) v += B.M[iy * NP + qy] * t1[qy * NP + ix] + B.K[iy * NP + qy] * t2[qy * NP + ix];
-        y[iy * NP + ix] = v;
+        y[iy * NP + ix] = ak * v;
       }
   }
   double dn[4 * kMaxN], r[4 * kMaxN] = {0.0}, c2[4 * kMaxN] = {0.0};
@@ -43,7 +43,7 @@ void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double*
       const double* dv = (s & 1) ? B.d1.data() : B.d0.data();
       double acc = 0.0;
       for (int q = 0; q < NP; ++q) acc += dv[q] * xk[sn(s, i, q, NP)];
-      dn[s * NP + i] = ((s & 1) ? 1.0 : -1.0) / hk * acc;
+      dn[s * NP + i] = ((s & 1) ? 1.0 : -1.0) * (ak / hk) * acc;   // a grad u . n
     }
   const double* T = M.h_tables.data();
   for (int s = 0; s < 4; ++s) {
@@ -58,7 +58,7 @@ void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double*
         const double* xn = x + m.off[f.nb];
         const int ke = (f.nb_side & 1) ? f.pn : 0;
         const double* dv = (f.nb_side & 1) ? Bn.d1.data() : Bn.d0.data();
-        const double sg = ((f.nb_side & 1) ? -1.0 : 1.0) / M.h_h[f.nb];
+        const double sg = ((f.nb_side & 1) ? -1.0 : 1.0) * (m.coef[f.nb] / M.h_h[f.nb]);
         for (int q = 0; q < np; ++q) {
           un[q] = xn[sn(f.nb_side, q, ke, np)];
           double acc = 0.0;
@@ -101,15 +101,15 @@ void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double*
         for (int i = 0; i < NP; ++i) {
           double g = 0.0;
           for (int q = 0; q < NP; ++q) g += B.Minv[i * NP + q] * jo[q];
-          go[i] = g * B.Minv[0] / (hk * hk);
+          go[i] = ak * (g * B.Minv[0] / (hk * hk));   // each side's lifting carries its a
         }
         if (np) {
           const Basis1D& Bn = basis1d(f.pn);
-          const double hn = M.h_h[f.nb];
+          const double hn = M.h_h[f.nb], an = m.coef[f.nb];
           for (int q = 0; q < np; ++q) {
             double g = 0.0;
             for (int t = 0; t < np; ++t) g += Bn.Minv[q * np + t] * jn[t];
-            gn[q] = g * Bn.Minv[0] / (hn * hn);
+            gn[q] = an * (g * Bn.Minv[0] / (hn * hn));
           }
         }
         const double coef = (f.nb < 0) ? 1.0 : 0.25;
@@ -125,10 +125,11 @@ void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double*
   for (int node = 0; node < NN; ++node) {
     const int ix = node % NP, iy = node / NP;
     double v = y[node];
-    v += -B.d0[ix] / hk * c2[0 * NP + iy];
-    v += B.d1[ix] / hk * c2[1 * NP + iy];
-    v += -B.d0[iy] / hk * c2[2 * NP + ix];
-    v += B.d1[iy] / hk * c2[3 * NP + ix];
+    const double aih = ak / hk;
+    v += -B.d0[ix] * aih * c2[0 * NP + iy];
+    v += B.d1[ix] * aih * c2[1 * NP + iy];
+    v += -B.d0[iy] * aih * c2[2 * NP + ix];
+    v += B.d1[iy] * aih * c2[3 * NP + ix];
     if (ix == 0) v += r[0 * NP + iy];
     if (ix == P) v += r[1 * NP + iy];
     if (iy == 0) v += r[2 * NP + ix];
@@ -145,15 +146,15 @@ void host_element_diag(const dg_mesh& M, int64_t k, double* d) {
   const HostMesh& m = M.host;
   const int P = m.p[k], NP = P + 1;
   const Basis1D& B = basis1d(P);
-  const double hk = M.h_h[k];
+  const double hk = M.h_h[k], ak = m.coef[k];
   const double* T = M.h_tables.data();
   const bool br2 = M.opts.form == DG_FORM_BR2;
   for (int iy = 0; iy < NP; ++iy)
     for (int ix = 0; ix < NP; ++ix)
-      d[iy * NP + ix] = B.K[ix * NP + ix] * B.M[iy * NP + iy] + B.M[ix * NP + ix] * B.K[iy * NP + iy];
+      d[iy * NP + ix] = ak * (B.K[ix * NP + ix] * B.M[iy * NP + iy] + B.M[ix * NP + ix] * B.K[iy * NP + iy]);
   double go[kMaxN], gn[kMaxN], jo[kMaxN], jn[kMaxN];
   for (int s = 0; s < 4; ++s) {
-    const double dv = ((s & 1) ? B.d1[P] : -B.d0[0]) / hk;
+    const double dv = ((s & 1) ? B.d1[P] : -B.d0[0]) * (ak / hk);   // a times the normal derivative
     for (int i = 0; i < NP; ++i) {
       const int node = (s < 2) ? (i * NP + ((s & 1) ? P : 0)) : (((s & 1) ? P : 0) * NP + i);
       double add = 0.0;
@@ -170,19 +171,19 @@ void host_element_diag(const dg_mesh& M, int64_t k, double* d) {
         for (int a = 0; a < NP; ++a) {
           double g = 0.0;
           for (int q = 0; q < NP; ++q) g += B.Minv[a * NP + q] * jo[q];
-          go[a] = g * B.Minv[0] / (hk * hk);
+          go[a] = ak * (g * B.Minv[0] / (hk * hk));
         }
         double st = 0.0;
         for (int a = 0; a < NP; ++a) st += T[f.tab_oo + i * NP + a] * go[a];
         if (interior) {
           const int np = f.pn + 1;
           const Basis1D& Bn = basis1d(f.pn);
-          const double hn = M.h_h[f.nb];
+          const double hn = M.h_h[f.nb], an = m.coef[f.nb];
           for (int q = 0; q < np; ++q) jn[q] = f.len * T[f.tab_on + i * np + q];
           for (int a = 0; a < np; ++a) {
             double g = 0.0;
             for (int q = 0; q < np; ++q) g += Bn.Minv[a * np + q] * jn[q];
-            gn[a] = g * Bn.Minv[0] / (hn * hn);
+            gn[a] = an * (g * Bn.Minv[0] / (hn * hn));
           }
           for (int a = 0; a < np; ++a) st += T[f.tab_on + i * np + a] * gn[a];
         }

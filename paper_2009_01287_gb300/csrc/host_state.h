@@ -117,8 +117,10 @@ struct dg_mesh {
   dg::DevArena arena;
   int32_t* d_p = nullptr;
   int64_t* d_off = nullptr;
-  double* d_h = nullptr;
   double* d_ih = nullptr;       // 1 / h
+  double* d_aih = nullptr;      // a / h (normal derivatives of traces and test functions)
+  double* d_ahk = nullptr;      // a h (volume term on cubes)
+  double* d_ak = nullptr;       // a
   int64_t* d_toff = nullptr;    // side-trace offsets (8 (p+1) doubles per element)
   double* d_tr = nullptr;       // side traces written by each apply
   int32_t* d_sf_ptr = nullptr;

@@ -170,6 +170,7 @@ static void validate_and_copy(const dg_mesh_desc* d, HostMesh& m) {
   DG_REQUIRE(m.extent[0] > 0 && m.extent[1] > 0, "extent must be positive");
   DG_REQUIRE((int64_t)m.extent[0] * m.extent[1] <= (1LL << 28), "lattice too large");
   m.lh = d->lattice_h;
+  copy_coeff(d, m.coef);
   m.lo.assign(d->lo, d->lo + 2 * m.n);
   m.size.assign(d->size, d->size + m.n);
   m.p.assign(d->p, d->p + m.n);
@@ -308,7 +309,7 @@ void build_mesh_host(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opt
         r.len = len * m.lh;
         r.tab_oo = ft.get(P, Lo, oo, P, Lo, oo);
         int pe = P;
-        double he = M->h_h[k];
+        double he = M->h_h[k], ae = m.coef[k];
         if (f.nb >= 0) {
           const int pn = m.p[f.nb];
           int na, nc, n0, n1;
@@ -319,13 +320,14 @@ void build_mesh_host(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opt
           r.tab_nn = ft.get(pn, Ln, on, pn, Ln, on);
           pe = std::max(P, pn);
           he = std::min(he, M->h_h[f.nb]);
+          ae = std::max(ae, m.coef[f.nb]);
         } else {
           r.pn = P;
           r.tab_on = r.tab_oo;
           r.tab_nn = r.tab_oo;
         }
         const double pp = (o.penalty_form == DG_PENALTY_P1SQ) ? (pe + 1.0) : (double)pe;
-        r.sigma = M->eta * pp * pp / he;
+        r.sigma = ae * (M->eta * pp * pp / he);   // the larger coefficient of the two sides
         M->h_sf[j] = r;
       }
     }

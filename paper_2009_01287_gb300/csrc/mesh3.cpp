@@ -47,6 +47,7 @@ void validate_and_copy3(const dg_mesh_desc* d, HostMesh& m) {
   }
   DG_REQUIRE((int64_t)m.extent[0] * m.extent[1] * m.extent[2] <= (1LL << 28), "lattice too large");
   m.lh = d->lattice_h;
+  copy_coeff(d, m.coef);
   m.lo.assign(d->lo, d->lo + 3 * m.n);
   m.size.assign(d->size, d->size + m.n);
   m.p.assign(d->p, d->p + m.n);
@@ -236,7 +237,7 @@ void build_mesh_host3(dg_mesh* M, const dg_mesh_desc* desc, const dg_options& o)
         r.tab_oo[0] = ft.get(P, Lo, oa, P, Lo, oa);
         r.tab_oo[1] = ft.get(P, Lo, ob, P, Lo, ob);
         int pe = P;
-        double he = M->h_h[k];
+        double he = M->h_h[k], ae = m.coef[k];
         if (f.nb >= 0) {
           const int pn = m.p[f.nb], nh = m.size[f.nb];
           const int nA = m.lo[3 * f.nb + ta], nB = m.lo[3 * f.nb + tb];
@@ -250,12 +251,13 @@ void build_mesh_host3(dg_mesh* M, const dg_mesh_desc* desc, const dg_options& o)
           r.tab_nn[1] = ft.get(pn, Ln, nbo, pn, Ln, nbo);
           pe = std::max(P, pn);
           he = std::min(he, M->h_h[f.nb]);
+          ae = std::max(ae, m.coef[f.nb]);
         } else {
           r.pn = P;
           for (int d = 0; d < 2; ++d) r.tab_on[d] = r.tab_nn[d] = r.tab_oo[d];
         }
         const double pp = (o.penalty_form == DG_PENALTY_P1SQ) ? (pe + 1.0) : (double)pe;
-        r.sigma = M->eta * pp * pp / he;
+        r.sigma = ae * (M->eta * pp * pp / he);   // the larger coefficient of the two sides
         M->h_sf3[j] = r;
       }
     }
@@ -307,7 +309,8 @@ void build_mesh_host3(dg_mesh* M, const dg_mesh_desc* desc, const dg_options& o)
         const bool in = r.nb >= 0;
         const double coef = in ? 0.25 : 1.0;
         const double hk = M->h_h[k];
-        r.cz = M->eta * coef * r.area * r.area * basis1d(P).Minv[0] / (hk * hk * hk);
+        // each side's lifting energy carries that side's coefficient
+        r.cz = m.coef[k] * (M->eta * coef * r.area * r.area * basis1d(P).Minv[0] / (hk * hk * hk));
         for (int d = 0; d < 2; ++d) {
           r.tab_z[d] = product(0, P, P, r.tab_oo[d], r.tab_oo[d], r.tab_oo[d]);
           if (in) {
@@ -320,7 +323,7 @@ void build_mesh_host3(dg_mesh* M, const dg_mesh_desc* desc, const dg_options& o)
         }
         if (in) {
           const double hn = M->h_h[r.nb];
-          r.cx = M->eta * coef * r.area * r.area * basis1d(r.pn).Minv[0] / (hn * hn * hn);
+          r.cx = m.coef[r.nb] * (M->eta * coef * r.area * r.area * basis1d(r.pn).Minv[0] / (hn * hn * hn));
         }
       }
   const int base = (int)M->h_tables.size();
@@ -415,7 +418,7 @@ void host_element_residual3(const dg_mesh& M, int64_t k, const double* x, double
       for (int ix = 0; ix < NP; ++ix) {
         double v = 0.0;
         for (int q = 0; q < NP; ++q) v += B.K[ix * NP + q] * C[r + q] + B.M[ix * NP + q] * D[r + q];
-        y[r + ix] = hk * v;
+        y[r + ix] = (m.coef[k] * hk) * v;
       }
   }
   // traces (value, outward normal derivative) of an element side
@@ -424,7 +427,7 @@ void host_element_residual3(const dg_mesh& M, int64_t k, const double* x, double
     const Basis1D& Be = basis1d(pe);
     const double* xe = x + m.off[e];
     const double* dv = (s & 1) ? Be.d1.data() : Be.d0.data();
-    const double sg = ((s & 1) ? 1.0 : -1.0) / M.h_h[e];
+    const double sg = ((s & 1) ? 1.0 : -1.0) * (m.coef[e] / M.h_h[e]);   // a grad u . n
     u.assign(ne * ne, 0.0);
     dn.assign(ne * ne, 0.0);
     for (int j = 0; j < ne; ++j)
@@ -511,7 +514,9 @@ void host_element_residual3(const dg_mesh& M, int64_t k, const double* x, double
           st2.assign(N2, 0.0);
         }
         const double coef = interior ? 0.25 : 1.0;
-        for (int q = 0; q < N2; ++q) r[s * N2 + q] += M.eta * coef * ar * (st1[q] + st2[q]);
+        const double an = interior ? m.coef[f.nb] : 0.0;
+        for (int q = 0; q < N2; ++q)
+          r[s * N2 + q] += M.eta * coef * ar * (m.coef[k] * st1[q] + an * st2[q]);
       }
     }
   }
@@ -523,7 +528,7 @@ void host_element_residual3(const dg_mesh& M, int64_t k, const double* x, double
       side_axes3(s, ax, ta, tb);
       const int q = idx[ax], i = idx[ta], j = idx[tb];
       const double dv = (s & 1) ? B.d1[q] : -B.d0[q];
-      v += dv / hk * c2[s * N2 + j * NP + i];
+      v += dv * (m.coef[k] / hk) * c2[s * N2 + j * NP + i];
       if (q == ((s & 1) ? P : 0)) v += r[s * N2 + j * NP + i];
     }
     y[node] = v;

@@ -457,7 +457,7 @@ void host_element_diag3(const dg_mesh& M, int64_t k, double* d) {
   const HostMesh& m = M.host;
   const int P = m.p[k], NP = P + 1, N2 = NP * NP;
   const Basis1D& B = basis1d(P);
-  const double hk = M.h_h[k];
+  const double hk = M.h_h[k], ak = m.coef[k];
   const double* T = M.h_tables.data();
   const bool br2 = M.opts.form == DG_FORM_BR2;
   for (int iz = 0; iz < NP; ++iz)
@@ -465,7 +465,7 @@ void host_element_diag3(const dg_mesh& M, int64_t k, double* d) {
       for (int ix = 0; ix < NP; ++ix) {
         const double kx = B.K[ix * NP + ix], ky = B.K[iy * NP + iy], kz = B.K[iz * NP + iz];
         const double mx = B.M[ix * NP + ix], my = B.M[iy * NP + iy], mz = B.M[iz * NP + iz];
-        d[(iz * NP + iy) * NP + ix] = hk * (kx * my * mz + mx * ky * mz + mx * my * kz);
+        d[(iz * NP + iy) * NP + ix] = (ak * hk) * (kx * my * mz + mx * ky * mz + mx * my * kz);
       }
   // quadratic form of a 1D table row against the inverse of a 1D mass matrix
   auto qform = [&](const double* row, int stride, int n, const std::vector<double>& Mi) {
@@ -478,7 +478,7 @@ void host_element_diag3(const dg_mesh& M, int64_t k, double* d) {
     int ax, ta, tb;
     side_axes3(s, ax, ta, tb);
     const int q = (s & 1) ? P : 0;
-    const double dv = ((s & 1) ? B.d1[P] : -B.d0[0]) / hk;
+    const double dv = ((s & 1) ? B.d1[P] : -B.d0[0]) * (ak / hk);   // a times the normal derivative
     for (int j = 0; j < NP; ++j)
       for (int i = 0; i < NP; ++i) {
         int idx[3];
@@ -495,14 +495,14 @@ void host_element_diag3(const dg_mesh& M, int64_t k, double* d) {
             continue;
           }
           add -= (interior ? 1.0 : 2.0) * f.area * moo * dv;
-          const double so = B.Minv[0] / (hk * hk * hk);
+          const double so = ak * (B.Minv[0] / (hk * hk * hk));   // each side's lifting carries its a
           double st = so * f.area * qform(T + f.tab_oo[0] + i, NP, NP, B.Minv) *
                       qform(T + f.tab_oo[1] + j, NP, NP, B.Minv);
           if (interior) {
             const int nn = f.pn + 1;
             const Basis1D& Bn = basis1d(f.pn);
             const double hn = M.h_h[f.nb];
-            const double sn = Bn.Minv[0] / (hn * hn * hn);
+            const double sn = m.coef[f.nb] * (Bn.Minv[0] / (hn * hn * hn));
             st += sn * f.area * qform(T + f.tab_on[0] + i * nn, 1, nn, Bn.Minv) *
                   qform(T + f.tab_on[1] + j * nn, 1, nn, Bn.Minv);
           }
@@ -672,7 +672,7 @@ HostPrecond build_host_precond3(const dg_mesh& M, const dg_options& o) {
                   const int ii = i + di - 1, jj = j + dj - 1, zz = kz + dz - 1;
                   if (ii < 0 || jj < 0 || zz < 0 || ii > P || jj > P || zz > P) continue;
                   At.idx.push_back((int32_t)(m.off[k] + (zz * NP + jj) * NP + ii));
-                  At.val.push_back(row[dz][dj][di]);
+                  At.val.push_back(m.coef[k] * row[dz][dj][di]);   // weighted by a_k
                 }
             At.ptr[m.off[k] + (kz * NP + j) * NP + i + 1] = (int64_t)At.idx.size();
           }

@@ -383,7 +383,7 @@ HostPrecond build_host_precond(const dg_mesh& M, const dg_options& o) {
               const int ii = i + di - 1, jj = j + dj - 1;
               if (ii < 0 || jj < 0 || ii > P || jj > P) continue;
               At.idx.push_back((int32_t)(m.off[k] + jj * NP + ii));
-              At.val.push_back(row[dj][di]);
+              At.val.push_back(m.coef[k] * row[dj][di]);   // weighted by a_k
             }
           At.ptr[m.off[k] + j * NP + i + 1] = (int64_t)At.idx.size();
         }

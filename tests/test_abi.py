@@ -63,14 +63,23 @@ BAD = {
     "3d-degree-9": lambda: _desc(3, [(0, 0, 0)], [1], [9], (1, 1, 1)),
     "3d-outside": lambda: _desc(3, [(0, 0, 0), (1, 0, 0)], [1, 1], [1, 1], (1, 1, 1)),
     "2d-gap": lambda: _desc(2, [(0, 0)], [1], [2], (2, 1)),
+    "2d-coeff-zero": lambda: _with_coeff(_desc(2, [(0, 0), (1, 0)], [1, 1], [1, 2], (2, 1)), [1.0, 0.0]),
+    "2d-coeff-nan": lambda: _with_coeff(_desc(2, [(0, 0), (1, 0)], [1, 1], [1, 2], (2, 1)), [float("nan"), 1.0]),
+    "3d-coeff-negative": lambda: _with_coeff(_desc(3, [(0, 0, 0)], [1], [2], (1, 1, 1)), [-20.0]),
 }
+
+
+def _with_coeff(mesh, a):
+    from paper_2009_01287_gb300 import inputs
+    return inputs.with_coeff(mesh, a)
 
 
 @pytest.mark.parametrize("name", list(BAD))
 def test_invalid_meshes_rejected(built_lib, name):
     """Invalid 2D and 3D descriptions give DG_EINVAL with a message, before
     any device work (overlap, gap, misaligned or non-dyadic boxes, degrees
-    outside 1..8, boxes outside the domain)."""
+    outside 1..8, boxes outside the domain, a coefficient that is not positive
+    and finite)."""
     try:
         built_lib.dg_mesh_create(BAD[name]())
         raise AssertionError("accepted an invalid mesh")

@@ -13,6 +13,10 @@ from paper_2009_01287_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
+def _coef(mesh, base):
+    return inputs.with_coeff(mesh, inputs.base_parity_coeff(mesh, base))
+
+
 MESHES = {
     "cfg0": (lambda: inputs.config0()[0], 10.0, "p1sq"),
     "hp-a": (lambda: inputs.small_hp_mesh(1, base=4, depth=3, prob=0.4, pmax=5), None, "paper"),
@@ -20,6 +24,9 @@ MESHES = {
     "hp-high": (lambda: inputs.small_hp_mesh(5, base=2, depth=2, prob=0.5, pmin=7, pmax=8), None, "paper"),
     "single": (lambda: inputs.uniform_mesh(2, 1, 8), None, "paper"),
     "ragged": (lambda: inputs.random_refined_mesh(2, 5, 3, 0.35, 1, 4, seed=9, base_y=3), None, "paper"),
+    # piecewise-constant coefficient a in {1, 20} by base-cell parity (Section 4.3)
+    "coef-a": (lambda: _coef(inputs.small_hp_mesh(6, base=4, depth=3, prob=0.4, pmax=6), 4), None, "paper"),
+    "coef-b": (lambda: _coef(inputs.small_hp_mesh(7, base=3, depth=2, prob=0.5, pmin=2, pmax=8), 3), None, "paper"),
 }
 
 
@@ -65,7 +72,7 @@ def test_apply_parity(built_lib, torch_mod, name, form):
 
 
 @pytest.mark.parametrize("lor", ["exact", "amg"])
-@pytest.mark.parametrize("name", ["cfg0", "hp-a", "hp-b", "ragged"])
+@pytest.mark.parametrize("name", ["cfg0", "hp-a", "hp-b", "ragged", "coef-a"])
 def test_precond_parity_fp64(built_lib, torch_mod, name, lor):
     mk, eta, pform = MESHES[name]
     mesh = mk()
@@ -119,7 +126,8 @@ def test_precond_mixed_close(built_lib, torch_mod):
 
 
 @pytest.mark.parametrize("name,lor,form,tol", [("cfg0", "exact", "sipg", 1e-10), ("hp-a", "amg", "sipg", 1e-8),
-                                               ("hp-b", "amg", "br2", 1e-8), ("ragged", "amg", "sipg", 1e-8)])
+                                               ("hp-b", "amg", "br2", 1e-8), ("ragged", "amg", "sipg", 1e-8),
+                                               ("coef-a", "amg", "sipg", 1e-8), ("coef-b", "amg", "br2", 1e-8)])
 def test_pcg_iterations_match_oracle(built_lib, torch_mod, name, lor, form, tol):
     mk, eta, pform = MESHES[name]
     mesh = mk()

@@ -12,12 +12,18 @@ from paper_2009_01287_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
+def _coef(mesh, base):
+    return inputs.with_coeff(mesh, inputs.base_parity_coeff(mesh, base))
+
+
 MESHES3 = {
     "hp0": lambda: inputs.small_hp_mesh(0, base=2, depth=2, prob=0.5, pmin=1, pmax=4, dim=3),
     "hp1": lambda: inputs.small_hp_mesh(1, base=2, depth=2, prob=0.5, pmin=1, pmax=5, dim=3),
     "p8": lambda: inputs.small_hp_mesh(1, base=2, depth=1, prob=0.2, pmin=6, pmax=8, dim=3),
     "single": lambda: inputs.uniform_mesh(3, 1, 4),
     "ragged": lambda: inputs.random_refined_mesh(3, 3, 2, 0.3, 1, 3, seed=4),
+    # piecewise-constant coefficient a in {1, 20} by base-cell parity (Section 4.3)
+    "coef": lambda: _coef(inputs.small_hp_mesh(2, base=2, depth=2, prob=0.5, pmin=1, pmax=4, dim=3), 2),
 }
 
 
@@ -67,7 +73,7 @@ def test_rhs3_parity(built_lib, torch_mod):
     assert rel(bd.cpu().numpy(), rhs.load_vector(space, r.amps, r.waves)) <= 1e-12
 
 
-PC3 = ["hp0", "hp1", "ragged"]
+PC3 = ["hp0", "hp1", "ragged", "coef"]
 
 
 def _opts3(B, form, **kw):
@@ -75,7 +81,7 @@ def _opts3(B, form, **kw):
 
 
 @pytest.mark.parametrize("name,lor", [("hp0", "exact"), ("ragged", "exact"), ("hp0", "amg"),
-                                      ("hp1", "amg"), ("ragged", "amg")])
+                                      ("hp1", "amg"), ("ragged", "amg"), ("coef", "amg")])
 def test_precond3_parity_fp64(built_lib, torch_mod, name, lor):
     mesh = MESHES3[name]()
     prob = solver.build_problem(mesh)

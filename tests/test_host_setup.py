@@ -7,12 +7,21 @@ import pytest
 from oracle import solver
 from paper_2009_01287_gb300 import inputs
 
+def _coef(mesh, base):
+    return inputs.with_coeff(mesh, inputs.base_parity_coeff(mesh, base))
+
+
 CASES = [
     ("cfg0", lambda: inputs.config0()[0], "sipg", 10.0, "p1sq"),
     ("hp1", lambda: inputs.small_hp_mesh(1, base=4, depth=3, prob=0.4, pmax=5), "sipg", None, "paper"),
     ("hp2-br2", lambda: inputs.small_hp_mesh(2, base=4, depth=3, prob=0.4, pmax=6), "br2", None, "paper"),
     ("hp3-p8", lambda: inputs.small_hp_mesh(3, base=3, depth=2, prob=0.5, pmin=6, pmax=8), "sipg", None, "paper"),
     ("single", lambda: inputs.uniform_mesh(2, 1, 3), "sipg", None, "paper"),
+    # piecewise-constant coefficient a in {1, 20} by base-cell parity (Section 4.3)
+    ("coef-sipg", lambda: _coef(inputs.small_hp_mesh(4, base=4, depth=3, prob=0.4, pmax=5), 4), "sipg", None,
+     "paper"),
+    ("coef-br2", lambda: _coef(inputs.small_hp_mesh(5, base=4, depth=2, prob=0.4, pmax=6), 4), "br2", None,
+     "paper"),
 ]
 
 

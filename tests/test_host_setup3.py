@@ -7,11 +7,16 @@ import pytest
 from oracle import dg, solver
 from paper_2009_01287_gb300 import inputs
 
+def _coef(mesh, base):
+    return inputs.with_coeff(mesh, inputs.base_parity_coeff(mesh, base))
+
+
 CASES = [
     ("hp0", lambda: inputs.small_hp_mesh(0, base=2, depth=2, prob=0.5, pmin=1, pmax=4, dim=3)),
     ("hp1", lambda: inputs.small_hp_mesh(1, base=2, depth=2, prob=0.5, pmin=1, pmax=4, dim=3)),
     ("hp1-p8", lambda: inputs.small_hp_mesh(1, base=2, depth=1, prob=0.2, pmin=6, pmax=8, dim=3)),
     ("single", lambda: inputs.uniform_mesh(3, 1, 3)),
+    ("coef", lambda: _coef(inputs.small_hp_mesh(2, base=2, depth=2, prob=0.5, pmin=1, pmax=4, dim=3), 2)),
 ]
 
 
@@ -35,6 +40,10 @@ PC_CASES = [
     ("hp1-br2", lambda: inputs.small_hp_mesh(1, base=2, depth=2, prob=0.3, pmin=1, pmax=4, dim=3), "br2"),
     ("hp3-sipg", lambda: inputs.small_hp_mesh(3, base=2, depth=2, prob=0.4, pmin=1, pmax=2, dim=3), "sipg"),
     ("uniform", lambda: inputs.uniform_mesh(3, 2, 3), "sipg"),
+    ("coef-sipg", lambda: _coef(inputs.small_hp_mesh(4, base=2, depth=2, prob=0.3, pmin=1, pmax=3, dim=3), 2),
+     "sipg"),
+    ("coef-br2", lambda: _coef(inputs.small_hp_mesh(5, base=2, depth=2, prob=0.3, pmin=1, pmax=3, dim=3), 2),
+     "br2"),
 ]
 
 
