@@ -1,5 +1,6 @@
 """Batched solver: every instance of the batch follows the iteration it would
-follow alone (same iteration count, same solution within round-off)."""
+follow alone (same iteration count, same solution within round-off), including
+an instance with a piecewise-constant coefficient."""
 import numpy as np
 import pytest
 
@@ -9,10 +10,13 @@ pytestmark = pytest.mark.gpu
 
 
 def _problems():
+    coef = inputs.small_hp_mesh(8, base=4, depth=2, prob=0.4, pmax=6)
+    coef = inputs.with_coeff(coef, inputs.base_parity_coeff(coef, 4))   # a in {1, 20}
     return [inputs.small_hp_mesh(1, base=4, depth=3, prob=0.4, pmax=5),
             inputs.random_refined_mesh(2, 5, 3, 0.35, 1, 4, seed=9, base_y=3),
             inputs.uniform_mesh(2, 3, 2),
-            inputs.small_hp_mesh(7, base=6, depth=2, prob=0.3, pmin=2, pmax=7)]
+            inputs.small_hp_mesh(7, base=6, depth=2, prob=0.3, pmin=2, pmax=7),
+            coef]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
