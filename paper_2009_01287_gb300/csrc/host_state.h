@@ -151,11 +151,14 @@ struct dg_precond {
   dg::DevCsr P, PT;          // P: n_dofs x n_c (rows = DG nodes), PT = P^T
   void* dinv = nullptr;      // n_dofs, 1/A_jj on V_J and 0 elsewhere
   int32_t* e_pos = nullptr;     // n_dofs, slot of the node's result in zE, or -1 outside the V_e
-  // block-solve work units, one per 32-row panel of a V_e block, largest blocks
-  // first: {slot of the block's first node in zE, d, first row, 0} and the offset
-  // of the panel's first row in blk_inv
+  // block-solve work units, largest blocks first: one per 32-row panel of a
+  // large V_e block, {slot of the block's first node in zE, d, first row, 0},
+  // with the offset of the panel's first row in blk_inv
   int32_t* blk_unit = nullptr;   // 4 per unit
   int64_t* blk_ubase = nullptr;
+  // small blocks, packed several to a unit {first block, count, 0, W}: per block
+  // {slot of its first node, d, inverse offset low / high 32 bits}
+  int32_t* blk_rec = nullptr;
   int32_t* blk_dofs = nullptr;   // DG node of every slot, block by block
   void* blk_inv = nullptr;   // dense inverses, column-major
   void* lor_inv = nullptr;   // exact LOR solve: dense inverse n_c x n_c

@@ -150,25 +150,56 @@ __global__ void dense_mv_kernel(const T* __restrict__ Ainv, const T* __restrict_
   }
 }
 
+// Small V_e blocks packed into one warp: segment g of W lanes (W a power of
+// two >= the block sizes) takes the g-th block of the unit, lane rr of the
+// segment forms row rr.  Same column order and four accumulators (by column
+// mod 4) as the panel path, so a block's result does not depend on the path.
+template <typename T, int W>
+__device__ __forceinline__ void block_solve_packed(const int4 h, const int4* __restrict__ brec,
+                                                   const int32_t* __restrict__ dofs,
+                                                   const T* __restrict__ inv, const double* __restrict__ r,
+                                                   T* __restrict__ zE, int lane) {
+  const int seg = lane / W, rr = lane % W;
+  const bool has = seg < h.y;   // h = {first block (sorted order), block count, 0, W}
+  const int4 br = has ? __ldg(brec + h.x + seg) : make_int4(0, 0, 0, 0);   // {slot, d, inverse offset}
+  const int d = br.y;
+  const bool act = rr < d;
+  const T* At = inv + ((int64_t)(unsigned)br.z | ((int64_t)br.w << 32)) + rr;
+  const T rv = act ? (T)__ldg(r + __ldg(dofs + br.x + rr)) : (T)0;
+  T v[W];
+#pragma unroll
+  for (int c = 0; c < W; ++c) v[c] = (act && c < d) ? __ldg(At + (int64_t)c * d) : (T)0;
+  T a[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int c = 0; c < W; ++c) a[c & 3] = fma(v[c], __shfl_sync(0xffffffffu, rv, c, W), a[c & 3]);
+  if (act) zE[br.x + rr] = (a[0] + a[1]) + (a[2] + a[3]);
+}
+
 // V_e block solves (Section 3.3, T_E = sum_e P_e): z_e = A_e^-1 r_e.  A work
-// unit is a panel of 32 consecutive rows of one block and is taken by one warp:
-// lane l forms row row0 + l over all d columns.  The inverse is stored
-// column-major, so every step reads 32 consecutive entries of one column; the
-// block's residual entries are gathered 32 at a time, one per lane, and reach
-// the other lanes by shuffles.  No shared memory and no block barrier; a warp
-// issues a whole chunk of column loads before its first FMA.  Units are sorted
-// by block size (largest first) and dealt round-robin over the grid's warps.
+// unit is taken by one warp: either a panel of 32 consecutive rows of one
+// block (lane l forms row row0 + l over all d columns), or up to 32 / W small
+// blocks of at most W rows side by side (block_solve_packed).  The inverses
+// are stored column-major, so every step reads consecutive entries of one
+// column; the block's residual entries are gathered 32 at a time, one per
+// lane, and reach the other lanes by shuffles.  No shared memory and no block
+// barrier; a warp issues a whole chunk of column loads before its first FMA.
+// Units are sorted by work (largest blocks first) and dealt round-robin over
+// the grid's warps.
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3)
 block_solve_kernel(const int4* __restrict__ unit, const int64_t* __restrict__ ubase,
-                   const int32_t* __restrict__ dofs, const T* __restrict__ inv,
-                   const double* __restrict__ r, T* __restrict__ zE, int nunits) {
+                   const int4* __restrict__ brec, const int32_t* __restrict__ dofs,
+                   const T* __restrict__ inv, const double* __restrict__ r, T* __restrict__ zE,
+                   int nunits) {
   pdl_entry();
   constexpr int H = 16;   // column loads per lane in one batch
   const int lane = threadIdx.x & 31;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nunits; u += nw) {
-    const int4 h = __ldg(unit + u);   // {slot of the block's first node, d, row0, -}
+    const int4 h = __ldg(unit + u);   // panel: {slot of the block's first node, d, row0, 0}
+    if (h.w == 4) { block_solve_packed<T, 4>(h, brec, dofs, inv, r, zE, lane); continue; }
+    if (h.w == 8) { block_solve_packed<T, 8>(h, brec, dofs, inv, r, zE, lane); continue; }
+    if (h.w == 16) { block_solve_packed<T, 16>(h, brec, dofs, inv, r, zE, lane); continue; }
     const int d = h.y, row = h.z + lane;
     const bool act = row < d;
     const T* At = inv + __ldg(ubase + u) + lane;   // column 0 of this lane's row
@@ -361,7 +392,7 @@ static void precond_impl(const dg_precond& pc, const double* r, double* z, Reduc
     const int64_t gc = (pc.n_units + 7) / 8, gmax = (sizeof(T) == 8 ? 2 : 3) * 152;
     const int g = (int)(gc < gmax ? gc : gmax);
     launch_k(block_solve_kernel<T>, g, 256, 0, pc.side, (const int4*)pc.blk_unit, pc.blk_ubase,
-        pc.blk_dofs, (const T*)pc.blk_inv, r, (T*)pc.zE, (int)pc.n_units);
+        (const int4*)pc.blk_rec, pc.blk_dofs, (const T*)pc.blk_inv, r, (T*)pc.zE, (int)pc.n_units);
     DG_CUDA(cudaGetLastError());
     DG_CUDA(cudaEventRecord(pc.ev_join, pc.side));
   }

@@ -143,23 +143,42 @@ void upload_union_precond(dg_precond* pc, const std::vector<InstSrc>& inst, cuda
   upload_csr_t<T>(a, csr_transpose(P), pc->PT, s);
   pc->dinv = a.upload(std::vector<T>(dinv.begin(), dinv.end()), s);
   pc->e_pos = a.upload(eb, s);
-  // block-solve units: 32-row panels, largest blocks first over all instances
+  // block-solve units, largest blocks first over all instances: 32-row panels
+  // of blocks of more than 16 nodes; blocks of at most W = 4, 8, 16 nodes
+  // packed 32 / W to a unit
   DG_REQUIRE(pc->max_block <= 32 * 256, "a V_e block has more than 8192 nodes");
-  std::vector<int64_t> uorder;
-  for (int64_t b = 0; b < nb; ++b)
-    for (int32_t r0 = 0; r0 < dims[b]; r0 += 32) uorder.push_back(b << 8 | (r0 >> 5));
-  std::stable_sort(uorder.begin(), uorder.end(),
-                   [&](int64_t x, int64_t y) { return dims[x >> 8] > dims[y >> 8]; });
-  std::vector<int32_t> unit;
+  std::vector<int64_t> bsort(nb);
+  for (int64_t b = 0; b < nb; ++b) bsort[b] = b;
+  std::stable_sort(bsort.begin(), bsort.end(), [&](int64_t x, int64_t y) { return dims[x] > dims[y]; });
+  std::vector<int32_t> unit, brec;
   std::vector<int64_t> ubase;
-  for (int64_t k : uorder) {
-    const int64_t b = k >> 8;
-    const int32_t r0 = (int32_t)(k & 255) * 32;
-    unit.insert(unit.end(), {dofs_off[b], dims[b], r0, 0});
-    ubase.push_back(inv_off[b] + r0);
+  for (int64_t k = 0; k < nb;) {
+    const int64_t b = bsort[k];
+    const int32_t d = dims[b];
+    if (d > 16) {
+      for (int32_t r0 = 0; r0 < d; r0 += 32) {
+        unit.insert(unit.end(), {dofs_off[b], d, r0, 0});
+        ubase.push_back(inv_off[b] + r0);
+      }
+      ++k;
+      continue;
+    }
+    const int32_t W = d > 8 ? 16 : (d > 4 ? 8 : 4);
+    int32_t cnt = 0;
+    const int64_t first = (int64_t)brec.size() / 4;
+    while (k < nb && cnt < 32 / W && dims[bsort[k]] <= W && (W == 4 || dims[bsort[k]] > W / 2)) {
+      const int64_t bb = bsort[k];
+      brec.insert(brec.end(), {dofs_off[bb], dims[bb], (int32_t)(uint32_t)(inv_off[bb] & 0xffffffffu),
+                               (int32_t)(inv_off[bb] >> 32)});
+      ++cnt;
+      ++k;
+    }
+    unit.insert(unit.end(), {(int32_t)first, cnt, 0, W});
+    ubase.push_back(0);
   }
   pc->blk_unit = a.upload(unit, s);
   pc->blk_ubase = a.upload(ubase, s);
+  pc->blk_rec = a.upload(brec, s);
   pc->blk_dofs = a.upload(dofs, s);
   pc->blk_inv = a.upload(inv, s);
   pc->zE = a.alloc<T>(dofs.size());
