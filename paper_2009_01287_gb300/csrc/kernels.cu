@@ -284,7 +284,7 @@ static int grid_for(int64_t n, int threads = kVecThreads) {
 }
 
 int precond_final_blocks(const dg_precond& pc) {
-  int64_t b = (pc.n_dofs * pc.P.group_all + kVecThreads - 1) / kVecThreads;
+  int64_t b = (pc.n_dofs + kVecThreads - 1) / kVecThreads;   // one lane per row
   if (b > kVecBlocks) b = kVecBlocks;
   return (int)(b < 1 ? 1 : b);
 }
@@ -415,9 +415,9 @@ static void precond_impl(const dg_precond& pc, const double* r, double* z, Reduc
   launch_k(precond_final_kernel<T, G>, nb, kVecThreads, 0, s,                                      \
       pc.P.ptr, pc.P.idx, (const T*)pc.P.val, (const T*)ec, (const T*)pc.dinv, pc.e_pos,     \
       (const T*)pc.zE, r, z, pc.n_dofs, red)
-  if (pc.P.group_all <= 1) DG_FINAL(1);
-  else if (pc.P.group_all == 2) DG_FINAL(2);
-  else DG_FINAL(4);
+  // one lane per DG row: measured faster than 2 or 4 lanes (P has about five
+  // entries per row; fewer rounds of dependent loads per thread count more)
+  DG_FINAL(1);
 #undef DG_FINAL
   DG_CUDA(cudaGetLastError());
 }
