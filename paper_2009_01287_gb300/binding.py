@@ -359,8 +359,48 @@ def inspect_lib():
         L.dginspect_level_nnz.restype = C.c_int64
         L.dginspect_level_A.argtypes = [vp, C.c_int, vp, vp, vp]
         L.dginspect_apply.argtypes = [vp, vp, vp]
+        L.dginspect_block_units.argtypes = [C.c_int64, vp, vp, vp, vp, vp, vp, C.c_int64]
+        L.dginspect_block_units.restype = C.c_int64
+        L.dginspect_csr_tiers.argtypes = [C.c_int64, vp, vp, vp, vp, vp]
+        L.dginspect_csr_tiers.restype = C.c_int
         _inspect = L
     return _inspect
+
+
+def plan_block_units(dims, slot, inv_off):
+    """The library's block-solve work units for blocks of the given sizes
+    (host planning only): (unit int32 (n, 4), ubase int64 (n,), brec int32 (m, 4))."""
+    L = inspect_lib()
+    dims = np.ascontiguousarray(dims, dtype=np.int32)
+    slot = np.ascontiguousarray(slot, dtype=np.int32)
+    inv_off = np.ascontiguousarray(inv_off, dtype=np.int64)
+    nb = len(dims)
+    cap = int(np.sum((dims.astype(np.int64) + 31) // 32)) + nb + 1
+    unit = np.zeros((cap, 4), dtype=np.int32)
+    ubase = np.zeros(cap, dtype=np.int64)
+    brec = np.zeros((max(nb, 1), 4), dtype=np.int32)
+    n = L.dginspect_block_units(nb, dims.ctypes.data, slot.ctypes.data, inv_off.ctypes.data,
+                                unit.ctypes.data, ubase.ctypes.data, brec.ctypes.data, cap)
+    if n < 0:
+        raise DGError(DG_EINVAL, L.dginspect_last_error().decode())
+    m = int(np.sum(unit[:n, 1][unit[:n, 3] != 0]))
+    return unit[:n].copy(), ubase[:n].copy(), brec[:m].copy()
+
+
+def plan_csr_tiers(ptr):
+    """The library's row tiers of the CSR row kernel for row pointers `ptr`
+    (host planning only): (group, long_min, cta rows, warp rows)."""
+    L = inspect_lib()
+    ptr = np.ascontiguousarray(ptr, dtype=np.int64)
+    rows = len(ptr) - 1
+    out2 = np.zeros(2, dtype=np.int32)
+    counts = np.zeros(2, dtype=np.int64)
+    cta = np.zeros(max(rows, 1), dtype=np.int32)
+    warp = np.zeros(max(rows, 1), dtype=np.int32)
+    if L.dginspect_csr_tiers(rows, ptr.ctypes.data, out2.ctypes.data, counts.ctypes.data, cta.ctypes.data,
+                             warp.ctypes.data) != 0:
+        raise DGError(DG_EINVAL, L.dginspect_last_error().decode())
+    return int(out2[0]), int(out2[1]), cta[:counts[0]].copy(), warp[:counts[1]].copy()
 
 
 class HostSetup:

@@ -9,6 +9,7 @@
 #include "dg_internal.h"
 #include "host_state.h"
 #include "precond_setup.h"
+#include "work_units.h"
 
 using namespace dg;
 
@@ -29,6 +30,51 @@ void set_last_error(const std::string& msg) { g_err = msg; }
 extern "C" {
 
 const char* dginspect_last_error(void) { return g_err.c_str(); }
+
+// Work units of the block solves for blocks of the given sizes, slots and
+// inverse offsets (see plan_block_units).  unit: 4 * cap ints, ubase: cap,
+// brec: 4 * nb ints.  Returns the number of units, -1 on error or when cap is
+// too small.
+int64_t dginspect_block_units(int64_t nb, const int32_t* dims, const int32_t* slot, const int64_t* inv_off,
+                              int32_t* unit, int64_t* ubase, int32_t* brec, int64_t cap) {
+  try {
+    std::vector<int32_t> d(dims, dims + nb), sl(slot, slot + nb), u, br;
+    std::vector<int64_t> io(inv_off, inv_off + nb), ub;
+    plan_block_units(d, sl, io, u, ub, br);
+    const int64_t n = (int64_t)ub.size();
+    if (n > cap) return -1;
+    std::memcpy(unit, u.data(), u.size() * sizeof(int32_t));
+    std::memcpy(ubase, ub.data(), ub.size() * sizeof(int64_t));
+    if (!br.empty()) std::memcpy(brec, br.data(), br.size() * sizeof(int32_t));
+    return n;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return -1;
+  }
+}
+
+// Row tiers of the CSR row kernel for a matrix with the given row pointers
+// (see plan_csr_tiers): out2 = {group, long_min}, counts = {n_cta, n_warp},
+// cta and warp: rows ints each.
+int dginspect_csr_tiers(int64_t rows, const int64_t* ptr, int32_t* out2, int64_t* counts, int32_t* cta,
+                        int32_t* warp) {
+  try {
+    Csr C;
+    C.rows = rows;
+    C.ptr.assign(ptr, ptr + rows + 1);
+    const CsrTierPlan T = plan_csr_tiers(C);
+    out2[0] = T.group;
+    out2[1] = T.long_min;
+    counts[0] = (int64_t)T.cta.size();
+    counts[1] = (int64_t)T.warp.size();
+    if (!T.cta.empty()) std::memcpy(cta, T.cta.data(), T.cta.size() * sizeof(int32_t));
+    if (!T.warp.empty()) std::memcpy(warp, T.warp.data(), T.warp.size() * sizeof(int32_t));
+    return 0;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return -1;
+  }
+}
 
 void* dginspect_create(const dg_mesh_desc* desc, const dg_options* opts, int with_amg) {
   try {

@@ -16,6 +16,7 @@
 #include "kernels.cuh"
 #include "precond_setup.h"
 #include "union.h"
+#include "work_units.h"
 
 namespace dg {
 
@@ -42,34 +43,13 @@ void upload_csr_t(DevArena& a, const Csr& C, DevCsr& D, cudaStream_t s) {
   D.rows = C.rows;
   D.nnz = C.nnz();
   D.group_all = csr_group_for(C.rows ? (double)C.nnz() / (double)C.rows : 1.0);
-  // row tiers: the group width follows the rows of at most 64 entries; rows
-  // longer than 8 group rounds go to a warp each, rows longer than
-  // kCsrCtaRow to a CTA each (longest first in both lists)
-  double ssum = 0.0;
-  int64_t scnt = 0;
-  for (int64_t i = 0; i < C.rows; ++i) {
-    const int64_t len = C.ptr[i + 1] - C.ptr[i];
-    if (len <= 64) ssum += (double)len, ++scnt;
-  }
-  // half the lanes the mean suggests: measured faster (each lane keeps about
-  // twice as many entries in flight, and a warp takes twice as many rows)
-  D.group = std::max(1, csr_group_for(scnt ? ssum / (double)scnt : 64.0) / 2);
-  D.long_min = D.group >= 32 ? kCsrCtaRow : std::max(8 * D.group, 16);
-  std::vector<int32_t> cta, warp;
-  for (int64_t i = 0; i < C.rows; ++i) {
-    const int64_t len = C.ptr[i + 1] - C.ptr[i];
-    if (len > kCsrCtaRow) cta.push_back((int32_t)i);
-    else if (len > D.long_min) warp.push_back((int32_t)i);
-  }
-  auto longer = [&](int32_t x, int32_t y) {
-    return C.ptr[x + 1] - C.ptr[x] > C.ptr[y + 1] - C.ptr[y];
-  };
-  std::stable_sort(cta.begin(), cta.end(), longer);
-  std::stable_sort(warp.begin(), warp.end(), longer);
-  D.n_cta = (int)cta.size();
-  D.n_warp = (int)warp.size();
-  if (!cta.empty()) D.cta_rows = a.upload(cta, s);
-  if (!warp.empty()) D.warp_rows = a.upload(warp, s);
+  const CsrTierPlan tp = plan_csr_tiers(C);
+  D.group = tp.group;
+  D.long_min = tp.long_min;
+  D.n_cta = (int)tp.cta.size();
+  D.n_warp = (int)tp.warp.size();
+  if (!tp.cta.empty()) D.cta_rows = a.upload(tp.cta, s);
+  if (!tp.warp.empty()) D.warp_rows = a.upload(tp.warp, s);
   D.ptr = a.upload(ptr, s);
   D.idx = a.upload(C.idx, s);
   D.val = a.upload(val, s);
@@ -145,39 +125,10 @@ void upload_union_precond(dg_precond* pc, const std::vector<InstSrc>& inst, cuda
   upload_csr_t<T>(a, csr_transpose(P), pc->PT, s);
   pc->dinv = a.upload(std::vector<T>(dinv.begin(), dinv.end()), s);
   pc->e_pos = a.upload(eb, s);
-  // block-solve units, largest blocks first over all instances: 32-row panels
-  // of blocks of more than 16 nodes; blocks of at most W = 4, 8, 16 nodes
-  // packed 32 / W to a unit
-  DG_REQUIRE(pc->max_block <= 32 * 256, "a V_e block has more than 8192 nodes");
-  std::vector<int64_t> bsort(nb);
-  for (int64_t b = 0; b < nb; ++b) bsort[b] = b;
-  std::stable_sort(bsort.begin(), bsort.end(), [&](int64_t x, int64_t y) { return dims[x] > dims[y]; });
+  // block-solve units over all instances, largest blocks first
   std::vector<int32_t> unit, brec;
   std::vector<int64_t> ubase;
-  for (int64_t k = 0; k < nb;) {
-    const int64_t b = bsort[k];
-    const int32_t d = dims[b];
-    if (d > 16) {
-      for (int32_t r0 = 0; r0 < d; r0 += 32) {
-        unit.insert(unit.end(), {dofs_off[b], d, r0, 0});
-        ubase.push_back(inv_off[b] + r0);
-      }
-      ++k;
-      continue;
-    }
-    const int32_t W = d > 8 ? 16 : (d > 4 ? 8 : 4);
-    int32_t cnt = 0;
-    const int64_t first = (int64_t)brec.size() / 4;
-    while (k < nb && cnt < 32 / W && dims[bsort[k]] <= W && (W == 4 || dims[bsort[k]] > W / 2)) {
-      const int64_t bb = bsort[k];
-      brec.insert(brec.end(), {dofs_off[bb], dims[bb], (int32_t)(uint32_t)(inv_off[bb] & 0xffffffffu),
-                               (int32_t)(inv_off[bb] >> 32)});
-      ++cnt;
-      ++k;
-    }
-    unit.insert(unit.end(), {(int32_t)first, cnt, 0, W});
-    ubase.push_back(0);
-  }
+  plan_block_units(dims, dofs_off, inv_off, unit, ubase, brec);
   pc->blk_unit = a.upload(unit, s);
   pc->blk_ubase = a.upload(ubase, s);
   pc->blk_rec = a.upload(brec, s);
