@@ -39,7 +39,7 @@ struct DevCsr {
   int32_t* idx = nullptr;
   void* val = nullptr;
   int group = 1;       // lanes per row in the group tier (power of two <= 32)
-  int group_all = 1;   // lanes per row from the mean of all rows (fused AMG up-sweep)
+  int group_all = 1;   // lanes per row of the fused AMG up-sweep (set per level from the mean row length)
   // rows read by a whole CTA (more than kCsrCtaRow entries) and by a whole
   // warp (more than long_min entries); the group tier skips both
   int32_t* cta_rows = nullptr;
