@@ -33,6 +33,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+# the CPU oracle legs report one core: keep numpy's BLAS on one thread (set
+# before numpy is first imported; the GPU path does no host BLAS work)
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
 
 WORKLOAD = "2D hp-random 32x32 base, prob 0.3, depth<=3, p~U{1..6}, SIPG eta=100, tol 1e-8, seed 0"
 METRIC = "DOF-iters/s (PCG on the 2D hp-random workload, mixed FP32 preconditioner / FP64 outer)"
@@ -463,12 +467,7 @@ def cpu_baseline3(args):
     """The oracle on a bounded sample of the 3D workload: the same refinement
     and degree recipe on a 4^3 base (25k DOFs; the full 16^3 mesh is beyond the
     oracle's setup), FP64 PCG iterations, one thread."""
-    from oracle import rhs, solver
-    from paper_2009_01287_gb300 import inputs
-    mesh, rh = inputs.config2(args.seed, base=4)
-    prob = solver.build_problem(mesh, form="br2")
-    pc = solver.Preconditioner(prob, lor="amg")
-    b = rhs.load_vector(prob.space, rh.amps, rh.waves)
+    prob, pc, b = _oracle_setup3(args.seed)
     dt = _oracle_step(prob, pc, b, ORACLE_SAMPLE_ITERS)
     return {"value": prob.space.n * ORACLE_SAMPLE_ITERS / dt, "unit": "DOF-iters/s", "cores": 1,
             "kind": "oracle",
@@ -485,19 +484,39 @@ def cpu_baseline(args, coef: bool = False):
                       f"(setup untimed), scipy sparse + numpy, one thread"}
 
 
+def _oracle_setup3(seed: int):
+    """The 3D recipe on a 4^3 base (the full 16^3 mesh is beyond the oracle's setup)."""
+    from oracle import rhs, solver
+    from paper_2009_01287_gb300 import inputs
+    mesh, rh = inputs.config2(seed, base=4)
+    prob = solver.build_problem(mesh, form="br2")
+    pc = solver.Preconditioner(prob, lor="amg")
+    b = rhs.load_vector(prob.space, rh.amps, rh.waves)
+    return prob, pc, b
+
+
 def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
         return
-    prob, pc, b = _oracle_setup(args.seed)
+    if args.workload in ("batched", "serving"):
+        print(json.dumps({"impl": "reference", "unavailable": f"the oracle has no {args.workload} form; "
+                          "its single-problem PCG is timed by the hp2d, hp2d-coef and hp3d workloads"}))
+        return
+    three = args.workload == "hp3d"
+    coef = args.workload == "hp2d-coef"
+    prob, pc, b = _oracle_setup3(args.seed) if three else _oracle_setup(args.seed, coef)
     for _ in range(args.warmup):
         _oracle_step(prob, pc, b, ORACLE_SAMPLE_ITERS)
     times = [_oracle_step(prob, pc, b, ORACLE_SAMPLE_ITERS) for _ in range(args.steps)]
     n = prob.space.n
     value = n * ORACLE_SAMPLE_ITERS * args.steps / sum(times)
+    sample = f"{ORACLE_SAMPLE_ITERS} FP64 PCG iterations per step"
+    if three:
+        sample += f" on the same recipe with a 4^3 base ({n} DOFs)"
     out = {
         "impl": "reference",
-        "metric": METRIC,
+        "metric": METRIC3 if three else (METRICC if coef else METRIC),
         "value": value,
         "unit": "DOF-iters/s",
         "n_gpus": ws,
@@ -509,9 +528,9 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_dofs": n},
+        "config": {"workload": WORKLOAD3 if three else (WORKLOADC if coef else WORKLOAD), "n_dofs": n},
         "cpu_baseline": {"value": value, "unit": "DOF-iters/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{ORACLE_SAMPLE_ITERS} FP64 PCG iterations per step"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": "DOF-iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
