@@ -147,3 +147,18 @@ def test_lor_equivalence_is_independent_of_the_contrast():
     lo1, hi1 = _lor_extremes(mesh)
     lo20, hi20 = _lor_extremes(inputs.with_coeff(mesh, inputs.base_parity_coeff(mesh, 2)))
     assert lo20 > 0.5 * lo1 and hi20 < 2.0 * hi1
+
+
+def test_sipg_condition_number_robust_in_the_contrast():
+    """kappa(BA) with the exact LOR solve on a small hp mesh stays within a
+    factor 1.5 of its a = 1 value for contrasts 20 and 1000 (SIPG, penalty with
+    the larger a of the two sides)."""
+    mesh = inputs.small_hp_mesh(2, base=4, depth=2, prob=0.4, pmin=1, pmax=4)
+    kap = []
+    for c in (1.0, 20.0, 1000.0):
+        m = inputs.with_coeff(mesh, inputs.base_parity_coeff(mesh, 4, (1.0, c)))
+        prob = solver.build_problem(m, form="sipg")
+        B = solver.Preconditioner(prob, lor="exact").matrix()
+        ev = np.real(np.linalg.eigvals(B @ prob.A.toarray()))
+        kap.append(ev.max() / ev.min())
+    assert max(kap) < 1.5 * kap[0] and min(kap) > kap[0] / 1.5
