@@ -2,11 +2,12 @@
  * dg.h - C ABI of the GB300 hp-DG subspace-correction solver.
  *
  * Problem (Section 2, Eq. poisson / fe-problem): -Laplace(u) = f on a box
- * domain with u = 0 on the boundary, discretised by the symmetric interior
- * penalty (SIPG) or BR2 (Section 4.4) DG method on a mesh of axis-aligned
- * leaf squares (2D) of variable size (hanging nodes, arbitrary irregularity)
- * and variable degree p in 1..8, with the Gauss-Lobatto nodal basis of
- * Section 2.2.  Solved by conjugate gradients (Section 4.1) preconditioned by
+ * domain with u = 0 on the boundary, or -div(a grad u) = f with a
+ * piecewise-constant coefficient a (Section 4.3; dg_mesh_desc.coeff),
+ * discretised by the symmetric interior penalty (SIPG) or BR2 (Section 4.4)
+ * DG method on a mesh of axis-aligned leaf squares (2D) or cubes (3D) of
+ * variable size (hanging nodes, arbitrary irregularity) and variable degree p
+ * in 1..8, with the Gauss-Lobatto nodal basis of Section 2.2.  Solved by conjugate gradients (Section 4.1) preconditioned by
  * B = B_B + B_C (Section 3.1, 3.3, 3.4): variational restriction P^T, a
  * low-order-refined (LOR) conforming solve (exact or one AMG V-cycle), the
  * prolongation P, point Jacobi on V_J and exact block solves on the V_e.
@@ -14,9 +15,10 @@
  * Conventions shared by every entry point
  *   - Vectors are DEVICE pointers to double, owned by the caller, in the
  *     element-major DG layout: element k (in the order given to
- *     dg_mesh_create) owns (p_k+1)^2 consecutive entries; inside an element
- *     the node (ix, iy) is entry iy*(p_k+1) + ix, nodes at the Gauss-Lobatto
- *     points of [0,1] mapped to the element.  Unless a name ends in _host.
+ *     dg_mesh_create) owns (p_k+1)^d consecutive entries; inside an element
+ *     the node (ix, iy[, iz]) is entry (iz*(p_k+1) + iy)*(p_k+1) + ix, nodes
+ *     at the Gauss-Lobatto points of [0,1] mapped to the element.  Unless a
+ *     name ends in _host.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
  *     is stream-ordered and returns once its work is enqueued, except where
  *     stated.  A handle is not thread-safe; distinct handles are.
