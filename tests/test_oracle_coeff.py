@@ -162,3 +162,41 @@ def test_sipg_condition_number_robust_in_the_contrast():
         ev = np.real(np.linalg.eigvals(B @ prob.A.toarray()))
         kap.append(ev.max() / ev.min())
     assert max(kap) < 1.5 * kap[0] and min(kap) > kap[0] / 1.5
+
+
+def test_sipg_penalty_closed_form_hanging_cubes_with_coefficient():
+    """One coarse cube next to four fine ones, piecewise-constant u and a: a(u,u)
+    = sum over sub-faces of sigma |F| [[u]]^2, sigma carrying the larger a."""
+    lh, eta = 0.25, 3.0
+    lo = [(0, 0, 0)] + [(2, j, k) for k in (0, 1) for j in (0, 1)]
+    size = [2, 1, 1, 1, 1]
+    p = [2, 1, 3, 2, 1]
+    a = [20.0, 1.0, 3.0, 1.0, 50.0]
+    mesh = _mesh(lo, size, p, (3, 2, 2), lh, a)
+    topo, space, A = solver.build_operator(mesh, form="sipg", eta=eta)
+    c = np.array([1.0, -2.0, 0.5, 3.0, 0.0])
+    u = np.concatenate([np.full((pk + 1) ** 3, ck) for pk, ck in zip(p, c)])
+    expect = 0.0
+    for f in topo.subfaces:
+        area = (f.hi[0] - f.lo[0]) * (f.hi[1] - f.lo[1]) * lh * lh
+        if f.kp >= 0:
+            s = max(a[f.km], a[f.kp]) * eta * max(p[f.km], p[f.kp]) ** 2 / (lh * min(size[f.km], size[f.kp]))
+            expect += s * area * (c[f.km] - c[f.kp]) ** 2
+        else:
+            s = a[f.km] * eta * p[f.km] ** 2 / (lh * size[f.km])
+            expect += s * area * c[f.km] ** 2
+    assert abs(u @ A @ u - expect) < 1e-12 * expect
+
+
+def test_br2_penalty_closed_form_cubes_with_coefficient():
+    """Conforming 2x1x1 cubes, u = 1 on the left one: each side's lifting energy
+    (p+1)^2 h (1/4 per side on the interior face, all of it on the five
+    boundary faces) carries that side's a."""
+    h, eta = 0.5, 2.0
+    for (pl, pr), (al, ar) in [((1, 1), (1.0, 20.0)), ((2, 3), (20.0, 1.0)), ((3, 1), (0.5, 4.0))]:
+        mesh = _mesh([(0, 0, 0), (1, 0, 0)], [1, 1], [pl, pr], (2, 1, 1), h, [al, ar])
+        _, space, A = solver.build_operator(mesh, form="br2", eta=eta)
+        u = np.zeros(space.n)
+        u[:(pl + 1) ** 3] = 1.0
+        expect = eta * (0.25 * (al * (pl + 1) ** 2 * h + ar * (pr + 1) ** 2 * h) + 5 * al * (pl + 1) ** 2 * h)
+        assert abs(u @ A @ u - expect) < 1e-11 * expect
