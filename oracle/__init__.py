@@ -19,9 +19,13 @@ Modules
     rhs        load vector of the synthetic sine right-hand side
 
 Parity status: every function is pinned by tests/test_oracle_*.py against
-closed forms, manufactured solutions, invariants or brute force, except the
-smoothed-aggregation AMG, whose aggregation choices have no counterpart in the
-paper (the paper uses BoomerAMG); its V-cycle is pinned only by properties
-(symmetry, exactness on a single level, Galerkin identity) - parity unpinned
-with respect to the paper.
+closed forms, manufactured solutions, invariants, hand-worked cases or brute
+force.  The smoothed-aggregation AMG has no counterpart in the paper (the paper
+uses BoomerAMG without stating its parameters), so it is pinned against its own
+stated algorithm: hand-worked aggregations and prolongator entries
+(tests/golden/amg_aggregation.txt), the error-propagation form of the V-cycle,
+symmetry, exactness on a single level and the Galerkin identity.
+dg.element_rows is pinned against the rows of dg.assemble, and
+rhs.load_vector against closed-form integrals within the Gauss rule's error
+bound.
 """
