@@ -115,6 +115,14 @@ typedef struct {
   int level_plain[16];   /* 1: level applied in the plain form (A, R, P),
                             0: composite operators (see dg_precond_setup)   */
   int kernels_per_apply; /* device kernel launches of one dg_precond_apply  */
+  int64_t device_bytes;  /* device memory held by the handle: the
+                            preconditioner and the PCG workspace of its
+                            solves (the mesh's own memory not included)     */
+  double apply_bytes;    /* algorithmic bytes of one dg_precond_apply: every
+                            matrix entry (value + index), row pointer and
+                            vector entry its kernels touch, counted once    */
+  double block_bytes;    /* the same for its block solves (the V_e inverses,
+                            node lists, gathered residual, results)         */
 } dg_precond_stats;
 
 typedef struct {
@@ -125,6 +133,7 @@ typedef struct {
   double apply_flops;     /* FP64 flops of one dg_apply as formulated (FMA = 2)  */
   double apply_bytes;     /* algorithmic bytes of one dg_apply: x read, y write,
                              per-element and per-sub-face records read once     */
+  int64_t device_bytes;   /* device memory held by the mesh handle              */
 } dg_mesh_stats;
 
 /* Build the mesh topology (sub-faces, hanging vertices, master edges) and
@@ -135,6 +144,12 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, const dg_options* opts,
 void dg_mesh_destroy(dg_mesh* mesh);
 int64_t dg_num_dofs(const dg_mesh* mesh);
 dg_status dg_mesh_stats_get(const dg_mesh* mesh, dg_mesh_stats* out);
+/* DOF layout (Section 2: V_h is the direct sum of the Q_{p_k} spaces of the
+ * elements): elem_offsets (HOST, n_elems + 1 entries) receives the offset of
+ * each element's first entry in a DG vector, in the element order given to
+ * dg_mesh_create; elem_offsets[n_elems] = n_dofs.  Inside an element the
+ * entries follow the node order stated at the top of this header. */
+dg_status dg_dof_layout(const dg_mesh* mesh, int64_t* elem_offsets);
 
 /* y = A x, the matrix-free DG operator of Eq. fe-problem (SIPG) or of the
  * BR2 form (Section 4.4), FP64.  x and y: device, n_dofs doubles, must not
@@ -149,16 +164,49 @@ dg_status dg_apply(const dg_mesh* mesh, const double* x, double* y, void* stream
  * the plain form (four kernels, about half the bytes); both are the same
  * V-cycle.  Host work, then uploads; synchronous. */
 dg_status dg_precond_setup(const dg_mesh* mesh, const dg_options* opts, dg_precond** out);
+/* (dg_precond_setup also creates the workspace and the captured graph of the
+ * PCG solves with this handle, so that dg_pcg_solve allocates nothing.) */
 void dg_precond_destroy(dg_precond* pc);
 dg_status dg_precond_stats_get(const dg_precond* pc, dg_precond_stats* out);
 
 /* z = B r (Section 4.1).  r, z: device, n_dofs doubles, must not overlap. */
 dg_status dg_precond_apply(const dg_precond* pc, const double* r, double* z, void* stream);
 
+/* ---- Profiling (CUDA events; stream-ordered, synchronous on `stream`).
+ * dg_precond_profile runs one z = B r with its parts one after another on
+ * `stream` (the block solves first, alone, instead of beside the V-cycle) and
+ * returns the time of each part: the block solves on the V_e (Section 3.3),
+ * the restriction P^T r, the LOR solve (Section 3.4), and the final
+ * combination z = P e_C + D_J^-1 r + block results.  z is the same as from
+ * dg_precond_apply.  dg_apply_profile times the two kernels of one y = A x:
+ * the side traces of x, then the operator kernel. */
+typedef struct {
+  double blocks_ms, restrict_ms, lor_ms, final_ms, total_ms;
+} dg_precond_times;
+dg_status dg_precond_profile(const dg_precond* pc, const double* r, double* z, dg_precond_times* out,
+                             void* stream);
+typedef struct {
+  double trace_ms, apply_ms;
+} dg_apply_times;
+dg_status dg_apply_profile(const dg_mesh* mesh, const double* x, double* y, dg_apply_times* out,
+                           void* stream);
+/* FP64 FMA throughput of the current device: 8 independent FMA chains per
+ * thread, 8 CTAs of 256 threads per SM, `iters` steps each, timed with CUDA
+ * events after one shorter warm-up launch.  The operator kernels are bound by
+ * FP64 arithmetic, so this is the peak their roofline is reported against.
+ * No counterpart in the paper (a measurement aid).  Synchronous. */
+dg_status dg_fp64_fma_probe(int64_t iters, double* tflops, double* ms, void* stream);
+
 /* PCG (Section 4.1) from x0 = 0 until ||r||_2 <= rtol ||b||_2 or maxit.
  * b, x: device, n_dofs doubles; x receives the solution (the last iterate on
- * DG_ENOTCONV).  The iteration runs as one CUDA graph with a device-side
- * while loop; the call waits for it (synchronous on `stream`). */
+ * DG_ENOTCONV).  A solve is one CUDA graph launch: the start (x = 0, r = b,
+ * z = B r, p = z) and a device-side while loop of PCG iterations, captured
+ * once per preconditioner on the handle's own copies of b and x (copied in
+ * and out inside the call) with rtol and maxit read from device memory, so
+ * any b, x, rtol and maxit reuse it.  The call waits for the solve
+ * (synchronous on `stream`); info->solve_ms is the CUDA-event time of
+ * everything the solve enqueues, from the copy of b to the copy of x, with no
+ * host round trip inside. */
 dg_status dg_pcg_solve(const dg_mesh* mesh, const dg_precond* pc, const double* b,
                        double* x, double rtol, int maxit, dg_solve_info* info,
                        void* stream);

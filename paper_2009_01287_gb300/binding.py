@@ -27,11 +27,12 @@ DG_SMOOTHER_FULL, DG_SMOOTHER_JACOBI_ONLY = 0, 1
 
 # every entry point declared in include/dg.h
 ABI_SYMBOLS = (
-    "dg_mesh_create", "dg_mesh_destroy", "dg_num_dofs", "dg_mesh_stats_get", "dg_apply", "dg_precond_setup",
+    "dg_mesh_create", "dg_mesh_destroy", "dg_num_dofs", "dg_mesh_stats_get", "dg_dof_layout", "dg_apply",
+    "dg_precond_setup",
     "dg_precond_destroy", "dg_precond_stats_get", "dg_precond_apply", "dg_pcg_solve",
     "dg_pcg_solve_host", "dg_pcg_solve_noalloc", "dg_rhs_sine", "dg_last_error",
     "dg_batch_create", "dg_batch_destroy", "dg_batch_num_dofs", "dg_batch_offsets", "dg_batch_rhs_sine",
-    "dg_batch_solve",
+    "dg_batch_solve", "dg_precond_profile", "dg_apply_profile", "dg_fp64_fma_probe",
 )
 
 
@@ -55,7 +56,8 @@ class DgSolveInfo(C.Structure):
 
 class DgMeshStats(C.Structure):
     _fields_ = [("n_elems", C.c_int64), ("n_dofs", C.c_int64), ("n_subfaces", C.c_int64),
-                ("max_level_gap", C.c_int64), ("apply_flops", C.c_double), ("apply_bytes", C.c_double)]
+                ("max_level_gap", C.c_int64), ("apply_flops", C.c_double), ("apply_bytes", C.c_double),
+                ("device_bytes", C.c_int64)]
 
 
 class DgPrecondStats(C.Structure):
@@ -63,7 +65,17 @@ class DgPrecondStats(C.Structure):
                 ("n_e", C.c_int64), ("n_blocks", C.c_int64), ("max_block", C.c_int64),
                 ("lor_nnz", C.c_int64), ("p_nnz", C.c_int64), ("n_levels", C.c_int),
                 ("level_rows", C.c_int64 * 16), ("level_nnz", C.c_int64 * 16),
-                ("level_plain", C.c_int * 16), ("kernels_per_apply", C.c_int)]
+                ("level_plain", C.c_int * 16), ("kernels_per_apply", C.c_int), ("device_bytes", C.c_int64),
+                ("apply_bytes", C.c_double), ("block_bytes", C.c_double)]
+
+
+class DgPrecondTimes(C.Structure):
+    _fields_ = [("blocks_ms", C.c_double), ("restrict_ms", C.c_double), ("lor_ms", C.c_double),
+                ("final_ms", C.c_double), ("total_ms", C.c_double)]
+
+
+class DgApplyTimes(C.Structure):
+    _fields_ = [("trace_ms", C.c_double), ("apply_ms", C.c_double)]
 
 
 _lib = None
@@ -86,6 +98,10 @@ def lib():
         L.dg_num_dofs.argtypes = [vp]
         L.dg_num_dofs.restype = i64
         L.dg_mesh_stats_get.argtypes = [vp, C.POINTER(DgMeshStats)]
+        L.dg_dof_layout.argtypes = [vp, vp]
+        L.dg_precond_profile.argtypes = [vp, dp, dp, C.POINTER(DgPrecondTimes), vp]
+        L.dg_apply_profile.argtypes = [vp, dp, dp, C.POINTER(DgApplyTimes), vp]
+        L.dg_fp64_fma_probe.argtypes = [C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
         L.dg_apply.argtypes = [vp, dp, dp, vp]
         L.dg_precond_setup.argtypes = [vp, C.POINTER(DgOptions), C.POINTER(vp)]
         L.dg_precond_destroy.argtypes = [vp]
@@ -186,6 +202,13 @@ def dg_mesh_stats_get(h: int) -> DgMeshStats:
     return s
 
 
+def dg_dof_layout(h: int, n_elems: int) -> np.ndarray:
+    """Offsets of each element's first DG entry (n_elems + 1 values)."""
+    out = np.zeros(n_elems + 1, dtype=np.int64)
+    _check(lib().dg_dof_layout(h, out.ctypes.data))
+    return out
+
+
 def dg_apply(h: int, x, y, stream=None) -> None:
     _check(lib().dg_apply(h, _ptr(x), _ptr(y), _stream(stream)))
 
@@ -208,6 +231,25 @@ def dg_precond_stats_get(h: int) -> DgPrecondStats:
 
 def dg_precond_apply(h: int, r, z, stream=None) -> None:
     _check(lib().dg_precond_apply(h, _ptr(r), _ptr(z), _stream(stream)))
+
+
+def dg_precond_profile(h: int, r, z, stream=None) -> DgPrecondTimes:
+    t = DgPrecondTimes()
+    _check(lib().dg_precond_profile(h, _ptr(r), _ptr(z), C.byref(t), _stream(stream)))
+    return t
+
+
+def dg_apply_profile(h: int, x, y, stream=None) -> DgApplyTimes:
+    t = DgApplyTimes()
+    _check(lib().dg_apply_profile(h, _ptr(x), _ptr(y), C.byref(t), _stream(stream)))
+    return t
+
+
+def dg_fp64_fma_probe(iters: int = 20000, stream=None):
+    """(TFLOP/s, ms) of the FP64 FMA-chain probe."""
+    tf, ms = C.c_double(), C.c_double()
+    _check(lib().dg_fp64_fma_probe(iters, C.byref(tf), C.byref(ms), _stream(stream)))
+    return tf.value, ms.value
 
 
 def dg_pcg_solve(mesh_h: int, pc_h: int, b, x, rtol: float, maxit: int, stream=None,

@@ -216,6 +216,14 @@ int apply_kernel_setup(const dg_mesh& M) {
   return sms * (per > 0 ? per : 1);
 }
 
+void launch_trace(const dg_mesh& M, const double* x, cudaStream_t s) {
+  if (M.n_tiles == 0) return;
+  const ApplyArgs A = make_apply_args(M, x, nullptr, Reduce{});
+  if (M.host.dim == 3) launch_k(trace3_kernel, M.n_tiles, kThreads, 0, s, A);
+  else launch_k(trace_kernel, M.n_tiles, kThreads, 0, s, A);
+  DG_CUDA(cudaGetLastError());
+}
+
 void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cudaStream_t s,
                   bool with_trace) {
   if (M.n_tiles == 0) return;

@@ -1,11 +1,13 @@
 // C ABI entry points (include/dg.h): validation, host setup, uploads, the
 // graph-captured PCG loop.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "kernels.cuh"
@@ -36,7 +38,8 @@ static dg_status guarded(F&& f) {
 }
 
 static void build_mesh(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opts, cudaStream_t s) {
-  build_mesh_host(M, desc, opts);
+  build_mesh_host(M, desc, opts);   // validates before any device work
+  DG_CUDA(cudaGetDevice(&M->device));
   upload_mesh(M, s);
 }
 
@@ -149,23 +152,23 @@ static void upload_precond(dg_precond* pc, HostPrecond& H, cudaStream_t s) {
 }
 
 // ----------------------------------------------------------------- PCG workspace
+// Created with the preconditioner (dg_precond_setup), so solves allocate
+// nothing: the work vectors, the solve's own copies of b and x, pinned scalars,
+// a capture stream, two events and the captured iteration graph.  The graph
+// reads b from and writes x to the workspace copies and takes the tolerance
+// and iteration limit from device scalars, so one capture serves every solve.
 struct PcgWork {
   int64_t n = 0;
   double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  double *b = nullptr, *x = nullptr;   // the solve's copies of b and x
   double *part_pq = nullptr, *part_rr = nullptr, *part_rz = nullptr, *part_bb = nullptr;
   double* sc = nullptr;
   unsigned* tick = nullptr;  // reduction tickets (TK_*)
-  double* hsc = nullptr;  // pinned host copy of the scalars
-  double* hb = nullptr;   // device copies for the host-buffer entry point
-  double* hx = nullptr;
+  double* hsc = nullptr;     // pinned: scalars read back (SC_COUNT) + limits sent (2)
   DevArena arena;
-  // captured iteration graph and the arguments it was captured with
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cap = nullptr;
-  double* g_x = nullptr;
-  int g_maxit = -1;
-  double g_rtol2 = -1.0;
   bool graph_failed = false;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   void drop_graph() {
@@ -198,6 +201,8 @@ static PcgWork& pcg_work(const dg_precond* pc) {
   w->z = w->arena.alloc<double>(w->n);
   w->p = w->arena.alloc<double>(w->n);
   w->q = w->arena.alloc<double>(w->n);
+  w->b = w->arena.alloc<double>(w->n);
+  w->x = w->arena.alloc<double>(w->n);
   w->part_pq = w->arena.alloc<double>(std::max(M->n_tiles, 1));
   w->part_rr = w->arena.alloc<double>(kVecBlocks);
   w->part_rz = w->arena.alloc<double>(kVecBlocks);
@@ -205,13 +210,15 @@ static PcgWork& pcg_work(const dg_precond* pc) {
   w->sc = w->arena.alloc<double>(SC_COUNT);
   w->tick = w->arena.alloc<unsigned>(TK_COUNT);
   DG_CUDA(cudaMemset(w->tick, 0, TK_COUNT * sizeof(unsigned)));
-  w->hb = w->arena.alloc<double>(w->n);
-  w->hx = w->arena.alloc<double>(w->n);
-  DG_CUDA(cudaMallocHost(&w->hsc, SC_COUNT * sizeof(double)));
+  DG_CUDA(cudaMallocHost(&w->hsc, (SC_COUNT + 2) * sizeof(double)));
   DG_CUDA(cudaEventCreate(&w->e0));
   DG_CUDA(cudaEventCreate(&w->e1));
   DG_CUDA(cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking));
   return *w;
+}
+
+static int64_t pcg_work_bytes(const dg_precond* pc) {
+  return pc->pcg_cache ? (int64_t)((PcgWork*)pc->pcg_cache)->arena.bytes : 0;
 }
 
 static void pcg_body(const dg_mesh* M, const dg_precond* pc, PcgWork& w, double* x, int maxit,
@@ -223,57 +230,86 @@ static void pcg_body(const dg_mesh* M, const dg_precond* pc, PcgWork& w, double*
   launch_pcg_p_trace(*M, w.p, w.z, w.sc, w.tick + TK_P, maxit, rtol2, (unsigned long long)h, use_cond, 0, s);
 }
 
-// PCG start: x = 0, r = b, z = B r, p = z, scalars; returns b . b (synchronises)
-static double pcg_start(const dg_precond* pc, PcgWork& w, const double* b, double* x, double* hsc,
-                        cudaStream_t s) {
+// PCG start: x = 0, r = b, z = B r, p = z with its side traces, the initial
+// scalars; with use_cond the last kernel sets the loop condition (b . b > 0)
+static void pcg_start_kernels(const dg_precond* pc, PcgWork& w, const double* b, double* x,
+                              cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
   launch_pcg_init(b, x, w.r, w.n, Reduce{w.part_bb, w.sc + SC_BB, w.tick + TK_BB}, s);
   launch_precond(*pc, w.r, w.z, Reduce{w.part_rz, w.sc + SC_RZNEW, w.tick + TK_RZ}, s);
-  launch_pcg_p_trace(*pc->mesh, w.p, w.z, w.sc, w.tick + TK_P, 0, 0.0, 0ull, 0, 1, s);
+  launch_pcg_p_trace(*pc->mesh, w.p, w.z, w.sc, w.tick + TK_P, 0, 0.0, (unsigned long long)h, use_cond, 1, s);
+}
+
+// host-driven start: the kernels above, then b . b read back (synchronises)
+static double pcg_start(const dg_precond* pc, PcgWork& w, const double* b, double* x, double* hsc,
+                        cudaStream_t s) {
+  pcg_start_kernels(pc, w, b, x, 0, 0, s);
   DG_CUDA(cudaMemcpyAsync(hsc, w.sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
   DG_CUDA(cudaStreamSynchronize(s));
   return hsc[SC_BB];
 }
 
-// one graph: while (cond) { PCG iteration }, the condition set on the device
-static bool pcg_capture(const dg_mesh* M, const dg_precond* pc, PcgWork& w, double* x, int maxit,
-                        double rtol2) {
-  if (w.exec && w.g_x == x && w.g_maxit == maxit && w.g_rtol2 == rtol2) return true;
-  w.drop_graph();
+// One graph for a whole solve: the start kernels, then a device-side while
+// node around one PCG iteration whose condition the kernels set.  Captured
+// once per preconditioner, on the workspace copies of b and x, with the limits
+// read from device scalars.
+static bool pcg_capture(const dg_mesh* M, const dg_precond* pc, PcgWork& w) {
+  if (w.exec) return true;
   if (w.graph_failed) return false;
   const char* env = std::getenv("DG_PCG_GRAPH");
   if (env && env[0] == '0') return false;  // host-driven loop requested
   cudaGraphConditionalHandle handle = 0;
   bool ok = false;
+  std::string why;
   if (cudaGraphCreate(&w.graph, 0) == cudaSuccess &&
-      cudaGraphConditionalHandleCreate(&handle, w.graph, 1, cudaGraphCondAssignDefault) == cudaSuccess) {
+      cudaGraphConditionalHandleCreate(&handle, w.graph, 0, cudaGraphCondAssignDefault) == cudaSuccess &&
+      cudaStreamBeginCaptureToGraph(w.cap, w.graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) ==
+          cudaSuccess) {
     cudaGraphNodeParams cp{};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = handle;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    if (cudaGraphAddNode(&node, w.graph, nullptr, nullptr, 0, &cp) == cudaSuccess) {
+    bool launched = true;
+    try {
+      pcg_start_kernels(pc, w, w.b, w.x, handle, 1, w.cap);
+      // the while node follows the start kernels
+      cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+      cudaGraph_t g = nullptr;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      DG_CUDA(cudaStreamGetCaptureInfo(w.cap, &st, nullptr, &g, &deps, nullptr, &nd));
+      cudaGraphNode_t cnode = nullptr;
+      DG_CUDA(cudaGraphAddNode(&cnode, g, deps, nullptr, nd, &cp));
+      DG_CUDA(cudaStreamUpdateCaptureDependencies(w.cap, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    } catch (const Error& e) {
+      launched = false;
+      why = e.what();
+    }
+    cudaGraph_t out = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(w.cap, &out);
+    ok = ec == cudaSuccess && launched;
+    if (ok) {
       cudaGraph_t body = cp.conditional.phGraph_out[0];
-      if (cudaStreamBeginCaptureToGraph(w.cap, body, nullptr, nullptr, 0,
-                                        cudaStreamCaptureModeRelaxed) == cudaSuccess) {
-        bool launched = true;
-        std::string why;
+      ec = cudaStreamBeginCaptureToGraph(w.cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+      if (ec == cudaSuccess) {
         try {
-          pcg_body(M, pc, w, x, maxit, rtol2, handle, 1, w.cap);
+          pcg_body(M, pc, w, w.x, -1, 0.0, handle, 1, w.cap);
         } catch (const Error& e) {
           launched = false;
           why = e.what();
         }
-        cudaGraph_t out = nullptr;
-        const cudaError_t ec = cudaStreamEndCapture(w.cap, &out);
-        cudaError_t ei = cudaErrorUnknown;
-        if (ec == cudaSuccess && launched) ei = cudaGraphInstantiate(&w.exec, w.graph, 0);
-        ok = ec == cudaSuccess && launched && ei == cudaSuccess;
-        if (!ok && std::getenv("DG_VERBOSE"))
-          std::fprintf(stderr, "dg: capture: launch [%s] end-capture %s instantiate %s\n", why.c_str(),
-                       cudaGetErrorString(ec), cudaGetErrorString(ei));
+        ec = cudaStreamEndCapture(w.cap, &out);
       }
+      ok = ec == cudaSuccess && launched;
     }
+    cudaError_t ei = cudaSuccess;
+    if (ok) {
+      ei = cudaGraphInstantiate(&w.exec, w.graph, 0);
+      ok = ei == cudaSuccess;
+    }
+    if (!ok && std::getenv("DG_VERBOSE"))
+      std::fprintf(stderr, "dg: capture: launch [%s] capture %s instantiate %s\n", why.c_str(),
+                   cudaGetErrorString(ec), cudaGetErrorString(ei));
   }
   const cudaError_t cap_err = cudaGetLastError();
   if (!ok) {
@@ -284,12 +320,12 @@ static bool pcg_capture(const dg_mesh* M, const dg_precond* pc, PcgWork& w, doub
     w.graph_failed = true;
     return false;
   }
-  w.g_x = x;
-  w.g_maxit = maxit;
-  w.g_rtol2 = rtol2;
   return true;
 }
 
+// Solve into the workspace copy of x.  solve_ms spans everything the solve
+// puts on the stream: the copy of b, the limits, the start, the iterations and
+// the copy of x; with the graph there is no host round trip inside it.
 static void pcg_run(const dg_mesh* M, const dg_precond* pc, const double* b, double* x, double rtol,
                     int maxit, dg_solve_info* info, cudaStream_t s) {
   DG_REQUIRE(M && pc && b && x, "null argument");
@@ -297,22 +333,26 @@ static void pcg_run(const dg_mesh* M, const dg_precond* pc, const double* b, dou
   DG_REQUIRE(rtol > 0.0 && maxit >= 1, "rtol must be > 0 and maxit >= 1");
   PcgWork& w = pcg_work(pc);
   const double rtol2 = rtol * rtol;
-  const bool use_graph = pcg_capture(M, pc, w, x, maxit, rtol2);
+  const bool use_graph = pcg_capture(M, pc, w);
+  // the previous solve with this handle has finished (solves are synchronous),
+  // so the pinned slots are free to take this solve's limits
+  w.hsc[SC_COUNT] = (double)maxit;
+  w.hsc[SC_COUNT + 1] = rtol2;
   DG_CUDA(cudaEventRecord(w.e0, s));
-  pcg_start(pc, w, b, x, w.hsc, s);
-  if (w.hsc[SC_BB] > 0.0) {
-    if (use_graph) {
-      DG_CUDA(cudaGraphLaunch(w.exec, s));
-    } else {
-      // host-driven loop, status read back every 8 iterations
-      for (int it = 0; it < maxit;) {
-        for (int j = 0; j < 8 && it < maxit; ++j, ++it) pcg_body(M, pc, w, x, maxit, rtol2, 0, 0, s);
-        DG_CUDA(cudaMemcpyAsync(w.hsc, w.sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
-        DG_CUDA(cudaStreamSynchronize(s));
-        if (w.hsc[SC_STATUS] != 0.0) break;
-      }
+  if (b != w.b) DG_CUDA(cudaMemcpyAsync(w.b, b, w.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  DG_CUDA(cudaMemcpyAsync(w.sc + SC_MAXIT, w.hsc + SC_COUNT, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (use_graph) {
+    DG_CUDA(cudaGraphLaunch(w.exec, s));
+  } else if (pcg_start(pc, w, w.b, w.x, w.hsc, s) > 0.0) {
+    // host-driven loop, status read back every 8 iterations
+    for (int it = 0; it < maxit;) {
+      for (int j = 0; j < 8 && it < maxit; ++j, ++it) pcg_body(M, pc, w, w.x, maxit, rtol2, 0, 0, s);
+      DG_CUDA(cudaMemcpyAsync(w.hsc, w.sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+      DG_CUDA(cudaStreamSynchronize(s));
+      if (w.hsc[SC_STATUS] != 0.0) break;
     }
   }
+  if (x != w.x) DG_CUDA(cudaMemcpyAsync(x, w.x, w.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   DG_CUDA(cudaEventRecord(w.e1, s));
   DG_CUDA(cudaMemcpyAsync(w.hsc, w.sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
   DG_CUDA(cudaStreamSynchronize(s));
@@ -360,6 +400,15 @@ dg_status dg_mesh_stats_get(const dg_mesh* mesh, dg_mesh_stats* out) {
   return guarded([&] {
     DG_REQUIRE(mesh && out, "null argument");
     *out = mesh->stats;
+    out->device_bytes = (int64_t)mesh->arena.bytes;
+  });
+}
+
+dg_status dg_dof_layout(const dg_mesh* mesh, int64_t* elem_offsets) {
+  return guarded([&] {
+    DG_REQUIRE(mesh && elem_offsets, "null argument");
+    const std::vector<int64_t>& off = mesh->host.off;
+    std::copy(off.begin(), off.end(), elem_offsets);
   });
 }
 
@@ -405,6 +454,8 @@ dg_status dg_precond_setup(const dg_mesh* mesh, const dg_options* opts, dg_preco
     cudaStream_t s = nullptr;
     if (o.precision == DG_PREC_MIXED) upload_precond<float>(pc, H, s);
     else upload_precond<double>(pc, H, s);
+    // the solves' workspace and graph, so that solves allocate nothing
+    pcg_capture(mesh, pc, pcg_work(pc));
   });
   if (st != DG_OK) { delete pc; return st; }
   *out = pc;
@@ -418,6 +469,8 @@ dg_status dg_precond_stats_get(const dg_precond* pc, dg_precond_stats* out) {
     DG_REQUIRE(pc && out, "null argument");
     *out = pc->stats;
     out->kernels_per_apply = precond_kernel_count(*pc);
+    out->device_bytes = (int64_t)pc->arena.bytes + pcg_work_bytes(pc);
+    precond_algorithmic_bytes(*pc, &out->apply_bytes, &out->block_bytes);
   });
 }
 
@@ -426,6 +479,60 @@ dg_status dg_precond_apply(const dg_precond* pc, const double* r, double* z, voi
     DG_REQUIRE(pc && r && z, "null argument");
     DG_REQUIRE(r != z, "r and z must not alias");
     launch_precond(*pc, r, z, Reduce{}, (cudaStream_t)stream);
+  });
+}
+
+// events of one profiled call, destroyed on every exit
+struct EventSet {
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  explicit EventSet(int n) {
+    for (int i = 0; i < n; ++i) DG_CUDA(cudaEventCreate(&ev[i]));
+  }
+  ~EventSet() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+  double ms(int a, int b) const {
+    float t = 0.0f;
+    DG_CUDA(cudaEventElapsedTime(&t, ev[a], ev[b]));
+    return t;
+  }
+};
+
+dg_status dg_precond_profile(const dg_precond* pc, const double* r, double* z, dg_precond_times* out,
+                             void* stream) {
+  return guarded([&] {
+    DG_REQUIRE(pc && r && z && out, "null argument");
+    DG_REQUIRE(r != z, "r and z must not alias");
+    const cudaStream_t s = (cudaStream_t)stream;
+    EventSet E(5);
+    PrecondMarks mk;
+    for (int i = 0; i < 5; ++i) mk.ev[i] = E.ev[i];
+    launch_precond(*pc, r, z, Reduce{}, s, &mk);
+    DG_CUDA(cudaEventSynchronize(E.ev[4]));
+    out->blocks_ms = E.ms(0, 1);
+    out->restrict_ms = E.ms(1, 2);
+    out->lor_ms = E.ms(2, 3);
+    out->final_ms = E.ms(3, 4);
+    out->total_ms = E.ms(0, 4);
+  });
+}
+
+dg_status dg_apply_profile(const dg_mesh* mesh, const double* x, double* y, dg_apply_times* out,
+                           void* stream) {
+  return guarded([&] {
+    DG_REQUIRE(mesh && x && y && out, "null argument");
+    DG_REQUIRE(x != y, "x and y must not alias");
+    const cudaStream_t s = (cudaStream_t)stream;
+    EventSet E(3);
+    DG_CUDA(cudaEventRecord(E.ev[0], s));
+    launch_trace(*mesh, x, s);
+    DG_CUDA(cudaEventRecord(E.ev[1], s));
+    launch_apply(*mesh, x, y, Reduce{}, s, false);
+    DG_CUDA(cudaEventRecord(E.ev[2], s));
+    DG_CUDA(cudaEventSynchronize(E.ev[2]));
+    out->trace_ms = E.ms(0, 1);
+    out->apply_ms = E.ms(1, 2);
   });
 }
 
@@ -442,17 +549,15 @@ dg_status dg_pcg_solve_host(const dg_mesh* mesh, const dg_precond* pc, const dou
     DG_REQUIRE(pc->mesh == mesh, "preconditioner belongs to another mesh");
     const cudaStream_t s = (cudaStream_t)stream;
     PcgWork& w = pcg_work(pc);
-    double* b = w.hb;
-    double* x = w.hx;
-    DG_CUDA(cudaMemcpyAsync(b, b_host, mesh->n_dofs * sizeof(double), cudaMemcpyHostToDevice, s));
+    DG_CUDA(cudaMemcpyAsync(w.b, b_host, mesh->n_dofs * sizeof(double), cudaMemcpyHostToDevice, s));
     dg_status st = DG_OK;
     try {
-      pcg_run(mesh, pc, b, x, rtol, maxit, info, s);
+      pcg_run(mesh, pc, w.b, w.x, rtol, maxit, info, s);
     } catch (const Error& e) {
       if (e.code != DG_ENOTCONV) throw;
       st = DG_ENOTCONV;
     }
-    DG_CUDA(cudaMemcpyAsync(x_host, x, mesh->n_dofs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    DG_CUDA(cudaMemcpyAsync(x_host, w.x, mesh->n_dofs * sizeof(double), cudaMemcpyDeviceToHost, s));
     DG_CUDA(cudaStreamSynchronize(s));
     if (st != DG_OK) throw Error(st, "PCG reached maxit");
   });
@@ -492,19 +597,30 @@ constexpr int64_t kNoAllocDoubles =
 // 8.1 MiB per device that loads the library, held until the process exits.
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
-// Device address of g_noalloc_scratch per device, looked up once per device.
-static double* g_noalloc_ptr[64] = {nullptr};
+// Device address of g_noalloc_scratch per device, looked up once per device
+// (under a lock; the pointers are read without it once set).
+static std::atomic<double*> g_noalloc_ptr[64];
+static std::mutex g_noalloc_mu;
 
-static double* noalloc_scratch_for_current_device() {
+// The scratch of the mesh's device, which must be the current device: the
+// kernels run on the current device and the array's address is per device.
+static double* noalloc_scratch_for(const dg_mesh* mesh) {
   int dev = 0;
   DG_CUDA(cudaGetDevice(&dev));
+  DG_REQUIRE(dev == mesh->device, "dg_pcg_solve_noalloc: the current device is not the mesh's device");
   DG_REQUIRE(dev >= 0 && dev < 64, "device ordinal out of range");
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    DG_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_noalloc_ptr[dev] = (double*)p;
+  double* p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+  if (!p) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    p = g_noalloc_ptr[dev].load(std::memory_order_relaxed);
+    if (!p) {
+      void* a = nullptr;
+      DG_CUDA(cudaGetSymbolAddress(&a, g_noalloc_scratch));
+      p = (double*)a;
+      g_noalloc_ptr[dev].store(p, std::memory_order_release);
+    }
   }
-  return g_noalloc_ptr[dev];
+  return p;
 }
 
 }  // namespace dg
@@ -518,13 +634,15 @@ extern "C" dg_status dg_pcg_solve_noalloc(const dg_mesh* mesh, const dg_precond*
       throw Error(DG_EINVAL, "dg_pcg_solve_noalloc: n_dofs " + std::to_string(mesh->n_dofs) +
                                  " exceeds the static scratch limit of " +
                                  std::to_string(kNoAllocMaxDofs));
+    // implied by the DOF limit (a tile holds at least three elements' nodes, 243
+    // or more), kept as a guard of the partials' slice
     if (mesh->n_tiles > kNoAllocMaxTiles)
       throw Error(DG_EINVAL, "dg_pcg_solve_noalloc: mesh needs more operator tiles than the static scratch holds");
     DG_REQUIRE(pc && b && x, "null argument");
     DG_REQUIRE(pc->mesh == mesh, "preconditioner belongs to another mesh");
     DG_REQUIRE(rtol > 0.0 && maxit >= 1, "rtol must be > 0 and maxit >= 1");
     const cudaStream_t s = (cudaStream_t)stream;
-    double* base = noalloc_scratch_for_current_device();
+    double* base = noalloc_scratch_for(mesh);
     // carve the work vectors; every kernel below writes a slot before reading it
     PcgWork w;
     w.n = mesh->n_dofs;

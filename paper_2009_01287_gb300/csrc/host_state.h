@@ -12,12 +12,14 @@ namespace dg {
 // device allocation tracked by its owner
 struct DevArena {
   std::vector<void*> ptrs;
+  size_t bytes = 0;   // total requested
   template <typename T>
   T* alloc(size_t n) {
     void* p = nullptr;
     if (n == 0) n = 1;
     DG_CUDA(cudaMalloc(&p, n * sizeof(T)));
     ptrs.push_back(p);
+    bytes += n * sizeof(T);
     return (T*)p;
   }
   template <typename T>
@@ -29,6 +31,7 @@ struct DevArena {
   void release() {
     for (void* p : ptrs) cudaFree(p);
     ptrs.clear();
+    bytes = 0;
   }
 };
 
@@ -85,6 +88,7 @@ struct DevLevel {
   int32_t* end_row = nullptr;      // n_end+1 row offsets (level numbering)
   int64_t* end_inv_off = nullptr;  // offsets of the row-major inverses
   void* end_inv = nullptr;
+  int64_t end_inv_entries = 0;
   void* b = nullptr;     // right-hand side of this level
   void* xo = nullptr;    // the level's output (after post-smoothing)
 };
@@ -93,6 +97,7 @@ struct DevLevel {
 
 struct dg_mesh {
   dg::HostMesh host;
+  int device = 0;          // CUDA device current at dg_mesh_create (holds the handle's memory)
   dg_options opts{};
   double eta = 0.0;
   int64_t n_dofs = 0;
@@ -167,9 +172,10 @@ struct dg_precond {
   void* ec = nullptr;        // n_c LOR correction
   void* zE = nullptr;        // block-solve results, one per V_e node (block order)
   int64_t n_blocks = 0, max_block = 0, n_units = 0;
+  int64_t blk_inv_entries = 0, blk_slots = 0;   // sizes of blk_inv and blk_dofs
   cudaStream_t side = nullptr;   // the block solves run here, beside the V-cycle
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  // PCG workspace and captured iteration graph, built on the first solve
+  // PCG workspace and captured solve graph, built by dg_precond_setup
   void* pcg_cache = nullptr;
   void (*pcg_cache_free)(void*) = nullptr;
   ~dg_precond() {

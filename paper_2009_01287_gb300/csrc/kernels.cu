@@ -383,33 +383,43 @@ static void vcycle(const dg_precond& pc, size_t l, cudaStream_t s) {
 
 template <typename T>
 static void precond_impl(const dg_precond& pc, const double* r, double* z, Reduce red,
-                         cudaStream_t s) {
-  // fork: the block solves depend only on r
+                         cudaStream_t s, const PrecondMarks* mk) {
+  // fork: the block solves depend only on r (profiling: run them first, alone)
+  if (mk) DG_CUDA(cudaEventRecord(mk->ev[0], s));
   if (pc.n_blocks > 0) {
-    DG_CUDA(cudaEventRecord(pc.ev_fork, s));
-    DG_CUDA(cudaStreamWaitEvent(pc.side, pc.ev_fork, 0));
+    cudaStream_t bs = mk ? s : pc.side;
+    if (!mk) {
+      DG_CUDA(cudaEventRecord(pc.ev_fork, s));
+      DG_CUDA(cudaStreamWaitEvent(pc.side, pc.ev_fork, 0));
+    }
     // 8 warps per CTA; as many CTAs as the launch bounds keep resident on 152 SMs
     const int64_t gc = (pc.n_units + 7) / 8, gmax = (sizeof(T) == 8 ? 2 : 3) * 152;
     const int g = (int)(gc < gmax ? gc : gmax);
-    launch_k(block_solve_kernel<T>, g, 256, 0, pc.side, (const int4*)pc.blk_unit, pc.blk_ubase,
+    launch_k(block_solve_kernel<T>, g, 256, 0, bs, (const int4*)pc.blk_unit, pc.blk_ubase,
         (const int4*)pc.blk_rec, pc.blk_dofs, (const T*)pc.blk_inv, r, (T*)pc.zE, (int)pc.n_units);
     DG_CUDA(cudaGetLastError());
-    DG_CUDA(cudaEventRecord(pc.ev_join, pc.side));
+    if (!mk) DG_CUDA(cudaEventRecord(pc.ev_join, pc.side));
   }
+  if (mk) DG_CUDA(cudaEventRecord(mk->ev[1], s));
   const void* ec = nullptr;
   if (pc.n_c > 0) {
     if (pc.lor == DG_LOR_EXACT) {
       launch_rows<T>(pc.PT, OpRestrict<T>{r, (T*)pc.rc}, s);
+      if (mk) DG_CUDA(cudaEventRecord(mk->ev[2], s));
       launch_k(dense_mv_kernel<T>, grid_for(pc.n_c * 32), kVecThreads, 0, s, 
           (const T*)pc.lor_inv, (const T*)pc.rc, (T*)pc.ec, pc.n_c);
       ec = pc.ec;
     } else {
       launch_rows<T>(pc.PT, OpRestrict<T>{r, (T*)pc.levels[0].b}, s);
+      if (mk) DG_CUDA(cudaEventRecord(mk->ev[2], s));
       vcycle<T>(pc, 0, s);
       ec = pc.levels[0].xo;
     }
+  } else if (mk) {
+    DG_CUDA(cudaEventRecord(mk->ev[2], s));
   }
-  if (pc.n_blocks > 0) DG_CUDA(cudaStreamWaitEvent(s, pc.ev_join, 0));
+  if (mk) DG_CUDA(cudaEventRecord(mk->ev[3], s));
+  if (pc.n_blocks > 0 && !mk) DG_CUDA(cudaStreamWaitEvent(s, pc.ev_join, 0));
   const int nb = precond_final_blocks(pc);
 #define DG_FINAL(G)                                                                          \
   launch_k(precond_final_kernel<T, G>, nb, kVecThreads, 0, s,                                      \
@@ -420,6 +430,44 @@ static void precond_impl(const dg_precond& pc, const double* r, double* z, Reduc
   DG_FINAL(1);
 #undef DG_FINAL
   DG_CUDA(cudaGetLastError());
+  if (mk) DG_CUDA(cudaEventRecord(mk->ev[4], s));
+}
+
+// bytes of a CSR matrix read once: values, column indices, row pointers
+static double csr_bytes(const DevCsr& A, size_t tsz) {
+  return (double)A.nnz * (4.0 + (double)tsz) + 4.0 * (double)(A.rows + 1);
+}
+
+void precond_algorithmic_bytes(const dg_precond& pc, double* total, double* blocks) {
+  const double T = pc.precision == DG_PREC_MIXED ? 4.0 : 8.0;
+  const double n = (double)pc.n_dofs;
+  // block solves: the inverses, the block node lists, r gathered, results written, the units
+  double blk = 0.0;
+  if (pc.n_blocks > 0)
+    blk = (double)pc.blk_inv_entries * T + (double)pc.blk_slots * (4.0 + 8.0 + T) + 16.0 * (double)pc.n_units;
+  double tot = blk;
+  if (pc.n_c > 0) {
+    tot += csr_bytes(pc.PT, (size_t)T) + 8.0 * n + T * (double)pc.n_c;   // restriction
+    if (pc.lor == DG_LOR_EXACT) {
+      tot += T * (double)pc.n_c * (double)pc.n_c + 2.0 * T * (double)pc.n_c;
+    } else {
+      for (size_t l = 0; l < pc.levels.size(); ++l) {
+        const DevLevel& L = pc.levels[l];
+        const double nc = (double)L.n_cont, ncn = l + 1 < pc.levels.size() ? (double)pc.levels[l + 1].n : 0.0;
+        if (L.n_cont > 0 && L.plain)   // A twice, R, P; b, D^-1, two work vectors, the coarse vectors
+          tot += 2.0 * csr_bytes(L.A, (size_t)T) + csr_bytes(L.R, (size_t)T) + csr_bytes(L.P, (size_t)T) +
+                 T * (6.0 * nc + 2.0 * ncn);
+        else if (L.n_cont > 0)         // Rpre, Sb, Sp; b read twice, xo, the coarse vectors
+          tot += csr_bytes(L.Rpre, (size_t)T) + csr_bytes(L.Sb, (size_t)T) + csr_bytes(L.Sp, (size_t)T) +
+                 T * (3.0 * nc + 2.0 * ncn);
+        tot += T * (double)L.end_inv_entries + 2.0 * T * (double)(L.n - L.n_cont);   // dense coarse blocks
+      }
+    }
+  }
+  // final combination: P, e_C, D_J^-1, the slot of each node, block results, r, z
+  tot += csr_bytes(pc.P, (size_t)T) + T * (double)pc.n_c + n * (T + 4.0 + 8.0 + 8.0) + T * (double)pc.blk_slots;
+  *total = tot;
+  *blocks = blk;
 }
 
 int precond_kernel_count(const dg_precond& pc) {
@@ -435,9 +483,10 @@ int precond_kernel_count(const dg_precond& pc) {
   return k;
 }
 
-void launch_precond(const dg_precond& pc, const double* r, double* z, Reduce red, cudaStream_t s) {
-  if (pc.precision == DG_PREC_MIXED) precond_impl<float>(pc, r, z, red, s);
-  else precond_impl<double>(pc, r, z, red, s);
+void launch_precond(const dg_precond& pc, const double* r, double* z, Reduce red, cudaStream_t s,
+                    const PrecondMarks* marks) {
+  if (pc.precision == DG_PREC_MIXED) precond_impl<float>(pc, r, z, red, s, marks);
+  else precond_impl<double>(pc, r, z, red, s, marks);
 }
 
 // ============================================================== PCG
@@ -538,6 +587,8 @@ pcg_p_trace_kernel(const ApplyArgs A, double* __restrict__ p, const double* __re
       sc[SC_RR] = sc[SC_BB];
       sc[SC_IT] = 0.0;
       sc[SC_STATUS] = 0.0;
+      // a zero right-hand side needs no iteration (x = 0 is exact)
+      if (use_cond) cudaGraphSetConditional(h, sc[SC_BB] > 0.0 ? 1u : 0u);
     }
     return;
   }
@@ -553,9 +604,11 @@ pcg_p_trace_kernel(const ApplyArgs A, double* __restrict__ p, const double* __re
     sc[SC_IT] = it;
     sc[SC_RR] = rr;
     sc[SC_RZ] = sc[SC_RZNEW];
+    const double lim = maxit < 0 ? sc[SC_MAXIT] : (double)maxit;
+    const double tol2 = maxit < 0 ? sc[SC_RTOL2] : rtol2;
     int cont = 1;
-    if (rr <= rtol2 * sc[SC_BB]) { sc[SC_STATUS] = 1.0; cont = 0; }
-    else if (it >= (double)maxit) { sc[SC_STATUS] = 2.0; cont = 0; }
+    if (rr <= tol2 * sc[SC_BB]) { sc[SC_STATUS] = 1.0; cont = 0; }
+    else if (it >= lim) { sc[SC_STATUS] = 2.0; cont = 0; }
     *ticket = 0u;
     if (use_cond) cudaGraphSetConditional(h, cont ? 1u : 0u);
   }

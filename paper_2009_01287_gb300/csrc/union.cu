@@ -134,6 +134,8 @@ void upload_union_precond(dg_precond* pc, const std::vector<InstSrc>& inst, cuda
   pc->blk_rec = a.upload(brec, s);
   pc->blk_dofs = a.upload(dofs, s);
   pc->blk_inv = a.upload(inv, s);
+  pc->blk_inv_entries = (int64_t)inv.size();
+  pc->blk_slots = (int64_t)dofs.size();
   pc->zE = a.alloc<T>(dofs.size());
   pc->n_blocks = nb;
   pc->n_units = (int64_t)ubase.size();
@@ -203,6 +205,7 @@ void upload_union_precond(dg_precond* pc, const std::vector<InstSrc>& inst, cuda
     D.end_row = a.upload(end_row, s);
     D.end_inv_off = a.upload(end_off, s);
     D.end_inv = a.upload(end_inv, s);
+    D.end_inv_entries = (int64_t)end_inv.size();
     D.b = a.alloc<T>(D.n);
     D.xo = a.alloc<T>(D.n);
     pc->stats.level_rows[l] = D.n;

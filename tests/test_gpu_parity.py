@@ -253,3 +253,44 @@ def test_pcg_host_loop_matches_graph(built_lib, torch_mod, monkeypatch):
     ih = B.dg_pcg_solve(M.h, pc_h.h, b, xh, 1e-10, 2000)
     assert ih.iters == ig.iters
     assert torch_mod.equal(xg, xh)
+
+
+def test_one_graph_serves_any_buffers_and_tolerance(built_lib, torch_mod):
+    """The solve graph is captured once per preconditioner (at setup) on the
+    handle's own copies of b and x, with the limits in device memory: solves
+    with other buffers, tolerances and limits on the same handle match solves
+    on fresh handles."""
+    mesh = MESHES["hp-a"][0]()
+    B = built_lib
+    M = B.Mesh(mesh)
+    pc = B.Precond(M)
+    runs = [(12, 1e-6, 2000), (13, 1e-10, 2000), (12, 1e-10, 5)]
+    got = []
+    for seed, tol, maxit in runs:
+        b = dev(torch_mod, inputs.random_vector(M.n_dofs, seed))
+        x = torch_mod.full_like(b, 5.0)
+        info = B.dg_pcg_solve(M.h, pc.h, b, x, tol, maxit, raise_on_notconv=False)
+        got.append((info.iters, info.status, x.clone()))
+    for (seed, tol, maxit), (it, st, x) in zip(runs, got):
+        M2 = B.Mesh(mesh)
+        pc2 = B.Precond(M2)
+        b = dev(torch_mod, inputs.random_vector(M2.n_dofs, seed))
+        x2 = torch_mod.empty_like(b)
+        info = B.dg_pcg_solve(M2.h, pc2.h, b, x2, tol, maxit, raise_on_notconv=False)
+        assert (info.iters, info.status) == (it, st)
+        assert torch_mod.equal(x, x2)
+    assert got[2][1] == B.DG_ENOTCONV and got[2][0] == 5
+
+
+def test_dof_layout_and_device_bytes(built_lib, torch_mod):
+    mesh = MESHES["ragged"][0]()
+    B = built_lib
+    M = B.Mesh(mesh)
+    off = B.dg_dof_layout(M.h, mesh.n_elems)
+    want = np.concatenate([[0], np.cumsum((mesh.p.astype(np.int64) + 1) ** 2)])
+    assert np.array_equal(off, want)
+    pc = B.Precond(M)
+    # the handles' own counts of their device bytes: at least the vectors
+    # (x / traces for the mesh; six PCG work vectors for the preconditioner)
+    assert M.stats.device_bytes > 8 * M.n_dofs
+    assert pc.stats.device_bytes > 6 * 8 * M.n_dofs
