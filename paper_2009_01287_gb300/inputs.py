@@ -188,3 +188,21 @@ def small_hp_mesh(seed: int, base: int = 3, depth: int = 2, prob: float = 0.4,
                   pmin: int = 1, pmax: int = 4, dim: int = 2) -> MeshDesc:
     """Small irregular hp mesh for parity tests."""
     return random_refined_mesh(dim, base, depth, prob, pmin, pmax, seed)
+
+
+def serving_meshes(m: int, seed: int = 0, dof_lo: float = 5e3, dof_hi: float = 2e6) -> List[MeshDesc]:
+    """m distinct meshes for the served workload, alternately squares (prob
+    0.3, depth <= 3) and cubes (prob 0.2, depth <= 2), p ~ U{1..6}, DOF targets
+    log-uniform in [dof_lo, dof_hi]; the base grid is chosen from the expected
+    DOFs per base cell (about 99 for squares, 605 for cubes)."""
+    rng = np.random.Generator(np.random.PCG64(777 + seed))
+    out = []
+    for j in range(m):
+        target = math.exp(rng.uniform(math.log(dof_lo), math.log(dof_hi)))
+        if j % 2 == 1:
+            base = max(1, int(round((target / 605.0) ** (1.0 / 3.0))))
+            out.append(random_refined_mesh(3, base, 2, 0.2, 1, 6, seed=9000 + j))
+        else:
+            base = max(2, int(round(math.sqrt(target / 99.0))))
+            out.append(random_refined_mesh(2, base, 3, 0.3, 1, 6, seed=9000 + j))
+    return out
