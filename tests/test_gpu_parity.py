@@ -294,3 +294,36 @@ def test_dof_layout_and_device_bytes(built_lib, torch_mod):
     # (x / traces for the mesh; six PCG work vectors for the preconditioner)
     assert M.stats.device_bytes > 8 * M.n_dofs
     assert pc.stats.device_bytes > 6 * 8 * M.n_dofs
+
+
+@pytest.mark.parametrize("name,lor", [("hp-a", "amg"), ("cfg0", "exact")])
+def test_profile_entries_compute_the_same(built_lib, torch_mod, name, lor):
+    """dg_precond_profile (parts run one after another) and dg_apply_profile
+    (trace and operator kernels timed apart) give bit-identical results to
+    dg_precond_apply and dg_apply, and positive part times."""
+    mk, eta, pform = MESHES[name]
+    B = built_lib
+    o = _opts(B, "sipg", eta, pform, lor=B.DG_LOR_EXACT if lor == "exact" else B.DG_LOR_AMG,
+              precision=B.DG_PREC_MIXED)
+    M = B.Mesh(mk(), o)
+    pc = B.Precond(M, o)
+    r = dev(torch_mod, inputs.random_vector(M.n_dofs, 31))
+    z1, z2 = torch_mod.empty_like(r), torch_mod.empty_like(r)
+    B.dg_precond_apply(pc.h, r, z1)
+    t = B.dg_precond_profile(pc.h, r, z2)
+    torch_mod.cuda.synchronize()
+    assert torch_mod.equal(z1, z2)
+    assert t.total_ms > 0 and t.final_ms > 0 and t.lor_ms > 0
+    assert pc.stats.apply_bytes > pc.stats.block_bytes >= 0
+    y1, y2 = torch_mod.empty_like(r), torch_mod.empty_like(r)
+    B.dg_apply(M.h, r, y1)
+    ta = B.dg_apply_profile(M.h, r, y2)
+    torch_mod.cuda.synchronize()
+    assert torch_mod.equal(y1, y2)
+    assert ta.trace_ms > 0 and ta.apply_ms > 0
+
+
+def test_fp64_probe_is_plausible(built_lib, torch_mod):
+    tf, ms = built_lib.dg_fp64_fma_probe(20000)
+    # GB300: about 1.2-1.3 TFLOP/s of FP64 FMA at full clock
+    assert 0.3 < tf < 3.0 and ms > 0
