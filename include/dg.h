@@ -57,9 +57,10 @@ typedef struct dg_precond dg_precond;
  * [0, extent_0*lattice_h] x ... .  The boxes must tile the domain exactly.
  * coeff: NULL (a = 1) or n_elems values a_kappa > 0 of the piecewise-constant
  * coefficient of -div(a grad u) = f (Section 4.3, random refinement): a_kappa
- * weights element kappa's volume term, its share of the face averages
- * {a grad u} and its BR2 lifting energy; the SIPG penalty of a sub-face takes
- * the larger a of its two sides; the LOR blocks are weighted by a_kappa.
+ * weights element kappa's volume term and its share of the face averages
+ * {a grad u}; the SIPG penalty of a sub-face and both sides' BR2 lifting
+ * energies take the larger a of its two sides; the LOR blocks are weighted by
+ * a_kappa.
  * A value that is not positive and finite is DG_EINVAL.  All pointers are
  * HOST pointers, read during the call. */
 typedef struct {

@@ -21,7 +21,9 @@ p_e = max, h_e = min over the two sides ("paper" form), or
 sigma = eta (p_e + 1)^2 / h_e ("p1sq" form of the 8x8 p=2 workload).
 BR2 stabilisation: sum_e int eta r_e([[u]]) . r_e([[v]]), with the lifting
 int r_e(phi).tau = -int_e phi.{tau} solved with each adjacent element's exact
-mass matrix; on a boundary sub-face {tau} = tau.
+mass matrix; on a boundary sub-face {tau} = tau.  With a coefficient a, both
+sides' lifting energies of a sub-face carry the larger a of its two sides
+(like the SIPG penalty).
 On the boundary (homogeneous Dirichlet): [[u]] = u n, {grad u} = grad u.
 """
 from __future__ import annotations
@@ -167,7 +169,7 @@ def assemble(space: DGSpace, eta: float, form: str = "sipg",
     broken_only: the broken Laplacian A-hat of Section 3.4 (volume terms only).
     With a coefficient a: a_k on the volume term of element k, the face
     averages of a grad u, the SIPG penalty times the larger a of the two sides,
-    and each side's BR2 lifting energy times that side's a."""
+    and both sides' BR2 lifting energies times that same larger a."""
     topo = space.topo
     rows, cols, vals = [], [], []
 
@@ -207,11 +209,12 @@ def assemble(space: DGSpace, eta: float, form: str = "sipg",
                 F = F + penalty(space, f, eta, penalty_form) * ((J.T * W) @ J)
             elif form == "br2":
                 coef = 0.25 if interior else 1.0
+                ae = max(space.coef[k] for k in sides)     # the larger a of the sub-face
                 for si, k in enumerate(sides):
                     v, _ = space.eval(k, pts)
                     b = (v.T * W) @ J                       # b[i, a] = int_e phi_i^k j_a
                     Minv = np.linalg.inv(space.mass(k))
-                    F = F + eta * coef * space.coef[k] * (b.T @ Minv @ b)
+                    F = F + eta * coef * ae * (b.T @ Minv @ b)
             else:
                 raise ValueError(form)
             add(I, I, F)
@@ -259,10 +262,11 @@ def element_rows(space: DGSpace, k: int, x: np.ndarray, eta: float, form: str = 
             F = F + penalty(space, f, eta, penalty_form) * ((Jm.T * FW) @ Jm)
         else:
             coef = 0.25 if interior else 1.0
+            ae = max(space.coef[e] for e in sides)
             for e in sides:
                 v, _ = space.eval(e, fpts)
                 b = (v.T * FW) @ Jm
-                F = F + eta * coef * space.coef[e] * (b.T @ np.linalg.inv(space.mass(e)) @ b)
+                F = F + eta * coef * ae * (b.T @ np.linalg.inv(space.mass(e)) @ b)
         nk = (p + 1) ** space.dim
         rows = slice(0, nk) if f.km == k else slice(len(I[0]), len(I[0]) + nk)
         y = y + F[rows] @ x[Im]

@@ -25,7 +25,8 @@
 //            For BR2 the sigma term becomes
 //              eta/4 [M_oo G_o (a - b) + M_on G_n (M_no u- - M_nn u+)]
 //            (eta [M_oo G_o a] on the boundary), G = edge block of the
-//            element mass inverse = h^-2 Minv_00 Minv.
+//            element mass inverse = h^-2 Minv_00 Minv, times the larger
+//            coefficient a of the sub-face's two sides.
 // Every sub-face is evaluated from both of its sides (no atomics): applies are
 // bit-reproducible.
 #pragma once
@@ -388,7 +389,10 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& 
 #pragma unroll
         for (int m = 0; m < NP; ++m) g = fma(__ldg(Mi + i * NP + m), sjo[t - i + m], g);
         const double ih = A.ih[k];
-        sgo[t] = A.ak[k] * (g * __ldg(Mi) * ih * ih);   // each side's lifting carries its a
+        const int nb = A.sf[b0 + j].nb;
+        // both sides' liftings carry the larger a of the sub-face
+        const double w = nb < 0 ? A.ak[k] : fmax(A.ak[k], A.ak[nb]);
+        sgo[t] = w * (g * __ldg(Mi) * ih * ih);
       }
       for (int t = tid; t < nnb; t += blockDim.x) {
         const int e = t / (4 * kMaxN), s = (t / kMaxN) & 3, m = t % kMaxN;
@@ -402,7 +406,8 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& 
         double g = 0.0;
         for (int q = 0; q < np; ++q) g = fma(__ldg(Mi + m * np + q), sjn[(e * 4 + s) * kMaxN + q], g);
         const double ihn = A.ih[f.nb];
-        sgn[(e * 4 + s) * kMaxN + m] = A.ak[f.nb] * (g * __ldg(Mi) * ihn * ihn);
+        const double w = fmax(A.ak[k], A.ak[f.nb]);
+        sgn[(e * 4 + s) * kMaxN + m] = w * (g * __ldg(Mi) * ihn * ihn);
       }
       __syncthreads();
       // stage C: stabilisation residual

@@ -89,7 +89,8 @@ struct SubFaceRec3 {
   int32_t tab_z[2], tab_v[2], tab_x[2], tab_y[2];
   double sigma;      // SIPG penalty
   double area;       // physical area of the sub-face
-  double cz, cx;     // BR2: eta coef area^2 Minv_00 / h^3 of the own / neighbour element
+  double cz, cx;     // BR2: a eta coef area^2 Minv_00 / h^3 of the own / neighbour element,
+                     // a the larger coefficient of the sub-face's two sides
 };
 
 // Shared-memory budget (doubles) of one 3D operator tile; the host sizes the

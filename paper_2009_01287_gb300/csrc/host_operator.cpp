@@ -2,6 +2,7 @@
 // formulation as the device kernel).  Used at setup to read the diagonal of A
 // on V_J and the dense blocks A_e = R_e A R_e^T of the V_e (Section 4.1, items
 // 2: "assembly of the diagonal ... and of the diagonal blocks").
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -98,18 +99,20 @@ void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double*
           jn[q] = v * f.len;
         }
         double go[kMaxN], gn[kMaxN] = {0.0};
+        // both sides' liftings carry the larger a of the sub-face
+        const double w = f.nb < 0 ? ak : std::max(ak, m.coef[f.nb]);
         for (int i = 0; i < NP; ++i) {
           double g = 0.0;
           for (int q = 0; q < NP; ++q) g += B.Minv[i * NP + q] * jo[q];
-          go[i] = ak * (g * B.Minv[0] / (hk * hk));   // each side's lifting carries its a
+          go[i] = w * (g * B.Minv[0] / (hk * hk));
         }
         if (np) {
           const Basis1D& Bn = basis1d(f.pn);
-          const double hn = M.h_h[f.nb], an = m.coef[f.nb];
+          const double hn = M.h_h[f.nb];
           for (int q = 0; q < np; ++q) {
             double g = 0.0;
             for (int t = 0; t < np; ++t) g += Bn.Minv[q * np + t] * jn[t];
-            gn[q] = an * (g * Bn.Minv[0] / (hn * hn));
+            gn[q] = w * (g * Bn.Minv[0] / (hn * hn));
           }
         }
         const double coef = (f.nb < 0) ? 1.0 : 0.25;
@@ -167,23 +170,24 @@ void host_element_diag(const dg_mesh& M, int64_t k, double* d) {
           continue;
         }
         add -= (interior ? 1.0 : 2.0) * f.len * moo * dv;
+        const double w = interior ? std::max(ak, m.coef[f.nb]) : ak;   // larger a of the sub-face
         for (int q = 0; q < NP; ++q) jo[q] = f.len * T[f.tab_oo + q * NP + i];
         for (int a = 0; a < NP; ++a) {
           double g = 0.0;
           for (int q = 0; q < NP; ++q) g += B.Minv[a * NP + q] * jo[q];
-          go[a] = ak * (g * B.Minv[0] / (hk * hk));
+          go[a] = w * (g * B.Minv[0] / (hk * hk));
         }
         double st = 0.0;
         for (int a = 0; a < NP; ++a) st += T[f.tab_oo + i * NP + a] * go[a];
         if (interior) {
           const int np = f.pn + 1;
           const Basis1D& Bn = basis1d(f.pn);
-          const double hn = M.h_h[f.nb], an = m.coef[f.nb];
+          const double hn = M.h_h[f.nb];
           for (int q = 0; q < np; ++q) jn[q] = f.len * T[f.tab_on + i * np + q];
           for (int a = 0; a < np; ++a) {
             double g = 0.0;
             for (int q = 0; q < np; ++q) g += Bn.Minv[a * np + q] * jn[q];
-            gn[a] = an * (g * Bn.Minv[0] / (hn * hn));
+            gn[a] = w * (g * Bn.Minv[0] / (hn * hn));
           }
           for (int a = 0; a < np; ++a) st += T[f.tab_on + i * np + a] * gn[a];
         }

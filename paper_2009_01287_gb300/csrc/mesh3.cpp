@@ -309,8 +309,9 @@ void build_mesh_host3(dg_mesh* M, const dg_mesh_desc* desc, const dg_options& o)
         const bool in = r.nb >= 0;
         const double coef = in ? 0.25 : 1.0;
         const double hk = M->h_h[k];
-        // each side's lifting energy carries that side's coefficient
-        r.cz = m.coef[k] * (M->eta * coef * r.area * r.area * basis1d(P).Minv[0] / (hk * hk * hk));
+        // both sides' lifting energies carry the larger coefficient of the sub-face
+        const double w = in ? std::max(m.coef[k], m.coef[r.nb]) : m.coef[k];
+        r.cz = w * (M->eta * coef * r.area * r.area * basis1d(P).Minv[0] / (hk * hk * hk));
         for (int d = 0; d < 2; ++d) {
           r.tab_z[d] = product(0, P, P, r.tab_oo[d], r.tab_oo[d], r.tab_oo[d]);
           if (in) {
@@ -323,7 +324,7 @@ void build_mesh_host3(dg_mesh* M, const dg_mesh_desc* desc, const dg_options& o)
         }
         if (in) {
           const double hn = M->h_h[r.nb];
-          r.cx = m.coef[r.nb] * (M->eta * coef * r.area * r.area * basis1d(r.pn).Minv[0] / (hn * hn * hn));
+          r.cx = w * (M->eta * coef * r.area * r.area * basis1d(r.pn).Minv[0] / (hn * hn * hn));
         }
       }
   const int base = (int)M->h_tables.size();
@@ -514,9 +515,10 @@ void host_element_residual3(const dg_mesh& M, int64_t k, const double* x, double
           st2.assign(N2, 0.0);
         }
         const double coef = interior ? 0.25 : 1.0;
-        const double an = interior ? m.coef[f.nb] : 0.0;
+        // both sides' lifting energies carry the larger a of the sub-face
+        const double w = interior ? std::max(m.coef[k], m.coef[f.nb]) : m.coef[k];
         for (int q = 0; q < N2; ++q)
-          r[s * N2 + q] += M.eta * coef * ar * (m.coef[k] * st1[q] + an * st2[q]);
+          r[s * N2 + q] += M.eta * coef * ar * w * (st1[q] + st2[q]);
       }
     }
   }

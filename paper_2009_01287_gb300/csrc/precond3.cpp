@@ -495,14 +495,16 @@ void host_element_diag3(const dg_mesh& M, int64_t k, double* d) {
             continue;
           }
           add -= (interior ? 1.0 : 2.0) * f.area * moo * dv;
-          const double so = ak * (B.Minv[0] / (hk * hk * hk));   // each side's lifting carries its a
+          // both sides' liftings carry the larger a of the sub-face
+          const double w = interior ? std::max(ak, m.coef[f.nb]) : ak;
+          const double so = w * (B.Minv[0] / (hk * hk * hk));
           double st = so * f.area * qform(T + f.tab_oo[0] + i, NP, NP, B.Minv) *
                       qform(T + f.tab_oo[1] + j, NP, NP, B.Minv);
           if (interior) {
             const int nn = f.pn + 1;
             const Basis1D& Bn = basis1d(f.pn);
             const double hn = M.h_h[f.nb];
-            const double sn = m.coef[f.nb] * (Bn.Minv[0] / (hn * hn * hn));
+            const double sn = w * (Bn.Minv[0] / (hn * hn * hn));
             st += sn * f.area * qform(T + f.tab_on[0] + i * nn, 1, nn, Bn.Minv) *
                   qform(T + f.tab_on[1] + j * nn, 1, nn, Bn.Minv);
           }

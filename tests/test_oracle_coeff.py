@@ -110,13 +110,14 @@ def test_sipg_penalty_closed_form_with_coefficient():
 
 def test_br2_penalty_closed_form_with_coefficient():
     """Same jump with BR2: each side's lifting energy (p+1)^2 (1/4 on the
-    interior face, 1 on the boundary) carries that side's a."""
+    interior face, 1 on the boundary) carries the larger a of the sub-face's
+    two sides (the boundary faces: the element's own a)."""
     for (pl, pr), (al, ar) in [((1, 1), (1.0, 20.0)), ((2, 3), (20.0, 1.0)), ((5, 2), (3.0, 0.5))]:
         mesh = _mesh([(0, 0), (1, 0)], [1, 1], [pl, pr], (2, 1), 0.25, [al, ar])
         prob = solver.build_problem(mesh, form="br2", eta=3.0)
         u = np.zeros(prob.space.n)
         u[:(pl + 1) ** 2] = 1.0
-        expect = 3.0 * (0.25 * (al * (pl + 1) ** 2 + ar * (pr + 1) ** 2) + 3 * al * (pl + 1) ** 2)
+        expect = 3.0 * (0.25 * max(al, ar) * ((pl + 1) ** 2 + (pr + 1) ** 2) + 3 * al * (pl + 1) ** 2)
         assert abs(u @ prob.A @ u - expect) < 1e-11 * expect
 
 
@@ -149,15 +150,17 @@ def test_lor_equivalence_is_independent_of_the_contrast():
     assert lo20 > 0.5 * lo1 and hi20 < 2.0 * hi1
 
 
-def test_sipg_condition_number_robust_in_the_contrast():
+@pytest.mark.parametrize("form", ["sipg", "br2"])
+def test_condition_number_robust_in_the_contrast(form):
     """kappa(BA) with the exact LOR solve on a small hp mesh stays within a
-    factor 1.5 of its a = 1 value for contrasts 20 and 1000 (SIPG, penalty with
-    the larger a of the two sides)."""
+    factor 1.5 of its a = 1 value for contrasts 20 and 1000 (SIPG penalty and
+    BR2 lifting energies both with the larger a of the two sides; BR2 with
+    each side's own a grows from 25 to about 1560 at contrast 1000)."""
     mesh = inputs.small_hp_mesh(2, base=4, depth=2, prob=0.4, pmin=1, pmax=4)
     kap = []
     for c in (1.0, 20.0, 1000.0):
         m = inputs.with_coeff(mesh, inputs.base_parity_coeff(mesh, 4, (1.0, c)))
-        prob = solver.build_problem(m, form="sipg")
+        prob = solver.build_problem(m, form=form)
         B = solver.Preconditioner(prob, lor="exact").matrix()
         ev = np.real(np.linalg.eigvals(B @ prob.A.toarray()))
         kap.append(ev.max() / ev.min())
@@ -191,12 +194,12 @@ def test_sipg_penalty_closed_form_hanging_cubes_with_coefficient():
 def test_br2_penalty_closed_form_cubes_with_coefficient():
     """Conforming 2x1x1 cubes, u = 1 on the left one: each side's lifting energy
     (p+1)^2 h (1/4 per side on the interior face, all of it on the five
-    boundary faces) carries that side's a."""
+    boundary faces) carries the larger a of the sub-face."""
     h, eta = 0.5, 2.0
     for (pl, pr), (al, ar) in [((1, 1), (1.0, 20.0)), ((2, 3), (20.0, 1.0)), ((3, 1), (0.5, 4.0))]:
         mesh = _mesh([(0, 0, 0), (1, 0, 0)], [1, 1], [pl, pr], (2, 1, 1), h, [al, ar])
         _, space, A = solver.build_operator(mesh, form="br2", eta=eta)
         u = np.zeros(space.n)
         u[:(pl + 1) ** 3] = 1.0
-        expect = eta * (0.25 * (al * (pl + 1) ** 2 * h + ar * (pr + 1) ** 2 * h) + 5 * al * (pl + 1) ** 2 * h)
+        expect = eta * (0.25 * max(al, ar) * ((pl + 1) ** 2 * h + (pr + 1) ** 2 * h) + 5 * al * (pl + 1) ** 2 * h)
         assert abs(u @ A @ u - expect) < 1e-11 * expect
