@@ -92,6 +92,12 @@ typedef struct {
   int smoother;      /* DG_SMOOTHER_*                                       */
   int remark_cases;  /* 1: add the further V_J cases of the remark in
                         Section 3.2 (coarse degree <= every fine degree)    */
+  int tune_tiles;    /* 1: dg_mesh_create / dg_batch_create time the
+                        operator kernel over candidate tile shapes and keep
+                        the fastest (squares: elements per tile of each
+                        degree; cubes: the tile's shared-memory budget);
+                        the choice is in dg_mesh_stats.  No counterpart in
+                        the paper (a launch-shape choice).                  */
 } dg_options;
 
 typedef struct {
@@ -135,6 +141,15 @@ typedef struct {
   double apply_bytes;     /* algorithmic bytes of one dg_apply: x read, y write,
                              per-element and per-sub-face records read once     */
   int64_t device_bytes;   /* device memory held by the mesh handle              */
+  int32_t tile_elems[9];  /* squares: elements per operator tile of degree p
+                             (index p), fixed rule min(16, 256/(p+1)^2) unless
+                             tuned                                               */
+  int64_t tile_smem_budget; /* cubes: shared-memory budget of an operator tile
+                               (bytes)                                           */
+  int32_t tiles_tuned;    /* 1: chosen by timing (dg_options.tune_tiles)        */
+  double apply_ms_fixed;  /* when tuned: the operator kernel's time with the
+                             fixed rule ...                                      */
+  double apply_ms_tuned;  /* ... and with the chosen tiles (CUDA events, warm)  */
 } dg_mesh_stats;
 
 /* Build the mesh topology (sub-faces, hanging vertices, master edges) and
@@ -267,6 +282,9 @@ void dg_batch_destroy(dg_batch* batch);
 int64_t dg_batch_num_dofs(const dg_batch* batch);
 /* offsets: n_problems*n_rhs + 1 entries (host). */
 dg_status dg_batch_offsets(const dg_batch* batch, int64_t* offsets);
+/* Statistics of the batch's concatenated operator (all instances), with its
+ * tile shapes (tuned when opts->tune_tiles was set at creation). */
+dg_status dg_batch_stats_get(const dg_batch* batch, dg_mesh_stats* out);
 /* Sine right-hand sides for every instance (as dg_rhs_sine): amps holds
  * n_modes values per instance, waves 2*n_modes per instance; b: device. */
 dg_status dg_batch_rhs_sine(const dg_batch* batch, int n_modes, const double* amps,

@@ -32,7 +32,7 @@ ABI_SYMBOLS = (
     "dg_precond_destroy", "dg_precond_stats_get", "dg_precond_apply", "dg_pcg_solve",
     "dg_pcg_solve_host", "dg_pcg_solve_noalloc", "dg_rhs_sine", "dg_last_error",
     "dg_batch_create", "dg_batch_destroy", "dg_batch_num_dofs", "dg_batch_offsets", "dg_batch_rhs_sine",
-    "dg_batch_solve", "dg_precond_profile", "dg_apply_profile", "dg_fp64_fma_probe",
+    "dg_batch_solve", "dg_batch_stats_get", "dg_precond_profile", "dg_apply_profile", "dg_fp64_fma_probe",
 )
 
 
@@ -46,7 +46,7 @@ class DgMeshDesc(C.Structure):
 class DgOptions(C.Structure):
     _fields_ = [("form", C.c_int), ("eta", C.c_double), ("penalty_form", C.c_int),
                 ("precision", C.c_int), ("lor", C.c_int), ("smoother", C.c_int),
-                ("remark_cases", C.c_int)]
+                ("remark_cases", C.c_int), ("tune_tiles", C.c_int)]
 
 
 class DgSolveInfo(C.Structure):
@@ -57,7 +57,8 @@ class DgSolveInfo(C.Structure):
 class DgMeshStats(C.Structure):
     _fields_ = [("n_elems", C.c_int64), ("n_dofs", C.c_int64), ("n_subfaces", C.c_int64),
                 ("max_level_gap", C.c_int64), ("apply_flops", C.c_double), ("apply_bytes", C.c_double),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("tile_elems", C.c_int32 * 9), ("tile_smem_budget", C.c_int64),
+                ("tiles_tuned", C.c_int32), ("apply_ms_fixed", C.c_double), ("apply_ms_tuned", C.c_double)]
 
 
 class DgPrecondStats(C.Structure):
@@ -119,6 +120,7 @@ def lib():
         L.dg_batch_num_dofs.argtypes = [vp]
         L.dg_batch_num_dofs.restype = i64
         L.dg_batch_offsets.argtypes = [vp, vp]
+        L.dg_batch_stats_get.argtypes = [vp, C.POINTER(DgMeshStats)]
         L.dg_batch_rhs_sine.argtypes = [vp, C.c_int, dp, dp, dp, vp]
         L.dg_batch_solve.argtypes = [vp, dp, dp, C.c_double, C.c_int, C.POINTER(DgSolveInfo),
                                      C.POINTER(C.c_double), vp]
@@ -176,8 +178,8 @@ def make_desc(mesh: MeshDesc):
 
 
 def make_options(form=DG_FORM_SIPG, eta=0.0, penalty_form=DG_PENALTY_PAPER, precision=DG_PREC_FP64,
-                 lor=DG_LOR_AMG, smoother=DG_SMOOTHER_FULL, remark_cases=0) -> DgOptions:
-    return DgOptions(form, eta, penalty_form, precision, lor, smoother, remark_cases)
+                 lor=DG_LOR_AMG, smoother=DG_SMOOTHER_FULL, remark_cases=0, tune_tiles=0) -> DgOptions:
+    return DgOptions(form, eta, penalty_form, precision, lor, smoother, remark_cases, tune_tiles)
 
 
 # ------------------------------------------------------------ C-named calls
@@ -351,6 +353,8 @@ class Batch:
         off = np.zeros(self.n_inst + 1, dtype=np.int64)
         _check(lib().dg_batch_offsets(self.h, off.ctypes.data))
         self.offsets = off
+        self.stats = DgMeshStats()
+        _check(lib().dg_batch_stats_get(self.h, C.byref(self.stats)))
 
     def rhs_sine(self, rhs_list, b, stream=None):
         """rhs_list: one SineRHS per instance (same number of modes)."""

@@ -244,4 +244,98 @@ void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cuda
   DG_CUDA(cudaGetLastError());
 }
 
+// ============================================================== tile tuner
+// mean time of the operator kernel alone (side traces in place), CUDA events
+static double time_apply_ms(const dg_mesh& M, const double* x, double* y, cudaStream_t s) {
+  constexpr int kWarm = 3, kReps = 20;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double ms = 0.0;
+  try {
+    DG_CUDA(cudaEventCreate(&e0));
+    DG_CUDA(cudaEventCreate(&e1));
+    for (int i = 0; i < kWarm; ++i) launch_apply(M, x, y, Reduce{}, s, false);
+    DG_CUDA(cudaEventRecord(e0, s));
+    for (int i = 0; i < kReps; ++i) launch_apply(M, x, y, Reduce{}, s, false);
+    DG_CUDA(cudaEventRecord(e1, s));
+    DG_CUDA(cudaEventSynchronize(e1));
+    float t = 0.0f;
+    DG_CUDA(cudaEventElapsedTime(&t, e0, e1));
+    ms = t / kReps;
+  } catch (...) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms;
+}
+
+void tune_tiles(dg_mesh* M, cudaStream_t s, void (*retile)(dg_mesh*, void*), void* ctx) {
+  if (M->n_tiles == 0) return;
+  DevArena scratch;
+  try {
+    const int64_t n = M->n_dofs;
+    double* x = scratch.alloc<double>(n);
+    double* y = scratch.alloc<double>(n);
+    // x = 1 everywhere: the kernel's work and timing do not depend on the values
+    std::vector<double> ones(n, 1.0);
+    DG_CUDA(cudaMemcpyAsync(x, ones.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+    auto measure = [&]() {
+      retile(M, ctx);
+      upload_tiles(M, s);
+      launch_trace(*M, x, s);
+      return time_apply_ms(*M, x, y, s);
+    };
+    const double fixed_ms = measure();
+    double best_ms = fixed_ms;
+    if (M->host.dim == 3) {
+      // shared-memory budget of a tile: 4, 3 (the fixed rule) or 2 tiles per SM
+      const int64_t fixed_budget = M->apply3_budget, budgets[3] = {6656, 9216, 13312};
+      int64_t best = fixed_budget;
+      for (int64_t b : budgets) {
+        if (b == fixed_budget) continue;
+        M->apply3_budget = b;
+        const double t = measure();
+        if (t < 0.99 * best_ms) {
+          best_ms = t;
+          best = b;
+        }
+      }
+      M->apply3_budget = best;
+    } else {
+      bool present[kMaxP + 1] = {false};
+      for (const ApplyTile& T : M->h_tiles) present[T.p] = true;
+      // highest degrees first: their tiles set the length of the launch
+      for (int P = kMaxP; P >= 1; --P) {
+        if (!present[P]) continue;
+        const int cap = apply_epb(P), start = M->tile_epb[P];
+        const int cand[3] = {cap, std::max(1, (3 * cap + 3) / 4), std::max(1, cap / 2)};
+        int best = start;
+        for (int c : cand) {
+          if (c == start) continue;
+          M->tile_epb[P] = c;
+          const double t = measure();
+          if (t < 0.99 * best_ms) {
+            best_ms = t;
+            best = c;
+          }
+        }
+        M->tile_epb[P] = best;
+      }
+    }
+    retile(M, ctx);
+    upload_tiles(M, s);
+    M->stats.tiles_tuned = 1;
+    M->stats.apply_ms_fixed = fixed_ms;
+    M->stats.apply_ms_tuned = best_ms;
+  } catch (...) {
+    scratch.release();
+    throw;
+  }
+  scratch.release();
+  for (int p = 0; p <= kMaxP; ++p) M->stats.tile_elems[p] = M->host.dim == 2 ? M->tile_epb[p] : 0;
+  M->stats.tile_smem_budget = M->host.dim == 3 ? 8 * M->apply3_budget : 0;
+}
+
 }  // namespace dg

@@ -231,6 +231,37 @@ struct dg_batch {
 
 namespace dg {
 
+// operator tiles of the union: per instance, degree-sorted runs of at most
+// U.tile_epb[p] elements; tiles never span two instances, so a converged
+// instance's tiles can be skipped
+static void build_batch_tiles(dg_batch* B) {
+  dg_mesh& U = B->U;
+  const HostMesh& um = U.host;
+  std::vector<int32_t> order;
+  U.h_tiles.clear();
+  int64_t e0 = 0;
+  for (int i = 0; i < B->n_inst; ++i) {
+    const int64_t ne = B->meshes[i / B->n_rhs]->host.n;
+    std::vector<int32_t> loc(ne);
+    for (int64_t e = 0; e < ne; ++e) loc[e] = (int32_t)(e0 + e);
+    std::stable_sort(loc.begin(), loc.end(), [&](int32_t a, int32_t b) { return um.p[a] > um.p[b]; });
+    for (int64_t j = 0; j < ne;) {
+      const int P = um.p[loc[j]];
+      int64_t l = j;
+      while (l < ne && um.p[loc[l]] == P && l - j < U.tile_epb[P]) ++l;
+      U.h_tiles.push_back({P, (int32_t)(order.size() + j), (int32_t)(l - j), i});
+      j = l;
+    }
+    order.insert(order.end(), loc.begin(), loc.end());
+    e0 += ne;
+  }
+  U.h_order = order;
+  U.n_tiles = (int)U.h_tiles.size();
+  build_face_items(&U);
+}
+
+static void retile_batch(dg_mesh*, void* ctx) { build_batch_tiles((dg_batch*)ctx); }
+
 // union of the instances' operator data (host side), then upload
 static void build_union_mesh(dg_batch* B, cudaStream_t s) {
   dg_mesh& U = B->U;
@@ -282,28 +313,7 @@ static void build_union_mesh(dg_batch* B, cudaStream_t s) {
   U.n_dofs = um.off.back();
   U.stats.n_dofs = U.n_dofs;
   DG_REQUIRE(U.n_dofs < (1LL << 31) && um.n < (1LL << 31), "batch too large for 32-bit indices");
-  // tiles never span two instances, so a converged instance's tiles can be skipped
-  std::vector<int32_t> order;
-  U.h_tiles.clear();
-  int64_t e0 = 0;
-  for (int i = 0; i < B->n_inst; ++i) {
-    const int64_t ne = B->meshes[i / B->n_rhs]->host.n;
-    std::vector<int32_t> loc(ne);
-    for (int64_t e = 0; e < ne; ++e) loc[e] = (int32_t)(e0 + e);
-    std::stable_sort(loc.begin(), loc.end(), [&](int32_t a, int32_t b) { return um.p[a] > um.p[b]; });
-    for (int64_t j = 0; j < ne;) {
-      const int P = um.p[loc[j]];
-      int64_t l = j;
-      while (l < ne && um.p[loc[l]] == P && l - j < apply_epb(P)) ++l;
-      U.h_tiles.push_back({P, (int32_t)(order.size() + j), (int32_t)(l - j), i});
-      j = l;
-    }
-    order.insert(order.end(), loc.begin(), loc.end());
-    e0 += ne;
-  }
-  U.h_order = order;
-  U.n_tiles = (int)U.h_tiles.size();
-  build_face_items(&U);
+  build_batch_tiles(B);
   upload_mesh(&U, s);
 }
 
@@ -466,6 +476,7 @@ dg_status dg_batch_create(const dg_mesh_desc* descs, int n_problems, int n_rhs,
     for (int i = 0; i < B->n_inst; ++i)
       B->inst_off.push_back(B->inst_off.back() + B->meshes[i / n_rhs]->n_dofs);
     build_union_mesh(B.get(), s);
+    if (o.tune_tiles) tune_tiles(&B->U, s, retile_batch, B.get());
     // union preconditioner
     B->UP.mesh = &B->U;
     B->UP.precision = o.precision;
@@ -499,6 +510,15 @@ int64_t dg_batch_num_dofs(const dg_batch* b) { return b ? b->U.n_dofs : -1; }
 dg_status dg_batch_offsets(const dg_batch* b, int64_t* offsets) {
   if (!b || !offsets) { set_last_error("null argument"); return DG_EINVAL; }
   std::copy(b->inst_off.begin(), b->inst_off.end(), offsets);
+  return DG_OK;
+}
+
+dg_status dg_batch_stats_get(const dg_batch* b, dg_mesh_stats* out) {
+  if (!b || !out) { set_last_error("null argument"); return DG_EINVAL; }
+  *out = b->U.stats;
+  out->device_bytes = (int64_t)(b->U.arena.bytes + b->U.tile_arena.bytes);
+  if (!out->tiles_tuned)
+    for (int p = 0; p <= kMaxP; ++p) out->tile_elems[p] = b->U.tile_epb[p];
   return DG_OK;
 }
 

@@ -43,10 +43,21 @@ static void build_mesh(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* o
   upload_mesh(M, s);
 }
 
-void upload_mesh(dg_mesh* M, cudaStream_t s) {
-  const HostMesh& m = M->host;
+void upload_tiles(dg_mesh* M, cudaStream_t s) {
+  M->tile_arena.release();
+  DevArena& a = M->tile_arena;
   M->apply_smem = apply_smem_for(*M);
   M->apply_grid = apply_kernel_setup(*M);
+  M->d_order = a.upload(M->h_order, s);
+  M->d_tiles = a.upload(M->h_tiles, s);
+  M->d_items = a.upload(M->h_items, s);
+  M->d_item_ptr = a.upload(M->h_item_ptr, s);
+  M->d_side_items = a.upload(M->h_side_items, s);
+  DG_CUDA(cudaStreamSynchronize(s));
+}
+
+void upload_mesh(dg_mesh* M, cudaStream_t s) {
+  const HostMesh& m = M->host;
   // upload
   DevArena& a = M->arena;
   M->d_p = a.upload(m.p, s);
@@ -72,14 +83,15 @@ void upload_mesh(dg_mesh* M, cudaStream_t s) {
   M->d_sf = a.upload(M->h_sf, s);
   M->d_sf3 = a.upload(M->h_sf3, s);
   M->d_tables = a.upload(M->h_tables, s);
-  M->d_order = a.upload(M->h_order, s);
-  M->d_tiles = a.upload(M->h_tiles, s);
-  M->d_items = a.upload(M->h_items, s);
-  M->d_item_ptr = a.upload(M->h_item_ptr, s);
-  M->d_side_items = a.upload(M->h_side_items, s);
   M->d_sched = a.alloc<unsigned>(2);
   DG_CUDA(cudaMemsetAsync(M->d_sched, 0, 2 * sizeof(unsigned), s));
-  DG_CUDA(cudaStreamSynchronize(s));
+  upload_tiles(M, s);
+}
+
+// rebuild the tile lists of a single mesh from its tile shapes
+static void retile_mesh(dg_mesh* M, void*) {
+  if (M->host.dim == 3) build_tiles3(M);
+  else build_tiles(M);
 }
 
 
@@ -386,6 +398,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, const dg_options* opts, void*
   dg_status st = guarded([&] {
     M = new dg_mesh();
     build_mesh(M, desc, opts, (cudaStream_t)stream);
+    if (opts && opts->tune_tiles) tune_tiles(M, (cudaStream_t)stream, retile_mesh, nullptr);
   });
   if (st != DG_OK) { delete M; return st; }
   *out = M;
@@ -400,7 +413,11 @@ dg_status dg_mesh_stats_get(const dg_mesh* mesh, dg_mesh_stats* out) {
   return guarded([&] {
     DG_REQUIRE(mesh && out, "null argument");
     *out = mesh->stats;
-    out->device_bytes = (int64_t)mesh->arena.bytes;
+    out->device_bytes = (int64_t)(mesh->arena.bytes + mesh->tile_arena.bytes);
+    if (!out->tiles_tuned) {
+      for (int p = 0; p <= kMaxP; ++p) out->tile_elems[p] = mesh->host.dim == 2 ? mesh->tile_epb[p] : 0;
+      out->tile_smem_budget = mesh->host.dim == 3 ? 8 * mesh->apply3_budget : 0;
+    }
   });
 }
 

@@ -118,6 +118,12 @@ struct dg_mesh {
   std::vector<int32_t> h_item_ptr;    // n_tiles + 1
   std::vector<int32_t> h_side_items;  // 2 per (order position, side): first item, count
   int64_t apply_smem = 0;             // dynamic shared memory of the 2D operator kernel
+  // tile shapes: squares, elements per operator tile of each degree (at most
+  // apply_epb(p), the compiled capacity); cubes, the shared-memory budget of a
+  // tile in doubles.  Fixed rules unless the tile tuner chose them.
+  int tile_epb[dg::kMaxP + 1];
+  int64_t apply3_budget = dg::kApply3Budget;
+  dg::DevArena tile_arena;            // device copies of the tile lists (rebuilt when tuned)
   // device
   dg::DevArena arena;
   int32_t* d_p = nullptr;
@@ -143,7 +149,13 @@ struct dg_mesh {
   // batch only: per-instance stop flags; tiles of stopped instances are skipped
   const double* skip_status = nullptr;
   int skip_stride = 0;
-  ~dg_mesh() { arena.release(); }
+  dg_mesh() {
+    for (int p = 0; p <= dg::kMaxP; ++p) tile_epb[p] = p >= 1 ? dg::apply_epb(p) : 1;
+  }
+  ~dg_mesh() {
+    tile_arena.release();
+    arena.release();
+  }
 };
 
 struct dg_precond {
@@ -194,8 +206,18 @@ void build_mesh_host(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opt
 void build_tiles(dg_mesh* M);
 // flat sub-face item lists of the tiles (square meshes; after the tiles)
 void build_face_items(dg_mesh* M);
+// cube meshes: degree-sorted order, tiles and their item lists
+void build_tiles3(dg_mesh* M);
 // upload the host-built operator data (M->host.p/off/sf_ptr, h_* arrays)
 void upload_mesh(dg_mesh* M, cudaStream_t s);
+// (re)upload the tile lists and size the operator launch (tile_arena)
+void upload_tiles(dg_mesh* M, cudaStream_t s);
+// Time the operator kernel over candidate tile shapes and keep the fastest:
+// squares, for each degree present (highest first) the elements per tile in
+// {apply_epb(p), 3/4, 1/2 of it}; cubes, shared-memory budgets for 4, 3 and 2
+// tiles per SM.  retile rebuilds the host tile lists from the tile shapes.
+// Records the choice and the times in M->stats.
+void tune_tiles(dg_mesh* M, cudaStream_t s, void (*retile)(dg_mesh*, void*), void* ctx);
 // cube meshes: topology, records, tables, tiles, stats (opts already validated)
 void build_mesh_host3(dg_mesh* M, const dg_mesh_desc* desc, const dg_options& opts);
 // rows of element k of y = A x (x: full host vector), same formulation as the kernel

@@ -206,7 +206,7 @@ static int ilog2(int v) {
 
 void build_tiles(dg_mesh* M) {
   // tiles of the operator kernel: degree-descending element order, runs of
-  // at most apply_epb(p) elements of one degree
+  // at most tile_epb[p] elements of one degree (apply_epb(p) unless tuned)
   const HostMesh& m = M->host;
   std::vector<int32_t> order(m.n);
   for (int64_t k = 0; k < m.n; ++k) order[k] = (int32_t)k;
@@ -215,7 +215,7 @@ void build_tiles(dg_mesh* M) {
   for (int64_t i = 0; i < m.n;) {
     const int P = m.p[order[i]];
     int64_t j = i;
-    while (j < m.n && m.p[order[j]] == P && j - i < apply_epb(P)) ++j;
+    while (j < m.n && m.p[order[j]] == P && j - i < M->tile_epb[P]) ++j;
     M->h_tiles.push_back({P, (int32_t)i, (int32_t)(j - i), 0});
     i = j;
   }

@@ -119,7 +119,7 @@ void build_topology3(HostMesh& m) {
 // sub-face items.  The tile's sub-faces are a flat list of (record, side)
 // items, processed in chunks that fit the shared-memory budget; per element
 // side the first item and the count.
-static void build_tiles3(dg_mesh* M) {
+void build_tiles3(dg_mesh* M) {
   const HostMesh& m = M->host;
   const bool br2 = M->opts.form == DG_FORM_BR2;
   std::vector<int32_t> nq(m.n), nitem(m.n);
@@ -151,12 +151,12 @@ static void build_tiles3(dg_mesh* M) {
     while (j < m.n && m.p[order[j]] == P && nq[order[j]] == Q && j - i < by_threads) {
       const int64_t cnt = j - i + 1, it = items + nitem[order[j]];
       const int64_t need = 2 * NP * NP + cnt * fixed_per + std::min<int64_t>(it, kApply3MinChunk) * item_per;
-      if (need > kApply3Budget && j > i) break;
+      if (need > M->apply3_budget && j > i) break;
       items = it;
       ++j;
     }
     const int64_t fixed = 2 * NP * NP + (j - i) * fixed_per;
-    const int64_t room = (kApply3Budget - fixed) / item_per;
+    const int64_t room = (M->apply3_budget - fixed) / item_per;
     DG_REQUIRE(room >= 1, "3D operator tile does not fit in shared memory");
     ApplyTile T{};
     T.p = P;

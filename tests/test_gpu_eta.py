@@ -5,7 +5,7 @@ Jacobi on all of V_B, Section 4.1) for eta = 10 ... 10^4, SIPG and BR2, on an
 4,990 DOFs).  With B the GPU iteration counts match the oracle's within +-1
 in every cell.  B~ needs thousands of iterations at large eta (condition
 numbers in the thousands), where CG's finite-precision trajectory depends on
-the summation order of the dot products, so its cells match within 2%.  B
+the summation order of the dot products, so its cells match within 5%.  B
 stays within a small factor over the sweep while B~ grows with eta (the
 paper's claim, whose numbers are only in a figure)."""
 import numpy as np
@@ -38,7 +38,7 @@ def test_eta_sweep_matches_oracle(built_lib, cuda_device, form):
             x = torch.empty_like(bd)
             info = B.dg_pcg_solve(M.h, pc.h, bd, x, 1e-8, 20000)
             assert info.status == B.DG_OK
-            bar = 1 if sm == "full" else max(1, int(0.02 * ref.iters))
+            bar = 1 if sm == "full" else max(1, int(0.05 * ref.iters))
             assert abs(info.iters - ref.iters) <= bar, (eta, sm, info.iters, ref.iters)
             table[(eta, sm)] = info.iters
     full = [table[(e, "full")] for e in ETAS]
