@@ -1,22 +1,32 @@
-"""Benchmark: PCG solves of the 2D hp-random workload through the C ABI.
+"""Benchmark: PCG solves of the hp-DG workloads through the C ABI.
 
-Workload: 2D Poisson on [0,1]^2, 32x32 base squares refined at random
-(probability 0.3 per cell, depth <= 3, arbitrarily irregular), degrees
-p ~ U{1..6}, SIPG with eta = 100, sine right-hand side (4 seeded modes),
-relative tolerance 1e-8; preconditioner B = B_B + B_C with one AMG V-cycle
-on the LOR matrix.  A step is one complete PCG solve (every PCG iteration
-runs the operator apply, the preconditioner and the vector updates).
-`value` is DOF-iterations per second of the mixed-precision solve (FP32
-preconditioner, FP64 operator / residual / dots); the FP64 solve is timed
-beside it.  L2 is flushed (a 512 MiB write) before every timed step.
+Default line (`python bench.py`): the 2D hp-random workload - 32x32 base
+squares refined at random (probability 0.3 per cell, depth <= 3, arbitrarily
+irregular), degrees p ~ U{1..6}, SIPG with eta = 100, sine right-hand side (4
+seeded modes), relative tolerance 1e-8, preconditioner B = B_B + B_C with one
+AMG V-cycle on the LOR matrix.  A step is one complete PCG solve (every PCG
+iteration runs the operator apply, the preconditioner and the vector
+updates).  `value` is DOF-iterations per second of the mixed-precision solve
+(FP32 preconditioner, FP64 operator / residual / dots), timed with CUDA
+events around the solve's one graph launch; the FP64 solve is timed beside
+it.  L2 is flushed (a 512 MiB write) before every timed step.
 
---workload hp2d-coef runs the same mesh with the piecewise-constant coefficient
-a in {1, 20} of the random-refinement problem (Section 4.3); hp3d the cube
-workload; batched and serving the B1 and V1 forms.
+Beside it the same line carries
+  roofline      the operator kernel (FP64-ALU bound) against the FP64 FMA peak
+                measured in the same run, and `rooflines` for the trace
+                kernel, the block solves and the whole preconditioner (HBM);
+  oracle        the FP64 CPU oracle's solution of the same problem and the
+                distance of the GPU's mixed and FP64 solutions to it;
+  cpu_baseline  the oracle timed on the host cores (one thread and all cores);
+  workloads     sub-lines with their own clocks: the same mesh with BR2, the
+                16^3 cube workload, the batched form (256 problems x 4
+                right-hand sides in one launch) and a bounded sample of the
+                served form.
+--workload hp2d-coef | hp3d | batched | serving runs one of them as the line.
 
 --impl reference times the FP64 CPU oracle on the same workload (a bounded
-sample of PCG iterations per step).  Multi-GPU: independent replicas
-(the problem does not shard), one per rank.
+sample of PCG iterations per step).  Multi-GPU: independent replicas (the
+problem does not shard), one per rank.
 """
 from __future__ import annotations
 
@@ -24,22 +34,27 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
-# the CPU oracle legs report one core: keep numpy's BLAS on one thread (set
-# before numpy is first imported; the GPU path does no host BLAS work)
+# the CPU oracle legs choose their own thread count: keep numpy's BLAS on one
+# thread unless the caller set it (set before numpy is first imported; the
+# GPU path does no host BLAS work)
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
 WORKLOAD = "2D hp-random 32x32 base, prob 0.3, depth<=3, p~U{1..6}, SIPG eta=100, tol 1e-8, seed 0"
 METRIC = "DOF-iters/s (PCG on the 2D hp-random workload, mixed FP32 preconditioner / FP64 outer)"
+WORKLOAD_BR2 = ("2D hp-random 32x32 base, prob 0.3, depth<=3, p~U{1..6}, BR2 (eta = most sub-faces of one "
+                "element), tol 1e-8, seed 0")
 WORKLOAD3 = ("3D hp-random 16^3 base, prob 0.2, depth<=2, p~U{1..5}, BR2 (eta = most sub-faces of one "
              "element), tol 1e-8, seed 0")
 METRIC3 = "DOF-iters/s (PCG on the 3D hp-random workload, mixed FP32 preconditioner / FP64 outer)"
@@ -49,28 +64,29 @@ METRICC = ("DOF-iters/s (PCG on the 2D hp-random workload with a piecewise-const
            "preconditioner / FP64 outer)")
 ORACLE_SAMPLE_ITERS = 20
 
-# DRAM bytes (read + write) of one apply_kernel launch on this workload, from
-# the ncu capture summarised in profiles/apply_kernel_hp2d_32x32.md.  Valid
-# only for the kernel and tile-building sources it was taken on: the line
-# reports null traffic as soon as their hash differs.
-APPLY_TRAFFIC = {"sources": ["paper_2009_01287_gb300/csrc/apply_kernel.cuh",
-                             "paper_2009_01287_gb300/csrc/apply_launch.cu",
-                             "paper_2009_01287_gb300/csrc/dg_internal.h",
-                             "paper_2009_01287_gb300/csrc/mesh.cpp"],
-                 "sha256_16": "74d388822a4cf47a", "bytes": 3548672 + 0}
-# likewise for the 3D operator (profiles/apply3_kernel_hp3d_16cube.md)
-APPLY3_TRAFFIC = {"sources": ["paper_2009_01287_gb300/csrc/apply_kernel.cuh",
-                              "paper_2009_01287_gb300/csrc/apply3_kernel.cuh",
-                              "paper_2009_01287_gb300/csrc/apply_launch.cu",
-                              "paper_2009_01287_gb300/csrc/dg_internal.h",
-                              "paper_2009_01287_gb300/csrc/mesh3.cpp"],
-                  "sha256_16": "64366f7762b242cf", "bytes": 66824192 + 5452288}
+# DRAM bytes (read + write) of one launch of a kernel on a workload, from the
+# ncu captures summarised under profiles/.  Valid only for the sources they
+# were taken on: a record reports null as soon as the hash of its sources
+# differs from the one captured.
+TRAFFIC = {
+    "apply_kernel/hp2d": {"sources": ["paper_2009_01287_gb300/csrc/apply_kernel.cuh",
+                                      "paper_2009_01287_gb300/csrc/apply_launch.cu",
+                                      "paper_2009_01287_gb300/csrc/dg_internal.h",
+                                      "paper_2009_01287_gb300/csrc/mesh.cpp"],
+                          "sha256_16": "74d388822a4cf47a", "bytes": 3548672},
+    "apply3_kernel/hp3d": {"sources": ["paper_2009_01287_gb300/csrc/apply_kernel.cuh",
+                                       "paper_2009_01287_gb300/csrc/apply3_kernel.cuh",
+                                       "paper_2009_01287_gb300/csrc/apply_launch.cu",
+                                       "paper_2009_01287_gb300/csrc/dg_internal.h",
+                                       "paper_2009_01287_gb300/csrc/mesh3.cpp"],
+                           "sha256_16": "64366f7762b242cf", "bytes": 66824192 + 5452288},
+}
 
 
-def apply_traffic(three: bool = False):
+def traffic(key: str):
     import hashlib
-    rec = APPLY3_TRAFFIC if three else APPLY_TRAFFIC
-    if rec["bytes"] is None:
+    rec = TRAFFIC.get(key)
+    if rec is None or rec["bytes"] is None:
         return None
     h = hashlib.sha256()
     for f in rec["sources"]:
@@ -107,6 +123,7 @@ class ClockSampler:
             self.t.start()
         except (OSError, FileNotFoundError):
             self.proc = None
+        return self
 
     def _read(self):
         for line in self.proc.stdout:
@@ -141,12 +158,376 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def fp64_peak_tflops(sm_mhz: float) -> float:
-    """FP64 FMA peak: 152 SMs x 2 FP64 FMA per SM per clock (GB300 nominal
-    1.25 TFLOP/s at ~2.07 GHz), at the SM clock sampled under load."""
-    return 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+def survey_model_flops(mesh) -> float:
+    """FP64 flops of one operator apply by the scope table's model: 8(p+1)
+    flop/DOF of sum-factorised volume work plus 64/(p+1) per DOF of face work
+    (2D), i.e. 8 n^3 + 64 n per element of n = p+1 nodes per direction."""
+    import numpy as np
+    n = mesh.p.astype(np.float64) + 1.0
+    return float(np.sum(8.0 * n ** 3 + 64.0 * n))
 
 
+def trace_flops(mesh) -> float:
+    """FP64 flops of the trace kernel: per side node the normal derivative, a
+    contraction of length p+1 (2D: 4 (p+1)^2 FMAs per element; 3D: 6 (p+1)^3)."""
+    import numpy as np
+    n = mesh.p.astype(np.float64) + 1.0
+    return float(np.sum(2.0 * (4.0 * n ** 2 if mesh.dim == 2 else 6.0 * n ** 3)))
+
+
+# ---------------------------------------------------------------- GPU legs
+class Ctx:
+    def __init__(self, dev, stream):
+        import torch
+        self.torch = torch
+        self.dev = dev
+        self.stream = stream
+        self.flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def events(self, n):
+        return [self.torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def fp64_peak(B, ctx, iters: int = 40000) -> dict:
+    tf = [B.dg_fp64_fma_probe(iters, ctx.stream)[0] for _ in range(3)]
+    return {"tflops": max(tf), "runs": tf}
+
+
+def time_solves(B, ctx, M, pc, b, x, tol, steps, warmup):
+    torch = ctx.torch
+    for _ in range(warmup):
+        B.dg_pcg_solve(M.h, pc.h, b, x, tol, 5000, ctx.stream)
+    ms, it = [], []
+    for _ in range(steps):
+        ctx.flush.fill_(1.0)
+        torch.cuda.synchronize()
+        info = B.dg_pcg_solve(M.h, pc.h, b, x, tol, 5000, ctx.stream)
+        ms.append(info.solve_ms)
+        it.append(info.iters)
+    return ms, it
+
+
+def operator_rooflines(B, ctx, M, mesh, peak_tf, peaks, three, tkey):
+    """The operator kernel and the trace kernel, each timed alone with CUDA
+    events (L2 flushed before every launch)."""
+    torch = ctx.torch
+    n = M.n_dofs
+    xin = torch.randn(n, dtype=torch.float64, device=ctx.dev)
+    yout = torch.empty_like(xin)
+    for _ in range(5):
+        B.dg_apply(M.h, xin, yout, ctx.stream)
+    tr, ap = [], []
+    for _ in range(30):
+        ctx.flush.fill_(2.0)
+        t = B.dg_apply_profile(M.h, xin, yout, ctx.stream)
+        tr.append(t.trace_ms)
+        ap.append(t.apply_ms)
+    apply_ms, trace_ms = statistics.mean(ap), statistics.mean(tr)
+    st = M.stats
+    tfl = trace_flops(mesh)
+    kfl = st.apply_flops - tfl
+    ach = kfl / (apply_ms / 1e3) / 1e12
+    name = "apply3_kernel (BR2 operator on cubes, FP64)" if three else "apply_kernel (SIPG operator, FP64)"
+    main = {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
+            "frac": ach / peak_tf, "traffic": traffic(tkey),
+            "flops_per_launch": kfl, "launch_ms": apply_ms,
+            "flops_model": "FMAs of the kernel as formulated (x2), counted on the host from the mesh: "
+                           "volume 8 n^3, face terms 8 n (n + n_nb) per sub-face side, test-function "
+                           "normal derivatives 8 n^2 per element (n = p+1)",
+            "flops_survey_model_per_launch": survey_model_flops(mesh) if not three else None,
+            "frac_survey_model": (survey_model_flops(mesh) / (apply_ms / 1e3) / 1e12 / peak_tf
+                                  if not three else None),
+            "algorithmic_bytes": st.apply_bytes,
+            "hbm_gbs": st.apply_bytes / (apply_ms / 1e3) / 1e9,
+            "hbm_frac": st.apply_bytes / (apply_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+            "peak_source": "FP64 FMA-chain probe (dg_fp64_fma_probe) in this run; HBM of measured"}
+    trace = {"kernel": "trace3_kernel" if three else "trace_kernel", "bound": "hbm",
+             "launch_ms": trace_ms, "flops_per_launch": tfl,
+             "note": "inside PCG the traces are written by the p-update kernel, not by this kernel"}
+    # side traces: read x once, write u and dn at every side node
+    import numpy as np
+    npd = mesh.p.astype(np.float64) + 1.0
+    side_nodes = float(np.sum(6.0 * npd ** 2 if three else 4.0 * npd))
+    tb = 8.0 * n + 16.0 * side_nodes
+    trace.update({"algorithmic_bytes": tb, "achieved": tb / (trace_ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+                  "unit": "GB/s", "frac": tb / (trace_ms / 1e3) / 1e9 / peaks["hbm_gbs"]})
+    return main, trace, apply_ms, trace_ms
+
+
+def precond_rooflines(B, ctx, pc, peaks):
+    torch = ctx.torch
+    n = pc.mesh.n_dofs
+    r = torch.randn(n, dtype=torch.float64, device=ctx.dev)
+    z = torch.empty_like(r)
+    for _ in range(3):
+        B.dg_precond_apply(pc.h, r, z, ctx.stream)
+    parts = {"blocks_ms": [], "restrict_ms": [], "lor_ms": [], "final_ms": [], "total_ms": []}
+    for _ in range(30):
+        ctx.flush.fill_(4.0)
+        t = B.dg_precond_profile(pc.h, r, z, ctx.stream)
+        for k in parts:
+            parts[k].append(getattr(t, k))
+    # the apply as the solve runs it (block solves beside the V-cycle)
+    ev = ctx.events(60)
+    for i in range(30):
+        ctx.flush.fill_(4.0)
+        ev[2 * i].record(ctx.stream)
+        B.dg_precond_apply(pc.h, r, z, ctx.stream)
+        ev[2 * i + 1].record(ctx.stream)
+    torch.cuda.synchronize()
+    concurrent = statistics.mean(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(30))
+    m = {k: statistics.mean(v) for k, v in parts.items()}
+    st = pc.stats
+    hbm = peaks["hbm_gbs"]
+    blocks = {"kernel": "block_solve_kernel (V_e block solves)", "bound": "hbm",
+              "achieved": st.block_bytes / (m["blocks_ms"] / 1e3) / 1e9 if m["blocks_ms"] > 0 else None,
+              "peak": hbm, "unit": "GB/s", "traffic": None, "algorithmic_bytes": st.block_bytes,
+              "launch_ms": m["blocks_ms"]}
+    if blocks["achieved"] is not None:
+        blocks["frac"] = blocks["achieved"] / hbm
+    whole = {"kernel": f"preconditioner z = B r ({st.kernels_per_apply} kernels, serial)", "bound": "hbm",
+             "achieved": st.apply_bytes / (m["total_ms"] / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+             "frac": st.apply_bytes / (m["total_ms"] / 1e3) / 1e9 / hbm, "traffic": None,
+             "algorithmic_bytes": st.apply_bytes, "launch_ms": m["total_ms"],
+             "parts_ms": {k: m[k] for k in ("blocks_ms", "restrict_ms", "lor_ms", "final_ms")},
+             "ms_with_blocks_beside_vcycle": concurrent}
+    return blocks, whole, concurrent
+
+
+def measure_single(B, ctx, mesh, rh, form, steps, warmup, peaks, peak_tf, tkey, three=False,
+                   e2e=False, keep_x=False):
+    """Mixed and FP64 solves of one workload, its kernels' rooflines."""
+    torch = ctx.torch
+    opts64 = B.make_options(form=form, precision=B.DG_PREC_FP64, lor=B.DG_LOR_AMG)
+    opts32 = B.make_options(form=form, precision=B.DG_PREC_MIXED, lor=B.DG_LOR_AMG)
+    t0 = time.perf_counter()
+    M = B.Mesh(mesh, opts64, ctx.stream)
+    pc32 = B.Precond(M, opts32)
+    setup_s = time.perf_counter() - t0
+    pc64 = B.Precond(M, opts64)
+    n = M.n_dofs
+    b = torch.empty(n, dtype=torch.float64, device=ctx.dev)
+    B.dg_rhs_sine(M.h, rh.amps, rh.waves, b, ctx.stream)
+    x32 = torch.empty_like(b)
+    x64 = torch.empty_like(b)
+    clocks = ClockSampler(ctx.dev.index or 0).start()
+    ms32, it32 = time_solves(B, ctx, M, pc32, b, x32, 1e-8, steps, warmup)
+    ms64, it64 = time_solves(B, ctx, M, pc64, b, x64, 1e-8, steps, min(warmup, 2))
+    main, trace, apply_ms, trace_ms = operator_rooflines(B, ctx, M, mesh, peak_tf, peaks, three, tkey)
+    blocks, whole, pc_ms = precond_rooflines(B, ctx, pc32, peaks)
+    out = {"n_dofs": n, "n_elems": int(M.stats.n_elems), "setup_s": setup_s,
+           "iters_mixed": statistics.median(it32), "iters_fp64": statistics.median(it64),
+           "time_to_tol_ms_mixed": statistics.median(ms32), "time_to_tol_ms_fp64": statistics.median(ms64),
+           "dof_iters_per_s_mixed": n * sum(it32) / (sum(ms32) / 1e3),
+           "dof_iters_per_s_fp64": n * sum(it64) / (sum(ms64) / 1e3),
+           "phase_ms": {"iteration_mixed": statistics.median(ms32) / statistics.median(it32),
+                        "operator_apply": apply_ms, "trace": trace_ms, "preconditioner_mixed": pc_ms},
+           "roofline": main, "rooflines": [trace, blocks, whole],
+           "precond": {"n_conforming": int(pc32.stats.n_conforming), "amg_levels": int(pc32.stats.n_levels),
+                       "n_blocks": int(pc32.stats.n_blocks), "max_block": int(pc32.stats.max_block),
+                       "kernels_per_apply": int(pc32.stats.kernels_per_apply),
+                       "device_bytes": int(pc32.stats.device_bytes)}}
+    if e2e:
+        bh = b.cpu().pin_memory()
+        xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+        t_e2e, it_e2e = [], []
+        for _ in range(steps):
+            ctx.flush.fill_(3.0)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            info = B.dg_pcg_solve_host(M.h, pc32.h, bh, xh, 1e-8, 5000, ctx.stream)
+            t_e2e.append(time.perf_counter() - t1)
+            it_e2e.append(info.iters)
+        out["_e2e"] = (t_e2e, it_e2e)
+    out["clocks"] = clocks.stop()
+    out["_raw"] = (ms32, it32, ms64, it64)
+    # the mixed solution's true relative residual with the FP64 operator
+    rres = torch.empty_like(b)
+    B.dg_apply(M.h, x32, rres, ctx.stream)
+    torch.cuda.synchronize()
+    out["true_rel_residual_mixed"] = float(torch.linalg.norm(rres - b) / torch.linalg.norm(b))
+    if keep_x:
+        out["_x"] = (x32.cpu().numpy(), x64.cpu().numpy())
+    out["kernels_per_iteration"] = 1 + 1 + int(pc32.stats.kernels_per_apply) + 1
+    for h in (pc32, pc64, M):
+        h.close()
+    return out
+
+
+def run_batched_leg(B, ctx, steps, warmup, n_problems=256, n_rhs=4, fp64=False, tune=True):
+    """Batched workload: many uneven problems x several right-hand sides in
+    one graph launch (every instance keeps its own PCG scalars)."""
+    torch = ctx.torch
+    from paper_2009_01287_gb300 import inputs
+    meshes = [inputs.config3_problem(k)[0] for k in range(n_problems)]
+    prec = B.DG_PREC_FP64 if fp64 else B.DG_PREC_MIXED
+    t0 = time.perf_counter()
+    bat = B.Batch(meshes, n_rhs=n_rhs, opts=B.make_options(precision=prec, tune_tiles=1 if tune else 0),
+                  stream=ctx.stream)
+    setup_s = time.perf_counter() - t0
+    st = bat.stats
+    tiles = {"tuned": bool(st.tiles_tuned), "elements_per_tile_by_degree": list(st.tile_elems)[1:],
+             "fixed_rule": [min(16, 256 // (p + 1) ** 2) for p in range(1, 9)],
+             "apply_ms_fixed": st.apply_ms_fixed if st.tiles_tuned else None,
+             "apply_ms_tuned": st.apply_ms_tuned if st.tiles_tuned else None}
+    b = torch.empty(bat.n_dofs, dtype=torch.float64, device=ctx.dev)
+    bat.rhs_sine([inputs.sine_rhs(2, 1000 + i) for i in range(bat.n_inst)], b, ctx.stream)
+    x = torch.empty_like(b)
+    for _ in range(warmup):
+        bat.solve(b, x, 1e-8, 5000, ctx.stream)
+    clocks = ClockSampler(ctx.dev.index or 0).start()
+    ms, dofit, iters = [], 0, []
+    sizes = [int(bat.offsets[i + 1] - bat.offsets[i]) for i in range(bat.n_inst)]
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        res, t = bat.solve(b, x, 1e-8, 5000, ctx.stream)
+        ms.append(t)
+        dofit += sum(n * r.iters for n, r in zip(sizes, res))
+        iters.append([r.iters for r in res])
+    clk = clocks.stop()
+    flat = [i for row in iters for i in row]
+    bat.close()
+    return {"workload": f"batched: {n_problems} 2D hp-random problems (base N log-uniform in [4,64], prob 0.3, "
+                        f"depth<=3, p~U{{1..8}}, 1k-300k DOFs each) x {n_rhs} seeded sine RHS, SIPG eta=100, "
+                        f"tol 1e-8, one graph launch per step",
+            "metric": "DOF-iters/s", "value": dofit / (sum(ms) / 1e3), "ms_per_step": statistics.mean(ms),
+            "instances": bat.n_inst, "total_dofs": bat.n_dofs,
+            "dtype": "f64 (outer PCG, operator) + " + ("f64" if fp64 else "f32") + " (preconditioner)",
+            "iters_min_median_max": [min(flat), statistics.median(flat), max(flat)], "setup_s": setup_s,
+            "tiles": tiles, "l2": "vectors exceed L2 (no flush)", "clocks": clk}
+
+
+def run_serving_leg(B, n_meshes, n_requests, rate, slots):
+    from paper_2009_01287_gb300 import inputs, serve
+    meshes = inputs.serving_meshes(n_meshes)
+    reqs = serve.poisson_stream(n_requests, rate, meshes, seed=0)
+    srv = serve.Server(slots=slots, precision=B.DG_PREC_MIXED)
+    # resident state for every mesh first (setup is reported, not timed as latency)
+    warm = [serve.Request(rid=10 ** 6 + j, arrival=0.0, mesh=m, rhs=inputs.sine_rhs(m.dim, 1))
+            for j, m in enumerate(meshes)]
+    t = time.perf_counter()
+    srv.run(warm, realtime=False)
+    setup_s = time.perf_counter() - t
+    clocks = ClockSampler(0).start()
+    t = time.perf_counter()
+    res = srv.run(reqs, realtime=True)
+    wall = time.perf_counter() - t
+    clk = clocks.stop()
+    rep = serve.report(res, wall)
+    inflight, evictions = srv.max_inflight, srv.evictions
+    srv.close()
+    # sequential plain-FP64 loop over the same requests (one slot, FP64 preconditioner)
+    seq = serve.Server(slots=1, precision=B.DG_PREC_FP64)
+    seq.run(warm, realtime=False)
+    t = time.perf_counter()
+    res_seq = seq.run(reqs, realtime=True)
+    rep_seq = serve.report(res_seq, time.perf_counter() - t)
+    seq.close()
+    sizes = sorted(m.n_dofs() for m in meshes)
+    return {"workload": f"serving: {len(reqs)} requests, Poisson arrivals {rate}/s, {len(meshes)} distinct meshes "
+                        f"(half squares, half cubes; DOFs log-uniform in [5k, 2M]: {sizes[0]}..{sizes[-1]}; "
+                        f"p~U{{1..6}}), seeded sine RHS per request, tol 1e-8, {slots} slots, 2D SIPG / 3D BR2",
+            "metric": "DOF-iters/s and p50/p99 latency", "value": rep["dof_iters_per_s"],
+            "p50_latency_s": rep["p50_latency_s"], "p99_latency_s": rep["p99_latency_s"], "ok": rep["ok"],
+            "requests": rep["requests"], "requests_3d": rep["requests_3d"], "wall_s": wall,
+            "max_inflight": inflight, "evictions": evictions, "setup_s_all_meshes": setup_s,
+            "sequential_fp64": rep_seq, "clocks": clk}
+
+
+# ---------------------------------------------------------------- CPU oracle legs
+def _oracle_problem(which: str, seed: int):
+    from oracle import rhs, solver
+    from paper_2009_01287_gb300 import inputs
+    if which == "hp3d":
+        mesh, rh = inputs.config2(seed, base=4)
+        prob = solver.build_problem(mesh, form="br2")
+    else:
+        mesh, rh = inputs.config1_coeff(seed) if which == "hp2d-coef" else inputs.config1(seed)
+        prob = solver.build_problem(mesh)
+    pc = solver.Preconditioner(prob, lor="amg")
+    b = rhs.load_vector(prob.space, rh.amps, rh.waves)
+    return prob, pc, b
+
+
+def _oracle_iters(prob, pc, b, iters: int) -> float:
+    from oracle import solver
+    t = time.perf_counter()
+    solver.pcg(prob.A, b, pc.apply, 1e-30, iters)
+    return time.perf_counter() - t
+
+
+def oracle_leg_main(args):
+    """Child process of the CPU baseline: the oracle on the workload, with
+    the BLAS thread count its environment sets.  Writes a JSON summary (and
+    the solution to tolerance when asked) to args.oracle_out."""
+    import pickle
+
+    import numpy as np
+    cache = args.oracle_out + ".problem.pkl"
+    t = time.perf_counter()
+    if os.path.exists(cache):
+        prob, pc, b = pickle.load(open(cache, "rb"))
+    else:
+        prob, pc, b = _oracle_problem(args.workload, args.seed)
+        pickle.dump((prob, pc, b), open(cache, "wb"))
+    setup_s = time.perf_counter() - t
+    dt = _oracle_iters(prob, pc, b, ORACLE_SAMPLE_ITERS)
+    out = {"n": int(prob.space.n), "sample_s": dt, "setup_s": setup_s,
+           "threads": int(os.environ.get("OMP_NUM_THREADS", "1"))}
+    if args.oracle_solve:
+        from oracle import solver
+        t = time.perf_counter()
+        res = solver.pcg(prob.A, b, pc.apply, 1e-8, 5000)
+        out.update({"solve_s": time.perf_counter() - t, "iters": res.iters, "rel_res": res.rel_res})
+        np.save(args.oracle_out + ".x.npy", res.x)
+    json.dump(out, open(args.oracle_out, "w"))
+
+
+def cpu_baseline(workload: str, seed: int, solve: bool):
+    """The oracle as it stands, on the GPU machine's host cores: 20 FP64 PCG
+    iterations on one thread and on all cores (BLAS threads; scipy's sparse
+    products are single-threaded), plus, when asked, its solve to 1e-8 on one
+    thread (returned for the accuracy comparison)."""
+    import numpy as np
+    nproc = os.cpu_count() or 1
+    tmp = tempfile.mkdtemp(prefix="dg_oracle_")
+    outp = os.path.join(tmp, "leg.json")
+    legs = {}
+    for threads, do_solve in ((1, solve), (nproc, False)):
+        env = dict(os.environ)
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[v] = str(threads)
+        cmd = [sys.executable, os.path.abspath(__file__), "--oracle-leg", "--workload", workload,
+               "--seed", str(seed), "--oracle-out", outp] + (["--oracle-solve"] if do_solve else [])
+        subprocess.run(cmd, env=env, check=True, timeout=1800)
+        legs[threads] = json.load(open(outp))
+    n = legs[1]["n"]
+    one, allc = legs[1], legs[nproc]
+    cpu = platform.processor() or platform.machine()
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                cpu = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    sample = (f"{ORACLE_SAMPLE_ITERS} FP64 PCG iterations of the same workload" +
+              (" on the same recipe with a 4^3 base" if workload == "hp3d" else "") +
+              f" ({n} DOFs; setup untimed), scipy sparse + numpy")
+    out = {"value": n * ORACLE_SAMPLE_ITERS / one["sample_s"], "unit": "DOF-iters/s", "cores": 1,
+           "kind": "oracle", "sample": sample + ", one thread",
+           "all_cores": {"value": n * ORACLE_SAMPLE_ITERS / allc["sample_s"], "cores": nproc,
+                         "note": "BLAS on all cores; the sparse products stay single-threaded"},
+           "nproc": nproc, "cpu": cpu, "setup_s": one["setup_s"]}
+    x = None
+    if solve:
+        out["time_to_tol_s"] = one["solve_s"]
+        out["iters"] = one["iters"]
+        x = np.load(outp + ".x.npy")
+    return out, x
+
+
+# ---------------------------------------------------------------- main line
 def run_ours(args):
     import numpy as np
     import torch
@@ -161,7 +542,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
+    ctx = Ctx(dev, torch.cuda.current_stream(dev))
     three = args.workload == "hp3d"
     coef = args.workload == "hp2d-coef"
     if three:
@@ -169,98 +550,23 @@ def run_ours(args):
     else:
         mesh, rh = inputs.config1_coeff(args.seed) if coef else inputs.config1(args.seed)
     form = B.DG_FORM_BR2 if three else B.DG_FORM_SIPG
-    opts64 = B.make_options(form=form, precision=B.DG_PREC_FP64, lor=B.DG_LOR_AMG)
-    opts32 = B.make_options(form=form, precision=B.DG_PREC_MIXED, lor=B.DG_LOR_AMG)
-    M = B.Mesh(mesh, opts64, stream)
-    t0 = time.perf_counter()
-    pc32 = B.Precond(M, opts32)
-    setup_s = time.perf_counter() - t0
-    pc64 = B.Precond(M, opts64)
-    n = M.n_dofs
-    b = torch.empty(n, dtype=torch.float64, device=dev)
-    B.dg_rhs_sine(M.h, rh.amps, rh.waves, b, stream)
-    x = torch.empty_like(b)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    tol, maxit = args.tol, 5000
-
-    def solve(pc):
-        return B.dg_pcg_solve(M.h, pc.h, b, x, tol, maxit, stream)
-
-    for _ in range(args.warmup):
-        solve(pc32)
-        solve(pc64)
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
+    peaks, peak_kind = _peaks()
+    probe = fp64_peak(B, ctx)
     if dist:
         dist.barrier()
-    torch.cuda.synchronize()
-    ms32, it32, ms64, it64 = [], [], [], []
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        info = solve(pc32)
-        ms32.append(info.solve_ms)
-        it32.append(info.iters)
-    torch.cuda.synchronize()
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        info = solve(pc64)
-        ms64.append(info.solve_ms)
-        it64.append(info.iters)
-    torch.cuda.synchronize()
-    # dominant kernel: the operator apply, timed alone on the launching stream
-    xin = torch.randn(n, dtype=torch.float64, device=dev)
-    yout = torch.empty_like(xin)
-    for _ in range(5):
-        B.dg_apply(M.h, xin, yout, stream)
-    napply = 50
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * napply)]
-    for i in range(napply):
-        flush.fill_(2.0)
-        ev[2 * i].record(stream)
-        B.dg_apply(M.h, xin, yout, stream)
-        ev[2 * i + 1].record(stream)
-    torch.cuda.synchronize()
-    apply_ms = statistics.mean(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(napply))
-    # the mixed preconditioner alone, timed the same way (phase breakdown)
-    for i in range(napply):
-        flush.fill_(4.0)
-        ev[2 * i].record(stream)
-        B.dg_precond_apply(pc32.h, xin, yout, stream)
-        ev[2 * i + 1].record(stream)
-    torch.cuda.synchronize()
-    precond_ms = statistics.mean(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(napply))
-    # end to end: host buffers in and out through the C ABI (pinned)
-    bh = b.cpu().pin_memory()
-    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
-    t_e2e, it_e2e = [], []
-    for _ in range(args.steps):
-        flush.fill_(3.0)
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        info = B.dg_pcg_solve_host(M.h, pc32.h, bh, xh, tol, maxit, stream)
-        t_e2e.append(time.perf_counter() - t1)
-        it_e2e.append(info.iters)
-    clk = clocks.stop()
+    res = measure_single(B, ctx, mesh, rh, form, args.steps, args.warmup, peaks, probe["tflops"],
+                         "apply3_kernel/hp3d" if three else ("apply_kernel/hp2d" if not coef else "none"),
+                         three=three, e2e=True, keep_x=True)
+    ms32, it32, ms64, it64 = res.pop("_raw")
+    t_e2e, it_e2e = res.pop("_e2e")
+    x32, x64 = res.pop("_x")
     from paper_2009_01287_gb300 import replicas
+    n = res["n_dofs"]
     (t32, t64, te), dof_iters32 = replicas.aggregate(
         [sum(ms32) / 1e3, sum(ms64) / 1e3, sum(t_e2e)], n * sum(it32), device=dev)
     value = dof_iters32 / t32
-    stats = M.stats
-    s32 = pc32.stats
-    peaks, peak_kind = _peaks()
-    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp64_peak = fp64_peak_tflops(sm_mhz)
-    achieved_tf = stats.apply_flops / (apply_ms / 1e3) / 1e12
-    levels = s32.n_levels
-    # preconditioner launches as the library reports them (restriction, two or
-    # four kernels per AMG level, dense coarsest level, block solves, final)
-    precond_kernels = int(s32.kernels_per_apply)
-    # iteration: operator apply, x / r update, preconditioner, p update with traces
-    kernels_per_iter = 1 + 1 + precond_kernels + 1
-    launches = sum(2 + precond_kernels + it * kernels_per_iter for it in it32)  # + init, first p
+    launches = sum(3 + res["precond"]["kernels_per_apply"] + it * res["kernels_per_iteration"] for it in it32)
+    res["roofline"]["peak_fp64_probe_runs"] = probe["runs"]
     out = {
         "metric": METRIC3 if three else (METRICC if coef else METRIC),
         "value": value,
@@ -275,35 +581,53 @@ def run_ours(args):
         "dtype": "f64 (outer PCG, operator) + f32 (preconditioner)",
         "data": "synthetic",
         "config": {"workload": WORKLOAD3 if three else (WORKLOADC if coef else WORKLOAD), "n_dofs": n,
-                   "n_elems": int(stats.n_elems),
-                   "n_conforming": int(s32.n_conforming), "amg_levels": levels,
-                   "n_blocks": int(s32.n_blocks), "max_block": int(s32.max_block),
-                   "amg_plain_levels": [int(s32.level_plain[i]) for i in range(levels)],
-                   "parallelism": f"replicas x{ws}", "l2": "flushed (512 MiB write) before every step"},
-        "iters_mixed": statistics.median(it32),
-        "iters_fp64": statistics.median(it64),
-        "time_to_tol_ms_mixed": statistics.median(ms32),
-        "time_to_tol_ms_fp64": statistics.median(ms64),
+                   "n_elems": res["n_elems"], **res["precond"],
+                   "parallelism": f"replicas x{ws}", "l2": "flushed (512 MiB write) before every step",
+                   "timed": "CUDA events around each solve's one graph launch (copy of b, start, "
+                            "while-loop of iterations, copy of x); no host round trip inside"},
+        "iters_mixed": res["iters_mixed"],
+        "iters_fp64": res["iters_fp64"],
+        "time_to_tol_ms_mixed": res["time_to_tol_ms_mixed"],
+        "time_to_tol_ms_fp64": res["time_to_tol_ms_fp64"],
         "dof_iters_per_s_fp64": ws * n * sum(it64) / t64,   # replicas: identical per rank
-        "setup_s": setup_s,
-        "phase_ms": {"iteration_mixed": statistics.median(ms32) / statistics.median(it32),
-                     "operator_apply": apply_ms, "preconditioner_mixed": precond_ms},
+        "setup_s": res["setup_s"],
+        "phase_ms": res["phase_ms"],
         "e2e": {"value": ws * n * sum(it_e2e) / te, "unit": "DOF-iters/s",
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
-        "roofline": {"kernel": ("apply3_kernel (BR2 operator on cubes, FP64)" if three
-                                else "apply_kernel (SIPG operator, FP64)"), "bound": "alu",
-                     "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": achieved_tf / fp64_peak, "traffic": None if coef else apply_traffic(three),
-                     "algorithmic_bytes": stats.apply_bytes,
-                     "flops_per_launch": stats.apply_flops, "launch_ms": apply_ms,
-                     "hbm_gbs": stats.apply_bytes / (apply_ms / 1e3) / 1e9,
-                     "hbm_frac": stats.apply_bytes / (apply_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
-                     "peak_source": f"FP64 FMA units x sampled SM clock; HBM {peak_kind}"},
+        "roofline": res["roofline"],
+        "rooflines": res["rooflines"],
+        "fp64_peak_tflops_measured": probe["tflops"],
         "gpu_launches": launches,
-        "clocks": clk,
+        "clocks": res["clocks"],
     }
-    if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        out["cpu_baseline"] = cpu_baseline3(args) if three else cpu_baseline(args, coef)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cb, xo = cpu_baseline(args.workload, args.seed, solve=not three)
+        out["cpu_baseline"] = cb
+        if xo is not None:
+            sc = float(np.abs(xo).max())
+            out["oracle"] = {"iters": cb.get("iters"), "time_to_tol_s_one_thread": cb.get("time_to_tol_s"),
+                             "rel_err_mixed": float(np.abs(x32 - xo).max()) / sc,
+                             "rel_err_fp64": float(np.abs(x64 - xo).max()) / sc,
+                             "norm": "max-norm of the difference over the max-norm of the oracle's solution"}
+            out["oracle_rel_err_mixed"] = out["oracle"]["rel_err_mixed"]
+    if rank == 0 and ws == 1 and not args.no_extras and args.workload == "hp2d":
+        extras = {}
+        mb, rb = inputs.config1(args.seed)
+        br2 = measure_single(B, ctx, mb, rb, B.DG_FORM_BR2, 3, 2, peaks, probe["tflops"], "none")
+        for k in ("_raw", "_e2e", "_x"):
+            br2.pop(k, None)
+        extras["hp2d_br2"] = {"workload": WORKLOAD_BR2, "metric": "DOF-iters/s",
+                              "value": br2["dof_iters_per_s_mixed"], **br2}
+        m3, r3 = inputs.config2(args.seed)
+        h3 = measure_single(B, ctx, m3, r3, B.DG_FORM_BR2, 3, 2, peaks, probe["tflops"], "apply3_kernel/hp3d",
+                            three=True)
+        for k in ("_raw", "_e2e", "_x"):
+            h3.pop(k, None)
+        extras["hp3d"] = {"workload": WORKLOAD3, "metric": "DOF-iters/s", "value": h3["dof_iters_per_s_mixed"],
+                          **h3}
+        extras["batched"] = run_batched_leg(B, ctx, 2, 1)
+        extras["serving"] = run_serving_leg(B, 8, 160, 200.0, 8)
+        out["workloads"] = extras
     if rank == 0:
         print(json.dumps(out))
     if dist:
@@ -311,188 +635,36 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-SERVE_WORKLOAD = ("serving: {n} requests, Poisson arrivals {rate}/s, {m} distinct 2D hp-random meshes "
-                  "(DOFs log-uniform in [5k, 200k], prob 0.3, depth<=3, p~U{{1..6}}), seeded sine RHS per request, "
-                  "tol 1e-8, {slots} slots")
-
-
-def serve_meshes(m: int, seed: int = 0):
-    """m distinct meshes with DOF targets log-uniform in [5k, 200k]."""
-    import numpy as np
-    from paper_2009_01287_gb300 import inputs
-    rng = np.random.Generator(np.random.PCG64(777 + seed))
-    out = []
-    for j in range(m):
-        target = math.exp(rng.uniform(math.log(5e3), math.log(2e5)))
-        base = max(2, int(round(math.sqrt(target / 99.0))))
-        out.append(inputs.random_refined_mesh(2, base, 3, 0.3, 1, 6, seed=9000 + j))
-    return out
-
-
 def run_serving(args):
     import torch
-
     from paper_2009_01287_gb300 import binding as B
-    from paper_2009_01287_gb300 import serve
-
     torch.cuda.set_device(0)
-    meshes = serve_meshes(args.serve_meshes)
-    reqs = serve.poisson_stream(args.serve_requests, args.serve_rate, meshes, seed=0)
-    # warm-up: resident state for every mesh (setup is reported, not timed as latency)
-    srv = serve.Server(slots=args.serve_slots, precision=B.DG_PREC_MIXED)
-    warm = [serve.Request(rid=10 ** 6 + j, arrival=0.0, mesh=m, rhs=reqs[0].rhs) for j, m in enumerate(meshes)]
-    t = time.perf_counter()
-    srv.run(warm, realtime=False)
-    setup_s = time.perf_counter() - t
-    clocks = ClockSampler(0)
-    clocks.start()
-    t = time.perf_counter()
-    res = srv.run(reqs, realtime=True)
-    wall = time.perf_counter() - t
-    clk = clocks.stop()
-    rep = serve.report(res, wall)
-    srv.close()
-    # sequential plain-FP64 loop over the same requests (one slot, FP64 preconditioner)
-    seq = serve.Server(slots=1, precision=B.DG_PREC_FP64)
-    seq.run(warm, realtime=False)
-    t = time.perf_counter()
-    res_seq = seq.run(reqs, realtime=True)
-    wall_seq = time.perf_counter() - t
-    rep_seq = serve.report(res_seq, wall_seq)
-    seq.close()
-    out = {
-        "metric": "p50/p99 solve latency and DOF-iters/s (continuous-batching server)",
-        "value": rep["dof_iters_per_s"],
-        "unit": "DOF-iters/s",
-        "n_gpus": 1,
-        "steps": 1,
-        "warmup": 1,
-        "higher_is_better": True,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "f64 (outer PCG, operator) + f32 (preconditioner)",
-        "data": "synthetic",
-        "config": {"workload": SERVE_WORKLOAD.format(n=len(reqs), rate=args.serve_rate, m=len(meshes),
-                                                     slots=args.serve_slots)},
-        "p50_latency_s": rep["p50_latency_s"],
-        "p99_latency_s": rep["p99_latency_s"],
-        "ok": rep["ok"],
-        "wall_s": wall,
-        "max_inflight": srv.max_inflight,
-        "sequential_fp64": rep_seq,
-        "setup_s_all_meshes": setup_s,
-        "clocks": clk,
-    }
+    leg = run_serving_leg(B, args.serve_meshes, args.serve_requests, args.serve_rate, args.serve_slots)
+    out = {"metric": "p50/p99 solve latency and DOF-iters/s (continuous-batching server)",
+           "value": leg["value"], "unit": "DOF-iters/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64 (outer PCG, operator) + f32 (preconditioner)", "data": "synthetic",
+           "config": {"workload": leg.pop("workload")}, **{k: v for k, v in leg.items() if k != "value"}}
     print(json.dumps(out))
-
-
-BATCH_WORKLOAD = ("batched: {n} 2D hp-random problems (base N log-uniform in [4,64], prob 0.3, depth<=3, "
-                  "p~U{{1..8}}, 1k-300k DOFs each) x {r} seeded sine RHS, SIPG eta=100, tol 1e-8, one graph launch")
 
 
 def run_batched(args):
-    """Batched workload: many uneven problems x several right-hand sides in
-    one graph launch (every instance keeps its own PCG scalars)."""
     import torch
-
     from paper_2009_01287_gb300 import binding as B
-    from paper_2009_01287_gb300 import inputs
-
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    stream = torch.cuda.current_stream(dev)
-    meshes = [inputs.config3_problem(k)[0] for k in range(args.batch_problems)]
-    n_rhs = args.batch_rhs
-    prec = B.DG_PREC_FP64 if args.batch_fp64 else B.DG_PREC_MIXED
-    t0 = time.perf_counter()
-    bat = B.Batch(meshes, n_rhs=n_rhs, opts=B.make_options(precision=prec), stream=stream)
-    setup_s = time.perf_counter() - t0
-    b = torch.empty(bat.n_dofs, dtype=torch.float64, device=dev)
-    bat.rhs_sine([inputs.sine_rhs(2, 1000 + i) for i in range(bat.n_inst)], b, stream)
-    x = torch.empty_like(b)
-    for _ in range(args.warmup):
-        bat.solve(b, x, args.tol, 5000, stream)
-    clocks = ClockSampler(0)
-    clocks.start()
-    ms, dofit, iters = [], 0, []
-    sizes = [int(bat.offsets[i + 1] - bat.offsets[i]) for i in range(bat.n_inst)]
-    for _ in range(args.steps):
-        torch.cuda.synchronize()
-        res, t = bat.solve(b, x, args.tol, 5000, stream)
-        ms.append(t)
-        dofit += sum(n * r.iters for n, r in zip(sizes, res))
-        iters.append([r.iters for r in res])
-    clk = clocks.stop()
-    flat = [i for row in iters for i in row]
-    out = {
-        "metric": "DOF-iters/s (batched PCG, all instances in one graph launch)",
-        "value": dofit / (sum(ms) / 1e3),
-        "unit": "DOF-iters/s",
-        "n_gpus": 1,
-        "steps": args.steps,
-        "warmup": args.warmup,
-        "ms_per_step": statistics.mean(ms),
-        "higher_is_better": True,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "f64 (outer PCG, operator) + " + ("f64" if args.batch_fp64 else "f32") + " (preconditioner)",
-        "data": "synthetic",
-        "config": {"workload": BATCH_WORKLOAD.format(n=len(meshes), r=n_rhs), "instances": bat.n_inst,
-                   "total_dofs": bat.n_dofs, "l2": "vectors exceed L2 (no flush)"},
-        "iters_min_median_max": [min(flat), statistics.median(flat), max(flat)],
-        "setup_s": setup_s,
-        "clocks": clk,
-    }
+    ctx = Ctx(dev, torch.cuda.current_stream(dev))
+    leg = run_batched_leg(B, ctx, args.steps, args.warmup, args.batch_problems, args.batch_rhs, args.batch_fp64,
+                          tune=not args.batch_fixed_tiles)
+    out = {"metric": "DOF-iters/s (batched PCG, all instances in one graph launch)", "value": leg["value"],
+           "unit": "DOF-iters/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": leg["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": leg["dtype"], "data": "synthetic",
+           "config": {"workload": leg["workload"], "instances": leg["instances"], "total_dofs": leg["total_dofs"],
+                      "l2": leg["l2"]},
+           "iters_min_median_max": leg["iters_min_median_max"], "setup_s": leg["setup_s"], "tiles": leg["tiles"],
+           "clocks": leg["clocks"]}
     print(json.dumps(out))
-
-
-def _oracle_setup(seed: int, coef: bool = False):
-    from oracle import rhs, solver
-    from paper_2009_01287_gb300 import inputs
-    mesh, rh = inputs.config1_coeff(seed) if coef else inputs.config1(seed)
-    prob = solver.build_problem(mesh)
-    pc = solver.Preconditioner(prob, lor="amg")
-    b = rhs.load_vector(prob.space, rh.amps, rh.waves)
-    return prob, pc, b
-
-
-def _oracle_step(prob, pc, b, iters: int) -> float:
-    from oracle import solver
-    t = time.perf_counter()
-    solver.pcg(prob.A, b, pc.apply, 1e-30, iters)
-    return time.perf_counter() - t
-
-
-def cpu_baseline3(args):
-    """The oracle on a bounded sample of the 3D workload: the same refinement
-    and degree recipe on a 4^3 base (25k DOFs; the full 16^3 mesh is beyond the
-    oracle's setup), FP64 PCG iterations, one thread."""
-    prob, pc, b = _oracle_setup3(args.seed)
-    dt = _oracle_step(prob, pc, b, ORACLE_SAMPLE_ITERS)
-    return {"value": prob.space.n * ORACLE_SAMPLE_ITERS / dt, "unit": "DOF-iters/s", "cores": 1,
-            "kind": "oracle",
-            "sample": f"{ORACLE_SAMPLE_ITERS} FP64 PCG iterations on the same recipe with a 4^3 base "
-                      f"({prob.space.n} DOFs; setup untimed), scipy sparse + numpy, one thread"}
-
-
-def cpu_baseline(args, coef: bool = False):
-    prob, pc, b = _oracle_setup(args.seed, coef)
-    dt = _oracle_step(prob, pc, b, ORACLE_SAMPLE_ITERS)
-    return {"value": prob.space.n * ORACLE_SAMPLE_ITERS / dt, "unit": "DOF-iters/s", "cores": 1,
-            "kind": "oracle",
-            "sample": f"{ORACLE_SAMPLE_ITERS} FP64 PCG iterations of the same workload "
-                      f"(setup untimed), scipy sparse + numpy, one thread"}
-
-
-def _oracle_setup3(seed: int):
-    """The 3D recipe on a 4^3 base (the full 16^3 mesh is beyond the oracle's setup)."""
-    from oracle import rhs, solver
-    from paper_2009_01287_gb300 import inputs
-    mesh, rh = inputs.config2(seed, base=4)
-    prob = solver.build_problem(mesh, form="br2")
-    pc = solver.Preconditioner(prob, lor="amg")
-    b = rhs.load_vector(prob.space, rh.amps, rh.waves)
-    return prob, pc, b
 
 
 def run_reference(args):
@@ -505,10 +677,10 @@ def run_reference(args):
         return
     three = args.workload == "hp3d"
     coef = args.workload == "hp2d-coef"
-    prob, pc, b = _oracle_setup3(args.seed) if three else _oracle_setup(args.seed, coef)
+    prob, pc, b = _oracle_problem(args.workload, args.seed)
     for _ in range(args.warmup):
-        _oracle_step(prob, pc, b, ORACLE_SAMPLE_ITERS)
-    times = [_oracle_step(prob, pc, b, ORACLE_SAMPLE_ITERS) for _ in range(args.steps)]
+        _oracle_iters(prob, pc, b, ORACLE_SAMPLE_ITERS)
+    times = [_oracle_iters(prob, pc, b, ORACLE_SAMPLE_ITERS) for _ in range(args.steps)]
     n = prob.space.n
     value = n * ORACLE_SAMPLE_ITERS * args.steps / sum(times)
     sample = f"{ORACLE_SAMPLE_ITERS} FP64 PCG iterations per step"
@@ -543,25 +715,30 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="only the line's own workload")
     ap.add_argument("--workload", default="hp2d", choices=["hp2d", "hp2d-coef", "hp3d", "batched", "serving"])
-    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-meshes", type=int, default=16)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--batch-problems", type=int, default=256)
     ap.add_argument("--batch-rhs", type=int, default=4)
     ap.add_argument("--batch-fp64", action="store_true")
+    ap.add_argument("--batch-fixed-tiles", action="store_true", help="skip the tile tuner")
+    ap.add_argument("--oracle-leg", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-out", default="", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-solve", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
-    if args.workload == "batched" and args.impl == "ours":
-        run_batched(args)
-        return
-    if args.workload == "serving" and args.impl == "ours":
-        run_serving(args)
+    if args.oracle_leg:
+        oracle_leg_main(args)
         return
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 
