@@ -237,8 +237,11 @@ static void pcg_body(const dg_mesh* M, const dg_precond* pc, PcgWork& w, double*
                      double rtol2, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
   // the side traces of p were written with p (launch_pcg_p_trace)
   launch_apply(*M, w.p, w.q, Reduce{w.part_pq, w.sc + SC_PQ, w.tick + TK_PQ}, s, false);
-  launch_pcg_update_xr(x, w.r, w.p, w.q, w.n, w.sc, Reduce{w.part_rr, w.sc + SC_RRNEW, w.tick + TK_RR}, s);
-  launch_precond(*pc, w.r, w.z, Reduce{w.part_rz, w.sc + SC_RZNEW, w.tick + TK_RZ}, s);
+  // x += alpha p, r -= alpha q; r . r is summed by the preconditioner's final
+  // kernel beside r . z (one grid reduction fewer per iteration)
+  launch_pcg_update_xr(x, w.r, w.p, w.q, w.n, w.sc, Reduce{}, s);
+  launch_precond(*pc, w.r, w.z, Reduce{w.part_rz, w.sc + SC_RZNEW, w.tick + TK_RZ}, s, nullptr,
+                 Reduce{w.part_rr, w.sc + SC_RRNEW, nullptr});
   launch_pcg_p_trace(*M, w.p, w.z, w.sc, w.tick + TK_P, maxit, rtol2, (unsigned long long)h, use_cond, 0, s);
 }
 

@@ -227,7 +227,8 @@ block_solve_kernel(const int4* __restrict__ unit, const int64_t* __restrict__ ub
   }
 }
 
-// z = P e_C + D_J^-1 r + (block result on V_e nodes), and the r . z reduction.
+// z = P e_C + D_J^-1 r + (block result on V_e nodes), the r . z reduction and,
+// when rr is given, the r . r reduction beside it (the PCG residual norm).
 // G lanes per DG row share its P entries; the row's own terms (r, D_J^-1, the
 // block result) are loaded before the P entries so that both chains of loads
 // are in flight together.
@@ -237,14 +238,14 @@ precond_final_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict_
                      const T* __restrict__ val, const T* __restrict__ ec,
                      const T* __restrict__ dinv, const int32_t* __restrict__ e_pos,
                      const T* __restrict__ zE, const double* __restrict__ r,
-                     double* __restrict__ z, int64_t n, Reduce red) {
+                     double* __restrict__ z, int64_t n, Reduce red, Reduce rr) {
   pdl_entry();
   __shared__ double sred[kVecThreads];
   const int lane = threadIdx.x % G;
   const int64_t groups_per_grid = ((int64_t)gridDim.x * blockDim.x) / G;
   const int64_t g0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
   const int64_t rounds = (n + groups_per_grid - 1) / groups_per_grid;
-  double dot = 0.0;
+  double dot = 0.0, dot_rr = 0.0;
   for (int64_t rd = 0; rd < rounds; ++rd) {
     const int64_t i = g0 + rd * groups_per_grid;
     T s = 0, tj = 0, te = 0;
@@ -268,9 +269,14 @@ precond_final_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict_
       const double zi = (double)s;
       z[i] = zi;
       dot += zi * ri;
+      dot_rr += ri * ri;
     }
   }
-  if (red.partial) {
+  if (rr.partial) {
+    const double t1 = block_sum<kVecThreads>(dot, sred);
+    const double t2 = block_sum<kVecThreads>(dot_rr, sred);
+    reduce_finalize2<kVecThreads>(t1, t2, red, rr, sred);
+  } else if (red.partial) {
     const double tot = block_sum<kVecThreads>(dot, sred);
     reduce_finalize<kVecThreads>(tot, red, sred);
   }
@@ -383,7 +389,7 @@ static void vcycle(const dg_precond& pc, size_t l, cudaStream_t s) {
 
 template <typename T>
 static void precond_impl(const dg_precond& pc, const double* r, double* z, Reduce red,
-                         cudaStream_t s, const PrecondMarks* mk) {
+                         cudaStream_t s, const PrecondMarks* mk, Reduce rr) {
   // fork: the block solves depend only on r (profiling: run them first, alone)
   if (mk) DG_CUDA(cudaEventRecord(mk->ev[0], s));
   if (pc.n_blocks > 0) {
@@ -424,7 +430,7 @@ static void precond_impl(const dg_precond& pc, const double* r, double* z, Reduc
 #define DG_FINAL(G)                                                                          \
   launch_k(precond_final_kernel<T, G>, nb, kVecThreads, 0, s,                                      \
       pc.P.ptr, pc.P.idx, (const T*)pc.P.val, (const T*)ec, (const T*)pc.dinv, pc.e_pos,     \
-      (const T*)pc.zE, r, z, pc.n_dofs, red)
+      (const T*)pc.zE, r, z, pc.n_dofs, red, rr)
   // one lane per DG row: measured faster than 2 or 4 lanes (P has about five
   // entries per row; fewer rounds of dependent loads per thread count more)
   DG_FINAL(1);
@@ -484,9 +490,10 @@ int precond_kernel_count(const dg_precond& pc) {
 }
 
 void launch_precond(const dg_precond& pc, const double* r, double* z, Reduce red, cudaStream_t s,
-                    const PrecondMarks* marks) {
-  if (pc.precision == DG_PREC_MIXED) precond_impl<float>(pc, r, z, red, s, marks);
-  else precond_impl<double>(pc, r, z, red, s, marks);
+                    const PrecondMarks* marks, Reduce rr) {
+  DG_REQUIRE(!rr.partial || red.partial, "the r . r reduction rides on the r . z reduction");
+  if (pc.precision == DG_PREC_MIXED) precond_impl<float>(pc, r, z, red, s, marks, rr);
+  else precond_impl<double>(pc, r, z, red, s, marks, rr);
 }
 
 // ============================================================== PCG
@@ -534,7 +541,8 @@ pcg_update_xr_kernel(double* __restrict__ x, double* __restrict__ r, const doubl
     r[i] = ri;
     s += ri * ri;
   }
-  reduce_finalize<kVecThreads>(block_sum<kVecThreads>(s, red), rr, red);
+  // r . r here only when the preconditioner's final kernel does not sum it
+  if (rr.partial) reduce_finalize<kVecThreads>(block_sum<kVecThreads>(s, red), rr, red);
 }
 
 void launch_pcg_update_xr(double* x, double* r, const double* p, const double* q, int64_t n,

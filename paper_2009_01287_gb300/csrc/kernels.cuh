@@ -32,8 +32,9 @@ struct PrecondMarks {
   cudaEvent_t ev[5];
 };
 // z = B r (FP64 or mixed); optional reduction of r . z
+// (with rr: the r . r reduction as well, in the final kernel; needs red)
 void launch_precond(const dg_precond& pc, const double* r, double* z, Reduce red, cudaStream_t s,
-                    const PrecondMarks* marks = nullptr);
+                    const PrecondMarks* marks = nullptr, Reduce rr = Reduce{});
 // algorithmic bytes of one preconditioner apply (every matrix entry and vector
 // the kernels touch, read or written once) and of its block-solve kernel
 void precond_algorithmic_bytes(const dg_precond& pc, double* total, double* blocks);
