@@ -546,7 +546,7 @@ def run_ours(args):
     three = args.workload == "hp3d"
     coef = args.workload == "hp2d-coef"
     if three:
-        mesh, rh = inputs.config2(args.seed)
+        mesh, rh = inputs.config2(args.seed, base=args.base3)
     else:
         mesh, rh = inputs.config1_coeff(args.seed) if coef else inputs.config1(args.seed)
     form = B.DG_FORM_BR2 if three else B.DG_FORM_SIPG
@@ -726,6 +726,8 @@ def main():
     ap.add_argument("--batch-rhs", type=int, default=4)
     ap.add_argument("--batch-fp64", action="store_true")
     ap.add_argument("--batch-fixed-tiles", action="store_true", help="skip the tile tuner")
+    ap.add_argument("--base3", type=int, default=16,
+                    help="cube workload: base grid per axis (16 is the workload; smaller for profiling captures)")
     ap.add_argument("--oracle-leg", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-out", default="", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-solve", action="store_true", help=argparse.SUPPRESS)

@@ -125,10 +125,11 @@ __device__ __forceinline__ void reduce_finalize(double tot, const Reduce& R, dou
 }
 
 // Two sums finalised together: the ticket of R1 counts the CTAs; the last one
-// sums both partial arrays in CTA order into R1.out and R2.out.
+// sums both partial arrays in CTA order into R1.out and R2.out, returns true
+// (in every thread of that CTA) and leaves the sums in *v1_out, *v2_out.
 template <int NT>
-__device__ __forceinline__ void reduce_finalize2(double t1, double t2, const Reduce& R1, const Reduce& R2,
-                                                 double* red) {
+__device__ __forceinline__ bool reduce_finalize2(double t1, double t2, const Reduce& R1, const Reduce& R2,
+                                                 double* red, double* v1_out, double* v2_out) {
   __shared__ unsigned s_last2;
   if (threadIdx.x == 0) {
     R1.partial[blockIdx.x] = t1;
@@ -151,7 +152,11 @@ __device__ __forceinline__ void reduce_finalize2(double t1, double t2, const Red
       *R2.out = v2;
       *R1.ticket = 0u;
     }
+    *v1_out = v1;
+    *v2_out = v2;
+    return true;
   }
+  return false;
 }
 
 struct ApplyArgs {

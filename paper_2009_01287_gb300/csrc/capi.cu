@@ -240,9 +240,12 @@ static void pcg_body(const dg_mesh* M, const dg_precond* pc, PcgWork& w, double*
   // x += alpha p, r -= alpha q; r . r is summed by the preconditioner's final
   // kernel beside r . z (one grid reduction fewer per iteration)
   launch_pcg_update_xr(x, w.r, w.p, w.q, w.n, w.sc, Reduce{}, s);
+  // the final kernel's last CTA then sets beta, tests convergence, counts the
+  // iteration and sets the while condition (PcgCtl)
   launch_precond(*pc, w.r, w.z, Reduce{w.part_rz, w.sc + SC_RZNEW, w.tick + TK_RZ}, s, nullptr,
-                 Reduce{w.part_rr, w.sc + SC_RRNEW, nullptr});
-  launch_pcg_p_trace(*M, w.p, w.z, w.sc, w.tick + TK_P, maxit, rtol2, (unsigned long long)h, use_cond, 0, s);
+                 Reduce{w.part_rr, w.sc + SC_RRNEW, nullptr},
+                 PcgCtl{w.sc, maxit, rtol2, (unsigned long long)h, use_cond});
+  launch_pcg_p_trace(*M, w.p, w.z, w.sc, (unsigned long long)h, use_cond, 0, s);
 }
 
 // PCG start: x = 0, r = b, z = B r, p = z with its side traces, the initial
@@ -251,7 +254,7 @@ static void pcg_start_kernels(const dg_precond* pc, PcgWork& w, const double* b,
                               cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
   launch_pcg_init(b, x, w.r, w.n, Reduce{w.part_bb, w.sc + SC_BB, w.tick + TK_BB}, s);
   launch_precond(*pc, w.r, w.z, Reduce{w.part_rz, w.sc + SC_RZNEW, w.tick + TK_RZ}, s);
-  launch_pcg_p_trace(*pc->mesh, w.p, w.z, w.sc, w.tick + TK_P, 0, 0.0, (unsigned long long)h, use_cond, 1, s);
+  launch_pcg_p_trace(*pc->mesh, w.p, w.z, w.sc, (unsigned long long)h, use_cond, 1, s);
 }
 
 // host-driven start: the kernels above, then b . b read back (synchronises)

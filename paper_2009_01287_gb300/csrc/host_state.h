@@ -91,6 +91,11 @@ struct DevLevel {
   int64_t end_inv_entries = 0;
   void* b = nullptr;     // right-hand side of this level
   void* xo = nullptr;    // the level's output (after post-smoothing)
+  // Coarse fusion (single problem, composite level next to the dense
+  // coarsest level): W = (coarsest inverse) Rpre, row-major n_next x n, so the
+  // restriction and the coarse solve are one dense product xo_next = W b.
+  void* coarse_w = nullptr;
+  int64_t coarse_w_rows = 0;
 };
 
 }  // namespace dg

@@ -238,7 +238,7 @@ precond_final_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict_
                      const T* __restrict__ val, const T* __restrict__ ec,
                      const T* __restrict__ dinv, const int32_t* __restrict__ e_pos,
                      const T* __restrict__ zE, const double* __restrict__ r,
-                     double* __restrict__ z, int64_t n, Reduce red, Reduce rr) {
+                     double* __restrict__ z, int64_t n, Reduce red, Reduce rr, PcgCtl ctl) {
   pdl_entry();
   __shared__ double sred[kVecThreads];
   const int lane = threadIdx.x % G;
@@ -275,7 +275,24 @@ precond_final_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict_
   if (rr.partial) {
     const double t1 = block_sum<kVecThreads>(dot, sred);
     const double t2 = block_sum<kVecThreads>(dot_rr, sred);
-    reduce_finalize2<kVecThreads>(t1, t2, red, rr, sred);
+    double rz_new = 0.0, rr_new = 0.0;
+    if (reduce_finalize2<kVecThreads>(t1, t2, red, rr, sred, &rz_new, &rr_new) && ctl.sc &&
+        threadIdx.x == 0 && ctl.sc[SC_STATUS] == 0.0) {
+      // iteration control (PcgCtl): this iteration's r . z and r . r are final
+      // here; an iteration queued after a stop (host-driven loop) changes nothing
+      double* sc = ctl.sc;
+      const double it = sc[SC_IT] + 1.0;
+      sc[SC_IT] = it;
+      sc[SC_RR] = rr_new;
+      sc[SC_BETA] = rz_new / sc[SC_RZ];
+      sc[SC_RZ] = rz_new;
+      const double lim = ctl.maxit < 0 ? sc[SC_MAXIT] : (double)ctl.maxit;
+      const double tol2 = ctl.maxit < 0 ? sc[SC_RTOL2] : ctl.rtol2;
+      int cont = 1;
+      if (rr_new <= tol2 * sc[SC_BB]) { sc[SC_STATUS] = 1.0; cont = 0; }
+      else if (it >= lim) { sc[SC_STATUS] = 2.0; cont = 0; }
+      if (ctl.use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)ctl.cond, cont ? 1u : 0u);
+    }
   } else if (red.partial) {
     const double tot = block_sum<kVecThreads>(dot, sred);
     reduce_finalize<kVecThreads>(tot, red, sred);
@@ -339,6 +356,22 @@ static void launch_up(const DevLevel& L, const T* b, const T* xc, T* xo, cudaStr
 #undef DG_UP
 }
 
+// y = W x for a dense row-major m x n matrix, one CTA per row (fixed block
+// tree): the fused last restriction and coarsest solve of the V-cycle
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads)
+dense_rect_kernel(const T* __restrict__ W, const T* __restrict__ x, T* __restrict__ y, int64_t m, int64_t n) {
+  pdl_entry();
+  __shared__ double sred[kVecThreads];
+  for (int64_t row = blockIdx.x; row < m; row += gridDim.x) {
+    const T* w = W + row * n;
+    T s = 0;
+    for (int64_t j = threadIdx.x; j < n; j += kVecThreads) s += __ldg(w + j) * __ldg(x + j);
+    const double tot = block_sum<kVecThreads>((double)s, sred);
+    if (threadIdx.x == 0) y[row] = (T)tot;
+  }
+}
+
 // dense solves of the coarsest blocks of a level: block j covers level rows
 // [row[j], row[j+1]); blockIdx.y picks 8 rows of it (one per warp)
 template <typename T>
@@ -374,6 +407,13 @@ static void vcycle(const dg_precond& pc, size_t l, cudaStream_t s) {
     vcycle<T>(pc, l + 1, s);
     launch_rows<T>(L.P, OpCorr<T>{b, dinv, (const T*)C.xo, (T*)L.t2}, s);   // D^-1 b + P xc
     launch_rows<T>(L.A, OpPost<T>{(const T*)L.t2, b, dinv, (T*)L.xo}, s);   // post-smoothing
+  } else if (L.n_cont > 0 && L.coarse_w) {
+    // restriction and the dense coarsest solve in one product: C.xo = W b
+    const DevLevel& C = pc.levels[l + 1];
+    const int g = (int)std::min<int64_t>(L.coarse_w_rows, 8 * 152);
+    launch_k(dense_rect_kernel<T>, g, kVecThreads, 0, s, (const T*)L.coarse_w, (const T*)L.b, (T*)C.xo,
+             L.coarse_w_rows, L.n);
+    launch_up<T>(L, (const T*)L.b, (const T*)C.xo, (T*)L.xo, s);    // correction + smoothing
   } else if (L.n_cont > 0) {
     const DevLevel& C = pc.levels[l + 1];
     launch_rows<T>(L.Rpre, OpSpmv<T>{(const T*)L.b, (T*)C.b}, s);   // restrict b - A D^-1 b
@@ -389,7 +429,7 @@ static void vcycle(const dg_precond& pc, size_t l, cudaStream_t s) {
 
 template <typename T>
 static void precond_impl(const dg_precond& pc, const double* r, double* z, Reduce red,
-                         cudaStream_t s, const PrecondMarks* mk, Reduce rr) {
+                         cudaStream_t s, const PrecondMarks* mk, Reduce rr, PcgCtl ctl) {
   // fork: the block solves depend only on r (profiling: run them first, alone)
   if (mk) DG_CUDA(cudaEventRecord(mk->ev[0], s));
   if (pc.n_blocks > 0) {
@@ -430,7 +470,7 @@ static void precond_impl(const dg_precond& pc, const double* r, double* z, Reduc
 #define DG_FINAL(G)                                                                          \
   launch_k(precond_final_kernel<T, G>, nb, kVecThreads, 0, s,                                      \
       pc.P.ptr, pc.P.idx, (const T*)pc.P.val, (const T*)ec, (const T*)pc.dinv, pc.e_pos,     \
-      (const T*)pc.zE, r, z, pc.n_dofs, red, rr)
+      (const T*)pc.zE, r, z, pc.n_dofs, red, rr, ctl)
   // one lane per DG row: measured faster than 2 or 4 lanes (P has about five
   // entries per row; fewer rounds of dependent loads per thread count more)
   DG_FINAL(1);
@@ -463,10 +503,15 @@ void precond_algorithmic_bytes(const dg_precond& pc, double* total, double* bloc
         if (L.n_cont > 0 && L.plain)   // A twice, R, P; b, D^-1, two work vectors, the coarse vectors
           tot += 2.0 * csr_bytes(L.A, (size_t)T) + csr_bytes(L.R, (size_t)T) + csr_bytes(L.P, (size_t)T) +
                  T * (6.0 * nc + 2.0 * ncn);
+        else if (L.n_cont > 0 && L.coarse_w)   // W (dense), Sb, Sp; b read twice, xo, the coarse output
+          tot += T * (double)L.coarse_w_rows * (double)L.n + csr_bytes(L.Sb, (size_t)T) +
+                 csr_bytes(L.Sp, (size_t)T) + T * (3.0 * nc + ncn);
         else if (L.n_cont > 0)         // Rpre, Sb, Sp; b read twice, xo, the coarse vectors
           tot += csr_bytes(L.Rpre, (size_t)T) + csr_bytes(L.Sb, (size_t)T) + csr_bytes(L.Sp, (size_t)T) +
                  T * (3.0 * nc + 2.0 * ncn);
-        tot += T * (double)L.end_inv_entries + 2.0 * T * (double)(L.n - L.n_cont);   // dense coarse blocks
+        const bool fused_here = l > 0 && pc.levels[l - 1].coarse_w;
+        if (!fused_here)   // dense coarse blocks
+          tot += T * (double)L.end_inv_entries + 2.0 * T * (double)(L.n - L.n_cont);
       }
     }
   }
@@ -481,19 +526,23 @@ int precond_kernel_count(const dg_precond& pc) {
   if (pc.n_c > 0) {
     k += 1;                                // restriction
     if (pc.lor == DG_LOR_EXACT) return k + 1;
-    for (const DevLevel& L : pc.levels) {
+    for (size_t l = 0; l < pc.levels.size(); ++l) {
+      const DevLevel& L = pc.levels[l];
       if (L.n_cont > 0) k += L.plain ? 4 : 2;
-      if (L.n_end > 0 && L.max_end > 0) k += 1;
+      // a fused coarse product replaces the next level's dense solve
+      const bool skipped = l > 0 && pc.levels[l - 1].coarse_w;
+      if (L.n_end > 0 && L.max_end > 0 && !skipped) k += 1;
     }
   }
   return k;
 }
 
 void launch_precond(const dg_precond& pc, const double* r, double* z, Reduce red, cudaStream_t s,
-                    const PrecondMarks* marks, Reduce rr) {
+                    const PrecondMarks* marks, Reduce rr, PcgCtl ctl) {
   DG_REQUIRE(!rr.partial || red.partial, "the r . r reduction rides on the r . z reduction");
-  if (pc.precision == DG_PREC_MIXED) precond_impl<float>(pc, r, z, red, s, marks, rr);
-  else precond_impl<double>(pc, r, z, red, s, marks, rr);
+  DG_REQUIRE(!ctl.sc || rr.partial, "the iteration control needs the r . r reduction");
+  if (pc.precision == DG_PREC_MIXED) precond_impl<float>(pc, r, z, red, s, marks, rr, ctl);
+  else precond_impl<double>(pc, r, z, red, s, marks, rr, ctl);
 }
 
 // ============================================================== PCG
@@ -559,19 +608,10 @@ void launch_pcg_update_xr(double* x, double* r, const double* p, const double* q
 template <bool CUBE>
 __global__ void __launch_bounds__(kThreads)
 pcg_p_trace_kernel(const ApplyArgs A, double* __restrict__ p, const double* __restrict__ z, double* sc,
-                   unsigned* ticket, int maxit, double rtol2, cudaGraphConditionalHandle h, int use_cond,
-                   int first) {
+                   cudaGraphConditionalHandle h, int use_cond, int first) {
   pdl_entry();
-  __shared__ unsigned s_last;
-  __shared__ double s_beta;
-  if (!first && sc[SC_STATUS] != 0.0) {
-    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
-    return;
-  }
-  // one FP64 division per CTA, shared through shared memory
-  if (threadIdx.x == 0) s_beta = first ? 0.0 : sc[SC_RZNEW] / sc[SC_RZ];
-  __syncthreads();
-  const double beta = s_beta;
+  if (!first && sc[SC_STATUS] != 0.0) return;   // stopped: the loop condition is already clear
+  const double beta = first ? 0.0 : sc[SC_BETA];
   const ApplyTile T = A.tiles[blockIdx.x];
   const int np = T.p + 1;
   const int nn = CUBE ? np * np * np : np * np;
@@ -589,49 +629,25 @@ pcg_p_trace_kernel(const ApplyArgs A, double* __restrict__ p, const double* __re
 #undef DG_TRACE_CASE
     default: break;
   }
-  if (first) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      sc[SC_RZ] = sc[SC_RZNEW];
-      sc[SC_RR] = sc[SC_BB];
-      sc[SC_IT] = 0.0;
-      sc[SC_STATUS] = 0.0;
-      // a zero right-hand side needs no iteration (x = 0 is exact)
-      if (use_cond) cudaGraphSetConditional(h, sc[SC_BB] > 0.0 ? 1u : 0u);
-    }
-    return;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
-  }
-  __syncthreads();
-  if (s_last && threadIdx.x == 0) {
-    const double it = sc[SC_IT] + 1.0;
-    const double rr = sc[SC_RRNEW];
-    sc[SC_IT] = it;
-    sc[SC_RR] = rr;
+  if (first && blockIdx.x == 0 && threadIdx.x == 0) {
     sc[SC_RZ] = sc[SC_RZNEW];
-    const double lim = maxit < 0 ? sc[SC_MAXIT] : (double)maxit;
-    const double tol2 = maxit < 0 ? sc[SC_RTOL2] : rtol2;
-    int cont = 1;
-    if (rr <= tol2 * sc[SC_BB]) { sc[SC_STATUS] = 1.0; cont = 0; }
-    else if (it >= lim) { sc[SC_STATUS] = 2.0; cont = 0; }
-    *ticket = 0u;
-    if (use_cond) cudaGraphSetConditional(h, cont ? 1u : 0u);
+    sc[SC_RR] = sc[SC_BB];
+    sc[SC_IT] = 0.0;
+    sc[SC_STATUS] = 0.0;
+    // a zero right-hand side needs no iteration (x = 0 is exact)
+    if (use_cond) cudaGraphSetConditional(h, sc[SC_BB] > 0.0 ? 1u : 0u);
   }
 }
 
-void launch_pcg_p_trace(const dg_mesh& M, double* p, const double* z, double* sc, unsigned* ticket,
-                        int maxit, double rtol2, unsigned long long cond_handle, int use_cond, int first,
-                        cudaStream_t s) {
+void launch_pcg_p_trace(const dg_mesh& M, double* p, const double* z, double* sc,
+                        unsigned long long cond_handle, int use_cond, int first, cudaStream_t s) {
   if (M.n_tiles == 0) return;
   const ApplyArgs A = make_apply_args(M, p, nullptr, Reduce{});
   if (M.host.dim == 3)
-    launch_k(pcg_p_trace_kernel<true>, M.n_tiles, kThreads, 0, s, A, p, z, sc, ticket, maxit, rtol2,
+    launch_k(pcg_p_trace_kernel<true>, M.n_tiles, kThreads, 0, s, A, p, z, sc,
              (cudaGraphConditionalHandle)cond_handle, use_cond, first);
   else
-    launch_k(pcg_p_trace_kernel<false>, M.n_tiles, kThreads, 0, s, A, p, z, sc, ticket, maxit, rtol2,
+    launch_k(pcg_p_trace_kernel<false>, M.n_tiles, kThreads, 0, s, A, p, z, sc,
              (cudaGraphConditionalHandle)cond_handle, use_cond, first);
   DG_CUDA(cudaGetLastError());
 }

@@ -24,6 +24,26 @@ void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cuda
 // the side traces of x alone (the first of the two kernels of launch_apply)
 void launch_trace(const dg_mesh& M, const double* x, cudaStream_t s);
 
+// PCG scalar slots (doubles) and reduction tickets
+enum {
+  SC_RZ = 0, SC_BB = 1, SC_RR = 2, SC_IT = 3, SC_ALPHA = 4, SC_STATUS = 5,
+  SC_PQ = 6, SC_RZNEW = 7, SC_RRNEW = 8,
+  SC_MAXIT = 9, SC_RTOL2 = 10,   // iteration limit and tol^2, read when the launch passes maxit < 0
+  SC_BETA = 11,                  // beta of the p update, set with the convergence test
+  SC_COUNT = 16
+};
+
+// PCG iteration control run by the last CTA of the preconditioner's final
+// kernel once r . z and r . r are summed: beta = (r.z)_new / (r.z)_old, the
+// convergence test ||r|| <= tol ||b|| or the iteration limit, the iteration
+// count and the graph's while condition.  sc null: no control.
+struct PcgCtl {
+  double* sc = nullptr;
+  int maxit = 0;                    // < 0: limit and tol^2 from sc[SC_MAXIT], sc[SC_RTOL2]
+  double rtol2 = 0.0;
+  unsigned long long cond = 0;      // cudaGraphConditionalHandle
+  int use_cond = 0;
+};
 // Events recorded between the parts of a preconditioner apply: ev[0] start,
 // ev[1] after the block solves, ev[2] after the restriction, ev[3] after the
 // LOR solve, ev[4] after the final combination.  With marks the block solves
@@ -32,9 +52,10 @@ struct PrecondMarks {
   cudaEvent_t ev[5];
 };
 // z = B r (FP64 or mixed); optional reduction of r . z
-// (with rr: the r . r reduction as well, in the final kernel; needs red)
+// (with rr: the r . r reduction as well, in the final kernel; needs red; with
+// ctl.sc also the iteration control, see PcgCtl)
 void launch_precond(const dg_precond& pc, const double* r, double* z, Reduce red, cudaStream_t s,
-                    const PrecondMarks* marks = nullptr, Reduce rr = Reduce{});
+                    const PrecondMarks* marks = nullptr, Reduce rr = Reduce{}, PcgCtl ctl = PcgCtl{});
 // algorithmic bytes of one preconditioner apply (every matrix entry and vector
 // the kernels touch, read or written once) and of its block-solve kernel
 void precond_algorithmic_bytes(const dg_precond& pc, double* total, double* blocks);
@@ -42,25 +63,17 @@ int precond_final_blocks(const dg_precond& pc);
 // device kernel launches of one preconditioner apply
 int precond_kernel_count(const dg_precond& pc);
 
-// PCG scalar slots (doubles) and reduction tickets
-enum {
-  SC_RZ = 0, SC_BB = 1, SC_RR = 2, SC_IT = 3, SC_ALPHA = 4, SC_STATUS = 5,
-  SC_PQ = 6, SC_RZNEW = 7, SC_RRNEW = 8,
-  SC_MAXIT = 9, SC_RTOL2 = 10,   // iteration limit and tol^2, read when the launch passes maxit < 0
-  SC_COUNT = 16
-};
 enum { TK_PQ = 0, TK_RR = 1, TK_RZ = 2, TK_P = 3, TK_BB = 4, TK_COUNT = 8 };
 
 void launch_pcg_init(const double* b, double* x, double* r, int64_t n, Reduce bb, cudaStream_t s);
 void launch_pcg_update_xr(double* x, double* r, const double* p, const double* q, int64_t n,
                           double* sc, Reduce rr, cudaStream_t s);
 // p = z + beta p (first: p = z and the initial scalars) tile by tile, writing
-// the side traces of the new p for the next operator apply; the last CTA
-// advances the iteration, tests convergence and sets the graph's while condition
-// (first: the condition is b . b > 0).  maxit < 0: the limit and tol^2 are read
-// from sc[SC_MAXIT] and sc[SC_RTOL2], so a captured graph serves any tolerance.
-void launch_pcg_p_trace(const dg_mesh& M, double* p, const double* z, double* sc, unsigned* ticket,
-                        int maxit, double rtol2, unsigned long long cond_handle, int use_cond, int first,
-                        cudaStream_t s);
+// the side traces of the new p for the next operator apply.  beta comes from
+// sc[SC_BETA], set with the convergence test by the preconditioner's final
+// kernel (PcgCtl); after a stop the kernel does nothing.  First: the initial
+// scalars and, with use_cond, the loop condition b . b > 0.
+void launch_pcg_p_trace(const dg_mesh& M, double* p, const double* z, double* sc,
+                        unsigned long long cond_handle, int use_cond, int first, cudaStream_t s);
 
 }  // namespace dg

@@ -48,6 +48,9 @@ constexpr int kAmgDenseMax = 8192;    // largest coarsest level inverted densely
 // which pays when the level is bandwidth-bound); smaller levels, bound by
 // launch latency, keep the two-kernel composite form.
 constexpr int64_t kAmgPlainNnz = 4000000;
+// Largest product W = (coarsest inverse) Rpre (entries) that replaces the last
+// composite restriction and the dense coarsest solve by one dense product.
+constexpr int64_t kCoarseFuseMax = 4000000;
 
 AmgHierarchy amg_setup(const Csr& A, double theta = kAmgTheta);
 void dense_inverse_spd(int n, std::vector<double>& a);  // in place, Cholesky based

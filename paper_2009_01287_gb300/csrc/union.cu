@@ -213,6 +213,30 @@ void upload_union_precond(dg_precond* pc, const std::vector<InstSrc>& inst, cuda
     pc->stats.level_plain[l] = D.plain ? 1 : 0;
   }
   pc->stats.n_levels = (int)nlev;
+  // coarse fusion: the last composite restriction and the dense coarsest solve
+  // as one dense product (one launch fewer per V-cycle), when W is modest
+  if (inst.size() == 1 && nlev >= 2) {
+    const size_t l = nlev - 2;
+    DevLevel& D = pc->levels[l];
+    const DevLevel& C = pc->levels[nlev - 1];
+    const AmgHierarchy& H = *inst[0].A;
+    const Csr& R = H.levels[l].Rpre;   // C.n x D.n
+    if (!D.plain && D.n_cont == D.n && C.n_cont == 0 && C.n_end == 1 && R.rows == C.n && R.cols == D.n &&
+        (int64_t)H.coarse_inv.size() == C.n * C.n && C.n * D.n <= kCoarseFuseMax) {
+      const int64_t m = C.n, n = D.n;
+      std::vector<double> W((size_t)(m * n), 0.0);
+      for (int64_t i = 0; i < m; ++i) {
+        double* wi = W.data() + i * n;
+        for (int64_t k = 0; k < m; ++k) {
+          const double g = H.coarse_inv[(size_t)(i * m + k)];
+          if (g == 0.0) continue;
+          for (int64_t t = R.ptr[k]; t < R.ptr[k + 1]; ++t) wi[R.idx[t]] += g * R.val[t];
+        }
+      }
+      D.coarse_w = a.upload(std::vector<T>(W.begin(), W.end()), s);
+      D.coarse_w_rows = m;
+    }
+  }
   DG_CUDA(cudaStreamCreateWithFlags(&pc->side, cudaStreamNonBlocking));
   DG_CUDA(cudaEventCreateWithFlags(&pc->ev_fork, cudaEventDisableTiming));
   DG_CUDA(cudaEventCreateWithFlags(&pc->ev_join, cudaEventDisableTiming));
