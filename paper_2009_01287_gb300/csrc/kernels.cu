@@ -2,6 +2,7 @@
 // Jacobi, block solves) and the PCG vector work.  The operator's launch code
 // is in apply_launch.cu.
 #include <cstdio>
+#include <type_traits>
 
 #include "kernels.cuh"
 
@@ -363,10 +364,27 @@ __global__ void __launch_bounds__(kVecThreads)
 dense_rect_kernel(const T* __restrict__ W, const T* __restrict__ x, T* __restrict__ y, int64_t m, int64_t n) {
   pdl_entry();
   __shared__ double sred[kVecThreads];
+  // 16-byte loads when W and x start 16-byte aligned and a row holds a whole
+  // number of them (every row then starts aligned too)
+  constexpr int V = 16 / sizeof(T);
+  using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  const bool vec = n % V == 0 && ((reinterpret_cast<uintptr_t>(W) | reinterpret_cast<uintptr_t>(x)) & 15) == 0;
   for (int64_t row = blockIdx.x; row < m; row += gridDim.x) {
     const T* w = W + row * n;
     T s = 0;
-    for (int64_t j = threadIdx.x; j < n; j += kVecThreads) s += __ldg(w + j) * __ldg(x + j);
+    if (vec) {
+      const Vec* w4 = reinterpret_cast<const Vec*>(w);
+      const Vec* x4 = reinterpret_cast<const Vec*>(x);
+      for (int64_t j = threadIdx.x; j < n / V; j += kVecThreads) {
+        const Vec a = __ldg(w4 + j), b = __ldg(x4 + j);
+        const T* av = reinterpret_cast<const T*>(&a);
+        const T* bv = reinterpret_cast<const T*>(&b);
+#pragma unroll
+        for (int u = 0; u < V; ++u) s += av[u] * bv[u];
+      }
+    } else {
+      for (int64_t j = threadIdx.x; j < n; j += kVecThreads) s += __ldg(w + j) * __ldg(x + j);
+    }
     const double tot = block_sum<kVecThreads>((double)s, sred);
     if (threadIdx.x == 0) y[row] = (T)tot;
   }
