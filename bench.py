@@ -351,7 +351,9 @@ def measure_single(B, ctx, mesh, rh, form, steps, warmup, peaks, peak_tf, tkey, 
     out["true_rel_residual_mixed"] = float(torch.linalg.norm(rres - b) / torch.linalg.norm(b))
     if keep_x:
         out["_x"] = (x32.cpu().numpy(), x64.cpu().numpy())
-    out["kernels_per_iteration"] = 1 + 1 + int(pc32.stats.kernels_per_apply) + 1
+    # operator, the preconditioner's kernels (the x / r update rides its final
+    # kernel), the p update with the side traces
+    out["kernels_per_iteration"] = 1 + int(pc32.stats.kernels_per_apply) + 1
     for h in (pc32, pc64, M):
         h.close()
     return out

@@ -182,6 +182,7 @@ struct ApplyArgs {
   double* dot_partial;        // optional reduction of x . y (see Reduce)
   double* dot_out;
   unsigned* dot_ticket;
+  double* pcg_sc;             // PCG scalars: with the x . y sum, alpha = (r.z) / (p.q)
   const double* skip;         // batch: tiles whose instance has skip[inst * skip_stride] != 0 are idle
   int skip_stride;
   int n_tiles;

@@ -24,10 +24,20 @@ __global__ void __launch_bounds__(kThreads) trace_kernel(const ApplyArgs A) {
 }
 
 // End of a persistent operator launch: the last CTA to leave resets the tile
-// counter and sums the tile partials of x . y in tile order.
+// counter and sums the tile partials of x . y in tile order.  Inside PCG
+// (pcg_sc set, x = p, y = q) it also forms the step alpha = (r.z) / (p.q) once
+// for the kernels that apply the update r -= alpha q, x += alpha p (alpha = 0
+// once the solve has stopped: iterations queued after the stop change nothing).
 __device__ __forceinline__ void apply_exit(const ApplyArgs& A, double* red) {
   __shared__ unsigned s_last;
+  // the scalars alpha needs, loaded before the ticket so that their latency
+  // overlaps it (no kernel writes them while the operator runs)
+  double rz = 0.0, status = 0.0;
   if (threadIdx.x == 0) {
+    if (A.pcg_sc) {
+      rz = A.pcg_sc[SC_RZ];
+      status = A.pcg_sc[SC_STATUS];
+    }
     __threadfence();
     s_last = (atomicAdd(A.sched + 1, 1u) == gridDim.x - 1) ? 1u : 0u;
   }
@@ -38,7 +48,10 @@ __device__ __forceinline__ void apply_exit(const ApplyArgs& A, double* red) {
       double v = 0.0;
       for (int i = threadIdx.x; i < A.n_tiles; i += kThreads) v += __ldcg(A.dot_partial + i);
       v = block_sum<kThreads>(v, red);
-      if (threadIdx.x == 0) *A.dot_out = v;
+      if (threadIdx.x == 0) {
+        *A.dot_out = v;
+        if (A.pcg_sc) A.pcg_sc[SC_ALPHA] = status == 0.0 ? rz / v : 0.0;
+      }
     }
     if (threadIdx.x == 0) {
       A.sched[0] = 0u;
@@ -177,6 +190,7 @@ ApplyArgs make_apply_args(const dg_mesh& M, const double* x, double* y, Reduce r
   A.dot_partial = red.partial;
   A.dot_out = red.out;
   A.dot_ticket = red.ticket;
+  A.pcg_sc = nullptr;
   A.skip = M.skip_status;
   A.skip_stride = M.skip_stride;
   A.n_tiles = M.n_tiles;
@@ -225,9 +239,11 @@ void launch_trace(const dg_mesh& M, const double* x, cudaStream_t s) {
 }
 
 void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cudaStream_t s,
-                  bool with_trace) {
+                  bool with_trace, double* pcg_sc) {
   if (M.n_tiles == 0) return;
-  const ApplyArgs A = make_apply_args(M, x, y, red);
+  DG_REQUIRE(!pcg_sc || red.partial, "the PCG step needs the p . q reduction");
+  ApplyArgs A = make_apply_args(M, x, y, red);
+  A.pcg_sc = pcg_sc;
   const int grid = M.n_tiles < M.apply_grid ? M.n_tiles : M.apply_grid;
   if (M.host.dim == 3) {
     if (with_trace) launch_k(trace3_kernel, M.n_tiles, kThreads, 0, s, A);

@@ -235,16 +235,17 @@ static int64_t pcg_work_bytes(const dg_precond* pc) {
 
 static void pcg_body(const dg_mesh* M, const dg_precond* pc, PcgWork& w, double* x, int maxit,
                      double rtol2, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
-  // the side traces of p were written with p (launch_pcg_p_trace)
-  launch_apply(*M, w.p, w.q, Reduce{w.part_pq, w.sc + SC_PQ, w.tick + TK_PQ}, s, false);
-  // x += alpha p, r -= alpha q; r . r is summed by the preconditioner's final
-  // kernel beside r . z (one grid reduction fewer per iteration)
-  launch_pcg_update_xr(x, w.r, w.p, w.q, w.n, w.sc, Reduce{}, s);
-  // the final kernel's last CTA then sets beta, tests convergence, counts the
-  // iteration and sets the while condition (PcgCtl)
+  // q = A p (the side traces of p were written with p by launch_pcg_p_trace);
+  // the launch's last CTA sums p . q and forms alpha
+  launch_apply(*M, w.p, w.q, Reduce{w.part_pq, w.sc + SC_PQ, w.tick + TK_PQ}, s, false, w.sc);
+  // z = B (r - alpha q): the preconditioner's kernels read the updated
+  // residual on the fly and its final kernel stores it with x += alpha p (no
+  // launch of its own), sums r . z and r . r, and its last CTA sets beta,
+  // tests convergence, counts the iteration and sets the while condition
   launch_precond(*pc, w.r, w.z, Reduce{w.part_rz, w.sc + SC_RZNEW, w.tick + TK_RZ}, s, nullptr,
                  Reduce{w.part_rr, w.sc + SC_RRNEW, nullptr},
-                 PcgCtl{w.sc, maxit, rtol2, (unsigned long long)h, use_cond});
+                 PcgCtl{w.sc, maxit, rtol2, (unsigned long long)h, use_cond},
+                 XrDefer{w.r, x, w.p, w.q, w.sc + SC_ALPHA});
   launch_pcg_p_trace(*M, w.p, w.z, w.sc, (unsigned long long)h, use_cond, 0, s);
 }
 

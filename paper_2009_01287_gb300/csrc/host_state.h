@@ -60,6 +60,8 @@ inline int csr_group_for(double avg) {
 
 // rows with more entries than this are read by a whole CTA in the row kernels
 constexpr int kCsrCtaRow = 1024;
+// threads resident on the whole GPU at full occupancy (152 SMs x 2048)
+constexpr int64_t kResidentThreads = 152 * 2048;
 
 // the CTA and warp tiers of a CSR row kernel launch (see DevCsr)
 struct CsrTiers {

@@ -21,8 +21,9 @@ namespace dg {
 template <typename T, int G, class Op>
 __global__ void __launch_bounds__(kVecThreads)
 csr_rows_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-                const T* __restrict__ val, int64_t rows, CsrTiers tiers, Op op) {
+                const T* __restrict__ val, int64_t rows, CsrTiers tiers, const Op op_arg) {
   pdl_entry();
+  const Op op = op_arg.bind();   // per-thread values an operation loads once (after the wait)
   int bid = blockIdx.x;
   if (bid < tiers.n_cta) {
     __shared__ double sred[kVecThreads];
@@ -70,18 +71,36 @@ csr_rows_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx
   }
 }
 
+// Entry j of the residual a preconditioner kernel reads: r_j, or with a
+// deferred PCG update (XrDefer) r_j - alpha q_j, by the same FMA in every
+// kernel and in the final kernel that stores it.  r is not written while the
+// readers run (the final kernel stores it after they end).
+__device__ __forceinline__ double resid_in(const double* r, const double* q, double alpha, int64_t j) {
+  const double rj = __ldg(r + j);
+  return q ? fma(-alpha, __ldg(q + j), rj) : rj;
+}
+
 template <typename T>
 struct OpSpmv {  // y = A v
   const T* v;
   T* y;
+  __device__ OpSpmv bind() const { return *this; }
   __device__ T x(int j) const { return __ldg(v + j); }
   __device__ void store(int64_t i, T s) const { y[i] = s; }
 };
 template <typename T>
-struct OpRestrict {  // out = P^T r, r in FP64
+struct OpRestrict {  // out = P^T r, r in FP64 (with q: r - alpha q, see XrDefer)
   const double* r;
   T* out;
-  __device__ T x(int j) const { return (T)__ldg(r + j); }
+  const double* q = nullptr;
+  const double* alpha = nullptr;
+  double a = 0.0;   // *alpha, loaded once per thread by bind()
+  __device__ OpRestrict bind() const {
+    OpRestrict o = *this;
+    if (q) o.a = __ldg(alpha);
+    return o;
+  }
+  __device__ T x(int j) const { return (T)resid_in(r, q, a, j); }
   __device__ void store(int64_t i, T s) const { out[i] = s; }
 };
 // plain V-cycle level (D = diag(l1 row sums)):
@@ -90,6 +109,7 @@ struct OpResid {  // out = b - A D^-1 b (pre-smoothing from zero, then the resid
   const T* b;
   const T* dinv;
   T* out;
+  __device__ OpResid bind() const { return *this; }
   __device__ T x(int j) const { return __ldg(b + j) * __ldg(dinv + j); }
   __device__ void store(int64_t i, T s) const { out[i] = b[i] - s; }
 };
@@ -99,6 +119,7 @@ struct OpCorr {  // out = D^-1 b + P xc (pre-smoothed iterate plus coarse correc
   const T* dinv;
   const T* xc;
   T* out;
+  __device__ OpCorr bind() const { return *this; }
   __device__ T x(int j) const { return __ldg(xc + j); }
   __device__ void store(int64_t i, T s) const { out[i] = fma(b[i], dinv[i], s); }
 };
@@ -108,6 +129,7 @@ struct OpPost {  // out = xp + D^-1 (b - A xp) (post-smoothing)
   const T* b;
   const T* dinv;
   T* out;
+  __device__ OpPost bind() const { return *this; }
   __device__ T x(int j) const { return __ldg(xp + j); }
   __device__ void store(int64_t i, T s) const { out[i] = fma(dinv[i], b[i] - s, xp[i]); }
 };
@@ -159,6 +181,7 @@ template <typename T, int W>
 __device__ __forceinline__ void block_solve_packed(const int4 h, const int4* __restrict__ brec,
                                                    const int32_t* __restrict__ dofs,
                                                    const T* __restrict__ inv, const double* __restrict__ r,
+                                                   const double* __restrict__ q, double alpha,
                                                    T* __restrict__ zE, int lane) {
   const int seg = lane / W, rr = lane % W;
   const bool has = seg < h.y;   // h = {first block (sorted order), block count, 0, W}
@@ -166,7 +189,7 @@ __device__ __forceinline__ void block_solve_packed(const int4 h, const int4* __r
   const int d = br.y;
   const bool act = rr < d;
   const T* At = inv + ((int64_t)(unsigned)br.z | ((int64_t)br.w << 32)) + rr;
-  const T rv = act ? (T)__ldg(r + __ldg(dofs + br.x + rr)) : (T)0;
+  const T rv = act ? (T)resid_in(r, q, alpha, __ldg(dofs + br.x + rr)) : (T)0;
   T v[W];
 #pragma unroll
   for (int c = 0; c < W; ++c) v[c] = (act && c < d) ? __ldg(At + (int64_t)c * d) : (T)0;
@@ -190,24 +213,25 @@ template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 2 : 3)
 block_solve_kernel(const int4* __restrict__ unit, const int64_t* __restrict__ ubase,
                    const int4* __restrict__ brec, const int32_t* __restrict__ dofs,
-                   const T* __restrict__ inv, const double* __restrict__ r, T* __restrict__ zE,
-                   int nunits) {
+                   const T* __restrict__ inv, const double* __restrict__ r,
+                   const double* __restrict__ q, const double* alpha_p, T* __restrict__ zE, int nunits) {
   pdl_entry();
+  const double alpha = q ? __ldg(alpha_p) : 0.0;   // deferred PCG step (XrDefer)
   constexpr int H = 16;   // column loads per lane in one batch
   const int lane = threadIdx.x & 31;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nunits; u += nw) {
     const int4 h = __ldg(unit + u);   // panel: {slot of the block's first node, d, row0, 0}
-    if (h.w == 4) { block_solve_packed<T, 4>(h, brec, dofs, inv, r, zE, lane); continue; }
-    if (h.w == 8) { block_solve_packed<T, 8>(h, brec, dofs, inv, r, zE, lane); continue; }
-    if (h.w == 16) { block_solve_packed<T, 16>(h, brec, dofs, inv, r, zE, lane); continue; }
+    if (h.w == 4) { block_solve_packed<T, 4>(h, brec, dofs, inv, r, q, alpha, zE, lane); continue; }
+    if (h.w == 8) { block_solve_packed<T, 8>(h, brec, dofs, inv, r, q, alpha, zE, lane); continue; }
+    if (h.w == 16) { block_solve_packed<T, 16>(h, brec, dofs, inv, r, q, alpha, zE, lane); continue; }
     const int d = h.y, row = h.z + lane;
     const bool act = row < d;
     const T* At = inv + __ldg(ubase + u) + lane;   // column 0 of this lane's row
     const int32_t* ds = dofs + h.x;
     T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     for (int c0 = 0; c0 < d; c0 += 32) {
-      const T rv = c0 + lane < d ? (T)__ldg(r + __ldg(ds + c0 + lane)) : (T)0;
+      const T rv = c0 + lane < d ? (T)resid_in(r, q, alpha, __ldg(ds + c0 + lane)) : (T)0;
 #pragma unroll
       for (int hh = 0; hh < 32; hh += H) {
         const int cnt = d - c0 - hh;   // columns left from this half on
@@ -230,6 +254,8 @@ block_solve_kernel(const int4* __restrict__ unit, const int64_t* __restrict__ ub
 
 // z = P e_C + D_J^-1 r + (block result on V_e nodes), the r . z reduction and,
 // when rr is given, the r . r reduction beside it (the PCG residual norm).
+// With a deferred PCG update (xr.q) r is r - alpha q, stored here with
+// x += alpha p: every other reader of r has finished when this kernel runs.
 // G lanes per DG row share its P entries; the row's own terms (r, D_J^-1, the
 // block result) are loaded before the P entries so that both chains of loads
 // are in flight together.
@@ -238,8 +264,8 @@ __global__ void __launch_bounds__(kVecThreads, 8)
 precond_final_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
                      const T* __restrict__ val, const T* __restrict__ ec,
                      const T* __restrict__ dinv, const int32_t* __restrict__ e_pos,
-                     const T* __restrict__ zE, const double* __restrict__ r,
-                     double* __restrict__ z, int64_t n, Reduce red, Reduce rr, PcgCtl ctl) {
+                     const T* __restrict__ zE, const double* r,
+                     double* __restrict__ z, int64_t n, Reduce red, Reduce rr, PcgCtl ctl, XrDefer xr) {
   pdl_entry();
   __shared__ double sred[kVecThreads];
   const int lane = threadIdx.x % G;
@@ -254,7 +280,14 @@ precond_final_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict_
     bool has_e = false;
     if (i < n) {
       if (lane == 0) {
-        ri = __ldg(r + i);
+        if (xr.q) {   // r is rewritten below: plain loads
+          const double a = *xr.alpha;
+          ri = fma(-a, xr.q[i], r[i]);
+          xr.r_out[i] = ri;
+          xr.x[i] = fma(a, xr.p[i], xr.x[i]);
+        } else {
+          ri = __ldg(r + i);
+        }
         tj = __ldg(dinv + i) * (T)ri;
         const int ep = __ldg(e_pos + i);
         has_e = ep >= 0;
@@ -274,24 +307,35 @@ precond_final_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict_
     }
   }
   if (rr.partial) {
+    // the scalars the controller reads, loaded by thread 0 of every CTA before
+    // the reductions (their latency overlaps them; only the last CTA uses
+    // them, and no CTA writes them before every CTA has passed this point)
+    double c_status = 0.0, c_it = 0.0, c_rz = 0.0, c_bb = 0.0, c_lim = 0.0, c_tol2 = 0.0;
+    if (ctl.sc && threadIdx.x == 0) {
+      const double* sc = ctl.sc;
+      c_status = sc[SC_STATUS];
+      c_it = sc[SC_IT];
+      c_rz = sc[SC_RZ];
+      c_bb = sc[SC_BB];
+      c_lim = ctl.maxit < 0 ? sc[SC_MAXIT] : (double)ctl.maxit;
+      c_tol2 = ctl.maxit < 0 ? sc[SC_RTOL2] : ctl.rtol2;
+    }
     const double t1 = block_sum<kVecThreads>(dot, sred);
     const double t2 = block_sum<kVecThreads>(dot_rr, sred);
     double rz_new = 0.0, rr_new = 0.0;
     if (reduce_finalize2<kVecThreads>(t1, t2, red, rr, sred, &rz_new, &rr_new) && ctl.sc &&
-        threadIdx.x == 0 && ctl.sc[SC_STATUS] == 0.0) {
+        threadIdx.x == 0 && c_status == 0.0) {
       // iteration control (PcgCtl): this iteration's r . z and r . r are final
       // here; an iteration queued after a stop (host-driven loop) changes nothing
       double* sc = ctl.sc;
-      const double it = sc[SC_IT] + 1.0;
+      const double it = c_it + 1.0;
       sc[SC_IT] = it;
       sc[SC_RR] = rr_new;
-      sc[SC_BETA] = rz_new / sc[SC_RZ];
+      sc[SC_BETA] = rz_new / c_rz;
       sc[SC_RZ] = rz_new;
-      const double lim = ctl.maxit < 0 ? sc[SC_MAXIT] : (double)ctl.maxit;
-      const double tol2 = ctl.maxit < 0 ? sc[SC_RTOL2] : ctl.rtol2;
       int cont = 1;
-      if (rr_new <= tol2 * sc[SC_BB]) { sc[SC_STATUS] = 1.0; cont = 0; }
-      else if (it >= lim) { sc[SC_STATUS] = 2.0; cont = 0; }
+      if (rr_new <= c_tol2 * c_bb) { sc[SC_STATUS] = 1.0; cont = 0; }
+      else if (it >= c_lim) { sc[SC_STATUS] = 2.0; cont = 0; }
       if (ctl.use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)ctl.cond, cont ? 1u : 0u);
     }
   } else if (red.partial) {
@@ -447,7 +491,7 @@ static void vcycle(const dg_precond& pc, size_t l, cudaStream_t s) {
 
 template <typename T>
 static void precond_impl(const dg_precond& pc, const double* r, double* z, Reduce red,
-                         cudaStream_t s, const PrecondMarks* mk, Reduce rr, PcgCtl ctl) {
+                         cudaStream_t s, const PrecondMarks* mk, Reduce rr, PcgCtl ctl, XrDefer xr) {
   // fork: the block solves depend only on r (profiling: run them first, alone)
   if (mk) DG_CUDA(cudaEventRecord(mk->ev[0], s));
   if (pc.n_blocks > 0) {
@@ -460,7 +504,8 @@ static void precond_impl(const dg_precond& pc, const double* r, double* z, Reduc
     const int64_t gc = (pc.n_units + 7) / 8, gmax = (sizeof(T) == 8 ? 2 : 3) * 152;
     const int g = (int)(gc < gmax ? gc : gmax);
     launch_k(block_solve_kernel<T>, g, 256, 0, bs, (const int4*)pc.blk_unit, pc.blk_ubase,
-        (const int4*)pc.blk_rec, pc.blk_dofs, (const T*)pc.blk_inv, r, (T*)pc.zE, (int)pc.n_units);
+        (const int4*)pc.blk_rec, pc.blk_dofs, (const T*)pc.blk_inv, r, xr.q, xr.alpha, (T*)pc.zE,
+        (int)pc.n_units);
     DG_CUDA(cudaGetLastError());
     if (!mk) DG_CUDA(cudaEventRecord(pc.ev_join, pc.side));
   }
@@ -468,13 +513,13 @@ static void precond_impl(const dg_precond& pc, const double* r, double* z, Reduc
   const void* ec = nullptr;
   if (pc.n_c > 0) {
     if (pc.lor == DG_LOR_EXACT) {
-      launch_rows<T>(pc.PT, OpRestrict<T>{r, (T*)pc.rc}, s);
+      launch_rows<T>(pc.PT, OpRestrict<T>{r, (T*)pc.rc, xr.q, xr.alpha}, s);
       if (mk) DG_CUDA(cudaEventRecord(mk->ev[2], s));
       launch_k(dense_mv_kernel<T>, grid_for(pc.n_c * 32), kVecThreads, 0, s, 
           (const T*)pc.lor_inv, (const T*)pc.rc, (T*)pc.ec, pc.n_c);
       ec = pc.ec;
     } else {
-      launch_rows<T>(pc.PT, OpRestrict<T>{r, (T*)pc.levels[0].b}, s);
+      launch_rows<T>(pc.PT, OpRestrict<T>{r, (T*)pc.levels[0].b, xr.q, xr.alpha}, s);
       if (mk) DG_CUDA(cudaEventRecord(mk->ev[2], s));
       vcycle<T>(pc, 0, s);
       ec = pc.levels[0].xo;
@@ -488,7 +533,7 @@ static void precond_impl(const dg_precond& pc, const double* r, double* z, Reduc
 #define DG_FINAL(G)                                                                          \
   launch_k(precond_final_kernel<T, G>, nb, kVecThreads, 0, s,                                      \
       pc.P.ptr, pc.P.idx, (const T*)pc.P.val, (const T*)ec, (const T*)pc.dinv, pc.e_pos,     \
-      (const T*)pc.zE, r, z, pc.n_dofs, red, rr, ctl)
+      (const T*)pc.zE, r, z, pc.n_dofs, red, rr, ctl, xr)
   // one lane per DG row: measured faster than 2 or 4 lanes (P has about five
   // entries per row; fewer rounds of dependent loads per thread count more)
   DG_FINAL(1);
@@ -556,11 +601,13 @@ int precond_kernel_count(const dg_precond& pc) {
 }
 
 void launch_precond(const dg_precond& pc, const double* r, double* z, Reduce red, cudaStream_t s,
-                    const PrecondMarks* marks, Reduce rr, PcgCtl ctl) {
+                    const PrecondMarks* marks, Reduce rr, PcgCtl ctl, XrDefer xr) {
   DG_REQUIRE(!rr.partial || red.partial, "the r . r reduction rides on the r . z reduction");
   DG_REQUIRE(!ctl.sc || rr.partial, "the iteration control needs the r . r reduction");
-  if (pc.precision == DG_PREC_MIXED) precond_impl<float>(pc, r, z, red, s, marks, rr, ctl);
-  else precond_impl<double>(pc, r, z, red, s, marks, rr, ctl);
+  DG_REQUIRE(!xr.q || (xr.r_out == r && xr.x && xr.p && xr.alpha && !marks),
+             "a deferred PCG update needs r_out = r, x, p, alpha, and no profiling marks");
+  if (pc.precision == DG_PREC_MIXED) precond_impl<float>(pc, r, z, red, s, marks, rr, ctl, xr);
+  else precond_impl<double>(pc, r, z, red, s, marks, rr, ctl, xr);
 }
 
 // ============================================================== PCG
@@ -582,39 +629,6 @@ pcg_init_kernel(const double* __restrict__ b, double* __restrict__ x, double* __
 
 void launch_pcg_init(const double* b, double* x, double* r, int64_t n, Reduce bb, cudaStream_t s) {
   launch_k(pcg_init_kernel, grid_for(n), kVecThreads, 0, s, b, x, r, n, bb);
-  DG_CUDA(cudaGetLastError());
-}
-
-__global__ void __launch_bounds__(kVecThreads)
-pcg_update_xr_kernel(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
-                     const double* __restrict__ q, int64_t n, double* sc, Reduce rr) {
-  pdl_entry();
-  __shared__ double red[kVecThreads];
-  __shared__ double s_alpha;
-  if (sc[SC_STATUS] != 0.0) return;  // converged or stopped: iterations queued after it are no-ops
-  // an FP64 division is a sequence of FP64 instructions: one thread per CTA
-  // forms it, the others read it from shared memory
-  if (threadIdx.x == 0) {
-    s_alpha = sc[SC_RZ] / sc[SC_PQ];
-    if (blockIdx.x == 0) sc[SC_ALPHA] = s_alpha;
-  }
-  __syncthreads();
-  const double alpha = s_alpha;
-  double s = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] = fma(alpha, p[i], x[i]);
-    const double ri = fma(-alpha, q[i], r[i]);
-    r[i] = ri;
-    s += ri * ri;
-  }
-  // r . r here only when the preconditioner's final kernel does not sum it
-  if (rr.partial) reduce_finalize<kVecThreads>(block_sum<kVecThreads>(s, red), rr, red);
-}
-
-void launch_pcg_update_xr(double* x, double* r, const double* p, const double* q, int64_t n,
-                          double* sc, Reduce rr, cudaStream_t s) {
-  launch_k(pcg_update_xr_kernel, grid_for(n), kVecThreads, 0, s, x, r, p, q, n, sc, rr);
   DG_CUDA(cudaGetLastError());
 }
 

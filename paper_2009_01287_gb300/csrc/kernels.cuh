@@ -18,9 +18,11 @@ int64_t apply_smem_for(const dg_mesh& M);
 
 ApplyArgs make_apply_args(const dg_mesh& M, const double* x, double* y, Reduce red);
 // y = A x; with_trace = false when the side traces of x are already in place
-// (written by launch_pcg_p_trace)
+// (written by launch_pcg_p_trace).  pcg_sc (PCG scalars, needs red): the
+// launch's last CTA also sets sc[SC_ALPHA] = sc[SC_RZ] / (x . y), or 0 once
+// sc[SC_STATUS] is set.
 void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cudaStream_t s,
-                  bool with_trace = true);
+                  bool with_trace = true, double* pcg_sc = nullptr);
 // the side traces of x alone (the first of the two kernels of launch_apply)
 void launch_trace(const dg_mesh& M, const double* x, cudaStream_t s);
 
@@ -51,11 +53,26 @@ struct PcgCtl {
 struct PrecondMarks {
   cudaEvent_t ev[5];
 };
+// The PCG update of this iteration, deferred into the preconditioner: its
+// kernels read the residual as r - alpha q (formed on the fly, the same FMA
+// everywhere), and the final kernel, which runs after every other reader of
+// r, stores it to r_out (the vector r itself) and sets x += alpha p.  alpha is
+// the device scalar written by the operator launch (launch_apply with pcg_sc).
+// q null: r as given.
+struct XrDefer {
+  double* r_out = nullptr;
+  double* x = nullptr;
+  const double* p = nullptr;
+  const double* q = nullptr;
+  const double* alpha = nullptr;
+};
 // z = B r (FP64 or mixed); optional reduction of r . z
 // (with rr: the r . r reduction as well, in the final kernel; needs red; with
-// ctl.sc also the iteration control, see PcgCtl)
+// ctl.sc also the iteration control, see PcgCtl; with xr.q the residual is
+// r - alpha q and is written back, see XrDefer)
 void launch_precond(const dg_precond& pc, const double* r, double* z, Reduce red, cudaStream_t s,
-                    const PrecondMarks* marks = nullptr, Reduce rr = Reduce{}, PcgCtl ctl = PcgCtl{});
+                    const PrecondMarks* marks = nullptr, Reduce rr = Reduce{}, PcgCtl ctl = PcgCtl{},
+                    XrDefer xr = XrDefer{});
 // algorithmic bytes of one preconditioner apply (every matrix entry and vector
 // the kernels touch, read or written once) and of its block-solve kernel
 void precond_algorithmic_bytes(const dg_precond& pc, double* total, double* blocks);
@@ -66,8 +83,6 @@ int precond_kernel_count(const dg_precond& pc);
 enum { TK_PQ = 0, TK_RR = 1, TK_RZ = 2, TK_P = 3, TK_BB = 4, TK_COUNT = 8 };
 
 void launch_pcg_init(const double* b, double* x, double* r, int64_t n, Reduce bb, cudaStream_t s);
-void launch_pcg_update_xr(double* x, double* r, const double* p, const double* q, int64_t n,
-                          double* sc, Reduce rr, cudaStream_t s);
 // p = z + beta p (first: p = z and the initial scalars) tile by tile, writing
 // the side traces of the new p for the next operator apply.  beta comes from
 // sc[SC_BETA], set with the convergence test by the preconditioner's final

@@ -198,8 +198,12 @@ void upload_union_precond(dg_precond* pc, const std::vector<InstSrc>& inst, cuda
       upload_csr_t<T>(a, Sp, D.Sp, s);
       upload_csr_t<T>(a, Rp, D.Rpre, s);
       // lanes per row of the fused up-sweep: half the power of two below the
-      // mean length of both operators' rows together (measured faster)
-      D.Sb.group_all = std::max(1, csr_group_for(ncont[l] ? (double)(Sb.nnz() + Sp.nnz()) / (double)ncont[l] : 1.0) / 2);
+      // mean length of both operators' rows together (measured faster), and
+      // on a level too small to fill the GPU at that width (rows x lanes under
+      // the resident threads of 152 SMs) twice that, up to a warp per row
+      int g = std::max(1, csr_group_for(ncont[l] ? (double)(Sb.nnz() + Sp.nnz()) / (double)ncont[l] : 1.0) / 2);
+      while (g < 32 && ncont[l] * (int64_t)g < kResidentThreads) g *= 2;
+      D.Sb.group_all = g;
     }
     D.n_end = (int)end_off.size();
     D.end_row = a.upload(end_row, s);
