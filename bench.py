@@ -298,13 +298,14 @@ def precond_rooflines(B, ctx, pc, peaks):
 
 
 def measure_single(B, ctx, mesh, rh, form, steps, warmup, peaks, peak_tf, tkey, three=False,
-                   e2e=False, keep_x=False):
+                   e2e=False, keep_x=False, tune=False):
     """Mixed and FP64 solves of one workload, its kernels' rooflines."""
     torch = ctx.torch
     opts64 = B.make_options(form=form, precision=B.DG_PREC_FP64, lor=B.DG_LOR_AMG)
     opts32 = B.make_options(form=form, precision=B.DG_PREC_MIXED, lor=B.DG_LOR_AMG)
     t0 = time.perf_counter()
-    M = B.Mesh(mesh, opts64, ctx.stream)
+    M = B.Mesh(mesh, B.make_options(form=form, precision=B.DG_PREC_FP64, lor=B.DG_LOR_AMG,
+                                    tune_tiles=1 if tune else 0), ctx.stream)
     pc32 = B.Precond(M, opts32)
     setup_s = time.perf_counter() - t0
     pc64 = B.Precond(M, opts64)
@@ -330,6 +331,12 @@ def measure_single(B, ctx, mesh, rh, form, steps, warmup, peaks, peak_tf, tkey, 
                        "n_blocks": int(pc32.stats.n_blocks), "max_block": int(pc32.stats.max_block),
                        "kernels_per_apply": int(pc32.stats.kernels_per_apply),
                        "device_bytes": int(pc32.stats.device_bytes)}}
+    ms = M.stats
+    out["tiles"] = {"tuned": bool(ms.tiles_tuned),
+                    "elements_per_tile_by_degree": None if three else list(ms.tile_elems)[1:],
+                    "smem_budget_bytes": int(ms.tile_smem_budget) if three else None,
+                    "apply_ms_fixed": ms.apply_ms_fixed if ms.tiles_tuned else None,
+                    "apply_ms_tuned": ms.apply_ms_tuned if ms.tiles_tuned else None}
     if e2e:
         bh = b.cpu().pin_memory()
         xh = torch.zeros(n, dtype=torch.float64).pin_memory()
@@ -561,7 +568,7 @@ def run_ours(args):
         dist.barrier()
     res = measure_single(B, ctx, mesh, rh, form, args.steps, args.warmup, peaks, probe["tflops"],
                          "apply3_kernel/hp3d" if three else ("apply_kernel/hp2d" if not coef else "none"),
-                         three=three, e2e=True, keep_x=True)
+                         three=three, e2e=True, keep_x=True, tune=args.tune_tiles)
     ms32, it32, ms64, it64 = res.pop("_raw")
     t_e2e, it_e2e = res.pop("_e2e")
     x32, x64 = res.pop("_x")
@@ -601,6 +608,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
         "roofline": res["roofline"],
         "rooflines": res["rooflines"],
+        "tiles": res["tiles"],
         "fp64_peak_tflops_measured": probe["tflops"],
         "gpu_launches": launches,
         "clocks": res["clocks"],
@@ -731,6 +739,8 @@ def main():
     ap.add_argument("--batch-rhs", type=int, default=4)
     ap.add_argument("--batch-fp64", action="store_true")
     ap.add_argument("--batch-fixed-tiles", action="store_true", help="skip the tile tuner")
+    ap.add_argument("--tune-tiles", action="store_true",
+                    help="single-mesh workloads: let dg_mesh_create tune the operator's tiles")
     ap.add_argument("--base3", type=int, default=16,
                     help="cube workload: base grid per axis (16 is the workload; smaller for profiling captures)")
     ap.add_argument("--oracle-leg", action="store_true", help=argparse.SUPPRESS)

@@ -149,7 +149,9 @@ typedef struct {
   int32_t tiles_tuned;    /* 1: chosen by timing (dg_options.tune_tiles)        */
   double apply_ms_fixed;  /* when tuned: the operator kernel's time with the
                              fixed rule ...                                      */
-  double apply_ms_tuned;  /* ... and with the chosen tiles (CUDA events, warm)  */
+  double apply_ms_tuned;  /* ... and with the chosen tiles (CUDA events around
+                             a graph of 20 launches, as a solve runs them,
+                             warm, best of 3, per launch)                       */
 } dg_mesh_stats;
 
 /* Build the mesh topology (sub-faces, hanging vertices, master edges) and
