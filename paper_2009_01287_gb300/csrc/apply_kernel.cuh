@@ -37,17 +37,20 @@
 
 namespace dg {
 
-// Programmatic dependent launch: every kernel lets the next kernel in its
-// stream start launching at once, then waits until its own predecessor has
-// completed (with its memory visible) before touching any data.  Launch
-// latency of the next kernel thus overlaps this kernel's execution.  Without
-// the launch attribute (graph captures) both instructions are no-ops.
-__device__ __forceinline__ void pdl_entry() {
+// Programmatic dependent launch.  Every kernel waits at entry until the
+// kernels it depends on have completed with their memory visible
+// (pdl_entry), and lets its dependents start launching once each of its CTAs
+// has done its main work (pdl_trigger, or the CTA's exit): the next kernel's
+// launch and CTA dispatch then overlap this kernel's stores and its
+// reduction tail.  The wait alone orders the data, wherever the trigger is.
+// Without the launch attribute both instructions are no-ops.
+__device__ __forceinline__ void pdl_entry() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
-// kernel launch with programmatic stream serialisation allowed
+// kernel launch with programmatic stream serialisation allowed (captured into
+// a graph, it becomes a programmatic edge from the kernel before it)
 template <typename... KArgs, typename... Args>
 inline void launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                      Args&&... args) {
@@ -60,10 +63,7 @@ inline void launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  // inside a CUDA graph capture plain edges measured faster: no attribute there
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  cudaStreamIsCapturing(s, &cs);
-  cfg.numAttrs = (cs == cudaStreamCaptureStatusActive) ? 0 : 1;
+  cfg.numAttrs = 1;
   DG_CUDA(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...));
 }
 

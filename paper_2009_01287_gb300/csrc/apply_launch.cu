@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(kThreads) trace_kernel(const ApplyArgs A) {
 // once the solve has stopped: iterations queued after the stop change nothing).
 __device__ __forceinline__ void apply_exit(const ApplyArgs& A, double* red) {
   __shared__ unsigned s_last;
+  pdl_trigger();   // this CTA's tiles are done: the next kernel may start launching
   // the scalars alpha needs, loaded before the ticket so that their latency
   // overlaps it (no kernel writes them while the operator runs)
   double rz = 0.0, status = 0.0;

@@ -31,6 +31,7 @@ csr_rows_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx
     const int e = ptr[row + 1];
     T s = 0;
     for (int t = ptr[row] + threadIdx.x; t < e; t += kVecThreads) s += __ldg(val + t) * op.x(__ldg(idx + t));
+    pdl_trigger();
     const double tot = block_sum<kVecThreads>((double)s, sred);
     if (threadIdx.x == 0) op.store(row, (T)tot);
     return;
@@ -306,6 +307,7 @@ precond_final_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict_
       dot_rr += ri * ri;
     }
   }
+  pdl_trigger();   // rows done: the next kernel launches during the reductions
   if (rr.partial) {
     // the scalars the controller reads, loaded by thread 0 of every CTA before
     // the reductions (their latency overlaps them; only the last CTA uses
@@ -624,6 +626,7 @@ pcg_init_kernel(const double* __restrict__ b, double* __restrict__ x, double* __
     r[i] = bi;
     s += bi * bi;
   }
+  pdl_trigger();
   reduce_finalize<kVecThreads>(block_sum<kVecThreads>(s, red), bb, red);
 }
 
