@@ -253,6 +253,11 @@ block_solve_kernel(const int4* __restrict__ unit, const int64_t* __restrict__ ub
   }
 }
 
+// CTAs of the final kernel resident per SM: its launch bound (48 registers,
+// no spills; 8 per SM would cap it at 32 registers and spill) and its grid
+// cap (one wave on 152 SMs)
+constexpr int kFinalCtasPerSm = 5;
+
 // z = P e_C + D_J^-1 r + (block result on V_e nodes), the r . z reduction and,
 // when rr is given, the r . r reduction beside it (the PCG residual norm).
 // With a deferred PCG update (xr.q) r is r - alpha q, stored here with
@@ -261,7 +266,7 @@ block_solve_kernel(const int4* __restrict__ unit, const int64_t* __restrict__ ub
 // block result) are loaded before the P entries so that both chains of loads
 // are in flight together.
 template <typename T, int G>
-__global__ void __launch_bounds__(kVecThreads, 8)
+__global__ void __launch_bounds__(kVecThreads, kFinalCtasPerSm)
 precond_final_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
                      const T* __restrict__ val, const T* __restrict__ ec,
                      const T* __restrict__ dinv, const int32_t* __restrict__ e_pos,
@@ -355,7 +360,7 @@ static int grid_for(int64_t n, int threads = kVecThreads) {
 
 int precond_final_blocks(const dg_precond& pc) {
   int64_t b = (pc.n_dofs + kVecThreads - 1) / kVecThreads;   // one lane per row
-  if (b > kVecBlocks) b = kVecBlocks;
+  if (b > kFinalCtasPerSm * 152) b = kFinalCtasPerSm * 152;   // one resident wave
   return (int)(b < 1 ? 1 : b);
 }
 
