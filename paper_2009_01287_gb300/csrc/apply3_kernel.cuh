@@ -14,8 +14,9 @@
 //            whose face-mass matrices are Kronecker products of 1D tables (first
 //            tangential axis a, second b), so every face product is two 1D
 //            contractions, one pass over all items of the chunk each, with a
-//            barrier between them; a third pass adds each item's partials to
-//            its side nodes in sub-face order (deterministic):
+//            barrier between them (a chunk's items sorted by the branches they
+//            take, so that warps split less); a third pass adds each item's
+//            partials to its side nodes in sub-face order (deterministic):
 //              a = M_oo u-, c = M_oo dn-, b = M_on u+, d = M_on dn+
 //            and, for SIPG, side residual += area (sigma (a - b) - (c - d) / 2)
 //            and normal-derivative coefficient c2 -= area (a - b) / 2
@@ -157,9 +158,9 @@ __device__ __forceinline__ void apply3_tile(const ApplyArgs& A, const ApplyTile&
     for (int t = tid; t < nc * WQ; t += blockDim.x) {
       const int it = t / WQ, q = t - it * WQ;
       const int i = q % NP, n = q / NP;
-      const int2 item = A.items[ib + c0 + it];
+      const int2 item = A.items[ib + c0 + it];   // chunk-sorted (see the tile build)
       const SubFaceRec3& f = A.sf3[item.x];
-      const int e = item.y / 6, s = item.y - e * 6;
+      const int es = item.y & 0xffff, e = es / 6, s = es - e * 6;
       const int k = A.order[T.first + e];
       const int np = f.pn + 1;
       const bool in = f.nb >= 0;
@@ -295,8 +296,9 @@ __device__ __forceinline__ void apply3_tile(const ApplyArgs& A, const ApplyTile&
       }
       if (BR2) rr += f.cz * (zz - vv) + f.cx * (xx - yy);
       else rr = fma(f.sigma * ar, jmp, rr);
-      sp[it * 2 * N2 + q] = rr;
-      sp[it * 2 * N2 + N2 + q] = cc;
+      const int pos = item.y >> 16;   // the item's position in sub-face order
+      sp[pos * 2 * N2 + q] = rr;
+      sp[pos * 2 * N2 + N2 + q] = cc;
     }
     __syncthreads();
     // P3: every side node adds the partials of its items in this chunk, in order

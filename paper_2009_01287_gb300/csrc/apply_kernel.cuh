@@ -301,9 +301,9 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& 
     double2* part = reinterpret_cast<double2*>(sm + S::PART);   // [nit][NP]
     for (int t = tid; t < nit * NP; t += blockDim.x) {
       const int it = t / NP, i = t - it * NP;
-      const int2 item = A.items[ib + it];
+      const int2 item = A.items[ib + it];   // sorted by branch; item.y >> 16: sub-face order
       const SubFaceRec f = A.sf[item.x];
-      const int e = item.y >> 2, s = item.y & 3;
+      const int e = (item.y & 0xffff) >> 2, s = item.y & 3;
       const int k = A.order[T.first + e];
       const double2* trk = reinterpret_cast<const double2*>(A.tr + A.toff[k]) + s * NP;
       const double* Moo = A.tab + f.tab_oo + i * NP;
@@ -334,7 +334,7 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& 
         r = f.len * (f.sigma * jmp - 0.5 * (c - d));
         c2 = -0.5 * f.len * jmp;
       }
-      part[t] = make_double2(r, c2);
+      part[(item.y >> 16) * NP + i] = make_double2(r, c2);
     }
     __syncthreads();
     for (int t = tid; t < nside; t += blockDim.x) {

@@ -121,7 +121,8 @@ struct dg_mesh {
   // square meshes, SIPG: the sub-face work of every tile as a flat list of
   // (record, tile-local side) items, and per element side (in tile order) the
   // first item and the item count
-  std::vector<int32_t> h_items;       // 2 per item: record index, e_local * 4 + s
+  std::vector<int32_t> h_items;       // 2 per item: record index, and (e_local * 4 + s, cubes
+                                      // e_local * 6 + s) | (position in sub-face order << 16)
   std::vector<int32_t> h_item_ptr;    // n_tiles + 1
   std::vector<int32_t> h_side_items;  // 2 per (order position, side): first item, count
   int64_t apply_smem = 0;             // dynamic shared memory of the 2D operator kernel

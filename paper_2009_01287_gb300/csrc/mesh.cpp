@@ -243,6 +243,28 @@ void build_face_items(dg_mesh* M) {
         }
       }
     }
+    // The tile's items in the order of the branches their threads take -
+    // interior first, by neighbour degree (the loop bound), then the boundary
+    // - so that a warp of the face pass spans fewer kinds of item.  The high
+    // half of the side field keeps the item's position in sub-face order,
+    // where the face pass writes its partials (the side sums read them there).
+    const int64_t t0 = M->h_item_ptr.back(), t1 = (int64_t)M->h_items.size() / 2;
+    DG_REQUIRE(t1 - t0 < 65536, "operator tile: too many sub-face items");
+    std::vector<std::pair<int32_t, int32_t>> key;   // (branch key, position in the tile)
+    for (int64_t g = t0; g < t1; ++g) {
+      const SubFaceRec& f = M->h_sf[M->h_items[2 * g]];
+      key.push_back({f.nb >= 0 ? 16 - f.pn : 32, (int32_t)(g - t0)});
+    }
+    std::stable_sort(key.begin(), key.end(),
+                     [](const std::pair<int32_t, int32_t>& a, const std::pair<int32_t, int32_t>& b) {
+                       return a.first < b.first;
+                     });
+    const std::vector<int32_t> rec(M->h_items.begin() + 2 * t0, M->h_items.end());
+    for (int64_t g = t0; g < t1; ++g) {
+      const int32_t pos = key[g - t0].second;
+      M->h_items[2 * g] = rec[2 * pos];
+      M->h_items[2 * g + 1] = rec[2 * pos + 1] | (pos << 16);
+    }
     M->h_item_ptr.push_back((int32_t)(M->h_items.size() / 2));
   }
 }

@@ -177,6 +177,39 @@ void build_tiles3(dg_mesh* M) {
         }
       }
     }
+    // Within each chunk the items go in the order of the branches their
+    // threads take - interior first, then the BR2 whole-face flags, then the
+    // neighbour degree (the loop bound) - so that a warp of the two
+    // contraction passes spans fewer kinds of item.  The high half of the
+    // side field keeps the item's position in sub-face order: the second pass
+    // writes the item's partials there, and the third adds them in that order.
+    {
+      const int64_t t0 = M->h_item_ptr.back(), t1 = (int64_t)M->h_items.size() / 2;
+      DG_REQUIRE(T.chunk < 65536, "3D operator: sub-face chunk too long");
+      std::vector<std::pair<int32_t, int32_t>> key;   // (branch key, position in the chunk)
+      std::vector<int32_t> rec, side;
+      for (int64_t c0 = t0; c0 < t1; c0 += T.chunk) {
+        const int64_t c1 = std::min<int64_t>(c0 + T.chunk, t1);
+        key.clear();
+        rec.assign(M->h_items.begin() + 2 * c0, M->h_items.begin() + 2 * c1);
+        for (int64_t g = c0; g < c1; ++g) {
+          const SubFaceRec3& f = M->h_sf3[M->h_items[2 * g]];
+          const bool in = f.nb >= 0;
+          const int zv = (br2 && !(f.full & 1)) ? 1 : 0, yy = (br2 && in && !(f.full & 2)) ? 1 : 0;
+          key.push_back({((in ? 0 : 1) << 12) | (zv << 11) | (yy << 10) | (in ? 16 - f.pn : 0),
+                         (int32_t)(g - c0)});
+        }
+        std::stable_sort(key.begin(), key.end(),
+                         [](const std::pair<int32_t, int32_t>& a, const std::pair<int32_t, int32_t>& b) {
+                           return a.first < b.first;
+                         });
+        for (int64_t g = c0; g < c1; ++g) {
+          const int32_t pos = key[g - c0].second;
+          M->h_items[2 * g] = rec[2 * pos];
+          M->h_items[2 * g + 1] = rec[2 * pos + 1] | (pos << 16);
+        }
+      }
+    }
     M->h_item_ptr.push_back((int32_t)(M->h_items.size() / 2));
     M->h_tiles.push_back(T);
     M->apply3_smem = std::max<int64_t>(M->apply3_smem, 8LL * (fixed + T.chunk * item_per));
