@@ -22,7 +22,7 @@ Beside it the same line carries
                 16^3 cube workload, the batched form (256 problems x 4
                 right-hand sides in one launch) and a bounded sample of the
                 served form.
---workload hp2d-coef | hp3d | batched | serving runs one of them as the line.
+--workload hp2d-br2 | hp2d-coef | hp3d | batched | serving runs one of them as the line.
 
 --impl reference times the FP64 CPU oracle on the same workload (a bounded
 sample of PCG iterations per step).  Multi-GPU: independent replicas (the
@@ -55,6 +55,7 @@ WORKLOAD = "2D hp-random 32x32 base, prob 0.3, depth<=3, p~U{1..6}, SIPG eta=100
 METRIC = "DOF-iters/s (PCG on the 2D hp-random workload, mixed FP32 preconditioner / FP64 outer)"
 WORKLOAD_BR2 = ("2D hp-random 32x32 base, prob 0.3, depth<=3, p~U{1..6}, BR2 (eta = most sub-faces of one "
                 "element), tol 1e-8, seed 0")
+METRIC_BR2 = "DOF-iters/s (PCG on the 2D hp-random workload with BR2, mixed FP32 preconditioner / FP64 outer)"
 WORKLOAD3 = ("3D hp-random 16^3 base, prob 0.2, depth<=2, p~U{1..5}, BR2 (eta = most sub-faces of one "
              "element), tol 1e-8, seed 0")
 METRIC3 = "DOF-iters/s (PCG on the 3D hp-random workload, mixed FP32 preconditioner / FP64 outer)"
@@ -455,7 +456,7 @@ def _oracle_problem(which: str, seed: int):
         prob = solver.build_problem(mesh, form="br2")
     else:
         mesh, rh = inputs.config1_coeff(seed) if which == "hp2d-coef" else inputs.config1(seed)
-        prob = solver.build_problem(mesh)
+        prob = solver.build_problem(mesh, form="br2" if which == "hp2d-br2" else "sipg")
     pc = solver.Preconditioner(prob, lor="amg")
     b = rhs.load_vector(prob.space, rh.amps, rh.waves)
     return prob, pc, b
@@ -557,17 +558,20 @@ def run_ours(args):
     ctx = Ctx(dev, torch.cuda.current_stream(dev))
     three = args.workload == "hp3d"
     coef = args.workload == "hp2d-coef"
+    br2 = args.workload == "hp2d-br2"
     if three:
         mesh, rh = inputs.config2(args.seed, base=args.base3)
     else:
         mesh, rh = inputs.config1_coeff(args.seed) if coef else inputs.config1(args.seed)
-    form = B.DG_FORM_BR2 if three else B.DG_FORM_SIPG
+    form = B.DG_FORM_BR2 if (three or br2) else B.DG_FORM_SIPG
+    metric, workload = ((METRIC3, WORKLOAD3) if three else (METRICC, WORKLOADC) if coef else
+                        (METRIC_BR2, WORKLOAD_BR2) if br2 else (METRIC, WORKLOAD))
     peaks, peak_kind = _peaks()
     probe = fp64_peak(B, ctx)
     if dist:
         dist.barrier()
     res = measure_single(B, ctx, mesh, rh, form, args.steps, args.warmup, peaks, probe["tflops"],
-                         "apply3_kernel/hp3d" if three else ("apply_kernel/hp2d" if not coef else "none"),
+                         "apply3_kernel/hp3d" if three else ("apply_kernel/hp2d" if not (coef or br2) else "none"),
                          three=three, e2e=True, keep_x=True, tune=args.tune_tiles)
     ms32, it32, ms64, it64 = res.pop("_raw")
     t_e2e, it_e2e = res.pop("_e2e")
@@ -580,7 +584,7 @@ def run_ours(args):
     launches = sum(3 + res["precond"]["kernels_per_apply"] + it * res["kernels_per_iteration"] for it in it32)
     res["roofline"]["peak_fp64_probe_runs"] = probe["runs"]
     out = {
-        "metric": METRIC3 if three else (METRICC if coef else METRIC),
+        "metric": metric,
         "value": value,
         "unit": "DOF-iters/s",
         "n_gpus": ws,
@@ -592,7 +596,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f64 (outer PCG, operator) + f32 (preconditioner)",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD3 if three else (WORKLOADC if coef else WORKLOAD), "n_dofs": n,
+        "config": {"workload": workload, "n_dofs": n,
                    "n_elems": res["n_elems"], **res["precond"],
                    "parallelism": f"replicas x{ws}", "l2": "flushed (512 MiB write) before every step",
                    "timed": "CUDA events around each solve's one graph launch (copy of b, start, "
@@ -686,10 +690,13 @@ def run_reference(args):
         return
     if args.workload in ("batched", "serving"):
         print(json.dumps({"impl": "reference", "unavailable": f"the oracle has no {args.workload} form; "
-                          "its single-problem PCG is timed by the hp2d, hp2d-coef and hp3d workloads"}))
+                          "its single-problem PCG is timed by the hp2d, hp2d-br2, hp2d-coef and hp3d workloads"}))
         return
     three = args.workload == "hp3d"
     coef = args.workload == "hp2d-coef"
+    br2 = args.workload == "hp2d-br2"
+    metric, workload = ((METRIC3, WORKLOAD3) if three else (METRICC, WORKLOADC) if coef else
+                        (METRIC_BR2, WORKLOAD_BR2) if br2 else (METRIC, WORKLOAD))
     prob, pc, b = _oracle_problem(args.workload, args.seed)
     for _ in range(args.warmup):
         _oracle_iters(prob, pc, b, ORACLE_SAMPLE_ITERS)
@@ -701,7 +708,7 @@ def run_reference(args):
         sample += f" on the same recipe with a 4^3 base ({n} DOFs)"
     out = {
         "impl": "reference",
-        "metric": METRIC3 if three else (METRICC if coef else METRIC),
+        "metric": metric,
         "value": value,
         "unit": "DOF-iters/s",
         "n_gpus": ws,
@@ -713,7 +720,7 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD3 if three else (WORKLOADC if coef else WORKLOAD), "n_dofs": n},
+        "config": {"workload": workload, "n_dofs": n},
         "cpu_baseline": {"value": value, "unit": "DOF-iters/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "DOF-iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -730,7 +737,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="only the line's own workload")
-    ap.add_argument("--workload", default="hp2d", choices=["hp2d", "hp2d-coef", "hp3d", "batched", "serving"])
+    ap.add_argument("--workload", default="hp2d",
+                    choices=["hp2d", "hp2d-br2", "hp2d-coef", "hp3d", "batched", "serving"])
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-meshes", type=int, default=16)
