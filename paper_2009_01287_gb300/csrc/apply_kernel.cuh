@@ -26,7 +26,12 @@
 //              eta/4 [M_oo G_o (a - b) + M_on G_n (M_no u- - M_nn u+)]
 //            (eta [M_oo G_o a] on the boundary), G = edge block of the
 //            element mass inverse = h^-2 Minv_00 Minv, times the larger
-//            coefficient a of the sub-face's two sides.
+//            coefficient a of the sub-face's two sides.  Multiplied out it is
+//            cz (Z u- - V u+) + cx (X u- - Y u+) with the product tables and
+//            scalars of SubFaceBr2, so an item forms up to four more 1D
+//            products in the same pass (none of the lifting's solves and
+//            barriers per sub-face); on whole sides Z, V, Y are M_oo or M_on,
+//            taken from a and b.
 // Every sub-face is evaluated from both of its sides (no atomics): applies are
 // bit-reproducible.
 #pragma once
@@ -171,6 +176,7 @@ struct ApplyArgs {
   double* tr;                 // side traces: [side][node][u, dn]
   const int32_t* sf_ptr;
   const SubFaceRec* sf;
+  const SubFaceBr2* sfb;      // square meshes, BR2: the multiplied-out liftings
   const SubFaceRec3* sf3;     // cube meshes
   const double* tab;          // basis + face tables
   const int32_t* order;       // degree-sorted element order
@@ -196,9 +202,8 @@ struct ApplyShape {
   static constexpr int NN = NP * NP;
   static constexpr int EPB = apply_epb(P);
   // shared doubles: M, K (2 NN) + x, T1, T2 (3 EPB NN) + r, c2 (8 EPB NP)
-  // + BR2: jo, go, cd (12 EPB NP), jn, gn (8 EPB kMaxN)
-  static constexpr int SMEM = 2 * NN + 3 * EPB * NN + 8 * EPB * NP + 12 * EPB * NP + 8 * EPB * kMaxN;
-  // start (doubles) of the SIPG sub-face item partials: double2, so 16-byte aligned
+  static constexpr int SMEM = 2 * NN + 3 * EPB * NN + 8 * EPB * NP;
+  // start (doubles) of the sub-face item partials: double2, so 16-byte aligned
   static constexpr int PART = (SMEM + 1) & ~1;
 };
 
@@ -253,11 +258,6 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& 
   double* sT2 = sT1 + EPB * NN;
   double* sr = sT2 + EPB * NN;           // [EPB][4][NP]
   double* sc2 = sr + EPB * 4 * NP;       // [EPB][4][NP]
-  double* sjo = sc2 + EPB * 4 * NP;      // BR2 [EPB][4][NP]
-  double* sgo = sjo + EPB * 4 * NP;
-  double* scd = sgo + EPB * 4 * NP;
-  double* sjn = scd + EPB * 4 * NP;      // [EPB][4][kMaxN]
-  double* sgn = sjn + EPB * 4 * kMaxN;
 
   const int tid = threadIdx.x;
   if (A.skip && A.skip[(int64_t)T.inst * A.skip_stride] != 0.0) {   // CTA-uniform
@@ -292,10 +292,10 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& 
     sT1[t] = t1;
     sT2[t] = t2;
   }
-  // ---- faces (SIPG): one thread per (sub-face item, side node) forms that
+  // ---- faces: one thread per (sub-face item, side node) forms that
   // sub-face's contribution to the node, then one thread per side node sums
   // its sub-faces' contributions in sub-face order (deterministic)
-  if (!BR2) {
+  {
     const int ib = A.item_ptr[tile];
     const int nit = A.item_ptr[tile + 1] - ib;
     double2* part = reinterpret_cast<double2*>(sm + S::PART);   // [nit][NP]
@@ -317,7 +317,19 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& 
       }
       double r, c2;
       if (f.nb < 0) {
-        r = f.len * (f.sigma * a - c);
+        if (BR2) {   // eta [M_oo G_o a]: cz (Z u-)_i, Z = M_oo on the whole side
+          const SubFaceBr2 g = A.sfb[item.x];
+          double z = a;
+          if (!(g.full & 1)) {
+            const double* Z = A.tab + g.tab_z + i * NP;
+            z = 0.0;
+#pragma unroll
+            for (int m = 0; m < NP; ++m) z = fma(__ldg(Z + m), trk[m].x, z);
+          }
+          r = fma(g.cz, z, -f.len * c);
+        } else {
+          r = f.len * (f.sigma * a - c);
+        }
         c2 = -f.len * a;
       } else {
         const int np = f.pn + 1;
@@ -331,7 +343,31 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& 
           d = fma(w, v.y, d);   // neighbour's outward dn: this side's dn+ is -v.y
         }
         const double jmp = a - b;
-        r = f.len * (f.sigma * jmp - 0.5 * (c - d));
+        if (BR2) {   // eta/4 [M_oo G_o jo + M_on G_n jn] = cz (Z u- - V u+) + cx (X u- - Y u+)
+          const SubFaceBr2 g = A.sfb[item.x];
+          const double* X = A.tab + g.tab_x + i * NP;
+          double xx = 0.0;
+#pragma unroll
+          for (int m = 0; m < NP; ++m) xx = fma(__ldg(X + m), trk[m].x, xx);
+          double z = a, v = b, y = b;   // whole own side: Z = M_oo, V = M_on; whole neighbour side: Y = M_on
+          if (!(g.full & 1)) {
+            const double* Z = A.tab + g.tab_z + i * NP;
+            const double* V = A.tab + g.tab_v + i * np;
+            z = 0.0;
+            v = 0.0;
+#pragma unroll
+            for (int m = 0; m < NP; ++m) z = fma(__ldg(Z + m), trk[m].x, z);
+            for (int m = 0; m < np; ++m) v = fma(__ldg(V + m), trn[m].x, v);
+          }
+          if (!(g.full & 2)) {
+            const double* Y = A.tab + g.tab_y + i * np;
+            y = 0.0;
+            for (int m = 0; m < np; ++m) y = fma(__ldg(Y + m), trn[m].x, y);
+          }
+          r = fma(g.cz, z - v, fma(g.cx, xx - y, -0.5 * f.len * (c - d)));
+        } else {
+          r = f.len * (f.sigma * jmp - 0.5 * (c - d));
+        }
         c2 = -0.5 * f.len * jmp;
       }
       part[(item.y >> 16) * NP + i] = make_double2(r, c2);
@@ -351,131 +387,8 @@ __device__ __forceinline__ void apply_tile(const ApplyArgs& A, const ApplyTile& 
       sr[t] = r;
       sc2[t] = c2;
     }
-  } else {
-    for (int t = tid; t < nside; t += blockDim.x) {
-      sr[t] = 0.0;
-      sc2[t] = 0.0;
-    }
   }
   __syncthreads();
-  if (BR2) {
-    int maxsub = 0;
-    for (int e = 0; e < count; ++e) {
-      const int k = A.order[T.first + e];
-      for (int s = 0; s < 4; ++s) {
-        const int c = A.sf_ptr[4 * k + s + 1] - A.sf_ptr[4 * k + s];
-        maxsub = c > maxsub ? c : maxsub;
-      }
-    }
-    const int nnb = count * 4 * kMaxN;
-    for (int j = 0; j < maxsub; ++j) {
-      // stage A: own-indexed jump projection / consistency, neighbour-indexed projection
-      for (int t = tid; t < nside; t += blockDim.x) {
-        const int e = t / (4 * NP), s = (t / NP) & 3, i = t % NP;
-        const int k = A.order[T.first + e];
-        const int b0 = A.sf_ptr[4 * k + s];
-        if (j >= A.sf_ptr[4 * k + s + 1] - b0) continue;
-        const SubFaceRec f = A.sf[b0 + j];
-        const double2* trk = reinterpret_cast<const double2*>(A.tr + A.toff[k]) + s * NP;
-        double a = 0.0, c = 0.0;
-#pragma unroll
-        for (int m = 0; m < NP; ++m) {
-          const double w = __ldg(A.tab + f.tab_oo + i * NP + m);
-          a = fma(w, trk[m].x, a);
-          c = fma(w, trk[m].y, c);
-        }
-        a *= f.len;
-        c *= f.len;
-        if (f.nb < 0) {
-          sc2[t] -= a;
-          sjo[t] = a;
-          scd[t] = -c;
-        } else {
-          const int np = f.pn + 1;
-          const double2* trn = reinterpret_cast<const double2*>(A.tr + A.toff[f.nb]) + f.nb_side * np;
-          double b = 0.0, d = 0.0;
-          for (int m = 0; m < np; ++m) {
-            const double w = __ldg(A.tab + f.tab_on + i * np + m);
-            b = fma(w, trn[m].x, b);
-            d = fma(w, trn[m].y, d);
-          }
-          b *= f.len;
-          d *= f.len;
-          sc2[t] -= 0.5 * (a - b);
-          sjo[t] = a - b;
-          scd[t] = -0.5 * (c - d);
-        }
-      }
-      for (int t = tid; t < nnb; t += blockDim.x) {
-        const int e = t / (4 * kMaxN), s = (t / kMaxN) & 3, m = t % kMaxN;
-        const int k = A.order[T.first + e];
-        const int b0 = A.sf_ptr[4 * k + s];
-        if (j >= A.sf_ptr[4 * k + s + 1] - b0) continue;
-        const SubFaceRec f = A.sf[b0 + j];
-        if (f.nb < 0 || m > f.pn) continue;
-        const int np = f.pn + 1;
-        const double2* trk = reinterpret_cast<const double2*>(A.tr + A.toff[k]) + s * NP;
-        const double2* trn = reinterpret_cast<const double2*>(A.tr + A.toff[f.nb]) + f.nb_side * np;
-        double v = 0.0;
-        for (int i = 0; i < NP; ++i) v = fma(__ldg(A.tab + f.tab_on + i * np + m), trk[i].x, v);
-        for (int q = 0; q < np; ++q) v = fma(-__ldg(A.tab + f.tab_nn + m * np + q), trn[q].x, v);
-        sjn[(e * 4 + s) * kMaxN + m] = v * f.len;
-      }
-      __syncthreads();
-      // stage B: apply the edge blocks of the two mass inverses
-      for (int t = tid; t < nside; t += blockDim.x) {
-        const int e = t / (4 * NP), s = (t / NP) & 3, i = t % NP;
-        const int k = A.order[T.first + e];
-        const int b0 = A.sf_ptr[4 * k + s];
-        if (j >= A.sf_ptr[4 * k + s + 1] - b0) continue;
-        const double* Mi = A.tab + bo.Minv;
-        double g = 0.0;
-#pragma unroll
-        for (int m = 0; m < NP; ++m) g = fma(__ldg(Mi + i * NP + m), sjo[t - i + m], g);
-        const double ih = A.ih[k];
-        const int nb = A.sf[b0 + j].nb;
-        // both sides' liftings carry the larger a of the sub-face
-        const double w = nb < 0 ? A.ak[k] : fmax(A.ak[k], A.ak[nb]);
-        sgo[t] = w * (g * __ldg(Mi) * ih * ih);
-      }
-      for (int t = tid; t < nnb; t += blockDim.x) {
-        const int e = t / (4 * kMaxN), s = (t / kMaxN) & 3, m = t % kMaxN;
-        const int k = A.order[T.first + e];
-        const int b0 = A.sf_ptr[4 * k + s];
-        if (j >= A.sf_ptr[4 * k + s + 1] - b0) continue;
-        const SubFaceRec f = A.sf[b0 + j];
-        if (f.nb < 0 || m > f.pn) continue;
-        const int np = f.pn + 1;
-        const double* Mi = A.tab + A.boff[f.pn].Minv;
-        double g = 0.0;
-        for (int q = 0; q < np; ++q) g = fma(__ldg(Mi + m * np + q), sjn[(e * 4 + s) * kMaxN + q], g);
-        const double ihn = A.ih[f.nb];
-        const double w = fmax(A.ak[k], A.ak[f.nb]);
-        sgn[(e * 4 + s) * kMaxN + m] = w * (g * __ldg(Mi) * ihn * ihn);
-      }
-      __syncthreads();
-      // stage C: stabilisation residual
-      for (int t = tid; t < nside; t += blockDim.x) {
-        const int e = t / (4 * NP), s = (t / NP) & 3, i = t % NP;
-        const int k = A.order[T.first + e];
-        const int b0 = A.sf_ptr[4 * k + s];
-        if (j >= A.sf_ptr[4 * k + s + 1] - b0) continue;
-        const SubFaceRec f = A.sf[b0 + j];
-        double st = 0.0;
-#pragma unroll
-        for (int m = 0; m < NP; ++m) st = fma(__ldg(A.tab + f.tab_oo + i * NP + m), sgo[t - i + m], st);
-        double coef = 1.0;
-        if (f.nb >= 0) {
-          const int np = f.pn + 1;
-          for (int m = 0; m < np; ++m)
-            st = fma(__ldg(A.tab + f.tab_on + i * np + m), sgn[(e * 4 + s) * kMaxN + m], st);
-          coef = 0.25;
-        }
-        sr[t] += scd[t] + A.eta * coef * f.len * st;
-      }
-      __syncthreads();
-    }
-  }
   // ---- gather: volume pass 2 + side residuals + normal-derivative terms
   double part = 0.0;
   for (int t = tid; t < nnode; t += blockDim.x) {

@@ -180,6 +180,7 @@ ApplyArgs make_apply_args(const dg_mesh& M, const double* x, double* y, Reduce r
   A.tr = M.d_tr;
   A.sf_ptr = M.d_sf_ptr;
   A.sf = M.d_sf;
+  A.sfb = M.d_sfb;
   A.sf3 = M.d_sf3;
   A.tab = M.d_tables;
   A.order = M.d_order;

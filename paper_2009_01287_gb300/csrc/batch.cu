@@ -303,6 +303,14 @@ static void build_union_mesh(dg_batch* B, cudaStream_t s) {
       g.tab_nn += (int32_t)tshift[k];
       U.h_sf.push_back(g);
     }
+    for (const SubFaceBr2& b : M.h_sfb) {   // BR2: one per record, in the same order
+      SubFaceBr2 g = b;
+      g.tab_z += (int32_t)tshift[k];
+      g.tab_v += (int32_t)tshift[k];
+      g.tab_x += (int32_t)tshift[k];
+      g.tab_y += (int32_t)tshift[k];
+      U.h_sfb.push_back(g);
+    }
     um.n += m.n;
     U.stats.n_elems += M.stats.n_elems;
     U.stats.n_subfaces += M.stats.n_subfaces;

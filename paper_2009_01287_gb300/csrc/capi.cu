@@ -81,6 +81,7 @@ void upload_mesh(dg_mesh* M, cudaStream_t s) {
   }
   M->d_sf_ptr = a.upload(m.sf_ptr, s);
   M->d_sf = a.upload(M->h_sf, s);
+  M->d_sfb = M->h_sfb.empty() ? nullptr : a.upload(M->h_sfb, s);
   M->d_sf3 = a.upload(M->h_sf3, s);
   M->d_tables = a.upload(M->h_tables, s);
   M->d_sched = a.alloc<unsigned>(2);

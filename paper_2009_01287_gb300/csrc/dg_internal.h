@@ -71,6 +71,22 @@ struct SubFaceRec {
   double len;        // physical length of the sub-face
 };
 
+// BR2 lifting of one sub-face of a square mesh, multiplied out (beside the
+// SubFaceRec of the same index): the stabilisation residual at own side node
+// i is cz [(Z u-)_i - (V u+)_i] + cx [(X u-)_i - (Y u+)_i] with the products
+// of the face tables and the 1D mass inverses Minv (own), Minv_n (neighbour)
+//   Z = M_oo Minv M_oo, V = M_oo Minv M_on, X = M_on Minv_n M_no, Y = M_on Minv_n M_nn
+// and cz, cx = eta coef len^2 a Minv_00 / h^2 of the own / neighbour element
+// (coef 1/4 inside, 1 on the boundary; a the larger coefficient of the two
+// sides).  On a sub-face that is the own element's whole side M_oo is the 1D
+// mass matrix, so Z = M_oo and V = M_on; on the neighbour's whole side Y = M_on.
+struct SubFaceBr2 {
+  int32_t tab_z, tab_v, tab_x, tab_y;   // table offsets ((p+1) x (p+1) or (p+1) x (pn+1))
+  int32_t full;                         // bit 0: own whole side, bit 1: neighbour's whole side
+  int32_t pad;
+  double cz, cx;
+};
+
 // One sub-face of a cube mesh seen from one of its sides.  The sub-face is a
 // square; its face integrals factor into two 1D tables, one per tangential
 // axis of the side (the lower-numbered axis first).

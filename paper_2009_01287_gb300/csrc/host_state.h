@@ -112,6 +112,7 @@ struct dg_mesh {
   // host copies of what the device holds
   std::vector<double> h_h;
   std::vector<dg::SubFaceRec> h_sf;
+  std::vector<dg::SubFaceBr2> h_sfb;    // square meshes, BR2: one per h_sf record
   std::vector<dg::SubFaceRec3> h_sf3;   // cube meshes
   int64_t apply3_smem = 0;              // dynamic shared memory of the 3D operator kernel
   std::vector<double> h_tables;
@@ -144,6 +145,7 @@ struct dg_mesh {
   double* d_tr = nullptr;       // side traces written by each apply
   int32_t* d_sf_ptr = nullptr;
   dg::SubFaceRec* d_sf = nullptr;
+  dg::SubFaceBr2* d_sfb = nullptr;
   dg::SubFaceRec3* d_sf3 = nullptr;
   double* d_tables = nullptr;
   int32_t* d_order = nullptr;

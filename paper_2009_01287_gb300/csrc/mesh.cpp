@@ -3,6 +3,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <tuple>
 
 #include "dg_internal.h"
 #include "host_state.h"
@@ -353,12 +355,83 @@ void build_mesh_host(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opt
         M->h_sf[j] = r;
       }
     }
+  // BR2: each sub-face's lifting multiplied out (SubFaceBr2), its product
+  // tables appended after the face tables
+  std::vector<double> prod;
+  M->h_sfb.clear();
+  if (o.form == DG_FORM_BR2) {
+    std::map<std::tuple<int, int, int, int>, int> pindex;
+    const int pbase = (int)ft.data.size();
+    // kind 0: Z = M_oo Minv M_oo, 1: V = M_oo Minv M_on, 2: X = M_on Minv_n M_no,
+    // 3: Y = M_on Minv_n M_nn (row-major, (p+1) rows)
+    auto product = [&](int kind, int p, int pn, int oo, int on, int nn) {
+      const auto key = std::make_tuple(kind, kind == 0 ? oo : on, kind == 3 ? nn : (kind == 1 ? oo : -1),
+                                       p * 16 + pn);
+      const auto it = pindex.find(key);
+      if (it != pindex.end()) return it->second;
+      const int a = p + 1, b = pn + 1;
+      const double* Moo = ft.data.data() + oo;
+      const double* Mon = ft.data.data() + on;
+      const double* Mnn = ft.data.data() + nn;
+      const std::vector<double>& Mi = basis1d(p).Minv;
+      const std::vector<double>& Min = basis1d(pn).Minv;
+      const int cols = (kind == 0 || kind == 2) ? a : b;
+      const int off = (int)prod.size();
+      prod.resize(off + (size_t)a * cols, 0.0);
+      for (int i = 0; i < a; ++i)
+        for (int j = 0; j < cols; ++j) {
+          double v = 0.0;
+          for (int u = 0; u < (kind < 2 ? a : b); ++u)
+            for (int w = 0; w < (kind < 2 ? a : b); ++w) {
+              if (kind == 0) v += Moo[i * a + u] * Mi[u * a + w] * Moo[w * a + j];
+              else if (kind == 1) v += Moo[i * a + u] * Mi[u * a + w] * Mon[w * b + j];
+              else if (kind == 2) v += Mon[i * b + u] * Min[u * b + w] * Mon[j * b + w];
+              else v += Mon[i * b + u] * Min[u * b + w] * Mnn[w * b + j];
+            }
+          prod[off + (size_t)i * cols + j] = v;
+        }
+      pindex.emplace(key, pbase + off);
+      return pbase + off;
+    };
+    M->h_sfb.assign(m.sf.size(), SubFaceBr2{});
+    for (int64_t k = 0; k < m.n; ++k)
+      for (int s = 0; s < 4; ++s)
+        for (int j = m.sf_ptr[4 * k + s]; j < m.sf_ptr[4 * k + s + 1]; ++j) {
+          const SubFaceRec& r = M->h_sf[j];
+          SubFaceBr2& g = M->h_sfb[j];
+          const int P = m.p[k], len = m.sf[j].t1 - m.sf[j].t0;
+          const bool in = r.nb >= 0;
+          const double coef = in ? 0.25 : 1.0, hk = M->h_h[k];
+          // both sides' lifting energies carry the larger coefficient of the sub-face
+          const double w = in ? std::max(m.coef[k], m.coef[r.nb]) : m.coef[k];
+          g.full = (m.size[k] == len ? 1 : 0) | (in && m.size[r.nb] == len ? 2 : 0);
+          g.cz = w * (M->eta * coef * r.len * r.len * basis1d(P).Minv[0] / (hk * hk));
+          g.tab_z = product(0, P, P, r.tab_oo, r.tab_oo, r.tab_oo);
+          if (in) {
+            const double hn = M->h_h[r.nb];
+            g.cx = w * (M->eta * coef * r.len * r.len * basis1d(r.pn).Minv[0] / (hn * hn));
+            g.tab_v = product(1, P, r.pn, r.tab_oo, r.tab_on, r.tab_nn);
+            g.tab_x = product(2, P, r.pn, r.tab_oo, r.tab_on, r.tab_nn);
+            g.tab_y = product(3, P, r.pn, r.tab_oo, r.tab_on, r.tab_nn);
+          } else {
+            g.tab_v = g.tab_x = g.tab_y = g.tab_z;
+          }
+        }
+  }
   const int base = (int)M->h_tables.size();
   M->h_tables.insert(M->h_tables.end(), ft.data.begin(), ft.data.end());
+  M->h_tables.insert(M->h_tables.end(), prod.begin(), prod.end());
+  DG_REQUIRE(M->h_tables.size() < (1ULL << 31), "face tables too large");
   for (auto& r : M->h_sf) {
     r.tab_oo += base;
     r.tab_on += base;
     r.tab_nn += base;
+  }
+  for (auto& g : M->h_sfb) {
+    g.tab_z += base;
+    g.tab_v += base;
+    g.tab_x += base;
+    g.tab_y += base;
   }
   build_tiles(M);
   // operation and byte counts of one operator apply, as the kernel does it
@@ -373,14 +446,21 @@ void build_mesh_host(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opt
     fl += 2.0 * (4.0 * n1 * n1 * n1 + 4.0 * n1 * n1 + 4.0 * n1 * n1);  // volume, own dn, gather
     for (int j = m.sf_ptr[4 * k]; j < m.sf_ptr[4 * k + 4]; ++j) {
       const auto& f = m.sf[j];
+      // BR2 products (SubFaceBr2): Z and X on the own trace, V and Y on the
+      // neighbour's; Z and V are not formed on the own element's whole side,
+      // Y not on the neighbour's whole side
+      const bool own_whole = m.size[k] == f.t1 - f.t0;
       if (f.nb < 0) {
         fl += 2.0 * (2.0 * n1 * n1);
-        if (o.form == DG_FORM_BR2) fl += 2.0 * (2.0 * n1 * n1);
+        if (o.form == DG_FORM_BR2 && !own_whole) fl += 2.0 * (n1 * n1);
         continue;
       }
       const double nn = m.p[f.nb] + 1.0;
       fl += 2.0 * (2.0 * n1 * n1 + 2.0 * n1 * nn);
-      if (o.form == DG_FORM_BR2) fl += 2.0 * (2.0 * n1 * nn + 2.0 * nn * nn + n1 * n1 + n1 * n1);
+      if (o.form == DG_FORM_BR2) {
+        const bool nb_whole = m.size[f.nb] == f.t1 - f.t0;
+        fl += 2.0 * (n1 * n1 + (own_whole ? 0.0 : n1 * n1 + n1 * nn) + (nb_whole ? 0.0 : n1 * nn));
+      }
       const int lg = std::abs(ilog2(m.size[k]) - ilog2(m.size[f.nb]));
       S.max_level_gap = std::max<int64_t>(S.max_level_gap, lg);
     }

@@ -65,3 +65,31 @@ def test_batch_zero_rhs_instance(built_lib, cuda_device):
     res, _ = bat.solve(b, x, 1e-8, 3000)
     assert res[0].iters == 0 and float(x[:bat.offsets[1]].abs().max()) == 0.0
     assert res[1].iters > 0 and res[1].rel_res <= 1e-8
+
+
+def test_batch_br2_matches_single_solves(built_lib, cuda_device):
+    """BR2 in the batched form (explicit eta): the union carries every mesh's
+    multiplied-out liftings, so each instance again follows its own solve."""
+    import torch
+    B = built_lib
+    opts = B.make_options(form=B.DG_FORM_BR2, eta=8.0, precision=B.DG_PREC_FP64)
+    meshes = _problems()[:3] + _problems()[4:]   # hanging levels, ragged, uniform, a in {1, 20}
+    bat = B.Batch(meshes, n_rhs=1, opts=opts)
+    b = torch.empty(bat.n_dofs, dtype=torch.float64, device=cuda_device)
+    singles = []
+    for k, m in enumerate(meshes):
+        M = B.Mesh(m, opts)
+        pc = B.Precond(M, opts)
+        seg = b[bat.offsets[k]:bat.offsets[k + 1]]
+        rh = inputs.sine_rhs(2, 30 + k)
+        B.dg_rhs_sine(M.h, rh.amps, rh.waves, seg)
+        x1 = torch.empty_like(seg)
+        info = B.dg_pcg_solve(M.h, pc.h, seg.clone(), x1, 1e-8, 3000)
+        singles.append((info, x1))
+    x = torch.empty_like(b)
+    res, _ = bat.solve(b, x, 1e-8, 3000)
+    for k, (info, x1) in enumerate(singles):
+        xk = x[bat.offsets[k]:bat.offsets[k + 1]]
+        assert res[k].status == B.DG_OK and res[k].rel_res <= 1e-8
+        assert res[k].iters == info.iters
+        assert float((xk - x1).abs().max()) <= 1e-10 * float(x1.abs().max())
