@@ -405,6 +405,8 @@ def inspect_lib():
         L.dginspect_level_nnz.restype = C.c_int64
         L.dginspect_level_A.argtypes = [vp, C.c_int, vp, vp, vp]
         L.dginspect_apply.argtypes = [vp, vp, vp]
+        L.dginspect_item_sizes.argtypes = [vp, vp]
+        L.dginspect_items.argtypes = [vp, vp, vp, vp, vp]
         L.dginspect_block_units.argtypes = [C.c_int64, vp, vp, vp, vp, vp, vp, C.c_int64]
         L.dginspect_block_units.restype = C.c_int64
         L.dginspect_csr_tiers.argtypes = [C.c_int64, vp, vp, vp, vp, vp]
@@ -500,6 +502,21 @@ class HostSetup:
         y = np.zeros(self.n)
         inspect_lib().dginspect_apply(self.h, x.ctypes.data, y.ctypes.data)
         return y
+
+    def face_items(self):
+        """The operator's tiles and sub-face items as the kernels read them:
+        (item_ptr, items (n, 2), chunk per tile, info (n, 3): interior,
+        neighbour degree, whole-side flags)."""
+        L = inspect_lib()
+        s = np.zeros(3, dtype=np.int64)
+        L.dginspect_item_sizes(self.h, s.ctypes.data)
+        nt, ni = int(s[0]), int(s[1])
+        ptr = np.zeros(nt + 1, dtype=np.int32)
+        items = np.zeros(2 * max(ni, 1), dtype=np.int32)
+        chunk = np.zeros(max(nt, 1), dtype=np.int32)
+        info = np.zeros(3 * max(ni, 1), dtype=np.int32)
+        L.dginspect_items(self.h, ptr.ctypes.data, items.ctypes.data, chunk.ctypes.data, info.ctypes.data)
+        return ptr, items[:2 * ni].reshape(ni, 2), chunk[:nt], info[:3 * ni].reshape(ni, 3)
 
     def __del__(self):
         try:

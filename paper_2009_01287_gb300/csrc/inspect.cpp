@@ -97,6 +97,41 @@ void* dginspect_create(const dg_mesh_desc* desc, const dg_options* opts, int wit
 
 void dginspect_destroy(void* h) { delete (Inspect*)h; }
 
+// the operator's tiles and sub-face items: out = [n_tiles, n_items, dim]
+void dginspect_item_sizes(void* h, int64_t* out) {
+  const dg_mesh& M = ((Inspect*)h)->mesh;
+  out[0] = M.n_tiles;
+  out[1] = (int64_t)M.h_items.size() / 2;
+  out[2] = M.host.dim;
+}
+
+// item_ptr (n_tiles + 1), items (2 per item, as the kernels read them), per
+// tile its chunk length (cubes; squares: the tile's item count), and per item
+// the fields its branches depend on: interior (0/1), neighbour degree, the
+// whole-side flags (BR2 records; 0 without them)
+void dginspect_items(void* h, int32_t* item_ptr, int32_t* items, int32_t* chunk, int32_t* info) {
+  const dg_mesh& M = ((Inspect*)h)->mesh;
+  std::memcpy(item_ptr, M.h_item_ptr.data(), M.h_item_ptr.size() * sizeof(int32_t));
+  std::memcpy(items, M.h_items.data(), M.h_items.size() * sizeof(int32_t));
+  for (int t = 0; t < M.n_tiles; ++t)
+    chunk[t] = M.host.dim == 3 ? M.h_tiles[t].chunk : M.h_item_ptr[t + 1] - M.h_item_ptr[t];
+  const int64_t n = (int64_t)M.h_items.size() / 2;
+  for (int64_t g = 0; g < n; ++g) {
+    const int32_t r = M.h_items[2 * g];
+    if (M.host.dim == 3) {
+      const SubFaceRec3& f = M.h_sf3[r];
+      info[3 * g] = f.nb >= 0 ? 1 : 0;
+      info[3 * g + 1] = f.pn;
+      info[3 * g + 2] = f.full;
+    } else {
+      const SubFaceRec& f = M.h_sf[r];
+      info[3 * g] = f.nb >= 0 ? 1 : 0;
+      info[3 * g + 1] = f.pn;
+      info[3 * g + 2] = M.h_sfb.empty() ? 0 : M.h_sfb[r].full;
+    }
+  }
+}
+
 // sizes: [n_dofs, n_c, nnz(P), nnz(Ac), n_blocks, total block dofs, n_levels,
 //         eta*1e6, sum of squared block dims]
 void dginspect_sizes(void* h, int64_t* out) {
