@@ -38,6 +38,9 @@ from .topology import Topology
 
 
 class DGSpace:
+    # quadrature points beyond the exact box rule (mapped elements: 1)
+    qextra = 0
+
     def __init__(self, topo: Topology, lattice_h: float, coef=None):
         self.topo = topo
         self.dim = int(getattr(topo, "dim", 2))
@@ -54,6 +57,14 @@ class DGSpace:
 
     def h(self, k: int) -> float:
         return float(self.topo.size[k]) * self.lh
+
+    def hpen(self, k: int) -> float:
+        """Element size h_kappa of the SIPG penalty (the edge length)."""
+        return self.h(k)
+
+    def phys(self, pts: np.ndarray) -> np.ndarray:
+        """Physical coordinates of quadrature points (boxes: the points)."""
+        return pts
 
     def origin(self, k: int) -> np.ndarray:
         return self.topo.lo[k].astype(np.float64) * self.lh
@@ -145,6 +156,14 @@ class DGSpace:
         return np.arange(self.offset[k], self.offset[k + 1])
 
 
+def normal_derivative(g: np.ndarray, n: np.ndarray) -> np.ndarray:
+    """grad phi . n at every point, for one normal (boxes) or one per point
+    (mapped elements): g (npts, nloc, d), n (d,) or (npts, d)."""
+    if n.ndim == 1:
+        return g @ n
+    return np.einsum("qid,qd->qi", g, n)
+
+
 def penalty(space: DGSpace, f, eta: float, form: str) -> float:
     """SIPG penalty of a sub-face (Section 2): eta p_e^2 / h_e with p_e the
     larger degree and h_e the smaller size of the two sides, times the larger
@@ -152,10 +171,10 @@ def penalty(space: DGSpace, f, eta: float, form: str) -> float:
     t = space.topo
     if f.kp >= 0:
         pe = max(int(t.p[f.km]), int(t.p[f.kp]))
-        he = min(space.h(f.km), space.h(f.kp))
+        he = min(space.hpen(f.km), space.hpen(f.kp))
         ae = max(space.coef[f.km], space.coef[f.kp])
     else:
-        pe, he, ae = int(t.p[f.km]), space.h(f.km), space.coef[f.km]
+        pe, he, ae = int(t.p[f.km]), space.hpen(f.km), space.coef[f.km]
     if form == "paper":
         return ae * eta * pe * pe / he
     if form == "p1sq":
@@ -181,7 +200,7 @@ def assemble(space: DGSpace, eta: float, form: str = "sipg",
 
     for k in range(topo.n):
         p = int(topo.p[k])
-        pts, W = space.volume_quadrature(k, p + 1)
+        pts, W = space.volume_quadrature(k, p + 1 + space.qextra)
         _, g = space.eval(k, pts)
         K = sum((g[:, :, d].T * W) @ g[:, :, d] for d in range(space.dim))
         add(space.dofs(k), space.dofs(k), space.coef[k] * K)
@@ -189,7 +208,7 @@ def assemble(space: DGSpace, eta: float, form: str = "sipg",
     if not broken_only:
         for f in topo.subfaces:
             sides = [f.km] + ([f.kp] if f.kp >= 0 else [])
-            q = max(int(topo.p[k]) for k in sides) + 1
+            q = max(int(topo.p[k]) for k in sides) + 1 + space.qextra
             pts, W, n = space.face_quadrature(f, q)
             interior = f.kp >= 0
             jump_parts, avg_parts, idx = [], [], []
@@ -197,7 +216,7 @@ def assemble(space: DGSpace, eta: float, form: str = "sipg",
                 v, g = space.eval(k, pts)
                 sgn = 1.0 if si == 0 else -1.0
                 jump_parts.append(sgn * v)                 # [[phi]] . n
-                dn = g @ n                                  # grad phi . n
+                dn = normal_derivative(g, n)                # grad phi . n
                 avg_parts.append((0.5 if interior else 1.0) * space.coef[k] * dn)   # {a grad phi} . n
                 idx.append(space.dofs(k))
             J = np.concatenate(jump_parts, axis=1)        # (q, nloc)
@@ -241,20 +260,20 @@ def element_rows(space: DGSpace, k: int, x: np.ndarray, eta: float, form: str = 
     used to check sampled outputs of very large meshes."""
     topo = space.topo
     p = int(topo.p[k])
-    pts, W = space.volume_quadrature(k, p + 1)
+    pts, W = space.volume_quadrature(k, p + 1 + space.qextra)
     _, g = space.eval(k, pts)
     K = sum((g[:, :, d].T * W) @ g[:, :, d] for d in range(space.dim))
     y = space.coef[k] * (K @ x[space.dofs(k)])
     for f in topo.faces_of(k):
         sides = [f.km] + ([f.kp] if f.kp >= 0 else [])
-        q = max(int(topo.p[e]) for e in sides) + 1
+        q = max(int(topo.p[e]) for e in sides) + 1 + space.qextra
         fpts, FW, n = space.face_quadrature(f, q)
         interior = f.kp >= 0
         J, D, I = [], [], []
         for si, e in enumerate(sides):
             v, gg = space.eval(e, fpts)
             J.append((1.0 if si == 0 else -1.0) * v)
-            D.append((0.5 if interior else 1.0) * space.coef[e] * (gg @ n))
+            D.append((0.5 if interior else 1.0) * space.coef[e] * normal_derivative(gg, n))
             I.append(space.dofs(e))
         Jm, Dm, Im = np.concatenate(J, axis=1), np.concatenate(D, axis=1), np.concatenate(I)
         F = -(Jm.T * FW) @ Dm - (Dm.T * FW) @ Jm

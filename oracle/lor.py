@@ -5,7 +5,8 @@ finite element stiffness matrix on the Cartesian sub-mesh whose vertices are
 the (p+1)^d Gauss-Lobatto nodes of k.  A-tilde is block diagonal with these
 blocks (on the DG numbering); the LOR conforming matrix is P^T A-tilde P.
 Each Q1 sub-cell matrix is integrated here with a 2^d Gauss rule from the
-Q1 shape functions (exact for the Q1 stiffness).
+Q1 shape functions (exact for the Q1 stiffness).  On mapped elements the
+sub-cells are the images of the Gauss-Lobatto cells (geometry.py).
 """
 from __future__ import annotations
 
@@ -77,8 +78,14 @@ def assemble_lor(space: DGSpace) -> sp.csr_matrix:
     """Block-diagonal A-tilde; element k's block is scaled by its coefficient
     a_k, so that A-tilde discretises the same -div(a grad u) as A."""
     blocks = []
+    mapped = hasattr(space, "map")
+    if mapped:
+        from .geometry import lor_element_mapped
     for k in range(space.topo.n):
-        blocks.append(space.coef[k] * lor_element(int(space.topo.p[k]), space.h(k), space.dim))
+        if mapped:
+            blocks.append(space.coef[k] * lor_element_mapped(space, k))
+        else:
+            blocks.append(space.coef[k] * lor_element(int(space.topo.p[k]), space.h(k), space.dim))
     return sp.block_diag([sp.csr_matrix(b) for b in blocks], format="csr")
 
 

@@ -1,6 +1,7 @@
 """Load vector b_i = int f phi_i of the synthetic sine right-hand side
 (Eq. fe-problem, right-hand side), with a (p+3)-point Gauss rule per
-direction on each element."""
+direction on each element (on mapped elements: in the pre-image, f taken at
+the physical points, the weights carrying det J)."""
 from __future__ import annotations
 
 import numpy as np
@@ -24,7 +25,7 @@ def load_vector(space: DGSpace, amps, waves) -> np.ndarray:
         p = int(space.topo.p[k])
         pts, W = space.volume_quadrature(k, p + 3)
         v, _ = space.eval(k, pts)
-        b[space.dofs(k)] = v.T @ (W * sine_f(amps, waves, pts))
+        b[space.dofs(k)] = v.T @ (W * sine_f(amps, waves, space.phys(pts)))
     return b
 
 
@@ -42,5 +43,5 @@ def load_vector_fn(space: DGSpace, fn, extra: int = 3) -> np.ndarray:
         p = int(space.topo.p[k])
         pts, W = space.volume_quadrature(k, p + extra)
         v, _ = space.eval(k, pts)
-        b[space.dofs(k)] = v.T @ (W * fn(pts))
+        b[space.dofs(k)] = v.T @ (W * fn(space.phys(pts)))
     return b

@@ -40,7 +40,12 @@ def build_operator(mesh, form: str = "sipg", eta: Optional[float] = None,
         topo = Topology3(mesh.lo, mesh.size, mesh.p, mesh.extent)
     else:
         topo = Topology(mesh.lo, mesh.size, mesh.p, mesh.extent)
-    space = DGSpace(topo, mesh.lattice_h, getattr(mesh, "coeff", None))
+    corners = getattr(mesh, "corners", None)
+    if corners is not None:
+        from .geometry import MappedDGSpace
+        space = MappedDGSpace(topo, mesh.lattice_h, corners, getattr(mesh, "coeff", None))
+    else:
+        space = DGSpace(topo, mesh.lattice_h, getattr(mesh, "coeff", None))
     if eta is None:
         eta = br2_eta(topo) if form == "br2" else 100.0
     return topo, space, assemble(space, eta, form=form, penalty_form=penalty_form)

@@ -38,6 +38,10 @@ class MeshDesc:
     # float64 (n,) piecewise-constant diffusion coefficient a per leaf, or
     # None for a = 1
     coeff: Optional[np.ndarray] = None
+    # float64 (4, 2) images of the lattice domain's corners (0, 0), (X, 0),
+    # (0, Y), (X, Y) under the bilinear map that carries the leaf boxes to
+    # quadrilaterals, or None for the boxes themselves (squares only)
+    corners: Optional[np.ndarray] = None
 
     @property
     def n_elems(self) -> int:
@@ -126,6 +130,16 @@ def with_coeff(mesh: MeshDesc, coeff: np.ndarray) -> MeshDesc:
     return dataclasses.replace(mesh, coeff=np.asarray(coeff, dtype=np.float64))
 
 
+def with_corners(mesh: MeshDesc, corners) -> MeshDesc:
+    return dataclasses.replace(mesh, corners=np.asarray(corners, dtype=np.float64).reshape(4, 2))
+
+
+# corner images of the unit square for the mapped workloads: a sheared
+# parallelogram (affine map) and a general convex quadrilateral (bilinear)
+PARALLELOGRAM = ((0.0, 0.0), (1.0, 0.0), (0.35, 0.9), (1.35, 0.9))
+QUADRILATERAL = ((0.0, 0.0), (1.2, 0.1), (0.15, 0.95), (1.05, 1.25))
+
+
 def uniform_mesh(dim: int, base: int, p: int) -> MeshDesc:
     """Conforming `base`^dim grid of unit squares/cubes with uniform degree p."""
     cells = [tuple(reversed(c)) for c in np.ndindex(*([base] * dim))]
@@ -164,6 +178,13 @@ def config1_coeff(seed: int = 0) -> Tuple[MeshDesc, SineRHS]:
     random-refinement problem (by base-cell parity)."""
     mesh, rhs = config1(seed)
     return with_coeff(mesh, base_parity_coeff(mesh, 32)), rhs
+
+
+def config1_mapped(seed: int = 0, corners=QUADRILATERAL) -> Tuple[MeshDesc, SineRHS]:
+    """The 2D hp-random workload carried by the bilinear map of the unit
+    square onto a general convex quadrilateral."""
+    mesh, rhs = config1(seed)
+    return with_corners(mesh, corners), rhs
 
 
 def config2(seed: int = 0, base: int = 16) -> Tuple[MeshDesc, SineRHS]:

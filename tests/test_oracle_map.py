@@ -1,0 +1,169 @@
+"""Pins of the oracle's mapped elements (Section 2: element maps T_kappa onto
+general quadrilaterals), each against something the mathematics fixes:
+  - a similarity map (rotation, scaling, shift) leaves the 2D SIPG matrix and
+    the LOR matrix unchanged;
+  - on an affine (sheared) map, a manufactured solution in the DG space is
+    reproduced exactly, with -Laplace(u) formed in closed form;
+  - on a bilinear map, harmonic polynomials that lie in the space give zero
+    residual on every element away from the boundary (element-wise
+    integration by parts, exact under the quadrature rule), and linear
+    functions do the same for the Q1 LOR blocks at the sub-grid's interior
+    nodes;
+  - element areas sum to the shoelace area of the domain, the load vector of
+    f = 1 sums to it, and the matrix is SPD."""
+import numpy as np
+import pytest
+
+from oracle import geometry, rhs, solver
+from paper_2009_01287_gb300 import inputs
+
+
+def _mesh(seed=1, pmin=1, pmax=4, base=3, depth=2):
+    return inputs.small_hp_mesh(seed, base=base, depth=depth, prob=0.5, pmin=pmin, pmax=pmax)
+
+
+def _shoelace(c):
+    q = np.asarray(c)[[0, 1, 3, 2]]      # corners in boundary order
+    x, y = q[:, 0], q[:, 1]
+    return 0.5 * abs(np.dot(x, np.roll(y, -1)) - np.dot(y, np.roll(x, -1)))
+
+
+def _interior_elements(topo):
+    bnd = set()
+    for f in topo.subfaces:
+        if f.kp < 0:
+            bnd.add(f.km)
+    return [k for k in range(topo.n) if k not in bnd]
+
+
+def test_bilinear_map_corners_and_jacobian():
+    c = np.array(inputs.QUADRILATERAL)
+    F = geometry.BilinearMap(c, 2.0, 3.0)
+    X = np.array([[0, 0], [2, 0], [0, 3], [2, 3]], dtype=float)
+    assert np.allclose(F(X), c, atol=1e-15)
+    # the Jacobian against central differences of the map
+    rng = np.random.default_rng(0)
+    P = rng.uniform([0, 0], [2, 3], size=(5, 2))
+    e = 1e-6
+    for j in range(2):
+        d = np.zeros(2)
+        d[j] = e
+        fd = (F(P + d) - F(P - d)) / (2 * e)
+        assert np.allclose(F.jacobian(P)[:, :, j], fd, atol=1e-8)
+
+
+def test_similarity_map_leaves_matrices_unchanged():
+    mesh = _mesh(2, pmax=5)
+    th, s, sh = 0.7, 1.3, np.array([0.4, -0.2])
+    R = s * np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    L = mesh.extent[0] * mesh.lattice_h
+    corners = [sh, sh + R @ [L, 0], sh + R @ [0, L], sh + R @ [L, L]]
+    pa = solver.build_problem(mesh)
+    pb = solver.build_problem(inputs.with_corners(mesh, corners))
+    assert abs(pa.A - pb.A).max() <= 1e-12 * abs(pa.A).max()
+    pca = solver.Preconditioner(pa, lor="exact")
+    pcb = solver.Preconditioner(pb, lor="exact")
+    assert abs(pca.Ac - pcb.Ac).max() <= 1e-12 * abs(pca.Ac).max()
+    for k in range(pa.topo.n):
+        assert abs(pb.space.hpen(k) - s * pa.space.hpen(k)) <= 1e-14
+
+
+def test_affine_map_reproduces_manufactured_solution():
+    # u = U(Phi^{-1}(x)), U(X, Y) = X (L - X) Y (L - Y): zero on the boundary
+    # of the parallelogram, in Q_2 of every element, so the discrete solution
+    # is u itself
+    mesh = _mesh(3, pmin=2, pmax=4)
+    c = np.array(inputs.PARALLELOGRAM)
+    md = inputs.with_corners(mesh, c)
+    L = mesh.extent[0] * mesh.lattice_h
+    A = np.stack([(c[1] - c[0]) / L, (c[2] - c[0]) / L], axis=1)      # x = c0 + A X
+    Ai = np.linalg.inv(A)
+    Gm = Ai @ Ai.T                                                   # d^2 / dx^2 = Ai^T H_X Ai
+
+    def pre(x):
+        return (x - c[0]) @ Ai.T
+
+    def u(x):
+        X = pre(x)
+        return X[:, 0] * (L - X[:, 0]) * X[:, 1] * (L - X[:, 1])
+
+    def f(x):   # -Laplace(u) = -tr(Gm H_X U)
+        X, Y = pre(x).T
+        hxx = -2.0 * Y * (L - Y)
+        hyy = -2.0 * X * (L - X)
+        hxy = (L - 2 * X) * (L - 2 * Y)
+        return -(Gm[0, 0] * hxx + 2 * Gm[0, 1] * hxy + Gm[1, 1] * hyy)
+
+    prob = solver.build_problem(md)
+    b = rhs.load_vector_fn(prob.space, f, extra=3)
+    x = np.linalg.solve(prob.A.toarray(), b)
+    ui = rhs.interpolate(prob.space, u)
+    assert np.abs(x - ui).max() <= 1e-10 * np.abs(ui).max()
+
+
+@pytest.mark.parametrize("fn", ["x2-y2", "xy", "linear"])
+def test_bilinear_map_harmonic_patch(fn):
+    pmin = 1 if fn == "linear" else 2
+    mesh = _mesh(4, pmin=pmin, pmax=5, base=4)
+    md = inputs.with_corners(mesh, inputs.QUADRILATERAL)
+    prob = solver.build_problem(md)
+    u = {"x2-y2": lambda x: x[:, 0] ** 2 - x[:, 1] ** 2,
+         "xy": lambda x: x[:, 0] * x[:, 1],
+         "linear": lambda x: 0.3 * x[:, 0] - 1.7 * x[:, 1] + 0.2}[fn]
+    ui = rhs.interpolate(prob.space, u)
+    r = prob.A @ ui
+    inner = _interior_elements(prob.topo)
+    assert inner
+    scale = np.abs(prob.A).max() * np.abs(ui).max()
+    for k in inner:
+        assert np.abs(r[prob.space.dofs(k)]).max() <= 1e-12 * scale
+    # the boundary rows do carry the boundary terms
+    assert np.abs(r).max() > 1e-6 * scale
+
+
+def test_bilinear_map_lor_patch():
+    mesh = _mesh(5, pmin=2, pmax=6)
+    md = inputs.with_corners(mesh, inputs.QUADRILATERAL)
+    prob = solver.build_problem(md)
+    u = lambda x: 0.8 * x[:, 0] + 0.5 * x[:, 1] - 0.1
+    for k in range(prob.topo.n):
+        p = int(prob.topo.p[k])
+        Ak = geometry.lor_element_mapped(prob.space, k)
+        assert np.abs(Ak - Ak.T).max() <= 1e-13 * np.abs(Ak).max()
+        r = Ak @ u(prob.space.node_coords(k))
+        n = p + 1
+        for j in range(1, p):
+            for i in range(1, p):
+                assert abs(r[j * n + i]) <= 1e-13 * np.abs(Ak).max()
+
+
+def test_mapped_lor_of_rectangle_is_q1_box():
+    g = np.array([[0.0, 0.0], [0.3, 0.0], [0.0, 0.7], [0.3, 0.7]])
+    from oracle import lor
+    assert np.abs(geometry.q1_quad_stiffness(g) - lor.q1_cell_stiffness(0.3, 0.7)).max() <= 1e-15
+
+
+@pytest.mark.parametrize("corners", [inputs.PARALLELOGRAM, inputs.QUADRILATERAL])
+def test_areas_and_load_vector_of_one(corners):
+    mesh = _mesh(6, pmax=3)
+    md = inputs.with_corners(mesh, corners)
+    prob = solver.build_problem(md)
+    tot = sum(prob.space.area(k) for k in range(prob.topo.n))
+    assert abs(tot - _shoelace(corners)) <= 1e-14
+    b = rhs.load_vector_fn(prob.space, lambda x: np.ones(len(x)))
+    assert abs(b.sum() - _shoelace(corners)) <= 1e-13
+
+
+def test_bilinear_map_spd():
+    mesh = _mesh(7, pmax=3)
+    md = inputs.with_corners(mesh, inputs.QUADRILATERAL)
+    A = solver.build_problem(md).A.toarray()
+    assert np.abs(A - A.T).max() <= 1e-12 * np.abs(A).max()
+    assert np.linalg.eigvalsh(A).min() > 0.0
+
+
+def test_non_convex_corners_rejected():
+    mesh = _mesh(1)
+    bad = ((0.0, 0.0), (1.0, 0.0), (0.0, 1.0), (0.2, 0.2))
+    with pytest.raises(ValueError):
+        solver.build_problem(inputs.with_corners(mesh, bad))
