@@ -19,10 +19,11 @@ Beside it the same line carries
                 distance of the GPU's mixed and FP64 solutions to it;
   cpu_baseline  the oracle timed on the host cores (one thread and all cores);
   workloads     sub-lines with their own clocks: the same mesh with BR2, the
-                16^3 cube workload, the batched form (256 problems x 4
-                right-hand sides in one launch) and a bounded sample of the
-                served form.
---workload hp2d-br2 | hp2d-coef | hp3d | batched | serving runs one of them as the line.
+                16^3 cube workload, the same mesh carried onto a general
+                quadrilateral (mapped elements), the batched form (256
+                problems x 4 right-hand sides in one launch) and a bounded
+                sample of the served form.
+--workload hp2d-br2 | hp2d-coef | hp2d-map | hp3d | batched | serving runs one of them as the line.
 
 --impl reference times the FP64 CPU oracle on the same workload (a bounded
 sample of PCG iterations per step).  Multi-GPU: independent replicas (the
@@ -63,6 +64,11 @@ WORKLOADC = ("2D hp-random 32x32 base, prob 0.3, depth<=3, p~U{1..6}, coefficien
              "parity, SIPG eta=100 (times the larger a of the two sides), tol 1e-8, seed 0")
 METRICC = ("DOF-iters/s (PCG on the 2D hp-random workload with a piecewise-constant coefficient, mixed FP32 "
            "preconditioner / FP64 outer)")
+WORKLOADM = ("2D hp-random 32x32 base, prob 0.3, depth<=3, p~U{1..6}, carried by the bilinear map of the unit "
+             "square onto the quadrilateral (0,0) (1.2,0.1) (0.15,0.95) (1.05,1.25), SIPG eta=100 "
+             "(h = sqrt(area)), p+2 Gauss points, tol 1e-8, seed 0")
+METRICM = ("DOF-iters/s (PCG on the 2D hp-random workload on mapped quadrilaterals, mixed FP32 preconditioner / "
+           "FP64 outer)")
 ORACLE_SAMPLE_ITERS = 20
 
 # DRAM bytes (read + write) of one launch of a kernel on a workload, from the
@@ -211,7 +217,7 @@ def time_solves(B, ctx, M, pc, b, x, tol, steps, warmup):
     return ms, it
 
 
-def operator_rooflines(B, ctx, M, mesh, peak_tf, peaks, three, tkey):
+def operator_rooflines(B, ctx, M, mesh, peak_tf, peaks, three, tkey, mapped=False):
     """The operator kernel and the trace kernel, each timed alone with CUDA
     events (L2 flushed before every launch)."""
     torch = ctx.torch
@@ -231,16 +237,25 @@ def operator_rooflines(B, ctx, M, mesh, peak_tf, peaks, three, tkey):
     tfl = trace_flops(mesh)
     kfl = st.apply_flops - tfl
     ach = kfl / (apply_ms / 1e3) / 1e12
-    name = "apply3_kernel (BR2 operator on cubes, FP64)" if three else "apply_kernel (SIPG operator, FP64)"
+    name = ("apply3_kernel (BR2 operator on cubes, FP64)" if three else
+            "apply_map_kernel (SIPG operator on mapped squares, FP64)" if mapped else
+            "apply_kernel (SIPG operator, FP64)")
+    model = ("FMAs of the kernel as formulated (x2), counted on the host from the mesh: volume 8 n^3, face "
+             "terms 8 n (n + n_nb) per sub-face side, test-function normal derivatives 8 n^2 per element "
+             "(n = p+1)")
+    if mapped:
+        model = ("FMAs of the kernel as formulated (x2), counted on the host from the mesh: volume at q = p+2 "
+                 "Gauss points 4 n q (n + q) plus 24 q^2 for the geometric factors, per sub-face side and "
+                 "Gauss point 6 (n + n_nb) + 60 (traces, geometry) and 6 n (side sums), test-function normal "
+                 "derivatives 8 n^2 per element (n = p+1)")
+    separable = not (three or mapped)
     main = {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
             "frac": ach / peak_tf, "traffic": traffic(tkey),
             "flops_per_launch": kfl, "launch_ms": apply_ms,
-            "flops_model": "FMAs of the kernel as formulated (x2), counted on the host from the mesh: "
-                           "volume 8 n^3, face terms 8 n (n + n_nb) per sub-face side, test-function "
-                           "normal derivatives 8 n^2 per element (n = p+1)",
-            "flops_survey_model_per_launch": survey_model_flops(mesh) if not three else None,
+            "flops_model": model,
+            "flops_survey_model_per_launch": survey_model_flops(mesh) if separable else None,
             "frac_survey_model": (survey_model_flops(mesh) / (apply_ms / 1e3) / 1e12 / peak_tf
-                                  if not three else None),
+                                  if separable else None),
             "algorithmic_bytes": st.apply_bytes,
             "hbm_gbs": st.apply_bytes / (apply_ms / 1e3) / 1e9,
             "hbm_frac": st.apply_bytes / (apply_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
@@ -299,7 +314,7 @@ def precond_rooflines(B, ctx, pc, peaks):
 
 
 def measure_single(B, ctx, mesh, rh, form, steps, warmup, peaks, peak_tf, tkey, three=False,
-                   e2e=False, keep_x=False, tune=False):
+                   e2e=False, keep_x=False, tune=False, mapped=False):
     """Mixed and FP64 solves of one workload, its kernels' rooflines."""
     torch = ctx.torch
     opts64 = B.make_options(form=form, precision=B.DG_PREC_FP64, lor=B.DG_LOR_AMG)
@@ -318,7 +333,7 @@ def measure_single(B, ctx, mesh, rh, form, steps, warmup, peaks, peak_tf, tkey, 
     clocks = ClockSampler(ctx.dev.index or 0).start()
     ms32, it32 = time_solves(B, ctx, M, pc32, b, x32, 1e-8, steps, warmup)
     ms64, it64 = time_solves(B, ctx, M, pc64, b, x64, 1e-8, steps, min(warmup, 2))
-    main, trace, apply_ms, trace_ms = operator_rooflines(B, ctx, M, mesh, peak_tf, peaks, three, tkey)
+    main, trace, apply_ms, trace_ms = operator_rooflines(B, ctx, M, mesh, peak_tf, peaks, three, tkey, mapped)
     blocks, whole, pc_ms = precond_rooflines(B, ctx, pc32, peaks)
     out = {"n_dofs": n, "n_elems": int(M.stats.n_elems), "setup_s": setup_s,
            "iters_mixed": statistics.median(it32), "iters_fp64": statistics.median(it64),
@@ -455,7 +470,8 @@ def _oracle_problem(which: str, seed: int):
         mesh, rh = inputs.config2(seed, base=4)
         prob = solver.build_problem(mesh, form="br2")
     else:
-        mesh, rh = inputs.config1_coeff(seed) if which == "hp2d-coef" else inputs.config1(seed)
+        mesh, rh = (inputs.config1_coeff(seed) if which == "hp2d-coef" else
+                    inputs.config1_mapped(seed) if which == "hp2d-map" else inputs.config1(seed))
         prob = solver.build_problem(mesh, form="br2" if which == "hp2d-br2" else "sipg")
     pc = solver.Preconditioner(prob, lor="amg")
     b = rhs.load_vector(prob.space, rh.amps, rh.waves)
@@ -559,20 +575,24 @@ def run_ours(args):
     three = args.workload == "hp3d"
     coef = args.workload == "hp2d-coef"
     br2 = args.workload == "hp2d-br2"
+    mapped = args.workload == "hp2d-map"
     if three:
         mesh, rh = inputs.config2(args.seed, base=args.base3)
     else:
-        mesh, rh = inputs.config1_coeff(args.seed) if coef else inputs.config1(args.seed)
+        mesh, rh = (inputs.config1_coeff(args.seed) if coef else
+                    inputs.config1_mapped(args.seed) if mapped else inputs.config1(args.seed))
     form = B.DG_FORM_BR2 if (three or br2) else B.DG_FORM_SIPG
     metric, workload = ((METRIC3, WORKLOAD3) if three else (METRICC, WORKLOADC) if coef else
+                        (METRICM, WORKLOADM) if mapped else
                         (METRIC_BR2, WORKLOAD_BR2) if br2 else (METRIC, WORKLOAD))
     peaks, peak_kind = _peaks()
     probe = fp64_peak(B, ctx)
     if dist:
         dist.barrier()
-    res = measure_single(B, ctx, mesh, rh, form, args.steps, args.warmup, peaks, probe["tflops"],
-                         "apply3_kernel/hp3d" if three else ("apply_kernel/hp2d" if not (coef or br2) else "none"),
-                         three=three, e2e=True, keep_x=True, tune=args.tune_tiles)
+    tkey = ("apply3_kernel/hp3d" if three else "apply_map_kernel/hp2d-map" if mapped else
+            "apply_kernel/hp2d" if not (coef or br2) else "none")
+    res = measure_single(B, ctx, mesh, rh, form, args.steps, args.warmup, peaks, probe["tflops"], tkey,
+                         three=three, e2e=True, keep_x=True, tune=args.tune_tiles, mapped=mapped)
     ms32, it32, ms64, it64 = res.pop("_raw")
     t_e2e, it_e2e = res.pop("_e2e")
     x32, x64 = res.pop("_x")
@@ -642,6 +662,13 @@ def run_ours(args):
             h3.pop(k, None)
         extras["hp3d"] = {"workload": WORKLOAD3, "metric": "DOF-iters/s", "value": h3["dof_iters_per_s_mixed"],
                           **h3}
+        mm, rm = inputs.config1_mapped(args.seed)
+        hm = measure_single(B, ctx, mm, rm, B.DG_FORM_SIPG, 3, 2, peaks, probe["tflops"],
+                            "apply_map_kernel/hp2d-map", mapped=True)
+        for k in ("_raw", "_e2e", "_x"):
+            hm.pop(k, None)
+        extras["hp2d_map"] = {"workload": WORKLOADM, "metric": "DOF-iters/s", "value": hm["dof_iters_per_s_mixed"],
+                              **hm}
         extras["batched"] = run_batched_leg(B, ctx, 2, 1)
         extras["serving"] = run_serving_leg(B, 8, 160, 200.0, 8)
         out["workloads"] = extras
@@ -690,12 +717,15 @@ def run_reference(args):
         return
     if args.workload in ("batched", "serving"):
         print(json.dumps({"impl": "reference", "unavailable": f"the oracle has no {args.workload} form; "
-                          "its single-problem PCG is timed by the hp2d, hp2d-br2, hp2d-coef and hp3d workloads"}))
+                          "its single-problem PCG is timed by the hp2d, hp2d-br2, hp2d-coef, hp2d-map and hp3d "
+                          "workloads"}))
         return
     three = args.workload == "hp3d"
     coef = args.workload == "hp2d-coef"
     br2 = args.workload == "hp2d-br2"
+    mapped = args.workload == "hp2d-map"
     metric, workload = ((METRIC3, WORKLOAD3) if three else (METRICC, WORKLOADC) if coef else
+                        (METRICM, WORKLOADM) if mapped else
                         (METRIC_BR2, WORKLOAD_BR2) if br2 else (METRIC, WORKLOAD))
     prob, pc, b = _oracle_problem(args.workload, args.seed)
     for _ in range(args.warmup):
@@ -738,7 +768,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="only the line's own workload")
     ap.add_argument("--workload", default="hp2d",
-                    choices=["hp2d", "hp2d-br2", "hp2d-coef", "hp3d", "batched", "serving"])
+                    choices=["hp2d", "hp2d-br2", "hp2d-coef", "hp2d-map", "hp3d", "batched", "serving"])
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-meshes", type=int, default=16)

@@ -61,8 +61,22 @@ typedef struct dg_precond dg_precond;
  * {a grad u}; the SIPG penalty of a sub-face and both sides' BR2 lifting
  * energies take the larger a of its two sides; the LOR blocks are weighted by
  * a_kappa.
- * A value that is not positive and finite is DG_EINVAL.  All pointers are
- * HOST pointers, read during the call. */
+ * A value that is not positive and finite is DG_EINVAL.
+ * corners: NULL (the boxes themselves), or, squares only, 8 doubles: the
+ * physical (x, y) images of the lattice domain's corners (0, 0), (X, 0),
+ * (0, Y), (X, Y) (X, Y = extent * lattice_h), in that order.  The boxes are
+ * then pre-images: the bilinear map of the domain onto the quadrilateral with
+ * these corners carries every leaf box to its element, so T_kappa of
+ * Section 2 is that map after the box's own affine map (parallelograms when
+ * the corners form one, general convex quadrilaterals otherwise; straight
+ * sub-faces, the same hanging structure).  Integrals on such elements use
+ * p+2 Gauss points per direction on the volume and max(p-, p+)+2 on a
+ * sub-face, the SIPG penalty takes h_kappa = sqrt(area of kappa), and the LOR
+ * blocks are the Q1 stiffness on the mapped Gauss-Lobatto cells.  SIPG only:
+ * corners with DG_FORM_BR2 are DG_EUNSUPPORTED, as are corners in a batch.
+ * Corners that do not bound a convex, counter-clockwise quadrilateral (det
+ * of the map's Jacobian not positive at a corner) are DG_EINVAL.
+ * All pointers are HOST pointers, read during the call. */
 typedef struct {
   int dim;
   int64_t n_elems;
@@ -72,6 +86,7 @@ typedef struct {
   const int32_t* extent;
   double lattice_h;
   const double* coeff;
+  const double* corners;
 } dg_mesh_desc;
 
 enum { DG_FORM_SIPG = 0, DG_FORM_BR2 = 1 };

@@ -40,7 +40,7 @@ class DgMeshDesc(C.Structure):
     _fields_ = [("dim", C.c_int), ("n_elems", C.c_int64), ("lo", C.POINTER(C.c_int32)),
                 ("size", C.POINTER(C.c_int32)), ("p", C.POINTER(C.c_int32)),
                 ("extent", C.POINTER(C.c_int32)), ("lattice_h", C.c_double),
-                ("coeff", C.POINTER(C.c_double))]
+                ("coeff", C.POINTER(C.c_double)), ("corners", C.POINTER(C.c_double))]
 
 
 class DgOptions(C.Structure):
@@ -169,11 +169,15 @@ def make_desc(mesh: MeshDesc):
     coeff = getattr(mesh, "coeff", None)
     if coeff is not None:
         coeff = np.ascontiguousarray(coeff, dtype=np.float64)
-    keep = (lo, size, p, ext, coeff)
+    corners = getattr(mesh, "corners", None)
+    if corners is not None:
+        corners = np.ascontiguousarray(corners, dtype=np.float64).reshape(8)
+    keep = (lo, size, p, ext, coeff, corners)
     d = DgMeshDesc(mesh.dim, mesh.n_elems, lo.ctypes.data_as(C.POINTER(C.c_int32)),
                    size.ctypes.data_as(C.POINTER(C.c_int32)), p.ctypes.data_as(C.POINTER(C.c_int32)),
                    ext.ctypes.data_as(C.POINTER(C.c_int32)), float(mesh.lattice_h),
-                   None if coeff is None else coeff.ctypes.data_as(C.POINTER(C.c_double)))
+                   None if coeff is None else coeff.ctypes.data_as(C.POINTER(C.c_double)),
+                   None if corners is None else corners.ctypes.data_as(C.POINTER(C.c_double)))
     return d, keep
 
 
@@ -392,6 +396,7 @@ def inspect_lib():
         vp = C.c_void_p
         L.dginspect_create.argtypes = [C.POINTER(DgMeshDesc), C.POINTER(DgOptions), C.c_int]
         L.dginspect_create.restype = vp
+        L.dginspect_last_status.restype = C.c_int
         L.dginspect_destroy.argtypes = [vp]
         L.dginspect_last_error.restype = C.c_char_p
         for n in ("dginspect_sizes", "dginspect_kind", "dginspect_dinv"):
@@ -462,7 +467,7 @@ class HostSetup:
         o = opts or make_options()
         self.h = L.dginspect_create(C.byref(d), C.byref(o), 1 if amg else 0)
         if not self.h:
-            raise DGError(DG_EINVAL, L.dginspect_last_error().decode())
+            raise DGError(int(L.dginspect_last_status()), L.dginspect_last_error().decode())
         s = np.zeros(9, dtype=np.int64)
         L.dginspect_sizes(self.h, s.ctypes.data)
         self.n, self.nC, nnzP, nnzA, nb, nbd, self.n_levels, eta, nsq = (int(v) for v in s)

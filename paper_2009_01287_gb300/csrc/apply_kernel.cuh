@@ -194,6 +194,12 @@ struct ApplyArgs {
   int n_tiles;
   unsigned* sched;            // [0] next tile, [1] exit ticket (both zero between launches)
   BasisOff boff[kMaxP + 1];
+  // mapped squares: per sub-face record its rule, tables and penalty; per
+  // element its pre-image box (X0, Y0, h); the domain map; the volume tables
+  const SubFaceMap* sfm;
+  const double* xo;
+  DomainMap dmap;
+  MapOff moff[kMaxP + 1];
 };
 
 template <int P>

@@ -2,6 +2,7 @@
 // Section 4.4): the trace kernels, the persistent operator kernels of square
 // and cube meshes, their shared-memory sizing and resident grid.  The tile
 // work itself is in apply_kernel.cuh and apply3_kernel.cuh.
+#include "apply_map_kernel.cuh"
 #include "kernels.cuh"
 
 namespace dg {
@@ -95,6 +96,35 @@ __global__ void __launch_bounds__(kThreads) apply_kernel(const ApplyArgs A) {
   apply_exit(A, red);
 }
 
+// Persistent operator kernel of mapped squares (same scheduling as on boxes).
+__global__ void __launch_bounds__(kThreads) apply_map_kernel(const ApplyArgs A) {
+  pdl_entry();
+  extern __shared__ __align__(16) double smem[];
+  __shared__ double red[kThreads];
+  __shared__ int s_tile;
+  while (true) {
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(A.sched, 1u);
+    __syncthreads();
+    const int t = s_tile;
+    __syncthreads();
+    if (t >= A.n_tiles) break;
+    const ApplyTile T = A.tiles[t];
+    switch (T.p) {
+      case 1: apply_map_tile<1>(A, T, t, smem, red); break;
+      case 2: apply_map_tile<2>(A, T, t, smem, red); break;
+      case 3: apply_map_tile<3>(A, T, t, smem, red); break;
+      case 4: apply_map_tile<4>(A, T, t, smem, red); break;
+      case 5: apply_map_tile<5>(A, T, t, smem, red); break;
+      case 6: apply_map_tile<6>(A, T, t, smem, red); break;
+      case 7: apply_map_tile<7>(A, T, t, smem, red); break;
+      case 8: apply_map_tile<8>(A, T, t, smem, red); break;
+      default: break;
+    }
+    __syncthreads();
+  }
+  apply_exit(A, red);
+}
+
 __global__ void __launch_bounds__(kThreads) trace3_kernel(const ApplyArgs A) {
   pdl_entry();
   const ApplyTile T = A.tiles[blockIdx.x];
@@ -155,8 +185,30 @@ static int apply_shape_smem(int p) {
   }
 }
 
+static int map_shape_smem(int p) {
+  switch (p) {
+    case 1: return MapShape<1>::PART;
+    case 2: return MapShape<2>::PART;
+    case 3: return MapShape<3>::PART;
+    case 4: return MapShape<4>::PART;
+    case 5: return MapShape<5>::PART;
+    case 6: return MapShape<6>::PART;
+    case 7: return MapShape<7>::PART;
+    default: return MapShape<8>::PART;
+  }
+}
+
 int64_t apply_smem_for(const dg_mesh& M) {
   if (M.host.dim == 3) return M.apply3_smem;
+  if (M.host.mapped) {   // the tile's layout plus 3 weights per (item, Gauss point)
+    int64_t mx = 0;
+    for (int t = 0; t < M.n_tiles; ++t) {
+      const ApplyTile& T = M.h_tiles[t];
+      const int64_t nit = M.h_item_ptr[t + 1] - M.h_item_ptr[t];
+      mx = std::max<int64_t>(mx, map_shape_smem(T.p) + 3 * kMapQMax * nit);
+    }
+    return 8 * mx;
+  }
   // the layout of the tile's degree plus its sub-face item partials
   int64_t mx = 0;
   for (int t = 0; t < M.n_tiles; ++t) {
@@ -198,6 +250,10 @@ ApplyArgs make_apply_args(const dg_mesh& M, const double* x, double* y, Reduce r
   A.n_tiles = M.n_tiles;
   A.sched = M.d_sched;
   for (int p = 0; p <= kMaxP; ++p) A.boff[p] = M.boff[p];
+  A.sfm = M.d_sfm;
+  A.xo = M.d_xo;
+  A.dmap = M.dmap;
+  for (int p = 0; p <= kMaxP; ++p) A.moff[p] = M.moff[p];
   return A;
 }
 
@@ -223,6 +279,11 @@ int apply_kernel_setup(const dg_mesh& M) {
   }
   const int smem = (int)M.apply_smem;
   DG_REQUIRE(smem <= optin, "operator tile needs too much shared memory");
+  if (M.host.mapped) {
+    DG_CUDA(cudaFuncSetAttribute(apply_map_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, apply_map_kernel, kThreads, smem));
+    return sms * (per > 0 ? per : 1);
+  }
   DG_CUDA(cudaFuncSetAttribute(apply_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   DG_CUDA(cudaFuncSetAttribute(apply_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   if (br2)
@@ -257,7 +318,8 @@ void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cuda
   }
   const int smem = (int)M.apply_smem;
   if (with_trace) launch_k(trace_kernel, M.n_tiles, kThreads, 0, s, A);
-  if (M.opts.form == DG_FORM_BR2) launch_k(apply_kernel<true>, grid, kThreads, smem, s, A);
+  if (M.host.mapped) launch_k(apply_map_kernel, grid, kThreads, smem, s, A);
+  else if (M.opts.form == DG_FORM_BR2) launch_k(apply_kernel<true>, grid, kThreads, smem, s, A);
   else launch_k(apply_kernel<false>, grid, kThreads, smem, s, A);
   DG_CUDA(cudaGetLastError());
 }

@@ -440,7 +440,8 @@ dg_status dg_batch_create(const dg_mesh_desc* descs, int n_problems, int n_rhs,
   try {
     DG_REQUIRE(descs && n_problems >= 1 && n_rhs >= 1, "bad batch size");
     for (int k = 0; k < n_problems; ++k)
-      if (descs[k].dim != 2) throw Error(DG_EUNSUPPORTED, "the batched solver takes square meshes only");
+      if (descs[k].dim != 2 || descs[k].corners)
+        throw Error(DG_EUNSUPPORTED, "the batched solver takes unmapped square meshes only");
     dg_options o{};
     o.form = DG_FORM_SIPG;
     o.precision = DG_PREC_MIXED;

@@ -83,6 +83,8 @@ void upload_mesh(dg_mesh* M, cudaStream_t s) {
   M->d_sf = a.upload(M->h_sf, s);
   M->d_sfb = M->h_sfb.empty() ? nullptr : a.upload(M->h_sfb, s);
   M->d_sf3 = a.upload(M->h_sf3, s);
+  M->d_sfm = M->h_sfm.empty() ? nullptr : a.upload(M->h_sfm, s);
+  M->d_xo = M->h_xo.empty() ? nullptr : a.upload(M->h_xo, s);
   M->d_tables = a.upload(M->h_tables, s);
   M->d_sched = a.alloc<unsigned>(2);
   DG_CUDA(cudaMemsetAsync(M->d_sched, 0, 2 * sizeof(unsigned), s));
@@ -116,14 +118,26 @@ void host_rhs_sine(const dg_mesh& mesh, int n_modes, const double* amps, const i
     for (int gz = 0; gz < qz; ++gz)
       for (int gy = 0; gy < q; ++gy)
         for (int gxi = 0; gxi < q; ++gxi) {
-          const double X[3] = {x0[0] + h * gx[gxi], x0[1] + h * gx[gy], x0[2] + h * gx[gz]};
+          double X[3] = {x0[0] + h * gx[gxi], x0[1] + h * gx[gy], x0[2] + h * gx[gz]};
+          double detJ = 1.0;
+          if (m.mapped) {   // f at the physical point, the weight times det J
+            const Jac2 J = domain_jacobian(mesh.dmap, X[0], X[1]);
+            detJ = J.j0 * J.j3 - J.j1 * J.j2;
+            const double s = X[0] / (m.extent[0] * m.lh), t = X[1] / (m.extent[1] * m.lh);
+            const double wc[4] = {(1 - s) * (1 - t), s * (1 - t), (1 - s) * t, s * t};
+            X[0] = X[1] = 0.0;
+            for (int a = 0; a < 4; ++a) {
+              X[0] += wc[a] * m.corners[2 * a];
+              X[1] += wc[a] * m.corners[2 * a + 1];
+            }
+          }
           double f = 0.0;
           for (int md = 0; md < n_modes; ++md) {
             double t = amps[md];
             for (int d = 0; d < dim; ++d) t *= std::sin(M_PI * waves[dim * md + d] * X[d]);
             f += t;
           }
-          double w = gw[gxi] * gw[gy] * h * h * f;
+          double w = gw[gxi] * gw[gy] * h * h * f * detJ;
           if (dim == 3) w *= gw[gz] * h;
           for (int iz = 0; iz < nz; ++iz) {
             const double lz = dim == 3 ? L[(size_t)gz * NP + iz] : 1.0;

@@ -139,6 +139,48 @@ struct ApplyTile {
   int32_t chunk;     // 3D: sub-face items processed at a time
 };
 
+// ------------------------------------------------------------------ mapped squares
+// The bilinear map of the lattice domain onto a quadrilateral (dg_mesh_desc
+// corners c0..c3, the images of (0,0), (Lx,0), (0,Ly), (Lx,Ly)).  In the
+// pre-image coordinates (X, Y) its Jacobian columns are
+//   dPhi/dX = u1 + Y u3,  dPhi/dY = u2 + X u3,
+// u1 = (c1 - c0) / Lx, u2 = (c2 - c0) / Ly, u3 = (c3 - c2 - c1 + c0) / (Lx Ly).
+struct DomainMap {
+  double u1x, u1y, u2x, u2y, u3x, u3y;
+};
+// the Jacobian of the domain map at the pre-image point (X, Y):
+// j0 = dx/dX, j1 = dx/dY, j2 = dy/dX, j3 = dy/dY
+struct Jac2 {
+  double j0, j1, j2, j3;
+};
+__host__ __device__ inline Jac2 domain_jacobian(const DomainMap& D, double X, double Y) {
+  return Jac2{D.u1x + Y * D.u3x, D.u2x + X * D.u3x, D.u1y + Y * D.u3y, D.u2y + X * D.u3y};
+}
+// Gauss points per direction of the mapped integrals: p + 2 on the volume,
+// max(p-, p+) + 2 on a sub-face
+constexpr int kMapQExtra = 1;
+constexpr int kMapQMax = kMaxP + 1 + kMapQExtra;
+
+// One sub-face of a mapped square mesh seen from one side (beside the
+// SubFaceRec of the same index): its Gauss rule, both sides' 1D basis values
+// and derivatives at the rule's points, its place in the pre-image and its
+// penalty.
+struct SubFaceMap {
+  int32_t qf;       // Gauss points, max(p, pn) + 2
+  int32_t tab_g;    // the rule on [0, 1]: qf points, then qf weights
+  int32_t tab_bo;   // own side: l_i(s_g) (qf rows of p+1), then l_i'(s_g)
+  int32_t tab_bn;   // the neighbour's side, the same with pn (boundary: tab_bo)
+  double xc;        // pre-image coordinate of the side's line (along its normal axis)
+  double xt0, xt1;  // pre-image tangential extent of the sub-face
+  double sigma;     // SIPG penalty with h_kappa = sqrt(area of kappa)
+};
+
+// Offsets of the degree-p volume tables of mapped meshes: the (p+2)-point
+// Gauss rule (points, weights) and l_j, l_j' at its points ((p+2) x (p+1)).
+struct MapOff {
+  int gx, gw, B, D;
+};
+
 // ------------------------------------------------------------------ mesh (host topology)
 // a_kappa of every element from a mesh description (all 1 when coeff is NULL)
 inline void copy_coeff(const dg_mesh_desc* d, std::vector<double>& coef) {
@@ -160,6 +202,8 @@ struct HostMesh {
   int32_t extent[3] = {0, 0, 1};
   double lh = 1.0;
   std::vector<double> coef;     // n coefficients a (1 when none given)
+  bool mapped = false;          // squares carried by the bilinear map of `corners`
+  double corners[8] = {0.0};    // images of (0,0), (Lx,0), (0,Ly), (Lx,Ly), (x, y) each
   std::vector<int64_t> off;     // n+1 DOF offsets
   std::vector<int32_t> cellmap; // lattice cell (x fastest) -> element
 

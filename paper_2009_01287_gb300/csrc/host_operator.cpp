@@ -12,6 +12,10 @@
 namespace dg {
 
 void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double* y) {
+  if (M.host.mapped) {
+    host_element_residual_map(M, k, x, y);
+    return;
+  }
   const HostMesh& m = M.host;
   const int P = m.p[k], NP = P + 1, NN = NP * NP;
   const Basis1D& B = basis1d(P);
@@ -146,6 +150,10 @@ void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double*
 // function (its trace is l_i on that side, its outward normal derivative is
 // dv l_i, dv = l_edge'(edge) / h with the outward sign).
 void host_element_diag(const dg_mesh& M, int64_t k, double* d) {
+  if (M.host.mapped) {
+    host_element_diag_map(M, k, d);
+    return;
+  }
   const HostMesh& m = M.host;
   const int P = m.p[k], NP = P + 1;
   const Basis1D& B = basis1d(P);

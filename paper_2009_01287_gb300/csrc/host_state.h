@@ -114,6 +114,12 @@ struct dg_mesh {
   std::vector<dg::SubFaceRec> h_sf;
   std::vector<dg::SubFaceBr2> h_sfb;    // square meshes, BR2: one per h_sf record
   std::vector<dg::SubFaceRec3> h_sf3;   // cube meshes
+  // mapped squares: one record per h_sf record, the volume tables of each
+  // degree, the map, and per element its pre-image corner and edge (X0, Y0, h)
+  std::vector<dg::SubFaceMap> h_sfm;
+  dg::MapOff moff[dg::kMaxP + 1];
+  dg::DomainMap dmap{};
+  std::vector<double> h_xo;
   int64_t apply3_smem = 0;              // dynamic shared memory of the 3D operator kernel
   std::vector<double> h_tables;
   dg::BasisOff boff[dg::kMaxP + 1];
@@ -147,6 +153,8 @@ struct dg_mesh {
   dg::SubFaceRec* d_sf = nullptr;
   dg::SubFaceBr2* d_sfb = nullptr;
   dg::SubFaceRec3* d_sf3 = nullptr;
+  dg::SubFaceMap* d_sfm = nullptr;   // mapped squares
+  double* d_xo = nullptr;            // mapped squares: 3 per element
   double* d_tables = nullptr;
   int32_t* d_order = nullptr;
   dg::ApplyTile* d_tiles = nullptr;
@@ -230,6 +238,15 @@ void upload_tiles(dg_mesh* M, cudaStream_t s);
 void tune_tiles(dg_mesh* M, cudaStream_t s, void (*retile)(dg_mesh*, void*), void* ctx);
 // cube meshes: topology, records, tables, tiles, stats (opts already validated)
 void build_mesh_host3(dg_mesh* M, const dg_mesh_desc* desc, const dg_options& opts);
+// mapped squares: records, tables and geometry (after the SIPG records), and
+// the flop and byte counts of the mapped operator (after the box counts)
+void build_mesh_map(dg_mesh* M);
+void map_stats(dg_mesh* M);
+// rows of element k of y = A x on a mapped mesh, and their diagonal, and the
+// LOR block of element k (dense (p+1)^2 x (p+1)^2, row-major)
+void host_element_residual_map(const dg_mesh& M, int64_t k, const double* x, double* y);
+void host_element_diag_map(const dg_mesh& M, int64_t k, double* d);
+void host_lor_block_map(const dg_mesh& M, int64_t k, double* A);
 // rows of element k of y = A x (x: full host vector), same formulation as the kernel
 void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double* y);
 void host_element_residual3(const dg_mesh& M, int64_t k, const double* x, double* y);

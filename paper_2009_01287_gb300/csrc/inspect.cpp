@@ -21,6 +21,7 @@ struct Inspect {
   std::string err;
 };
 thread_local std::string g_err;
+thread_local int g_status = DG_OK;
 }  // namespace
 
 namespace dg {
@@ -30,6 +31,8 @@ void set_last_error(const std::string& msg) { g_err = msg; }
 extern "C" {
 
 const char* dginspect_last_error(void) { return g_err.c_str(); }
+// the dg_status of the last failed dginspect_create (DG_EINVAL for other errors)
+int dginspect_last_status(void) { return g_status; }
 
 // Work units of the block solves for blocks of the given sizes, slots and
 // inverse offsets (see plan_block_units).  unit: 4 * cap ints, ubase: cap,
@@ -88,9 +91,15 @@ void* dginspect_create(const dg_mesh_desc* desc, const dg_options* opts, int wit
     I->pc = (I->mesh.host.dim == 3) ? build_host_precond3(I->mesh, o) : build_host_precond(I->mesh, o);
     if (with_amg && I->pc.nC > 0)
       I->amg = amg_setup(I->pc.Ac, I->mesh.host.dim == 3 ? kAmgTheta3 : kAmgTheta);
+    g_status = DG_OK;
     return I.release();
+  } catch (const Error& e) {
+    g_err = e.what();
+    g_status = e.code;
+    return nullptr;
   } catch (const std::exception& e) {
     g_err = e.what();
+    g_status = DG_EINVAL;
     return nullptr;
   }
 }

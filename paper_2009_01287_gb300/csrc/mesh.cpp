@@ -286,6 +286,14 @@ void build_mesh_host(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opt
     return;
   }
   validate_and_copy(desc, m);
+  if (desc->corners) {
+    if (o.form != DG_FORM_SIPG) throw Error(DG_EUNSUPPORTED, "mapped elements (corners): SIPG only");
+    for (int i = 0; i < 8; ++i) {
+      DG_REQUIRE(std::isfinite(desc->corners[i]), "corners must be finite");
+      m.corners[i] = desc->corners[i];
+    }
+    m.mapped = true;
+  }
   build_topology(m);
   M->n_dofs = m.off[m.n];
   DG_REQUIRE(M->n_dofs < (1LL << 31), "too many unknowns for 32-bit indices");
@@ -433,6 +441,7 @@ void build_mesh_host(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opt
     g.tab_x += base;
     g.tab_y += base;
   }
+  if (m.mapped) build_mesh_map(M);   // the mapped records and tables
   build_tiles(M);
   // operation and byte counts of one operator apply, as the kernel does it
   dg_mesh_stats& S = M->stats;
@@ -468,6 +477,7 @@ void build_mesh_host(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opt
   S.apply_flops = fl;
   S.apply_bytes = 16.0 * (double)M->n_dofs + (double)m.n * (4 + 8 + 8 + 4 + 16) +
                   (double)m.sf.size() * sizeof(SubFaceRec);
+  if (m.mapped) map_stats(M);
 }
 
 }  // namespace dg

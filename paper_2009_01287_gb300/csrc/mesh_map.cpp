@@ -1,0 +1,426 @@
+// Mapped square meshes (Section 2: element maps T_kappa onto general
+// quadrilaterals).  The leaf boxes of the lattice are pre-images; the bilinear
+// map of the lattice domain onto the quadrilateral with the given corners
+// carries them to the elements.  This file builds what the mapped operator
+// kernel reads - the map, each element's pre-image box, per sub-face its Gauss
+// rule, both sides' 1D basis values and derivatives at the rule's points and
+// its penalty, per degree the volume rule - and holds the host mirror of that
+// kernel (element rows, their diagonal) and the LOR blocks on mapped cells
+// (Section 3.4).
+//
+// The SIPG form is the one of boxes, evaluated at Gauss points:
+//   volume  int a grad u . grad v = int a (grad_xi u)^T G (grad_xi v) dxi,
+//           G = det(J) J^-1 J^-T of the domain map at the point (the box's own
+//           scaling cancels in 2D), p+2 points per direction;
+//   faces   on every sub-face, max(p-, p+)+2 points, arc length |J t| dt,
+//           physical normal n = J^-T nu / |J^-T nu| (nu the pre-image normal),
+//           grad u . n = grad_X u . (J^-1 n) with grad_X u from the side's trace
+//           values (tangential) and its normal-derivative line (normal),
+//           sigma = a_e eta p_e^2 / min(h-, h+) with h_kappa = sqrt(|kappa|).
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <numeric>
+#include <tuple>
+#include <vector>
+
+#include "dg_internal.h"
+#include "host_state.h"
+
+namespace dg {
+
+namespace {
+
+int append_rule(std::vector<double>& t, int q, std::map<int, int>& cache) {
+  auto it = cache.find(q);
+  if (it != cache.end()) return it->second;
+  std::vector<double> x, w;
+  gauss_rule(q, x, w);
+  const int off = (int)t.size();
+  t.insert(t.end(), x.begin(), x.end());
+  t.insert(t.end(), w.begin(), w.end());
+  cache.emplace(q, off);
+  return off;
+}
+
+// degree-p values and derivatives at the points s_g = (num + len x_g) / den of
+// the q-point Gauss rule: q rows of p+1 values, then q rows of derivatives
+int append_side_table(std::vector<double>& t, int p, int q, int num, int len, int den,
+                      std::map<std::tuple<int, int, int, int, int>, int>& cache) {
+  const int g = std::gcd(std::gcd(num, len), den);
+  const auto key = std::make_tuple(p, q, num / g, len / g, den / g);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  std::vector<double> x, w;
+  gauss_rule(q, x, w);
+  const int n = p + 1;
+  const int off = (int)t.size();
+  t.resize(off + 2 * (size_t)q * n);
+  const auto& nodes = basis1d(p).nodes;
+  for (int r = 0; r < q; ++r) {
+    const double s = ((double)num + (double)len * x[r]) / (double)den;
+    lagrange_eval(nodes, s, &t[off + (size_t)r * n]);
+    lagrange_deriv_eval(nodes, s, &t[off + (size_t)(q + r) * n]);
+  }
+  cache.emplace(key, off);
+  return off;
+}
+
+// det J of the domain map is linear in (X, Y) (the XY terms cancel), so its
+// mean over a box is its value at the centre
+double box_area(const DomainMap& D, double X0, double Y0, double h) {
+  const Jac2 J = domain_jacobian(D, X0 + 0.5 * h, Y0 + 0.5 * h);
+  return (J.j0 * J.j3 - J.j1 * J.j2) * h * h;
+}
+
+}  // namespace
+
+void build_mesh_map(dg_mesh* M) {
+  HostMesh& m = M->host;
+  const double Lx = m.extent[0] * m.lh, Ly = m.extent[1] * m.lh;
+  const double* c = m.corners;
+  DomainMap& D = M->dmap;
+  D.u1x = (c[2] - c[0]) / Lx;
+  D.u1y = (c[3] - c[1]) / Lx;
+  D.u2x = (c[4] - c[0]) / Ly;
+  D.u2y = (c[5] - c[1]) / Ly;
+  D.u3x = (c[6] - c[4] - c[2] + c[0]) / (Lx * Ly);
+  D.u3y = (c[7] - c[5] - c[3] + c[1]) / (Lx * Ly);
+  // det J is linear in (X, Y): positive everywhere iff at the four corners
+  const double XY[4][2] = {{0.0, 0.0}, {Lx, 0.0}, {0.0, Ly}, {Lx, Ly}};
+  for (const auto& p : XY) {
+    const Jac2 J = domain_jacobian(D, p[0], p[1]);
+    DG_REQUIRE(J.j0 * J.j3 - J.j1 * J.j2 > 0.0,
+               "corners do not bound a convex, counter-clockwise quadrilateral");
+  }
+  // element pre-image boxes and penalty sizes h_kappa = sqrt(|kappa|)
+  M->h_xo.resize(3 * (size_t)m.n);
+  std::vector<double> hpen(m.n);
+  for (int64_t k = 0; k < m.n; ++k) {
+    const double X0 = m.lo[2 * k] * m.lh, Y0 = m.lo[2 * k + 1] * m.lh, h = m.size[k] * m.lh;
+    M->h_xo[3 * k] = X0;
+    M->h_xo[3 * k + 1] = Y0;
+    M->h_xo[3 * k + 2] = h;
+    hpen[k] = std::sqrt(box_area(D, X0, Y0, h));
+  }
+  // tables, appended after the box tables
+  std::vector<double>& T = M->h_tables;
+  std::map<int, int> rules;
+  std::map<std::tuple<int, int, int, int, int>, int> sides;
+  for (int p = 1; p <= kMaxP; ++p) {
+    const int q = p + 1 + kMapQExtra, n = p + 1;
+    const int r = append_rule(T, q, rules);
+    M->moff[p].gx = r;
+    M->moff[p].gw = r + q;
+    std::vector<double> x(T.begin() + r, T.begin() + r + q);
+    const auto& nodes = basis1d(p).nodes;
+    M->moff[p].B = (int)T.size();
+    T.resize(T.size() + 2 * (size_t)q * n);
+    M->moff[p].D = M->moff[p].B + q * n;
+    for (int g = 0; g < q; ++g) {
+      lagrange_eval(nodes, x[g], &T[M->moff[p].B + (size_t)g * n]);
+      lagrange_deriv_eval(nodes, x[g], &T[M->moff[p].D + (size_t)g * n]);
+    }
+  }
+  M->moff[0] = M->moff[1];
+  M->h_sfm.assign(m.sf.size(), SubFaceMap{});
+  const dg_options& o = M->opts;
+  for (int64_t k = 0; k < m.n; ++k)
+    for (int s = 0; s < 4; ++s) {
+      int axis, cc, t0, t1;
+      m.side_segment((int)k, s, axis, cc, t0, t1);
+      const int P = m.p[k];
+      for (int j = m.sf_ptr[4 * k + s]; j < m.sf_ptr[4 * k + s + 1]; ++j) {
+        const auto& f = m.sf[j];
+        SubFaceMap& r = M->h_sfm[j];
+        const int len = f.t1 - f.t0;
+        int pe = P;
+        double he = hpen[k], ae = m.coef[k];
+        if (f.nb >= 0) {
+          pe = std::max(P, m.p[f.nb]);
+          he = std::min(he, hpen[f.nb]);
+          ae = std::max(ae, m.coef[f.nb]);
+        }
+        r.qf = pe + 1 + kMapQExtra;
+        r.tab_g = append_rule(T, r.qf, rules);
+        r.tab_bo = append_side_table(T, P, r.qf, f.t0 - t0, len, m.size[k], sides);
+        if (f.nb >= 0) {
+          int na, nc, n0, n1;
+          m.side_segment(f.nb, f.nb_side, na, nc, n0, n1);
+          r.tab_bn = append_side_table(T, m.p[f.nb], r.qf, f.t0 - n0, len, m.size[f.nb], sides);
+        } else {
+          r.tab_bn = r.tab_bo;
+        }
+        r.xc = cc * m.lh;
+        r.xt0 = f.t0 * m.lh;
+        r.xt1 = f.t1 * m.lh;
+        const double pp = (o.penalty_form == DG_PENALTY_P1SQ) ? (pe + 1.0) : (double)pe;
+        r.sigma = ae * (M->eta * pp * pp / he);
+      }
+    }
+  DG_REQUIRE(T.size() < (1ULL << 31), "face tables too large");
+}
+
+void map_stats(dg_mesh* M) {
+  // operation and byte counts of one mapped operator apply, as the kernel does it
+  const HostMesh& m = M->host;
+  dg_mesh_stats& S = M->stats;
+  double fl = 0.0;
+  for (int64_t k = 0; k < m.n; ++k) {
+    const double n1 = m.p[k] + 1.0, q = m.p[k] + 1.0 + kMapQExtra;
+    // volume: two products per pass (x, then y), four passes, the point step;
+    // the side traces' normal derivatives (trace kernel) and the gather's
+    // normal-derivative terms
+    fl += 2.0 * (2.0 * n1 * n1 * q + 2.0 * q * q * n1 + 2.0 * n1 * q * q + 2.0 * n1 * n1 * q) + 24.0 * q * q;
+    fl += 2.0 * 4.0 * n1 * n1 + 2.0 * 4.0 * n1 * n1;
+    for (int j = m.sf_ptr[4 * k]; j < m.sf_ptr[4 * k + 4]; ++j) {
+      const auto& f = m.sf[j];
+      const double qf = M->h_sfm[j].qf;
+      const double nn = f.nb >= 0 ? m.p[f.nb] + 1.0 : 0.0;
+      // per point: three own and three neighbour sums, the geometry; per side
+      // node and point: three sums
+      fl += qf * (2.0 * 3.0 * (n1 + nn) + 60.0) + 2.0 * 3.0 * n1 * qf;
+    }
+  }
+  S.apply_flops = fl;
+  S.apply_bytes += (double)m.n * 24.0 + (double)m.sf.size() * sizeof(SubFaceMap);
+}
+
+// ---------------------------------------------------------------- host mirror
+void host_element_residual_map(const dg_mesh& M, int64_t k, const double* x, double* y) {
+  const HostMesh& m = M.host;
+  const double* T = M.h_tables.data();
+  const int P = m.p[k], NP = P + 1, Q = P + 1 + kMapQExtra;
+  const MapOff& mo = M.moff[P];
+  const double* gx = T + mo.gx;
+  const double* gw = T + mo.gw;
+  const double* Bq = T + mo.B;   // Bq[g * NP + j] = l_j(x_g)
+  const double* Dq = T + mo.D;
+  const double X0 = M.h_xo[3 * k], Y0 = M.h_xo[3 * k + 1], hX = M.h_xo[3 * k + 2];
+  const double ak = m.coef[k], aih = ak / hX;
+  const double* xk = x + m.off[k];
+  // ---- volume
+  std::vector<double> A1(NP * Q), A2(NP * Q), F1(Q * Q), F2(Q * Q);
+  for (int jy = 0; jy < NP; ++jy)
+    for (int g = 0; g < Q; ++g) {
+      double a = 0.0, b = 0.0;
+      for (int jx = 0; jx < NP; ++jx) {
+        a += Dq[g * NP + jx] * xk[jy * NP + jx];
+        b += Bq[g * NP + jx] * xk[jy * NP + jx];
+      }
+      A1[jy * Q + g] = a;
+      A2[jy * Q + g] = b;
+    }
+  for (int gyi = 0; gyi < Q; ++gyi)
+    for (int gxi = 0; gxi < Q; ++gxi) {
+      double ux = 0.0, uy = 0.0;
+      for (int jy = 0; jy < NP; ++jy) {
+        ux += Bq[gyi * NP + jy] * A1[jy * Q + gxi];
+        uy += Dq[gyi * NP + jy] * A2[jy * Q + gxi];
+      }
+      const Jac2 J = domain_jacobian(M.dmap, X0 + hX * gx[gxi], Y0 + hX * gx[gyi]);
+      const double det = J.j0 * J.j3 - J.j1 * J.j2;
+      const double w = ak * gw[gxi] * gw[gyi] / det;
+      const double g11 = J.j1 * J.j1 + J.j3 * J.j3;
+      const double g12 = -(J.j0 * J.j1 + J.j2 * J.j3);
+      const double g22 = J.j0 * J.j0 + J.j2 * J.j2;
+      F1[gyi * Q + gxi] = w * (g11 * ux + g12 * uy);
+      F2[gyi * Q + gxi] = w * (g12 * ux + g22 * uy);
+    }
+  std::vector<double> C1(NP * Q), C2(NP * Q);
+  for (int iy = 0; iy < NP; ++iy)
+    for (int g = 0; g < Q; ++g) {
+      double a = 0.0, b = 0.0;
+      for (int gy = 0; gy < Q; ++gy) {
+        a += Bq[gy * NP + iy] * F1[gy * Q + g];
+        b += Dq[gy * NP + iy] * F2[gy * Q + g];
+      }
+      C1[iy * Q + g] = a;
+      C2[iy * Q + g] = b;
+    }
+  for (int iy = 0; iy < NP; ++iy)
+    for (int ix = 0; ix < NP; ++ix) {
+      double v = 0.0;
+      for (int g = 0; g < Q; ++g) v += Dq[g * NP + ix] * C1[iy * Q + g] + Bq[g * NP + ix] * C2[iy * Q + g];
+      y[iy * NP + ix] = v;
+    }
+  // ---- faces: side traces (value, a times the outward pre-image normal
+  // derivative) as the trace kernel writes them
+  auto sn = [](int s, int i, int q, int np) { return (s < 2) ? (i * np + q) : (q * np + i); };
+  auto trace = [&](int64_t e, int s, double* u, double* dn) {
+    const int p = m.p[e], np = p + 1;
+    const Basis1D& B = basis1d(p);
+    const double* xe = x + m.off[e];
+    const double* dv = (s & 1) ? B.d1.data() : B.d0.data();
+    const double sg = ((s & 1) ? 1.0 : -1.0) * m.coef[e] / (m.size[e] * m.lh);
+    for (int i = 0; i < np; ++i) {
+      u[i] = xe[sn(s, i, (s & 1) ? p : 0, np)];
+      double acc = 0.0;
+      for (int q = 0; q < np; ++q) acc += dv[q] * xe[sn(s, i, q, np)];
+      dn[i] = sg * acc;
+    }
+  };
+  double r[4 * kMaxN] = {0.0}, c2[4 * kMaxN] = {0.0};
+  for (int s = 0; s < 4; ++s) {
+    double uo[kMaxN], fo[kMaxN];
+    trace(k, s, uo, fo);
+    const double so = (s & 1) ? 1.0 : -1.0;   // own outward sign along the normal axis
+    for (int j = m.sf_ptr[4 * k + s]; j < m.sf_ptr[4 * k + s + 1]; ++j) {
+      const SubFaceRec& f = M.h_sf[j];
+      const SubFaceMap& g = M.h_sfm[j];
+      const int qf = g.qf;
+      double un[kMaxN], fn[kMaxN];
+      int npn = 0;
+      double ihn = 0.0, an = 0.0;
+      if (f.nb >= 0) {
+        trace(f.nb, f.nb_side, un, fn);
+        npn = f.pn + 1;
+        ihn = 1.0 / (m.size[f.nb] * m.lh);
+        an = m.coef[f.nb];
+      }
+      for (int q = 0; q < qf; ++q) {
+        const double xg = T[g.tab_g + q], wg = T[g.tab_g + qf + q];
+        const double* Bo = T + g.tab_bo + (size_t)q * NP;
+        const double* Do = T + g.tab_bo + (size_t)(qf + q) * NP;
+        double u0 = 0.0, du0 = 0.0, f0 = 0.0;
+        for (int i = 0; i < NP; ++i) {
+          u0 += Bo[i] * uo[i];
+          du0 += Do[i] * uo[i];
+          f0 += Bo[i] * fo[i];
+        }
+        du0 /= hX;
+        const double Xt = g.xt0 + (g.xt1 - g.xt0) * xg;
+        const Jac2 J = s < 2 ? domain_jacobian(M.dmap, g.xc, Xt) : domain_jacobian(M.dmap, Xt, g.xc);
+        // tangent J e_t, normal J^-T nu (nu = so e_n), m = J^-1 n
+        const double tx = s < 2 ? J.j1 : J.j0, ty = s < 2 ? J.j3 : J.j2;
+        const double ds = std::sqrt(tx * tx + ty * ty);
+        const double det = J.j0 * J.j3 - J.j1 * J.j2;
+        double nx, ny;
+        if (s < 2) { nx = so * J.j3; ny = -so * J.j1; }
+        else { nx = -so * J.j2; ny = so * J.j0; }
+        const double nl = std::sqrt(nx * nx + ny * ny);
+        nx /= nl;
+        ny /= nl;
+        const double mX = (J.j3 * nx - J.j1 * ny) / det, mY = (-J.j2 * nx + J.j0 * ny) / det;
+        const double mn = s < 2 ? mX : mY, mt = s < 2 ? mY : mX;
+        const double W = wg * (g.xt1 - g.xt0) * ds;
+        const double Fo = so * f0 * mn + ak * du0 * mt;
+        double jmp, flux, cc;
+        if (f.nb >= 0) {
+          const double* Bn = T + g.tab_bn + (size_t)q * npn;
+          const double* Dn = T + g.tab_bn + (size_t)(qf + q) * npn;
+          double u1 = 0.0, du1 = 0.0, f1 = 0.0;
+          for (int i = 0; i < npn; ++i) {
+            u1 += Bn[i] * un[i];
+            du1 += Dn[i] * un[i];
+            f1 += Bn[i] * fn[i];
+          }
+          du1 *= ihn;
+          const double Fn = -so * f1 * mn + an * du1 * mt;
+          jmp = u0 - u1;
+          flux = 0.5 * (Fo + Fn);
+          cc = 0.5;
+        } else {
+          jmp = u0;
+          flux = Fo;
+          cc = 1.0;
+        }
+        const double rho1 = W * (g.sigma * jmp - flux);
+        const double rho2 = -cc * W * jmp * mt;
+        const double rho3 = -cc * W * jmp * mn * so;
+        for (int i = 0; i < NP; ++i) {
+          r[s * NP + i] += Bo[i] * rho1 + aih * Do[i] * rho2;
+          c2[s * NP + i] += Bo[i] * rho3;
+        }
+      }
+    }
+  }
+  const Basis1D& B = basis1d(P);
+  for (int node = 0; node < NP * NP; ++node) {
+    const int ix = node % NP, iy = node / NP;
+    double v = y[node];
+    double gg = -B.d0[ix] * c2[0 * NP + iy];
+    gg += B.d1[ix] * c2[1 * NP + iy];
+    gg += -B.d0[iy] * c2[2 * NP + ix];
+    gg += B.d1[iy] * c2[3 * NP + ix];
+    v += gg * aih;
+    if (ix == 0) v += r[0 * NP + iy];
+    if (ix == P) v += r[1 * NP + iy];
+    if (iy == 0) v += r[2 * NP + ix];
+    if (iy == P) v += r[3 * NP + ix];
+    y[node] = v;
+  }
+}
+
+void host_element_diag_map(const dg_mesh& M, int64_t k, double* d) {
+  // column by column: the element's own rows of A e_i
+  const HostMesh& m = M.host;
+  thread_local std::vector<double> x;
+  if ((int64_t)x.size() < M.n_dofs) x.assign(M.n_dofs, 0.0);
+  const int NN = (m.p[k] + 1) * (m.p[k] + 1);
+  std::vector<double> y(NN);
+  for (int i = 0; i < NN; ++i) {
+    x[m.off[k] + i] = 1.0;
+    host_element_residual_map(M, k, x.data(), y.data());
+    x[m.off[k] + i] = 0.0;
+    d[i] = y[i];
+  }
+}
+
+void host_lor_block_map(const dg_mesh& M, int64_t k, double* A) {
+  // Q1 stiffness on the images of the Gauss-Lobatto cells, 2 x 2 Gauss
+  const HostMesh& m = M.host;
+  const int P = m.p[k], NP = P + 1, NN = NP * NP;
+  const auto& gn = basis1d(P).nodes;
+  const double X0 = M.h_xo[3 * k], Y0 = M.h_xo[3 * k + 1], hX = M.h_xo[3 * k + 2];
+  const double* c = m.corners;
+  const double Lx = m.extent[0] * m.lh, Ly = m.extent[1] * m.lh;
+  auto phi = [&](double X, double Y, double* out) {
+    const double s = X / Lx, t = Y / Ly;
+    const double w[4] = {(1 - s) * (1 - t), s * (1 - t), (1 - s) * t, s * t};
+    out[0] = out[1] = 0.0;
+    for (int a = 0; a < 4; ++a) {
+      out[0] += w[a] * c[2 * a];
+      out[1] += w[a] * c[2 * a + 1];
+    }
+  };
+  std::vector<double> gx, gw;
+  gauss_rule(2, gx, gw);
+  std::fill(A, A + (size_t)NN * NN, 0.0);
+  for (int cj = 0; cj < P; ++cj)
+    for (int ci = 0; ci < P; ++ci) {
+      double V[4][2];
+      const int idx[4] = {cj * NP + ci, cj * NP + ci + 1, (cj + 1) * NP + ci, (cj + 1) * NP + ci + 1};
+      for (int a = 0; a < 4; ++a) {
+        const double ex = gn[ci + (a & 1)], ey = gn[cj + (a >> 1)];
+        phi(X0 + hX * ex, Y0 + hX * ey, V[a]);
+      }
+      double K[4][4] = {{0.0}};
+      for (int qy = 0; qy < 2; ++qy)
+        for (int qx = 0; qx < 2; ++qx) {
+          const double s = gx[qx], t = gx[qy];
+          const double ds[4] = {-(1 - t), 1 - t, -t, t};
+          const double dt[4] = {-(1 - s), -s, 1 - s, s};
+          double j00 = 0, j01 = 0, j10 = 0, j11 = 0;
+          for (int a = 0; a < 4; ++a) {
+            j00 += ds[a] * V[a][0];
+            j01 += dt[a] * V[a][0];
+            j10 += ds[a] * V[a][1];
+            j11 += dt[a] * V[a][1];
+          }
+          const double det = j00 * j11 - j01 * j10;
+          double gxv[4], gyv[4];
+          for (int a = 0; a < 4; ++a) {   // J^-T (ds, dt)
+            gxv[a] = (j11 * ds[a] - j10 * dt[a]) / det;
+            gyv[a] = (-j01 * ds[a] + j00 * dt[a]) / det;
+          }
+          const double w = gw[qx] * gw[qy] * det;
+          for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) K[a][b] += w * (gxv[a] * gxv[b] + gyv[a] * gyv[b]);
+        }
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) A[(size_t)idx[a] * NN + idx[b]] += K[a][b];
+    }
+}
+
+}  // namespace dg

@@ -361,14 +361,27 @@ HostPrecond build_host_precond(const dg_mesh& M, const dg_options& o) {
     At.ptr.assign(n + 1, 0);
     const double m1[2][2] = {{2.0 / 6.0, 1.0 / 6.0}, {1.0 / 6.0, 2.0 / 6.0}};
     const double k1[2][2] = {{1.0, -1.0}, {-1.0, 1.0}};
+    std::vector<double> blk;
     for (int64_t k = 0; k < m.n; ++k) {
       const int P = m.p[k], NP = P + 1;
       const auto& g = basis1d(P).nodes;
+      if (m.mapped) {   // Q1 on the mapped cells: the dense block, read in the same stencil
+        blk.resize((size_t)NP * NP * NP * NP);
+        host_lor_block_map(M, k, blk.data());
+      }
       // local stencil: node (i, j) couples to (i+di, j+dj), |di|,|dj| <= 1
       for (int j = 0; j < NP; ++j)
         for (int i = 0; i < NP; ++i) {
           double row[3][3] = {{0}};
-          for (int cj = j - 1; cj <= j; ++cj)
+          if (m.mapped) {
+            for (int dj = 0; dj < 3; ++dj)
+              for (int di = 0; di < 3; ++di) {
+                const int ii = i + di - 1, jj = j + dj - 1;
+                if (ii < 0 || jj < 0 || ii > P || jj > P) continue;
+                row[dj][di] = blk[(size_t)(j * NP + i) * NP * NP + jj * NP + ii];
+              }
+          }
+          for (int cj = j - 1; cj <= j && !m.mapped; ++cj)
             for (int ci = i - 1; ci <= i; ++ci) {
               if (ci < 0 || cj < 0 || ci >= P || cj >= P) continue;
               const double a = g[ci + 1] - g[ci], b = g[cj + 1] - g[cj];

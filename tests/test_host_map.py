@@ -1,0 +1,87 @@
+"""The library's host setup on mapped squares (Section 2 element maps onto
+general quadrilaterals), run through the inspection library without a GPU,
+against the oracle's mapped space: the host mirror of the mapped operator
+kernel, the conforming prolongation, the V_J / V_e split, the Q1 LOR matrix on
+the mapped cells, the block inverses, the Jacobi diagonal and the AMG
+hierarchy; and the input checks of mapped meshes."""
+import numpy as np
+import pytest
+
+from oracle import solver
+from paper_2009_01287_gb300 import inputs
+
+
+def _coef(mesh, base):
+    return inputs.with_coeff(mesh, inputs.base_parity_coeff(mesh, base))
+
+
+CASES = [
+    ("par-hp", lambda: inputs.with_corners(inputs.small_hp_mesh(1, base=4, depth=3, prob=0.4, pmax=5),
+                                           inputs.PARALLELOGRAM)),
+    ("quad-hp", lambda: inputs.with_corners(inputs.small_hp_mesh(2, base=4, depth=3, prob=0.4, pmax=6),
+                                            inputs.QUADRILATERAL)),
+    ("quad-p8", lambda: inputs.with_corners(inputs.small_hp_mesh(3, base=3, depth=2, prob=0.5, pmin=6, pmax=8),
+                                            inputs.QUADRILATERAL)),
+    ("quad-coef", lambda: inputs.with_corners(_coef(inputs.small_hp_mesh(4, base=4, depth=3, prob=0.4, pmax=5), 4),
+                                              inputs.QUADRILATERAL)),
+    ("quad-ragged", lambda: inputs.with_corners(inputs.random_refined_mesh(2, 5, 3, 0.35, 1, 4, seed=9, base_y=3),
+                                                ((0.0, 0.0), (1.1, 0.2), (-0.1, 0.6), (0.9, 0.75)))),
+]
+
+
+@pytest.mark.parametrize("name,mk", CASES, ids=[c[0] for c in CASES])
+def test_host_setup_matches_oracle_mapped(built_lib, name, mk):
+    mesh = mk()
+    prob = solver.build_problem(mesh)
+    B = built_lib
+    hs = B.HostSetup(mesh, B.make_options())
+    x = inputs.random_vector(prob.space.n, 11)
+    ya, yb = prob.A @ x, hs.apply(x)
+    assert np.abs(ya - yb).max() <= 1e-12 * np.abs(ya).max()
+    assert hs.nC == prob.cs.n
+    assert abs(prob.cs.P - hs.P).max() < 1e-13
+    assert np.array_equal(prob.cs.kind, hs.kind)
+    assert len(hs.blocks) == len(prob.cs.blocks)
+    for a, b in zip(prob.cs.blocks, hs.blocks):
+        assert np.array_equal(a, b)
+    pc = solver.Preconditioner(prob, lor="amg")
+    assert abs(pc.Ac - hs.Ac).max() <= 1e-13 * abs(pc.Ac).max()
+    d = np.where(pc.jmask, pc.dinv, 0.0)
+    assert np.abs(d - hs.dinv).max() <= 1e-12 * np.abs(d).max()
+    for a, b in zip(pc.block_inv, hs.block_inv):
+        assert np.abs(a - b).max() <= 1e-10 * np.abs(a).max()
+    assert [L.n for L in pc.levels] == [l.shape[0] for l in hs.levels]
+    for L, l in zip(pc.levels, hs.levels):
+        assert abs(L.A - l).max() <= 1e-11 * abs(L.A).max()
+
+
+def test_similarity_corners_give_the_box_operator(built_lib):
+    """A rotated, scaled, shifted square gives the operator of the boxes."""
+    mesh = inputs.small_hp_mesh(5, base=3, depth=2, prob=0.5, pmax=6)
+    th, s, sh = -0.4, 0.8, np.array([2.0, 1.0])
+    R = s * np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    L = mesh.extent[0] * mesh.lattice_h
+    corners = [sh, sh + R @ [L, 0], sh + R @ [0, L], sh + R @ [L, L]]
+    B = built_lib
+    a = B.HostSetup(mesh, B.make_options(), amg=False)
+    b = B.HostSetup(inputs.with_corners(mesh, corners), B.make_options(), amg=False)
+    x = inputs.random_vector(a.n, 2)
+    ya, yb = a.apply(x), b.apply(x)
+    assert np.abs(ya - yb).max() <= 1e-12 * np.abs(ya).max()
+    assert abs(a.Ac - b.Ac).max() <= 1e-12 * abs(a.Ac).max()
+
+
+def test_mapped_input_checks(built_lib):
+    B = built_lib
+    mesh = inputs.small_hp_mesh(1)
+    with pytest.raises(B.DGError) as e:
+        B.HostSetup(inputs.with_corners(mesh, ((0, 0), (1, 0), (0, 1), (0.2, 0.2))), B.make_options())
+    assert e.value.code == B.DG_EINVAL
+    # clockwise corners (a reflection) are rejected too
+    with pytest.raises(B.DGError):
+        B.HostSetup(inputs.with_corners(mesh, ((0, 0), (0, 1), (1, 0), (1, 1))), B.make_options())
+    with pytest.raises(B.DGError) as e:
+        B.HostSetup(inputs.with_corners(mesh, inputs.QUADRILATERAL), B.make_options(form=B.DG_FORM_BR2))
+    assert e.value.code == B.DG_EUNSUPPORTED
+    with pytest.raises(B.DGError):
+        B.HostSetup(inputs.with_corners(mesh, ((0, 0), (1, 0), (0, 1), (np.nan, 1))), B.make_options())
