@@ -194,11 +194,13 @@ struct ApplyArgs {
   int n_tiles;
   unsigned* sched;            // [0] next tile, [1] exit ticket (both zero between launches)
   BasisOff boff[kMaxP + 1];
-  // mapped squares: per sub-face record its rule, tables and penalty; per
-  // element its pre-image box (X0, Y0, h); the domain map; the volume tables
+  // mapped squares: per sub-face record its rule size, tables, factors and
+  // penalty; the geometric factors at the Gauss points (volume per element,
+  // faces per record); the volume tables
   const SubFaceMap* sfm;
-  const double* xo;
-  DomainMap dmap;
+  const double* gvol;
+  const int64_t* goff;
+  const double* gface;
   MapOff moff[kMaxP + 1];
 };
 

@@ -251,8 +251,9 @@ ApplyArgs make_apply_args(const dg_mesh& M, const double* x, double* y, Reduce r
   A.sched = M.d_sched;
   for (int p = 0; p <= kMaxP; ++p) A.boff[p] = M.boff[p];
   A.sfm = M.d_sfm;
-  A.xo = M.d_xo;
-  A.dmap = M.dmap;
+  A.gvol = M.d_gvol;
+  A.goff = M.d_goff;
+  A.gface = M.d_gface;
   for (int p = 0; p <= kMaxP; ++p) A.moff[p] = M.moff[p];
   return A;
 }

@@ -9,14 +9,15 @@
 //   volume  u at the (p+2)^2 Gauss points by sum factorisation (B = l_j(x_g),
 //           D = l_j'(x_g)): grad_xi u = ((B (x) D) u, (D (x) B) u); at every
 //           point the flux a w_g w_h G grad_xi u with G = det(J) J^-1 J^-T of
-//           the map there (J from the map's closed form, no stored factors);
-//           back to the nodes with the transposed products: four passes of
+//           the map there (three factors per point, stored at setup); back to
+//           the nodes with the transposed products: four passes of
 //           O((p+1)(p+2)^2) work per element instead of two;
 //   faces   one thread per (sub-face item, Gauss point) evaluates both sides'
 //           traces there (values and a-weighted normal derivatives from the
-//           trace array, tangential derivatives from the trace values), the
-//           physical normal n = J^-T nu / |J^-T nu| and m = J^-1 n, and writes
-//           three adjoint weights: of the test function's value, of its
+//           trace array, tangential derivatives from the trace values) and,
+//           with the point's stored factors (the arc-length weight w and w m
+//           for m = J^-1 n, n = J^-T nu / |J^-T nu| the physical normal),
+//           writes three adjoint weights: of the test function's value, of its
 //           tangential derivative and of its normal derivative; one thread per
 //           side node then sums them over its sub-faces in sub-face order
 //           (deterministic) with the side's basis tables, and the gather adds
@@ -36,9 +37,9 @@ struct MapShape {
   static constexpr int Q = P + 1 + kMapQExtra;
   static constexpr int QQ = Q * Q;
   static constexpr int EPB = apply_epb(P);
-  // shared doubles: B, D (2 Q NP), rule (2 Q), x (EPB NN), stage 1 / 3
-  // (2 EPB NP Q), point fluxes (2 EPB QQ), side sums r, c2 (8 EPB NP)
-  static constexpr int SMEM = 2 * Q * NP + 2 * Q + EPB * NN + 2 * EPB * NP * Q + 2 * EPB * QQ + 8 * EPB * NP;
+  // shared doubles: B, D (2 Q NP), x (EPB NN), stage 1 / 3 (2 EPB NP Q),
+  // point fluxes (2 EPB QQ), side sums r, c2 (8 EPB NP)
+  static constexpr int SMEM = 2 * Q * NP + EPB * NN + 2 * EPB * NP * Q + 2 * EPB * QQ + 8 * EPB * NP;
   // then the sub-face item weights: [item][kMapQMax][3]
   static constexpr int PART = SMEM;
 };
@@ -50,9 +51,7 @@ __device__ __forceinline__ void apply_map_tile(const ApplyArgs& A, const ApplyTi
   constexpr int NP = S::NP, NN = S::NN, Q = S::Q, QQ = S::QQ, EPB = S::EPB;
   double* sB = sm;                    // [Q][NP]
   double* sD = sB + Q * NP;
-  double* sgx = sD + Q * NP;          // [Q]
-  double* sgw = sgx + Q;
-  double* sx = sgw + Q;               // [EPB][NN]
+  double* sx = sD + Q * NP;           // [EPB][NN]
   double* sA1 = sx + EPB * NN;        // [EPB][NP][Q]; stage 3 reuses it
   double* sA2 = sA1 + EPB * NP * Q;
   double* sF1 = sA2 + EPB * NP * Q;   // [EPB][Q][Q]
@@ -67,10 +66,6 @@ __device__ __forceinline__ void apply_map_tile(const ApplyArgs& A, const ApplyTi
   for (int i = tid; i < Q * NP; i += blockDim.x) {
     sB[i] = __ldg(A.tab + mo.B + i);
     sD[i] = __ldg(A.tab + mo.D + i);
-  }
-  for (int i = tid; i < Q; i += blockDim.x) {
-    sgx[i] = __ldg(A.tab + mo.gx + i);
-    sgw[i] = __ldg(A.tab + mo.gw + i);
   }
   for (int t = tid; t < count * NN; t += blockDim.x) {
     const int e = t / NN;
@@ -104,7 +99,6 @@ __device__ __forceinline__ void apply_map_tile(const ApplyArgs& A, const ApplyTi
     const int e = (item.y & 0xffff) >> 2, s = item.y & 3;
     const int k = A.order[T.first + e];
     const double2* trk = reinterpret_cast<const double2*>(A.tr + A.toff[k]) + s * NP;
-    const double xg = __ldg(A.tab + fm.tab_g + g), wg = __ldg(A.tab + fm.tab_g + qf + g);
     const double* Bo = A.tab + fm.tab_bo + g * NP;
     const double* Do = A.tab + fm.tab_bo + (qf + g) * NP;
     double u0 = 0.0, du0 = 0.0, f0 = 0.0;
@@ -117,28 +111,10 @@ __device__ __forceinline__ void apply_map_tile(const ApplyArgs& A, const ApplyTi
       f0 = fma(b, v.y, f0);
     }
     du0 *= A.ih[k];
-    // the point in the pre-image and the map's Jacobian there
-    const double Xt = fma(fm.xt1 - fm.xt0, xg, fm.xt0);
-    const Jac2 J = s < 2 ? domain_jacobian(A.dmap, fm.xc, Xt) : domain_jacobian(A.dmap, Xt, fm.xc);
-    const double so = (s & 1) ? 1.0 : -1.0;   // outward along the normal axis
-    const double tx = s < 2 ? J.j1 : J.j0, ty = s < 2 ? J.j3 : J.j2;
-    const double ds = sqrt(tx * tx + ty * ty);
-    const double det = J.j0 * J.j3 - J.j1 * J.j2;
-    double nx, ny;   // J^-T nu, normalised
-    if (s < 2) {
-      nx = so * J.j3;
-      ny = -so * J.j1;
-    } else {
-      nx = -so * J.j2;
-      ny = so * J.j0;
-    }
-    const double nl = sqrt(nx * nx + ny * ny);
-    nx /= nl;
-    ny /= nl;
-    const double mX = (J.j3 * nx - J.j1 * ny) / det, mY = (J.j0 * ny - J.j2 * nx) / det;
-    const double mn = s < 2 ? mX : mY, mt = s < 2 ? mY : mX;
-    const double W = wg * (fm.xt1 - fm.xt0) * ds;
-    const double Fo = so * f0 * mn + A.ak[k] * du0 * mt;   // (a grad u-) . n
+    // the point's factors: w = w_g |J t| dt, w m_t, w m_n s (m = J^-1 n)
+    const double* gf = A.gface + fm.geo;
+    const double w = __ldg(gf + g), wmt = __ldg(gf + qf + g), wmn = __ldg(gf + 2 * qf + g);
+    const double Fo = fma(f0, wmn, A.ak[k] * du0 * wmt);   // w (a grad u-) . n
     double jmp, flux, cc;
     if (f.nb >= 0) {
       const int npn = f.pn + 1;
@@ -154,7 +130,7 @@ __device__ __forceinline__ void apply_map_tile(const ApplyArgs& A, const ApplyTi
         f1 = fma(b, v.y, f1);
       }
       du1 *= A.ih[f.nb];
-      const double Fn = -so * f1 * mn + A.ak[f.nb] * du1 * mt;   // (a grad u+) . n
+      const double Fn = fma(-f1, wmn, A.ak[f.nb] * du1 * wmt);   // w (a grad u+) . n
       jmp = u0 - u1;
       flux = 0.5 * (Fo + Fn);
       cc = 0.5;
@@ -164,12 +140,12 @@ __device__ __forceinline__ void apply_map_tile(const ApplyArgs& A, const ApplyTi
       cc = 1.0;
     }
     double* pp = part + ((item.y >> 16) * kMapQMax + g) * 3;
-    pp[0] = W * (fm.sigma * jmp - flux);   // weight of v-
-    pp[1] = -cc * W * jmp * mt;            // of a d v- / d t (times a / h and l' at the gather)
-    pp[2] = -cc * W * jmp * mn * so;       // of a times the outward normal derivative of v-
+    pp[0] = fma(fm.sigma * jmp, w, -flux);   // weight of v-
+    pp[1] = -cc * jmp * wmt;                 // of d v- / d t (times a / h and l' at the side sums)
+    pp[2] = -cc * jmp * wmn;                 // of a times the outward normal derivative of v-
   }
   __syncthreads();
-  // ---- volume stage 2 and the geometric factors at every Gauss point
+  // ---- volume stage 2 and the flux at every Gauss point
   for (int t = tid; t < count * QQ; t += blockDim.x) {
     const int e = t / QQ, rem = t - e * QQ;
     const int gy = rem / Q, gxi = rem - gy * Q;
@@ -181,17 +157,11 @@ __device__ __forceinline__ void apply_map_tile(const ApplyArgs& A, const ApplyTi
       ux = fma(sB[gy * NP + j], a1[j * Q], ux);
       uy = fma(sD[gy * NP + j], a2[j * Q], uy);
     }
-    const int k = A.order[T.first + e];
-    const double* xo = A.xo + 3 * (int64_t)k;
-    const double h = xo[2];
-    const Jac2 J = domain_jacobian(A.dmap, fma(h, sgx[gxi], xo[0]), fma(h, sgx[gy], xo[1]));
-    const double det = J.j0 * J.j3 - J.j1 * J.j2;
-    const double w = A.ak[k] * sgw[gxi] * sgw[gy] / det;
-    const double g11 = J.j1 * J.j1 + J.j3 * J.j3;
-    const double g12 = -(J.j0 * J.j1 + J.j2 * J.j3);
-    const double g22 = J.j0 * J.j0 + J.j2 * J.j2;
-    sF1[t] = w * (g11 * ux + g12 * uy);
-    sF2[t] = w * (g12 * ux + g22 * uy);
+    // the point's factors a w_g w_h G (three planes per element)
+    const double* G = A.gvol + A.goff[A.order[T.first + e]] + rem;
+    const double g11 = __ldg(G), g12 = __ldg(G + QQ), g22 = __ldg(G + 2 * QQ);
+    sF1[t] = fma(g11, ux, g12 * uy);
+    sF2[t] = fma(g12, ux, g22 * uy);
   }
   // ---- faces, pass 2: one thread per side node sums its sub-faces' weights
   // in sub-face order with the side's basis tables

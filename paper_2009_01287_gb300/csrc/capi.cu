@@ -83,8 +83,12 @@ void upload_mesh(dg_mesh* M, cudaStream_t s) {
   M->d_sf = a.upload(M->h_sf, s);
   M->d_sfb = M->h_sfb.empty() ? nullptr : a.upload(M->h_sfb, s);
   M->d_sf3 = a.upload(M->h_sf3, s);
-  M->d_sfm = M->h_sfm.empty() ? nullptr : a.upload(M->h_sfm, s);
-  M->d_xo = M->h_xo.empty() ? nullptr : a.upload(M->h_xo, s);
+  if (m.mapped) {
+    M->d_sfm = a.upload(M->h_sfm, s);
+    M->d_gvol = a.upload(M->h_gvol, s);
+    M->d_goff = a.upload(M->h_goff, s);
+    M->d_gface = a.upload(M->h_gface, s);
+  }
   M->d_tables = a.upload(M->h_tables, s);
   M->d_sched = a.alloc<unsigned>(2);
   DG_CUDA(cudaMemsetAsync(M->d_sched, 0, 2 * sizeof(unsigned), s));

@@ -162,16 +162,16 @@ constexpr int kMapQExtra = 1;
 constexpr int kMapQMax = kMaxP + 1 + kMapQExtra;
 
 // One sub-face of a mapped square mesh seen from one side (beside the
-// SubFaceRec of the same index): its Gauss rule, both sides' 1D basis values
-// and derivatives at the rule's points, its place in the pre-image and its
+// SubFaceRec of the same index): its Gauss rule size, both sides' 1D basis
+// values and derivatives at the rule's points, its geometric factors and its
 // penalty.
 struct SubFaceMap {
   int32_t qf;       // Gauss points, max(p, pn) + 2
-  int32_t tab_g;    // the rule on [0, 1]: qf points, then qf weights
   int32_t tab_bo;   // own side: l_i(s_g) (qf rows of p+1), then l_i'(s_g)
   int32_t tab_bn;   // the neighbour's side, the same with pn (boundary: tab_bo)
-  double xc;        // pre-image coordinate of the side's line (along its normal axis)
-  double xt0, xt1;  // pre-image tangential extent of the sub-face
+  int32_t geo;      // offset of the point factors in the face geometry: qf values of
+                    // w = w_g |J t| dt, then w m_t, then w m_n s (m = J^-1 n in the
+                    // pre-image axes, s = +1 / -1 for an upper / lower side)
   double sigma;     // SIPG penalty with h_kappa = sqrt(area of kappa)
 };
 

@@ -115,11 +115,14 @@ struct dg_mesh {
   std::vector<dg::SubFaceBr2> h_sfb;    // square meshes, BR2: one per h_sf record
   std::vector<dg::SubFaceRec3> h_sf3;   // cube meshes
   // mapped squares: one record per h_sf record, the volume tables of each
-  // degree, the map, and per element its pre-image corner and edge (X0, Y0, h)
+  // degree, the map; the geometric factors at the Gauss points - per element
+  // (offset h_goff[k]) the volume factors a w_g w_h G of its (p+2)^2 points as
+  // three planes G11, G12, G22; per sub-face record its face factors
   std::vector<dg::SubFaceMap> h_sfm;
   dg::MapOff moff[dg::kMaxP + 1];
   dg::DomainMap dmap{};
-  std::vector<double> h_xo;
+  std::vector<double> h_gvol, h_gface;
+  std::vector<int64_t> h_goff;
   int64_t apply3_smem = 0;              // dynamic shared memory of the 3D operator kernel
   std::vector<double> h_tables;
   dg::BasisOff boff[dg::kMaxP + 1];
@@ -154,7 +157,9 @@ struct dg_mesh {
   dg::SubFaceBr2* d_sfb = nullptr;
   dg::SubFaceRec3* d_sf3 = nullptr;
   dg::SubFaceMap* d_sfm = nullptr;   // mapped squares
-  double* d_xo = nullptr;            // mapped squares: 3 per element
+  double* d_gvol = nullptr;          // mapped squares: geometric factors (h_gvol, h_goff, h_gface)
+  int64_t* d_goff = nullptr;
+  double* d_gface = nullptr;
   double* d_tables = nullptr;
   int32_t* d_order = nullptr;
   dg::ApplyTile* d_tiles = nullptr;

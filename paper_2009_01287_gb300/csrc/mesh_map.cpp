@@ -2,11 +2,11 @@
 // quadrilaterals).  The leaf boxes of the lattice are pre-images; the bilinear
 // map of the lattice domain onto the quadrilateral with the given corners
 // carries them to the elements.  This file builds what the mapped operator
-// kernel reads - the map, each element's pre-image box, per sub-face its Gauss
-// rule, both sides' 1D basis values and derivatives at the rule's points and
-// its penalty, per degree the volume rule - and holds the host mirror of that
-// kernel (element rows, their diagonal) and the LOR blocks on mapped cells
-// (Section 3.4).
+// kernel reads - per degree the volume rule's basis tables, the geometric
+// factors at every volume and sub-face Gauss point, per sub-face its rule
+// size, both sides' 1D basis values and derivatives at the rule's points and
+// its penalty - and holds the host mirror of that kernel (element rows, their
+// diagonal) and the LOR blocks on mapped cells (Section 3.4).
 //
 // The SIPG form is the one of boxes, evaluated at Gauss points:
 //   volume  int a grad u . grad v = int a (grad_xi u)^T G (grad_xi v) dxi,
@@ -93,16 +93,10 @@ void build_mesh_map(dg_mesh* M) {
     DG_REQUIRE(J.j0 * J.j3 - J.j1 * J.j2 > 0.0,
                "corners do not bound a convex, counter-clockwise quadrilateral");
   }
-  // element pre-image boxes and penalty sizes h_kappa = sqrt(|kappa|)
-  M->h_xo.resize(3 * (size_t)m.n);
+  // penalty sizes h_kappa = sqrt(|kappa|)
   std::vector<double> hpen(m.n);
-  for (int64_t k = 0; k < m.n; ++k) {
-    const double X0 = m.lo[2 * k] * m.lh, Y0 = m.lo[2 * k + 1] * m.lh, h = m.size[k] * m.lh;
-    M->h_xo[3 * k] = X0;
-    M->h_xo[3 * k + 1] = Y0;
-    M->h_xo[3 * k + 2] = h;
-    hpen[k] = std::sqrt(box_area(D, X0, Y0, h));
-  }
+  for (int64_t k = 0; k < m.n; ++k)
+    hpen[k] = std::sqrt(box_area(D, m.lo[2 * k] * m.lh, m.lo[2 * k + 1] * m.lh, m.size[k] * m.lh));
   // tables, appended after the box tables
   std::vector<double>& T = M->h_tables;
   std::map<int, int> rules;
@@ -123,13 +117,40 @@ void build_mesh_map(dg_mesh* M) {
     }
   }
   M->moff[0] = M->moff[1];
+  // volume factors a w_g w_h G = a w_g w_h det(J) J^-1 J^-T at every Gauss
+  // point (the box's own scaling cancels in 2D), three planes per element
+  M->h_goff.assign(m.n + 1, 0);
+  for (int64_t k = 0; k < m.n; ++k) {
+    const int64_t q = m.p[k] + 1 + kMapQExtra;
+    M->h_goff[k + 1] = M->h_goff[k] + 3 * q * q;
+  }
+  M->h_gvol.assign(M->h_goff[m.n], 0.0);
+  for (int64_t k = 0; k < m.n; ++k) {
+    const int P = m.p[k], Q = P + 1 + kMapQExtra, QQ = Q * Q;
+    const double* gx = T.data() + M->moff[P].gx;
+    const double* gw = T.data() + M->moff[P].gw;
+    const double X0 = m.lo[2 * k] * m.lh, Y0 = m.lo[2 * k + 1] * m.lh, h = m.size[k] * m.lh;
+    double* G = M->h_gvol.data() + M->h_goff[k];
+    for (int gy = 0; gy < Q; ++gy)
+      for (int gxi = 0; gxi < Q; ++gxi) {
+        const Jac2 J = domain_jacobian(D, X0 + h * gx[gxi], Y0 + h * gx[gy]);
+        const double det = J.j0 * J.j3 - J.j1 * J.j2;
+        const double w = m.coef[k] * gw[gxi] * gw[gy] / det;
+        const int pt = gy * Q + gxi;
+        G[pt] = w * (J.j1 * J.j1 + J.j3 * J.j3);
+        G[QQ + pt] = -w * (J.j0 * J.j1 + J.j2 * J.j3);
+        G[2 * QQ + pt] = w * (J.j0 * J.j0 + J.j2 * J.j2);
+      }
+  }
   M->h_sfm.assign(m.sf.size(), SubFaceMap{});
+  M->h_gface.clear();
   const dg_options& o = M->opts;
   for (int64_t k = 0; k < m.n; ++k)
     for (int s = 0; s < 4; ++s) {
       int axis, cc, t0, t1;
       m.side_segment((int)k, s, axis, cc, t0, t1);
       const int P = m.p[k];
+      const double so = (s & 1) ? 1.0 : -1.0;   // outward along the normal axis
       for (int j = m.sf_ptr[4 * k + s]; j < m.sf_ptr[4 * k + s + 1]; ++j) {
         const auto& f = m.sf[j];
         SubFaceMap& r = M->h_sfm[j];
@@ -141,21 +162,44 @@ void build_mesh_map(dg_mesh* M) {
           he = std::min(he, hpen[f.nb]);
           ae = std::max(ae, m.coef[f.nb]);
         }
-        r.qf = pe + 1 + kMapQExtra;
-        r.tab_g = append_rule(T, r.qf, rules);
-        r.tab_bo = append_side_table(T, P, r.qf, f.t0 - t0, len, m.size[k], sides);
+        const int qf = pe + 1 + kMapQExtra;
+        r.qf = qf;
+        r.tab_bo = append_side_table(T, P, qf, f.t0 - t0, len, m.size[k], sides);
         if (f.nb >= 0) {
           int na, nc, n0, n1;
           m.side_segment(f.nb, f.nb_side, na, nc, n0, n1);
-          r.tab_bn = append_side_table(T, m.p[f.nb], r.qf, f.t0 - n0, len, m.size[f.nb], sides);
+          r.tab_bn = append_side_table(T, m.p[f.nb], qf, f.t0 - n0, len, m.size[f.nb], sides);
         } else {
           r.tab_bn = r.tab_bo;
         }
-        r.xc = cc * m.lh;
-        r.xt0 = f.t0 * m.lh;
-        r.xt1 = f.t1 * m.lh;
         const double pp = (o.penalty_form == DG_PENALTY_P1SQ) ? (pe + 1.0) : (double)pe;
         r.sigma = ae * (M->eta * pp * pp / he);
+        // face factors at the rule's points: arc length |J t| dt, the physical
+        // normal n = J^-T nu / |J^-T nu| (nu = so e_n), m = J^-1 n
+        const int rg = append_rule(T, qf, rules);
+        DG_REQUIRE(M->h_gface.size() + 3 * (size_t)qf < (1ULL << 31), "face geometry too large");
+        r.geo = (int32_t)M->h_gface.size();
+        M->h_gface.resize(M->h_gface.size() + 3 * (size_t)qf);
+        double* G = M->h_gface.data() + r.geo;
+        const double xc = cc * m.lh, xt0 = f.t0 * m.lh, xt1 = f.t1 * m.lh;
+        for (int g = 0; g < qf; ++g) {
+          const double Xt = xt0 + (xt1 - xt0) * T[rg + g];
+          const Jac2 J = s < 2 ? domain_jacobian(D, xc, Xt) : domain_jacobian(D, Xt, xc);
+          const double tx = s < 2 ? J.j1 : J.j0, ty = s < 2 ? J.j3 : J.j2;
+          const double det = J.j0 * J.j3 - J.j1 * J.j2;
+          double nx, ny;
+          if (s < 2) { nx = so * J.j3; ny = -so * J.j1; }
+          else { nx = -so * J.j2; ny = so * J.j0; }
+          const double nl = std::sqrt(nx * nx + ny * ny);
+          nx /= nl;
+          ny /= nl;
+          const double mX = (J.j3 * nx - J.j1 * ny) / det, mY = (J.j0 * ny - J.j2 * nx) / det;
+          const double mn = s < 2 ? mX : mY, mt = s < 2 ? mY : mX;
+          const double W = T[rg + qf + g] * (xt1 - xt0) * std::sqrt(tx * tx + ty * ty);
+          G[g] = W;
+          G[qf + g] = W * mt;
+          G[2 * qf + g] = W * mn * so;
+        }
       }
     }
   DG_REQUIRE(T.size() < (1ULL << 31), "face tables too large");
@@ -168,39 +212,41 @@ void map_stats(dg_mesh* M) {
   double fl = 0.0;
   for (int64_t k = 0; k < m.n; ++k) {
     const double n1 = m.p[k] + 1.0, q = m.p[k] + 1.0 + kMapQExtra;
-    // volume: two products per pass (x, then y), four passes, the point step;
-    // the side traces' normal derivatives (trace kernel) and the gather's
-    // normal-derivative terms
-    fl += 2.0 * (2.0 * n1 * n1 * q + 2.0 * q * q * n1 + 2.0 * n1 * q * q + 2.0 * n1 * n1 * q) + 24.0 * q * q;
+    // volume: two products per pass (x, then y), four passes, the point step
+    // (two 2-term sums); the side traces' normal derivatives (trace kernel)
+    // and the gather's normal-derivative terms
+    fl += 2.0 * (2.0 * n1 * n1 * q + 2.0 * q * q * n1 + 2.0 * n1 * q * q + 2.0 * n1 * n1 * q) + 8.0 * q * q;
     fl += 2.0 * 4.0 * n1 * n1 + 2.0 * 4.0 * n1 * n1;
     for (int j = m.sf_ptr[4 * k]; j < m.sf_ptr[4 * k + 4]; ++j) {
       const auto& f = m.sf[j];
       const double qf = M->h_sfm[j].qf;
       const double nn = f.nb >= 0 ? m.p[f.nb] + 1.0 : 0.0;
-      // per point: three own and three neighbour sums, the geometry; per side
-      // node and point: three sums
-      fl += qf * (2.0 * 3.0 * (n1 + nn) + 60.0) + 2.0 * 3.0 * n1 * qf;
+      // per point: three own and three neighbour sums and the weights; per
+      // side node and point: three sums
+      fl += qf * (2.0 * 3.0 * (n1 + nn) + 16.0) + 2.0 * 3.0 * n1 * qf;
     }
   }
   S.apply_flops = fl;
-  S.apply_bytes += (double)m.n * 24.0 + (double)m.sf.size() * sizeof(SubFaceMap);
+  S.apply_bytes += 8.0 * (double)(M->h_gvol.size() + M->h_gface.size() + m.n) +
+                   (double)m.sf.size() * sizeof(SubFaceMap);
 }
 
 // ---------------------------------------------------------------- host mirror
+// The mapped kernel's formulation, written plainly, on the same stored
+// geometric factors (so the CPU tests against the oracle check those too).
 void host_element_residual_map(const dg_mesh& M, int64_t k, const double* x, double* y) {
   const HostMesh& m = M.host;
   const double* T = M.h_tables.data();
-  const int P = m.p[k], NP = P + 1, Q = P + 1 + kMapQExtra;
+  const int P = m.p[k], NP = P + 1, Q = P + 1 + kMapQExtra, QQ = Q * Q;
   const MapOff& mo = M.moff[P];
-  const double* gx = T + mo.gx;
-  const double* gw = T + mo.gw;
   const double* Bq = T + mo.B;   // Bq[g * NP + j] = l_j(x_g)
   const double* Dq = T + mo.D;
-  const double X0 = M.h_xo[3 * k], Y0 = M.h_xo[3 * k + 1], hX = M.h_xo[3 * k + 2];
+  const double* G = M.h_gvol.data() + M.h_goff[k];
+  const double hX = m.size[k] * m.lh;
   const double ak = m.coef[k], aih = ak / hX;
   const double* xk = x + m.off[k];
   // ---- volume
-  std::vector<double> A1(NP * Q), A2(NP * Q), F1(Q * Q), F2(Q * Q);
+  std::vector<double> A1(NP * Q), A2(NP * Q), F1(QQ), F2(QQ);
   for (int jy = 0; jy < NP; ++jy)
     for (int g = 0; g < Q; ++g) {
       double a = 0.0, b = 0.0;
@@ -218,14 +264,9 @@ void host_element_residual_map(const dg_mesh& M, int64_t k, const double* x, dou
         ux += Bq[gyi * NP + jy] * A1[jy * Q + gxi];
         uy += Dq[gyi * NP + jy] * A2[jy * Q + gxi];
       }
-      const Jac2 J = domain_jacobian(M.dmap, X0 + hX * gx[gxi], Y0 + hX * gx[gyi]);
-      const double det = J.j0 * J.j3 - J.j1 * J.j2;
-      const double w = ak * gw[gxi] * gw[gyi] / det;
-      const double g11 = J.j1 * J.j1 + J.j3 * J.j3;
-      const double g12 = -(J.j0 * J.j1 + J.j2 * J.j3);
-      const double g22 = J.j0 * J.j0 + J.j2 * J.j2;
-      F1[gyi * Q + gxi] = w * (g11 * ux + g12 * uy);
-      F2[gyi * Q + gxi] = w * (g12 * ux + g22 * uy);
+      const int pt = gyi * Q + gxi;
+      F1[pt] = G[pt] * ux + G[QQ + pt] * uy;
+      F2[pt] = G[QQ + pt] * ux + G[2 * QQ + pt] * uy;
     }
   std::vector<double> C1(NP * Q), C2(NP * Q);
   for (int iy = 0; iy < NP; ++iy)
@@ -264,11 +305,11 @@ void host_element_residual_map(const dg_mesh& M, int64_t k, const double* x, dou
   for (int s = 0; s < 4; ++s) {
     double uo[kMaxN], fo[kMaxN];
     trace(k, s, uo, fo);
-    const double so = (s & 1) ? 1.0 : -1.0;   // own outward sign along the normal axis
     for (int j = m.sf_ptr[4 * k + s]; j < m.sf_ptr[4 * k + s + 1]; ++j) {
       const SubFaceRec& f = M.h_sf[j];
       const SubFaceMap& g = M.h_sfm[j];
       const int qf = g.qf;
+      const double* W = M.h_gface.data() + g.geo;
       double un[kMaxN], fn[kMaxN];
       int npn = 0;
       double ihn = 0.0, an = 0.0;
@@ -279,7 +320,6 @@ void host_element_residual_map(const dg_mesh& M, int64_t k, const double* x, dou
         an = m.coef[f.nb];
       }
       for (int q = 0; q < qf; ++q) {
-        const double xg = T[g.tab_g + q], wg = T[g.tab_g + qf + q];
         const double* Bo = T + g.tab_bo + (size_t)q * NP;
         const double* Do = T + g.tab_bo + (size_t)(qf + q) * NP;
         double u0 = 0.0, du0 = 0.0, f0 = 0.0;
@@ -289,22 +329,8 @@ void host_element_residual_map(const dg_mesh& M, int64_t k, const double* x, dou
           f0 += Bo[i] * fo[i];
         }
         du0 /= hX;
-        const double Xt = g.xt0 + (g.xt1 - g.xt0) * xg;
-        const Jac2 J = s < 2 ? domain_jacobian(M.dmap, g.xc, Xt) : domain_jacobian(M.dmap, Xt, g.xc);
-        // tangent J e_t, normal J^-T nu (nu = so e_n), m = J^-1 n
-        const double tx = s < 2 ? J.j1 : J.j0, ty = s < 2 ? J.j3 : J.j2;
-        const double ds = std::sqrt(tx * tx + ty * ty);
-        const double det = J.j0 * J.j3 - J.j1 * J.j2;
-        double nx, ny;
-        if (s < 2) { nx = so * J.j3; ny = -so * J.j1; }
-        else { nx = -so * J.j2; ny = so * J.j0; }
-        const double nl = std::sqrt(nx * nx + ny * ny);
-        nx /= nl;
-        ny /= nl;
-        const double mX = (J.j3 * nx - J.j1 * ny) / det, mY = (-J.j2 * nx + J.j0 * ny) / det;
-        const double mn = s < 2 ? mX : mY, mt = s < 2 ? mY : mX;
-        const double W = wg * (g.xt1 - g.xt0) * ds;
-        const double Fo = so * f0 * mn + ak * du0 * mt;
+        const double w = W[q], wmt = W[qf + q], wmn = W[2 * qf + q];
+        const double Fo = f0 * wmn + ak * du0 * wmt;   // w (a grad u-) . n
         double jmp, flux, cc;
         if (f.nb >= 0) {
           const double* Bn = T + g.tab_bn + (size_t)q * npn;
@@ -316,7 +342,7 @@ void host_element_residual_map(const dg_mesh& M, int64_t k, const double* x, dou
             f1 += Bn[i] * fn[i];
           }
           du1 *= ihn;
-          const double Fn = -so * f1 * mn + an * du1 * mt;
+          const double Fn = -f1 * wmn + an * du1 * wmt;   // w (a grad u+) . n
           jmp = u0 - u1;
           flux = 0.5 * (Fo + Fn);
           cc = 0.5;
@@ -325,9 +351,9 @@ void host_element_residual_map(const dg_mesh& M, int64_t k, const double* x, dou
           flux = Fo;
           cc = 1.0;
         }
-        const double rho1 = W * (g.sigma * jmp - flux);
-        const double rho2 = -cc * W * jmp * mt;
-        const double rho3 = -cc * W * jmp * mn * so;
+        const double rho1 = g.sigma * jmp * w - flux;
+        const double rho2 = -cc * jmp * wmt;
+        const double rho3 = -cc * jmp * wmn;
         for (int i = 0; i < NP; ++i) {
           r[s * NP + i] += Bo[i] * rho1 + aih * Do[i] * rho2;
           c2[s * NP + i] += Bo[i] * rho3;
@@ -372,7 +398,7 @@ void host_lor_block_map(const dg_mesh& M, int64_t k, double* A) {
   const HostMesh& m = M.host;
   const int P = m.p[k], NP = P + 1, NN = NP * NP;
   const auto& gn = basis1d(P).nodes;
-  const double X0 = M.h_xo[3 * k], Y0 = M.h_xo[3 * k + 1], hX = M.h_xo[3 * k + 2];
+  const double X0 = m.lo[2 * k] * m.lh, Y0 = m.lo[2 * k + 1] * m.lh, hX = m.size[k] * m.lh;
   const double* c = m.corners;
   const double Lx = m.extent[0] * m.lh, Ly = m.extent[1] * m.lh;
   auto phi = [&](double X, double Y, double* out) {
