@@ -90,6 +90,12 @@ TRAFFIC = {
                            # captured on the same recipe at a 10^3 base (428,796 DOFs), scaled
                            # by the DOFs to the 16^3 workload (1,706,529 DOFs)
                            "bytes": 16861440 * 1706529 // 428796},
+    "apply_map_kernel/hp2d-map": {"sources": ["paper_2009_01287_gb300/csrc/apply_map_kernel.cuh",
+                                              "paper_2009_01287_gb300/csrc/apply_kernel.cuh",
+                                              "paper_2009_01287_gb300/csrc/apply_launch.cu",
+                                              "paper_2009_01287_gb300/csrc/dg_internal.h",
+                                              "paper_2009_01287_gb300/csrc/mesh_map.cpp"],
+                                  "sha256_16": "66b2520655a88353", "bytes": 10654720},
 }
 
 
