@@ -15,12 +15,19 @@ quadrilaterals otherwise.  Lattice lines map to straight lines, so a hanging
 sub-face is a straight segment of its master edge on both sides and the
 nonconforming structure of the box mesh carries over unchanged.
 
+A caller-supplied smooth map may take Phi's place (curved elements): the
+sub-faces are then the images of the lattice segments, curved in general,
+and both sides of a sub-face are evaluated at the same pre-image points, so
+the hanging structure still matches exactly.
+
 Readings (the paper fixes none of these for non-box elements):
   - quadrature: Gauss-Legendre with p+2 points per direction on the volume
     and max(p-, p+)+2 on a sub-face, in the pre-image coordinates (exact for
-    affine Phi; the integrands are rational for a bilinear Phi);
+    affine Phi; the integrands are rational for a bilinear Phi and
+    transcendental for a curved map);
   - the penalty's element size h_kappa = sqrt(|kappa|), the square root of
-    the physical area (the edge length for a square);
+    the physical area (the edge length for a square), the area taken by the
+    element's own volume rule;
   - physical normals n = J^{-T} nu / |J^{-T} nu| with nu the pre-image
     normal, and the arc length ds = |J t| dt along the pre-image tangent t.
 
@@ -73,22 +80,31 @@ class MappedDGSpace(DGSpace):
 
     qextra = 1   # p+2 (volume) and max(p-, p+)+2 (faces) Gauss points
 
-    def __init__(self, topo, lattice_h: float, corners, coef=None):
+    def __init__(self, topo, lattice_h: float, corners=None, coef=None, mapping=None):
+        """corners: the bilinear map's corner images; or mapping: any map of
+        the lattice domain with __call__(X) -> x and jacobian(X) -> J (curved
+        elements: the faces are the images of the lattice segments, curved
+        in general, with the normal and arc length varying along them)."""
         if int(getattr(topo, "dim", 2)) != 2:
             raise ValueError("mapped elements: squares only")
         super().__init__(topo, lattice_h, coef)
         ext = topo.extent
-        self.map = BilinearMap(corners, ext[0] * self.lh, ext[1] * self.lh)
-        X = np.array([[0.0, 0.0], [ext[0], 0.0], [0.0, ext[1]], [ext[0], ext[1]]]) * self.lh
-        if not np.all(np.linalg.det(self.map.jacobian(X)) > 0.0):
-            raise ValueError("the corners do not bound a convex, positively oriented quadrilateral")
+        if mapping is not None:
+            self.map = mapping
+        else:
+            self.map = BilinearMap(corners, ext[0] * self.lh, ext[1] * self.lh)
+            X = np.array([[0.0, 0.0], [ext[0], 0.0], [0.0, ext[1]], [ext[0], ext[1]]]) * self.lh
+            if not np.all(np.linalg.det(self.map.jacobian(X)) > 0.0):
+                raise ValueError("the corners do not bound a convex, positively oriented quadrilateral")
 
     def phys(self, pts: np.ndarray) -> np.ndarray:
         return self.map(pts)
 
     def area(self, k: int) -> float:
-        # det J is bilinear in X, so the 2-point Gauss rule integrates it exactly
-        pts, W = DGSpace.volume_quadrature(self, k, 2)
+        """|kappa| = int det J over the pre-image box by the element's own
+        volume rule (p+2 points per direction; exact for a bilinear map, whose
+        det J is linear)."""
+        pts, W = DGSpace.volume_quadrature(self, k, int(self.topo.p[k]) + 1 + self.qextra)
         return float(W @ np.linalg.det(self.map.jacobian(pts)))
 
     def hpen(self, k: int) -> float:
@@ -105,7 +121,10 @@ class MappedDGSpace(DGSpace):
 
     def volume_quadrature(self, k: int, q: int):
         pts, W = DGSpace.volume_quadrature(self, k, q)
-        return pts, W * np.linalg.det(self.map.jacobian(pts))
+        det = np.linalg.det(self.map.jacobian(pts))
+        if not np.all(det > 0.0):
+            raise ValueError("the map is not orientation preserving at a quadrature point")
+        return pts, W * det
 
     def face_quadrature(self, f, q: int):
         pts, W, nu = DGSpace.face_quadrature(self, f, q)

@@ -41,9 +41,10 @@ def build_operator(mesh, form: str = "sipg", eta: Optional[float] = None,
     else:
         topo = Topology(mesh.lo, mesh.size, mesh.p, mesh.extent)
     corners = getattr(mesh, "corners", None)
-    if corners is not None:
+    mapping = getattr(mesh, "mapping", None)
+    if corners is not None or mapping is not None:
         from .geometry import MappedDGSpace
-        space = MappedDGSpace(topo, mesh.lattice_h, corners, getattr(mesh, "coeff", None))
+        space = MappedDGSpace(topo, mesh.lattice_h, corners, getattr(mesh, "coeff", None), mapping=mapping)
     else:
         space = DGSpace(topo, mesh.lattice_h, getattr(mesh, "coeff", None))
     if eta is None:

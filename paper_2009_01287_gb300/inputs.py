@@ -42,6 +42,9 @@ class MeshDesc:
     # (0, Y), (X, Y) under the bilinear map that carries the leaf boxes to
     # quadrilaterals, or None for the boxes themselves (squares only)
     corners: Optional[np.ndarray] = None
+    # or a smooth map of the lattice domain (curved elements): an object with
+    # __call__(X) -> x and jacobian(X) -> J, J[m, i, j] = d x_i / d X_j
+    mapping: Optional[object] = None
 
     @property
     def n_elems(self) -> int:
@@ -140,6 +143,35 @@ PARALLELOGRAM = ((0.0, 0.0), (1.0, 0.0), (0.35, 0.9), (1.35, 0.9))
 QUADRILATERAL = ((0.0, 0.0), (1.2, 0.1), (0.15, 0.95), (1.05, 1.25))
 
 
+def with_mapping(mesh: MeshDesc, mapping) -> MeshDesc:
+    return dataclasses.replace(mesh, mapping=mapping)
+
+
+class WavyMap:
+    """A curved domain for the mapped-element workloads (problem geometry, an
+    input like the mesh): x = X + ax L sin(pi Y / L), y = Y + ay L sin(pi X / L)
+    on the lattice domain [0, L]^2.  Lattice lines become sine curves, so
+    every element and every sub-face is curved and the left and bottom sides
+    of the domain bulge."""
+
+    def __init__(self, L: float = 1.0, ax: float = 0.06, ay: float = 0.04):
+        self.L, self.ax, self.ay = float(L), float(ax), float(ay)
+
+    def __call__(self, X: np.ndarray) -> np.ndarray:
+        L = self.L
+        return np.stack([X[:, 0] + self.ax * L * np.sin(np.pi * X[:, 1] / L),
+                         X[:, 1] + self.ay * L * np.sin(np.pi * X[:, 0] / L)], axis=1)
+
+    def jacobian(self, X: np.ndarray) -> np.ndarray:
+        L = self.L
+        J = np.zeros((len(X), 2, 2))
+        J[:, 0, 0] = 1.0
+        J[:, 0, 1] = self.ax * np.pi * np.cos(np.pi * X[:, 1] / L)
+        J[:, 1, 0] = self.ay * np.pi * np.cos(np.pi * X[:, 0] / L)
+        J[:, 1, 1] = 1.0
+        return J
+
+
 def uniform_mesh(dim: int, base: int, p: int) -> MeshDesc:
     """Conforming `base`^dim grid of unit squares/cubes with uniform degree p."""
     cells = [tuple(reversed(c)) for c in np.ndindex(*([base] * dim))]
@@ -185,6 +217,12 @@ def config1_mapped(seed: int = 0, corners=QUADRILATERAL) -> Tuple[MeshDesc, Sine
     square onto a general convex quadrilateral."""
     mesh, rhs = config1(seed)
     return with_corners(mesh, corners), rhs
+
+
+def config1_curved(seed: int = 0) -> Tuple[MeshDesc, SineRHS]:
+    """The 2D hp-random workload on the curved domain of WavyMap."""
+    mesh, rhs = config1(seed)
+    return with_mapping(mesh, WavyMap()), rhs
 
 
 def config2(seed: int = 0, base: int = 16) -> Tuple[MeshDesc, SineRHS]:

@@ -10,7 +10,12 @@ general quadrilaterals), each against something the mathematics fixes:
     functions do the same for the Q1 LOR blocks at the sub-grid's interior
     nodes;
   - element areas sum to the shoelace area of the domain, the load vector of
-    f = 1 sums to it, and the matrix is SPD."""
+    f = 1 sums to it, and the matrix is SPD;
+  - curved maps (a caller's smooth map): the map's Jacobian against finite
+    differences, areas against a global high-order rule, a bilinear map given
+    as a generic map gives the corner form's matrix, and the nodal error of a
+    manufactured solution on the curved domain (f by symbolic differentiation
+    of the pulled-back Laplacian) falls like h^(p+1) under refinement."""
 import numpy as np
 import pytest
 
@@ -167,3 +172,80 @@ def test_non_convex_corners_rejected():
     bad = ((0.0, 0.0), (1.0, 0.0), (0.0, 1.0), (0.2, 0.2))
     with pytest.raises(ValueError):
         solver.build_problem(inputs.with_corners(mesh, bad))
+
+
+# ---------------------------------------------------------------- curved maps
+def test_wavy_map_jacobian_and_area():
+    F = inputs.WavyMap()
+    rng = np.random.default_rng(1)
+    P = rng.uniform(0, 1, size=(6, 2))
+    e = 1e-6
+    for j in range(2):
+        d = np.zeros(2)
+        d[j] = e
+        assert np.allclose(F.jacobian(P)[:, :, j], (F(P + d) - F(P - d)) / (2 * e), atol=1e-8)
+    # element areas (each by its own p+2 rule) sum to the domain's area, here
+    # by a 40-point tensor rule over the whole domain
+    mesh = _mesh(6, pmax=3)
+    prob = solver.build_problem(inputs.with_mapping(mesh, F))
+    from oracle import basis
+    x, w = basis.gauss(40)
+    X = np.stack(np.meshgrid(x, x), axis=-1).reshape(-1, 2)
+    ref = np.outer(w, w).ravel() @ np.linalg.det(F.jacobian(X))
+    assert abs(sum(prob.space.area(k) for k in range(prob.topo.n)) - ref) <= 1e-8
+
+
+def test_bilinear_map_as_a_generic_map_matches_corners():
+    mesh = _mesh(3, pmax=5)
+    c = np.array(inputs.QUADRILATERAL)
+    L = mesh.extent[0] * mesh.lattice_h
+    pa = solver.build_problem(inputs.with_corners(mesh, c))
+    pb = solver.build_problem(inputs.with_mapping(mesh, geometry.BilinearMap(c, L, L)))
+    assert abs(pa.A - pb.A).max() <= 1e-13 * abs(pa.A).max()
+
+
+def _wavy_manufactured():
+    """U(X, Y) = sin(pi X) sin(pi Y) in the pre-image, zero on the boundary of
+    the curved domain; f = -Laplace_x(u) pulled back to X by the chain rule,
+    -(1/det J) div_X(det J J^-1 J^-T grad_X U), differentiated symbolically."""
+    sympy = pytest.importorskip("sympy")
+    F = inputs.WavyMap()
+    X, Y = sympy.symbols("X Y")
+    L, ax, ay = F.L, F.ax, F.ay
+    J = sympy.Matrix([[1, ax * sympy.pi * sympy.cos(sympy.pi * Y / L)],
+                      [ay * sympy.pi * sympy.cos(sympy.pi * X / L), 1]])
+    det = J.det()
+    Ji = J.inv()
+    K = sympy.simplify(det * Ji * Ji.T)
+    U = sympy.sin(sympy.pi * X) * sympy.sin(sympy.pi * Y)
+    g = sympy.Matrix([sympy.diff(U, X), sympy.diff(U, Y)])
+    flux = K * g
+    lap = (sympy.diff(flux[0], X) + sympy.diff(flux[1], Y)) / det
+    f = sympy.lambdify((X, Y), -lap, "numpy")
+    u = sympy.lambdify((X, Y), U, "numpy")
+    return F, (lambda P: f(P[:, 0], P[:, 1])), (lambda P: u(P[:, 0], P[:, 1]))
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_curved_map_converges_at_the_optimal_rate(p):
+    """Nodal error of the SIPG solution on the curved domain under uniform
+    refinement falls like h^(p+1) (a wrong metric term, normal or weight
+    breaks this)."""
+    F, fX, uX = _wavy_manufactured()
+    errs = []
+    for base in (2, 4, 8):
+        mesh = inputs.with_mapping(inputs.uniform_mesh(2, base, p), F)
+        prob = solver.build_problem(mesh)
+        sp_ = prob.space
+        b = np.zeros(sp_.n)
+        for k in range(prob.topo.n):
+            pts, W = sp_.volume_quadrature(k, p + 3)
+            v, _ = sp_.eval(k, pts)
+            b[sp_.dofs(k)] = v.T @ (W * fX(pts))
+        x = np.linalg.solve(prob.A.toarray(), b)
+        from oracle.dg import DGSpace
+        Xn = np.concatenate([DGSpace.node_coords(sp_, k) for k in range(prob.topo.n)])
+        errs.append(np.abs(x - uX(Xn)).max())
+    rates = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert errs[-1] < 1e-3
+    assert rates[-1] > p + 1 - 0.6, (errs, rates)
