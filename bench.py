@@ -20,10 +20,12 @@ Beside it the same line carries
   cpu_baseline  the oracle timed on the host cores (one thread and all cores);
   workloads     sub-lines with their own clocks: the same mesh with BR2, the
                 16^3 cube workload, the same mesh carried onto a general
-                quadrilateral (mapped elements), the batched form (256
+                quadrilateral and onto a curved domain (mapped elements),
+                the batched form (256
                 problems x 4 right-hand sides in one launch) and a bounded
                 sample of the served form.
---workload hp2d-br2 | hp2d-coef | hp2d-map | hp3d | batched | serving runs one of them as the line.
+--workload hp2d-br2 | hp2d-coef | hp2d-map | hp2d-curved | hp3d | batched | serving runs one of them as
+the line.
 
 --impl reference times the FP64 CPU oracle on the same workload (a bounded
 sample of PCG iterations per step).  Multi-GPU: independent replicas (the
@@ -68,6 +70,11 @@ WORKLOADM = ("2D hp-random 32x32 base, prob 0.3, depth<=3, p~U{1..6}, carried by
              "square onto the quadrilateral (0,0) (1.2,0.1) (0.15,0.95) (1.05,1.25), SIPG eta=100 "
              "(h = sqrt(area)), p+2 Gauss points, tol 1e-8, seed 0")
 METRICM = ("DOF-iters/s (PCG on the 2D hp-random workload on mapped quadrilaterals, mixed FP32 preconditioner / "
+           "FP64 outer)")
+WORKLOADW = ("2D hp-random 32x32 base, prob 0.3, depth<=3, p~U{1..6}, carried by the curved map x = X + 0.06 "
+             "sin(pi Y), y = Y + 0.04 sin(pi X) of the unit square (curved elements and faces), SIPG eta=100 "
+             "(h = sqrt(area)), p+2 Gauss points, tol 1e-8, seed 0")
+METRICW = ("DOF-iters/s (PCG on the 2D hp-random workload on curved elements, mixed FP32 preconditioner / "
            "FP64 outer)")
 ORACLE_SAMPLE_ITERS = 20
 
@@ -477,7 +484,8 @@ def _oracle_problem(which: str, seed: int):
         prob = solver.build_problem(mesh, form="br2")
     else:
         mesh, rh = (inputs.config1_coeff(seed) if which == "hp2d-coef" else
-                    inputs.config1_mapped(seed) if which == "hp2d-map" else inputs.config1(seed))
+                    inputs.config1_mapped(seed) if which == "hp2d-map" else
+                    inputs.config1_curved(seed) if which == "hp2d-curved" else inputs.config1(seed))
         prob = solver.build_problem(mesh, form="br2" if which == "hp2d-br2" else "sipg")
     pc = solver.Preconditioner(prob, lor="amg")
     b = rhs.load_vector(prob.space, rh.amps, rh.waves)
@@ -581,21 +589,24 @@ def run_ours(args):
     three = args.workload == "hp3d"
     coef = args.workload == "hp2d-coef"
     br2 = args.workload == "hp2d-br2"
-    mapped = args.workload == "hp2d-map"
+    curved = args.workload == "hp2d-curved"
+    mapped = args.workload == "hp2d-map" or curved
     if three:
         mesh, rh = inputs.config2(args.seed, base=args.base3)
     else:
         mesh, rh = (inputs.config1_coeff(args.seed) if coef else
+                    inputs.config1_curved(args.seed) if curved else
                     inputs.config1_mapped(args.seed) if mapped else inputs.config1(args.seed))
     form = B.DG_FORM_BR2 if (three or br2) else B.DG_FORM_SIPG
     metric, workload = ((METRIC3, WORKLOAD3) if three else (METRICC, WORKLOADC) if coef else
-                        (METRICM, WORKLOADM) if mapped else
+                        (METRICW, WORKLOADW) if curved else (METRICM, WORKLOADM) if mapped else
                         (METRIC_BR2, WORKLOAD_BR2) if br2 else (METRIC, WORKLOAD))
     peaks, peak_kind = _peaks()
     probe = fp64_peak(B, ctx)
     if dist:
         dist.barrier()
-    tkey = ("apply3_kernel/hp3d" if three else "apply_map_kernel/hp2d-map" if mapped else
+    tkey = ("apply3_kernel/hp3d" if three else "apply_map_kernel/hp2d-map" if (mapped and not curved) else
+            "none" if curved else
             "apply_kernel/hp2d" if not (coef or br2) else "none")
     res = measure_single(B, ctx, mesh, rh, form, args.steps, args.warmup, peaks, probe["tflops"], tkey,
                          three=three, e2e=True, keep_x=True, tune=args.tune_tiles, mapped=mapped)
@@ -675,6 +686,12 @@ def run_ours(args):
             hm.pop(k, None)
         extras["hp2d_map"] = {"workload": WORKLOADM, "metric": "DOF-iters/s", "value": hm["dof_iters_per_s_mixed"],
                               **hm}
+        mw, rw = inputs.config1_curved(args.seed)
+        hw = measure_single(B, ctx, mw, rw, B.DG_FORM_SIPG, 3, 2, peaks, probe["tflops"], "none", mapped=True)
+        for k in ("_raw", "_e2e", "_x"):
+            hw.pop(k, None)
+        extras["hp2d_curved"] = {"workload": WORKLOADW, "metric": "DOF-iters/s",
+                                 "value": hw["dof_iters_per_s_mixed"], **hw}
         extras["batched"] = run_batched_leg(B, ctx, 2, 1)
         extras["serving"] = run_serving_leg(B, 8, 160, 200.0, 8)
         out["workloads"] = extras
@@ -723,15 +740,16 @@ def run_reference(args):
         return
     if args.workload in ("batched", "serving"):
         print(json.dumps({"impl": "reference", "unavailable": f"the oracle has no {args.workload} form; "
-                          "its single-problem PCG is timed by the hp2d, hp2d-br2, hp2d-coef, hp2d-map and hp3d "
-                          "workloads"}))
+                          "its single-problem PCG is timed by the hp2d, hp2d-br2, hp2d-coef, hp2d-map, hp2d-curved "
+                          "and hp3d workloads"}))
         return
     three = args.workload == "hp3d"
     coef = args.workload == "hp2d-coef"
     br2 = args.workload == "hp2d-br2"
     mapped = args.workload == "hp2d-map"
+    curved = args.workload == "hp2d-curved"
     metric, workload = ((METRIC3, WORKLOAD3) if three else (METRICC, WORKLOADC) if coef else
-                        (METRICM, WORKLOADM) if mapped else
+                        (METRICM, WORKLOADM) if mapped else (METRICW, WORKLOADW) if curved else
                         (METRIC_BR2, WORKLOAD_BR2) if br2 else (METRIC, WORKLOAD))
     prob, pc, b = _oracle_problem(args.workload, args.seed)
     for _ in range(args.warmup):
@@ -774,7 +792,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="only the line's own workload")
     ap.add_argument("--workload", default="hp2d",
-                    choices=["hp2d", "hp2d-br2", "hp2d-coef", "hp2d-map", "hp3d", "batched", "serving"])
+                    choices=["hp2d", "hp2d-br2", "hp2d-coef", "hp2d-map", "hp2d-curved", "hp3d", "batched",
+                             "serving"])
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-meshes", type=int, default=16)

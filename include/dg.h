@@ -76,7 +76,20 @@ typedef struct dg_precond dg_precond;
  * corners with DG_FORM_BR2 are DG_EUNSUPPORTED, as are corners in a batch.
  * Corners that do not bound a convex, counter-clockwise quadrilateral (det
  * of the map's Jacobian not positive at a corner) are DG_EINVAL.
+ * map, map_ctx: NULL (the boxes, or the corners' bilinear map), or, squares
+ * only and with corners NULL, a smooth map of the lattice domain chosen by
+ * the caller (curved elements): for n pre-image points X (n x 2, row-major)
+ * it writes their images x (n x 2) and the map's Jacobian there, J (n x 4:
+ * dx/dX, dx/dY, dy/dX, dy/dY).  The element maps are then T_kappa = map o
+ * (box map) and the sub-faces the images of the lattice segments (curved
+ * faces, the same hanging structure); the map is evaluated at every
+ * quadrature point, Gauss-Lobatto node and load-vector point during
+ * dg_mesh_create only, on the calling thread (never afterwards), and the
+ * geometric factors are stored.  The same forms, rules and penalty size as
+ * for corners.  A map whose Jacobian determinant is not positive, or whose
+ * values are not finite, at any of those points is DG_EINVAL.
  * All pointers are HOST pointers, read during the call. */
+typedef void (*dg_map_fn)(int64_t n, const double* X, double* x, double* J, void* ctx);
 typedef struct {
   int dim;
   int64_t n_elems;
@@ -87,6 +100,8 @@ typedef struct {
   double lattice_h;
   const double* coeff;
   const double* corners;
+  dg_map_fn map;
+  void* map_ctx;
 } dg_mesh_desc;
 
 enum { DG_FORM_SIPG = 0, DG_FORM_BR2 = 1 };

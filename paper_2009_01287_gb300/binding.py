@@ -36,11 +36,32 @@ ABI_SYMBOLS = (
 )
 
 
+# dg_map_fn: (n, X, x, J, ctx) - images and Jacobians of n pre-image points
+DgMapFn = C.CFUNCTYPE(None, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                      C.c_void_p)
+
+
 class DgMeshDesc(C.Structure):
     _fields_ = [("dim", C.c_int), ("n_elems", C.c_int64), ("lo", C.POINTER(C.c_int32)),
                 ("size", C.POINTER(C.c_int32)), ("p", C.POINTER(C.c_int32)),
                 ("extent", C.POINTER(C.c_int32)), ("lattice_h", C.c_double),
-                ("coeff", C.POINTER(C.c_double)), ("corners", C.POINTER(C.c_double))]
+                ("coeff", C.POINTER(C.c_double)), ("corners", C.POINTER(C.c_double)),
+                ("map", DgMapFn), ("map_ctx", C.c_void_p)]
+
+
+def _map_callback(mapping):
+    """A dg_map_fn that evaluates a Python map object (__call__(X) -> x,
+    jacobian(X) -> J of shape (n, 2, 2)).  An exception inside leaves the
+    outputs as the library pre-filled them (NaN), which it reports as
+    DG_EINVAL."""
+    def cb(n, X, x, J, ctx):
+        try:
+            Xa = np.ctypeslib.as_array(X, shape=(n, 2))
+            np.ctypeslib.as_array(x, shape=(n, 2))[:] = mapping(Xa)
+            np.ctypeslib.as_array(J, shape=(n, 4))[:] = np.asarray(mapping.jacobian(Xa)).reshape(n, 4)
+        except Exception:   # noqa: BLE001 - reported through the NaN outputs
+            pass
+    return DgMapFn(cb)
 
 
 class DgOptions(C.Structure):
@@ -172,12 +193,15 @@ def make_desc(mesh: MeshDesc):
     corners = getattr(mesh, "corners", None)
     if corners is not None:
         corners = np.ascontiguousarray(corners, dtype=np.float64).reshape(8)
-    keep = (lo, size, p, ext, coeff, corners)
+    mapping = getattr(mesh, "mapping", None)
+    fn = _map_callback(mapping) if mapping is not None else DgMapFn()
+    keep = (lo, size, p, ext, coeff, corners, fn)
     d = DgMeshDesc(mesh.dim, mesh.n_elems, lo.ctypes.data_as(C.POINTER(C.c_int32)),
                    size.ctypes.data_as(C.POINTER(C.c_int32)), p.ctypes.data_as(C.POINTER(C.c_int32)),
                    ext.ctypes.data_as(C.POINTER(C.c_int32)), float(mesh.lattice_h),
                    None if coeff is None else coeff.ctypes.data_as(C.POINTER(C.c_double)),
-                   None if corners is None else corners.ctypes.data_as(C.POINTER(C.c_double)))
+                   None if corners is None else corners.ctypes.data_as(C.POINTER(C.c_double)),
+                   fn, None)
     return d, keep
 
 

@@ -440,7 +440,7 @@ dg_status dg_batch_create(const dg_mesh_desc* descs, int n_problems, int n_rhs,
   try {
     DG_REQUIRE(descs && n_problems >= 1 && n_rhs >= 1, "bad batch size");
     for (int k = 0; k < n_problems; ++k)
-      if (descs[k].dim != 2 || descs[k].corners)
+      if (descs[k].dim != 2 || descs[k].corners || descs[k].map)
         throw Error(DG_EUNSUPPORTED, "the batched solver takes unmapped square meshes only");
     dg_options o{};
     o.form = DG_FORM_SIPG;

@@ -124,16 +124,11 @@ void host_rhs_sine(const dg_mesh& mesh, int n_modes, const double* amps, const i
         for (int gxi = 0; gxi < q; ++gxi) {
           double X[3] = {x0[0] + h * gx[gxi], x0[1] + h * gx[gy], x0[2] + h * gx[gz]};
           double detJ = 1.0;
-          if (m.mapped) {   // f at the physical point, the weight times det J
-            const Jac2 J = domain_jacobian(mesh.dmap, X[0], X[1]);
-            detJ = J.j0 * J.j3 - J.j1 * J.j2;
-            const double s = X[0] / (m.extent[0] * m.lh), t = X[1] / (m.extent[1] * m.lh);
-            const double wc[4] = {(1 - s) * (1 - t), s * (1 - t), (1 - s) * t, s * t};
-            X[0] = X[1] = 0.0;
-            for (int a = 0; a < 4; ++a) {
-              X[0] += wc[a] * m.corners[2 * a];
-              X[1] += wc[a] * m.corners[2 * a + 1];
-            }
+          if (m.mapped) {   // f at the physical point, the weight times det J (stored at creation)
+            const double* pt = mesh.h_xrhs.data() + mesh.h_roff[k] + 3 * (gy * q + gxi);
+            X[0] = pt[0];
+            X[1] = pt[1];
+            detJ = pt[2];
           }
           double f = 0.0;
           for (int md = 0; md < n_modes; ++md) {

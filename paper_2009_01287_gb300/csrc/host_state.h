@@ -123,6 +123,12 @@ struct dg_mesh {
   dg::DomainMap dmap{};
   std::vector<double> h_gvol, h_gface;
   std::vector<int64_t> h_goff;
+  // host only: per element the images of its (p+1)^2 Gauss-Lobatto nodes (the
+  // LOR cells' vertices) and, at the (p+3)^2 points of the load-vector rule,
+  // the image and det J (x, y, det per point; offsets h_roff), so that no
+  // later call needs the caller's map
+  std::vector<double> h_xnode, h_xrhs;
+  std::vector<int64_t> h_roff;
   int64_t apply3_smem = 0;              // dynamic shared memory of the 3D operator kernel
   std::vector<double> h_tables;
   dg::BasisOff boff[dg::kMaxP + 1];
@@ -245,7 +251,7 @@ void tune_tiles(dg_mesh* M, cudaStream_t s, void (*retile)(dg_mesh*, void*), voi
 void build_mesh_host3(dg_mesh* M, const dg_mesh_desc* desc, const dg_options& opts);
 // mapped squares: records, tables and geometry (after the SIPG records), and
 // the flop and byte counts of the mapped operator (after the box counts)
-void build_mesh_map(dg_mesh* M);
+void build_mesh_map(dg_mesh* M, const dg_mesh_desc* desc);
 void map_stats(dg_mesh* M);
 // rows of element k of y = A x on a mapped mesh, and their diagonal, and the
 // LOR block of element k (dense (p+1)^2 x (p+1)^2, row-major)

@@ -286,12 +286,14 @@ void build_mesh_host(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opt
     return;
   }
   validate_and_copy(desc, m);
-  if (desc->corners) {
-    if (o.form != DG_FORM_SIPG) throw Error(DG_EUNSUPPORTED, "mapped elements (corners): SIPG only");
-    for (int i = 0; i < 8; ++i) {
-      DG_REQUIRE(std::isfinite(desc->corners[i]), "corners must be finite");
-      m.corners[i] = desc->corners[i];
-    }
+  if (desc->corners || desc->map) {
+    DG_REQUIRE(!(desc->corners && desc->map), "give corners or a map, not both");
+    if (o.form != DG_FORM_SIPG) throw Error(DG_EUNSUPPORTED, "mapped elements: SIPG only");
+    if (desc->corners)
+      for (int i = 0; i < 8; ++i) {
+        DG_REQUIRE(std::isfinite(desc->corners[i]), "corners must be finite");
+        m.corners[i] = desc->corners[i];
+      }
     m.mapped = true;
   }
   build_topology(m);
@@ -441,7 +443,7 @@ void build_mesh_host(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opt
     g.tab_x += base;
     g.tab_y += base;
   }
-  if (m.mapped) build_mesh_map(M);   // the mapped records and tables
+  if (m.mapped) build_mesh_map(M, desc);   // the mapped records, tables and factors
   build_tiles(M);
   // operation and byte counts of one operator apply, as the kernel does it
   dg_mesh_stats& S = M->stats;

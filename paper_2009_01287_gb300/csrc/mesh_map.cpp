@@ -66,37 +66,66 @@ int append_side_table(std::vector<double>& t, int p, int q, int num, int len, in
   return off;
 }
 
-// det J of the domain map is linear in (X, Y) (the XY terms cancel), so its
-// mean over a box is its value at the centre
-double box_area(const DomainMap& D, double X0, double Y0, double h) {
-  const Jac2 J = domain_jacobian(D, X0 + 0.5 * h, Y0 + 0.5 * h);
-  return (J.j0 * J.j3 - J.j1 * J.j2) * h * h;
-}
+// The map at a batch of pre-image points: the caller's map, or the bilinear
+// map of the corners in closed form.  x: 2 per point, J: 4 per point.
+struct MapEval {
+  const dg_mesh_desc* desc;
+  const DomainMap* D;
+  const double* c;
+  double Lx, Ly;
+  void operator()(int64_t n, const double* X, double* x, double* J) const {
+    if (desc->map) {
+      std::fill(x, x + 2 * n, std::nan(""));
+      std::fill(J, J + 4 * n, std::nan(""));
+      desc->map(n, X, x, J, desc->map_ctx);
+      for (int64_t i = 0; i < 2 * n; ++i) DG_REQUIRE(std::isfinite(x[i]), "the map returned a non-finite point");
+      for (int64_t i = 0; i < 4 * n; ++i) DG_REQUIRE(std::isfinite(J[i]), "the map returned a non-finite Jacobian");
+    } else {
+      for (int64_t i = 0; i < n; ++i) {
+        const double s = X[2 * i] / Lx, t = X[2 * i + 1] / Ly;
+        const double w[4] = {(1 - s) * (1 - t), s * (1 - t), (1 - s) * t, s * t};
+        x[2 * i] = x[2 * i + 1] = 0.0;
+        for (int a = 0; a < 4; ++a) {
+          x[2 * i] += w[a] * c[2 * a];
+          x[2 * i + 1] += w[a] * c[2 * a + 1];
+        }
+        const Jac2 j = domain_jacobian(*D, X[2 * i], X[2 * i + 1]);
+        J[4 * i] = j.j0;
+        J[4 * i + 1] = j.j1;
+        J[4 * i + 2] = j.j2;
+        J[4 * i + 3] = j.j3;
+      }
+    }
+    for (int64_t i = 0; i < n; ++i)
+      DG_REQUIRE(J[4 * i] * J[4 * i + 3] - J[4 * i + 1] * J[4 * i + 2] > 0.0,
+                 "the map is not orientation preserving at a quadrature point");
+  }
+};
 
 }  // namespace
 
-void build_mesh_map(dg_mesh* M) {
+void build_mesh_map(dg_mesh* M, const dg_mesh_desc* desc) {
   HostMesh& m = M->host;
   const double Lx = m.extent[0] * m.lh, Ly = m.extent[1] * m.lh;
   const double* c = m.corners;
   DomainMap& D = M->dmap;
-  D.u1x = (c[2] - c[0]) / Lx;
-  D.u1y = (c[3] - c[1]) / Lx;
-  D.u2x = (c[4] - c[0]) / Ly;
-  D.u2y = (c[5] - c[1]) / Ly;
-  D.u3x = (c[6] - c[4] - c[2] + c[0]) / (Lx * Ly);
-  D.u3y = (c[7] - c[5] - c[3] + c[1]) / (Lx * Ly);
-  // det J is linear in (X, Y): positive everywhere iff at the four corners
-  const double XY[4][2] = {{0.0, 0.0}, {Lx, 0.0}, {0.0, Ly}, {Lx, Ly}};
-  for (const auto& p : XY) {
-    const Jac2 J = domain_jacobian(D, p[0], p[1]);
-    DG_REQUIRE(J.j0 * J.j3 - J.j1 * J.j2 > 0.0,
-               "corners do not bound a convex, counter-clockwise quadrilateral");
+  D = DomainMap{};
+  if (!desc->map) {
+    D.u1x = (c[2] - c[0]) / Lx;
+    D.u1y = (c[3] - c[1]) / Lx;
+    D.u2x = (c[4] - c[0]) / Ly;
+    D.u2y = (c[5] - c[1]) / Ly;
+    D.u3x = (c[6] - c[4] - c[2] + c[0]) / (Lx * Ly);
+    D.u3y = (c[7] - c[5] - c[3] + c[1]) / (Lx * Ly);
+    // det J is linear in (X, Y): positive everywhere iff at the four corners
+    const double XY[4][2] = {{0.0, 0.0}, {Lx, 0.0}, {0.0, Ly}, {Lx, Ly}};
+    for (const auto& p : XY) {
+      const Jac2 J = domain_jacobian(D, p[0], p[1]);
+      DG_REQUIRE(J.j0 * J.j3 - J.j1 * J.j2 > 0.0,
+                 "corners do not bound a convex, counter-clockwise quadrilateral");
+    }
   }
-  // penalty sizes h_kappa = sqrt(|kappa|)
-  std::vector<double> hpen(m.n);
-  for (int64_t k = 0; k < m.n; ++k)
-    hpen[k] = std::sqrt(box_area(D, m.lo[2 * k] * m.lh, m.lo[2 * k + 1] * m.lh, m.size[k] * m.lh));
+  const MapEval map{desc, &D, c, Lx, Ly};
   // tables, appended after the box tables
   std::vector<double>& T = M->h_tables;
   std::map<int, int> rules;
@@ -118,29 +147,43 @@ void build_mesh_map(dg_mesh* M) {
   }
   M->moff[0] = M->moff[1];
   // volume factors a w_g w_h G = a w_g w_h det(J) J^-1 J^-T at every Gauss
-  // point (the box's own scaling cancels in 2D), three planes per element
+  // point (the box's own scaling cancels in 2D), three planes per element;
+  // the element's area by the same rule gives its penalty size sqrt(|kappa|)
   M->h_goff.assign(m.n + 1, 0);
   for (int64_t k = 0; k < m.n; ++k) {
     const int64_t q = m.p[k] + 1 + kMapQExtra;
     M->h_goff[k + 1] = M->h_goff[k] + 3 * q * q;
   }
   M->h_gvol.assign(M->h_goff[m.n], 0.0);
+  std::vector<double> hpen(m.n), X, x, J;
   for (int64_t k = 0; k < m.n; ++k) {
     const int P = m.p[k], Q = P + 1 + kMapQExtra, QQ = Q * Q;
     const double* gx = T.data() + M->moff[P].gx;
     const double* gw = T.data() + M->moff[P].gw;
     const double X0 = m.lo[2 * k] * m.lh, Y0 = m.lo[2 * k + 1] * m.lh, h = m.size[k] * m.lh;
-    double* G = M->h_gvol.data() + M->h_goff[k];
+    X.resize(2 * QQ);
+    x.resize(2 * QQ);
+    J.resize(4 * QQ);
     for (int gy = 0; gy < Q; ++gy)
       for (int gxi = 0; gxi < Q; ++gxi) {
-        const Jac2 J = domain_jacobian(D, X0 + h * gx[gxi], Y0 + h * gx[gy]);
-        const double det = J.j0 * J.j3 - J.j1 * J.j2;
-        const double w = m.coef[k] * gw[gxi] * gw[gy] / det;
-        const int pt = gy * Q + gxi;
-        G[pt] = w * (J.j1 * J.j1 + J.j3 * J.j3);
-        G[QQ + pt] = -w * (J.j0 * J.j1 + J.j2 * J.j3);
-        G[2 * QQ + pt] = w * (J.j0 * J.j0 + J.j2 * J.j2);
+        X[2 * (gy * Q + gxi)] = X0 + h * gx[gxi];
+        X[2 * (gy * Q + gxi) + 1] = Y0 + h * gx[gy];
       }
+    map(QQ, X.data(), x.data(), J.data());
+    double* G = M->h_gvol.data() + M->h_goff[k];
+    double area = 0.0;
+    for (int gy = 0; gy < Q; ++gy)
+      for (int gxi = 0; gxi < Q; ++gxi) {
+        const int pt = gy * Q + gxi;
+        const double* j = &J[4 * pt];
+        const double det = j[0] * j[3] - j[1] * j[2];
+        const double w = m.coef[k] * gw[gxi] * gw[gy] / det;
+        G[pt] = w * (j[1] * j[1] + j[3] * j[3]);
+        G[QQ + pt] = -w * (j[0] * j[1] + j[2] * j[3]);
+        G[2 * QQ + pt] = w * (j[0] * j[0] + j[2] * j[2]);
+        area += gw[gxi] * gw[gy] * det * h * h;
+      }
+    hpen[k] = std::sqrt(area);
   }
   M->h_sfm.assign(m.sf.size(), SubFaceMap{});
   M->h_gface.clear();
@@ -182,18 +225,26 @@ void build_mesh_map(dg_mesh* M) {
         M->h_gface.resize(M->h_gface.size() + 3 * (size_t)qf);
         double* G = M->h_gface.data() + r.geo;
         const double xc = cc * m.lh, xt0 = f.t0 * m.lh, xt1 = f.t1 * m.lh;
+        X.resize(2 * qf);
+        x.resize(2 * qf);
+        J.resize(4 * qf);
         for (int g = 0; g < qf; ++g) {
           const double Xt = xt0 + (xt1 - xt0) * T[rg + g];
-          const Jac2 J = s < 2 ? domain_jacobian(D, xc, Xt) : domain_jacobian(D, Xt, xc);
-          const double tx = s < 2 ? J.j1 : J.j0, ty = s < 2 ? J.j3 : J.j2;
-          const double det = J.j0 * J.j3 - J.j1 * J.j2;
+          X[2 * g] = s < 2 ? xc : Xt;
+          X[2 * g + 1] = s < 2 ? Xt : xc;
+        }
+        map(qf, X.data(), x.data(), J.data());
+        for (int g = 0; g < qf; ++g) {
+          const double* jj = &J[4 * g];
+          const double tx = s < 2 ? jj[1] : jj[0], ty = s < 2 ? jj[3] : jj[2];
+          const double det = jj[0] * jj[3] - jj[1] * jj[2];
           double nx, ny;
-          if (s < 2) { nx = so * J.j3; ny = -so * J.j1; }
-          else { nx = -so * J.j2; ny = so * J.j0; }
+          if (s < 2) { nx = so * jj[3]; ny = -so * jj[1]; }
+          else { nx = -so * jj[2]; ny = so * jj[0]; }
           const double nl = std::sqrt(nx * nx + ny * ny);
           nx /= nl;
           ny /= nl;
-          const double mX = (J.j3 * nx - J.j1 * ny) / det, mY = (J.j0 * ny - J.j2 * nx) / det;
+          const double mX = (jj[3] * nx - jj[1] * ny) / det, mY = (jj[0] * ny - jj[2] * nx) / det;
           const double mn = s < 2 ? mX : mY, mt = s < 2 ? mY : mX;
           const double W = T[rg + qf + g] * (xt1 - xt0) * std::sqrt(tx * tx + ty * ty);
           G[g] = W;
@@ -203,6 +254,43 @@ void build_mesh_map(dg_mesh* M) {
       }
     }
   DG_REQUIRE(T.size() < (1ULL << 31), "face tables too large");
+  // images of the Gauss-Lobatto nodes (LOR cells) and of the load-vector
+  // rule's points with det J, kept so that no later call needs the map
+  M->h_xnode.clear();
+  M->h_xrhs.clear();
+  M->h_roff.assign(m.n + 1, 0);
+  for (int64_t k = 0; k < m.n; ++k) {
+    const int P = m.p[k], NP = P + 1, q = P + 3;
+    const auto& gn = basis1d(P).nodes;
+    std::vector<double> rx, rw;
+    gauss_rule(q, rx, rw);
+    const double X0 = m.lo[2 * k] * m.lh, Y0 = m.lo[2 * k + 1] * m.lh, h = m.size[k] * m.lh;
+    X.resize(2 * NP * NP);
+    x.resize(2 * NP * NP);
+    J.resize(4 * NP * NP);
+    for (int j = 0; j < NP; ++j)
+      for (int i = 0; i < NP; ++i) {
+        X[2 * (j * NP + i)] = X0 + h * gn[i];
+        X[2 * (j * NP + i) + 1] = Y0 + h * gn[j];
+      }
+    map(NP * NP, X.data(), x.data(), J.data());
+    M->h_xnode.insert(M->h_xnode.end(), x.begin(), x.end());
+    X.resize(2 * q * q);
+    x.resize(2 * q * q);
+    J.resize(4 * q * q);
+    for (int gy = 0; gy < q; ++gy)
+      for (int gxi = 0; gxi < q; ++gxi) {
+        X[2 * (gy * q + gxi)] = X0 + h * rx[gxi];
+        X[2 * (gy * q + gxi) + 1] = Y0 + h * rx[gy];
+      }
+    map(q * q, X.data(), x.data(), J.data());
+    for (int pt = 0; pt < q * q; ++pt) {
+      M->h_xrhs.push_back(x[2 * pt]);
+      M->h_xrhs.push_back(x[2 * pt + 1]);
+      M->h_xrhs.push_back(J[4 * pt] * J[4 * pt + 3] - J[4 * pt + 1] * J[4 * pt + 2]);
+    }
+    M->h_roff[k + 1] = (int64_t)M->h_xrhs.size();
+  }
 }
 
 void map_stats(dg_mesh* M) {
@@ -397,19 +485,9 @@ void host_lor_block_map(const dg_mesh& M, int64_t k, double* A) {
   // Q1 stiffness on the images of the Gauss-Lobatto cells, 2 x 2 Gauss
   const HostMesh& m = M.host;
   const int P = m.p[k], NP = P + 1, NN = NP * NP;
-  const auto& gn = basis1d(P).nodes;
-  const double X0 = m.lo[2 * k] * m.lh, Y0 = m.lo[2 * k + 1] * m.lh, hX = m.size[k] * m.lh;
-  const double* c = m.corners;
-  const double Lx = m.extent[0] * m.lh, Ly = m.extent[1] * m.lh;
-  auto phi = [&](double X, double Y, double* out) {
-    const double s = X / Lx, t = Y / Ly;
-    const double w[4] = {(1 - s) * (1 - t), s * (1 - t), (1 - s) * t, s * t};
-    out[0] = out[1] = 0.0;
-    for (int a = 0; a < 4; ++a) {
-      out[0] += w[a] * c[2 * a];
-      out[1] += w[a] * c[2 * a + 1];
-    }
-  };
+  // the element's node images: h_xnode holds 2 (p+1)^2 values per element,
+  // element by element like the DOFs
+  const double* xn = M.h_xnode.data() + 2 * m.off[k];
   std::vector<double> gx, gw;
   gauss_rule(2, gx, gw);
   std::fill(A, A + (size_t)NN * NN, 0.0);
@@ -418,8 +496,8 @@ void host_lor_block_map(const dg_mesh& M, int64_t k, double* A) {
       double V[4][2];
       const int idx[4] = {cj * NP + ci, cj * NP + ci + 1, (cj + 1) * NP + ci, (cj + 1) * NP + ci + 1};
       for (int a = 0; a < 4; ++a) {
-        const double ex = gn[ci + (a & 1)], ey = gn[cj + (a >> 1)];
-        phi(X0 + hX * ex, Y0 + hX * ey, V[a]);
+        V[a][0] = xn[2 * idx[a]];
+        V[a][1] = xn[2 * idx[a] + 1];
       }
       double K[4][4] = {{0.0}};
       for (int qy = 0; qy < 2; ++qy)

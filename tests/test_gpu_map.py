@@ -1,6 +1,6 @@
 """GPU parity on mapped squares (Section 2: element maps T_kappa onto general
-quadrilaterals; the mapped operator kernel) through the C ABI, against the
-oracle's mapped space.
+quadrilaterals, bilinear or curved; the mapped operator kernel) through the C
+ABI, against the oracle's mapped space.
 
 Tolerances as for boxes: operator and FP64 preconditioner applies to 1e-12
 relative (max-norm), PCG iterations within +-1 of the oracle, the mixed
@@ -31,6 +31,11 @@ MESHES = {
                                                ((0.0, 0.0), (1.1, 0.2), (-0.1, 0.6), (0.9, 0.75))),
     "quad-coef": lambda: inputs.with_corners(_coef(inputs.small_hp_mesh(6, base=4, depth=3, prob=0.4, pmax=6), 4),
                                              inputs.QUADRILATERAL),
+    # curved elements: the caller's smooth map (inputs.WavyMap) evaluated at setup
+    "wavy-hp": lambda: inputs.with_mapping(inputs.small_hp_mesh(1, base=4, depth=3, prob=0.4, pmax=5),
+                                           inputs.WavyMap()),
+    "wavy-coef-p8": lambda: inputs.with_mapping(
+        _coef(inputs.small_hp_mesh(3, base=3, depth=2, prob=0.5, pmin=5, pmax=8), 3), inputs.WavyMap(ax=0.1)),
 }
 
 
@@ -67,7 +72,7 @@ def test_apply_parity_mapped(built_lib, torch_mod, name):
 
 
 @pytest.mark.parametrize("lor", ["exact", "amg"])
-@pytest.mark.parametrize("name", ["par-hp", "quad-ragged", "quad-coef"])
+@pytest.mark.parametrize("name", ["par-hp", "quad-ragged", "quad-coef", "wavy-hp"])
 def test_precond_parity_fp64_mapped(built_lib, torch_mod, name, lor):
     mesh = MESHES[name]()
     prob = solver.build_problem(mesh)
@@ -84,7 +89,7 @@ def test_precond_parity_fp64_mapped(built_lib, torch_mod, name, lor):
     assert rel(zd.cpu().numpy(), opc.apply(r)) <= 1e-12
 
 
-@pytest.mark.parametrize("name", ["par-hp", "quad-hp", "quad-ragged", "quad-coef"])
+@pytest.mark.parametrize("name", ["par-hp", "quad-hp", "quad-ragged", "quad-coef", "wavy-hp", "wavy-coef-p8"])
 def test_pcg_iterations_match_oracle_mapped(built_lib, torch_mod, name):
     mesh = MESHES[name]()
     prob = solver.build_problem(mesh)
@@ -117,12 +122,13 @@ def test_pcg_iterations_match_oracle_mapped(built_lib, torch_mod, name):
     assert float(torch_mod.linalg.norm(r - bd) / torch_mod.linalg.norm(bd)) <= 1.5e-8
 
 
-def test_full_size_mapped_sampled(built_lib, torch_mod):
-    """The 98,127-DOF 2D hp-random workload on the general quadrilateral: the
-    apply in the launch configuration the benchmark times, on sampled elements
-    whose rows the oracle computes one by one, and a mixed solve checked by its
-    true FP64 residual."""
-    mesh, rh = inputs.config1_mapped(0)
+@pytest.mark.parametrize("which", ["quad", "wavy"])
+def test_full_size_mapped_sampled(built_lib, torch_mod, which):
+    """The 98,127-DOF 2D hp-random workload on the general quadrilateral and on
+    the curved domain: the apply in the launch configuration the benchmark
+    times, on sampled elements whose rows the oracle computes one by one, and
+    a mixed solve checked by its true FP64 residual."""
+    mesh, rh = inputs.config1_mapped(0) if which == "quad" else inputs.config1_curved(0)
     B = built_lib
     M = B.Mesh(mesh)
     x = inputs.random_vector(M.n_dofs, 10)
@@ -134,7 +140,7 @@ def test_full_size_mapped_sampled(built_lib, torch_mod):
     from oracle.geometry import MappedDGSpace
     from oracle.topology import Topology
     topo = Topology(mesh.lo, mesh.size, mesh.p, mesh.extent)
-    space = MappedDGSpace(topo, mesh.lattice_h, mesh.corners)
+    space = MappedDGSpace(topo, mesh.lattice_h, mesh.corners, mapping=mesh.mapping)
     rng = np.random.default_rng(0)
     for k in rng.choice(topo.n, size=40, replace=False):
         ref = dg.element_rows(space, int(k), x, 100.0)

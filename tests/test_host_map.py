@@ -85,3 +85,58 @@ def test_mapped_input_checks(built_lib):
     assert e.value.code == B.DG_EUNSUPPORTED
     with pytest.raises(B.DGError):
         B.HostSetup(inputs.with_corners(mesh, ((0, 0), (1, 0), (0, 1), (np.nan, 1))), B.make_options())
+
+
+# ---------------------------------------------------------------- curved maps
+CURVED = [
+    ("wavy-hp", lambda: inputs.with_mapping(inputs.small_hp_mesh(1, base=4, depth=3, prob=0.4, pmax=5),
+                                            inputs.WavyMap())),
+    ("wavy-coef-p8", lambda: inputs.with_mapping(
+        _coef(inputs.small_hp_mesh(3, base=3, depth=2, prob=0.5, pmin=5, pmax=8), 3), inputs.WavyMap(ax=0.1))),
+]
+
+
+@pytest.mark.parametrize("name,mk", CURVED, ids=[c[0] for c in CURVED])
+def test_host_setup_matches_oracle_curved(built_lib, name, mk):
+    test_host_setup_matches_oracle_mapped(built_lib, name, mk)
+
+
+def test_bilinear_callback_matches_corners(built_lib):
+    """The corners' bilinear map given through the map callback builds the
+    same operator and LOR matrix as the corners themselves."""
+    from oracle.geometry import BilinearMap
+    mesh = inputs.small_hp_mesh(2, base=4, depth=3, prob=0.4, pmax=6)
+    L = mesh.extent[0] * mesh.lattice_h
+    B = built_lib
+    a = B.HostSetup(inputs.with_corners(mesh, inputs.QUADRILATERAL), B.make_options(), amg=False)
+    b = B.HostSetup(inputs.with_mapping(mesh, BilinearMap(inputs.QUADRILATERAL, L, L)), B.make_options(),
+                    amg=False)
+    x = inputs.random_vector(a.n, 5)
+    ya, yb = a.apply(x), b.apply(x)
+    assert np.abs(ya - yb).max() <= 1e-13 * np.abs(ya).max()
+    assert abs(a.Ac - b.Ac).max() <= 1e-13 * abs(a.Ac).max()
+
+
+class _Folded(inputs.WavyMap):
+    """A map that folds the domain over (det J < 0 inside)."""
+    def jacobian(self, X):
+        J = super().jacobian(X)
+        J[:, 1, 1] = -0.5
+        return J
+
+
+class _Broken(inputs.WavyMap):
+    def __call__(self, X):
+        raise RuntimeError("no geometry here")
+
+
+def test_curved_input_checks(built_lib):
+    B = built_lib
+    mesh = inputs.small_hp_mesh(1)
+    for bad in (_Folded(), _Broken()):
+        with pytest.raises(B.DGError) as e:
+            B.HostSetup(inputs.with_mapping(mesh, bad), B.make_options())
+        assert e.value.code == B.DG_EINVAL
+    both = inputs.with_mapping(inputs.with_corners(mesh, inputs.QUADRILATERAL), inputs.WavyMap())
+    with pytest.raises(B.DGError):
+        B.HostSetup(both, B.make_options())
