@@ -148,7 +148,7 @@ class DGSpace:
 
     def mass(self, k: int) -> np.ndarray:
         p = int(self.topo.p[k])
-        pts, W = self.volume_quadrature(k, p + 1)
+        pts, W = self.volume_quadrature(k, p + 1 + self.qextra)
         v, _ = self.eval(k, pts)
         return v.T @ (W[:, None] * v)
 

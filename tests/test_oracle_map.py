@@ -249,3 +249,104 @@ def test_curved_map_converges_at_the_optimal_rate(p):
     rates = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert errs[-1] < 1e-3
     assert rates[-1] > p + 1 - 0.6, (errs, rates)
+
+
+# ---------------------------------------------------------------- BR2 on mapped elements
+def test_br2_similarity_map_leaves_matrix_unchanged():
+    mesh = _mesh(2, pmax=5)
+    th, s, sh = -1.1, 0.7, np.array([0.3, 0.9])
+    R = s * np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    L = mesh.extent[0] * mesh.lattice_h
+    corners = [sh, sh + R @ [L, 0], sh + R @ [0, L], sh + R @ [L, L]]
+    pa = solver.build_problem(mesh, form="br2")
+    pb = solver.build_problem(inputs.with_corners(mesh, corners), form="br2")
+    assert abs(pa.A - pb.A).max() <= 1e-12 * abs(pa.A).max()
+
+
+def test_br2_affine_map_reproduces_manufactured_solution():
+    mesh = _mesh(3, pmin=2, pmax=4)
+    c = np.array(inputs.PARALLELOGRAM)
+    L = mesh.extent[0] * mesh.lattice_h
+    A = np.stack([(c[1] - c[0]) / L, (c[2] - c[0]) / L], axis=1)
+    Ai = np.linalg.inv(A)
+    Gm = Ai @ Ai.T
+
+    def pre(x):
+        return (x - c[0]) @ Ai.T
+
+    def u(x):
+        X = pre(x)
+        return X[:, 0] * (L - X[:, 0]) * X[:, 1] * (L - X[:, 1])
+
+    def f(x):
+        X, Y = pre(x).T
+        return -(Gm[0, 0] * -2.0 * Y * (L - Y) + 2 * Gm[0, 1] * (L - 2 * X) * (L - 2 * Y)
+                 + Gm[1, 1] * -2.0 * X * (L - X))
+
+    prob = solver.build_problem(inputs.with_corners(mesh, c), form="br2")
+    b = rhs.load_vector_fn(prob.space, f, extra=3)
+    x = np.linalg.solve(prob.A.toarray(), b)
+    ui = rhs.interpolate(prob.space, u)
+    assert np.abs(x - ui).max() <= 1e-10 * np.abs(ui).max()
+
+
+def test_br2_bilinear_harmonic_patch_and_spd():
+    mesh = _mesh(4, pmin=2, pmax=5, base=4)
+    prob = solver.build_problem(inputs.with_corners(mesh, inputs.QUADRILATERAL), form="br2")
+    ui = rhs.interpolate(prob.space, lambda x: x[:, 0] * x[:, 1])
+    r = prob.A @ ui
+    scale = np.abs(prob.A).max() * np.abs(ui).max()
+    for k in _interior_elements(prob.topo):
+        assert np.abs(r[prob.space.dofs(k)]).max() <= 1e-12 * scale
+    A = prob.A.toarray()
+    assert np.abs(A - A.T).max() <= 1e-12 * np.abs(A).max()
+    assert np.linalg.eigvalsh(A).min() > 0.0
+
+
+@pytest.mark.parametrize("p", [2])
+def test_br2_curved_map_converges(p):
+    F, fX, uX = _wavy_manufactured()
+    errs = []
+    for base in (2, 4, 8):
+        prob = solver.build_problem(inputs.with_mapping(inputs.uniform_mesh(2, base, p), F), form="br2")
+        sp_ = prob.space
+        b = np.zeros(sp_.n)
+        for k in range(prob.topo.n):
+            pts, W = sp_.volume_quadrature(k, p + 3)
+            v, _ = sp_.eval(k, pts)
+            b[sp_.dofs(k)] = v.T @ (W * fX(pts))
+        x = np.linalg.solve(prob.A.toarray(), b)
+        from oracle.dg import DGSpace
+        Xn = np.concatenate([DGSpace.node_coords(sp_, k) for k in range(prob.topo.n)])
+        errs.append(np.abs(x - uX(Xn)).max())
+    rate = np.log2(errs[1] / errs[2])
+    assert rate > p + 1 - 0.6, (errs, rate)
+
+
+def test_br2_lifting_energy_uses_the_mapped_mass():
+    """On one mapped element, the BR2 lifting energy of the boundary jump of u
+    is eta * b^T M^-1 b with M the element's physical mass matrix: checked
+    against the same quantity from an independently assembled mass matrix
+    (a 12-point rule; exact for the bilinear map)."""
+    mesh = inputs.uniform_mesh(2, 1, 3)
+    md = inputs.with_corners(mesh, inputs.QUADRILATERAL)
+    prob = solver.build_problem(md, form="br2", eta=1.0)
+    sp_ = prob.space
+    from oracle import basis
+    from oracle.dg import DGSpace
+    pts, W = DGSpace.volume_quadrature(sp_, 0, 12)
+    W = W * np.linalg.det(sp_.map.jacobian(pts))
+    v, _ = sp_.eval(0, pts)
+    M = v.T @ (W[:, None] * v)
+    Minv = np.linalg.inv(M)
+    # A with eta = 1 minus A with eta = 0 is the lifting energy alone
+    A0 = solver.build_problem(md, form="br2", eta=0.0).A.toarray()
+    E = prob.A.toarray() - A0
+    Bf = np.zeros((sp_.n, sp_.n))
+    for f in prob.topo.subfaces:
+        q = int(prob.topo.p[0]) + 2
+        fp, fw, _ = sp_.face_quadrature(f, q)
+        vf, _ = sp_.eval(0, fp)
+        bb = (vf.T * fw) @ vf
+        Bf += bb.T @ Minv @ bb
+    assert np.abs(E - Bf).max() <= 1e-10 * np.abs(Bf).max()
