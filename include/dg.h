@@ -71,9 +71,10 @@ typedef struct dg_precond dg_precond;
  * the corners form one, general convex quadrilaterals otherwise; straight
  * sub-faces, the same hanging structure).  Integrals on such elements use
  * p+2 Gauss points per direction on the volume and max(p-, p+)+2 on a
- * sub-face, the SIPG penalty takes h_kappa = sqrt(area of kappa), and the LOR
- * blocks are the Q1 stiffness on the mapped Gauss-Lobatto cells.  SIPG only:
- * corners with DG_FORM_BR2 are DG_EUNSUPPORTED, as are corners in a batch.
+ * sub-face, the SIPG penalty takes h_kappa = sqrt(area of kappa), the BR2
+ * liftings the element's own (mapped) mass matrix, and the LOR blocks are the
+ * Q1 stiffness on the mapped Gauss-Lobatto cells.  Corners (or a map) in a
+ * batch are DG_EUNSUPPORTED.
  * Corners that do not bound a convex, counter-clockwise quadrilateral (det
  * of the map's Jacobian not positive at a corner) are DG_EINVAL.
  * map, map_ctx: NULL (the boxes, or the corners' bilinear map), or, squares

@@ -201,6 +201,8 @@ struct ApplyArgs {
   const double* gvol;
   const int64_t* goff;
   const double* gface;
+  const double* gbr2;         // BR2: mass-inverse side blocks, per element from g2off[k]
+  const int64_t* g2off;
   MapOff moff[kMaxP + 1];
 };
 

@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(kThreads) apply_kernel(const ApplyArgs A) {
 }
 
 // Persistent operator kernel of mapped squares (same scheduling as on boxes).
+template <bool BR2>
 __global__ void __launch_bounds__(kThreads) apply_map_kernel(const ApplyArgs A) {
   pdl_entry();
   extern __shared__ __align__(16) double smem[];
@@ -110,14 +111,14 @@ __global__ void __launch_bounds__(kThreads) apply_map_kernel(const ApplyArgs A) 
     if (t >= A.n_tiles) break;
     const ApplyTile T = A.tiles[t];
     switch (T.p) {
-      case 1: apply_map_tile<1>(A, T, t, smem, red); break;
-      case 2: apply_map_tile<2>(A, T, t, smem, red); break;
-      case 3: apply_map_tile<3>(A, T, t, smem, red); break;
-      case 4: apply_map_tile<4>(A, T, t, smem, red); break;
-      case 5: apply_map_tile<5>(A, T, t, smem, red); break;
-      case 6: apply_map_tile<6>(A, T, t, smem, red); break;
-      case 7: apply_map_tile<7>(A, T, t, smem, red); break;
-      case 8: apply_map_tile<8>(A, T, t, smem, red); break;
+      case 1: apply_map_tile<1, BR2>(A, T, t, smem, red); break;
+      case 2: apply_map_tile<2, BR2>(A, T, t, smem, red); break;
+      case 3: apply_map_tile<3, BR2>(A, T, t, smem, red); break;
+      case 4: apply_map_tile<4, BR2>(A, T, t, smem, red); break;
+      case 5: apply_map_tile<5, BR2>(A, T, t, smem, red); break;
+      case 6: apply_map_tile<6, BR2>(A, T, t, smem, red); break;
+      case 7: apply_map_tile<7, BR2>(A, T, t, smem, red); break;
+      case 8: apply_map_tile<8, BR2>(A, T, t, smem, red); break;
       default: break;
     }
     __syncthreads();
@@ -200,12 +201,13 @@ static int map_shape_smem(int p) {
 
 int64_t apply_smem_for(const dg_mesh& M) {
   if (M.host.dim == 3) return M.apply3_smem;
-  if (M.host.mapped) {   // the tile's layout plus 3 weights per (item, Gauss point)
+  if (M.host.mapped) {   // the tile's layout plus the item weights (and BR2's lifting vectors)
+    const int per_item = kMapItemDoubles + (M.opts.form == DG_FORM_BR2 ? kMapItemBr2 : 0);
     int64_t mx = 0;
     for (int t = 0; t < M.n_tiles; ++t) {
       const ApplyTile& T = M.h_tiles[t];
       const int64_t nit = M.h_item_ptr[t + 1] - M.h_item_ptr[t];
-      mx = std::max<int64_t>(mx, map_shape_smem(T.p) + 3 * kMapQMax * nit);
+      mx = std::max<int64_t>(mx, map_shape_smem(T.p) + per_item * nit);
     }
     return 8 * mx;
   }
@@ -254,6 +256,8 @@ ApplyArgs make_apply_args(const dg_mesh& M, const double* x, double* y, Reduce r
   A.gvol = M.d_gvol;
   A.goff = M.d_goff;
   A.gface = M.d_gface;
+  A.gbr2 = M.d_gbr2;
+  A.g2off = M.d_g2off;
   for (int p = 0; p <= kMaxP; ++p) A.moff[p] = M.moff[p];
   return A;
 }
@@ -281,8 +285,10 @@ int apply_kernel_setup(const dg_mesh& M) {
   const int smem = (int)M.apply_smem;
   DG_REQUIRE(smem <= optin, "operator tile needs too much shared memory");
   if (M.host.mapped) {
-    DG_CUDA(cudaFuncSetAttribute(apply_map_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, apply_map_kernel, kThreads, smem));
+    DG_CUDA(cudaFuncSetAttribute(apply_map_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    DG_CUDA(cudaFuncSetAttribute(apply_map_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    if (br2) DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, apply_map_kernel<true>, kThreads, smem));
+    else DG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, apply_map_kernel<false>, kThreads, smem));
     return sms * (per > 0 ? per : 1);
   }
   DG_CUDA(cudaFuncSetAttribute(apply_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
@@ -319,7 +325,10 @@ void launch_apply(const dg_mesh& M, const double* x, double* y, Reduce red, cuda
   }
   const int smem = (int)M.apply_smem;
   if (with_trace) launch_k(trace_kernel, M.n_tiles, kThreads, 0, s, A);
-  if (M.host.mapped) launch_k(apply_map_kernel, grid, kThreads, smem, s, A);
+  if (M.host.mapped) {
+    if (M.opts.form == DG_FORM_BR2) launch_k(apply_map_kernel<true>, grid, kThreads, smem, s, A);
+    else launch_k(apply_map_kernel<false>, grid, kThreads, smem, s, A);
+  }
   else if (M.opts.form == DG_FORM_BR2) launch_k(apply_kernel<true>, grid, kThreads, smem, s, A);
   else launch_k(apply_kernel<false>, grid, kThreads, smem, s, A);
   DG_CUDA(cudaGetLastError());

@@ -1,5 +1,6 @@
-// Matrix-free SIPG operator y = A x on mapped squares (Section 2: element maps
-// T_kappa onto general quadrilaterals; Eq. fe-problem), FP64.
+// Matrix-free SIPG / BR2 operator y = A x on mapped squares (Section 2:
+// element maps T_kappa onto general quadrilaterals; Eq. fe-problem; BR2 of
+// Section 4.4), FP64.
 //
 // The elements are the images of the leaf boxes under the bilinear map of the
 // lattice domain (DomainMap), so the geometric factors vary inside every
@@ -22,6 +23,12 @@
 //           side node then sums them over its sub-faces in sub-face order
 //           (deterministic) with the side's basis tables, and the gather adds
 //           the normal-derivative weights through l_k'(0 or 1) / h as on boxes.
+//   BR2     the mass matrix of a mapped element is not a Kronecker product, so
+//           the lifting takes the block of each element's mass inverse on a
+//           side's nodes (stored at setup): per item the jump projected onto
+//           both sides' nodes, the two blocks applied, and the lifted values
+//           at the item's points added to the value weights (three more
+//           passes of the tile's items).
 // Every sub-face is evaluated from both of its sides (no atomics): applies are
 // bit-reproducible.
 #pragma once
@@ -40,11 +47,14 @@ struct MapShape {
   // shared doubles: B, D (2 Q NP), x (EPB NN), stage 1 / 3 (2 EPB NP Q),
   // point fluxes (2 EPB QQ), side sums r, c2 (8 EPB NP)
   static constexpr int SMEM = 2 * Q * NP + EPB * NN + 2 * EPB * NP * Q + 2 * EPB * QQ + 8 * EPB * NP;
-  // then the sub-face item weights: [item][kMapQMax][3]
+  // then the sub-face item weights: [item][kMapQMax][3]; BR2 adds per item
+  // the weighted jumps at its points and both sides' lifting vectors
   static constexpr int PART = SMEM;
 };
+constexpr int kMapItemDoubles = 3 * kMapQMax;
+constexpr int kMapItemBr2 = kMapQMax + 4 * kMaxN;   // w [[u]] per point; j-, j+, z-, z+
 
-template <int P>
+template <int P, bool BR2>
 __device__ __forceinline__ void apply_map_tile(const ApplyArgs& A, const ApplyTile& T, int tile, double* sm,
                                                double* red) {
   using S = MapShape<P>;
@@ -89,6 +99,7 @@ __device__ __forceinline__ void apply_map_tile(const ApplyArgs& A, const ApplyTi
   // ---- faces, pass 1: one thread per (sub-face item, Gauss point)
   const int ib = A.item_ptr[tile];
   const int nit = A.item_ptr[tile + 1] - ib;
+  double* br2 = part + kMapItemDoubles * nit;   // BR2: [item][kMapItemBr2]
   for (int t = tid; t < nit * kMapQMax; t += blockDim.x) {
     const int it = t / kMapQMax, g = t - it * kMapQMax;
     const int2 item = A.items[ib + it];
@@ -140,11 +151,83 @@ __device__ __forceinline__ void apply_map_tile(const ApplyArgs& A, const ApplyTi
       cc = 1.0;
     }
     double* pp = part + ((item.y >> 16) * kMapQMax + g) * 3;
-    pp[0] = fma(fm.sigma * jmp, w, -flux);   // weight of v-
+    if (BR2) {
+      pp[0] = -flux;                                    // the lifting term is added below
+      br2[(item.y >> 16) * kMapItemBr2 + g] = w * jmp;
+    } else {
+      pp[0] = fma(fm.sigma * jmp, w, -flux);   // weight of v-
+    }
     pp[1] = -cc * jmp * wmt;                 // of d v- / d t (times a / h and l' at the side sums)
     pp[2] = -cc * jmp * wmn;                 // of a times the outward normal derivative of v-
   }
   __syncthreads();
+  if (BR2) {
+    // BR2 liftings (Section 4.4) of every sub-face on both of its sides:
+    // j = int phi_j [[u]] ds on each side's nodes, z = (block of that
+    // element's mass inverse on the side) j, and at every point the weight
+    // eta coef a w (z-(x_g) + z+(x_g)) of the own test function's value.
+    // One thread per (item, side node) for j and z, per (item, point) after.
+    for (int t = tid; t < nit * kMaxN; t += blockDim.x) {
+      const int it = t / kMaxN, j = t - it * kMaxN;
+      const int2 item = A.items[ib + it];
+      const SubFaceMap fm = A.sfm[item.x];
+      const SubFaceRec f = A.sf[item.x];
+      double* b = br2 + (item.y >> 16) * kMapItemBr2;
+      if (j < NP) {
+        double a = 0.0;
+        for (int g = 0; g < fm.qf; ++g) a = fma(__ldg(A.tab + fm.tab_bo + g * NP + j), b[g], a);
+        b[kMapQMax + j] = a;
+      }
+      if (f.nb >= 0 && j <= f.pn) {
+        const int npn = f.pn + 1;
+        double a = 0.0;
+        for (int g = 0; g < fm.qf; ++g) a = fma(__ldg(A.tab + fm.tab_bn + g * npn + j), b[g], a);
+        b[kMapQMax + kMaxN + j] = a;
+      }
+    }
+    __syncthreads();
+    for (int t = tid; t < nit * kMaxN; t += blockDim.x) {
+      const int it = t / kMaxN, j = t - it * kMaxN;
+      const int2 item = A.items[ib + it];
+      const SubFaceRec f = A.sf[item.x];
+      const int e = (item.y & 0xffff) >> 2, s = item.y & 3;
+      double* b = br2 + (item.y >> 16) * kMapItemBr2;
+      if (j < NP) {
+        const int k = A.order[T.first + e];
+        const double* Go = A.gbr2 + A.g2off[k] + s * NP * NP + j * NP;
+        double z = 0.0;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) z = fma(__ldg(Go + i), b[kMapQMax + i], z);
+        b[kMapQMax + 2 * kMaxN + j] = z;
+      }
+      if (f.nb >= 0 && j <= f.pn) {
+        const int npn = f.pn + 1;
+        const double* Gn = A.gbr2 + A.g2off[f.nb] + f.nb_side * npn * npn + j * npn;
+        double z = 0.0;
+        for (int i = 0; i < npn; ++i) z = fma(__ldg(Gn + i), b[kMapQMax + kMaxN + i], z);
+        b[kMapQMax + 3 * kMaxN + j] = z;
+      }
+    }
+    __syncthreads();
+    for (int t = tid; t < nit * kMapQMax; t += blockDim.x) {
+      const int it = t / kMapQMax, g = t - it * kMapQMax;
+      const int2 item = A.items[ib + it];
+      const SubFaceMap fm = A.sfm[item.x];
+      if (g >= fm.qf) continue;
+      const SubFaceRec f = A.sf[item.x];
+      const double* b = br2 + (item.y >> 16) * kMapItemBr2;
+      double v = 0.0;
+#pragma unroll
+      for (int i = 0; i < NP; ++i) v = fma(__ldg(A.tab + fm.tab_bo + g * NP + i), b[kMapQMax + 2 * kMaxN + i], v);
+      if (f.nb >= 0) {
+        const int npn = f.pn + 1;
+        for (int i = 0; i < npn; ++i)
+          v = fma(__ldg(A.tab + fm.tab_bn + g * npn + i), b[kMapQMax + 3 * kMaxN + i], v);
+      }
+      part[((item.y >> 16) * kMapQMax + g) * 3] += fm.cbr2 * __ldg(A.gface + fm.geo + g) * v;
+    }
+    __syncthreads();
+  }
   // ---- volume stage 2 and the flux at every Gauss point
   for (int t = tid; t < count * QQ; t += blockDim.x) {
     const int e = t / QQ, rem = t - e * QQ;

@@ -88,6 +88,10 @@ void upload_mesh(dg_mesh* M, cudaStream_t s) {
     M->d_gvol = a.upload(M->h_gvol, s);
     M->d_goff = a.upload(M->h_goff, s);
     M->d_gface = a.upload(M->h_gface, s);
+    if (!M->h_gbr2.empty()) {
+      M->d_gbr2 = a.upload(M->h_gbr2, s);
+      M->d_g2off = a.upload(M->h_g2off, s);
+    }
   }
   M->d_tables = a.upload(M->h_tables, s);
   M->d_sched = a.alloc<unsigned>(2);

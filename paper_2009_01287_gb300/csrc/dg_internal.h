@@ -173,6 +173,8 @@ struct SubFaceMap {
                     // w = w_g |J t| dt, then w m_t, then w m_n s (m = J^-1 n in the
                     // pre-image axes, s = +1 / -1 for an upper / lower side)
   double sigma;     // SIPG penalty with h_kappa = sqrt(area of kappa)
+  double cbr2;      // BR2: eta coef a (coef 1/4 inside, 1 on the boundary; a the
+                    // larger coefficient of the two sides), 0 for SIPG
 };
 
 // Offsets of the degree-p volume tables of mapped meshes: the (p+2)-point

@@ -123,6 +123,11 @@ struct dg_mesh {
   dg::DomainMap dmap{};
   std::vector<double> h_gvol, h_gface;
   std::vector<int64_t> h_goff;
+  // BR2 on mapped squares: per element side the block of the element's mass
+  // inverse on that side's nodes ((p+1)^2 row-major, four per element, from
+  // h_g2off[k])
+  std::vector<double> h_gbr2;
+  std::vector<int64_t> h_g2off;
   // host only: per element the images of its (p+1)^2 Gauss-Lobatto nodes (the
   // LOR cells' vertices) and, at the (p+3)^2 points of the load-vector rule,
   // the image and det J (x, y, det per point; offsets h_roff), so that no
@@ -166,6 +171,8 @@ struct dg_mesh {
   double* d_gvol = nullptr;          // mapped squares: geometric factors (h_gvol, h_goff, h_gface)
   int64_t* d_goff = nullptr;
   double* d_gface = nullptr;
+  double* d_gbr2 = nullptr;          // mapped squares, BR2 (h_gbr2, h_g2off)
+  int64_t* d_g2off = nullptr;
   double* d_tables = nullptr;
   int32_t* d_order = nullptr;
   dg::ApplyTile* d_tiles = nullptr;

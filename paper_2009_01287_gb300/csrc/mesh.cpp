@@ -288,7 +288,6 @@ void build_mesh_host(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opt
   validate_and_copy(desc, m);
   if (desc->corners || desc->map) {
     DG_REQUIRE(!(desc->corners && desc->map), "give corners or a map, not both");
-    if (o.form != DG_FORM_SIPG) throw Error(DG_EUNSUPPORTED, "mapped elements: SIPG only");
     if (desc->corners)
       for (int i = 0; i < 8; ++i) {
         DG_REQUIRE(std::isfinite(desc->corners[i]), "corners must be finite");

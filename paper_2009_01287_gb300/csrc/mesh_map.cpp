@@ -155,7 +155,10 @@ void build_mesh_map(dg_mesh* M, const dg_mesh_desc* desc) {
     M->h_goff[k + 1] = M->h_goff[k] + 3 * q * q;
   }
   M->h_gvol.assign(M->h_goff[m.n], 0.0);
-  std::vector<double> hpen(m.n), X, x, J;
+  const bool br2 = M->opts.form == DG_FORM_BR2;
+  M->h_gbr2.clear();
+  M->h_g2off.assign(br2 ? m.n + 1 : 0, 0);
+  std::vector<double> hpen(m.n), X, x, J, Mk;
   for (int64_t k = 0; k < m.n; ++k) {
     const int P = m.p[k], Q = P + 1 + kMapQExtra, QQ = Q * Q;
     const double* gx = T.data() + M->moff[P].gx;
@@ -184,6 +187,32 @@ void build_mesh_map(dg_mesh* M, const dg_mesh_desc* desc) {
         area += gw[gxi] * gw[gy] * det * h * h;
       }
     hpen[k] = std::sqrt(area);
+    if (br2) {
+      // the element's mass matrix by the same rule, its inverse, and the
+      // inverse's block on each side's nodes (the BR2 lifting, Section 4.4)
+      const int NP = P + 1, NN = NP * NP;
+      const double* Bq = T.data() + M->moff[P].B;
+      Mk.assign((size_t)NN * NN, 0.0);
+      for (int gy = 0; gy < Q; ++gy)
+        for (int gxi = 0; gxi < Q; ++gxi) {
+          const double* j = &J[4 * (gy * Q + gxi)];
+          const double W = gw[gxi] * gw[gy] * (j[0] * j[3] - j[1] * j[2]) * h * h;
+          for (int a = 0; a < NN; ++a) {
+            const double va = W * Bq[gxi * NP + a % NP] * Bq[gy * NP + a / NP];
+            for (int b = 0; b < NN; ++b) Mk[(size_t)a * NN + b] += va * Bq[gxi * NP + b % NP] * Bq[gy * NP + b / NP];
+          }
+        }
+      dense_inverse_spd(NN, Mk);
+      for (int sd = 0; sd < 4; ++sd) {
+        auto node = [&](int i) {
+          const int e = (sd & 1) ? P : 0;
+          return sd < 2 ? i * NP + e : e * NP + i;
+        };
+        for (int i = 0; i < NP; ++i)
+          for (int i2 = 0; i2 < NP; ++i2) M->h_gbr2.push_back(Mk[(size_t)node(i) * NN + node(i2)]);
+      }
+      M->h_g2off[k + 1] = (int64_t)M->h_gbr2.size();
+    }
   }
   M->h_sfm.assign(m.sf.size(), SubFaceMap{});
   M->h_gface.clear();
@@ -217,6 +246,7 @@ void build_mesh_map(dg_mesh* M, const dg_mesh_desc* desc) {
         }
         const double pp = (o.penalty_form == DG_PENALTY_P1SQ) ? (pe + 1.0) : (double)pe;
         r.sigma = ae * (M->eta * pp * pp / he);
+        r.cbr2 = br2 ? ae * M->eta * (f.nb >= 0 ? 0.25 : 1.0) : 0.0;
         // face factors at the rule's points: arc length |J t| dt, the physical
         // normal n = J^-T nu / |J^-T nu| (nu = so e_n), m = J^-1 n
         const int rg = append_rule(T, qf, rules);
@@ -312,10 +342,12 @@ void map_stats(dg_mesh* M) {
       // per point: three own and three neighbour sums and the weights; per
       // side node and point: three sums
       fl += qf * (2.0 * 3.0 * (n1 + nn) + 16.0) + 2.0 * 3.0 * n1 * qf;
+      // BR2: both sides' projections, side-block products and values at the points
+      if (M->opts.form == DG_FORM_BR2) fl += 2.0 * (2.0 * qf * (n1 + nn) + n1 * n1 + nn * nn) + 4.0 * qf;
     }
   }
   S.apply_flops = fl;
-  S.apply_bytes += 8.0 * (double)(M->h_gvol.size() + M->h_gface.size() + m.n) +
+  S.apply_bytes += 8.0 * (double)(M->h_gvol.size() + M->h_gface.size() + M->h_gbr2.size() + m.n) +
                    (double)m.sf.size() * sizeof(SubFaceMap);
 }
 
@@ -407,6 +439,8 @@ void host_element_residual_map(const dg_mesh& M, int64_t k, const double* x, dou
         ihn = 1.0 / (m.size[f.nb] * m.lh);
         an = m.coef[f.nb];
       }
+      const bool br2 = M.opts.form == DG_FORM_BR2;
+      double rho1v[kMapQMax], wj[kMapQMax];
       for (int q = 0; q < qf; ++q) {
         const double* Bo = T + g.tab_bo + (size_t)q * NP;
         const double* Do = T + g.tab_bo + (size_t)(qf + q) * NP;
@@ -439,14 +473,41 @@ void host_element_residual_map(const dg_mesh& M, int64_t k, const double* x, dou
           flux = Fo;
           cc = 1.0;
         }
-        const double rho1 = g.sigma * jmp * w - flux;
         const double rho2 = -cc * jmp * wmt;
         const double rho3 = -cc * jmp * wmn;
+        rho1v[q] = br2 ? -flux : g.sigma * jmp * w - flux;
+        wj[q] = w * jmp;
         for (int i = 0; i < NP; ++i) {
-          r[s * NP + i] += Bo[i] * rho1 + aih * Do[i] * rho2;
+          r[s * NP + i] += aih * Do[i] * rho2;
           c2[s * NP + i] += Bo[i] * rho3;
         }
       }
+      if (br2) {
+        // liftings on both sides: j = int phi_j [[u]] ds on each side's nodes,
+        // z = (mass-inverse side block) j, and at every point the weight
+        // eta coef a w (z-(x_g) + z+(x_g)) of the own test function's value
+        double jo[kMaxN] = {0.0}, jn[kMaxN] = {0.0}, zo[kMaxN] = {0.0}, zn[kMaxN] = {0.0};
+        for (int q = 0; q < qf; ++q)
+          for (int i = 0; i < NP; ++i) jo[i] += T[g.tab_bo + (size_t)q * NP + i] * wj[q];
+        const double* Go = M.h_gbr2.data() + M.h_g2off[k] + (size_t)s * NP * NP;
+        for (int i = 0; i < NP; ++i)
+          for (int i2 = 0; i2 < NP; ++i2) zo[i] += Go[i * NP + i2] * jo[i2];
+        if (f.nb >= 0) {
+          for (int q = 0; q < qf; ++q)
+            for (int i = 0; i < npn; ++i) jn[i] += T[g.tab_bn + (size_t)q * npn + i] * wj[q];
+          const double* Gn = M.h_gbr2.data() + M.h_g2off[f.nb] + (size_t)f.nb_side * npn * npn;
+          for (int i = 0; i < npn; ++i)
+            for (int i2 = 0; i2 < npn; ++i2) zn[i] += Gn[i * npn + i2] * jn[i2];
+        }
+        for (int q = 0; q < qf; ++q) {
+          double v = 0.0;
+          for (int i = 0; i < NP; ++i) v += T[g.tab_bo + (size_t)q * NP + i] * zo[i];
+          for (int i = 0; i < npn; ++i) v += T[g.tab_bn + (size_t)q * npn + i] * zn[i];
+          rho1v[q] += g.cbr2 * W[q] * v;
+        }
+      }
+      for (int q = 0; q < qf; ++q)
+        for (int i = 0; i < NP; ++i) r[s * NP + i] += T[g.tab_bo + (size_t)q * NP + i] * rho1v[q];
     }
   }
   const Basis1D& B = basis1d(P);

@@ -53,12 +53,17 @@ def dev(torch, a):
     return torch.tensor(np.asarray(a), dtype=torch.float64, device="cuda")
 
 
+def _opts(B, form, **kw):
+    return B.make_options(form=B.DG_FORM_BR2 if form == "br2" else B.DG_FORM_SIPG, **kw)
+
+
+@pytest.mark.parametrize("form", ["sipg", "br2"])
 @pytest.mark.parametrize("name", list(MESHES))
-def test_apply_parity_mapped(built_lib, torch_mod, name):
+def test_apply_parity_mapped(built_lib, torch_mod, name, form):
     mesh = MESHES[name]()
-    prob = solver.build_problem(mesh)
+    prob = solver.build_problem(mesh, form=form)
     B = built_lib
-    M = B.Mesh(mesh)
+    M = B.Mesh(mesh, _opts(B, form))
     x = inputs.random_vector(M.n_dofs, 3)
     xd = dev(torch_mod, x)
     yd = torch_mod.empty_like(xd)
@@ -89,18 +94,20 @@ def test_precond_parity_fp64_mapped(built_lib, torch_mod, name, lor):
     assert rel(zd.cpu().numpy(), opc.apply(r)) <= 1e-12
 
 
-@pytest.mark.parametrize("name", ["par-hp", "quad-hp", "quad-ragged", "quad-coef", "wavy-hp", "wavy-coef-p8"])
-def test_pcg_iterations_match_oracle_mapped(built_lib, torch_mod, name):
+@pytest.mark.parametrize("name,form", [("par-hp", "sipg"), ("quad-hp", "sipg"), ("quad-ragged", "sipg"),
+                                       ("quad-coef", "sipg"), ("wavy-hp", "sipg"), ("wavy-coef-p8", "sipg"),
+                                       ("quad-hp", "br2"), ("quad-coef", "br2"), ("wavy-hp", "br2")])
+def test_pcg_iterations_match_oracle_mapped(built_lib, torch_mod, name, form):
     mesh = MESHES[name]()
-    prob = solver.build_problem(mesh)
+    prob = solver.build_problem(mesh, form=form)
     opc = solver.Preconditioner(prob, lor="amg")
     rh = inputs.sine_rhs(2, 0)
     b = rhs.load_vector(prob.space, rh.amps, rh.waves)
     tol = 1e-8
     ref = solver.pcg(prob.A, b, opc.apply, tol, 2000)
     B = built_lib
-    M = B.Mesh(mesh)
-    pc = B.Precond(M)
+    M = B.Mesh(mesh, _opts(B, form))
+    pc = B.Precond(M, _opts(B, form))
     bd = dev(torch_mod, b)
     # the library's own load vector of the same right-hand side
     bl = torch_mod.empty_like(bd)
@@ -112,7 +119,7 @@ def test_pcg_iterations_match_oracle_mapped(built_lib, torch_mod, name):
     assert abs(info.iters - ref.iters) <= 1
     assert rel(xd.cpu().numpy(), ref.x) <= 1e2 * tol
     # mixed precision: within +10% iterations, true FP64 residual at tolerance
-    pc32 = B.Precond(M, B.make_options(precision=B.DG_PREC_MIXED))
+    pc32 = B.Precond(M, _opts(B, form, precision=B.DG_PREC_MIXED))
     x32 = torch_mod.empty_like(bd)
     i32 = B.dg_pcg_solve(M.h, pc32.h, bd, x32, tol, 2000)
     assert i32.iters <= int(1.1 * info.iters) + 1
@@ -159,9 +166,6 @@ def test_full_size_mapped_sampled(built_lib, torch_mod, which):
 def test_mapped_unsupported_forms(built_lib, torch_mod):
     B = built_lib
     mesh = MESHES["par-hp"]()
-    with pytest.raises(B.DGError) as e:
-        B.Mesh(mesh, B.make_options(form=B.DG_FORM_BR2))
-    assert e.value.code == B.DG_EUNSUPPORTED
     with pytest.raises(B.DGError) as e:
         B.Batch([mesh], n_rhs=1)
     assert e.value.code == B.DG_EUNSUPPORTED

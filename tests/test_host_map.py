@@ -3,7 +3,7 @@ general quadrilaterals), run through the inspection library without a GPU,
 against the oracle's mapped space: the host mirror of the mapped operator
 kernel, the conforming prolongation, the V_J / V_e split, the Q1 LOR matrix on
 the mapped cells, the block inverses, the Jacobi diagonal and the AMG
-hierarchy; and the input checks of mapped meshes."""
+hierarchy, for SIPG and BR2; and the input checks of mapped meshes."""
 import numpy as np
 import pytest
 
@@ -30,11 +30,12 @@ CASES = [
 
 
 @pytest.mark.parametrize("name,mk", CASES, ids=[c[0] for c in CASES])
-def test_host_setup_matches_oracle_mapped(built_lib, name, mk):
+def test_host_setup_matches_oracle_mapped(built_lib, name, mk, form="sipg"):
     mesh = mk()
-    prob = solver.build_problem(mesh)
+    prob = solver.build_problem(mesh, form=form)
     B = built_lib
-    hs = B.HostSetup(mesh, B.make_options())
+    hs = B.HostSetup(mesh, B.make_options(form=B.DG_FORM_BR2 if form == "br2" else B.DG_FORM_SIPG))
+    assert abs(hs.eta - (dg_br2_eta(prob) if form == "br2" else 100.0)) < 1e-6
     x = inputs.random_vector(prob.space.n, 11)
     ya, yb = prob.A @ x, hs.apply(x)
     assert np.abs(ya - yb).max() <= 1e-12 * np.abs(ya).max()
@@ -53,6 +54,18 @@ def test_host_setup_matches_oracle_mapped(built_lib, name, mk):
     assert [L.n for L in pc.levels] == [l.shape[0] for l in hs.levels]
     for L, l in zip(pc.levels, hs.levels):
         assert abs(L.A - l).max() <= 1e-11 * abs(L.A).max()
+
+
+def dg_br2_eta(prob):
+    from oracle import dg
+    return dg.br2_eta(prob.topo)
+
+
+@pytest.mark.parametrize("name,mk", CASES[:3] + [
+    ("wavy-br2", lambda: inputs.with_mapping(inputs.small_hp_mesh(6, base=4, depth=3, prob=0.4, pmax=5),
+                                             inputs.WavyMap()))], ids=["par-hp", "quad-hp", "quad-p8", "wavy-br2"])
+def test_host_setup_matches_oracle_mapped_br2(built_lib, name, mk):
+    test_host_setup_matches_oracle_mapped(built_lib, name, mk, form="br2")
 
 
 def test_similarity_corners_give_the_box_operator(built_lib):
@@ -80,9 +93,6 @@ def test_mapped_input_checks(built_lib):
     # clockwise corners (a reflection) are rejected too
     with pytest.raises(B.DGError):
         B.HostSetup(inputs.with_corners(mesh, ((0, 0), (0, 1), (1, 0), (1, 1))), B.make_options())
-    with pytest.raises(B.DGError) as e:
-        B.HostSetup(inputs.with_corners(mesh, inputs.QUADRILATERAL), B.make_options(form=B.DG_FORM_BR2))
-    assert e.value.code == B.DG_EUNSUPPORTED
     with pytest.raises(B.DGError):
         B.HostSetup(inputs.with_corners(mesh, ((0, 0), (1, 0), (0, 1), (np.nan, 1))), B.make_options())
 
