@@ -87,7 +87,7 @@ TRAFFIC = {
                                       "paper_2009_01287_gb300/csrc/apply_launch.cu",
                                       "paper_2009_01287_gb300/csrc/dg_internal.h",
                                       "paper_2009_01287_gb300/csrc/mesh.cpp"],
-                          "sha256_16": "51e2042d8b854ddb", "bytes": 3550208},
+                          "sha256_16": "1d706091b138a282", "bytes": 3550208},
     "apply3_kernel/hp3d": {"sources": ["paper_2009_01287_gb300/csrc/apply_kernel.cuh",
                                        "paper_2009_01287_gb300/csrc/apply3_kernel.cuh",
                                        "paper_2009_01287_gb300/csrc/apply_launch.cu",
@@ -102,7 +102,7 @@ TRAFFIC = {
                                               "paper_2009_01287_gb300/csrc/apply_launch.cu",
                                               "paper_2009_01287_gb300/csrc/dg_internal.h",
                                               "paper_2009_01287_gb300/csrc/mesh_map.cpp"],
-                                  "sha256_16": "66b2520655a88353", "bytes": 10654720},
+                                  "sha256_16": "26d3dd4699954ae0", "bytes": 10816000},
 }
 
 
