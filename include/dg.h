@@ -298,6 +298,22 @@ dg_status dg_pcg_solve_noalloc(const dg_mesh* mesh, const dg_precond* pc, const 
 dg_status dg_rhs_sine(const dg_mesh* mesh, int n_modes, const double* amps,
                       const int32_t* waves, double* b, void* stream);
 
+/* Load vector of caller-supplied data (Section 2, Eq. fe-problem, right-hand
+ * side; the adaptive-refinement problems of Section 4.2 have inhomogeneous
+ * Dirichlet data): b_i = int f phi_i, plus, when g is given, the terms of the
+ * boundary condition u = g imposed weakly by SIPG,
+ *   sum over boundary sub-faces of int g (sigma phi_i - a grad phi_i . n) ds.
+ * f and g are host callbacks (dg_field_fn: n physical points x, n x 2
+ * row-major, into out, n values), called on the calling thread during the
+ * call; either may be NULL (no volume term / homogeneous data).  Quadrature:
+ * p+3 Gauss points per direction on the volume and on each boundary
+ * sub-face.  Square meshes; g needs an unmapped mesh and the SIPG form
+ * (otherwise DG_EUNSUPPORTED).  A non-finite value from a callback is
+ * DG_EINVAL.  b: device; host arithmetic, synchronous on `stream`. */
+typedef void (*dg_field_fn)(int64_t n, const double* x, double* out, void* ctx);
+dg_status dg_rhs_eval(const dg_mesh* mesh, dg_field_fn f, dg_field_fn g, void* ctx, double* b,
+                      void* stream);
+
 /* ---- Batched solver: many problems x several right-hand sides, one launch.
  * Each (problem k, right-hand side r) pair is an instance, numbered
  * k*n_rhs + r; the batch's vectors hold all instances one after another

@@ -45,3 +45,28 @@ def load_vector_fn(space: DGSpace, fn, extra: int = 3) -> np.ndarray:
         v, _ = space.eval(k, pts)
         b[space.dofs(k)] = v.T @ (W * fn(space.phys(pts)))
     return b
+
+
+def dirichlet_load(space: DGSpace, f_fn, g_fn, eta: float, penalty_form: str = "paper",
+                   extra: int = 3) -> np.ndarray:
+    """Load vector of -div(a grad u) = f with u = g on the boundary, imposed
+    weakly by SIPG (Section 2 with inhomogeneous data): b_i = int f phi_i +
+    sum over boundary sub-faces of int g (sigma phi_i - a grad phi_i . n).
+    The boundary terms come from replacing [[u]] by u - g on the boundary in
+    the consistency and penalty terms; with g = 0 this is load_vector_fn.
+    Quadrature: p+extra points per direction (volume), p+extra on each
+    boundary sub-face."""
+    from .dg import normal_derivative, penalty
+    b = load_vector_fn(space, f_fn, extra)
+    for f in space.topo.subfaces:
+        if f.kp >= 0:
+            continue
+        k = f.km
+        p = int(space.topo.p[k])
+        pts, W, n = space.face_quadrature(f, p + extra)
+        v, g = space.eval(k, pts)
+        gv = g_fn(space.phys(pts))
+        sig = penalty(space, f, eta, penalty_form)
+        dn = space.coef[k] * normal_derivative(g, n)
+        b[space.dofs(k)] += (v.T * W) @ (sig * gv) - (dn.T * W) @ gv
+    return b

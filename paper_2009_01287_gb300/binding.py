@@ -30,7 +30,7 @@ ABI_SYMBOLS = (
     "dg_mesh_create", "dg_mesh_destroy", "dg_num_dofs", "dg_mesh_stats_get", "dg_dof_layout", "dg_apply",
     "dg_precond_setup",
     "dg_precond_destroy", "dg_precond_stats_get", "dg_precond_apply", "dg_pcg_solve",
-    "dg_pcg_solve_host", "dg_pcg_solve_noalloc", "dg_rhs_sine", "dg_last_error",
+    "dg_pcg_solve_host", "dg_pcg_solve_noalloc", "dg_rhs_sine", "dg_rhs_eval", "dg_last_error",
     "dg_batch_create", "dg_batch_destroy", "dg_batch_num_dofs", "dg_batch_offsets", "dg_batch_rhs_sine",
     "dg_batch_solve", "dg_batch_stats_get", "dg_precond_profile", "dg_apply_profile", "dg_fp64_fma_probe",
 )
@@ -47,6 +47,25 @@ class DgMeshDesc(C.Structure):
                 ("extent", C.POINTER(C.c_int32)), ("lattice_h", C.c_double),
                 ("coeff", C.POINTER(C.c_double)), ("corners", C.POINTER(C.c_double)),
                 ("map", DgMapFn), ("map_ctx", C.c_void_p)]
+
+
+# dg_field_fn: (n, x, out, ctx) - values of a field at n physical points
+DgFieldFn = C.CFUNCTYPE(None, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p)
+
+
+def _field_callback(fn):
+    """A dg_field_fn evaluating fn(x) (x: (n, 2)) -> (n,); None -> NULL.  On an
+    exception the outputs are set to NaN, which the library reports."""
+    if fn is None:
+        return DgFieldFn()
+
+    def cb(n, x, out, ctx):
+        o = np.ctypeslib.as_array(out, shape=(n,))
+        try:
+            o[:] = fn(np.ctypeslib.as_array(x, shape=(n, 2)))
+        except Exception:   # noqa: BLE001 - reported through the NaN outputs
+            o[:] = np.nan
+    return DgFieldFn(cb)
 
 
 def _map_callback(mapping):
@@ -133,6 +152,7 @@ def lib():
         L.dg_pcg_solve_host.argtypes = [vp, vp, dp, dp, C.c_double, C.c_int, C.POINTER(DgSolveInfo), vp]
         L.dg_pcg_solve_noalloc.argtypes = [vp, vp, dp, dp, C.c_double, C.c_int, C.POINTER(DgSolveInfo), vp]
         L.dg_rhs_sine.argtypes = [vp, C.c_int, dp, dp, dp, vp]
+        L.dg_rhs_eval.argtypes = [vp, DgFieldFn, DgFieldFn, vp, dp, vp]
         L.dg_last_error.restype = C.c_char_p
         L.dg_batch_create.argtypes = [C.POINTER(DgMeshDesc), C.c_int, C.c_int, C.POINTER(DgOptions), vp,
                                       C.POINTER(vp)]
@@ -315,6 +335,13 @@ def dg_pcg_solve_noalloc(mesh_h: int, pc_h: int, b, x, rtol: float, maxit: int, 
     return info
 
 
+def dg_rhs_eval(mesh_h: int, f, g, b, stream=None) -> None:
+    """b = load vector of f (volume) and weakly imposed boundary data g (SIPG);
+    f, g: Python functions of the (n, 2) physical points, or None."""
+    cf, cg = _field_callback(f), _field_callback(g)
+    _check(lib().dg_rhs_eval(mesh_h, cf, cg, None, _ptr(b), _stream(stream)))
+
+
 def dg_rhs_sine(mesh_h: int, amps, waves, b, stream=None) -> None:
     a = np.ascontiguousarray(amps, dtype=np.float64)
     w = np.ascontiguousarray(waves, dtype=np.int32)
@@ -421,6 +448,8 @@ def inspect_lib():
         L.dginspect_create.argtypes = [C.POINTER(DgMeshDesc), C.POINTER(DgOptions), C.c_int]
         L.dginspect_create.restype = vp
         L.dginspect_last_status.restype = C.c_int
+        L.dginspect_rhs_eval.argtypes = [vp, DgFieldFn, DgFieldFn, vp, C.c_void_p]
+        L.dginspect_rhs_eval.restype = C.c_int
         L.dginspect_destroy.argtypes = [vp]
         L.dginspect_last_error.restype = C.c_char_p
         for n in ("dginspect_sizes", "dginspect_kind", "dginspect_dinv"):
@@ -531,6 +560,14 @@ class HostSetup:
         y = np.zeros(self.n)
         inspect_lib().dginspect_apply(self.h, x.ctypes.data, y.ctypes.data)
         return y
+
+    def rhs_eval(self, f, g) -> np.ndarray:
+        """The library's load vector of f and boundary data g (host_load)."""
+        L = inspect_lib()
+        b = np.zeros(self.n)
+        if L.dginspect_rhs_eval(self.h, _field_callback(f), _field_callback(g), None, b.ctypes.data) != 0:
+            raise DGError(DG_EINVAL, L.dginspect_last_error().decode())
+        return b
 
     def face_items(self):
         """The operator's tiles and sub-face items as the kernels read them:

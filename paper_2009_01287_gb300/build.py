@@ -18,7 +18,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libdgsc.so")
 INSPECT_LIB = os.path.join(OUT_DIR, "libdgsc_inspect.so")
 # host-only translation units that also make up the inspection library
-HOST_ONLY = ("basis.cpp", "mesh.cpp", "mesh3.cpp", "mesh_map.cpp", "sparse.cpp", "host_operator.cpp",
+HOST_ONLY = ("basis.cpp", "mesh.cpp", "mesh3.cpp", "mesh_map.cpp", "load.cpp", "sparse.cpp", "host_operator.cpp",
              "precond_setup.cpp", "work_units.cpp",
              "precond3.cpp")
 INSPECT_ONLY = ("inspect.cpp",)

@@ -605,6 +605,17 @@ dg_status dg_pcg_solve_host(const dg_mesh* mesh, const dg_precond* pc, const dou
   });
 }
 
+dg_status dg_rhs_eval(const dg_mesh* mesh, dg_field_fn f, dg_field_fn g, void* ctx, double* b, void* stream) {
+  return guarded([&] {
+    DG_REQUIRE(mesh && b, "bad argument");
+    std::vector<double> hb(mesh->n_dofs, 0.0);
+    host_load(*mesh, f, g, ctx, hb.data());
+    DG_CUDA(cudaMemcpyAsync(b, hb.data(), hb.size() * sizeof(double), cudaMemcpyHostToDevice,
+                            (cudaStream_t)stream));
+    DG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  });
+}
+
 dg_status dg_rhs_sine(const dg_mesh* mesh, int n_modes, const double* amps, const int32_t* waves,
                       double* b, void* stream) {
   return guarded([&] {

@@ -268,6 +268,9 @@ void host_lor_block_map(const dg_mesh& M, int64_t k, double* A);
 // rows of element k of y = A x (x: full host vector), same formulation as the kernel
 void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double* y);
 void host_element_residual3(const dg_mesh& M, int64_t k, const double* x, double* y);
+// load vector of caller-supplied f (volume) and boundary data g (SIPG, weak)
+// into hb (n_dofs doubles); either may be null
+void host_load(const dg_mesh& M, dg_field_fn f, dg_field_fn g, void* ctx, double* hb);
 // load vector of the sine right-hand side into hb (n_dofs doubles, zeroed)
 void host_rhs_sine(const dg_mesh& mesh, int n_modes, const double* amps, const int32_t* waves,
                    double* hb);

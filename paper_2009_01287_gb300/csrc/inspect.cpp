@@ -203,6 +203,18 @@ void dginspect_level_A(void* h, int l, int64_t* ptr, int32_t* idx, double* val) 
   copy_csr(((Inspect*)h)->amg.levels[l].A, ptr, idx, val);
 }
 
+// the load vector of caller-supplied f and boundary data g (host_load) into
+// b (n_dofs doubles); 0, or -1 with the message in dginspect_last_error
+int dginspect_rhs_eval(void* h, dg_field_fn f, dg_field_fn g, void* ctx, double* b) {
+  try {
+    host_load(((Inspect*)h)->mesh, f, g, ctx, b);
+    return 0;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return -1;
+  }
+}
+
 // y = A x with the host mirror of the operator kernel
 void dginspect_apply(void* h, const double* x, double* y) {
   Inspect* I = (Inspect*)h;

@@ -150,3 +150,28 @@ def test_curved_input_checks(built_lib):
     both = inputs.with_mapping(inputs.with_corners(mesh, inputs.QUADRILATERAL), inputs.WavyMap())
     with pytest.raises(B.DGError):
         B.HostSetup(both, B.make_options())
+
+
+# ---------------------------------------------------------------- load vectors from callbacks
+def test_host_load_matches_oracle(built_lib):
+    """The library's load vector of caller-supplied f and weakly imposed
+    Dirichlet data g (host_load) against the oracle's dirichlet_load, on a
+    hanging hp mesh with a coefficient; f alone on a curved mesh."""
+    from oracle import rhs as R
+    B = built_lib
+    f = lambda x: np.sin(3 * x[:, 0]) * np.exp(x[:, 1])
+    g = lambda x: np.arctan(20.0 * (np.hypot(x[:, 0] + 0.05, x[:, 1] + 0.05) - 0.7))
+    mesh = _coef(inputs.small_hp_mesh(4, base=4, depth=3, prob=0.4, pmax=6), 4)
+    prob = solver.build_problem(mesh)
+    hs = B.HostSetup(mesh, B.make_options(), amg=False)
+    ref = R.dirichlet_load(prob.space, f, g, 100.0)
+    assert np.abs(hs.rhs_eval(f, g) - ref).max() <= 1e-12 * np.abs(ref).max()
+    md = inputs.with_mapping(inputs.small_hp_mesh(5, base=3, depth=2, prob=0.5, pmax=5), inputs.WavyMap())
+    prob = solver.build_problem(md)
+    hs = B.HostSetup(md, B.make_options(), amg=False)
+    ref = R.load_vector_fn(prob.space, f)
+    assert np.abs(hs.rhs_eval(f, None) - ref).max() <= 1e-12 * np.abs(ref).max()
+    with pytest.raises(B.DGError):
+        hs.rhs_eval(f, g)   # boundary data on a mapped mesh
+    with pytest.raises(B.DGError):
+        hs.rhs_eval(lambda x: x[:, 5], None)   # a failing callback
