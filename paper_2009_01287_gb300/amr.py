@@ -1,0 +1,227 @@
+"""hp-adaptive refinement driver (Section 4.2: adaptively refined meshes and
+spaces), for the internal-layer problem of that section: -Laplace(u) = f on
+the unit square with u = g on the boundary, the exact solution
+u = atan(alpha (r - r0)), r the distance from (-0.05, -0.05), alpha = 200,
+r0 = 0.7 (the paper writes Laplace(u) = f; the sign of f is flipped here as
+everywhere in this library).
+
+Each step solves on the current mesh through the C ABI (dg_mesh_create,
+dg_precond_setup, dg_rhs_eval with the boundary data, dg_pcg_solve), records
+the PCG iterations of B = B_B + B_C and of B~ = J_B + B_C with the V_e
+statistics (the columns of the paper's AMR tables), then marks and refines.
+The paper names neither its error estimator nor its hp decision; this driver
+takes (readings, stated here and in the design notes):
+  - indicator: eta_k = h_k max over the element's nodes of |u - u_h| (the
+    exact solution is known for this benchmark problem);
+  - marking: the smallest set of elements, largest eta first (ties by element
+    number), whose eta^2 sum reaches THETA of the total (bulk marking);
+  - hp decision: a marked element of degree 1 gets p = 2; otherwise its
+    solution is expanded in tensor Legendre polynomials and it is p-enriched
+    when the last shell (max(i, j) = p) holds less than SMOOTH of the
+    coefficient norm of the two last shells (fast decay, smooth), else split
+    into four; p is capped at P_MAX (then split) and the depth at DEPTH_MAX
+    levels below the base (then enriched, while p allows).
+The marking and refinement are host logic on the solution copied back; the
+solves are the library's.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Callable, List, Optional
+
+import numpy as np
+
+from . import inputs
+
+ALPHA, R0, CENTRE = 200.0, 0.7, (-0.05, -0.05)
+THETA = 0.5       # bulk marking fraction of the squared indicators
+SMOOTH = 0.3      # last-shell ratio below which a marked element is p-enriched
+P_MAX = 8
+DEPTH_MAX = 10
+
+
+def layer_u(x: np.ndarray) -> np.ndarray:
+    r = np.hypot(x[:, 0] - CENTRE[0], x[:, 1] - CENTRE[1])
+    return np.arctan(ALPHA * (r - R0))
+
+
+def layer_f(x: np.ndarray) -> np.ndarray:
+    """f = -Laplace(u) for u = atan(alpha (r - r0)): -(u_rr + u_r / r)."""
+    r = np.hypot(x[:, 0] - CENTRE[0], x[:, 1] - CENTRE[1])
+    s = ALPHA * (r - R0)
+    ur = ALPHA / (1.0 + s * s)
+    urr = -2.0 * ALPHA ** 2 * s / (1.0 + s * s) ** 2
+    return -(urr + ur / r)
+
+
+def initial_mesh(base: int = 4, p: int = 1) -> inputs.MeshDesc:
+    """4 x 4 squares of degree 1: the 64 DOFs the paper's internal-layer table
+    starts from."""
+    return inputs.uniform_mesh(2, base, p)
+
+
+# ---------------------------------------------------------------- 1D helpers
+def _gll(p: int) -> np.ndarray:
+    """Gauss-Lobatto points on [0, 1] (the library's nodal points)."""
+    from numpy.polynomial import legendre as L
+    inner = np.sort(L.Legendre.basis(p).deriv().roots().real) if p > 1 else np.zeros(0)
+    return 0.5 * (np.concatenate([[-1.0], inner, [1.0]]) + 1.0)
+
+
+def _legendre_vandermonde(p: int) -> np.ndarray:
+    """V[i, j] = P_j(2 x_i - 1) at the Gauss-Lobatto points."""
+    from numpy.polynomial import legendre as L
+    return L.legvander(2.0 * _gll(p) - 1.0, p)
+
+
+# ---------------------------------------------------------------- indicators
+def element_indicators(mesh: inputs.MeshDesc, x: np.ndarray, exact: Callable = layer_u):
+    """Per element: eta = h max_nodes |u - u_h| and the last-shell ratio of
+    the tensor Legendre coefficients of u_h (1 for p = 1)."""
+    n = mesh.n_elems
+    eta = np.zeros(n)
+    ratio = np.ones(n)
+    off = np.concatenate([[0], np.cumsum((mesh.p.astype(np.int64) + 1) ** 2)])
+    h_all = mesh.size.astype(np.float64) * mesh.lattice_h
+    cache = {}
+    for k in range(n):
+        p = int(mesh.p[k])
+        if p not in cache:
+            g = _gll(p)
+            V = _legendre_vandermonde(p)
+            cache[p] = (g, np.linalg.inv(V))
+        g, Vi = cache[p]
+        h = h_all[k]
+        X, Y = np.meshgrid(g, g)                       # iy outer, ix inner
+        pts = np.stack([mesh.lo[k, 0] * mesh.lattice_h + h * X.ravel(),
+                        mesh.lo[k, 1] * mesh.lattice_h + h * Y.ravel()], axis=1)
+        uh = x[off[k]:off[k + 1]]
+        eta[k] = h * np.abs(exact(pts) - uh).max()
+        if p >= 2:
+            U = uh.reshape(p + 1, p + 1)               # U[iy, ix]
+            Cf = Vi @ U @ Vi.T                         # Cf[j, i]: P_j(y) P_i(x)
+            I, J = np.meshgrid(np.arange(p + 1), np.arange(p + 1))
+            shell = np.maximum(I, J)
+            top = np.sqrt(np.sum(Cf[shell == p] ** 2))
+            nxt = np.sqrt(np.sum(Cf[shell == p - 1] ** 2))
+            # two last shells at round-off against the whole expansion: smooth
+            ratio[k] = top / max(top + nxt, 1e-12 * np.sqrt(np.sum(Cf ** 2)), 1e-300)
+    return eta, ratio
+
+
+def bulk_mark(eta: np.ndarray, theta: float = THETA) -> np.ndarray:
+    """Smallest set, largest first (ties by index), with sum eta^2 >= theta total."""
+    order = np.lexsort((np.arange(len(eta)), -eta))
+    e2 = eta[order] ** 2
+    tot = e2.sum()
+    mark = np.zeros(len(eta), dtype=bool)
+    if tot <= 0.0:
+        return mark
+    cut = int(np.searchsorted(np.cumsum(e2), theta * tot) + 1)
+    mark[order[:min(cut, len(eta))]] = True
+    return mark
+
+
+# ---------------------------------------------------------------- refinement
+def refine(mesh: inputs.MeshDesc, h_mark: np.ndarray, p_mark: np.ndarray) -> inputs.MeshDesc:
+    """Split the h-marked elements into four children of the same degree and
+    raise the degree of the p-marked ones by one; the lattice is halved first
+    when a split element has the finest size.  Children follow their parent in
+    the element order (Morton order inside the parent)."""
+    lo, size, p = mesh.lo.astype(np.int64), mesh.size.astype(np.int64), mesh.p.astype(np.int64)
+    ext, lh = np.asarray(mesh.extent, dtype=np.int64), float(mesh.lattice_h)
+    if np.any(h_mark & (size == 1)):
+        lo, size, ext, lh = lo * 2, size * 2, ext * 2, lh / 2.0
+    nlo, nsz, npp = [], [], []
+    for k in range(mesh.n_elems):
+        if h_mark[k]:
+            s = size[k] // 2
+            for dy in (0, 1):
+                for dx in (0, 1):
+                    nlo.append((lo[k, 0] + dx * s, lo[k, 1] + dy * s))
+                    nsz.append(s)
+                    npp.append(p[k])
+        else:
+            nlo.append((lo[k, 0], lo[k, 1]))
+            nsz.append(size[k])
+            npp.append(min(P_MAX, p[k] + 1) if p_mark[k] else p[k])
+    return inputs.MeshDesc(dim=2, lo=np.asarray(nlo, dtype=np.int32).reshape(-1, 2),
+                           size=np.asarray(nsz, dtype=np.int32), p=np.asarray(npp, dtype=np.int32),
+                           extent=tuple(int(e) for e in ext), lattice_h=lh)
+
+
+def decide(mesh: inputs.MeshDesc, mark: np.ndarray, ratio: np.ndarray, base_size: float):
+    """hp decision for the marked elements: (h_mark, p_mark)."""
+    depth = np.round(np.log2(base_size / (mesh.size.astype(np.float64) * mesh.lattice_h))).astype(int)
+    smooth = (mesh.p < 2) | (ratio < SMOOTH)
+    p_mark = mark & ((smooth & (mesh.p < P_MAX)) | ((depth >= DEPTH_MAX) & (mesh.p < P_MAX)))
+    h_mark = mark & ~p_mark & (depth < DEPTH_MAX)
+    return h_mark, p_mark
+
+
+@dataclasses.dataclass
+class AmrStep:
+    step: int
+    n_elems: int
+    n_dofs: int
+    iters: int                 # PCG iterations with B = B_B + B_C
+    iters_jacobi: Optional[int]  # with B~ = J_B + B_C
+    n_blocks: int              # nontrivial V_e
+    max_block: int
+    err_max: float             # max nodal |u - u_h|
+    solve_ms: float
+    n_h: int = 0               # elements split after this step
+    n_p: int = 0               # elements enriched after this step
+
+
+def run(solve: Callable, steps: int = 20, mesh: Optional[inputs.MeshDesc] = None,
+        callback: Optional[Callable] = None) -> List[AmrStep]:
+    """The AMR loop: solve(mesh) -> (x, info dict with iters, iters_jacobi,
+    n_blocks, max_block, solve_ms); mark, decide, refine; `steps` refinements
+    after the initial solve."""
+    mesh = mesh if mesh is not None else initial_mesh()
+    base_size = float(mesh.size.max()) * mesh.lattice_h
+    out = []
+    for step in range(steps + 1):
+        x, info = solve(mesh)
+        eta, ratio = element_indicators(mesh, x)
+        off = np.concatenate([[0], np.cumsum((mesh.p.astype(np.int64) + 1) ** 2)])
+        rec = AmrStep(step, mesh.n_elems, int(off[-1]), int(info["iters"]), info.get("iters_jacobi"),
+                      int(info.get("n_blocks", 0)), int(info.get("max_block", 0)),
+                      float((eta / (mesh.size * mesh.lattice_h)).max()), float(info.get("solve_ms", 0.0)))
+        if callback:
+            callback(mesh, x, rec)
+        if step < steps:
+            mark = bulk_mark(eta)
+            h_mark, p_mark = decide(mesh, mark, ratio, base_size)
+            rec.n_h, rec.n_p = int(h_mark.sum()), int(p_mark.sum())
+            mesh = refine(mesh, h_mark, p_mark)
+        out.append(rec)
+    return out
+
+
+def library_solver(B, torch, rtol: float = 1e-8, precision=None, with_jacobi: bool = True, stream=None):
+    """solve(mesh) through the C ABI: FP64 (or the given precision) PCG with
+    B = B_B + B_C and, when asked, with B~ = J_B + B_C on the same system."""
+    def solve(mesh):
+        prec = B.DG_PREC_FP64 if precision is None else precision
+        o = B.make_options(precision=prec)
+        M = B.Mesh(mesh, o, stream)
+        pc = B.Precond(M, o)
+        b = torch.empty(M.n_dofs, dtype=torch.float64, device="cuda")
+        B.dg_rhs_eval(M.h, layer_f, layer_u, b, stream)
+        x = torch.empty_like(b)
+        info = B.dg_pcg_solve(M.h, pc.h, b, x, rtol, 20000, stream)
+        res = {"iters": info.iters, "n_blocks": int(pc.stats.n_blocks), "max_block": int(pc.stats.max_block),
+               "solve_ms": info.solve_ms, "iters_jacobi": None}
+        if with_jacobi:
+            oj = B.make_options(precision=prec, smoother=B.DG_SMOOTHER_JACOBI_ONLY)
+            pcj = B.Precond(M, oj)
+            xj = torch.empty_like(b)
+            res["iters_jacobi"] = B.dg_pcg_solve(M.h, pcj.h, b, xj, rtol, 20000, stream).iters
+            pcj.close()
+        xs = x.cpu().numpy()
+        pc.close()
+        M.close()
+        return xs, res
+    return solve

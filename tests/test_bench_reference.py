@@ -32,3 +32,9 @@ def test_reference_line_has_the_contract_keys():
 def test_reference_unavailable_for_batched_form():
     d = _run("--workload", "batched")
     assert d["impl"] == "reference" and "unavailable" in d
+
+
+def test_reference_amr_sequence():
+    d = _run("--workload", "amr-layer", "--amr-steps", "3")
+    assert d["impl"] == "reference" and d["value"] > 0 and len(d["table"]) == 4
+    assert d["table"][-1]["n_dofs"] > d["table"][0]["n_dofs"]
