@@ -84,16 +84,19 @@ class Topology:
         return [(x0, y0), (x0 + h, y0), (x0, y0 + h), (x0 + h, y0 + h)]
 
     def _check_cover(self) -> None:
-        area = int(np.sum(self.size ** 2))
-        if area != self.extent[0] * self.extent[1]:
-            raise ValueError("leaves do not tile the domain")
+        """The domain is the union of the leaves: they may not overlap; lattice
+        cells no leaf covers are holes (an L-shaped domain, say), whose edges
+        are boundary like the lattice's own."""
         occ = np.zeros(self.extent[::-1], dtype=np.int32)
         for k in range(self.n):
             x0, y0 = self.lo[k]
             h = self.size[k]
+            if x0 < 0 or y0 < 0 or x0 + h > self.extent[0] or y0 + h > self.extent[1]:
+                raise ValueError("leaf outside the lattice")
             occ[y0:y0 + h, x0:x0 + h] += 1
-        if not np.all(occ == 1):
-            raise ValueError("leaves overlap or leave gaps")
+        if np.any(occ > 1):
+            raise ValueError("leaves overlap")
+        self.covered = occ == 1
 
     def _build_sides(self) -> None:
         # line key (axis, c) -> list of (element, side, t0, t1)
@@ -113,12 +116,18 @@ class Topology:
                     t0, t1 = max(a0, b0), min(a1, b1)
                     if t1 > t0:
                         self.subfaces.append(SubFace(km, kp, ax, c, t0, t1, +1))
-            if c == 0:
-                for (k, s, a0, a1) in plus:
-                    self.subfaces.append(SubFace(k, -1, ax, c, a0, a1, -1))
-            if c == self.extent[ax]:
-                for (k, s, a0, a1) in minus:
-                    self.subfaces.append(SubFace(k, -1, ax, c, a0, a1, +1))
+            # the parts of a side that no opposite side covers are boundary
+            # (the lattice's edge, or the edge of a hole)
+            for group, opp, sign in ((plus, minus, -1), (minus, plus, +1)):
+                for (k, s, a0, a1) in group:
+                    cov = sorted((max(a0, b0), min(a1, b1)) for (_, _, b0, b1) in opp if min(a1, b1) > max(a0, b0))
+                    t = a0
+                    for (u0, u1) in cov:
+                        if u0 > t:
+                            self.subfaces.append(SubFace(k, -1, ax, c, t, u0, sign))
+                        t = max(t, u1)
+                    if t < a1:
+                        self.subfaces.append(SubFace(k, -1, ax, c, t, a1, sign))
 
     def _build_vertices(self) -> None:
         self.vertices = sorted({v for k in range(self.n) for v in self.corners(k)})
@@ -142,11 +151,19 @@ class Topology:
         return self.containing_side(v) is not None
 
     def on_boundary(self, v: Tuple[int, int]) -> bool:
-        return v[0] in (0, self.extent[0]) or v[1] in (0, self.extent[1])
+        """A vertex of the domain boundary: one of the four lattice cells around
+        it is outside the lattice or a hole."""
+        x, y = v
+        for cy in (y - 1, y):
+            for cx in (x - 1, x):
+                if not (0 <= cx < self.extent[0] and 0 <= cy < self.extent[1]) or not self.covered[cy, cx]:
+                    return True
+        return False
 
     def _build_masters(self) -> None:
         self.masters: Dict[Tuple[int, int, int, int], MasterEdge] = {}
         self.side_master: Dict[Tuple[int, int], Tuple[int, int, int, int]] = {}
+        bnd: Dict[Tuple[int, int, int, int], bool] = {}
         for (ax, c), items in self.lines.items():
             for (k, s, t0, t1) in items:
                 opp = [it for it in items if (it[1] in (0, 2)) != (s in (0, 2))]
@@ -157,12 +174,13 @@ class Topology:
                     key = (ax, c, u0, u1)
                 else:
                     key = (ax, c, t0, t1)
+                    # a boundary edge: no element across it (lattice edge or hole)
+                    bnd[key] = not any(min(t1, it[3]) > max(t0, it[2]) for it in opp)
                 self.side_master[(k, s)] = key
         for (k, s), key in self.side_master.items():
             ax, c, t0, t1 = key
             if key not in self.masters:
-                self.masters[key] = MasterEdge(ax, c, t0, t1, [], [], c in (0, self.extent[ax]),
-                                               10 ** 9, [])
+                self.masters[key] = MasterEdge(ax, c, t0, t1, [], [], bnd[key], 10 ** 9, [])
             m = self.masters[key]
             seg = self.side_segment(k, s)
             if (seg[2], seg[3]) == (t0, t1):

@@ -143,6 +143,20 @@ PARALLELOGRAM = ((0.0, 0.0), (1.0, 0.0), (0.35, 0.9), (1.35, 0.9))
 QUADRILATERAL = ((0.0, 0.0), (1.2, 0.1), (0.15, 0.95), (1.05, 1.25))
 
 
+def lshape(mesh: MeshDesc) -> MeshDesc:
+    """The leaves of a square lattice mesh outside its lower-left quarter: an
+    L-shaped domain with the re-entrant corner at the lattice's centre (the
+    extents must be even in base cells, so that no leaf straddles the hole)."""
+    hx, hy = mesh.extent[0] // 2, mesh.extent[1] // 2
+    x0, y0, s = mesh.lo[:, 0], mesh.lo[:, 1], mesh.size
+    inside = (x0 + s <= hx) & (y0 + s <= hy)
+    if np.any((x0 < hx) & (y0 < hy) & ~inside):
+        raise ValueError("a leaf straddles the hole")
+    keep = ~inside
+    return dataclasses.replace(mesh, lo=mesh.lo[keep].copy(), size=mesh.size[keep].copy(), p=mesh.p[keep].copy(),
+                               coeff=None if mesh.coeff is None else mesh.coeff[keep].copy())
+
+
 def with_mapping(mesh: MeshDesc, mapping) -> MeshDesc:
     return dataclasses.replace(mesh, mapping=mapping)
 
