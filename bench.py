@@ -736,7 +736,7 @@ def run_batched(args):
 
 
 def run_amr(args):
-    """hp-adaptive refinement of the internal-layer problem (Section 4.2):
+    """hp-adaptive refinement of the internal-layer or the L-shape problem (Section 4.2):
     `--amr-steps` refinements after the first solve, every solve through the C
     ABI (mixed-precision B = B_B + B_C, and FP64 B~ = J_B + B_C for the
     iteration column the paper reports beside it)."""
@@ -745,8 +745,9 @@ def run_amr(args):
     from paper_2009_01287_gb300 import amr
     from paper_2009_01287_gb300 import binding as B
     torch.cuda.set_device(0)
-    mixed = amr.library_solver(B, torch, precision=B.DG_PREC_MIXED, with_jacobi=False)
-    b_tilde = amr.library_solver(B, torch, with_jacobi=True)
+    problem = amr.LSHAPE if args.workload == "amr-lshape" else amr.LAYER
+    mixed = amr.library_solver(B, torch, precision=B.DG_PREC_MIXED, with_jacobi=False, problem=problem)
+    b_tilde = amr.library_solver(B, torch, with_jacobi=True, problem=problem)
     steps = []
 
     def solve(mesh):
@@ -756,7 +757,7 @@ def run_amr(args):
 
     clocks = ClockSampler(0).start()
     t0 = time.perf_counter()
-    recs = amr.run(solve, steps=args.amr_steps, callback=lambda m, x, r: steps.append(r))
+    recs = amr.run(solve, steps=args.amr_steps, callback=lambda m, x, r: steps.append(r), problem=problem)
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     di = sum(r.n_dofs * r.iters for r in recs)
@@ -765,9 +766,9 @@ def run_amr(args):
            "value": di / (ms / 1e3), "unit": "DOF-iters/s", "n_gpus": 1, "steps": len(recs), "warmup": 0,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64 (outer PCG, operator) + f32 (preconditioner)", "data": "synthetic",
-           "config": {"workload": "hp-AMR of the internal-layer problem u = atan(200 (r - 0.7)) on the unit "
-                                  f"square, 4x4 p=1 start, {args.amr_steps} refinements, SIPG eta=100, "
-                                  "tol 1e-8, weak Dirichlet data"},
+           "config": {"workload": f"hp-AMR of the {problem.name}, {problem.initial().n_elems} p=1 squares to "
+                                  f"start, {args.amr_steps} refinements, SIPG eta=100, tol 1e-8, weak Dirichlet "
+                                  "data"},
            "wall_s_with_setup": wall,
            "table": [dataclasses.asdict(r) for r in recs], "clocks": clk}
     print(json.dumps(out))
@@ -779,19 +780,20 @@ def run_reference_amr(args):
     from oracle import rhs, solver
 
     from paper_2009_01287_gb300 import amr
+    problem = amr.LSHAPE if args.workload == "amr-lshape" else amr.LAYER
     pcg_s = []
 
     def solve(mesh):
         prob = solver.build_problem(mesh)
         pc = solver.Preconditioner(prob, lor="amg")
-        b = rhs.dirichlet_load(prob.space, amr.layer_f, amr.layer_u, 100.0)
+        b = rhs.dirichlet_load(prob.space, problem.f, problem.u, 100.0)
         t = time.perf_counter()
         res = solver.pcg(prob.A, b, pc.apply, 1e-8, 20000)
         pcg_s.append(time.perf_counter() - t)
         return res.x, {"iters": res.iters, "n_blocks": len(prob.cs.blocks),
                        "max_block": max((len(bk) for bk in prob.cs.blocks), default=0)}
 
-    recs = amr.run(solve, steps=args.amr_steps)
+    recs = amr.run(solve, steps=args.amr_steps, problem=problem)
     di = sum(r.n_dofs * r.iters for r in recs)
     value = di / sum(pcg_s)
     sample = f"the {args.amr_steps}-step AMR sequence driven by the oracle's own solves, FP64 PCG timed"
@@ -799,8 +801,8 @@ def run_reference_amr(args):
         "impl": "reference", "metric": "DOF-iters/s over the solves of the AMR sequence", "value": value,
         "unit": "DOF-iters/s", "n_gpus": 1, "steps": len(recs), "warmup": 0, "ms_per_step": 1e3 * sum(pcg_s) / len(recs),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "hp-AMR of the internal-layer problem u = atan(200 (r - 0.7)) on the unit square, "
-                               f"4x4 p=1 start, {args.amr_steps} refinements, SIPG eta=100, tol 1e-8"},
+        "config": {"workload": f"hp-AMR of the {problem.name}, {problem.initial().n_elems} p=1 squares to start, "
+                               f"{args.amr_steps} refinements, SIPG eta=100, tol 1e-8, weak Dirichlet data"},
         "cpu_baseline": {"value": value, "unit": "DOF-iters/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "DOF-iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "table": [dataclasses.asdict(r) for r in recs]}))
@@ -810,7 +812,7 @@ def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
         return
-    if args.workload == "amr-layer":
+    if args.workload in ("amr-layer", "amr-lshape"):
         run_reference_amr(args)
         return
     if args.workload in ("batched", "serving"):
@@ -868,7 +870,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="only the line's own workload")
     ap.add_argument("--workload", default="hp2d",
                     choices=["hp2d", "hp2d-br2", "hp2d-coef", "hp2d-map", "hp2d-curved", "hp3d", "batched",
-                             "serving", "amr-layer"])
+                             "serving", "amr-layer", "amr-lshape"])
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-meshes", type=int, default=16)
@@ -881,7 +883,7 @@ def main():
                     help="single-mesh workloads: let dg_mesh_create tune the operator's tiles")
     ap.add_argument("--base3", type=int, default=16,
                     help="cube workload: base grid per axis (16 is the workload; smaller for profiling captures)")
-    ap.add_argument("--amr-steps", type=int, default=20, help="amr-layer workload: refinement steps")
+    ap.add_argument("--amr-steps", type=int, default=20, help="amr workloads: refinement steps")
     ap.add_argument("--oracle-leg", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-out", default="", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-solve", action="store_true", help=argparse.SUPPRESS)
@@ -895,7 +897,7 @@ def main():
         run_batched(args)
     elif args.workload == "serving":
         run_serving(args)
-    elif args.workload == "amr-layer":
+    elif args.workload in ("amr-layer", "amr-lshape"):
         run_amr(args)
     else:
         run_ours(args)

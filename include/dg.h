@@ -54,7 +54,12 @@ typedef struct dg_precond dg_precond;
  * dim is 2 (squares) or 3 (cubes).  lo: n_elems*dim lower corners (lattice
  * units); size: n_elems edge lengths (powers of two); p: n_elems degrees in
  * 1..8; extent: dim domain lengths in lattice units; the physical domain is
- * [0, extent_0*lattice_h] x ... .  The boxes must tile the domain exactly.
+ * [0, extent_0*lattice_h] x ... .  The boxes must not overlap; cubes must
+ * tile the lattice exactly, while on squares lattice cells that no box covers
+ * are holes of the domain (an L-shaped domain, say: the domain is the union of
+ * the boxes), whose edges are boundary like the lattice's own; an element
+ * side must then border a hole along its whole length or not at all
+ * (DG_EINVAL otherwise).
  * coeff: NULL (a = 1) or n_elems values a_kappa > 0 of the piecewise-constant
  * coefficient of -div(a grad u) = f (Section 4.3, random refinement): a_kappa
  * weights element kappa's volume term and its share of the face averages

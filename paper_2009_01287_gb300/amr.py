@@ -1,9 +1,11 @@
 """hp-adaptive refinement driver (Section 4.2: adaptively refined meshes and
-spaces), for the internal-layer problem of that section: -Laplace(u) = f on
-the unit square with u = g on the boundary, the exact solution
-u = atan(alpha (r - r0)), r the distance from (-0.05, -0.05), alpha = 200,
-r0 = 0.7 (the paper writes Laplace(u) = f; the sign of f is flipped here as
-everywhere in this library).
+spaces), for the two problems of that section, both -Laplace(u) = f with
+u = g on the boundary and a known solution (the paper writes Laplace(u) = f;
+the sign of f is flipped here as everywhere in this library):
+  - the internal layer on the unit square, u = atan(alpha (r - r0)), r the
+    distance from (-0.05, -0.05), alpha = 200, r0 = 0.7 (LAYER);
+  - the L-shaped domain, u = r^(2/3) sin(2 theta / 3 + pi / 3) about the
+    re-entrant corner, f = 0 (LSHAPE; the lattice with a hole).
 
 Each step solves on the current mesh through the C ABI (dg_mesh_create,
 dg_precond_setup, dg_rhs_eval with the boundary data, dg_pcg_solve), records
@@ -11,8 +13,8 @@ the PCG iterations of B = B_B + B_C and of B~ = J_B + B_C with the V_e
 statistics (the columns of the paper's AMR tables), then marks and refines.
 The paper names neither its error estimator nor its hp decision; this driver
 takes (readings, stated here and in the design notes):
-  - indicator: eta_k = h_k max over the element's nodes of |u - u_h| (the
-    exact solution is known for this benchmark problem);
+  - indicator: eta_k = ||u - u_h||_L2(kappa) by the (p+3)-point Gauss rule
+    per direction (the exact solution is known for these benchmark problems);
   - marking: the smallest set of elements, largest eta first (ties by element
     number), whose eta^2 sum reaches THETA of the total (bulk marking);
   - hp decision: a marked element of degree 1 gets p = 2; otherwise its
@@ -60,12 +62,62 @@ def initial_mesh(base: int = 4, p: int = 1) -> inputs.MeshDesc:
     return inputs.uniform_mesh(2, base, p)
 
 
+# the L-shaped domain problem of Section 4.2: Laplace(u) = 0 with u = g on the
+# boundary, g = r^(2/3) sin(2 theta / 3 + pi / 3) in polar coordinates about
+# the re-entrant corner.  Here the domain is [0, 2]^2 without [0, 1]^2 (the
+# corner at (1, 1)), so theta = atan2 runs over [-pi/2, pi] on it and u
+# vanishes on the two edges that meet at the corner.
+LCORNER = (1.0, 1.0)
+
+
+def lshape_u(x: np.ndarray) -> np.ndarray:
+    dx, dy = x[:, 0] - LCORNER[0], x[:, 1] - LCORNER[1]
+    r = np.hypot(dx, dy)
+    th = np.arctan2(dy, dx)
+    return r ** (2.0 / 3.0) * np.sin(2.0 * th / 3.0 + np.pi / 3.0)
+
+
+def lshape_f(x: np.ndarray) -> np.ndarray:
+    return np.zeros(len(x))
+
+
+def lshape_initial(p: int = 1) -> inputs.MeshDesc:
+    """Twelve squares of side 1/2 on the L-shaped domain (the paper's initial
+    mesh has 12 elements), degree p."""
+    m = inputs.uniform_mesh(2, 4, p)
+    return inputs.lshape(dataclasses.replace(m, lattice_h=0.5))
+
+
+@dataclasses.dataclass(frozen=True)
+class Problem:
+    name: str
+    u: Callable
+    f: Callable
+    initial: Callable
+
+
+LAYER = Problem("internal layer: u = atan(200 (r - 0.7)), r from (-0.05, -0.05), on the unit square",
+                layer_u, layer_f, initial_mesh)
+LSHAPE = Problem("L-shape: u = r^(2/3) sin(2 theta/3 + pi/3) about the re-entrant corner of [0,2]^2 minus [0,1]^2",
+                 lshape_u, lshape_f, lshape_initial)
+
+
 # ---------------------------------------------------------------- 1D helpers
 def _gll(p: int) -> np.ndarray:
     """Gauss-Lobatto points on [0, 1] (the library's nodal points)."""
     from numpy.polynomial import legendre as L
     inner = np.sort(L.Legendre.basis(p).deriv().roots().real) if p > 1 else np.zeros(0)
     return 0.5 * (np.concatenate([[-1.0], inner, [1.0]]) + 1.0)
+
+
+def _lagrange(nodes: np.ndarray, t: np.ndarray) -> np.ndarray:
+    """L[m, j] = l_j(t_m), the Lagrange basis on `nodes` (product form)."""
+    L = np.ones((len(t), len(nodes)))
+    for j in range(len(nodes)):
+        for i in range(len(nodes)):
+            if i != j:
+                L[:, j] *= (t - nodes[i]) / (nodes[j] - nodes[i])
+    return L
 
 
 def _legendre_vandermonde(p: int) -> np.ndarray:
@@ -76,8 +128,10 @@ def _legendre_vandermonde(p: int) -> np.ndarray:
 
 # ---------------------------------------------------------------- indicators
 def element_indicators(mesh: inputs.MeshDesc, x: np.ndarray, exact: Callable = layer_u):
-    """Per element: eta = h max_nodes |u - u_h| and the last-shell ratio of
-    the tensor Legendre coefficients of u_h (1 for p = 1)."""
+    """Per element: eta = ||u - u_h||_L2(element) by the (p+3)-point Gauss
+    rule per direction, and the last-shell ratio of the tensor Legendre
+    coefficients of u_h (1 for p = 1)."""
+    from numpy.polynomial import legendre as Lg
     n = mesh.n_elems
     eta = np.zeros(n)
     ratio = np.ones(n)
@@ -89,16 +143,19 @@ def element_indicators(mesh: inputs.MeshDesc, x: np.ndarray, exact: Callable = l
         if p not in cache:
             g = _gll(p)
             V = _legendre_vandermonde(p)
-            cache[p] = (g, np.linalg.inv(V))
-        g, Vi = cache[p]
+            gq, wq = Lg.leggauss(p + 3)
+            gq, wq = 0.5 * (gq + 1.0), 0.5 * wq
+            cache[p] = (g, np.linalg.inv(V), gq, wq, _lagrange(g, gq))
+        g, Vi, gq, wq, Lq = cache[p]
         h = h_all[k]
-        X, Y = np.meshgrid(g, g)                       # iy outer, ix inner
-        pts = np.stack([mesh.lo[k, 0] * mesh.lattice_h + h * X.ravel(),
-                        mesh.lo[k, 1] * mesh.lattice_h + h * Y.ravel()], axis=1)
         uh = x[off[k]:off[k + 1]]
-        eta[k] = h * np.abs(exact(pts) - uh).max()
+        U = uh.reshape(p + 1, p + 1)                   # U[iy, ix]
+        Xq, Yq = np.meshgrid(gq, gq)                   # iy outer, ix inner
+        pts = np.stack([mesh.lo[k, 0] * mesh.lattice_h + h * Xq.ravel(),
+                        mesh.lo[k, 1] * mesh.lattice_h + h * Yq.ravel()], axis=1)
+        uq = (Lq @ U @ Lq.T).ravel()                   # u_h at the Gauss points
+        eta[k] = h * np.sqrt(np.outer(wq, wq).ravel() @ (exact(pts) - uq) ** 2)
         if p >= 2:
-            U = uh.reshape(p + 1, p + 1)               # U[iy, ix]
             Cf = Vi @ U @ Vi.T                         # Cf[j, i]: P_j(y) P_i(x)
             I, J = np.meshgrid(np.arange(p + 1), np.arange(p + 1))
             shell = np.maximum(I, J)
@@ -168,27 +225,27 @@ class AmrStep:
     iters_jacobi: Optional[int]  # with B~ = J_B + B_C
     n_blocks: int              # nontrivial V_e
     max_block: int
-    err_max: float             # max nodal |u - u_h|
+    err_l2: float              # ||u - u_h||_L2 over the domain
     solve_ms: float
     n_h: int = 0               # elements split after this step
     n_p: int = 0               # elements enriched after this step
 
 
 def run(solve: Callable, steps: int = 20, mesh: Optional[inputs.MeshDesc] = None,
-        callback: Optional[Callable] = None) -> List[AmrStep]:
+        callback: Optional[Callable] = None, problem: Problem = LAYER) -> List[AmrStep]:
     """The AMR loop: solve(mesh) -> (x, info dict with iters, iters_jacobi,
     n_blocks, max_block, solve_ms); mark, decide, refine; `steps` refinements
     after the initial solve."""
-    mesh = mesh if mesh is not None else initial_mesh()
+    mesh = mesh if mesh is not None else problem.initial()
     base_size = float(mesh.size.max()) * mesh.lattice_h
     out = []
     for step in range(steps + 1):
         x, info = solve(mesh)
-        eta, ratio = element_indicators(mesh, x)
+        eta, ratio = element_indicators(mesh, x, problem.u)
         off = np.concatenate([[0], np.cumsum((mesh.p.astype(np.int64) + 1) ** 2)])
         rec = AmrStep(step, mesh.n_elems, int(off[-1]), int(info["iters"]), info.get("iters_jacobi"),
                       int(info.get("n_blocks", 0)), int(info.get("max_block", 0)),
-                      float((eta / (mesh.size * mesh.lattice_h)).max()), float(info.get("solve_ms", 0.0)))
+                      float(np.sqrt(np.sum(eta ** 2))), float(info.get("solve_ms", 0.0)))
         if callback:
             callback(mesh, x, rec)
         if step < steps:
@@ -200,7 +257,8 @@ def run(solve: Callable, steps: int = 20, mesh: Optional[inputs.MeshDesc] = None
     return out
 
 
-def library_solver(B, torch, rtol: float = 1e-8, precision=None, with_jacobi: bool = True, stream=None):
+def library_solver(B, torch, rtol: float = 1e-8, precision=None, with_jacobi: bool = True, stream=None,
+                   problem: Problem = LAYER):
     """solve(mesh) through the C ABI: FP64 (or the given precision) PCG with
     B = B_B + B_C and, when asked, with B~ = J_B + B_C on the same system."""
     def solve(mesh):
@@ -209,7 +267,7 @@ def library_solver(B, torch, rtol: float = 1e-8, precision=None, with_jacobi: bo
         M = B.Mesh(mesh, o, stream)
         pc = B.Precond(M, o)
         b = torch.empty(M.n_dofs, dtype=torch.float64, device="cuda")
-        B.dg_rhs_eval(M.h, layer_f, layer_u, b, stream)
+        B.dg_rhs_eval(M.h, problem.f, problem.u, b, stream)
         x = torch.empty_like(b)
         info = B.dg_pcg_solve(M.h, pc.h, b, x, rtol, 20000, stream)
         res = {"iters": info.iters, "n_blocks": int(pc.stats.n_blocks), "max_block": int(pc.stats.max_block),

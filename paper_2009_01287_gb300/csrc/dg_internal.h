@@ -239,8 +239,13 @@ struct HostMesh {
   bool corner_of(int k, int x, int y) const;
   // element + side containing (x,y) in the relative interior of the side, or -1
   int containing_side(int x, int y, int* side) const;
+  // a vertex of the domain boundary: one of the four cells around it is
+  // outside the lattice or a hole (no element covers it)
   bool on_boundary(int x, int y) const {
-    return x == 0 || y == 0 || x == extent[0] || y == extent[1];
+    for (int cy = y - 1; cy <= y; ++cy)
+      for (int cx = x - 1; cx <= x; ++cx)
+        if (cx < 0 || cy < 0 || cx >= extent[0] || cy >= extent[1] || elem_at(cx, cy) < 0) return true;
+    return false;
   }
   bool is_hp_vertex(int x, int y) const;
 };

@@ -32,7 +32,7 @@ int HostMesh::containing_side(int x, int y, int* side) const {
       int cx = x + dx, cy = y + dy;
       if (cx < 0 || cy < 0 || cx >= extent[0] || cy >= extent[1]) continue;
       int e = elem_at(cx, cy);
-      if (corner_of(e, x, y)) continue;
+      if (e < 0 || corner_of(e, x, y)) continue;   // a hole, or a corner of e
       const int x0 = lo[2 * e], y0 = lo[2 * e + 1], h = size[e];
       int s;
       if (x == x0) s = 0;
@@ -54,6 +54,7 @@ bool HostMesh::is_hp_vertex(int x, int y) const {
       int cx = x + dx, cy = y + dy;
       if (cx < 0 || cy < 0 || cx >= extent[0] || cy >= extent[1]) continue;
       int e = elem_at(cx, cy);
+      if (e < 0) continue;   // a hole
       if (pv < 0) pv = p[e];
       else if (p[e] != pv) return true;
     }
@@ -74,18 +75,29 @@ void build_topology(HostMesh& m) {
       if (bdry) {
         m.sf.push_back({-1, -1, t0, t1});
       } else {
-        int t = t0;
+        // the cells across the side: elements (one sub-face each) or holes of
+        // the domain (the side is then boundary; a side must not border a hole
+        // in part only)
+        int t = t0, holes = 0, elems = 0;
         while (t < t1) {
           int cx, cy;
           if (axis == 0) { cx = outward_plus ? c : c - 1; cy = t; }
           else { cx = t; cy = outward_plus ? c : c - 1; }
           int nb = m.elem_at(cx, cy);
+          if (nb < 0) {
+            ++holes;
+            ++t;
+            continue;
+          }
           int u0 = m.lo[2 * nb + (1 - axis)];
           int u1 = u0 + m.size[nb];
           int e1 = std::min(t1, u1);
           m.sf.push_back({nb, s ^ 1, t, e1});
+          ++elems;
           t = e1;
         }
+        DG_REQUIRE(holes == 0 || elems == 0, "an element side borders a hole in part only");
+        if (holes) m.sf.push_back({-1, -1, t0, t1});
       }
       m.sf_ptr[4 * k + s + 1] = (int32_t)m.sf.size();
     }
@@ -192,7 +204,10 @@ static void validate_and_copy(const dg_mesh_desc* d, HostMesh& m) {
       }
     m.off[k + 1] = m.off[k] + (int64_t)(m.p[k] + 1) * (m.p[k] + 1);
   }
-  for (int32_t c : m.cellmap) DG_REQUIRE(c >= 0, "elements do not cover the domain");
+  // cells no element covers are holes of the domain (their edges are boundary)
+  int64_t covered = 0;
+  for (int32_t c : m.cellmap) covered += c >= 0;
+  DG_REQUIRE(covered > 0, "no element");
 }
 
 static void append(std::vector<double>& t, const std::vector<double>& v, int& off) {

@@ -62,7 +62,8 @@ BAD = {
     "3d-degree-0": lambda: _desc(3, [(0, 0, 0)], [1], [0], (1, 1, 1)),
     "3d-degree-9": lambda: _desc(3, [(0, 0, 0)], [1], [9], (1, 1, 1)),
     "3d-outside": lambda: _desc(3, [(0, 0, 0), (1, 0, 0)], [1, 1], [1, 1], (1, 1, 1)),
-    "2d-gap": lambda: _desc(2, [(0, 0)], [1], [2], (2, 1)),
+    # squares may leave holes, but a side may not border a hole in part only
+    "2d-partial-hole": lambda: _desc(2, [(0, 0), (2, 0), (3, 0), (3, 1)], [2, 1, 1, 1], [1, 1, 1, 1], (4, 2)),
     "2d-coeff-zero": lambda: _with_coeff(_desc(2, [(0, 0), (1, 0)], [1, 1], [1, 2], (2, 1)), [1.0, 0.0]),
     "2d-coeff-nan": lambda: _with_coeff(_desc(2, [(0, 0), (1, 0)], [1, 1], [1, 2], (2, 1)), [float("nan"), 1.0]),
     "3d-coeff-negative": lambda: _with_coeff(_desc(3, [(0, 0, 0)], [1], [2], (1, 1, 1)), [-20.0]),
@@ -77,7 +78,8 @@ def _with_coeff(mesh, a):
 @pytest.mark.parametrize("name", list(BAD))
 def test_invalid_meshes_rejected(built_lib, name):
     """Invalid 2D and 3D descriptions give DG_EINVAL with a message, before
-    any device work (overlap, gap, misaligned or non-dyadic boxes, degrees
+    any device work (overlap, a gap in a cube mesh or a square's side along
+    part of a hole, misaligned or non-dyadic boxes, degrees
     outside 1..8, boxes outside the domain, a coefficient that is not positive
     and finite)."""
     try:

@@ -64,10 +64,10 @@ def test_smoothness_ratio():
     assert r[0] > amr.SMOOTH
 
 
-def oracle_solver(mesh):
+def oracle_solver(mesh, problem=amr.LAYER):
     prob = solver.build_problem(mesh)
     pc = solver.Preconditioner(prob, lor="amg")
-    b = rhs.dirichlet_load(prob.space, amr.layer_f, amr.layer_u, 100.0)
+    b = rhs.dirichlet_load(prob.space, problem.f, problem.u, 100.0)
     res = solver.pcg(prob.A, b, pc.apply, 1e-8, 5000)
     pcj = solver.Preconditioner(prob, lor="amg", smoother="jacobi_only")
     resj = solver.pcg(prob.A, b, pcj.apply, 1e-8, 5000)
@@ -78,12 +78,41 @@ def oracle_solver(mesh):
 
 def test_amr_steps_with_the_oracle():
     meshes = []
-    recs = amr.run(oracle_solver, steps=4, callback=lambda m, x, r: meshes.append(m))
+    recs = amr.run(oracle_solver, steps=8, callback=lambda m, x, r: meshes.append(m))
     for m in meshes:
         _area_ok(m)
-    assert [r.step for r in recs] == list(range(5))
+    assert [r.step for r in recs] == list(range(9))
     assert all(r.n_dofs > 0 for r in recs)
-    assert recs[-1].err_max < recs[0].err_max
+    assert recs[-1].err_l2 < recs[0].err_l2
     assert recs[-1].n_dofs > recs[0].n_dofs
     assert max(r.iters for r in recs) < 200
     assert any(r.n_h for r in recs[:-1]) and any(r.n_p for r in recs[:-1])
+
+
+def test_lshape_solution_is_harmonic_and_vanishes_on_the_corner_edges():
+    rng = np.random.default_rng(2)
+    x = rng.uniform(1.05, 1.95, size=(40, 2))      # away from the corner, inside the domain
+    e = 1e-4
+    lap = np.zeros(len(x))
+    for d in range(2):
+        dd = np.zeros(2)
+        dd[d] = e
+        lap += (amr.lshape_u(x + dd) - 2 * amr.lshape_u(x) + amr.lshape_u(x - dd)) / e ** 2
+    assert np.abs(lap).max() <= 1e-5
+    t = np.linspace(0.0, 1.0, 7)
+    edges = np.concatenate([np.stack([1.0 + 0 * t, t], 1), np.stack([t, 1.0 + 0 * t], 1)])
+    assert np.abs(amr.lshape_u(edges)).max() <= 1e-15
+    m = amr.lshape_initial()
+    _area_ok_l(m)
+
+
+def _area_ok_l(mesh):
+    Topology(mesh.lo, mesh.size, mesh.p, mesh.extent)
+    assert mesh.n_elems == 12 and (mesh.size.astype(np.int64) ** 2).sum() == 12
+
+
+def test_amr_lshape_steps_with_the_oracle():
+    recs = amr.run(lambda m: oracle_solver(m, amr.LSHAPE), steps=6, problem=amr.LSHAPE)
+    assert recs[0].n_dofs == 48 and recs[-1].n_dofs > 48
+    assert recs[-1].err_l2 < recs[0].err_l2
+    assert max(r.iters for r in recs) < 100

@@ -22,6 +22,11 @@ CASES = [
      "paper"),
     ("coef-br2", lambda: _coef(inputs.small_hp_mesh(5, base=4, depth=2, prob=0.4, pmax=6), 4), "br2", None,
      "paper"),
+    # a domain with a hole: the L-shape of the adaptive-refinement problems (Section 4.2)
+    ("lshape", lambda: inputs.lshape(inputs.small_hp_mesh(6, base=4, depth=3, prob=0.4, pmax=5)), "sipg", None,
+     "paper"),
+    ("lshape-br2", lambda: inputs.lshape(inputs.small_hp_mesh(7, base=4, depth=2, prob=0.5, pmax=4)), "br2", None,
+     "paper"),
 ]
 
 
@@ -61,3 +66,17 @@ def test_default_br2_penalty_matches(built_lib):
     prob, hs = _pair(built_lib, CASES[2][1], "br2", None, "paper")
     from oracle.dg import br2_eta
     assert hs.eta == br2_eta(prob.topo)
+
+
+def test_lshape_load_with_boundary_data(built_lib):
+    """The library's load vector with weak Dirichlet data on an L-shaped hp
+    mesh (boundary sub-faces along the hole) against the oracle's."""
+    from oracle import rhs as R
+    mesh = inputs.lshape(inputs.small_hp_mesh(8, base=4, depth=3, prob=0.4, pmax=6))
+    prob = solver.build_problem(mesh)
+    B = built_lib
+    hs = B.HostSetup(mesh, B.make_options(), amg=False)
+    f = lambda x: np.cos(2 * x[:, 0]) + x[:, 1]
+    g = lambda x: np.hypot(x[:, 0] - 0.5, x[:, 1] - 0.5) ** (2.0 / 3.0)
+    ref = R.dirichlet_load(prob.space, f, g, 100.0)
+    assert np.abs(hs.rhs_eval(f, g) - ref).max() <= 1e-12 * np.abs(ref).max()
