@@ -462,6 +462,7 @@ dg_status dg_batch_create(const dg_mesh_desc* descs, int n_problems, int n_rhs,
     std::vector<std::thread> pool;
     for (int t = 0; t < nth; ++t)
       pool.emplace_back([&, t] {
+        SerialSetup serial;   // one problem per thread already
         for (int k = t; k < n_problems; k += nth) {
           try {
             B->meshes[k].reset(new dg_mesh());

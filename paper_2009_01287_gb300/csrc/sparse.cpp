@@ -16,6 +16,10 @@
 //              does not shrink below 0.9 n, or at kAmgMaxLevels levels; the
 //              last level is inverted densely.
 #include <algorithm>
+#include <cstdlib>
+#include <cstdio>
+#include <chrono>
+#include <thread>
 #include <cmath>
 #include <numeric>
 
@@ -70,15 +74,16 @@ Csr csr_transpose(const Csr& A) {
   return T;
 }
 
-Csr csr_multiply(const Csr& A, const Csr& B) {
-  Csr C;
-  C.rows = A.rows;
-  C.cols = B.cols;
-  C.ptr.assign(A.rows + 1, 0);
+namespace {
+
+// rows [r0, r1) of C = A B: per row the columns in increasing order and the
+// sums in the order of A's row and B's rows (the same whatever the split)
+void multiply_rows(const Csr& A, const Csr& B, int64_t r0, int64_t r1, std::vector<int64_t>& cnt,
+                   std::vector<int32_t>& idx, std::vector<double>& val) {
   std::vector<int64_t> mark(B.cols, -1);
   std::vector<double> acc(B.cols, 0.0);
   std::vector<int32_t> cols;
-  for (int64_t i = 0; i < A.rows; ++i) {
+  for (int64_t i = r0; i < r1; ++i) {
     cols.clear();
     for (int64_t t = A.ptr[i]; t < A.ptr[i + 1]; ++t) {
       const int32_t a = A.idx[t];
@@ -95,10 +100,57 @@ Csr csr_multiply(const Csr& A, const Csr& B) {
     }
     std::sort(cols.begin(), cols.end());
     for (int32_t b : cols) {
-      C.idx.push_back(b);
-      C.val.push_back(acc[b]);
+      idx.push_back(b);
+      val.push_back(acc[b]);
     }
-    C.ptr[i + 1] = (int64_t)C.idx.size();
+    cnt[i - r0] = (int64_t)cols.size();
+  }
+}
+
+thread_local bool t_serial = false;
+
+}  // namespace
+
+SerialSetup::SerialSetup() : prev(t_serial) { t_serial = true; }
+SerialSetup::~SerialSetup() { t_serial = prev; }
+
+Csr csr_multiply(const Csr& A, const Csr& B) {
+  Csr C;
+  C.rows = A.rows;
+  C.cols = B.cols;
+  C.ptr.assign(A.rows + 1, 0);
+  // large products are split into row ranges of about equal work (A's
+  // nonzeros) computed by threads; every row is computed exactly as in one
+  // pass, so the result does not depend on the split
+  int nth = 1;
+  if (!t_serial && A.nnz() > (1 << 16))
+    nth = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  if (nth <= 1) {
+    std::vector<int64_t> cnt(A.rows);
+    multiply_rows(A, B, 0, A.rows, cnt, C.idx, C.val);
+    for (int64_t i = 0; i < A.rows; ++i) C.ptr[i + 1] = C.ptr[i] + cnt[i];
+    return C;
+  }
+  std::vector<int64_t> cut(nth + 1, A.rows);
+  cut[0] = 0;
+  for (int t = 1; t < nth; ++t) {
+    const int64_t target = A.nnz() * t / nth;
+    cut[t] = std::upper_bound(A.ptr.begin(), A.ptr.end(), target) - A.ptr.begin() - 1;
+    cut[t] = std::max(cut[t], cut[t - 1]);
+  }
+  std::vector<std::vector<int64_t>> cnt(nth);
+  std::vector<std::vector<int32_t>> idx(nth);
+  std::vector<std::vector<double>> val(nth);
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nth; ++t) {
+    cnt[t].resize(cut[t + 1] - cut[t]);
+    pool.emplace_back([&, t] { multiply_rows(A, B, cut[t], cut[t + 1], cnt[t], idx[t], val[t]); });
+  }
+  for (auto& th : pool) th.join();
+  for (int t = 0; t < nth; ++t) {
+    for (int64_t i = cut[t]; i < cut[t + 1]; ++i) C.ptr[i + 1] = C.ptr[i] + cnt[t][i - cut[t]];
+    C.idx.insert(C.idx.end(), idx[t].begin(), idx[t].end());
+    C.val.insert(C.val.end(), val[t].begin(), val[t].end());
   }
   return C;
 }
@@ -195,6 +247,14 @@ std::vector<double> l1_diag(const Csr& A) {
 }  // namespace
 
 AmgHierarchy amg_setup(const Csr& A0, double theta) {
+  const bool timing = std::getenv("DG_SETUP_TIMING") != nullptr;
+  auto t0 = std::chrono::steady_clock::now();
+  auto lap = [&](const char* what) {
+    if (!timing) return;
+    auto t1 = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "[amg]    %-12s %8.3f s\n", what, std::chrono::duration<double>(t1 - t0).count());
+    t0 = t1;
+  };
   AmgHierarchy H;
   H.levels.push_back({A0, l1_diag(A0), {}, {}});
   while (true) {
@@ -202,6 +262,7 @@ AmgHierarchy amg_setup(const Csr& A0, double theta) {
     const int64_t n = L.A.rows;
     if (n <= kAmgCoarseMax || (int)H.levels.size() >= kAmgMaxLevels) break;
     std::vector<int32_t> agg = aggregate(L.A, theta);
+    lap("aggregate");
     int64_t nc = 0;
     for (int32_t a : agg) nc = std::max<int64_t>(nc, a + 1);
     if ((double)nc >= 0.9 * (double)n) break;
@@ -231,18 +292,23 @@ AmgHierarchy amg_setup(const Csr& A0, double theta) {
       }
     }
     Csr P = csr_from_triplets(n, nc, r, c, v);
+    lap("P");
     Csr R = csr_transpose(P);
     Csr Ac = csr_multiply(R, csr_multiply(L.A, P));
+    lap("RAP");
     L.P = std::move(P);
     L.R = std::move(R);
     AmgLevel next{std::move(Ac), {}, {}, {}};
     next.dl1 = l1_diag(next.A);
     H.levels.push_back(std::move(next));
   }
-  // composite operators of every level that continues
+  // composite operators of every level that continues, except the levels
+  // the device applies in the plain form anyway (more than kAmgPlainNnz
+  // nonzeros: so many in any union of instances that holds this level)
   for (size_t l = 0; l + 1 < H.levels.size(); ++l) {
     AmgLevel& L = H.levels[l];
     const Csr& A = L.A;
+    if (A.nnz() > kAmgPlainNnz) continue;
     const std::vector<double>& d = L.dl1;
     Csr M1 = A, M2 = A, Sb = A;   // I - A D^-1, I - D^-1 A, 2 D^-1 - D^-1 A D^-1
     for (int64_t i = 0; i < A.rows; ++i)
@@ -257,6 +323,7 @@ AmgHierarchy amg_setup(const Csr& A0, double theta) {
     L.Sp = csr_multiply(M2, L.P);
     L.Sb = std::move(Sb);
   }
+  lap("composite");
   const Csr& C = H.levels.back().A;
   if (C.rows > kAmgDenseMax)
     throw Error(DG_EUNSUPPORTED, "AMG coarsening stalled above the dense coarse-solve limit");
@@ -265,6 +332,7 @@ AmgHierarchy amg_setup(const Csr& A0, double theta) {
   for (int64_t i = 0; i < nc; ++i)
     for (int64_t t = C.ptr[i]; t < C.ptr[i + 1]; ++t) H.coarse_inv[i * nc + C.idx[t]] = C.val[t];
   dense_inverse_spd(nc, H.coarse_inv);
+  lap("coarse");
   return H;
 }
 

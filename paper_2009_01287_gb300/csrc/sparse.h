@@ -20,6 +20,14 @@ Csr csr_from_triplets(int64_t rows, int64_t cols, std::vector<int64_t>& r,
                       std::vector<int32_t>& c, std::vector<double>& v);
 Csr csr_transpose(const Csr& A);
 Csr csr_multiply(const Csr& A, const Csr& B);   // sorted columns, exact zeros kept
+// While an instance lives, csr_multiply on this thread stays on it (callers
+// that already run one setup per thread, like the batched solver's, keep the
+// machine from being oversubscribed).  Results are the same either way.
+struct SerialSetup {
+  SerialSetup();
+  ~SerialSetup();
+  bool prev;
+};
 
 // Deterministic smoothed-aggregation AMG hierarchy (setup only).
 struct AmgLevel {
