@@ -297,6 +297,7 @@ void build_mesh_host(dg_mesh* M, const dg_mesh_desc* desc, const dg_options* opt
   M->opts = o;
   DG_REQUIRE(desc != nullptr, "null mesh description");
   if (desc->dim == 3) {
+    if (desc->corners || desc->map) throw Error(DG_EUNSUPPORTED, "mapped elements: square meshes only");
     build_mesh_host3(M, desc, o);
     return;
   }

@@ -1,12 +1,16 @@
 // Mapped square meshes (Section 2: element maps T_kappa onto general
 // quadrilaterals).  The leaf boxes of the lattice are pre-images; the bilinear
-// map of the lattice domain onto the quadrilateral with the given corners
-// carries them to the elements.  This file builds what the mapped operator
-// kernel reads - per degree the volume rule's basis tables, the geometric
-// factors at every volume and sub-face Gauss point, per sub-face its rule
-// size, both sides' 1D basis values and derivatives at the rule's points and
-// its penalty - and holds the host mirror of that kernel (element rows, their
-// diagonal) and the LOR blocks on mapped cells (Section 3.4).
+// map of the lattice domain onto the quadrilateral with the given corners, or
+// the caller's smooth map (curved elements), carries them to the elements.
+// This file builds what the mapped operator kernel reads - per degree the
+// volume rule's basis tables, the geometric factors at every volume and
+// sub-face Gauss point, per sub-face its rule size, both sides' 1D basis values
+// and derivatives at the rule's points and its penalty, for BR2 the blocks of
+// every element's mass inverse on its sides' nodes - and holds the host mirror
+// of that kernel (element rows, their diagonal) and the LOR blocks on mapped
+// cells (Section 3.4).  The map is evaluated here, inside dg_mesh_create, and
+// nowhere else: what later calls need of it (the LOR cells' vertices, the load
+// vector's points) is stored.
 //
 // The SIPG form is the one of boxes, evaluated at Gauss points:
 //   volume  int a grad u . grad v = int a (grad_xi u)^T G (grad_xi v) dxi,
@@ -16,7 +20,10 @@
 //           physical normal n = J^-T nu / |J^-T nu| (nu the pre-image normal),
 //           grad u . n = grad_X u . (J^-1 n) with grad_X u from the side's trace
 //           values (tangential) and its normal-derivative line (normal),
-//           sigma = a_e eta p_e^2 / min(h-, h+) with h_kappa = sqrt(|kappa|).
+//           sigma = a_e eta p_e^2 / min(h-, h+) with h_kappa = sqrt(|kappa|);
+//   BR2     the lifting of a sub-face's jump on each side with that element's
+//           own mass matrix (the p+2 rule; not a Kronecker product on a mapped
+//           element), of which only the block on the side's nodes is needed.
 #include <algorithm>
 #include <cmath>
 #include <map>

@@ -175,3 +175,16 @@ def test_host_load_matches_oracle(built_lib):
         hs.rhs_eval(f, g)   # boundary data on a mapped mesh
     with pytest.raises(B.DGError):
         hs.rhs_eval(lambda x: x[:, 5], None)   # a failing callback
+
+
+def test_mapped_cubes_refused(built_lib):
+    B = built_lib
+    mesh = inputs.small_hp_mesh(0, base=2, depth=1, prob=0.4, pmin=1, pmax=2, dim=3)
+    with pytest.raises(B.DGError) as e:
+        B.HostSetup(inputs.with_mapping(mesh, inputs.WavyMap()), B.make_options())
+    assert e.value.code == B.DG_EUNSUPPORTED
+    bad = inputs.MeshDesc(dim=3, lo=mesh.lo, size=mesh.size, p=mesh.p, extent=mesh.extent,
+                          lattice_h=mesh.lattice_h, corners=np.zeros((4, 2)))
+    with pytest.raises(B.DGError) as e:
+        B.HostSetup(bad, B.make_options())
+    assert e.value.code == B.DG_EUNSUPPORTED
