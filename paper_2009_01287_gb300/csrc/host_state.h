@@ -267,7 +267,9 @@ void host_element_diag_map(const dg_mesh& M, int64_t k, double* d);
 void host_lor_block_map(const dg_mesh& M, int64_t k, double* A);
 // rows of element k of y = A x (x: full host vector), same formulation as the kernel
 void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double* y);
-void host_element_residual3(const dg_mesh& M, int64_t k, const double* x, double* y);
+// (source >= 0: x vanishes outside element `source`, and the terms that are
+// exact zeros then are skipped; the result is the same)
+void host_element_residual3(const dg_mesh& M, int64_t k, const double* x, double* y, int64_t source = -1);
 // load vector of caller-supplied f (volume) and boundary data g (SIPG, weak)
 // into hb (n_dofs doubles); either may be null
 void host_load(const dg_mesh& M, dg_field_fn f, dg_field_fn g, void* ctx, double* hb);

@@ -412,7 +412,7 @@ void build_mesh_host3(dg_mesh* M, const dg_mesh_desc* desc, const dg_options& o)
 
 // Rows of element k of y = A x on a cube mesh, with the records and tables the
 // kernel uses and the same algebra, written as plain loops.
-void host_element_residual3(const dg_mesh& M, int64_t k, const double* x, double* y) {
+void host_element_residual3(const dg_mesh& M, int64_t k, const double* x, double* y, int64_t source) {
   const HostMesh& m = M.host;
   const int P = m.p[k], NP = P + 1, N2 = NP * NP, N3 = N2 * NP;
   const Basis1D& B = basis1d(P);
@@ -420,10 +420,14 @@ void host_element_residual3(const dg_mesh& M, int64_t k, const double* x, double
   const double* xk = x + m.off[k];
   const double* T = M.h_tables.data();
   const bool br2 = M.opts.form == DG_FORM_BR2;
+  // x vanishes outside element `source` (when >= 0): on another element k the
+  // volume term and every sub-face not shared with `source` add exact zeros
+  const bool own_zero = source >= 0 && source != k;
+  if (own_zero) std::fill(y, y + N3, 0.0);
   // volume: h (K x M x M + M x K x M + M x M x K) x, index ix + NP (iy + NP iz),
   // sum factorised: along z A = M x, Bz = K x; along y C = M A, D = K A + M Bz;
   // along x y = h (K C + M D)
-  {
+  if (!own_zero) {
     double A[kMaxN * kMaxN * kMaxN], Bz[kMaxN * kMaxN * kMaxN];
     double C[kMaxN * kMaxN * kMaxN], D[kMaxN * kMaxN * kMaxN];
     for (int iz = 0; iz < NP; ++iz)
@@ -510,6 +514,7 @@ void host_element_residual3(const dg_mesh& M, int64_t k, const double* x, double
     trace(k, s, uo, dno);
     for (int j = m.sf_ptr[6 * k + s]; j < m.sf_ptr[6 * k + s + 1]; ++j) {
       const SubFaceRec3& f = M.h_sf3[j];
+      if (own_zero && f.nb != source) continue;
       const double ar = f.area;
       contract(f.tab_oo[0], f.tab_oo[1], NP, NP, false, uo, a);
       contract(f.tab_oo[0], f.tab_oo[1], NP, NP, false, dno, c);
