@@ -11,7 +11,7 @@
 
 namespace dg {
 
-void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double* y) {
+void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double* y, int64_t source) {
   if (M.host.mapped) {
     host_element_residual_map(M, k, x, y);
     return;
@@ -20,10 +20,14 @@ void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double*
   const int P = m.p[k], NP = P + 1, NN = NP * NP;
   const Basis1D& B = basis1d(P);
   const double hk = M.h_h[k], ak = m.coef[k];
+  // x vanishes outside element `source` (when >= 0): on another element the
+  // volume term and every sub-face not shared with `source` add exact zeros
+  const bool own_zero = source >= 0 && source != k;
   const double* xk = x + m.off[k];
   auto sn = [](int s, int i, int q, int np) { return (s < 2) ? (i * np + q) : (q * np + i); };
   // volume: (K (x) M + M (x) K) x  with local index iy*NP + ix, two passes
-  {
+  if (own_zero) std::fill(y, y + NN, 0.0);
+  else {
     double t1[kMaxN * kMaxN], t2[kMaxN * kMaxN];
     for (int qy = 0; qy < NP; ++qy)
       for (int ix = 0; ix < NP; ++ix) {
@@ -55,6 +59,7 @@ void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double*
     const int kedge = (s & 1) ? P : 0;
     for (int j = m.sf_ptr[4 * k + s]; j < m.sf_ptr[4 * k + s + 1]; ++j) {
       const SubFaceRec& f = M.h_sf[j];
+      if (own_zero && f.nb != source) continue;
       double un[kMaxN] = {0.0}, dnn[kMaxN] = {0.0};
       int np = 0;
       if (f.nb >= 0) {

@@ -266,7 +266,7 @@ void host_element_residual_map(const dg_mesh& M, int64_t k, const double* x, dou
 void host_element_diag_map(const dg_mesh& M, int64_t k, double* d);
 void host_lor_block_map(const dg_mesh& M, int64_t k, double* A);
 // rows of element k of y = A x (x: full host vector), same formulation as the kernel
-void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double* y);
+void host_element_residual(const dg_mesh& M, int64_t k, const double* x, double* y, int64_t source = -1);
 // (source >= 0: x vanishes outside element `source`, and the terms that are
 // exact zeros then are skipped; the result is the same)
 void host_element_residual3(const dg_mesh& M, int64_t k, const double* x, double* y, int64_t source = -1);

@@ -337,7 +337,7 @@ HostPrecond build_host_precond(const dg_mesh& M, const dg_options& o) {
       near.erase(std::unique(near.begin(), near.end()), near.end());
       for (int64_t k : near) {
         if (!std::binary_search(uel.begin(), uel.end(), k)) continue;
-        host_element_residual(M, k, x.data(), y.data());
+        host_element_residual(M, k, x.data(), y.data(), kb);   // x = e_b lives in kb
         for (int a = 0; a < d; ++a)
           if (el[a] == k) Ab[(int64_t)a * d + b] = y[blk[a] - m.off[k]];
       }
