@@ -21,7 +21,8 @@ Beside it the same line carries
   workloads     sub-lines with their own clocks: the same mesh with BR2, the
                 16^3 cube workload, the same mesh carried onto a general
                 quadrilateral and onto a curved domain (mapped elements),
-                the batched form (256
+                the hp-AMR sequences of the L-shape and internal-layer
+                problems, the batched form (256
                 problems x 4 right-hand sides in one launch) and a bounded
                 sample of the served form.
 --workload hp2d-br2 | hp2d-coef | hp2d-map | hp2d-curved | hp3d | batched | serving runs one of them as
@@ -693,6 +694,11 @@ def run_ours(args):
             hw.pop(k, None)
         extras["hp2d_curved"] = {"workload": WORKLOADW, "metric": "DOF-iters/s",
                                  "value": hw["dof_iters_per_s_mixed"], **hw}
+        for which in ("lshape", "layer"):   # the adaptive problems of Section 4.2
+            try:
+                extras[f"amr_{which}"] = amr_leg(B, torch, which, 20)
+            except Exception as exc:   # noqa: BLE001 - recorded, the line still prints
+                extras[f"amr_{which}"] = {"error": f"{type(exc).__name__}: {exc}"}
         extras["batched"] = run_batched_leg(B, ctx, 2, 1)
         extras["serving"] = run_serving_leg(B, 8, 160, 200.0, 8)
         out["workloads"] = extras
@@ -735,20 +741,15 @@ def run_batched(args):
     print(json.dumps(out))
 
 
-def run_amr(args):
-    """hp-adaptive refinement of the internal-layer or the L-shape problem (Section 4.2):
-    `--amr-steps` refinements after the first solve, every solve through the C
-    ABI (mixed-precision B = B_B + B_C, and FP64 B~ = J_B + B_C for the
-    iteration column the paper reports beside it)."""
-    import torch
-
+def amr_leg(B, torch, which: str, n_steps: int) -> dict:
+    """The AMR sequence of one problem of Section 4.2 (`which`: "lshape" or
+    "layer") through the C ABI: mixed-precision solves with B = B_B + B_C
+    drive the refinement, and every step also solves with FP64 B~ = J_B + B_C
+    for the iteration column the paper reports beside it."""
     from paper_2009_01287_gb300 import amr
-    from paper_2009_01287_gb300 import binding as B
-    torch.cuda.set_device(0)
-    problem = amr.LSHAPE if args.workload == "amr-lshape" else amr.LAYER
+    problem = amr.LSHAPE if which == "lshape" else amr.LAYER
     mixed = amr.library_solver(B, torch, precision=B.DG_PREC_MIXED, with_jacobi=False, problem=problem)
     b_tilde = amr.library_solver(B, torch, with_jacobi=True, problem=problem)
-    steps = []
 
     def solve(mesh):
         x, info = mixed(mesh)
@@ -757,20 +758,33 @@ def run_amr(args):
 
     clocks = ClockSampler(0).start()
     t0 = time.perf_counter()
-    recs = amr.run(solve, steps=args.amr_steps, callback=lambda m, x, r: steps.append(r), problem=problem)
+    recs = amr.run(solve, steps=n_steps, problem=problem)
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     di = sum(r.n_dofs * r.iters for r in recs)
     ms = sum(r.solve_ms for r in recs)
-    out = {"metric": "DOF-iters/s over the solves of the AMR sequence (mixed FP32 preconditioner / FP64 outer)",
-           "value": di / (ms / 1e3), "unit": "DOF-iters/s", "n_gpus": 1, "steps": len(recs), "warmup": 0,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64 (outer PCG, operator) + f32 (preconditioner)", "data": "synthetic",
-           "config": {"workload": f"hp-AMR of the {problem.name}, {problem.initial().n_elems} p=1 squares to "
-                                  f"start, {args.amr_steps} refinements, SIPG eta=100, tol 1e-8, weak Dirichlet "
-                                  "data"},
-           "wall_s_with_setup": wall,
-           "table": [dataclasses.asdict(r) for r in recs], "clocks": clk}
+    return {"workload": f"hp-AMR of the {problem.name}, {problem.initial().n_elems} p=1 squares to start, "
+                        f"{n_steps} refinements, SIPG eta=100, tol 1e-8, weak Dirichlet data",
+            "metric": "DOF-iters/s over the solves of the AMR sequence (mixed FP32 preconditioner / FP64 outer)",
+            "value": di / (ms / 1e3), "wall_s_with_setup": wall,
+            "table": [dataclasses.asdict(r) for r in recs], "clocks": clk}
+
+
+def run_amr(args):
+    """hp-adaptive refinement of the internal-layer or the L-shape problem (Section 4.2):
+    `--amr-steps` refinements after the first solve, every solve through the C
+    ABI (mixed-precision B = B_B + B_C, and FP64 B~ = J_B + B_C for the
+    iteration column the paper reports beside it)."""
+    import torch
+
+    from paper_2009_01287_gb300 import binding as B
+    torch.cuda.set_device(0)
+    leg = amr_leg(B, torch, "lshape" if args.workload == "amr-lshape" else "layer", args.amr_steps)
+    out = {"metric": leg["metric"], "value": leg["value"], "unit": "DOF-iters/s", "n_gpus": 1,
+           "steps": len(leg["table"]), "warmup": 0, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64 (outer PCG, operator) + f32 (preconditioner)", "data": "synthetic",
+           "config": {"workload": leg["workload"]}, "wall_s_with_setup": leg["wall_s_with_setup"],
+           "table": leg["table"], "clocks": leg["clocks"]}
     print(json.dumps(out))
 
 
