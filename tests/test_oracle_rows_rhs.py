@@ -36,6 +36,25 @@ def test_element_rows_equal_assembled_rows(dim, form, coef):
         assert np.abs(yk - y[space.dofs(k)]).max() <= 1e-12 * scale, k
 
 
+@pytest.mark.parametrize("geom", ["quad", "wavy", "lshape"])
+@pytest.mark.parametrize("form", ["sipg", "br2"])
+def test_element_rows_equal_assembled_rows_mapped(geom, form):
+    """The same on mapped, curved and L-shaped meshes (the full-size GPU tests
+    of those check sampled elements against element_rows)."""
+    mesh = inputs.small_hp_mesh(6, base=4, depth=2, prob=0.45, pmin=1, pmax=5)
+    mesh = {"quad": lambda: inputs.with_corners(mesh, inputs.QUADRILATERAL),
+            "wavy": lambda: inputs.with_mapping(mesh, inputs.WavyMap()),
+            "lshape": lambda: inputs.lshape(mesh)}[geom]()
+    topo, space, A = solver.build_operator(mesh, form=form)
+    eta = dg.br2_eta(topo) if form == "br2" else 100.0
+    x = inputs.random_vector(space.n, 12)
+    y = A @ x
+    scale = np.abs(y).max()
+    for k in range(topo.n):
+        yk = dg.element_rows(space, k, x, eta, form=form)
+        assert np.abs(yk - y[space.dofs(k)]).max() <= 1e-12 * scale, k
+
+
 # ---------------------------------------------------------------- load vector
 
 # Gauss-Lobatto points on [0,1] in closed form (the golden file
