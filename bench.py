@@ -183,7 +183,7 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def survey_model_flops(mesh) -> float:
+def scope_model_flops(mesh) -> float:
     """FP64 flops of one operator apply by the scope table's model: 8(p+1)
     flop/DOF of sum-factorised volume work plus 64/(p+1) per DOF of face work
     (2D), i.e. 8 n^3 + 64 n per element of n = p+1 nodes per direction."""
@@ -268,8 +268,8 @@ def operator_rooflines(B, ctx, M, mesh, peak_tf, peaks, three, tkey, mapped=Fals
             "frac": ach / peak_tf, "traffic": traffic(tkey),
             "flops_per_launch": kfl, "launch_ms": apply_ms,
             "flops_model": model,
-            "flops_survey_model_per_launch": survey_model_flops(mesh) if separable else None,
-            "frac_survey_model": (survey_model_flops(mesh) / (apply_ms / 1e3) / 1e12 / peak_tf
+            "flops_scope_model_per_launch": scope_model_flops(mesh) if separable else None,
+            "frac_scope_model": (scope_model_flops(mesh) / (apply_ms / 1e3) / 1e12 / peak_tf
                                   if separable else None),
             "algorithmic_bytes": st.apply_bytes,
             "hbm_gbs": st.apply_bytes / (apply_ms / 1e3) / 1e9,
