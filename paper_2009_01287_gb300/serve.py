@@ -79,11 +79,20 @@ class Result:
 
 
 def mesh_key(m: MeshDesc) -> str:
+    """Cache key of a mesh: its boxes, degrees, coefficient and geometry (the
+    corners' values; a caller's map by the identity of the map object, which
+    must not change while the server holds the mesh)."""
     h = hashlib.sha1()
     for a in (m.lo, m.size, m.p, np.asarray(m.extent)):
         h.update(np.ascontiguousarray(a).tobytes())
     if m.coeff is not None:
-        h.update(np.ascontiguousarray(m.coeff).tobytes())
+        h.update(b"coeff")
+        h.update(np.ascontiguousarray(m.coeff, dtype=np.float64).tobytes())
+    if getattr(m, "corners", None) is not None:
+        h.update(b"corners")
+        h.update(np.ascontiguousarray(m.corners, dtype=np.float64).tobytes())
+    if getattr(m, "mapping", None) is not None:
+        h.update(b"map%d" % id(m.mapping))
     h.update(repr((m.dim, m.lattice_h)).encode())
     return h.hexdigest()
 
