@@ -189,7 +189,7 @@ def refine(mesh: inputs.MeshDesc, h_mark: np.ndarray, p_mark: np.ndarray) -> inp
     ext, lh = np.asarray(mesh.extent, dtype=np.int64), float(mesh.lattice_h)
     if np.any(h_mark & (size == 1)):
         lo, size, ext, lh = lo * 2, size * 2, ext * 2, lh / 2.0
-    nlo, nsz, npp = [], [], []
+    nlo, nsz, npp, parent = [], [], [], []
     for k in range(mesh.n_elems):
         if h_mark[k]:
             s = size[k] // 2
@@ -198,13 +198,19 @@ def refine(mesh: inputs.MeshDesc, h_mark: np.ndarray, p_mark: np.ndarray) -> inp
                     nlo.append((lo[k, 0] + dx * s, lo[k, 1] + dy * s))
                     nsz.append(s)
                     npp.append(p[k])
+                    parent.append(k)
         else:
             nlo.append((lo[k, 0], lo[k, 1]))
             nsz.append(size[k])
             npp.append(min(P_MAX, p[k] + 1) if p_mark[k] else p[k])
+            parent.append(k)
+    # children keep their parent's coefficient; the domain's geometry (corners
+    # or map, on the same physical domain) is unchanged by the lattice halving
+    coeff = None if mesh.coeff is None else np.asarray(mesh.coeff, dtype=np.float64)[parent]
     return inputs.MeshDesc(dim=2, lo=np.asarray(nlo, dtype=np.int32).reshape(-1, 2),
                            size=np.asarray(nsz, dtype=np.int32), p=np.asarray(npp, dtype=np.int32),
-                           extent=tuple(int(e) for e in ext), lattice_h=lh)
+                           extent=tuple(int(e) for e in ext), lattice_h=lh, coeff=coeff,
+                           corners=mesh.corners, mapping=mesh.mapping)
 
 
 def decide(mesh: inputs.MeshDesc, mark: np.ndarray, ratio: np.ndarray, base_size: float):

@@ -116,3 +116,13 @@ def test_amr_lshape_steps_with_the_oracle():
     assert recs[0].n_dofs == 48 and recs[-1].n_dofs > 48
     assert recs[-1].err_l2 < recs[0].err_l2
     assert max(r.iters for r in recs) < 100
+
+
+def test_refine_keeps_coefficient_and_geometry():
+    mesh = inputs.with_coeff(inputs.uniform_mesh(2, 2, 1), [1.0, 2.0, 3.0, 4.0])
+    mesh = inputs.with_corners(mesh, inputs.QUADRILATERAL)
+    m2 = amr.refine(mesh, np.array([False, True, False, False]), np.array([True, False, False, False]))
+    assert m2.coeff.tolist() == [1.0, 2.0, 2.0, 2.0, 2.0, 3.0, 4.0]
+    assert np.array_equal(m2.corners, mesh.corners)
+    # the physical domain is the same: the lattice doubled, its spacing halved
+    assert m2.extent[0] * m2.lattice_h == mesh.extent[0] * mesh.lattice_h
