@@ -89,7 +89,7 @@ TRAFFIC = {
                                       "paper_2009_01287_gb300/csrc/apply_launch.cu",
                                       "paper_2009_01287_gb300/csrc/dg_internal.h",
                                       "paper_2009_01287_gb300/csrc/mesh.cpp"],
-                          "sha256_16": "1d706091b138a282", "bytes": 3550208},
+                          "sha256_16": "cc1d2ecc3337aba4", "bytes": 3550208},
     "apply3_kernel/hp3d": {"sources": ["paper_2009_01287_gb300/csrc/apply_kernel.cuh",
                                        "paper_2009_01287_gb300/csrc/apply3_kernel.cuh",
                                        "paper_2009_01287_gb300/csrc/apply_launch.cu",
@@ -104,7 +104,7 @@ TRAFFIC = {
                                               "paper_2009_01287_gb300/csrc/apply_launch.cu",
                                               "paper_2009_01287_gb300/csrc/dg_internal.h",
                                               "paper_2009_01287_gb300/csrc/mesh_map.cpp"],
-                                  "sha256_16": "26d3dd4699954ae0", "bytes": 10816000},
+                                  "sha256_16": "a0ee107b47d30eb9", "bytes": 10816000},
 }
 
 
