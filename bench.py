@@ -95,7 +95,7 @@ TRAFFIC = {
                                        "paper_2009_01287_gb300/csrc/apply_launch.cu",
                                        "paper_2009_01287_gb300/csrc/dg_internal.h",
                                        "paper_2009_01287_gb300/csrc/mesh3.cpp"],
-                           "sha256_16": "59ee544008bde113",
+                           "sha256_16": "83a21a1d591c4a38",
                            # captured on the same recipe at a 10^3 base (428,796 DOFs), scaled
                            # by the DOFs to the 16^3 workload (1,706,529 DOFs)
                            "bytes": 16861440 * 1706529 // 428796},
