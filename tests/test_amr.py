@@ -126,3 +126,23 @@ def test_refine_keeps_coefficient_and_geometry():
     assert np.array_equal(m2.corners, mesh.corners)
     # the physical domain is the same: the lattice doubled, its spacing halved
     assert m2.extent[0] * m2.lattice_h == mesh.extent[0] * mesh.lattice_h
+
+
+def test_l2_indicator_is_exact_on_polynomials():
+    """eta_k = ||u - u_h||_L2(k): zero when u_h interpolates a polynomial of
+    degree <= p exactly, and the element's area^(1/2) * |c| for u - u_h = c."""
+    mesh = inputs.small_hp_mesh(3, base=3, depth=2, prob=0.5, pmin=2, pmax=4)
+    off = np.concatenate([[0], np.cumsum((mesh.p.astype(np.int64) + 1) ** 2)])
+    u = lambda x: 1.0 + x[:, 0] * x[:, 1] - 0.5 * x[:, 1] ** 2
+    x = np.zeros(off[-1])
+    h = mesh.size * mesh.lattice_h
+    for k in range(mesh.n_elems):
+        g = amr._gll(int(mesh.p[k]))
+        X, Y = np.meshgrid(g, g)
+        pts = np.stack([mesh.lo[k, 0] * mesh.lattice_h + h[k] * X.ravel(),
+                        mesh.lo[k, 1] * mesh.lattice_h + h[k] * Y.ravel()], axis=1)
+        x[off[k]:off[k + 1]] = u(pts)
+    eta, _ = amr.element_indicators(mesh, x, exact=u)
+    assert eta.max() <= 1e-13
+    eta, _ = amr.element_indicators(mesh, x, exact=lambda p: u(p) + 0.25)
+    assert np.abs(eta - 0.25 * h).max() <= 1e-13
