@@ -1,5 +1,7 @@
 """Deterministic smoothed-aggregation AMG for the LOR conforming matrix.
 
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
 The paper approximates the inverse of the LOR matrix by one V-cycle of
 BoomerAMG (Section 3.4 and Section 4.1) without giving its parameters.  This
 oracle instead fixes one plain algorithm (the same one the CUDA library sets

@@ -1,5 +1,7 @@
 """1D polynomial machinery on the reference interval [0, 1] (Section 2.2).
 
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
 The nodal basis of Section 2.2 is the Lagrange basis at the p+1 Gauss-Lobatto
 points.  Exact integration uses Gauss-Legendre rules.  Everything here is the
 textbook definition written out; numpy's Legendre module supplies roots and

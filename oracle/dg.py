@@ -1,6 +1,8 @@
 """Explicit assembly of the DG stiffness matrix (Section 2, Eq. fe-problem;
 BR2 form of Section 4.4), on squares (2D) or cubes (3D).
 
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
 Global numbering: element-major, element k owns (p_k+1)^d consecutive DOFs;
 inside an element the nodal DOF (ix, iy[, iz]) has local index
 ix + (p+1) iy [+ (p+1)^2 iz], with the Gauss-Lobatto nodes of Section 2.2 in

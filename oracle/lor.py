@@ -1,5 +1,7 @@
 """Low-order-refined matrices (Section 3.4).
 
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
 For element k of degree p the LOR element matrix is the (bi/tri)linear (Q1)
 finite element stiffness matrix on the Cartesian sub-mesh whose vertices are
 the (p+1)^d Gauss-Lobatto nodes of k.  A-tilde is block diagonal with these

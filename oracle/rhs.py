@@ -1,7 +1,12 @@
-"""Load vector b_i = int f phi_i of the synthetic sine right-hand side
-(Eq. fe-problem, right-hand side), with a (p+3)-point Gauss rule per
-direction on each element (on mapped elements: in the pre-image, f taken at
-the physical points, the weights carrying det J)."""
+"""Load vectors b_i = int f phi_i (Eq. fe-problem, right-hand side) of the
+synthetic sine right-hand side and of any f given as a function, with a
+(p+3)-point Gauss rule per direction on each element (on mapped elements: in
+the pre-image, f taken at the physical points, the weights carrying det J);
+and the load vector with inhomogeneous Dirichlet data imposed weakly by SIPG
+(the boundary terms that u = g moves to the right-hand side).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+"""
 from __future__ import annotations
 
 import numpy as np

@@ -1,6 +1,8 @@
 """The additive subspace-correction preconditioner and PCG (Sections 3.1, 3.3,
 3.4, 4.1).
 
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
 B r = P M_C P^T r + sum_e R_e^T A_e^{-1} R_e r + sum_{j in J} r_j / A_jj e_j
 (Section 3.1: B = sum_i R_i Q_i with exact solves on V_e and on the 1D spaces
 V_j; Section 4.1: B = B_B + B_C).  M_C is either the exact inverse of the LOR

@@ -1,5 +1,7 @@
 """Conforming prolongation and the boundary-space decomposition (Section 3).
 
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
 Conforming basis (Section 3.2.1, conforming nodal points): Lagrange basis at
 * every regular vertex not on the boundary (V_C is read as V_h cap H^1_0,
   since the problem has homogeneous Dirichlet conditions),

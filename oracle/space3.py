@@ -1,6 +1,8 @@
 """Conforming prolongation and the V_J / V_e split on box meshes of any
 dimension, built from master entities (Section 3, read for hexahedra).
 
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
 The paper states Section 3 for quadrilaterals.  Here every closed element is
 split into entities (vertices, edges, faces, the interior: the boxes obtained
 by fixing each axis at the lower end, the upper end, or letting it span), and

@@ -1,5 +1,7 @@
 """Mesh topology of a 2D leaf-box mesh, computed by brute force (Section 2, 3.2).
 
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
 Elements are axis-aligned squares on an integer lattice.  A side s of an
 element is 0: left (x = x0), 1: right, 2: bottom (y = y0), 3: top.  On a side
 the tangential coordinate t runs along the other axis, increasing.

@@ -1,5 +1,7 @@
 """Sub-faces of a 3D leaf-box mesh (Section 2, read for hexahedra).
 
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
 The paper states the method for quadrilaterals; in three dimensions the same
 definitions hold with the faces of axis-aligned cubes: a sub-face is a maximal
 rectangle shared by the upper face of one element and the lower face of a
