@@ -130,8 +130,11 @@ def _legendre_vandermonde(p: int) -> np.ndarray:
 def element_indicators(mesh: inputs.MeshDesc, x: np.ndarray, exact: Callable = layer_u):
     """Per element: eta = ||u - u_h||_L2(element) by the (p+3)-point Gauss
     rule per direction, and the last-shell ratio of the tensor Legendre
-    coefficients of u_h (1 for p = 1)."""
+    coefficients of u_h (1 for p = 1).  Squares only: the Gauss points are
+    placed on the leaf boxes themselves."""
     from numpy.polynomial import legendre as Lg
+    if mesh.corners is not None or mesh.mapping is not None:
+        raise ValueError("AMR indicators are defined on meshes of squares (no corners or map)")
     n = mesh.n_elems
     eta = np.zeros(n)
     ratio = np.ones(n)

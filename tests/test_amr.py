@@ -146,3 +146,11 @@ def test_l2_indicator_is_exact_on_polynomials():
     assert eta.max() <= 1e-13
     eta, _ = amr.element_indicators(mesh, x, exact=lambda p: u(p) + 0.25)
     assert np.abs(eta - 0.25 * h).max() <= 1e-13
+
+
+def test_indicators_refuse_mapped_meshes():
+    mesh = inputs.uniform_mesh(2, 2, 2)
+    x = np.zeros(mesh.n_dofs())
+    for m in (inputs.with_corners(mesh, inputs.QUADRILATERAL), inputs.with_mapping(mesh, inputs.WavyMap())):
+        with pytest.raises(ValueError):
+            amr.element_indicators(m, x)
