@@ -588,13 +588,13 @@ HostPrecond build_host_precond3(const dg_mesh& M, const dg_options& o) {
     auto elem_of = [&](int64_t r) {
       return (int64_t)(std::upper_bound(m.off.begin(), m.off.end(), r) - m.off.begin() - 1);
     };
-    const int nth = std::max(1, std::min<int>((int)H.blocks.size(),
-                                              (int)std::thread::hardware_concurrency()));
+    const int nth = std::max(1, std::min<int>((int)H.blocks.size(), setup_threads()));
     std::vector<std::thread> pool;
     std::vector<std::string> errs(nth);
     for (int t = 0; t < nth; ++t)
       pool.emplace_back([&, t] {
         try {
+          SerialSetup serial;   // one block per thread already
           std::vector<double> x(n, 0.0), y((size_t)kMaxN * kMaxN * kMaxN);
           for (size_t bi = t; bi < H.blocks.size(); bi += nth) {
             const auto& blk = H.blocks[bi];

@@ -17,6 +17,8 @@
 #include <cmath>
 #include <functional>
 #include <numeric>
+#include <string>
+#include <thread>
 #include <unordered_map>
 #include <chrono>
 #include <cstdio>
@@ -303,7 +305,7 @@ HostPrecond build_host_precond(const dg_mesh& M, const dg_options& o) {
   lap("components");
   // ---- entries of A: diagonal on V_J and the V_e blocks, read off element rows
   H.dinv.assign(n, 0.0);
-  std::vector<double> x(n, 0.0), y((kMaxN) * (kMaxN));
+  std::vector<double> y((kMaxN) * (kMaxN));
   for (int64_t k = 0; k < m.n; ++k) {
     const int P = m.p[k], NN = (P + 1) * (P + 1);
     host_element_diag(M, k, y.data());
@@ -318,39 +320,67 @@ HostPrecond build_host_precond(const dg_mesh& M, const dg_options& o) {
   auto elem_of = [&](int64_t r) {
     return (int64_t)(std::upper_bound(m.off.begin(), m.off.end(), r) - m.off.begin() - 1);
   };
-  for (auto& blk : H.blocks) {
-    const int d = (int)blk.size();
-    std::vector<double> Ab((int64_t)d * d, 0.0);
-    std::vector<int64_t> el(d);
-    for (int a = 0; a < d; ++a) el[a] = elem_of(blk[a]);
-    std::vector<int64_t> uel(el);
-    std::sort(uel.begin(), uel.end());
-    uel.erase(std::unique(uel.begin(), uel.end()), uel.end());
-    for (int b = 0; b < d; ++b) {
-      x[blk[b]] = 1.0;
-      const int64_t kb = el[b];
-      // rows that can see column b: its own element and the elements sharing a sub-face
-      std::vector<int64_t> near{kb};
-      for (int j = m.sf_ptr[4 * kb]; j < m.sf_ptr[4 * kb + 4]; ++j)
-        if (m.sf[j].nb >= 0) near.push_back(m.sf[j].nb);
-      std::sort(near.begin(), near.end());
-      near.erase(std::unique(near.begin(), near.end()), near.end());
-      for (int64_t k : near) {
-        if (!std::binary_search(uel.begin(), uel.end(), k)) continue;
-        host_element_residual(M, k, x.data(), y.data(), kb);   // x = e_b lives in kb
-        for (int a = 0; a < d; ++a)
-          if (el[a] == k) Ab[(int64_t)a * d + b] = y[blk[a] - m.off[k]];
+  // one block at a time per thread (each block's entries and inverse are
+  // computed the same way on any thread)
+  H.block_inv.resize(H.blocks.size());
+  auto block_range = [&](size_t first, size_t step) {
+    SerialSetup serial;
+    std::vector<double> xs(n, 0.0), ys((kMaxN) * (kMaxN));
+    for (size_t bi = first; bi < H.blocks.size(); bi += step) {
+      const auto& blk = H.blocks[bi];
+      const int d = (int)blk.size();
+      std::vector<double> Ab((int64_t)d * d, 0.0);
+      std::vector<int64_t> el(d);
+      for (int a = 0; a < d; ++a) el[a] = elem_of(blk[a]);
+      std::vector<int64_t> uel(el);
+      std::sort(uel.begin(), uel.end());
+      uel.erase(std::unique(uel.begin(), uel.end()), uel.end());
+      for (int b = 0; b < d; ++b) {
+        xs[blk[b]] = 1.0;
+        const int64_t kb = el[b];
+        // rows that can see column b: its own element and the elements sharing a sub-face
+        std::vector<int64_t> near{kb};
+        for (int j = m.sf_ptr[4 * kb]; j < m.sf_ptr[4 * kb + 4]; ++j)
+          if (m.sf[j].nb >= 0) near.push_back(m.sf[j].nb);
+        std::sort(near.begin(), near.end());
+        near.erase(std::unique(near.begin(), near.end()), near.end());
+        for (int64_t k : near) {
+          if (!std::binary_search(uel.begin(), uel.end(), k)) continue;
+          host_element_residual(M, k, xs.data(), ys.data(), kb);   // x = e_b lives in kb
+          for (int a = 0; a < d; ++a)
+            if (el[a] == k) Ab[(int64_t)a * d + b] = ys[blk[a] - m.off[k]];
+        }
+        xs[blk[b]] = 0.0;
       }
-      x[blk[b]] = 0.0;
+      // symmetrise the round-off before the inverse
+      for (int a = 0; a < d; ++a)
+        for (int b = a + 1; b < d; ++b) {
+          const double s = 0.5 * (Ab[(int64_t)a * d + b] + Ab[(int64_t)b * d + a]);
+          Ab[(int64_t)a * d + b] = Ab[(int64_t)b * d + a] = s;
+        }
+      dense_inverse_spd(d, Ab);
+      H.block_inv[bi] = std::move(Ab);
     }
-    // symmetrise the round-off before the inverse
-    for (int a = 0; a < d; ++a)
-      for (int b = a + 1; b < d; ++b) {
-        const double s = 0.5 * (Ab[(int64_t)a * d + b] + Ab[(int64_t)b * d + a]);
-        Ab[(int64_t)a * d + b] = Ab[(int64_t)b * d + a] = s;
-      }
-    dense_inverse_spd(d, Ab);
-    H.block_inv.push_back(std::move(Ab));
+  };
+  {
+    const int nth = H.blocks.size() >= 64 ? std::min<int>((int)H.blocks.size(), setup_threads()) : 1;
+    if (nth <= 1) {
+      block_range(0, 1);
+    } else {
+      std::vector<std::thread> pool;
+      std::vector<std::string> errs(nth);
+      for (int t = 0; t < nth; ++t)
+        pool.emplace_back([&, t] {
+          try {
+            block_range((size_t)t, (size_t)nth);
+          } catch (const std::exception& e) {
+            errs[t] = e.what();
+          }
+        });
+      for (auto& th : pool) th.join();
+      for (auto& e : errs)
+        if (!e.empty()) throw Error(DG_EINVAL, e);
+    }
   }
   lap("blocks");
   // ---- LOR: Q1 stiffness on the Gauss-Lobatto sub-grid of each element

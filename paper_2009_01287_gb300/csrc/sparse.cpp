@@ -114,6 +114,10 @@ thread_local bool t_serial = false;
 SerialSetup::SerialSetup() : prev(t_serial) { t_serial = true; }
 SerialSetup::~SerialSetup() { t_serial = prev; }
 
+int setup_threads() {
+  return t_serial ? 1 : (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+}
+
 Csr csr_multiply(const Csr& A, const Csr& B) {
   Csr C;
   C.rows = A.rows;
@@ -122,9 +126,7 @@ Csr csr_multiply(const Csr& A, const Csr& B) {
   // large products are split into row ranges of about equal work (A's
   // nonzeros) computed by threads; every row is computed exactly as in one
   // pass, so the result does not depend on the split
-  int nth = 1;
-  if (!t_serial && A.nnz() > (1 << 16))
-    nth = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  const int nth = A.nnz() > (1 << 16) ? setup_threads() : 1;
   if (nth <= 1) {
     std::vector<int64_t> cnt(A.rows);
     multiply_rows(A, B, 0, A.rows, cnt, C.idx, C.val);
@@ -156,36 +158,91 @@ Csr csr_multiply(const Csr& A, const Csr& B) {
 }
 
 void dense_inverse_spd(int n, std::vector<double>& a) {
-  // Cholesky A = L L^T, then A^-1 = L^-T L^-1 (column by column)
+  // Cholesky A = L L^T, then A^-1 = L^-T L^-1 column by column.  Every entry
+  // is one fixed sequence of operations (sums in ascending k); rows of L are
+  // formed four at a time and the columns of the inverse four at a time (on
+  // several threads when n is large) only to overlap independent sums, so the
+  // result does not depend on the grouping or the thread count.
   std::vector<double> L(a);
   for (int j = 0; j < n; ++j) {
-    double d = L[(int64_t)j * n + j];
-    for (int k = 0; k < j; ++k) d -= L[(int64_t)j * n + k] * L[(int64_t)j * n + k];
+    const double* Lj = &L[(int64_t)j * n];
+    double d = Lj[j];
+    for (int k = 0; k < j; ++k) d -= Lj[k] * Lj[k];
     if (!(d > 0.0)) throw Error(DG_EINVAL, "matrix not positive definite");
     d = std::sqrt(d);
     L[(int64_t)j * n + j] = d;
-    for (int i = j + 1; i < n; ++i) {
-      double s = L[(int64_t)i * n + j];
-      for (int k = 0; k < j; ++k) s -= L[(int64_t)i * n + k] * L[(int64_t)j * n + k];
-      L[(int64_t)i * n + j] = s / d;
+    int i = j + 1;
+    for (; i + 4 <= n; i += 4) {
+      double* R0 = &L[(int64_t)i * n];
+      double *R1 = R0 + n, *R2 = R1 + n, *R3 = R2 + n;
+      double s0 = R0[j], s1 = R1[j], s2 = R2[j], s3 = R3[j];
+      for (int k = 0; k < j; ++k) {
+        const double l = Lj[k];
+        s0 -= R0[k] * l;
+        s1 -= R1[k] * l;
+        s2 -= R2[k] * l;
+        s3 -= R3[k] * l;
+      }
+      R0[j] = s0 / d;
+      R1[j] = s1 / d;
+      R2[j] = s2 / d;
+      R3[j] = s3 / d;
+    }
+    for (; i < n; ++i) {
+      double* Ri = &L[(int64_t)i * n];
+      double s = Ri[j];
+      for (int k = 0; k < j; ++k) s -= Ri[k] * Lj[k];
+      Ri[j] = s / d;
     }
   }
-  std::vector<double> col(n);
-  for (int c = 0; c < n; ++c) {
-    // solve L y = e_c
-    for (int i = 0; i < n; ++i) {
-      double s = (i == c) ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) s -= L[(int64_t)i * n + k] * col[k];
-      col[i] = s / L[(int64_t)i * n + i];
+  // L^T row by row, so that the backward solves read contiguous memory
+  std::vector<double> Lt((int64_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int k = i; k < n; ++k) Lt[(int64_t)i * n + k] = L[(int64_t)k * n + i];
+  constexpr int W = 4;
+  auto solve_columns = [&](int c0, int c1) {
+    std::vector<double> col((int64_t)n * W);   // col[i * W + r]: column c + r
+    for (int c = c0; c < c1; c += W) {
+      const int w = std::min(W, c1 - c);
+      // L y = e_c
+      for (int i = 0; i < n; ++i) {
+        const double* Li = &L[(int64_t)i * n];
+        double s[W];
+        for (int r = 0; r < W; ++r) s[r] = (i == c + r) ? 1.0 : 0.0;
+        for (int k = 0; k < i; ++k) {
+          const double l = Li[k];
+          for (int r = 0; r < W; ++r) s[r] -= l * col[(int64_t)k * W + r];
+        }
+        for (int r = 0; r < W; ++r) col[(int64_t)i * W + r] = s[r] / Li[i];
+      }
+      // L^T z = y
+      for (int i = n - 1; i >= 0; --i) {
+        const double* Ti = &Lt[(int64_t)i * n];
+        double s[W];
+        for (int r = 0; r < W; ++r) s[r] = col[(int64_t)i * W + r];
+        for (int k = i + 1; k < n; ++k) {
+          const double l = Ti[k];
+          for (int r = 0; r < W; ++r) s[r] -= l * col[(int64_t)k * W + r];
+        }
+        for (int r = 0; r < W; ++r) col[(int64_t)i * W + r] = s[r] / Ti[i];
+      }
+      for (int i = 0; i < n; ++i)
+        for (int r = 0; r < w; ++r) a[(int64_t)i * n + c + r] = col[(int64_t)i * W + r];
     }
-    // solve L^T z = y
-    for (int i = n - 1; i >= 0; --i) {
-      double s = col[i];
-      for (int k = i + 1; k < n; ++k) s -= L[(int64_t)k * n + i] * col[k];
-      col[i] = s / L[(int64_t)i * n + i];
-    }
-    for (int i = 0; i < n; ++i) a[(int64_t)i * n + c] = col[i];
+  };
+  const int nth = n >= 256 ? setup_threads() : 1;
+  const int nblk = (n + W - 1) / W;
+  if (nth <= 1) {
+    solve_columns(0, n);
+    return;
   }
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nth; ++t) {
+    const int c0 = (int)((int64_t)nblk * t / nth) * W;
+    const int c1 = std::min(n, (int)((int64_t)nblk * (t + 1) / nth) * W);
+    if (c0 < c1) pool.emplace_back(solve_columns, c0, c1);
+  }
+  for (auto& th : pool) th.join();
 }
 
 namespace {

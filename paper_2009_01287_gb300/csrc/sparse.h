@@ -28,6 +28,9 @@ struct SerialSetup {
   ~SerialSetup();
   bool prev;
 };
+// Threads a setup step may use on this thread: 1 under SerialSetup, else the
+// hardware threads (at most 16).
+int setup_threads();
 
 // Deterministic smoothed-aggregation AMG hierarchy (setup only).
 struct AmgLevel {
