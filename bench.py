@@ -668,39 +668,32 @@ def run_ours(args):
             out["oracle_rel_err_mixed"] = out["oracle"]["rel_err_mixed"]
     if rank == 0 and ws == 1 and not args.no_extras and args.workload == "hp2d":
         extras = {}
-        mb, rb = inputs.config1(args.seed)
-        br2 = measure_single(B, ctx, mb, rb, B.DG_FORM_BR2, 3, 2, peaks, probe["tflops"], "none")
-        for k in ("_raw", "_e2e", "_x"):
-            br2.pop(k, None)
-        extras["hp2d_br2"] = {"workload": WORKLOAD_BR2, "metric": "DOF-iters/s",
-                              "value": br2["dof_iters_per_s_mixed"], **br2}
-        m3, r3 = inputs.config2(args.seed)
-        h3 = measure_single(B, ctx, m3, r3, B.DG_FORM_BR2, 3, 2, peaks, probe["tflops"], "apply3_kernel/hp3d",
-                            three=True)
-        for k in ("_raw", "_e2e", "_x"):
-            h3.pop(k, None)
-        extras["hp3d"] = {"workload": WORKLOAD3, "metric": "DOF-iters/s", "value": h3["dof_iters_per_s_mixed"],
-                          **h3}
-        mm, rm = inputs.config1_mapped(args.seed)
-        hm = measure_single(B, ctx, mm, rm, B.DG_FORM_SIPG, 3, 2, peaks, probe["tflops"],
-                            "apply_map_kernel/hp2d-map", mapped=True)
-        for k in ("_raw", "_e2e", "_x"):
-            hm.pop(k, None)
-        extras["hp2d_map"] = {"workload": WORKLOADM, "metric": "DOF-iters/s", "value": hm["dof_iters_per_s_mixed"],
-                              **hm}
-        mw, rw = inputs.config1_curved(args.seed)
-        hw = measure_single(B, ctx, mw, rw, B.DG_FORM_SIPG, 3, 2, peaks, probe["tflops"], "none", mapped=True)
-        for k in ("_raw", "_e2e", "_x"):
-            hw.pop(k, None)
-        extras["hp2d_curved"] = {"workload": WORKLOADW, "metric": "DOF-iters/s",
-                                 "value": hw["dof_iters_per_s_mixed"], **hw}
-        for which in ("lshape", "layer"):   # the adaptive problems of Section 4.2
+
+        def leg(name, fn):
+            # a failing sub-line is recorded as such; the main line still prints
             try:
-                extras[f"amr_{which}"] = amr_leg(B, torch, which, 20)
-            except Exception as exc:   # noqa: BLE001 - recorded, the line still prints
-                extras[f"amr_{which}"] = {"error": f"{type(exc).__name__}: {exc}"}
-        extras["batched"] = run_batched_leg(B, ctx, 2, 1)
-        extras["serving"] = run_serving_leg(B, 8, 160, 200.0, 8)
+                extras[name] = fn()
+            except Exception as exc:   # noqa: BLE001
+                extras[name] = {"error": f"{type(exc).__name__}: {exc}"}
+
+        def single(workload, mesh_rhs, form, traffic_key, **kw):
+            mesh, rhs_ = mesh_rhs
+            r = measure_single(B, ctx, mesh, rhs_, form, 3, 2, peaks, probe["tflops"], traffic_key, **kw)
+            for k in ("_raw", "_e2e", "_x"):
+                r.pop(k, None)
+            return {"workload": workload, "metric": "DOF-iters/s", "value": r["dof_iters_per_s_mixed"], **r}
+
+        leg("hp2d_br2", lambda: single(WORKLOAD_BR2, inputs.config1(args.seed), B.DG_FORM_BR2, "none"))
+        leg("hp3d", lambda: single(WORKLOAD3, inputs.config2(args.seed), B.DG_FORM_BR2, "apply3_kernel/hp3d",
+                                   three=True))
+        leg("hp2d_map", lambda: single(WORKLOADM, inputs.config1_mapped(args.seed), B.DG_FORM_SIPG,
+                                       "apply_map_kernel/hp2d-map", mapped=True))
+        leg("hp2d_curved", lambda: single(WORKLOADW, inputs.config1_curved(args.seed), B.DG_FORM_SIPG, "none",
+                                          mapped=True))
+        for which in ("lshape", "layer"):   # the adaptive problems of Section 4.2
+            leg(f"amr_{which}", lambda which=which: amr_leg(B, torch, which, 20))
+        leg("batched", lambda: run_batched_leg(B, ctx, 2, 1))
+        leg("serving", lambda: run_serving_leg(B, 8, 160, 200.0, 8))
         out["workloads"] = extras
     if rank == 0:
         print(json.dumps(out))
