@@ -104,7 +104,7 @@ TRAFFIC = {
                                               "paper_2009_01287_gb300/csrc/apply_launch.cu",
                                               "paper_2009_01287_gb300/csrc/dg_internal.h",
                                               "paper_2009_01287_gb300/csrc/mesh_map.cpp"],
-                                  "sha256_16": "a0ee107b47d30eb9", "bytes": 10816000},
+                                  "sha256_16": "297ed5dbf05f2fa2", "bytes": 10816000},
 }
 
 

@@ -312,8 +312,10 @@ dg_status dg_rhs_sine(const dg_mesh* mesh, int n_modes, const double* amps,
  * row-major, into out, n values), called on the calling thread during the
  * call; either may be NULL (no volume term / homogeneous data).  Quadrature:
  * p+3 Gauss points per direction on the volume and on each boundary
- * sub-face.  Square meshes; g needs an unmapped mesh and the SIPG form
- * (otherwise DG_EUNSUPPORTED).  A non-finite value from a callback is
+ * sub-face, at physical points (on mapped meshes the points, weights and
+ * normals were stored by dg_mesh_create, so the map is not called again).
+ * Square meshes, mapped or not; g needs the SIPG form (otherwise, and on
+ * cube meshes, DG_EUNSUPPORTED).  A non-finite value from a callback is
  * DG_EINVAL.  b: device; host arithmetic, synchronous on `stream`. */
 typedef void (*dg_field_fn)(int64_t n, const double* x, double* out, void* ctx);
 dg_status dg_rhs_eval(const dg_mesh* mesh, dg_field_fn f, dg_field_fn g, void* ctx, double* b,

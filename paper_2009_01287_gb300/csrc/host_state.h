@@ -134,6 +134,12 @@ struct dg_mesh {
   // later call needs the caller's map
   std::vector<double> h_xnode, h_xrhs;
   std::vector<int64_t> h_roff;
+  // host only: per boundary sub-face record j (h_boff[j] >= 0) at the p+3
+  // Gauss points of the element's degree along it: the image (x, y), the
+  // weight w |J t| dt and m = J^-1 n of the outward physical normal n (five
+  // values per point), for weakly imposed Dirichlet data on mapped meshes
+  std::vector<double> h_xbnd;
+  std::vector<int64_t> h_boff;
   int64_t apply3_smem = 0;              // dynamic shared memory of the 3D operator kernel
   std::vector<double> h_tables;
   dg::BasisOff boff[dg::kMaxP + 1];

@@ -328,6 +328,51 @@ void build_mesh_map(dg_mesh* M, const dg_mesh_desc* desc) {
     }
     M->h_roff[k + 1] = (int64_t)M->h_xrhs.size();
   }
+  // boundary sub-faces at the p+3 Gauss points of the element's degree: the
+  // image, the weight with the arc length and m = J^-1 n, n the outward
+  // physical normal (the boundary terms of weak Dirichlet data)
+  M->h_xbnd.clear();
+  M->h_boff.assign(m.sf.size(), -1);
+  for (int64_t k = 0; k < m.n; ++k)
+    for (int s = 0; s < 4; ++s) {
+      int axis, cc, t0, t1;
+      m.side_segment((int)k, s, axis, cc, t0, t1);
+      const double so = (s & 1) ? 1.0 : -1.0;
+      const int q = m.p[k] + 3;
+      std::vector<double> rx, rw;
+      gauss_rule(q, rx, rw);
+      for (int j = m.sf_ptr[4 * k + s]; j < m.sf_ptr[4 * k + s + 1]; ++j) {
+        const auto& f = m.sf[j];
+        if (f.nb >= 0) continue;
+        const double xc = cc * m.lh, xt0 = f.t0 * m.lh, xt1 = f.t1 * m.lh;
+        X.resize(2 * q);
+        x.resize(2 * q);
+        J.resize(4 * q);
+        for (int g = 0; g < q; ++g) {
+          const double Xt = xt0 + (xt1 - xt0) * rx[g];
+          X[2 * g] = s < 2 ? xc : Xt;
+          X[2 * g + 1] = s < 2 ? Xt : xc;
+        }
+        map(q, X.data(), x.data(), J.data());
+        M->h_boff[j] = (int64_t)M->h_xbnd.size();
+        for (int g = 0; g < q; ++g) {
+          const double* jj = &J[4 * g];
+          const double tx = s < 2 ? jj[1] : jj[0], ty = s < 2 ? jj[3] : jj[2];
+          const double det = jj[0] * jj[3] - jj[1] * jj[2];
+          double nx, ny;
+          if (s < 2) { nx = so * jj[3]; ny = -so * jj[1]; }
+          else { nx = -so * jj[2]; ny = so * jj[0]; }
+          const double nl = std::sqrt(nx * nx + ny * ny);
+          nx /= nl;
+          ny /= nl;
+          M->h_xbnd.push_back(x[2 * g]);
+          M->h_xbnd.push_back(x[2 * g + 1]);
+          M->h_xbnd.push_back(rw[g] * (xt1 - xt0) * std::sqrt(tx * tx + ty * ty));
+          M->h_xbnd.push_back((jj[3] * nx - jj[1] * ny) / det);
+          M->h_xbnd.push_back((jj[0] * ny - jj[2] * nx) / det);
+        }
+      }
+    }
 }
 
 void map_stats(dg_mesh* M) {

@@ -156,7 +156,8 @@ def test_curved_input_checks(built_lib):
 def test_host_load_matches_oracle(built_lib):
     """The library's load vector of caller-supplied f and weakly imposed
     Dirichlet data g (host_load) against the oracle's dirichlet_load, on a
-    hanging hp mesh with a coefficient; f alone on a curved mesh."""
+    hanging hp mesh with a coefficient, on a mapped quadrilateral and on
+    curved elements (f alone and with g)."""
     from oracle import rhs as R
     B = built_lib
     f = lambda x: np.sin(3 * x[:, 0]) * np.exp(x[:, 1])
@@ -166,15 +167,20 @@ def test_host_load_matches_oracle(built_lib):
     hs = B.HostSetup(mesh, B.make_options(), amg=False)
     ref = R.dirichlet_load(prob.space, f, g, 100.0)
     assert np.abs(hs.rhs_eval(f, g) - ref).max() <= 1e-12 * np.abs(ref).max()
-    md = inputs.with_mapping(inputs.small_hp_mesh(5, base=3, depth=2, prob=0.5, pmax=5), inputs.WavyMap())
-    prob = solver.build_problem(md)
-    hs = B.HostSetup(md, B.make_options(), amg=False)
-    ref = R.load_vector_fn(prob.space, f)
-    assert np.abs(hs.rhs_eval(f, None) - ref).max() <= 1e-12 * np.abs(ref).max()
-    with pytest.raises(B.DGError):
-        hs.rhs_eval(f, g)   # boundary data on a mapped mesh
+    base = inputs.small_hp_mesh(5, base=3, depth=2, prob=0.5, pmax=5)
+    for md in (inputs.with_mapping(base, inputs.WavyMap()),
+               inputs.with_corners(_coef(base, 3), inputs.QUADRILATERAL)):
+        prob = solver.build_problem(md)
+        hs = B.HostSetup(md, B.make_options(), amg=False)
+        ref = R.load_vector_fn(prob.space, f)
+        assert np.abs(hs.rhs_eval(f, None) - ref).max() <= 1e-12 * np.abs(ref).max()
+        ref = R.dirichlet_load(prob.space, f, g, 100.0)
+        assert np.abs(hs.rhs_eval(f, g) - ref).max() <= 1e-12 * np.abs(ref).max()
     with pytest.raises(B.DGError):
         hs.rhs_eval(lambda x: x[:, 5], None)   # a failing callback
+    hb = B.HostSetup(md, B.make_options(form=B.DG_FORM_BR2), amg=False)
+    with pytest.raises(B.DGError):
+        hb.rhs_eval(f, g)   # boundary data: SIPG only
 
 
 def test_mapped_cubes_refused(built_lib):
