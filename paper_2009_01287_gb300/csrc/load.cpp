@@ -7,7 +7,8 @@
 // boundary sub-face.  Mapped meshes take the images and det J of the volume
 // points and, on boundary sub-faces, the images, the weights with the arc
 // length and m = J^-1 n stored when the mesh was made (grad phi . n =
-// grad_X phi . m, grad_X the pre-image gradient).
+// grad_X phi . m, grad_X the pre-image gradient).  The callbacks' outputs are
+// NaN before each call, so values a callback leaves unwritten are reported.
 #include <cmath>
 #include <vector>
 
@@ -35,7 +36,7 @@ void host_load(const dg_mesh& M, dg_field_fn f, dg_field_fn g, void* ctx, double
     const double* dv = (s & 1) ? B.d1.data() : B.d0.data();
     std::vector<double> rx, rw;
     gauss_rule(q, rx, rw);
-    std::vector<double> Ls((size_t)q * NP), Ds((size_t)q * NP), pts(2 * (size_t)q), gv(q, 0.0);
+    std::vector<double> Ls((size_t)q * NP), Ds((size_t)q * NP), pts(2 * (size_t)q), gv(q, std::nan(""));
     const double* geo = M.h_xbnd.data() + M.h_boff[j];
     for (int r = 0; r < q; ++r) {
       const double t = ((sf.t0 - t0) + (sf.t1 - sf.t0) * rx[r]) / (double)m.size[k];
@@ -75,7 +76,7 @@ void host_load(const dg_mesh& M, dg_field_fn f, dg_field_fn g, void* ctx, double
     for (int r = 0; r < q; ++r) lagrange_eval(B.nodes, gx[r], &L[(size_t)r * NP]);
     if (f) {
       X.resize(2 * (size_t)q * q);
-      val.assign((size_t)q * q, 0.0);
+      val.assign((size_t)q * q, std::nan(""));
       std::vector<double> det((size_t)q * q, 1.0);
       for (int gy = 0; gy < q; ++gy)
         for (int gxi = 0; gxi < q; ++gxi) {
@@ -117,7 +118,7 @@ void host_load(const dg_mesh& M, dg_field_fn f, dg_field_fn g, void* ctx, double
         }
         const double len = (sf.t1 - sf.t0) * m.lh;
         X.resize(2 * (size_t)q);
-        val.assign(q, 0.0);
+        val.assign(q, std::nan(""));
         std::vector<double> Ls((size_t)q * NP);
         for (int r = 0; r < q; ++r) {
           const double t = (sf.t0 + (sf.t1 - sf.t0) * gx[r]) * m.lh;

@@ -194,3 +194,18 @@ def test_mapped_cubes_refused(built_lib):
     with pytest.raises(B.DGError) as e:
         B.HostSetup(bad, B.make_options())
     assert e.value.code == B.DG_EUNSUPPORTED
+
+
+def test_load_callback_that_writes_nothing_is_reported(built_lib):
+    """A C callback that leaves its outputs unwritten: the library pre-fills
+    them with NaN and reports DG_EINVAL instead of using stale values."""
+    B = built_lib
+    L = B.inspect_lib()
+    silent = B.DgFieldFn(lambda n, x, out, ctx: None)
+    for mesh in (inputs.uniform_mesh(2, 2, 2), inputs.with_mapping(inputs.uniform_mesh(2, 2, 2), inputs.WavyMap())):
+        hs = B.HostSetup(mesh, B.make_options(), amg=False)
+        b = np.zeros(hs.n)
+        assert L.dginspect_rhs_eval(hs.h, silent, B.DgFieldFn(), None, b.ctypes.data) != 0
+        assert L.dginspect_rhs_eval(hs.h, B.DgFieldFn(), silent, None, b.ctypes.data) != 0
+        assert L.dginspect_rhs_eval(hs.h, B.DgFieldFn(), B.DgFieldFn(), None, b.ctypes.data) == 0
+        assert not b.any()
