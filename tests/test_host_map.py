@@ -209,3 +209,32 @@ def test_load_callback_that_writes_nothing_is_reported(built_lib):
         assert L.dginspect_rhs_eval(hs.h, B.DgFieldFn(), silent, None, b.ctypes.data) != 0
         assert L.dginspect_rhs_eval(hs.h, B.DgFieldFn(), B.DgFieldFn(), None, b.ctypes.data) == 0
         assert not b.any()
+
+
+# ---------------------------------------------------------------- mapped domains with holes
+HOLED = [
+    ("lshape-quad", lambda: inputs.with_corners(
+        inputs.lshape(inputs.small_hp_mesh(8, base=4, depth=3, prob=0.4, pmax=6)), inputs.QUADRILATERAL)),
+    ("lshape-wavy", lambda: inputs.with_mapping(
+        inputs.lshape(inputs.small_hp_mesh(7, base=4, depth=2, prob=0.5, pmax=5)), inputs.WavyMap())),
+]
+
+
+@pytest.mark.parametrize("form", ["sipg", "br2"])
+@pytest.mark.parametrize("name,mk", HOLED, ids=[c[0] for c in HOLED])
+def test_host_setup_matches_oracle_mapped_holes(built_lib, name, mk, form):
+    """L-shaped lattices (a hole) carried by the bilinear and the curved map:
+    the boundary sub-faces along the hole take the mapped face factors."""
+    test_host_setup_matches_oracle_mapped(built_lib, name, mk, form=form)
+
+
+@pytest.mark.parametrize("name,mk", HOLED, ids=[c[0] for c in HOLED])
+def test_host_load_mapped_holes(built_lib, name, mk):
+    from oracle import rhs as R
+    mesh = mk()
+    prob = solver.build_problem(mesh)
+    hs = built_lib.HostSetup(mesh, built_lib.make_options(), amg=False)
+    f = lambda x: np.cos(2 * x[:, 0]) + x[:, 1]
+    g = lambda x: np.hypot(x[:, 0] - 0.5, x[:, 1] - 0.5) ** (2.0 / 3.0)
+    ref = R.dirichlet_load(prob.space, f, g, 100.0)
+    assert np.abs(hs.rhs_eval(f, g) - ref).max() <= 1e-12 * np.abs(ref).max()
